@@ -1,0 +1,209 @@
+"""Contraction plans for circuit tensor networks (input generation only).
+
+A plan is the pair (order, sliced): a pairwise contraction order in SSA form
+and a list of bond indices to slice.  The paper treats finding both as the
+high-level challenge solved before any amplitude is computed (Sec. III-A);
+QuantEx uses FlowCutter tree decompositions for the order and the greedy
+"tree trimming" rule of Schutski et al. for the sliced bonds.  This module
+supplies stand-ins that produce valid plans for the synthetic workloads:
+
+* ``greedy_order``: repeatedly contract the pair of tensors sharing a bond
+  that minimises size(out) - size(A) - size(B), ties to the lowest SSA ids;
+  ``randomized_greedy`` perturbs that cost with seeded Gumbel noise and keeps
+  the best of several trials (a common way to improve on plain greedy).
+* ``tree_trim_slices``: the greedy slicing rule of Sec. III-A: slice a bond
+  that shrinks the largest intermediate; among those prefer the one in the
+  most largest intermediates, then the one in the most intermediates, then
+  the one saving the most total memory, then a seeded random choice.
+
+Only index bookkeeping lives here (which bond sits on which tensor); no
+tensor values are touched.  The network labelling below is the canonical
+one of the C-ABI (tensor ids: inputs, gates, outputs of closed qubits; bond
+ids: input wires 0..n-1, then each gate's output legs in creation order).
+"""
+from __future__ import annotations
+
+import heapq
+import math
+
+from .circuits import SplitMix64
+
+
+def network_legs(n_qubits: int, gate_qubits, open_mask=None):
+    """Canonical tensor legs.
+
+    Returns (legs, n_edges, open_edges): legs[t] is the list of bond ids on
+    tensor t in its storage order.  Inputs have [wire]; a one-qubit gate has
+    [out, in]; a two-qubit gate has [out0, out1, in0, in1]; outputs [wire].
+    """
+    if open_mask is None:
+        open_mask = [0] * n_qubits
+    wire = list(range(n_qubits))
+    legs = [[q] for q in range(n_qubits)]
+    ne = n_qubits
+    for qs in gate_qubits:
+        outs = []
+        for q in qs:
+            outs.append(ne)
+            ne += 1
+        legs.append(outs + [wire[q] for q in qs])
+        for q, e in zip(qs, outs):
+            wire[q] = e
+    open_edges = []
+    for q in range(n_qubits):
+        if open_mask[q]:
+            open_edges.append(wire[q])
+        else:
+            legs.append([wire[q]])
+    return legs, ne, open_edges
+
+
+def _greedy(legs, noise_rng=None, temperature=0.0, alpha=1.0):
+    n0 = len(legs)
+    sets = {i: frozenset(l) for i, l in enumerate(legs)}
+    owner = {}
+    for i, s in sets.items():
+        for e in s:
+            owner.setdefault(e, set()).add(i)
+
+    def cost(a, b):
+        sa, sb = sets[a], sets[b]
+        c = float((1 << len(sa ^ sb)) - alpha * ((1 << len(sa)) + (1 << len(sb))))
+        if noise_rng is not None and temperature > 0:
+            u = max(noise_rng.uniform(), 1e-300)
+            # Gumbel-perturbed log-size cost keeps the scale of large tensors comparable
+            c = math.copysign(math.log2(1 + abs(c)), c) - temperature * math.log(-math.log(u) + 1e-300)
+        return c
+
+    heap = []
+
+    def push_pairs(i):
+        nb = set()
+        for e in sets[i]:
+            nb |= owner[e]
+        nb.discard(i)
+        for j in nb:
+            a, b = (i, j) if i < j else (j, i)
+            heapq.heappush(heap, (cost(a, b), a, b))
+
+    for i in list(sets):
+        push_pairs(i)
+    order = []
+    nxt = n0
+    while len(sets) > 1:
+        pair = None
+        while heap:
+            c, a, b = heapq.heappop(heap)
+            if a in sets and b in sets:
+                pair = (a, b)
+                break
+        if pair is None:  # disconnected components: outer product of the two lowest ids
+            ids = sorted(sets)
+            pair = (ids[0], ids[1])
+        a, b = pair
+        out = sets[a] ^ sets[b]
+        for e in sets[a] | sets[b]:
+            owner[e].discard(a)
+            owner[e].discard(b)
+        del sets[a], sets[b]
+        sets[nxt] = out
+        for e in out:
+            owner[e].add(nxt)
+        order.append((a, b))
+        push_pairs(nxt)
+        nxt += 1
+    return order
+
+
+def greedy_order(legs):
+    """Deterministic greedy SSA order (see module docstring)."""
+    return _greedy(legs)
+
+
+def intermediates(legs, order):
+    """Bond sets of every tensor created by the plan, in step order."""
+    sets = [frozenset(l) for l in legs]
+    out = []
+    for a, b in order:
+        s = sets[a] ^ sets[b]
+        sets.append(s)
+        out.append(s)
+    return out
+
+
+def plan_cost(legs, order, sliced=()):
+    """(max rank, total flops per slice (8 M K N convention), total entries written) of a plan."""
+    sl = frozenset(sliced)
+    sets = [frozenset(l) - sl for l in legs]
+    max_rank = 0
+    flops = 0
+    for a, b in order:
+        sa, sb = sets[a], sets[b]
+        shared = sa & sb
+        out = sa ^ sb
+        m, k, n = len(sa - shared), len(shared), len(sb - shared)
+        flops += 8 * (1 << (m + k + n))
+        max_rank = max(max_rank, len(out))
+        sets.append(out)
+    return max_rank, flops
+
+
+def tree_trim_slices(legs, order, n_slice, seed=0, open_edges=()):
+    """Greedy tree-trimming choice of n_slice bonds to slice (Sec. III-A)."""
+    rng = SplitMix64(seed)
+    inter = intermediates(legs, order)
+    open_set = frozenset(open_edges)
+    sliced = []
+    for _ in range(n_slice):
+        sl = frozenset(sliced)
+        ranks = [len(s - sl) for s in inter]
+        # the largest intermediates that still hold a sliceable bond
+        cands = set()
+        for rmax in sorted(set(ranks), reverse=True):
+            largest = [s - sl for s, r in zip(inter, ranks) if r == rmax]
+            for s in largest:
+                cands |= s
+            cands -= open_set
+            if cands:
+                break
+        if not cands:
+            raise ValueError("no bond left to slice")
+        best = None
+        for e in sorted(cands):
+            k1 = sum(1 for s in largest if e in s)
+            k2 = sum(1 for s in inter if e in s and e not in sl)
+            k3 = sum(1 << (r - 1) for s, r in zip(inter, ranks) if e in s)
+            key = (k1, k2, k3, rng.next_u64())
+            if best is None or key > best[0]:
+                best = (key, e)
+        sliced.append(best[1])
+    return sliced
+
+
+def randomized_greedy(legs, trials, seed, n_slice=0, open_edges=(), settings=((1.0, 0.6), (0.75, 0.3),
+                      (0.75, 0.6), (0.5, 0.6), (0.25, 0.3)), keep=6):
+    """Best plan over seeded Gumbel-perturbed greedy orders.
+
+    Each (alpha, temperature) setting runs `trials` orders with the cost
+    size(out) - alpha (size(A) + size(B)); the `keep` cheapest orders by
+    unsliced flops are then sliced by tree trimming and the plan with the
+    fewest flops after slicing (then the smallest peak) wins.  The
+    deterministic greedy order is always a candidate.
+    """
+    rng = SplitMix64(seed)
+    cands = [(plan_cost(legs, o)[1], 0, o) for o in [_greedy(legs)]]
+    k = 1
+    for alpha, temp in settings:
+        for _ in range(trials):
+            o = _greedy(legs, rng, temp, alpha)
+            cands.append((plan_cost(legs, o)[1], k, o))
+            k += 1
+    cands.sort(key=lambda c: (c[0], c[1]))
+    best = None
+    for flops0, k, order in cands[:keep]:
+        sliced = tree_trim_slices(legs, order, n_slice, seed + k, open_edges) if n_slice else []
+        peak, flops = plan_cost(legs, order, sliced)
+        key = (flops, peak, k)
+        if best is None or key < best[0]:
+            best = (key, order, sliced)
+    return best[1], best[2]

@@ -1,0 +1,131 @@
+"""The five synthetic workloads (seeded circuits, bitstrings and plans).
+
+Seeds: circuit seed = 1000 * config + j (j = circuit number within the
+config), bitstring seed = circuit seed + 500000, slicer / planner seed =
+circuit seed + 700000.  The paper's own workloads are the Boixo random
+circuits on qubit grids (Sec. IV-B); these seeded circuits stand in for them.
+
+* small:   3x4 grid, depth 8, <0...0| and 16 random bitstrings, greedy plan,
+           no slicing.
+* sliced:  4x5 grid, depth 12, 6 sliced bonds (64 slices), 256 bitstrings.
+* large:   6x6 grid, depth 14, 10 sliced bonds (1024 slices), qubits 30..35
+           left open (64 amplitudes per contraction), peak <= 2^28 entries.
+* batched: 256 circuits, n ~ U{16..28} on near-square grids, depth ~ U{8..16},
+           S ~ U{0..8}, 1..64 bitstrings each.
+* serving: 32 circuits, n ~ U{20..40}, depth ~ U{10..16}, plans sliced until
+           the peak intermediate fits 8 GB of complex64 (2^30 entries).
+"""
+from __future__ import annotations
+
+import functools
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from .circuits import (Circuit, SplitMix64, gates_to_records, near_square_shape, random_bitstrings,
+                       random_grid_circuit)
+from .plan import (greedy_order, network_legs, plan_cost, randomized_greedy, tree_trim_slices)
+
+
+@dataclass
+class Workload:
+    name: str
+    circuit: Circuit
+    open_mask: np.ndarray
+    order: list
+    sliced: list
+    bitstrings: np.ndarray
+    peak_rank: int = 0
+    flops_per_slice: int = 0
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def n_qubits(self):
+        return self.circuit.n_qubits
+
+    @property
+    def gates(self):
+        return gates_to_records(self.circuit)
+
+    @property
+    def n_open(self):
+        return int(np.sum(self.open_mask))
+
+    @property
+    def n_slices(self):
+        return 1 << len(self.sliced)
+
+    def order_array(self):
+        return np.asarray(self.order, dtype=np.int64).reshape(-1, 2)
+
+    def sliced_array(self):
+        return np.asarray(self.sliced, dtype=np.int64)
+
+
+def make_plan(circ: Circuit, open_mask, n_slice, seed, trials=0, peak_rank=None, keep=12):
+    legs, _, open_edges = network_legs(circ.n_qubits, [g.qubits for g in circ.gates], open_mask)
+    if trials:
+        order, sliced = randomized_greedy(legs, trials, seed, n_slice, open_edges, keep=keep)
+    else:
+        order = greedy_order(legs)
+        sliced = tree_trim_slices(legs, order, n_slice, seed, open_edges) if n_slice else []
+    if peak_rank is not None:
+        # keep slicing until the largest intermediate fits
+        while plan_cost(legs, order, sliced)[0] > peak_rank:
+            sliced = tree_trim_slices(legs, order, len(sliced) + 1, seed, open_edges)
+    peak, flops = plan_cost(legs, order, sliced)
+    return order, sliced, peak, flops
+
+
+def _workload(name, circ, open_mask, n_slice, cseed, bits, trials=0, peak_rank=None, meta=None):
+    order, sliced, peak, flops = make_plan(circ, open_mask, n_slice, cseed + 700000, trials, peak_rank)
+    return Workload(name, circ, np.asarray(open_mask, np.uint8), order, sliced, bits, peak, flops, meta or {})
+
+
+@functools.lru_cache(maxsize=None)
+def small():
+    cseed = 1001
+    circ = random_grid_circuit(3, 4, 8, cseed)
+    bits = np.concatenate([np.zeros((1, 12), np.uint8), random_bitstrings(12, 16, cseed + 500000)])
+    return _workload("grid3x4_d8_amp17", circ, np.zeros(12, np.uint8), 0, cseed, bits)
+
+
+@functools.lru_cache(maxsize=None)
+def sliced():
+    cseed = 2001
+    circ = random_grid_circuit(4, 5, 12, cseed)
+    bits = random_bitstrings(20, 256, cseed + 500000)
+    return _workload("grid4x5_d12_s6_amp256", circ, np.zeros(20, np.uint8), 6, cseed, bits)
+
+
+@functools.lru_cache(maxsize=None)
+def large():
+    cseed = 3001
+    circ = random_grid_circuit(6, 6, 14, cseed)
+    om = np.zeros(36, np.uint8)
+    om[30:] = 1
+    bits = random_bitstrings(36, 1, cseed + 500000)
+    return _workload("grid6x6_d14_s10_open6", circ, om, 10, cseed, bits, trials=64, peak_rank=28)
+
+
+def batched_specs(count=256):
+    """Per-circuit (n, depth, n_slice, n_bits) draws of the batched workload."""
+    rng = SplitMix64(4000)
+    specs = []
+    for j in range(count):
+        n = 16 + rng.randint(13)
+        depth = 8 + rng.randint(9)
+        s = rng.randint(9)
+        nb = 1 + rng.randint(64)
+        specs.append((n, depth, s, nb))
+    return specs
+
+
+def batched_circuit(j, spec=None):
+    n, depth, s, nb = spec or batched_specs()[j]
+    cseed = 4000 + j
+    rows, cols = near_square_shape(n)
+    circ = random_grid_circuit(rows, cols, depth, cseed, n=n)
+    bits = random_bitstrings(n, nb, cseed + 500000)
+    return _workload(f"batched{j}_n{n}_d{depth}_s{s}", circ, np.zeros(n, np.uint8), s, cseed, bits,
+                     trials=4, meta={"n": n, "depth": depth})
