@@ -1,0 +1,356 @@
+#!/usr/bin/env python
+"""Throughput of sliced circuit tensor-network contraction on GB300.
+
+Default workload: the 20-qubit 4x5 grid circuit of depth 12 with 6 sliced
+bonds (64 slices, each contracted and summed in FP64) for 256 random
+bitstrings, complex64.  One step = one full contraction of that workload
+(every slice for every bitstring) from device-resident bitstrings to
+device-resident complex128 amplitudes.
+
+Prints one JSON line (rank 0).  `--impl reference` times the CPU oracle on a
+bounded sample of the same workload instead.  Under torchrun each rank
+contracts its own 256 bitstrings (weak scaling, no data-path collective).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from qxgen import circuits as C  # noqa: E402
+from qxgen import workloads as W  # noqa: E402
+
+L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default="sliced", choices=["small", "sliced", "large"])
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+def workload(name):
+    return {"small": W.small, "sliced": W.sliced, "large": W.large}[name]()
+
+
+def rank_bits(w, rank):
+    if rank == 0:
+        return w.bitstrings
+    return C.random_bitstrings(w.n_qubits, len(w.bitstrings), w.circuit.seed + 500000 + 7919 * rank)
+
+
+def config_of(w, extra=None):
+    cfg = {"workload": w.name, "n_qubits": w.n_qubits, "depth": w.circuit.depth,
+           "grid": f"{w.circuit.rows}x{w.circuit.cols}", "sliced_bonds": len(w.sliced), "slices": w.n_slices,
+           "bitstrings_per_gpu": int(len(w.bitstrings)), "open_qubits": w.n_open,
+           "amplitudes_per_gpu": int(len(w.bitstrings)) << w.n_open, "peak_entries": 1 << w.peak_rank,
+           "plan": "seeded greedy (order) + tree trimming (slices)", "precision": "c64 (FP32 FMA), FP64 slice sum"}
+    cfg.update(extra or {})
+    return cfg
+
+
+# --------------------------------------------------------------------------------------------------
+# clocks during the timed region
+# --------------------------------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------------------------------
+# CPU oracle leg
+# --------------------------------------------------------------------------------------------------
+def cpu_oracle_sample(w, n_slices_sample):
+    """Time the einsum oracle on 1 bitstring x n_slices_sample slices; returns (amps/s, seconds)."""
+    from oracle import einsum as oe
+    t0 = time.perf_counter()
+    oe.amplitudes(w.n_qubits, w.gates, w.open_mask, w.order, w.sliced, w.bitstrings[:1],
+                  slices=range(n_slices_sample))
+    dt = time.perf_counter() - t0
+    amps = (n_slices_sample / w.n_slices) * (1 << w.n_open)
+    return amps / dt, dt
+
+
+def cpu_threads():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count()
+
+
+def sample_slices(w):
+    """Slices of one bitstring the oracle contracts per sample (a few seconds of host work)."""
+    return 1 if w.n_slices == 1 else 16 if w.n_slices == 64 else 2
+
+
+def reference_arm(args, w, rank, world):
+    if rank != 0:
+        return
+    ns = sample_slices(w)
+    for _ in range(args.warmup):
+        cpu_oracle_sample(w, ns)
+    times = []
+    for _ in range(args.steps):
+        _, dt = cpu_oracle_sample(w, ns)
+        times.append(dt)
+    amps_per_step = (ns / w.n_slices) * (1 << w.n_open)
+    value = amps_per_step * len(times) / sum(times)
+    sample = f"1 bitstring x {ns} of {w.n_slices} slices per step (complex128 numpy plan einsum)"
+    line = {"impl": "reference", "metric": "amplitudes/s", "value": value, "unit": "amplitudes/s", "n_gpus": 0,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
+            "config": config_of(w, {"sample": sample}),
+            "cpu_baseline": {"value": value, "unit": "amplitudes/s", "cores": cpu_threads(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "amplitudes/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------------------------------
+# our arm
+# --------------------------------------------------------------------------------------------------
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def traffic_for(kind):
+    """Per-launch DRAM bytes of a kernel kind from the committed ncu summary, if still current."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        import hashlib
+        src = os.path.join(ROOT, "paper_2110_09894_gb300", "csrc", d.get("source", ""))
+        with open(src, "rb") as f:
+            if hashlib.sha256(f.read()).hexdigest() != d.get("source_sha256"):
+                return None
+        return d.get("kernels", {}).get(kind, {}).get("dram_bytes_per_launch")
+    except (OSError, ValueError):
+        return None
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    w = workload(args.workload)
+    if args.impl == "reference":
+        reference_arm(args, w, rank, world)
+        return
+
+    import torch
+    from paper_2110_09894_gb300 import build as qxbuild
+    if rank == 0 or world == 1:
+        qxbuild.build()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        qxbuild.build()  # no-op once rank 0 built it
+    from paper_2110_09894_gb300 import qx
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream(dev)
+    bits = rank_bits(w, rank)
+    n_bits = len(bits)
+    amps_per_step = n_bits << w.n_open
+    with torch.cuda.stream(stream):
+        c = qx.Contractor(w.n_qubits, w.gates, w.open_mask, w.order, w.sliced, n_bits, device=local, stream=stream)
+        d_bits = torch.from_numpy(bits).to(dev)
+        d_amps = torch.empty((n_bits, 1 << w.n_open, 2), dtype=torch.float64, device=dev)
+        flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    ws_gb = c.workspace.numel() / 1e9
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    for _ in range(args.warmup):
+        c.contract_device(d_bits, d_amps)
+    stream.synchronize()
+    launches_per_step = c.stats()["launches"]
+    flops_exec = c.stats()["flops"]
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    sampler = ClockSampler(local)
+    barrier()
+    sampler.start()
+    t_wall = time.perf_counter()
+    for i in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(i & 0xFF)  # evict L2 between timed steps (outside the events)
+        ev[i][0].record(stream)
+        c.contract_device(d_bits, d_amps)
+        ev[i][1].record(stream)
+    barrier()
+    t_wall = time.perf_counter() - t_wall
+    clocks = sampler.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    my_ms = sum(step_ms)
+    t = torch.tensor([my_ms], dtype=torch.float64, device=dev)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    max_ms = float(t.item())
+    value = amps_per_step * world * args.steps / (max_ms / 1e3)
+    ms_per_step = max_ms / args.steps
+    # algorithmic complex flops of the plan: 8 M K N per step, for every (slice, bitstring) pair
+    flops_alg = float(w.flops_per_slice) * w.n_slices * n_bits
+    tflops = flops_alg * world * args.steps / (max_ms / 1e3) / 1e12
+
+    # per-kernel event timing over K more steps on the same stream
+    qx.qx_set_profiling(c.h, True)
+    for _ in range(args.steps):
+        c.contract_device(d_bits, d_amps)
+    prof = qx.qx_profile_read(c.h)
+    qx.qx_set_profiling(c.h, False)
+
+    # end to end through the public host API: pinned bitstrings in, pinned amplitudes out
+    h_bits = torch.from_numpy(bits).pin_memory()
+    h_amps = torch.empty((n_bits, 1 << w.n_open, 2), dtype=torch.float64).pin_memory()
+    c.contract_host_ptr(h_bits.data_ptr(), n_bits, h_amps.data_ptr())
+    barrier()
+    lat = []
+    t_e2e = time.perf_counter()
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        c.contract_host_ptr(h_bits.data_ptr(), n_bits, h_amps.data_ptr())
+        lat.append(time.perf_counter() - t0)
+    barrier()
+    t_e2e = time.perf_counter() - t_e2e
+    te = torch.tensor([t_e2e], dtype=torch.float64, device=dev)
+    if dist is not None:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e_value = amps_per_step * world * args.steps / float(te.item())
+
+    if rank != 0:
+        dist.destroy_process_group()
+        return
+
+    pk, pk_src = peaks()
+    dom = max(prof, key=lambda k: prof[k]["ms"])
+    d = prof[dom]
+    avg_ms = d["ms"] / max(d["launches"], 1)
+    if dom == "gemm":
+        clk = pk.get("sm_max_mhz", 2070.0)
+        n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+        peak = n_sm * 128 * 2 * clk * 1e6 / 1e12  # FP32 FMA lanes x 2 flops x clock
+        achieved = d["flops"] / (d["ms"] / 1e3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "peak_source": f"{n_sm} SMs x 128 FP32 lanes x 2 x {clk:.0f} MHz (max clock)"}
+    else:
+        peak = pk["hbm_gbs"]
+        achieved = d["bytes"] / (d["ms"] / 1e3) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "peak_source": f"hbm_gbs ({pk_src})"}
+    traffic = traffic_for(dom)
+    roof.update({"kernel": dom, "traffic": traffic, "avg_launch_ms": avg_ms,
+                 "algorithmic_per_launch": (d["flops"] if dom == "gemm" else d["bytes"]) / max(d["launches"], 1),
+                 "share_of_kernel_time": d["ms"] / max(sum(v["ms"] for v in prof.values()), 1e-12)})
+    kernels = {k: {"ms_per_step": v["ms"] / args.steps, "launches_per_step": v["launches"] / args.steps,
+                   "tflops": v["flops"] / max(v["ms"], 1e-12) / 1e9, "gbs": v["bytes"] / max(v["ms"], 1e-12) / 1e6}
+               for k, v in prof.items()}
+
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        ns = sample_slices(w)
+        v, dt = cpu_oracle_sample(w, ns)
+        cpu = {"value": v, "unit": "amplitudes/s", "cores": cpu_threads(), "kind": "oracle",
+               "sample": f"1 bitstring x {ns} of {w.n_slices} slices, complex128 numpy plan einsum, {dt:.1f} s"}
+        if w.n_qubits <= 26:
+            import oracle
+            t0 = time.perf_counter()
+            ref = oracle.sv_amplitudes(w.n_qubits, w.gates, w.open_mask, bits)
+            cpu["statevector_amplitudes_per_s"] = ref.size / (time.perf_counter() - t0)
+            got = d_amps.cpu().numpy()
+            got = got[..., 0] + 1j * got[..., 1]
+            cpu["rel_err_vs_oracle"] = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+
+    line = {"metric": "amplitudes/s", "value": value, "unit": "amplitudes/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "c64", "data": "synthetic",
+            "config": config_of(w, {"parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
+                                    "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MiB write); "
+                                          f"workspace {ws_gb:.1f} GB",
+                                    "batches_per_step": c.stats()["batches"]}),
+            "complex_tflops": tflops, "flops_per_step_algorithmic": flops_alg, "flops_per_step_executed": flops_exec,
+            "latency_ms": {"p50": 1e3 * float(np.percentile(lat, 50)), "p99": 1e3 * float(np.percentile(lat, 99))},
+            "roofline": roof, "kernels": kernels, "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": "amplitudes/s", "h2d_bytes_per_step": int(bits.nbytes),
+                    "d2h_bytes_per_step": int(h_amps.numel() * 8)},
+            "gpu_launches": int(launches_per_step * args.steps), "clocks": clocks, "wall_s_timed": t_wall}
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

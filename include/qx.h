@@ -1,0 +1,170 @@
+/*
+ * qx.h -- C ABI of libqx: sliced contraction of a quantum-circuit tensor
+ * network to output amplitudes on one GB300 (sm_103a).
+ *
+ * The calls follow the paper's statement of the problem (arXiv 2110.09894):
+ *   - build the tensor network of a circuit (Sec. II: |0> inputs, gate tensors
+ *     attached to the open legs of their qubits in circuit order, outputs
+ *     closed by <x_q| except on qubits left open);
+ *   - take a contraction plan: a pairwise order (Sec. III-A) and a set of
+ *     sliced bonds (Sec. III-A, Eq. 2);
+ *   - contract for a list of bitstrings to get amplitudes <x|C|0> (Sec. II),
+ *     summing the sliced sub-networks in FP64 with compensated summation.
+ *
+ * Canonical labels, so that a plan made elsewhere addresses this network:
+ *   tensor ids  0..n-1        input |0> of qubit q
+ *               n..n+G-1      gates in list order
+ *               n+G..         one output <x_q| per CLOSED qubit, increasing q
+ *   bond ids    0..n-1        the input wires
+ *               n..           each gate's output legs in creation order
+ *                             (gate g on (q0,q1) creates q0's leg, then q1's)
+ *   plan        order[t] = {i, j}: step t contracts tensors i and j (each id
+ *               used once) into the new tensor with id N_tensors + t; a full
+ *               plan has N_tensors - 1 steps.
+ *   slices      slice s fixes sliced[j] to bit j of s, s in [0, 2^n_sliced).
+ *
+ * Amplitude layout: out[b][o] (complex128 as {re, im} doubles) for bitstring
+ * b and open-qubit assignment o, the first open qubit (lowest qubit index)
+ * being the most significant bit of o.  Bit order of a state: qubit 0 is the
+ * most significant bit; a bitstring is n bytes, byte q = value of qubit q.
+ *
+ * Memory and streams: every device buffer the library touches is either
+ * caller-owned (qx_bind_workspace, qx_contract_device) or, only when the
+ * caller passes NULL to qx_bind_workspace, allocated once there.  No
+ * call allocates inside qx_contract / qx_contract_device.  All device work
+ * is issued on the stream given to qx_create (NULL = legacy default stream).
+ *
+ * Errors: every int-returning call gives QX_OK (0) or a negative code and
+ * leaves a message for qx_last_error; on error no partial result is written.
+ * Handles are not thread-safe: one host thread drives a handle at a time.
+ */
+#ifndef QX_H
+#define QX_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define QX_OK        0
+#define QX_EINVAL   -1  /* malformed circuit, plan, bitstring or argument */
+#define QX_ENOMEM   -2  /* the bound workspace is too small for the request */
+#define QX_ECUDA    -3  /* a CUDA runtime call or kernel launch failed */
+#define QX_ETIMEOUT -4  /* a bounded device wait expired */
+#define QX_ESTATE   -5  /* call out of order (e.g. contract before plan) */
+
+/* Precision forms of the contraction (the cross-slice sum is always FP64). */
+#define QX_PREC_C64         0  /* complex64 operands, FP32 FMA (plain form)   */
+#define QX_PREC_3XTF32      1  /* tcgen05 TF32, 3-product compensated split   */
+#define QX_PREC_SPLIT_BF16  2  /* tcgen05 BF16, 3-way split, 6 products       */
+#define QX_PREC_FP16_SCALED 3  /* tcgen05 FP16 with per-tensor power-2 scale  */
+
+typedef struct qx_ctx* qx_handle;
+
+/* One gate: nq = 1 or 2 target qubits q[0] (, q[1]); explicit unitary,
+ * row-major, 2x2 or 4x4 in the basis |q0 q1> (row = 2*b(q0) + b(q1)).
+ * Entries beyond nq's matrix are ignored.  272 bytes. */
+typedef struct {
+    int32_t nq;
+    int32_t q[2];
+    int32_t pad;
+    double re[16];
+    double im[16];
+} qx_gate;
+
+typedef struct {
+    int32_t precision;       /* QX_PREC_*                                     */
+    int32_t max_items;       /* (slice, bitstring) pairs per batch; 0 = fill  */
+    int32_t gemm_min_bits;   /* steps with k, m, n >= this run as GEMM; 0 = 5 */
+    int32_t reserved;
+    int64_t timeout_cycles;  /* bound on device spin-waits; 0 = default      */
+} qx_options;
+
+/* Create a handle on CUDA device `device`; `cuda_stream` is a cudaStream_t
+ * (may be NULL).  device = -1 gives a host-only handle that can build
+ * networks, check plans and size workspaces but not contract.  opt may be
+ * NULL for defaults.  *h is owned by the caller and released by qx_destroy.
+ * QX_ECUDA for a device that does not exist, QX_EINVAL for bad options. */
+int qx_create(qx_handle* h, int device, void* cuda_stream, const qx_options* opt);
+void qx_destroy(qx_handle h);
+const char* qx_last_error(qx_handle h);
+int qx_set_options(qx_handle h, const qx_options* opt);
+
+/* Build the network of a circuit (Sec. II).  gates: n_gates records, host
+ * memory, copied.  open_mask: n_qubits bytes, 1 = leave that qubit's output
+ * leg open (may be NULL = all closed).  Drops any previous plan.
+ * QX_EINVAL on qubit indices out of range or nq not in {1, 2}. */
+int qx_build_network(qx_handle h, int32_t n_qubits, const qx_gate* gates, int64_t n_gates,
+                     const uint8_t* open_mask);
+
+/* Number of tensors and bonds of the built network (for plan makers). */
+int qx_network_info(qx_handle h, int64_t* n_tensors, int64_t* n_bonds);
+
+/* Set the contraction plan (Sec. III-A): order = n_steps x 2 SSA ids (host,
+ * copied), sliced = n_sliced bond ids (host, copied; each must join two
+ * tensors and must not be the final wire of a qubit).  *peak_entries_out
+ * (may be NULL) receives the largest intermediate of one slice in complex
+ * entries.  QX_EINVAL on a malformed plan. */
+int qx_set_plan(qx_handle h, const int64_t* order, int64_t n_steps, const int64_t* sliced,
+                int32_t n_sliced, int64_t* peak_entries_out);
+
+/* Device bytes a workspace needs to contract up to max_bits bitstrings per
+ * call with batches of `items` (slice, bitstring) pairs (items <= 0: one
+ * pair).  Requires a plan. */
+int qx_workspace_size(qx_handle h, int64_t max_bits, int64_t items, int64_t* bytes_out);
+
+/* Bind device memory (256-byte aligned) of `bytes` bytes as the workspace for
+ * calls of up to max_bits bitstrings; batches are sized to fill it.  The
+ * caller keeps ownership and must keep it alive until the next bind or
+ * qx_destroy.  dptr = NULL asks the library to cudaMalloc `bytes` itself
+ * (freed on the next bind or by qx_destroy).  Requires a plan; setting a new
+ * plan unbinds.  QX_ENOMEM if not even one pair fits. */
+int qx_bind_workspace(qx_handle h, void* dptr, int64_t bytes, int64_t max_bits);
+
+/* Contract for n_bits bitstrings (host, n_bits x n_qubits bytes of 0/1; bytes
+ * at open qubits are ignored) and write amplitudes to amps_out (host,
+ * caller-owned, n_bits x 2^n_open x {re, im} doubles).  Copies the
+ * bitstrings to the device, runs every slice, copies the result back and
+ * synchronises the stream.  QX_EINVAL on a non-0/1 byte, QX_ENOMEM when
+ * n_bits exceeds what the workspace was sized for. */
+int qx_contract(qx_handle h, const uint8_t* bitstrings, int64_t n_bits, double* amps_out);
+
+/* As qx_contract, but both buffers are device memory and the call only
+ * enqueues work on the stream (no synchronisation, no host copies).
+ * Bitstring bytes are not validated on this path. */
+int qx_contract_device(qx_handle h, const uint8_t* d_bitstrings, int64_t n_bits, double* d_amps_out);
+
+/* Partial sums for multi-process slice sharding (Sec. IV-A: slices are
+ * balanced over processes and recombined): as qx_contract /
+ * qx_contract_device, but only slices s in [s_begin, s_end) are contracted
+ * and summed (FP64, compensated).  QX_EINVAL for an empty or out-of-range
+ * slice range. */
+int qx_contract_slices(qx_handle h, const uint8_t* bitstrings, int64_t n_bits, int64_t s_begin, int64_t s_end,
+                       double* amps_out);
+int qx_contract_slices_device(qx_handle h, const uint8_t* d_bitstrings, int64_t n_bits, int64_t s_begin,
+                              int64_t s_end, double* d_amps_out);
+
+/* Statistics of the last contraction (host values, any pointer may be NULL):
+ * algorithmic complex flops (8 M K N per step, per pair), kernel launches,
+ * batches. */
+int qx_last_stats(qx_handle h, double* flops, int64_t* launches, int64_t* batches);
+
+/* Kernel timing for roofline reports.  With profiling on, every kernel launch
+ * of a contraction is bracketed by CUDA events on the handle's stream;
+ * qx_profile_read synchronises the stream and returns, for one kernel kind,
+ * the summed event time (ms), launches, algorithmic complex flops (8 M K N
+ * per pair) and algorithmic bytes (operands read once, result written once)
+ * since profiling was last switched.  qx_set_profiling resets the totals. */
+#define QX_KERNEL_PERMUTE 0
+#define QX_KERNEL_SMALL   1
+#define QX_KERNEL_GEMM    2
+#define QX_KERNEL_SUM     3
+#define QX_KERNEL_KINDS   4
+int qx_set_profiling(qx_handle h, int enable);
+int qx_profile_read(qx_handle h, int kind, double* ms, int64_t* launches, double* flops, double* bytes);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* QX_H */

@@ -1,0 +1,1002 @@
+// Host side of libqx: the circuit network (Sec. II), plan validation and
+// compilation (Sec. III-A order and slicing), the workspace plan, and the
+// batched executor that drives the kernels in qx_kernels.cu.
+//
+// Execution model.  The contraction of every (slice, bitstring) pair follows
+// the same plan, so the pairs of a batch are contracted together: each plan
+// step is one kernel launch over all pairs of the batch (the slice-parallel
+// and bitstring-parallel levels of Sec. IV-A inside one launch).  Sliced
+// bonds and the closed output wires are "fixed" bonds: a leaf tensor touching
+// one is read at the offset that the pair's slice bit or bitstring byte
+// selects, so slicing never copies data.  Intermediates that depend on no
+// fixed bond are the same for every pair; they are computed once per call
+// (prologue) and read by every pair with item stride 0.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <limits>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "qx.h"
+#include "qx_internal.h"
+
+using namespace qx;
+
+namespace {
+
+constexpr int64_t kAlignEntries = 32;  // 256 bytes
+constexpr int64_t kLive = std::numeric_limits<int64_t>::max() / 4;
+
+int64_t align_up(int64_t v, int64_t a) { return (v + a - 1) / a * a; }
+
+struct Node {
+    std::vector<int> legs;  // bond ids, leg 0 most significant
+    std::vector<int> pos;   // address bit of each leg
+    std::vector<std::pair<int32_t, int64_t>> fix;  // (source, stride) of fixed legs
+    bool const_one = false;
+    bool variant = false;
+    bool leaf = false;
+    int64_t leaf_off = 0;   // entries into the leaf buffer
+    int storage = -1;       // intermediate storage id
+    int under_rank = 0;     // rank of the stored tensor
+};
+
+struct Storage {
+    int64_t entries = 0;
+    bool variant = false;
+    int64_t def = 0, last = 0;
+    int64_t off = 0;        // entries within its region (per pair for the item region)
+};
+
+enum OpType { OP_PERM, OP_SMALL, OP_GEMM };
+
+struct Op {
+    OpType type;
+    bool variant;
+    int64_t step;
+    // OP_PERM: node -> storage
+    int src = -1;
+    std::vector<int> target_legs;
+    // OP_SMALL: x, y nodes
+    int x = -1, y = -1;
+    std::vector<int> shared;
+    // OP_GEMM: operand storages, shapes
+    int sa = -1, sb = -1;
+    bool a_km = true, b_km = true;
+    int mb = 0, nb = 0, kb = 0;
+    int dst = -1;           // output storage
+    double flops = 0;
+};
+
+}  // namespace
+
+struct qx_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    qx_options opt{};
+    std::string err;
+
+    // network
+    bool have_net = false;
+    int nq = 0;
+    std::vector<qx_gate> gates;
+    std::vector<uint8_t> open_mask;
+    int64_t n_tensors = 0, n_bonds = 0;
+    std::vector<std::vector<int>> tensor_legs;   // canonical legs of each leaf tensor
+    std::vector<int64_t> tensor_vals_off;        // offset of its values in leaf_vals (-1: output)
+    std::vector<float2> leaf_vals;
+    std::vector<int> final_wire;                 // per qubit
+    std::vector<int> open_wires;                 // final wires of open qubits, increasing qubit
+    std::vector<int> bond_deg;                   // tensors touching each bond
+
+    // plan
+    bool have_plan = false;
+    std::vector<int64_t> sliced;
+    std::vector<Node> nodes;
+    std::vector<Storage> stor;
+    std::vector<Op> ops;
+    int root = -1;
+    int64_t peak_entries = 0;
+    int64_t item_entries = 0;  // per pair
+    int64_t inv_entries = 0;
+    int64_t n_slices = 1;
+    double flops_inv = 0, flops_item = 0;
+
+    // workspace
+    char* ws = nullptr;
+    int64_t ws_bytes = 0;
+    bool ws_owned = false;
+    int64_t max_bits = 0;
+    int64_t off_leaf = 0, off_bits = 0, off_acc = 0, off_amps = 0, off_inv = 0, off_item = 0;
+    int64_t items_cap = 0;
+    bool leaves_on_device = false;
+
+    // stats
+    double last_flops = 0;
+    int64_t last_launches = 0, last_batches = 0;
+
+    // profiling: an event pair around every launch, folded per kernel kind on read
+    bool profiling = false;
+    std::vector<cudaEvent_t> ev_pool;
+    size_t ev_used = 0;
+    struct Rec { int kind; size_t e0; double flops, bytes; };
+    std::vector<Rec> recs;
+    double prof_ms[QX_KERNEL_KINDS] = {0}, prof_flops[QX_KERNEL_KINDS] = {0}, prof_bytes[QX_KERNEL_KINDS] = {0};
+    int64_t prof_launches[QX_KERNEL_KINDS] = {0};
+};
+
+static int fail(qx_ctx* h, int code, const char* fmt, ...);
+
+static cudaError_t prof_begin(qx_ctx* h, int kind, double flops, double bytes, size_t* slot) {
+    *slot = SIZE_MAX;
+    if (!h->profiling) return cudaSuccess;
+    while (h->ev_used + 2 > h->ev_pool.size()) {
+        cudaEvent_t e;
+        cudaError_t r = cudaEventCreate(&e);
+        if (r != cudaSuccess) return r;
+        h->ev_pool.push_back(e);
+    }
+    *slot = h->ev_used;
+    h->ev_used += 2;
+    h->recs.push_back({kind, *slot, flops, bytes});
+    return cudaEventRecord(h->ev_pool[*slot], h->stream);
+}
+
+static cudaError_t prof_end(qx_ctx* h, size_t slot) {
+    if (slot == SIZE_MAX) return cudaSuccess;
+    return cudaEventRecord(h->ev_pool[slot + 1], h->stream);
+}
+
+// fold recorded event pairs into the per-kind totals (synchronises the stream)
+static int prof_collect(qx_ctx* h) {
+    if (h->recs.empty()) return QX_OK;
+    cudaError_t r = cudaStreamSynchronize(h->stream);
+    if (r != cudaSuccess) return fail(h, QX_ECUDA, "profile sync: %s", cudaGetErrorString(r));
+    for (const auto& rc : h->recs) {
+        float ms = 0;
+        r = cudaEventElapsedTime(&ms, h->ev_pool[rc.e0], h->ev_pool[rc.e0 + 1]);
+        if (r != cudaSuccess) return fail(h, QX_ECUDA, "profile events: %s", cudaGetErrorString(r));
+        h->prof_ms[rc.kind] += ms;
+        h->prof_flops[rc.kind] += rc.flops;
+        h->prof_bytes[rc.kind] += rc.bytes;
+        h->prof_launches[rc.kind] += 1;
+    }
+    h->recs.clear();
+    h->ev_used = 0;
+    return QX_OK;
+}
+
+static int fail(qx_ctx* h, int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    h->err = buf;
+    return code;
+}
+
+#define CUDA_TRY(h, expr)                                                                         \
+    do {                                                                                          \
+        cudaError_t e_ = (expr);                                                                  \
+        if (e_ != cudaSuccess) return fail(h, QX_ECUDA, "%s: %s", #expr, cudaGetErrorString(e_)); \
+    } while (0)
+
+// ------------------------------------------------------------------------------------------------
+// Network (Sec. II)
+// ------------------------------------------------------------------------------------------------
+static int build_network(qx_ctx* h, int32_t n, const qx_gate* gates, int64_t ng, const uint8_t* open_mask) {
+    if (n < 1 || n > 62) return fail(h, QX_EINVAL, "n_qubits %d out of range [1, 62]", n);
+    if (ng < 0 || (ng > 0 && !gates)) return fail(h, QX_EINVAL, "bad gate list");
+    for (int64_t g = 0; g < ng; ++g) {
+        const qx_gate& gt = gates[g];
+        if (gt.nq != 1 && gt.nq != 2) return fail(h, QX_EINVAL, "gate %lld: nq = %d", (long long)g, gt.nq);
+        for (int j = 0; j < gt.nq; ++j)
+            if (gt.q[j] < 0 || gt.q[j] >= n)
+                return fail(h, QX_EINVAL, "gate %lld: qubit %d out of range", (long long)g, gt.q[j]);
+        if (gt.nq == 2 && gt.q[0] == gt.q[1]) return fail(h, QX_EINVAL, "gate %lld: repeated qubit", (long long)g);
+    }
+    h->have_net = false;
+    h->have_plan = false;
+    h->nq = n;
+    h->gates.assign(gates, gates + ng);
+    h->open_mask.assign(n, 0);
+    if (open_mask)
+        for (int q = 0; q < n; ++q) h->open_mask[q] = open_mask[q] ? 1 : 0;
+    h->tensor_legs.clear();
+    h->tensor_vals_off.clear();
+    h->leaf_vals.clear();
+    std::vector<int> wire(n);
+    for (int q = 0; q < n; ++q) {
+        wire[q] = q;
+        h->tensor_legs.push_back({q});
+        h->tensor_vals_off.push_back((int64_t)h->leaf_vals.size());
+        h->leaf_vals.push_back(make_float2(1.f, 0.f));  // |0>
+        h->leaf_vals.push_back(make_float2(0.f, 0.f));
+    }
+    int next = n;
+    for (int64_t g = 0; g < ng; ++g) {
+        const qx_gate& gt = gates[g];
+        std::vector<int> legs;
+        for (int j = 0; j < gt.nq; ++j) legs.push_back(next++);
+        for (int j = 0; j < gt.nq; ++j) legs.push_back(wire[gt.q[j]]);
+        for (int j = 0; j < gt.nq; ++j) wire[gt.q[j]] = legs[j];
+        h->tensor_legs.push_back(legs);
+        h->tensor_vals_off.push_back((int64_t)h->leaf_vals.size());
+        const int d = gt.nq == 1 ? 2 : 4;
+        // T[o.., i..] = U[row(o), col(i)], row-major: entry index = row * d + col
+        for (int e = 0; e < d * d; ++e) h->leaf_vals.push_back(make_float2((float)gt.re[e], (float)gt.im[e]));
+    }
+    h->final_wire = wire;
+    h->open_wires.clear();
+    for (int q = 0; q < n; ++q) {
+        if (h->open_mask[q]) {
+            h->open_wires.push_back(wire[q]);
+        } else {
+            h->tensor_legs.push_back({wire[q]});
+            h->tensor_vals_off.push_back(-1);  // output <x_q|
+        }
+    }
+    h->n_tensors = (int64_t)h->tensor_legs.size();
+    h->n_bonds = next;
+    h->bond_deg.assign(next, 0);
+    for (auto& l : h->tensor_legs)
+        for (int e : l) h->bond_deg[e]++;
+    h->have_net = true;
+    h->leaves_on_device = false;
+    return QX_OK;
+}
+
+// ------------------------------------------------------------------------------------------------
+// Plan compilation
+// ------------------------------------------------------------------------------------------------
+static Operand make_operand(const qx_ctx* h, int node) {
+    const Node& nd = h->nodes[node];
+    Operand op{};
+    op.rank = (int32_t)nd.legs.size();
+    for (int j = 0; j < op.rank; ++j) op.pos[j] = (int8_t)nd.pos[j];
+    op.n_fix = (int32_t)nd.fix.size();
+    for (int f = 0; f < op.n_fix; ++f) {
+        op.fix_src[f] = nd.fix[f].first;
+        op.fix_stride[f] = nd.fix[f].second;
+    }
+    return op;
+}
+
+static int64_t node_entries(const Node& n) { return (int64_t)1 << n.legs.size(); }
+
+static int new_storage(qx_ctx* h, int64_t entries, bool variant, int64_t def) {
+    Storage s;
+    s.entries = entries;
+    s.variant = variant;
+    s.def = def;
+    s.last = def;
+    h->stor.push_back(s);
+    return (int)h->stor.size() - 1;
+}
+
+static void use_node(qx_ctx* h, int node, int64_t step) {
+    const Node& nd = h->nodes[node];
+    if (nd.storage >= 0) h->stor[nd.storage].last = std::max(h->stor[nd.storage].last, step);
+}
+
+static Node contiguous_node(const std::vector<int>& legs, bool variant, int storage) {
+    Node n;
+    n.legs = legs;
+    const int r = (int)legs.size();
+    n.pos.resize(r);
+    for (int j = 0; j < r; ++j) n.pos[j] = r - 1 - j;
+    n.variant = variant;
+    n.storage = storage;
+    n.under_rank = r;
+    return n;
+}
+
+// First-fit offsets for storages of one region (intervals [def, last] inclusive).
+static int64_t assign_offsets(qx_ctx* h, bool variant) {
+    std::vector<int> ids;
+    for (int i = 0; i < (int)h->stor.size(); ++i)
+        if (h->stor[i].variant == variant) ids.push_back(i);
+    std::sort(ids.begin(), ids.end(), [&](int a, int b) {
+        if (h->stor[a].def != h->stor[b].def) return h->stor[a].def < h->stor[b].def;
+        return a < b;
+    });
+    std::vector<int> placed;
+    int64_t top = 0;
+    for (int id : ids) {
+        Storage& s = h->stor[id];
+        const int64_t need = align_up(s.entries, kAlignEntries);
+        std::vector<std::pair<int64_t, int64_t>> busy;
+        for (int p : placed) {
+            const Storage& o = h->stor[p];
+            if (o.last >= s.def && s.last >= o.def) busy.push_back({o.off, o.off + align_up(o.entries, kAlignEntries)});
+        }
+        std::sort(busy.begin(), busy.end());
+        int64_t cand = 0;
+        for (auto& b : busy) {
+            if (cand + need <= b.first) break;
+            cand = std::max(cand, b.second);
+        }
+        s.off = cand;
+        top = std::max(top, cand + need);
+        placed.push_back(id);
+    }
+    return top;
+}
+
+static int compile_plan(qx_ctx* h, const int64_t* order, int64_t n_steps, const int64_t* sliced, int32_t n_sliced) {
+    const int64_t N = h->n_tensors;
+    if (n_steps != N - 1)
+        return fail(h, QX_EINVAL, "plan has %lld steps, a full contraction of %lld tensors needs %lld",
+                    (long long)n_steps, (long long)N, (long long)(N - 1));
+    if (n_sliced < 0 || n_sliced > 40) return fail(h, QX_EINVAL, "n_sliced %d out of range [0, 40]", n_sliced);
+    std::vector<int> fixsrc(h->n_bonds, INT32_MIN);  // source of each fixed bond
+    for (int j = 0; j < n_sliced; ++j) {
+        const int64_t e = sliced[j];
+        if (e < 0 || e >= h->n_bonds) return fail(h, QX_EINVAL, "sliced bond %lld out of range", (long long)e);
+        if (h->bond_deg[e] != 2) return fail(h, QX_EINVAL, "sliced bond %lld is open", (long long)e);
+        if (fixsrc[e] != INT32_MIN) return fail(h, QX_EINVAL, "sliced bond %lld repeated", (long long)e);
+        for (int q = 0; q < h->nq; ++q)
+            if (h->final_wire[q] == e)
+                return fail(h, QX_EINVAL, "sliced bond %lld is the final wire of qubit %d", (long long)e, q);
+        fixsrc[e] = j;
+    }
+    for (int q = 0; q < h->nq; ++q)
+        if (!h->open_mask[q]) fixsrc[h->final_wire[q]] = -(q + 1);
+
+    h->nodes.clear();
+    h->stor.clear();
+    h->ops.clear();
+    h->sliced.assign(sliced, sliced + n_sliced);
+    h->n_slices = (int64_t)1 << n_sliced;
+
+    // leaves
+    for (int64_t t = 0; t < N; ++t) {
+        Node nd;
+        nd.leaf = true;
+        if (h->tensor_vals_off[t] < 0) {
+            nd.const_one = true;  // <x_q| with its bond fixed to x_q is the scalar 1
+        } else {
+            const auto& L = h->tensor_legs[t];
+            const int R = (int)L.size();
+            nd.under_rank = R;
+            nd.leaf_off = h->tensor_vals_off[t];
+            for (int j = 0; j < R; ++j) {
+                const int p = R - 1 - j;
+                if (fixsrc[L[j]] != INT32_MIN) {
+                    nd.fix.push_back({fixsrc[L[j]], (int64_t)1 << p});
+                } else {
+                    nd.legs.push_back(L[j]);
+                    nd.pos.push_back(p);
+                }
+            }
+            nd.variant = !nd.fix.empty();
+        }
+        h->nodes.push_back(nd);
+    }
+    std::vector<char> used(N + n_steps, 0);
+    const int gemm_bits = h->opt.gemm_min_bits > 0 ? h->opt.gemm_min_bits : 5;
+    h->peak_entries = 1;
+    for (int64_t t = 0; t < n_steps; ++t) {
+        const int64_t ia = order[2 * t], ib = order[2 * t + 1];
+        if (ia < 0 || ib < 0 || ia >= N + t || ib >= N + t || ia == ib || used[ia] || used[ib])
+            return fail(h, QX_EINVAL, "plan step %lld uses an invalid or consumed id (%lld, %lld)", (long long)t,
+                        (long long)ia, (long long)ib);
+        used[ia] = used[ib] = 1;
+        const int a = (int)ia, b = (int)ib;
+        const Node A = h->nodes[a], B = h->nodes[b];
+        if (A.const_one || B.const_one) {  // contracting with a closed output is a re-labelling
+            Node c = A.const_one ? B : A;
+            use_node(h, a, t);
+            use_node(h, b, t);
+            h->nodes.push_back(c);
+            continue;
+        }
+        std::vector<int> shared, freeA, freeB;
+        for (int e : A.legs) {
+            if (std::find(B.legs.begin(), B.legs.end(), e) != B.legs.end()) shared.push_back(e);
+            else freeA.push_back(e);
+        }
+        for (int e : B.legs)
+            if (std::find(A.legs.begin(), A.legs.end(), e) == A.legs.end()) freeB.push_back(e);
+        const int kb = (int)shared.size();
+        const bool variant = A.variant || B.variant;
+        const int rc = (int)(freeA.size() + freeB.size());
+        if (rc > kMaxRank) return fail(h, QX_EINVAL, "step %lld: intermediate rank %d too large", (long long)t, rc);
+        h->peak_entries = std::max(h->peak_entries, (int64_t)1 << rc);
+        use_node(h, a, t);
+        use_node(h, b, t);
+
+        // gather path: one operand small enough for shared memory, few shared and free bits
+        int small_y = -1;
+        for (int cand : {0, 1}) {
+            const Node& Y = cand ? A : B;
+            const int ny = (int)(cand ? freeA.size() : freeB.size());
+            if (node_entries(Y) <= 1024 && kb <= kSmallMaxK && ny <= kSmallMaxN) {
+                if (small_y < 0 || node_entries(Y) < node_entries(small_y ? A : B)) small_y = cand;
+            }
+        }
+        const bool big_gemm = kb >= gemm_bits && (int)freeA.size() >= gemm_bits && (int)freeB.size() >= gemm_bits;
+        if (small_y >= 0 && !big_gemm) {
+            const int xn = small_y ? b : a, yn = small_y ? a : b;
+            const Node& X = h->nodes[xn];
+            const Node& Y = h->nodes[yn];
+            std::vector<int> fx, fy;
+            for (int e : X.legs)
+                if (std::find(shared.begin(), shared.end(), e) == shared.end()) fx.push_back(e);
+            for (int e : Y.legs)
+                if (std::find(shared.begin(), shared.end(), e) == shared.end()) fy.push_back(e);
+            std::vector<int> cl = fx;
+            cl.insert(cl.end(), fy.begin(), fy.end());
+            const int st = new_storage(h, (int64_t)1 << cl.size(), variant, t);
+            Op op{};
+            op.type = OP_SMALL;
+            op.variant = variant;
+            op.step = t;
+            op.x = xn;
+            op.y = yn;
+            op.shared = shared;
+            op.dst = st;
+            op.mb = (int)fx.size();
+            op.kb = kb;
+            op.nb = (int)fy.size();
+            op.flops = 8.0 * std::ldexp(1.0, op.mb + op.kb + op.nb);
+            h->ops.push_back(op);
+            h->nodes.push_back(contiguous_node(cl, variant, st));
+            continue;
+        }
+
+        // TTGT path: operands as matrices [M][K] / [K][M] and [N][K] / [K][N], C = [M][N]
+        auto contiguous_is = [&](const Node& X, const std::vector<int>& want) {
+            return !X.leaf && X.fix.empty() && X.legs == want;
+        };
+        struct Choice { std::vector<int> S; bool pa, pb, akm, bkm; double cost; };
+        std::vector<std::vector<int>> cands = {shared};
+        {
+            std::vector<int> sB;
+            for (int e : B.legs)
+                if (std::find(shared.begin(), shared.end(), e) != shared.end()) sB.push_back(e);
+            if (sB != shared) cands.push_back(sB);
+        }
+        Choice best{};
+        best.cost = -1;
+        for (auto& S : cands) {
+            Choice c{S, true, true, true, true, 0};
+            std::vector<int> ak = freeA, am = S, bk = freeB, bm = S;
+            ak.insert(ak.end(), S.begin(), S.end());
+            am.insert(am.end(), freeA.begin(), freeA.end());
+            bk.insert(bk.end(), S.begin(), S.end());
+            bm.insert(bm.end(), freeB.begin(), freeB.end());
+            if (contiguous_is(A, ak)) { c.pa = false; c.akm = true; }
+            else if (contiguous_is(A, am)) { c.pa = false; c.akm = false; }
+            if (contiguous_is(B, bk)) { c.pb = false; c.bkm = true; }
+            else if (contiguous_is(B, bm)) { c.pb = false; c.bkm = false; }
+            c.cost = (c.pa ? (double)node_entries(A) : 0.0) + (c.pb ? (double)node_entries(B) : 0.0);
+            if (best.cost < 0 || c.cost < best.cost) best = c;
+        }
+        Op g{};
+        g.type = OP_GEMM;
+        g.variant = variant;
+        g.step = t;
+        g.mb = (int)freeA.size();
+        g.nb = (int)freeB.size();
+        g.kb = kb;
+        g.a_km = best.akm;
+        g.b_km = best.bkm;
+        for (int side = 0; side < 2; ++side) {
+            const int nid = side ? b : a;
+            const bool perm = side ? best.pb : best.pa;
+            const std::vector<int>& fr = side ? freeB : freeA;
+            int sid;
+            if (perm) {
+                std::vector<int> tl = fr;
+                tl.insert(tl.end(), best.S.begin(), best.S.end());
+                const Node& X = h->nodes[nid];
+                // an invariant operand of a per-pair step is permuted once in the prologue and kept
+                const bool keep = !X.variant && variant;
+                sid = new_storage(h, node_entries(X), X.variant, t);
+                if (keep) h->stor[sid].last = kLive;
+                Op p{};
+                p.type = OP_PERM;
+                p.variant = X.variant;
+                p.step = t;
+                p.src = nid;
+                p.target_legs = tl;
+                p.dst = sid;
+                h->ops.push_back(p);
+            } else {
+                sid = h->nodes[nid].storage;
+            }
+            (side ? g.sb : g.sa) = sid;
+        }
+        std::vector<int> cl = freeA;
+        cl.insert(cl.end(), freeB.begin(), freeB.end());
+        const int st = new_storage(h, (int64_t)1 << cl.size(), variant, t);
+        g.dst = st;
+        g.flops = 8.0 * std::ldexp(1.0, g.mb + g.kb + g.nb);
+        h->ops.push_back(g);
+        h->nodes.push_back(contiguous_node(cl, variant, st));
+    }
+    h->root = (int)h->nodes.size() - 1;
+    const Node& R = h->nodes[h->root];
+    {
+        std::vector<int> rl = R.legs, ow = h->open_wires;
+        std::sort(rl.begin(), rl.end());
+        std::sort(ow.begin(), ow.end());
+        if (R.const_one ? !ow.empty() : rl != ow)
+            return fail(h, QX_EINVAL, "plan result legs do not match the open qubits");
+    }
+    if (R.storage >= 0) h->stor[R.storage].last = kLive;
+    // invariant storages read by per-pair work stay resident
+    for (const Op& op : h->ops) {
+        if (!op.variant) continue;
+        auto keep = [&](int node) {
+            const Node& nd = h->nodes[node];
+            if (nd.storage >= 0 && !nd.variant) h->stor[nd.storage].last = kLive;
+        };
+        if (op.type == OP_PERM) keep(op.src);
+        if (op.type == OP_SMALL) { keep(op.x); keep(op.y); }
+        if (op.type == OP_GEMM) {
+            if (!h->stor[op.sa].variant) h->stor[op.sa].last = kLive;
+            if (!h->stor[op.sb].variant) h->stor[op.sb].last = kLive;
+        }
+    }
+    if (!R.variant && R.storage >= 0) h->stor[R.storage].last = kLive;
+    h->item_entries = std::max<int64_t>(assign_offsets(h, true), kAlignEntries);
+    h->inv_entries = assign_offsets(h, false);
+    h->flops_inv = h->flops_item = 0;
+    for (const Op& op : h->ops) (op.variant ? h->flops_item : h->flops_inv) += op.flops;
+    h->have_plan = true;
+    return QX_OK;
+}
+
+// ------------------------------------------------------------------------------------------------
+// Workspace layout: leaves | bitstrings | accumulators | amplitudes | invariant | per-pair region
+// ------------------------------------------------------------------------------------------------
+static int64_t n_open(const qx_ctx* h) { return (int64_t)h->open_wires.size(); }
+
+static void layout(qx_ctx* h, int64_t max_bits, int64_t* fixed_bytes) {
+    int64_t off = 0;
+    h->off_leaf = off;
+    off += align_up((int64_t)h->leaf_vals.size() * 8, 256);
+    h->off_bits = off;
+    off += align_up(max_bits * h->nq, 256);
+    h->off_acc = off;
+    off += align_up((max_bits << n_open(h)) * 32, 256);
+    h->off_amps = off;
+    off += align_up((max_bits << n_open(h)) * 16, 256);
+    h->off_inv = off;
+    off += align_up(h->inv_entries * 8, 256);
+    h->off_item = off;
+    *fixed_bytes = off;
+}
+
+static float2* item_base(const qx_ctx* h) { return (float2*)(h->ws + h->off_item); }
+static float2* inv_base(const qx_ctx* h) { return (float2*)(h->ws + h->off_inv); }
+
+// device address and item stride of a storage
+static void storage_addr(const qx_ctx* h, int sid, float2** p, int64_t* is) {
+    const Storage& s = h->stor[sid];
+    if (s.variant) {
+        *p = item_base(h) + s.off * h->items_cap;
+        *is = s.entries;
+    } else {
+        *p = inv_base(h) + s.off;
+        *is = 0;
+    }
+}
+
+static Operand node_operand(const qx_ctx* h, int node) {
+    Operand op = make_operand(h, node);
+    const Node& nd = h->nodes[node];
+    if (nd.leaf) {
+        op.base = (const float2*)(h->ws + h->off_leaf) + nd.leaf_off;
+        op.item_stride = 0;
+    } else {
+        float2* p;
+        int64_t is;
+        storage_addr(h, nd.storage, &p, &is);
+        op.base = p;
+        op.item_stride = is;
+    }
+    return op;
+}
+
+static PermDesc perm_desc(const qx_ctx* h, const Op& op) {
+    PermDesc d{};
+    d.in = node_operand(h, op.src);
+    const Node& X = h->nodes[op.src];
+    const int r = (int)op.target_legs.size();
+    d.rank = r;
+    for (int ob = 0; ob < r; ++ob) {
+        const int leg = op.target_legs[r - 1 - ob];
+        const int j = (int)(std::find(X.legs.begin(), X.legs.end(), leg) - X.legs.begin());
+        d.in_pos[ob] = (int8_t)X.pos[j];
+    }
+    const int L = std::min(5, r);
+    std::vector<char> in_tile(r, 0);
+    for (int ob = 0; ob < L; ++ob) in_tile[ob] = 1;
+    std::vector<int> by_in(r);
+    for (int i = 0; i < r; ++i) by_in[i] = i;
+    std::sort(by_in.begin(), by_in.end(), [&](int a, int b) { return d.in_pos[a] < d.in_pos[b]; });
+    for (int i = 0; i < L; ++i) in_tile[by_in[i]] = 1;
+    int t = 0;
+    for (int ob = 0; ob < r; ++ob) t += in_tile[ob];
+    for (int ob = 0; ob < r && t < std::min(r, 10); ++ob)
+        if (!in_tile[ob]) { in_tile[ob] = 1; ++t; }
+    d.t = t;
+    int k = 0;
+    for (int i = 0; i < r; ++i)
+        if (in_tile[by_in[i]]) d.tile_in[k++] = (int8_t)by_in[i];
+    k = 0;
+    for (int ob = 0; ob < r; ++ob)
+        if (in_tile[ob]) d.tile_out[k++] = (int8_t)ob;
+    k = 0;
+    for (int ob = 0; ob < r; ++ob)
+        if (!in_tile[ob]) d.outer[k++] = (int8_t)ob;
+    d.n_outer = k;
+    return d;
+}
+
+static SmallDesc small_desc(const qx_ctx* h, const Op& op) {
+    SmallDesc d{};
+    d.x = node_operand(h, op.x);
+    d.y = node_operand(h, op.y);
+    const Node& X = h->nodes[op.x];
+    const Node& Y = h->nodes[op.y];
+    d.mb = op.mb;
+    d.kb = op.kb;
+    d.nb = op.nb;
+    std::vector<char> freepos(X.under_rank, 0);
+    for (size_t j = 0; j < X.legs.size(); ++j)
+        if (std::find(op.shared.begin(), op.shared.end(), X.legs[j]) == op.shared.end()) freepos[X.pos[j]] = 1;
+    int nh = 0;
+    for (int p = 0; p < X.under_rank; ++p)
+        if (!freepos[p]) d.holes[nh++] = (int8_t)p;
+    d.n_holes = nh;
+    for (int i = 0; i < op.kb; ++i) {
+        const int e = op.shared[i];
+        d.xk_pos[i] = (int8_t)X.pos[std::find(X.legs.begin(), X.legs.end(), e) - X.legs.begin()];
+        d.yk_pos[i] = (int8_t)Y.pos[std::find(Y.legs.begin(), Y.legs.end(), e) - Y.legs.begin()];
+    }
+    std::vector<int> fy;
+    for (size_t j = 0; j < Y.legs.size(); ++j)
+        if (std::find(op.shared.begin(), op.shared.end(), Y.legs[j]) == op.shared.end()) fy.push_back((int)j);
+    for (int i = 0; i < op.nb; ++i) d.yn_pos[i] = (int8_t)Y.pos[fy[op.nb - 1 - i]];
+    return d;
+}
+
+static double op_bytes(const qx_ctx* h, const Op& op) {
+    // algorithmic bytes per pair: each operand read once, the result written once
+    if (op.type == OP_PERM) return 16.0 * (double)h->stor[op.dst].entries;
+    const double c = 8.0 * (double)h->stor[op.dst].entries;
+    if (op.type == OP_SMALL)
+        return c + 8.0 * (double)(node_entries(h->nodes[op.x]) + node_entries(h->nodes[op.y]));
+    return c + 8.0 * (double)(h->stor[op.sa].entries + h->stor[op.sb].entries);
+}
+
+static int run_op(qx_ctx* h, const Op& op, const ItemCtx& ic, int64_t n_items) {
+    float2* dp;
+    int64_t dis;
+    storage_addr(h, op.dst, &dp, &dis);
+    const int kind = op.type == OP_PERM ? QX_KERNEL_PERMUTE : op.type == OP_SMALL ? QX_KERNEL_SMALL : QX_KERNEL_GEMM;
+    size_t slot;
+    cudaError_t e = prof_begin(h, kind, op.flops * (double)n_items, op_bytes(h, op) * (double)n_items, &slot);
+    if (e != cudaSuccess) return fail(h, QX_ECUDA, "profiling event: %s", cudaGetErrorString(e));
+    if (op.type == OP_PERM) {
+        e = launch_permute(perm_desc(h, op), ic, n_items, dp, dis, h->stream);
+    } else if (op.type == OP_SMALL) {
+        e = launch_small(small_desc(h, op), ic, n_items, dp, dis, h->stream);
+    } else {
+        float2 *ap, *bp;
+        int64_t ais, bis;
+        storage_addr(h, op.sa, &ap, &ais);
+        storage_addr(h, op.sb, &bp, &bis);
+        e = launch_gemm_c64(ap, ais, op.a_km, bp, bis, op.b_km, dp, dis, op.mb, op.nb, op.kb, n_items, h->stream);
+    }
+    if (e != cudaSuccess) return fail(h, QX_ECUDA, "kernel launch failed: %s", cudaGetErrorString(e));
+    e = prof_end(h, slot);
+    if (e != cudaSuccess) return fail(h, QX_ECUDA, "profiling event: %s", cudaGetErrorString(e));
+    h->last_launches++;
+    h->last_flops += op.flops * (double)n_items;
+    return QX_OK;
+}
+
+static int contract_impl(qx_ctx* h, const uint8_t* d_bits, int64_t n_bits, int64_t s_begin, int64_t s_end,
+                         double* d_amps) {
+    const int64_t n_o = (int64_t)1 << n_open(h);
+    h->last_flops = 0;
+    h->last_launches = 0;
+    h->last_batches = 0;
+    if (!h->leaves_on_device) {
+        CUDA_TRY(h, cudaMemcpyAsync(h->ws + h->off_leaf, h->leaf_vals.data(), h->leaf_vals.size() * sizeof(float2),
+                                    cudaMemcpyHostToDevice, h->stream));
+        CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+        h->leaves_on_device = true;
+    }
+    double* acc = (double*)(h->ws + h->off_acc);
+    CUDA_TRY(h, cudaMemsetAsync(acc, 0, (size_t)(n_bits * n_o * 32), h->stream));
+    ItemCtx ic{};
+    ic.n_qubits = h->nq;
+    ic.bits = d_bits;
+    ic.n_b = 1;
+    ic.n_items = 1;
+    // prologue: everything that no slice or bitstring touches
+    for (const Op& op : h->ops)
+        if (!op.variant) {
+            int rc = run_op(h, op, ic, 1);
+            if (rc) return rc;
+        }
+    // batches of (slice, bitstring) pairs
+    int64_t nb_batch, ns_batch;
+    if (h->items_cap >= n_bits) {
+        nb_batch = n_bits;
+        ns_batch = std::min<int64_t>(h->n_slices, h->items_cap / n_bits);
+    } else {
+        nb_batch = h->items_cap;
+        ns_batch = 1;
+    }
+    SumDesc sd{};
+    sd.root = node_operand(h, h->root);
+    sd.open_bits = (int32_t)n_open(h);
+    {
+        const Node& R = h->nodes[h->root];
+        for (int ob = 0; ob < sd.open_bits; ++ob) {
+            const int wire = h->open_wires[sd.open_bits - 1 - ob];
+            const int j = (int)(std::find(R.legs.begin(), R.legs.end(), wire) - R.legs.begin());
+            sd.obit_pos[ob] = (int8_t)R.pos[j];
+        }
+    }
+    for (int64_t s0 = s_begin; s0 < s_end; s0 += ns_batch) {
+        const int64_t ns = std::min(ns_batch, s_end - s0);
+        for (int64_t b0 = 0; b0 < n_bits; b0 += nb_batch) {
+            const int64_t nb = std::min(nb_batch, n_bits - b0);
+            ic.s0 = s0;
+            ic.b0 = b0;
+            ic.n_b = (int32_t)nb;
+            ic.n_items = ns * nb;
+            for (const Op& op : h->ops)
+                if (op.variant) {
+                    int rc = run_op(h, op, ic, ic.n_items);
+                    if (rc) return rc;
+                }
+            sd.n_s = (int32_t)ns;
+            size_t slot;
+            const double sum_bytes = (double)(ns * nb << sd.open_bits) * 8.0 + (double)(nb << sd.open_bits) * 64.0;
+            cudaError_t e = prof_begin(h, QX_KERNEL_SUM, 0.0, sum_bytes, &slot);
+            if (e == cudaSuccess) e = launch_slice_sum(sd, ic, acc, h->stream);
+            if (e == cudaSuccess) e = prof_end(h, slot);
+            if (e != cudaSuccess) return fail(h, QX_ECUDA, "slice sum launch failed: %s", cudaGetErrorString(e));
+            h->last_launches++;
+            h->last_batches++;
+        }
+    }
+    cudaError_t e = launch_finalize(acc, d_amps, n_bits * n_o, h->stream);
+    if (e != cudaSuccess) return fail(h, QX_ECUDA, "finalize launch failed: %s", cudaGetErrorString(e));
+    h->last_launches++;
+    return QX_OK;
+}
+
+// ------------------------------------------------------------------------------------------------
+// C ABI
+// ------------------------------------------------------------------------------------------------
+extern "C" {
+
+int qx_create(qx_handle* out, int device, void* stream, const qx_options* opt) {
+    if (!out) return QX_EINVAL;
+    *out = nullptr;
+    if (device != -1) {  // -1: host-only handle (network, plan and sizes; no contraction)
+        int n = 0;
+        if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) return QX_ECUDA;
+    }
+    qx_ctx* h = new qx_ctx();
+    h->device = device;
+    h->stream = (cudaStream_t)stream;
+    if (opt) h->opt = *opt;
+    if (h->opt.precision != QX_PREC_C64) {
+        delete h;
+        return QX_EINVAL;
+    }
+    *out = h;
+    return QX_OK;
+}
+
+void qx_destroy(qx_handle h) {
+    if (!h) return;
+    for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
+    if (h->ws_owned && h->ws) {
+        cudaSetDevice(h->device);
+        cudaFree(h->ws);
+    }
+    delete h;
+}
+
+const char* qx_last_error(qx_handle h) { return h ? h->err.c_str() : "null handle"; }
+
+int qx_set_options(qx_handle h, const qx_options* opt) {
+    if (!h || !opt) return QX_EINVAL;
+    if (opt->precision != QX_PREC_C64) return fail(h, QX_EINVAL, "precision form %d is not available", opt->precision);
+    if (opt->max_items < 0) return fail(h, QX_EINVAL, "max_items < 0");
+    h->opt = *opt;
+    return QX_OK;
+}
+
+int qx_build_network(qx_handle h, int32_t n_qubits, const qx_gate* gates, int64_t n_gates, const uint8_t* open_mask) {
+    if (!h) return QX_EINVAL;
+    h->have_plan = false;
+    return build_network(h, n_qubits, gates, n_gates, open_mask);
+}
+
+int qx_network_info(qx_handle h, int64_t* n_tensors, int64_t* n_bonds) {
+    if (!h) return QX_EINVAL;
+    if (!h->have_net) return fail(h, QX_ESTATE, "no network");
+    if (n_tensors) *n_tensors = h->n_tensors;
+    if (n_bonds) *n_bonds = h->n_bonds;
+    return QX_OK;
+}
+
+static void unbind(qx_ctx* h) {
+    if (h->ws_owned && h->ws) {
+        cudaSetDevice(h->device);
+        cudaFree(h->ws);
+    }
+    h->ws = nullptr;
+    h->ws_bytes = 0;
+    h->ws_owned = false;
+    h->items_cap = 0;
+    h->leaves_on_device = false;
+}
+
+int qx_set_plan(qx_handle h, const int64_t* order, int64_t n_steps, const int64_t* sliced, int32_t n_sliced,
+                int64_t* peak_entries_out) {
+    if (!h) return QX_EINVAL;
+    if (!h->have_net) return fail(h, QX_ESTATE, "qx_set_plan before qx_build_network");
+    if ((n_steps > 0 && !order) || (n_sliced > 0 && !sliced)) return fail(h, QX_EINVAL, "null plan arrays");
+    unbind(h);
+    h->have_plan = false;
+    int rc = compile_plan(h, order, n_steps, sliced, n_sliced);
+    if (rc) return rc;
+    if (peak_entries_out) *peak_entries_out = h->peak_entries;
+    return QX_OK;
+}
+
+int qx_workspace_size(qx_handle h, int64_t max_bits, int64_t items, int64_t* bytes_out) {
+    if (!h || !bytes_out) return QX_EINVAL;
+    if (!h->have_plan) return fail(h, QX_ESTATE, "qx_workspace_size before qx_set_plan");
+    if (max_bits < 1) return fail(h, QX_EINVAL, "max_bits < 1");
+    if (items < 1) items = 1;
+    int64_t fixed;
+    layout(h, max_bits, &fixed);
+    *bytes_out = fixed + items * h->item_entries * 8;
+    return QX_OK;
+}
+
+int qx_bind_workspace(qx_handle h, void* dptr, int64_t bytes, int64_t max_bits) {
+    if (!h) return QX_EINVAL;
+    if (h->device < 0) return fail(h, QX_ESTATE, "host-only handle has no device");
+    if (!h->have_plan) return fail(h, QX_ESTATE, "qx_bind_workspace before qx_set_plan");
+    if (max_bits < 1) return fail(h, QX_EINVAL, "max_bits < 1");
+    if (((uintptr_t)dptr) % 256) return fail(h, QX_EINVAL, "workspace must be 256-byte aligned");
+    unbind(h);
+    int64_t fixed;
+    layout(h, max_bits, &fixed);
+    int64_t items = (bytes - fixed) / (h->item_entries * 8);
+    if (h->opt.max_items > 0) items = std::min<int64_t>(items, h->opt.max_items);
+    items = std::min<int64_t>(items, kMaxBatchItems);
+    items = std::min<int64_t>(items, h->n_slices * max_bits);
+    if (items < 1)
+        return fail(h, QX_ENOMEM, "workspace of %lld bytes holds no (slice, bitstring) pair; need %lld", (long long)bytes,
+                    (long long)(fixed + h->item_entries * 8));
+    CUDA_TRY(h, cudaSetDevice(h->device));
+    if (!dptr) {
+        CUDA_TRY(h, cudaMalloc(&dptr, (size_t)bytes));
+        h->ws_owned = true;
+    }
+    h->ws = (char*)dptr;
+    h->ws_bytes = bytes;
+    h->max_bits = max_bits;
+    h->items_cap = items;
+    h->leaves_on_device = false;
+    return QX_OK;
+}
+
+static int check_range(qx_ctx* h, int64_t s_begin, int64_t s_end) {
+    if (s_begin < 0 || s_end > h->n_slices || s_begin >= s_end)
+        return fail(h, QX_EINVAL, "slice range [%lld, %lld) not within [0, %lld)", (long long)s_begin,
+                    (long long)s_end, (long long)h->n_slices);
+    return QX_OK;
+}
+
+static int check_ready(qx_ctx* h, int64_t n_bits) {
+    if (!h->have_plan) return fail(h, QX_ESTATE, "contract before qx_set_plan");
+    if (!h->ws) return fail(h, QX_ESTATE, "contract before qx_bind_workspace");
+    if (n_bits < 1) return fail(h, QX_EINVAL, "n_bits < 1");
+    if (n_bits > h->max_bits)
+        return fail(h, QX_ENOMEM, "%lld bitstrings exceed the workspace's %lld", (long long)n_bits, (long long)h->max_bits);
+    return QX_OK;
+}
+
+int qx_contract_slices(qx_handle h, const uint8_t* bits, int64_t n_bits, int64_t s_begin, int64_t s_end,
+                       double* amps_out) {
+    if (!h) return QX_EINVAL;
+    int rc = check_ready(h, n_bits);
+    if (rc) return rc;
+    rc = check_range(h, s_begin, s_end);
+    if (rc) return rc;
+    if (!bits || !amps_out) return fail(h, QX_EINVAL, "null buffer");
+    for (int64_t i = 0; i < n_bits * h->nq; ++i)
+        if (bits[i] > 1) return fail(h, QX_EINVAL, "bitstring %lld has a byte that is not 0/1", (long long)(i / h->nq));
+    CUDA_TRY(h, cudaSetDevice(h->device));
+    uint8_t* d_bits = (uint8_t*)(h->ws + h->off_bits);
+    double* d_amps = (double*)(h->ws + h->off_amps);
+    CUDA_TRY(h, cudaMemcpyAsync(d_bits, bits, (size_t)(n_bits * h->nq), cudaMemcpyHostToDevice, h->stream));
+    rc = contract_impl(h, d_bits, n_bits, s_begin, s_end, d_amps);
+    if (rc) return rc;
+    const size_t out_bytes = (size_t)((n_bits << n_open(h)) * 16);
+    CUDA_TRY(h, cudaMemcpyAsync(amps_out, d_amps, out_bytes, cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    return QX_OK;
+}
+
+int qx_contract(qx_handle h, const uint8_t* bits, int64_t n_bits, double* amps_out) {
+    if (!h) return QX_EINVAL;
+    return qx_contract_slices(h, bits, n_bits, 0, h->n_slices, amps_out);
+}
+
+int qx_contract_slices_device(qx_handle h, const uint8_t* d_bits, int64_t n_bits, int64_t s_begin, int64_t s_end,
+                              double* d_amps) {
+    if (!h) return QX_EINVAL;
+    int rc = check_ready(h, n_bits);
+    if (rc) return rc;
+    rc = check_range(h, s_begin, s_end);
+    if (rc) return rc;
+    if (!d_bits || !d_amps) return fail(h, QX_EINVAL, "null buffer");
+    CUDA_TRY(h, cudaSetDevice(h->device));
+    return contract_impl(h, d_bits, n_bits, s_begin, s_end, d_amps);
+}
+
+int qx_contract_device(qx_handle h, const uint8_t* d_bits, int64_t n_bits, double* d_amps) {
+    if (!h) return QX_EINVAL;
+    return qx_contract_slices_device(h, d_bits, n_bits, 0, h->n_slices, d_amps);
+}
+
+int qx_set_profiling(qx_handle h, int enable) {
+    if (!h) return QX_EINVAL;
+    int rc = prof_collect(h);
+    if (rc) return rc;
+    h->profiling = enable != 0;
+    for (int k = 0; k < QX_KERNEL_KINDS; ++k) {
+        h->prof_ms[k] = h->prof_flops[k] = h->prof_bytes[k] = 0;
+        h->prof_launches[k] = 0;
+    }
+    return QX_OK;
+}
+
+int qx_profile_read(qx_handle h, int kind, double* ms, int64_t* launches, double* flops, double* bytes) {
+    if (!h) return QX_EINVAL;
+    if (kind < 0 || kind >= QX_KERNEL_KINDS) return fail(h, QX_EINVAL, "kernel kind %d out of range", kind);
+    int rc = prof_collect(h);
+    if (rc) return rc;
+    if (ms) *ms = h->prof_ms[kind];
+    if (launches) *launches = h->prof_launches[kind];
+    if (flops) *flops = h->prof_flops[kind];
+    if (bytes) *bytes = h->prof_bytes[kind];
+    return QX_OK;
+}
+
+int qx_last_stats(qx_handle h, double* flops, int64_t* launches, int64_t* batches) {
+    if (!h) return QX_EINVAL;
+    if (flops) *flops = h->last_flops;
+    if (launches) *launches = h->last_launches;
+    if (batches) *batches = h->last_batches;
+    return QX_OK;
+}
+
+}  // extern "C"

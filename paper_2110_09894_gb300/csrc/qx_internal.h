@@ -1,0 +1,91 @@
+// Internal interface between the host orchestration (qx_host.cpp) and the
+// CUDA kernels (qx_kernels.cu).  Not part of the public C ABI.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace qx {
+
+constexpr int kMaxRank = 48;   // effective legs of one operand
+constexpr int kMaxFix = 8;     // fixed (sliced / output) legs of one leaf
+constexpr int kSmallMaxK = 5;  // shared bits handled by the gather kernel
+constexpr int kSmallMaxN = 5;  // free bits of its small operand
+constexpr int kMaxBatchItems = 65535;
+
+// The (slice, bitstring) pairs of one batch: item = s_local * n_b + b_local.
+struct ItemCtx {
+    int64_t s0;            // first slice of the batch
+    int64_t b0;            // first bitstring of the batch
+    int64_t n_items;       // pairs in the batch
+    int32_t n_b;           // bitstrings per slice in the batch
+    int32_t n_qubits;      // bytes per bitstring
+    const uint8_t* bits;   // device bitstrings [n_bits][n_qubits]
+};
+
+// Address of entry (leg bits) of an operand for item i:
+//   base + i * item_stride + sum_f value_f * fix_stride[f] + sum_j bit_j << pos[j]
+// value_f is bit fix_src[f] of the slice index (fix_src >= 0) or the byte of
+// output qubit -(fix_src+1) of the bitstring (fix_src < 0).  Leg 0 is the
+// most significant; positions are strictly decreasing in leg order.
+struct Operand {
+    const float2* base;
+    int64_t item_stride;
+    int32_t n_fix;
+    int32_t rank;
+    int32_t fix_src[kMaxFix];
+    int64_t fix_stride[kMaxFix];
+    int8_t pos[kMaxRank];
+};
+
+// Bit permutation out[y] = in[x]: output bit ob (0 = least significant) is
+// taken from input address position in_pos[ob].  The tile holds `t` bits:
+// tile_in lists them (as output-bit ids) by increasing input position,
+// tile_out by increasing output bit; `outer` lists the remaining output bits.
+struct PermDesc {
+    Operand in;
+    int32_t rank;
+    int32_t t;
+    int32_t n_outer;
+    int8_t in_pos[kMaxRank];
+    int8_t tile_in[10];
+    int8_t tile_out[10];
+    int8_t outer[kMaxRank];
+};
+
+// Gather contraction with one small operand Y (<= 2^10 entries):
+//   C[m * 2^nb + n] = sum_k X[m, k] * Y[k, n]
+// m enumerates X's free legs (bit i = i-th lowest free position), k the
+// shared legs, n Y's free legs (in Y's leg order, last leg = bit 0).
+struct SmallDesc {
+    Operand x, y;
+    int32_t mb, kb, nb;
+    int32_t n_holes;           // X positions that are not free (shared + fixed), ascending
+    int8_t holes[kMaxRank];
+    int8_t xk_pos[kSmallMaxK]; // X position of shared bit i of k
+    int8_t yk_pos[kSmallMaxK]; // Y position of shared bit i of k
+    int8_t yn_pos[kSmallMaxN]; // Y position of bit i of n
+};
+
+// Cross-slice FP64 compensated sum of the root tensor into accumulators.
+struct SumDesc {
+    Operand root;
+    int32_t open_bits;
+    int32_t n_s;               // slices in the batch
+    int8_t obit_pos[kMaxRank]; // root position of canonical open bit ob (0 = least significant)
+};
+
+// Launchers; each returns the launch error (cudaSuccess on success).
+cudaError_t launch_permute(const PermDesc& d, const ItemCtx& ic, int64_t n_items, float2* out,
+                           int64_t out_item_stride, cudaStream_t st);
+cudaError_t launch_small(const SmallDesc& d, const ItemCtx& ic, int64_t n_items, float2* out,
+                         int64_t out_item_stride, cudaStream_t st);
+// Batched complex GEMM, C[M][N] = A . B with A stored [M][K] (a_kmajor) or
+// [K][M], B stored [N][K] (b_kmajor) or [K][N]; M = 2^mb etc.
+cudaError_t launch_gemm_c64(const float2* a, int64_t a_is, bool a_kmajor, const float2* b, int64_t b_is,
+                            bool b_kmajor, float2* c, int64_t c_is, int mb, int nb, int kb, int64_t n_items,
+                            cudaStream_t st);
+cudaError_t launch_slice_sum(const SumDesc& d, const ItemCtx& ic, double* acc, cudaStream_t st);
+cudaError_t launch_finalize(const double* acc, double* amps, int64_t n, cudaStream_t st);
+
+}  // namespace qx

@@ -1,0 +1,328 @@
+// CUDA kernels of the contraction path (sm_103a): the index permutation of
+// the TTGT scheme, the complex64 SIMT GEMM, the gather contraction for steps
+// with a small operand, and the FP64 compensated cross-slice sum.
+//
+// Paper background: contracting a network is a sequence of pairwise
+// contractions mapped to matrix multiplications on the GPU (Sec. IV-A, the
+// three levels of parallelism); the primitives needed are contract, reshape,
+// permute, slice and recombine (Sec. III-B).  Slicing (Eq. 2) turns into
+// per-item address offsets here, recombination into the FP64 sum.
+#include <cuda_runtime.h>
+
+#include "qx_internal.h"
+
+namespace qx {
+
+__device__ __forceinline__ int64_t fix_offset(const Operand& op, const ItemCtx& ic, int64_t item) {
+    int64_t off = item * op.item_stride;
+    if (op.n_fix) {
+        const int64_t s = ic.s0 + item / ic.n_b;
+        const int64_t b = ic.b0 + item % ic.n_b;
+        for (int f = 0; f < op.n_fix; ++f) {
+            const int src = op.fix_src[f];
+            const int64_t v = src >= 0 ? ((s >> src) & 1) : (int64_t)(ic.bits[b * ic.n_qubits + (-src - 1)] & 1);
+            off += v * op.fix_stride[f];
+        }
+    }
+    return off;
+}
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+__device__ __forceinline__ void cfma(float2& acc, float2 a, float2 b) {
+    acc.x = fmaf(a.x, b.x, acc.x);
+    acc.x = fmaf(-a.y, b.y, acc.x);
+    acc.y = fmaf(a.x, b.y, acc.y);
+    acc.y = fmaf(a.y, b.x, acc.y);
+}
+
+// ---------------------------------------------------------------------------------------------
+// Bit permutation through a shared-memory tile.  Reads walk the tile in input
+// order (the lowest input positions vary fastest, so warps read contiguous
+// runs) and writes walk it in output order (contiguous runs again); the tile
+// holds up to 2^10 entries with one float2 of padding per 32.
+// ---------------------------------------------------------------------------------------------
+__device__ __forceinline__ int pad32(int j) { return j + (j >> 5); }
+
+__global__ void __launch_bounds__(256) k_permute(const PermDesc d, const ItemCtx ic, float2* __restrict__ out,
+                                                 int64_t out_is) {
+    __shared__ float2 tile[1024 + 32];
+    __shared__ int64_t in_lo[32], in_hi[32], out_lo[32], out_hi[32];
+    __shared__ int map_lo[32], map_hi[32];
+    const int tid = threadIdx.x;
+    const int t = d.t;
+    if (tid < 32) {
+        int64_t a = 0, b = 0, c = 0, e = 0;
+        int ml = 0, mh = 0;
+        for (int i = 0; i < 5; ++i) {
+            if ((tid >> i) & 1) {
+                if (i < t) {
+                    a += (int64_t)1 << d.in_pos[d.tile_in[i]];
+                    c += (int64_t)1 << d.tile_out[i];
+                }
+                if (i + 5 < t) {
+                    b += (int64_t)1 << d.in_pos[d.tile_in[i + 5]];
+                    e += (int64_t)1 << d.tile_out[i + 5];
+                }
+            }
+        }
+        // where output-ordered tile bit i sits in the input-ordered tile index
+        for (int i = 0; i < 10 && i < t; ++i) {
+            int r = 0;
+            for (int j = 0; j < t; ++j)
+                if (d.tile_in[j] == d.tile_out[i]) r = j;
+            if (i < 5) {
+                if ((tid >> i) & 1) ml |= 1 << r;
+            } else {
+                if ((tid >> (i - 5)) & 1) mh |= 1 << r;
+            }
+        }
+        in_lo[tid] = a;
+        in_hi[tid] = b;
+        out_lo[tid] = c;
+        out_hi[tid] = e;
+        map_lo[tid] = ml;
+        map_hi[tid] = mh;
+    }
+    const int64_t item = blockIdx.y;
+    const int64_t u = blockIdx.x;
+    int64_t ib = fix_offset(d.in, ic, item);
+    int64_t ob = item * out_is;
+    for (int i = 0; i < d.n_outer; ++i) {
+        if ((u >> i) & 1) {
+            ib += (int64_t)1 << d.in_pos[d.outer[i]];
+            ob += (int64_t)1 << d.outer[i];
+        }
+    }
+    __syncthreads();
+    const int n = 1 << t;
+    const float2* __restrict__ src = d.in.base + ib;
+    for (int j = tid; j < n; j += blockDim.x) tile[pad32(j)] = src[in_lo[j & 31] + in_hi[j >> 5]];
+    __syncthreads();
+    float2* __restrict__ dst = out + ob;
+    for (int j = tid; j < n; j += blockDim.x) dst[out_lo[j & 31] + out_hi[j >> 5]] = tile[pad32(map_lo[j & 31] | map_hi[j >> 5])];
+}
+
+cudaError_t launch_permute(const PermDesc& d, const ItemCtx& ic, int64_t n_items, float2* out, int64_t out_is,
+                           cudaStream_t st) {
+    if (n_items <= 0) return cudaSuccess;
+    dim3 grid((unsigned)(1ll << d.n_outer), (unsigned)n_items);
+    k_permute<<<grid, 256, 0, st>>>(d, ic, out, out_is);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------------------
+// Gather contraction against a small operand Y held in shared memory.  One
+// thread per free index m of the large operand X: it loads the 2^k entries
+// X[m, k] straight from X's native layout (no permute) and writes the 2^n
+// outputs C[m, n].  Used for the many steps that absorb a gate-sized tensor.
+// ---------------------------------------------------------------------------------------------
+template <int KB>
+__global__ void __launch_bounds__(256) k_small(const SmallDesc d, const ItemCtx ic, float2* __restrict__ out,
+                                               int64_t out_is) {
+    __shared__ float2 ys[1 << (kSmallMaxK + kSmallMaxN)];
+    __shared__ int64_t kofs[1 << kSmallMaxK];
+    const int64_t item = blockIdx.y;
+    const int nb = d.nb;
+    const int nn = 1 << nb;
+    const int64_t yoff = fix_offset(d.y, ic, item);
+    for (int idx = threadIdx.x; idx < ((1 << KB) << nb); idx += blockDim.x) {
+        const int kk = idx >> nb, n = idx & (nn - 1);
+        int64_t a = yoff;
+        for (int i = 0; i < KB; ++i)
+            if ((kk >> i) & 1) a += (int64_t)1 << d.yk_pos[i];
+        for (int i = 0; i < nb; ++i)
+            if ((n >> i) & 1) a += (int64_t)1 << d.yn_pos[i];
+        ys[idx] = d.y.base[a];
+    }
+    if (threadIdx.x < (1 << KB)) {
+        int64_t a = 0;
+        for (int i = 0; i < KB; ++i)
+            if ((threadIdx.x >> i) & 1) a += (int64_t)1 << d.xk_pos[i];
+        kofs[threadIdx.x] = a;
+    }
+    __syncthreads();
+    const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= ((int64_t)1 << d.mb)) return;
+    int64_t xa = m;
+    for (int h = 0; h < d.n_holes; ++h) {
+        const int p = d.holes[h];
+        xa = ((xa >> p) << (p + 1)) | (xa & (((int64_t)1 << p) - 1));
+    }
+    const float2* __restrict__ xp = d.x.base + fix_offset(d.x, ic, item) + xa;
+    float2 a[1 << KB];
+#pragma unroll
+    for (int kk = 0; kk < (1 << KB); ++kk) a[kk] = xp[kofs[kk]];
+    float2* __restrict__ cp = out + item * out_is + (m << nb);
+    for (int n = 0; n < nn; ++n) {
+        float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int kk = 0; kk < (1 << KB); ++kk) cfma(acc, a[kk], ys[kk * nn + n]);
+        cp[n] = acc;
+    }
+}
+
+cudaError_t launch_small(const SmallDesc& d, const ItemCtx& ic, int64_t n_items, float2* out, int64_t out_is,
+                         cudaStream_t st) {
+    if (n_items <= 0) return cudaSuccess;
+    const int64_t m = (int64_t)1 << d.mb;
+    dim3 grid((unsigned)((m + 255) / 256), (unsigned)n_items);
+    const int threads = m < 256 ? (int)((m + 31) / 32 * 32) : 256;
+    switch (d.kb) {
+        case 0: k_small<0><<<grid, threads, 0, st>>>(d, ic, out, out_is); break;
+        case 1: k_small<1><<<grid, threads, 0, st>>>(d, ic, out, out_is); break;
+        case 2: k_small<2><<<grid, threads, 0, st>>>(d, ic, out, out_is); break;
+        case 3: k_small<3><<<grid, threads, 0, st>>>(d, ic, out, out_is); break;
+        case 4: k_small<4><<<grid, threads, 0, st>>>(d, ic, out, out_is); break;
+        case 5: k_small<5><<<grid, threads, 0, st>>>(d, ic, out, out_is); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------------------
+// Complex64 SIMT GEMM (the plain reference form): 64 x 64 complex output tile
+// per CTA, 16 complex K per stage, 256 threads with 4 x 4 complex accumulators
+// each (rows ty + 16 i, columns tx + 16 j).  Batched over items in grid.y.
+// ---------------------------------------------------------------------------------------------
+constexpr int GBM = 64, GBN = 64, GBK = 16;
+
+template <bool AK, bool BK>
+__global__ void __launch_bounds__(256) k_gemm_c64(const float2* __restrict__ A, int64_t a_is,
+                                                  const float2* __restrict__ B, int64_t b_is, float2* __restrict__ C,
+                                                  int64_t c_is, int mb, int nb, int kb, int tiles_n) {
+    __shared__ float2 As[GBK][GBM + 1];
+    __shared__ float2 Bs[GBK][GBN + 1];
+    const int64_t M = (int64_t)1 << mb, N = (int64_t)1 << nb, K = (int64_t)1 << kb;
+    const int64_t item = blockIdx.y;
+    const int64_t m0 = (int64_t)(blockIdx.x / tiles_n) * GBM;
+    const int64_t n0 = (int64_t)(blockIdx.x % tiles_n) * GBN;
+    const float2* Ap = A + item * a_is;
+    const float2* Bp = B + item * b_is;
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    float2 acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = make_float2(0.f, 0.f);
+    const float2 zero = make_float2(0.f, 0.f);
+    for (int64_t k0 = 0; k0 < K; k0 += GBK) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int idx = tid + 256 * r;
+            int mm, kk;
+            if (AK) { kk = idx & 15; mm = idx >> 4; } else { mm = idx & 63; kk = idx >> 6; }
+            const int64_t gm = m0 + mm, gk = k0 + kk;
+            float2 v = zero;
+            if (gm < M && gk < K) v = AK ? Ap[gm * K + gk] : Ap[gk * M + gm];
+            As[kk][mm] = v;
+            int nn;
+            if (BK) { kk = idx & 15; nn = idx >> 4; } else { nn = idx & 63; kk = idx >> 6; }
+            const int64_t gn = n0 + nn, gk2 = k0 + kk;
+            float2 w = zero;
+            if (gn < N && gk2 < K) w = BK ? Bp[gn * K + gk2] : Bp[gk2 * N + gn];
+            Bs[kk][nn] = w;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < GBK; ++kk) {
+            float2 a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) cfma(acc[i][j], a[i], b[j]);
+        }
+        __syncthreads();
+    }
+    float2* Cp = C + item * c_is;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int64_t gm = m0 + ty + 16 * i;
+        if (gm >= M) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int64_t gn = n0 + tx + 16 * j;
+            if (gn < N) Cp[gm * N + gn] = acc[i][j];
+        }
+    }
+}
+
+cudaError_t launch_gemm_c64(const float2* a, int64_t a_is, bool a_kmajor, const float2* b, int64_t b_is,
+                            bool b_kmajor, float2* c, int64_t c_is, int mb, int nb, int kb, int64_t n_items,
+                            cudaStream_t st) {
+    if (n_items <= 0) return cudaSuccess;
+    const int64_t tm = ((1ll << mb) + GBM - 1) / GBM, tn = ((1ll << nb) + GBN - 1) / GBN;
+    dim3 grid((unsigned)(tm * tn), (unsigned)n_items);
+    if (a_kmajor && b_kmajor)
+        k_gemm_c64<true, true><<<grid, 256, 0, st>>>(a, a_is, b, b_is, c, c_is, mb, nb, kb, (int)tn);
+    else if (a_kmajor)
+        k_gemm_c64<true, false><<<grid, 256, 0, st>>>(a, a_is, b, b_is, c, c_is, mb, nb, kb, (int)tn);
+    else if (b_kmajor)
+        k_gemm_c64<false, true><<<grid, 256, 0, st>>>(a, a_is, b, b_is, c, c_is, mb, nb, kb, (int)tn);
+    else
+        k_gemm_c64<false, false><<<grid, 256, 0, st>>>(a, a_is, b, b_is, c, c_is, mb, nb, kb, (int)tn);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------------------
+// Recombination of slices (Eq. 2) in FP64 with Neumaier compensation.  One
+// thread per (bitstring, open index); it walks the batch's slices in order,
+// so the result does not depend on thread scheduling.  acc holds
+// {sum_re, sum_im, comp_re, comp_im} per amplitude.
+// ---------------------------------------------------------------------------------------------
+__device__ __forceinline__ void neumaier(double& s, double& c, double x) {
+    const double t = s + x;
+    if (fabs(s) >= fabs(x)) c += (s - t) + x;
+    else c += (x - t) + s;
+    s = t;
+}
+
+__global__ void k_slice_sum(const SumDesc d, const ItemCtx ic, double* __restrict__ acc) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t n_o = (int64_t)1 << d.open_bits;
+    if (idx >= (int64_t)ic.n_b * n_o) return;
+    const int64_t bl = idx >> d.open_bits, o = idx & (n_o - 1);
+    int64_t rel = 0;
+    for (int ob = 0; ob < d.open_bits; ++ob)
+        if ((o >> ob) & 1) rel += (int64_t)1 << d.obit_pos[ob];
+    double* a = acc + ((ic.b0 + bl) * n_o + o) * 4;
+    double sr = a[0], si = a[1], cr = a[2], ci = a[3];
+    for (int s = 0; s < d.n_s; ++s) {
+        const int64_t item = (int64_t)s * ic.n_b + bl;
+        const float2 v = d.root.base[fix_offset(d.root, ic, item) + rel];
+        neumaier(sr, cr, (double)v.x);
+        neumaier(si, ci, (double)v.y);
+    }
+    a[0] = sr;
+    a[1] = si;
+    a[2] = cr;
+    a[3] = ci;
+}
+
+cudaError_t launch_slice_sum(const SumDesc& d, const ItemCtx& ic, double* acc, cudaStream_t st) {
+    const int64_t n = (int64_t)ic.n_b << d.open_bits;
+    if (n <= 0) return cudaSuccess;
+    k_slice_sum<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(d, ic, acc);
+    return cudaGetLastError();
+}
+
+__global__ void k_finalize(const double* __restrict__ acc, double* __restrict__ amps, int64_t n) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    amps[2 * i] = acc[4 * i] + acc[4 * i + 2];
+    amps[2 * i + 1] = acc[4 * i + 1] + acc[4 * i + 3];
+}
+
+cudaError_t launch_finalize(const double* acc, double* amps, int64_t n, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    k_finalize<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(acc, amps, n);
+    return cudaGetLastError();
+}
+
+}  // namespace qx

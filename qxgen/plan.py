@@ -149,7 +149,11 @@ def plan_cost(legs, order, sliced=()):
 
 
 def tree_trim_slices(legs, order, n_slice, seed=0, open_edges=()):
-    """Greedy tree-trimming choice of n_slice bonds to slice (Sec. III-A)."""
+    """Greedy tree-trimming choice of n_slice bonds to slice (Sec. III-A).
+
+    Bonds listed in open_edges are never chosen (pass every qubit's final
+    wire: open ones are not bonds and closed ones carry the bitstring).
+    """
     rng = SplitMix64(seed)
     inter = intermediates(legs, order)
     open_set = frozenset(open_edges)

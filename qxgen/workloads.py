@@ -64,6 +64,9 @@ class Workload:
 
 def make_plan(circ: Circuit, open_mask, n_slice, seed, trials=0, peak_rank=None, keep=12):
     legs, _, open_edges = network_legs(circ.n_qubits, [g.qubits for g in circ.gates], open_mask)
+    # a qubit's final wire cannot be sliced: open ones are not bonds, closed ones carry the bitstring
+    n_out = circ.n_qubits - len(open_edges)
+    open_edges = list(open_edges) + [legs[t][0] for t in range(len(legs) - n_out, len(legs))]
     if trials:
         order, sliced = randomized_greedy(legs, trials, seed, n_slice, open_edges, keep=keep)
     else:

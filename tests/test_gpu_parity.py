@@ -1,0 +1,199 @@
+"""CUDA path vs the complex128 oracle, through the C ABI (needs a GPU).
+
+Element-by-element comparisons on seeded inputs at sizes the oracle finishes
+in seconds (several tiles, ragged batches), plus the full-size workloads in
+the launch configuration the benchmark uses, and closed-form cases.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import einsum as oe
+from qxgen import circuits as C
+from qxgen import workloads as W
+
+from ._util import TOL_C64, grid_case, rel_l2
+
+pytestmark = pytest.mark.gpu
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+@pytest.fixture(scope="module")
+def qx():
+    from paper_2110_09894_gb300 import build
+    build.build()
+    from paper_2110_09894_gb300 import qx as mod
+    return mod
+
+
+def _contractor(qx, circ, om, order, sliced, max_bits, **kw):
+    return qx.Contractor(circ.n_qubits, C.gates_to_records(circ), om, order, sliced, max_bits, **kw)
+
+
+def test_small_workload_vs_statevector(qx):
+    w = W.small()
+    c = qx.Contractor(w.n_qubits, w.gates, w.open_mask, w.order, w.sliced, len(w.bitstrings))
+    got = c.contract(w.bitstrings)
+    ref = oracle.sv_amplitudes(w.n_qubits, w.gates, w.open_mask, w.bitstrings)
+    assert rel_l2(got, ref) <= TOL_C64
+    assert c.stats()["launches"] > 0
+
+
+def test_sliced_workload_vs_statevector_and_unsliced(qx):
+    w = W.sliced()
+    ref = oracle.sv_amplitudes(w.n_qubits, w.gates, w.open_mask, w.bitstrings)
+    c = qx.Contractor(w.n_qubits, w.gates, w.open_mask, w.order, w.sliced, len(w.bitstrings))
+    got = c.contract(w.bitstrings)
+    assert rel_l2(got, ref) <= TOL_C64
+    # per-bitstring relative error too (amplitudes of a 20-qubit random circuit are ~1e-3)
+    per = np.abs(got - ref).reshape(-1) / np.sqrt(np.mean(np.abs(ref) ** 2))
+    assert per.max() < 1e-4
+    c.close()
+    u = qx.Contractor(w.n_qubits, w.gates, w.open_mask, w.order, [], len(w.bitstrings))
+    unsliced = u.contract(w.bitstrings)
+    assert rel_l2(unsliced, ref) <= TOL_C64
+
+
+@pytest.mark.parametrize("rows,cols,depth,n_open,n_slice,n_bits", [
+    (3, 3, 8, 3, 2, 5), (2, 5, 10, 0, 4, 33), (3, 4, 6, 2, 3, 1), (4, 4, 8, 4, 5, 7)])
+def test_grid_cases_vs_statevector(qx, rows, cols, depth, n_open, n_slice, n_bits):
+    circ, om, order, sliced, bits = grid_case(rows, cols, depth, 31 + depth, n_open, n_slice, n_bits)
+    c = _contractor(qx, circ, om, order, sliced, n_bits)
+    got = c.contract(bits)
+    ref = oracle.sv_amplitudes(circ.n_qubits, C.gates_to_records(circ), om, bits)
+    assert got.shape == ref.shape
+    assert rel_l2(got, ref) <= TOL_C64
+
+
+@pytest.mark.parametrize("max_items", [1, 3, 64, 0])
+def test_batch_size_does_not_change_the_result(qx, max_items):
+    circ, om, order, sliced, bits = grid_case(3, 4, 8, 77, 1, 4, 6)
+    base = _contractor(qx, circ, om, order, sliced, 6, max_items=1).contract(bits)
+    got = _contractor(qx, circ, om, order, sliced, 6, max_items=max_items).contract(bits)
+    assert np.array_equal(got, base)  # same per-pair kernels, same slice order in the FP64 sum
+
+
+def test_ghz_closed_form(qx):
+    n = 12
+    circ = C.ghz_circuit(n)
+    om = np.zeros(n, np.uint8)
+    from qxgen.workloads import make_plan
+    order, sliced, _, _ = make_plan(circ, om, 3, 5)
+    bits = np.array([[0] * n, [1] * n, [0, 1] * (n // 2)], np.uint8)
+    got = _contractor(qx, circ, om, order, sliced, 3).contract(bits)[:, 0]
+    s = 1 / math.sqrt(2)
+    assert np.allclose(got, [s, s, 0], atol=1e-6)
+
+
+def test_product_state_closed_form(qx):
+    n = 10
+    circ = C.product_circuit(n, 4, seed=3)
+    v = [np.eye(2, dtype=np.complex128) for _ in range(n)]
+    for g in circ.gates:
+        v[g.qubits[0]] = g.matrix @ v[g.qubits[0]]
+    bits = C.random_bitstrings(n, 9, 4)
+    want = np.array([np.prod([v[q][x[q], 0] for q in range(n)]) for x in bits])
+    from qxgen.workloads import make_plan
+    om = np.zeros(n, np.uint8)
+    order, sliced, _, _ = make_plan(circ, om, 0, 1)
+    got = _contractor(qx, circ, om, order, sliced, 9).contract(bits)[:, 0]
+    assert rel_l2(got, want) <= TOL_C64
+
+
+def test_all_open_no_slices_gives_the_state(qx):
+    # every tensor is then independent of slices and bitstrings (prologue only)
+    circ, om, order, sliced, bits = grid_case(2, 4, 6, 12, n_open=8, n_slice=0, n_bits=2)
+    got = _contractor(qx, circ, om, order, sliced, 2).contract(bits)
+    psi = oracle.statevector(8, C.gates_to_records(circ))
+    assert rel_l2(got[0], psi) <= TOL_C64
+    assert np.array_equal(got[0], got[1])
+    assert abs(np.sum(np.abs(got[0]) ** 2) - 1) < 1e-5
+
+
+def test_trivial_networks(qx):
+    # one qubit, no gates: <x|0>
+    circ = C.Circuit(1)
+    c = _contractor(qx, circ, np.zeros(1, np.uint8), [(0, 1)], [], 2)
+    got = c.contract(np.array([[0], [1]], np.uint8))[:, 0]
+    assert np.allclose(got, [1, 0])
+
+
+def test_mirror_circuit_36_qubits(qx):
+    u = C.random_grid_circuit(6, 6, 3, 55)
+    circ = u.then(u.inverse())
+    from qxgen.workloads import make_plan
+    om = np.zeros(36, np.uint8)
+    order, sliced, _, _ = make_plan(circ, om, 3, 9)
+    bits = np.concatenate([np.zeros((1, 36), np.uint8), C.random_bitstrings(36, 3, 8)])
+    got = _contractor(qx, circ, om, order, sliced, 4).contract(bits)[:, 0]
+    assert abs(got[0] - 1) < 1e-5
+    assert np.all(np.abs(got[1:]) < 1e-5)
+
+
+def test_slice_ranges_add_up_and_match_oracle(qx):
+    circ, om, order, sliced, bits = grid_case(3, 4, 8, 91, 2, 4, 3)
+    c = _contractor(qx, circ, om, order, sliced, 3)
+    full = c.contract(bits)
+    parts = c.contract_slices(bits, 0, 5) + c.contract_slices(bits, 5, 16)
+    assert rel_l2(parts, full) < 1e-12
+    ref = oe.amplitudes(circ.n_qubits, C.gates_to_records(circ), om, order, sliced, bits, slices=range(5, 16))
+    assert rel_l2(c.contract_slices(bits, 5, 16), ref) <= TOL_C64
+
+
+def test_device_path_matches_host_path(qx):
+    import torch
+    circ, om, order, sliced, bits = grid_case(3, 4, 8, 5, 1, 3, 9)
+    c = _contractor(qx, circ, om, order, sliced, 9)
+    host = c.contract(bits)
+    d_bits = torch.from_numpy(bits).cuda()
+    d_amps = c.contract_device(d_bits)
+    torch.cuda.synchronize()
+    dev = d_amps.cpu().numpy()
+    assert np.array_equal(dev[..., 0] + 1j * dev[..., 1], host)
+
+
+def test_errors_through_the_abi(qx):
+    circ, om, order, sliced, bits = grid_case(2, 3, 4, 5, 0, 1, 2)
+    c = _contractor(qx, circ, om, order, sliced, 2)
+    bad = bits.copy()
+    bad[0, 0] = 2
+    with pytest.raises(qx.QXError) as e:
+        c.contract(bad)
+    assert e.value.code == qx.QX_EINVAL
+    with pytest.raises(qx.QXError) as e:
+        c.contract(np.zeros((3, 6), np.uint8))
+    assert e.value.code == qx.QX_ENOMEM
+    with pytest.raises(qx.QXError) as e:
+        c.contract_slices(bits, 1, 1)
+    assert e.value.code == qx.QX_EINVAL
+    h = qx.qx_create(0)
+    qx.qx_build_network(h, circ.n_qubits, C.gates_to_records(circ), om)
+    with pytest.raises(qx.QXError) as e:
+        qx.qx_contract(h, bits, circ.n_qubits, 0)
+    assert e.value.code == qx.QX_ESTATE
+    qx.qx_destroy(h)
+
+
+def _golden_large():
+    p = os.path.join(HERE, "golden", "large_slices0_31.json")
+    with open(p) as f:
+        g = json.load(f)
+    return g, np.array(g["re"]) + 1j * np.array(g["im"])
+
+
+def test_large_workload_32_slices_vs_einsum_oracle(qx):
+    """6x6 depth-14 workload, bench launch configuration, slices 0..31."""
+    w = W.large()
+    g, ref = _golden_large()
+    from tests.golden.make_large_golden import plan_digest
+    assert g["plan_sha256"] == plan_digest(w), "planner output changed; regenerate the golden file"
+    c = qx.Contractor(w.n_qubits, w.gates, w.open_mask, w.order, w.sliced, 1)
+    got = c.contract_slices(w.bitstrings, 0, 32)[0]
+    assert rel_l2(got, ref) <= TOL_C64
+    # one slice recomputed by the oracle in the test itself
+    one = oe.contract_once(w.n_qubits, w.gates, w.open_mask, w.order, w.sliced, 7, w.bitstrings[0])
+    assert rel_l2(c.contract_slices(w.bitstrings, 7, 8)[0], one) <= TOL_C64
