@@ -39,6 +39,7 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default="sliced", choices=["small", "sliced", "large"])
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--max-items", type=int, default=0, help="cap on (slice, bitstring) pairs per batch (0 = fill)")
     return p.parse_args()
 
 
@@ -223,7 +224,8 @@ def main():
     n_bits = len(bits)
     amps_per_step = n_bits << w.n_open
     with torch.cuda.stream(stream):
-        c = qx.Contractor(w.n_qubits, w.gates, w.open_mask, w.order, w.sliced, n_bits, device=local, stream=stream)
+        c = qx.Contractor(w.n_qubits, w.gates, w.open_mask, w.order, w.sliced, n_bits, device=local, stream=stream,
+                          max_items=args.max_items)
         d_bits = torch.from_numpy(bits).to(dev)
         d_amps = torch.empty((n_bits, 1 << w.n_open, 2), dtype=torch.float64, device=dev)
         flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)

@@ -95,6 +95,7 @@ struct qx_ctx {
     std::vector<int> final_wire;                 // per qubit
     std::vector<int> open_wires;                 // final wires of open qubits, increasing qubit
     std::vector<int> bond_deg;                   // tensors touching each bond
+    double leaf_scale[2] = {1.0, 0.0};           // product over leaves of alpha (complex, FP64)
 
     // plan
     bool have_plan = false;
@@ -213,6 +214,8 @@ static int build_network(qx_ctx* h, int32_t n, const qx_gate* gates, int64_t ng,
     h->tensor_legs.clear();
     h->tensor_vals_off.clear();
     h->leaf_vals.clear();
+    h->leaf_scale[0] = 1.0;
+    h->leaf_scale[1] = 0.0;
     std::vector<int> wire(n);
     for (int q = 0; q < n; ++q) {
         wire[q] = q;
@@ -231,8 +234,29 @@ static int build_network(qx_ctx* h, int32_t n, const qx_gate* gates, int64_t ng,
         h->tensor_legs.push_back(legs);
         h->tensor_vals_off.push_back((int64_t)h->leaf_vals.size());
         const int d = gt.nq == 1 ? 2 : 4;
-        // T[o.., i..] = U[row(o), col(i)], row-major: entry index = row * d + col
-        for (int e = 0; e < d * d; ++e) h->leaf_vals.push_back(make_float2((float)gt.re[e], (float)gt.im[e]));
+        // T[o.., i..] = U[row(o), col(i)], row-major: entry index = row * d + col.
+        // Rounding U to complex64 scales it slightly (every entry of a Sycamore
+        // one-qubit gate is 1/sqrt(2) in modulus and rounds the same way), and
+        // an amplitude is a product over all gates, so those scales add up to a
+        // bias of (number of gates) x 2^-25.  The complex least-squares factor
+        // alpha = <Uf, U> / <Uf, Uf> (FP64) restores U ~ alpha Uf; every leaf
+        // enters every contraction exactly once, so the product of the alphas
+        // multiplies the final FP64 amplitudes exactly.
+        double num_re = 0, num_im = 0, den = 0;
+        for (int e = 0; e < d * d; ++e) {
+            const float fr = (float)gt.re[e], fi = (float)gt.im[e];
+            h->leaf_vals.push_back(make_float2(fr, fi));
+            num_re += (double)fr * gt.re[e] + (double)fi * gt.im[e];
+            num_im += (double)fr * gt.im[e] - (double)fi * gt.re[e];
+            den += (double)fr * fr + (double)fi * fi;
+        }
+        if (den > 0) {
+            const double ar = num_re / den, ai = num_im / den;
+            const double pr = h->leaf_scale[0] * ar - h->leaf_scale[1] * ai;
+            const double pi = h->leaf_scale[0] * ai + h->leaf_scale[1] * ar;
+            h->leaf_scale[0] = pr;
+            h->leaf_scale[1] = pi;
+        }
     }
     h->final_wire = wire;
     h->open_wires.clear();
@@ -778,7 +802,7 @@ static int contract_impl(qx_ctx* h, const uint8_t* d_bits, int64_t n_bits, int64
             h->last_batches++;
         }
     }
-    cudaError_t e = launch_finalize(acc, d_amps, n_bits * n_o, h->stream);
+    cudaError_t e = launch_finalize(acc, d_amps, n_bits * n_o, h->leaf_scale[0], h->leaf_scale[1], h->stream);
     if (e != cudaSuccess) return fail(h, QX_ECUDA, "finalize launch failed: %s", cudaGetErrorString(e));
     h->last_launches++;
     return QX_OK;
@@ -1000,3 +1024,4 @@ int qx_last_stats(qx_handle h, double* flops, int64_t* launches, int64_t* batche
 }
 
 }  // extern "C"
+

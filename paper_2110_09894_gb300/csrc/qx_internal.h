@@ -86,6 +86,8 @@ cudaError_t launch_gemm_c64(const float2* a, int64_t a_is, bool a_kmajor, const 
                             bool b_kmajor, float2* c, int64_t c_is, int mb, int nb, int kb, int64_t n_items,
                             cudaStream_t st);
 cudaError_t launch_slice_sum(const SumDesc& d, const ItemCtx& ic, double* acc, cudaStream_t st);
-cudaError_t launch_finalize(const double* acc, double* amps, int64_t n, cudaStream_t st);
+// amps[i] = (sum + compensation) * (scale_re + i scale_im), all in FP64
+cudaError_t launch_finalize(const double* acc, double* amps, int64_t n, double scale_re, double scale_im,
+                            cudaStream_t st);
 
 }  // namespace qx

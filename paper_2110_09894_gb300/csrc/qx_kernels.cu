@@ -183,91 +183,208 @@ cudaError_t launch_small(const SmallDesc& d, const ItemCtx& ic, int64_t n_items,
 }
 
 // ---------------------------------------------------------------------------------------------
-// Complex64 SIMT GEMM (the plain reference form): 64 x 64 complex output tile
-// per CTA, 16 complex K per stage, 256 threads with 4 x 4 complex accumulators
-// each (rows ty + 16 i, columns tx + 16 j).  Batched over items in grid.y.
+// Complex64 SIMT GEMM (the plain reference form).  BM x BN complex output tile
+// per CTA (16 x 16 threads, each (BM/16) x (BN/16) outputs at rows ty + 16 i,
+// columns tx + 16 j), 16 complex K per stage, register-staged double buffer
+// (one barrier per stage), batched over items in grid.y.
+//
+// Accumulation is blocked: products are summed in FP32 over 64 K (4 stages)
+// into a partial that is then added to the running total.  A single running
+// FP32 sum over K = 2^15 terms loses about sqrt(K) ulps; blocking keeps the
+// error near (sqrt(64) + sqrt(K/64)) ulps at the cost of one add per output
+// per 64 K.
 // ---------------------------------------------------------------------------------------------
-constexpr int GBM = 64, GBN = 64, GBK = 16;
+constexpr int GBK = 16;
+constexpr int GFOLD = 4;  // stages per partial
 
-template <bool AK, bool BK>
-__global__ void __launch_bounds__(256) k_gemm_c64(const float2* __restrict__ A, int64_t a_is,
-                                                  const float2* __restrict__ B, int64_t b_is, float2* __restrict__ C,
-                                                  int64_t c_is, int mb, int nb, int kb, int tiles_n) {
-    __shared__ float2 As[GBK][GBM + 1];
-    __shared__ float2 Bs[GBK][GBN + 1];
+template <int BM, int BN>
+__global__ void __launch_bounds__(256) k_gemm_c64(const float2* __restrict__ A, int64_t a_is, bool akm,
+                                                  const float2* __restrict__ B, int64_t b_is, bool bkm,
+                                                  float2* __restrict__ C, int64_t c_is, int mb, int nb, int kb,
+                                                  int tiles_n) {
+    constexpr int TM = BM / 16, TN = BN / 16, LA = BM * GBK / 256, LB = BN * GBK / 256;
+    __shared__ float2 As[2][GBK][BM + 1];
+    __shared__ float2 Bs[2][GBK][BN + 1];
     const int64_t M = (int64_t)1 << mb, N = (int64_t)1 << nb, K = (int64_t)1 << kb;
     const int64_t item = blockIdx.y;
-    const int64_t m0 = (int64_t)(blockIdx.x / tiles_n) * GBM;
-    const int64_t n0 = (int64_t)(blockIdx.x % tiles_n) * GBN;
+    const int64_t m0 = (int64_t)(blockIdx.x / tiles_n) * BM;
+    const int64_t n0 = (int64_t)(blockIdx.x % tiles_n) * BN;
     const float2* Ap = A + item * a_is;
     const float2* Bp = B + item * b_is;
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-    float2 acc[4][4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = make_float2(0.f, 0.f);
     const float2 zero = make_float2(0.f, 0.f);
-    for (int64_t k0 = 0; k0 < K; k0 += GBK) {
+    float2 ra[LA], rb[LB];
+
+    auto gload = [&](int64_t k0) {
 #pragma unroll
-        for (int r = 0; r < 4; ++r) {
+        for (int r = 0; r < LA; ++r) {
             const int idx = tid + 256 * r;
-            int mm, kk;
-            if (AK) { kk = idx & 15; mm = idx >> 4; } else { mm = idx & 63; kk = idx >> 6; }
+            const int kk = akm ? (idx & (GBK - 1)) : (idx / BM);
+            const int mm = akm ? (idx / GBK) : (idx & (BM - 1));
             const int64_t gm = m0 + mm, gk = k0 + kk;
-            float2 v = zero;
-            if (gm < M && gk < K) v = AK ? Ap[gm * K + gk] : Ap[gk * M + gm];
-            As[kk][mm] = v;
-            int nn;
-            if (BK) { kk = idx & 15; nn = idx >> 4; } else { nn = idx & 63; kk = idx >> 6; }
-            const int64_t gn = n0 + nn, gk2 = k0 + kk;
-            float2 w = zero;
-            if (gn < N && gk2 < K) w = BK ? Bp[gn * K + gk2] : Bp[gk2 * N + gn];
-            Bs[kk][nn] = w;
+            ra[r] = (gm < M && gk < K) ? (akm ? Ap[gm * K + gk] : Ap[gk * M + gm]) : zero;
         }
-        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < LB; ++r) {
+            const int idx = tid + 256 * r;
+            const int kk = bkm ? (idx & (GBK - 1)) : (idx / BN);
+            const int nn = bkm ? (idx / GBK) : (idx & (BN - 1));
+            const int64_t gn = n0 + nn, gk = k0 + kk;
+            rb[r] = (gn < N && gk < K) ? (bkm ? Bp[gn * K + gk] : Bp[gk * N + gn]) : zero;
+        }
+    };
+    auto sstore = [&](int buf) {
+#pragma unroll
+        for (int r = 0; r < LA; ++r) {
+            const int idx = tid + 256 * r;
+            const int kk = akm ? (idx & (GBK - 1)) : (idx / BM);
+            const int mm = akm ? (idx / GBK) : (idx & (BM - 1));
+            As[buf][kk][mm] = ra[r];
+        }
+#pragma unroll
+        for (int r = 0; r < LB; ++r) {
+            const int idx = tid + 256 * r;
+            const int kk = bkm ? (idx & (GBK - 1)) : (idx / BN);
+            const int nn = bkm ? (idx / GBK) : (idx & (BN - 1));
+            Bs[buf][kk][nn] = rb[r];
+        }
+    };
+
+    float2 tot[TM][TN], acc[TM][TN];
+#pragma unroll
+    for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) tot[i][j] = acc[i][j] = zero;
+    gload(0);
+    sstore(0);
+    __syncthreads();
+    int buf = 0, stage = 0;
+    for (int64_t k0 = 0; k0 < K; k0 += GBK) {
+        const bool more = k0 + GBK < K;
+        if (more) gload(k0 + GBK);
 #pragma unroll
         for (int kk = 0; kk < GBK; ++kk) {
-            float2 a[4], b[4];
+            float2 a[TM], b[TN];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+            for (int i = 0; i < TM; ++i) a[i] = As[buf][kk][ty + 16 * i];
 #pragma unroll
-            for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+            for (int j = 0; j < TN; ++j) b[j] = Bs[buf][kk][tx + 16 * j];
 #pragma unroll
-            for (int i = 0; i < 4; ++i)
+            for (int i = 0; i < TM; ++i)
 #pragma unroll
-                for (int j = 0; j < 4; ++j) cfma(acc[i][j], a[i], b[j]);
+                for (int j = 0; j < TN; ++j) cfma(acc[i][j], a[i], b[j]);
         }
+        if (++stage == GFOLD || !more) {
+            stage = 0;
+#pragma unroll
+            for (int i = 0; i < TM; ++i)
+#pragma unroll
+                for (int j = 0; j < TN; ++j) {
+                    tot[i][j].x += acc[i][j].x;
+                    tot[i][j].y += acc[i][j].y;
+                    acc[i][j] = zero;
+                }
+        }
+        if (more) sstore(buf ^ 1);
         __syncthreads();
+        buf ^= 1;
     }
     float2* Cp = C + item * c_is;
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
+    for (int i = 0; i < TM; ++i) {
         const int64_t gm = m0 + ty + 16 * i;
         if (gm >= M) continue;
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
+        for (int j = 0; j < TN; ++j) {
             const int64_t gn = n0 + tx + 16 * j;
-            if (gn < N) Cp[gm * N + gn] = acc[i][j];
+            if (gn < N) Cp[gm * N + gn] = tot[i][j];
         }
     }
+}
+
+// Long dot products (M * N <= 16 outputs, large K): one CTA per item, the 256
+// threads stride over K with a private partial per output, then a fixed-order
+// tree reduction (deterministic).
+template <int MB, int NB>
+__global__ void __launch_bounds__(256) k_dot_c64(const float2* __restrict__ A, int64_t a_is, bool akm,
+                                                 const float2* __restrict__ B, int64_t b_is, bool bkm,
+                                                 float2* __restrict__ C, int64_t c_is, int kb) {
+    constexpr int M = 1 << MB, N = 1 << NB, MN = M * N;
+    __shared__ float2 red[MN][256];
+    const int64_t K = (int64_t)1 << kb;
+    const int64_t item = blockIdx.x;
+    const float2* Ap = A + item * a_is;
+    const float2* Bp = B + item * b_is;
+    const int tid = threadIdx.x;
+    float2 acc[MN];
+#pragma unroll
+    for (int i = 0; i < MN; ++i) acc[i] = make_float2(0.f, 0.f);
+    for (int64_t k = tid; k < K; k += 256) {
+        float2 a[M], b[N];
+#pragma unroll
+        for (int m = 0; m < M; ++m) a[m] = akm ? Ap[m * K + k] : Ap[k * M + m];
+#pragma unroll
+        for (int n = 0; n < N; ++n) b[n] = bkm ? Bp[n * K + k] : Bp[k * N + n];
+#pragma unroll
+        for (int m = 0; m < M; ++m)
+#pragma unroll
+            for (int n = 0; n < N; ++n) cfma(acc[m * N + n], a[m], b[n]);
+    }
+#pragma unroll
+    for (int i = 0; i < MN; ++i) red[i][tid] = acc[i];
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (tid < w) {
+#pragma unroll
+            for (int i = 0; i < MN; ++i) {
+                red[i][tid].x += red[i][tid + w].x;
+                red[i][tid].y += red[i][tid + w].y;
+            }
+        }
+        __syncthreads();
+    }
+    if (tid < MN) C[item * c_is + tid] = red[tid][0];
+}
+
+template <int BM, int BN>
+static void gemm_tile(dim3 grid, cudaStream_t st, const float2* a, int64_t a_is, bool akm, const float2* b,
+                      int64_t b_is, bool bkm, float2* c, int64_t c_is, int mb, int nb, int kb, int tn) {
+    k_gemm_c64<BM, BN><<<grid, 256, 0, st>>>(a, a_is, akm, b, b_is, bkm, c, c_is, mb, nb, kb, tn);
 }
 
 cudaError_t launch_gemm_c64(const float2* a, int64_t a_is, bool a_kmajor, const float2* b, int64_t b_is,
                             bool b_kmajor, float2* c, int64_t c_is, int mb, int nb, int kb, int64_t n_items,
                             cudaStream_t st) {
     if (n_items <= 0) return cudaSuccess;
-    const int64_t tm = ((1ll << mb) + GBM - 1) / GBM, tn = ((1ll << nb) + GBN - 1) / GBN;
+    if (mb + nb <= 4 && kb >= 8) {
+        dim3 grid((unsigned)n_items);
+#define QX_DOT_CASE(X, Y)                                                                                   \
+    if (mb == X && nb == Y) {                                                                               \
+        k_dot_c64<X, Y><<<grid, 256, 0, st>>>(a, a_is, a_kmajor, b, b_is, b_kmajor, c, c_is, kb);          \
+        return cudaGetLastError();                                                                          \
+    }
+        QX_DOT_CASE(0, 0) QX_DOT_CASE(0, 1) QX_DOT_CASE(0, 2) QX_DOT_CASE(0, 3) QX_DOT_CASE(0, 4)
+        QX_DOT_CASE(1, 0) QX_DOT_CASE(1, 1) QX_DOT_CASE(1, 2) QX_DOT_CASE(1, 3)
+        QX_DOT_CASE(2, 0) QX_DOT_CASE(2, 1) QX_DOT_CASE(2, 2)
+        QX_DOT_CASE(3, 0) QX_DOT_CASE(3, 1) QX_DOT_CASE(4, 0)
+#undef QX_DOT_CASE
+        return cudaErrorInvalidValue;
+    }
+    const int bmb = mb >= 6 ? 6 : mb >= 5 ? 5 : 4;  // tile edge 64 / 32 / 16 complex
+    const int bnb = nb >= 6 ? 6 : nb >= 5 ? 5 : 4;
+    const int64_t tm = ((1ll << mb) + (1 << bmb) - 1) >> bmb, tn = ((1ll << nb) + (1 << bnb) - 1) >> bnb;
     dim3 grid((unsigned)(tm * tn), (unsigned)n_items);
-    if (a_kmajor && b_kmajor)
-        k_gemm_c64<true, true><<<grid, 256, 0, st>>>(a, a_is, b, b_is, c, c_is, mb, nb, kb, (int)tn);
-    else if (a_kmajor)
-        k_gemm_c64<true, false><<<grid, 256, 0, st>>>(a, a_is, b, b_is, c, c_is, mb, nb, kb, (int)tn);
-    else if (b_kmajor)
-        k_gemm_c64<false, true><<<grid, 256, 0, st>>>(a, a_is, b, b_is, c, c_is, mb, nb, kb, (int)tn);
-    else
-        k_gemm_c64<false, false><<<grid, 256, 0, st>>>(a, a_is, b, b_is, c, c_is, mb, nb, kb, (int)tn);
-    return cudaGetLastError();
+#define QX_GEMM_CASE(X, Y)                                                                            \
+    if (bmb == X && bnb == Y) {                                                                       \
+        gemm_tile<(1 << X), (1 << Y)>(grid, st, a, a_is, a_kmajor, b, b_is, b_kmajor, c, c_is, mb, nb, kb, \
+                                      (int)tn);                                                       \
+        return cudaGetLastError();                                                                    \
+    }
+    QX_GEMM_CASE(6, 6) QX_GEMM_CASE(6, 5) QX_GEMM_CASE(6, 4)
+    QX_GEMM_CASE(5, 6) QX_GEMM_CASE(5, 5) QX_GEMM_CASE(5, 4)
+    QX_GEMM_CASE(4, 6) QX_GEMM_CASE(4, 5) QX_GEMM_CASE(4, 4)
+#undef QX_GEMM_CASE
+    return cudaErrorInvalidValue;
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -312,16 +429,19 @@ cudaError_t launch_slice_sum(const SumDesc& d, const ItemCtx& ic, double* acc, c
     return cudaGetLastError();
 }
 
-__global__ void k_finalize(const double* __restrict__ acc, double* __restrict__ amps, int64_t n) {
+__global__ void k_finalize(const double* __restrict__ acc, double* __restrict__ amps, int64_t n, double sr,
+                           double si) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    amps[2 * i] = acc[4 * i] + acc[4 * i + 2];
-    amps[2 * i + 1] = acc[4 * i + 1] + acc[4 * i + 3];
+    const double re = acc[4 * i] + acc[4 * i + 2];
+    const double im = acc[4 * i + 1] + acc[4 * i + 3];
+    amps[2 * i] = re * sr - im * si;
+    amps[2 * i + 1] = re * si + im * sr;
 }
 
-cudaError_t launch_finalize(const double* acc, double* amps, int64_t n, cudaStream_t st) {
+cudaError_t launch_finalize(const double* acc, double* amps, int64_t n, double sr, double si, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
-    k_finalize<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(acc, amps, n);
+    k_finalize<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(acc, amps, n, sr, si);
     return cudaGetLastError();
 }
 
