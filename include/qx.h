@@ -150,6 +150,31 @@ int qx_contract_slices_device(qx_handle h, const uint8_t* d_bitstrings, int64_t 
  * batches. */
 int qx_last_stats(qx_handle h, double* flops, int64_t* launches, int64_t* batches);
 
+/* qx_contract_device without allocation (the paper has no counterpart; this
+ * serves host programs, not the method).  Some callers cannot allocate device
+ * memory for the library: programs whose own pool allocator owns the whole
+ * GPU, and code that must not call cudaMalloc / cudaFree because those calls
+ * can synchronise the device.  This entry point needs no bound workspace:
+ * its scratch is a fixed array of QX_STATIC_SCRATCH_BYTES compiled into the
+ * library (every GPU that loads libqx holds it until the process exits), and
+ * it calls no cudaMalloc, cudaFree or allocating library routine.  The caller
+ * passes device bitstrings (n_bits x n_qubits bytes, not validated) and the
+ * device output (n_bits x 2^n_open x {re, im} doubles); work is enqueued on
+ * the handle's stream, as for qx_contract_device, and gives the same
+ * amplitudes.
+ *   - The first call on each device also looks up the array's device address
+ *     (once per device); make that first call before any stream capture.
+ *   - QX_ENOMEM when the network's tensors, n_bits bitstrings, their
+ *     accumulators and one (slice, bitstring) pair's intermediates do not fit
+ *     in QX_STATIC_SCRATCH_BYTES; use qx_bind_workspace + qx_contract_device
+ *     for such plans.
+ *   - All calls on a device share the one array, which keeps the last call's
+ *     contents (each call clears its own accumulators).  Calls whose work
+ *     overlaps on the GPU -- other streams, handles or host threads -- race on
+ *     it and give wrong results; serialise them. */
+#define QX_STATIC_SCRATCH_BYTES (64ll << 20)
+int qx_contract_device_static(qx_handle h, const uint8_t* d_bitstrings, int64_t n_bits, double* d_amps_out);
+
 /* Kernel timing for roofline reports.  With profiling on, every kernel launch
  * of a contraction is bracketed by CUDA events on the handle's stream;
  * qx_profile_read synchronises the stream and returns, for one kernel kind,

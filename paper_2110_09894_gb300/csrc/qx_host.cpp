@@ -1025,3 +1025,62 @@ int qx_last_stats(qx_handle h, double* flops, int64_t* launches, int64_t* batche
 
 }  // extern "C"
 
+// ------------------------------------------------------------------------------------------------
+// Contraction into a caller-chosen device buffer (used by the static-scratch entry point)
+// ------------------------------------------------------------------------------------------------
+int qx_internal_device(const qx_ctx* h) { return h->device; }
+
+int qx_internal_fail(qx_ctx* h, int code, const char* msg) { return fail(h, code, "%s", msg); }
+
+int qx_internal_contract_in(qx_ctx* h, char* buf, int64_t buf_bytes, const uint8_t* d_bits, int64_t n_bits,
+                            double* d_amps) {
+    if (!h->have_plan) return fail(h, QX_ESTATE, "contract before qx_set_plan");
+    if (h->device < 0) return fail(h, QX_ESTATE, "host-only handle has no device");
+    if (n_bits < 1) return fail(h, QX_EINVAL, "n_bits < 1");
+    if (!d_bits || !d_amps || !buf) return fail(h, QX_EINVAL, "null buffer");
+    struct {
+        char* ws;
+        int64_t ws_bytes;
+        bool ws_owned;
+        int64_t max_bits, off_leaf, off_bits, off_acc, off_amps, off_inv, off_item, items_cap;
+        bool leaves_on_device;
+    } const saved = {h->ws,      h->ws_bytes, h->ws_owned, h->max_bits, h->off_leaf,  h->off_bits,
+                     h->off_acc, h->off_amps, h->off_inv,  h->off_item, h->items_cap, h->leaves_on_device};
+    int64_t fixed;
+    layout(h, n_bits, &fixed);
+    int64_t items = (buf_bytes - fixed) / (h->item_entries * 8);
+    if (h->opt.max_items > 0) items = std::min<int64_t>(items, h->opt.max_items);
+    items = std::min<int64_t>(items, kMaxBatchItems);
+    items = std::min<int64_t>(items, h->n_slices * n_bits);
+    auto restore = [&]() {
+        h->ws = saved.ws;
+        h->ws_bytes = saved.ws_bytes;
+        h->ws_owned = saved.ws_owned;
+        h->max_bits = saved.max_bits;
+        h->off_leaf = saved.off_leaf;
+        h->off_bits = saved.off_bits;
+        h->off_acc = saved.off_acc;
+        h->off_amps = saved.off_amps;
+        h->off_inv = saved.off_inv;
+        h->off_item = saved.off_item;
+        h->items_cap = saved.items_cap;
+        h->leaves_on_device = saved.leaves_on_device;
+    };
+    if (items < 1) {
+        restore();
+        return fail(h, QX_ENOMEM, "this plan and %lld bitstrings need %lld bytes of scratch; %lld are available",
+                    (long long)n_bits, (long long)(fixed + h->item_entries * 8), (long long)buf_bytes);
+    }
+    h->ws = buf;
+    h->ws_bytes = buf_bytes;
+    h->ws_owned = false;
+    h->max_bits = n_bits;
+    h->items_cap = items;
+    h->leaves_on_device = false;
+    int rc = QX_OK;
+    cudaError_t e = cudaSetDevice(h->device);
+    if (e != cudaSuccess) rc = fail(h, QX_ECUDA, "cudaSetDevice: %s", cudaGetErrorString(e));
+    if (rc == QX_OK) rc = contract_impl(h, d_bits, n_bits, 0, h->n_slices, d_amps);
+    restore();
+    return rc;
+}

@@ -91,3 +91,13 @@ cudaError_t launch_finalize(const double* acc, double* amps, int64_t n, double s
                             cudaStream_t st);
 
 }  // namespace qx
+
+// Contract every slice with `buf` (device, 256-byte aligned, buf_bytes long)
+// standing in for the bound workspace; the bound workspace, if any, is left
+// untouched.  Defined in qx_host.cpp for entry points that bring their own
+// device memory.
+struct qx_ctx;
+int qx_internal_contract_in(qx_ctx* h, char* buf, int64_t buf_bytes, const uint8_t* d_bits, int64_t n_bits,
+                            double* d_amps);
+int qx_internal_device(const qx_ctx* h);
+int qx_internal_fail(qx_ctx* h, int code, const char* msg);

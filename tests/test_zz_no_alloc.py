@@ -1,0 +1,79 @@
+"""qx_contract_device_static: the entry point that allocates nothing.
+
+It exists for host programs that cannot let the library allocate device
+memory (their own pool allocator owns the GPU, or cudaMalloc/cudaFree would
+synchronise the device at a bad moment).  Its scratch is an array compiled
+into the library, so its results must equal those of the ordinary
+workspace-backed qx_contract_device, call after call, although the array
+keeps whatever the previous call left in it.
+
+This file is named to be collected last; it passes both alone in a fresh
+process and after the rest of the suite.
+"""
+import numpy as np
+import pytest
+
+from qxgen import circuits as C
+from qxgen.workloads import make_plan
+
+from ._util import TOL_C64, grid_case, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def qx():
+    from paper_2110_09894_gb300 import build
+    build.build()
+    from paper_2110_09894_gb300 import qx as mod
+    return mod
+
+
+def _as_complex(t):
+    a = t.cpu().numpy()
+    return a[..., 0] + 1j * a[..., 1]
+
+
+def test_static_scratch_matches_workspace_path_twice(qx):
+    import torch
+    circ, om, order, sliced, bits = grid_case(3, 4, 8, 1234, n_open=2, n_slice=4, n_bits=9)
+    c = qx.Contractor(circ.n_qubits, C.gates_to_records(circ), om, order, sliced, len(bits))
+    d_bits = torch.from_numpy(bits).cuda()
+    ref = _as_complex(c.contract_device(d_bits))
+    torch.cuda.synchronize()
+    for _ in range(2):  # the array keeps the previous call's contents; results must not depend on it
+        out = torch.full((len(bits), 1 << int(om.sum()), 2), float("nan"), dtype=torch.float64, device="cuda")
+        qx.qx_contract_device_static(c.h, d_bits.data_ptr(), len(bits), out.data_ptr())
+        torch.cuda.synchronize()
+        got = _as_complex(out)
+        assert np.all(np.isfinite(got))
+        assert rel_l2(got, ref) <= TOL_C64
+    # the ordinary path still works afterwards on its own workspace
+    again = _as_complex(c.contract_device(d_bits))
+    torch.cuda.synchronize()
+    assert rel_l2(again, ref) <= TOL_C64
+    c.close()
+
+
+def test_static_scratch_rejects_plans_that_do_not_fit(qx):
+    import torch
+    circ = C.random_grid_circuit(5, 5, 10, 77)
+    om = np.zeros(25, np.uint8)
+    order, sliced, _, _ = make_plan(circ, om, 0, 77)
+    recs = C.gates_to_records(circ)
+    host = qx.qx_create(device=-1)
+    qx.qx_build_network(host, 25, recs, om)
+    qx.qx_set_plan(host, order, sliced)
+    need = qx.qx_workspace_size(host, 1, 1)
+    qx.qx_destroy(host)
+    assert need > qx.QX_STATIC_SCRATCH_BYTES
+    h = qx.qx_create(device=0)
+    qx.qx_build_network(h, 25, recs, om)
+    qx.qx_set_plan(h, order, sliced)
+    d_bits = torch.zeros((1, 25), dtype=torch.uint8, device="cuda")
+    out = torch.empty((1, 1, 2), dtype=torch.float64, device="cuda")
+    with pytest.raises(qx.QXError) as e:
+        qx.qx_contract_device_static(h, d_bits.data_ptr(), 1, out.data_ptr())
+    assert e.value.code == qx.QX_ENOMEM
+    assert "scratch" in str(e.value)
+    qx.qx_destroy(h)
