@@ -29,6 +29,8 @@ from qxgen import circuits as C  # noqa: E402
 from qxgen import workloads as W  # noqa: E402
 
 L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
+# name -> (C-ABI code, tensor-core products per real MMA, peak ratio to measured BF16)
+PRECISIONS = {"c64": (0, 0, 0.0), "3xtf32": (1, 3, 1.1 / 2.25), "bf16x3": (2, 6, 1.0)}
 
 
 def parse():
@@ -40,6 +42,7 @@ def parse():
     p.add_argument("--workload", default="sliced", choices=["small", "sliced", "large"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--max-items", type=int, default=0, help="cap on (slice, bitstring) pairs per batch (0 = fill)")
+    p.add_argument("--precision", default="c64", choices=list(PRECISIONS))
     return p.parse_args()
 
 
@@ -58,7 +61,7 @@ def config_of(w, extra=None):
            "grid": f"{w.circuit.rows}x{w.circuit.cols}", "sliced_bonds": len(w.sliced), "slices": w.n_slices,
            "bitstrings_per_gpu": int(len(w.bitstrings)), "open_qubits": w.n_open,
            "amplitudes_per_gpu": int(len(w.bitstrings)) << w.n_open, "peak_entries": 1 << w.peak_rank,
-           "plan": "seeded greedy (order) + tree trimming (slices)", "precision": "c64 (FP32 FMA), FP64 slice sum"}
+           "plan": "seeded greedy (order) + tree trimming (slices)", "precision": None}
     cfg.update(extra or {})
     return cfg
 
@@ -225,7 +228,7 @@ def main():
     amps_per_step = n_bits << w.n_open
     with torch.cuda.stream(stream):
         c = qx.Contractor(w.n_qubits, w.gates, w.open_mask, w.order, w.sliced, n_bits, device=local, stream=stream,
-                          max_items=args.max_items)
+                          max_items=args.max_items, precision=PRECISIONS[args.precision][0])
         d_bits = torch.from_numpy(bits).to(dev)
         d_amps = torch.empty((n_bits, 1 << w.n_open, 2), dtype=torch.float64, device=dev)
         flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
@@ -301,7 +304,14 @@ def main():
     dom = max(prof, key=lambda k: prof[k]["ms"])
     d = prof[dom]
     avg_ms = d["ms"] / max(d["launches"], 1)
-    if dom == "gemm":
+    if dom == "tc_gemm":
+        code, products, ratio = PRECISIONS[args.precision]
+        peak = pk["bf16_tflops"] * ratio
+        achieved = d["flops"] * products / (d["ms"] / 1e3) / 1e12  # issued real tensor flops
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "peak_source": f"bf16_tflops ({pk_src}, burst) x {ratio:.3f} nominal {args.precision} ratio",
+                "issued_products": products}
+    elif dom == "gemm":
         clk = pk.get("sm_max_mhz", 2070.0)
         n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
         peak = n_sm * 128 * 2 * clk * 1e6 / 1e12  # FP32 FMA lanes x 2 flops x clock
@@ -338,8 +348,9 @@ def main():
 
     line = {"metric": "amplitudes/s", "value": value, "unit": "amplitudes/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "c64", "data": "synthetic",
-            "config": config_of(w, {"parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
+            "vs_baseline": None, "dtype": {"c64": "c64", "3xtf32": "tf32x3", "bf16x3": "bf16x3"}[args.precision],
+            "data": "synthetic",
+            "config": config_of(w, {"precision": args.precision + " contraction, FP64 slice sum", "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
                                     "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MiB write); "
                                           f"workspace {ws_gb:.1f} GB",
                                     "batches_per_step": c.stats()["batches"]}),

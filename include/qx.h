@@ -59,6 +59,9 @@ extern "C" {
 #define QX_PREC_3XTF32      1  /* tcgen05 TF32, 3-product compensated split   */
 #define QX_PREC_SPLIT_BF16  2  /* tcgen05 BF16, 3-way split, 6 products       */
 #define QX_PREC_FP16_SCALED 3  /* tcgen05 FP16 with per-tensor power-2 scale  */
+/* The tensor-core forms apply to contraction steps with M >= 128, N >= 64 and
+ * K >= 32 (complex; the larger free side is taken as M); every other step runs
+ * in the complex64 SIMT kernels. */
 
 typedef struct qx_ctx* qx_handle;
 
@@ -150,6 +153,12 @@ int qx_contract_slices_device(qx_handle h, const uint8_t* d_bitstrings, int64_t 
  * batches. */
 int qx_last_stats(qx_handle h, double* flops, int64_t* launches, int64_t* batches);
 
+/* Synchronise the handle's stream and report a device-side failure of the
+ * work enqueued since the last contraction started: QX_OK, or QX_ETIMEOUT if
+ * a bounded wait inside a kernel expired (the kernel then returned early and
+ * the amplitudes are invalid).  qx_contract checks this itself. */
+int qx_device_status(qx_handle h);
+
 /* qx_contract_device without allocation (the paper has no counterpart; this
  * serves host programs, not the method).  Some callers cannot allocate device
  * memory for the library: programs whose own pool allocator owns the whole
@@ -185,7 +194,9 @@ int qx_contract_device_static(qx_handle h, const uint8_t* d_bitstrings, int64_t 
 #define QX_KERNEL_SMALL   1
 #define QX_KERNEL_GEMM    2
 #define QX_KERNEL_SUM     3
-#define QX_KERNEL_KINDS   4
+#define QX_KERNEL_TC_PREP 4  /* operand split / expansion for the tensor-core forms */
+#define QX_KERNEL_TC_GEMM 5  /* tcgen05 complex GEMM */
+#define QX_KERNEL_KINDS   6
 int qx_set_profiling(qx_handle h, int enable);
 int qx_profile_read(qx_handle h, int kind, double* ms, int64_t* launches, double* flops, double* bytes);
 

@@ -72,6 +72,8 @@ struct Op {
     bool a_km = true, b_km = true;
     int mb = 0, nb = 0, kb = 0;
     int dst = -1;           // output storage
+    int tc = 0;             // tensor-core form (0: SIMT)
+    int spa = -1, spb = -1; // split-part storages of the tensor-core form
     double flops = 0;
 };
 
@@ -115,7 +117,7 @@ struct qx_ctx {
     int64_t ws_bytes = 0;
     bool ws_owned = false;
     int64_t max_bits = 0;
-    int64_t off_leaf = 0, off_bits = 0, off_acc = 0, off_amps = 0, off_inv = 0, off_item = 0;
+    int64_t off_err = 0, off_leaf = 0, off_bits = 0, off_acc = 0, off_amps = 0, off_inv = 0, off_item = 0;
     int64_t items_cap = 0;
     bool leaves_on_device = false;
 
@@ -477,7 +479,18 @@ static int compile_plan(qx_ctx* h, const int64_t* order, int64_t n_steps, const 
             continue;
         }
 
-        // TTGT path: operands as matrices [M][K] / [K][M] and [N][K] / [K][N], C = [M][N]
+        // TTGT path: operands as matrices [M][K] / [K][M] and [N][K] / [K][N], C = [M][N].
+        // The tensor-core kernel tiles M by 128, so the larger free side becomes M.
+        const int tc_form = h->opt.precision == QX_PREC_3XTF32      ? TC_FORM_3XTF32
+                            : h->opt.precision == QX_PREC_SPLIT_BF16 ? TC_FORM_BF16X3
+                                                                     : 0;
+        int ga = a, gb = b;
+        std::vector<int> fA = freeA, fB = freeB;
+        if (tc_form && (int)fA.size() < 7 && (int)fB.size() >= 7) {
+            std::swap(ga, gb);
+            std::swap(fA, fB);
+        }
+        const Node GA = h->nodes[ga], GB = h->nodes[gb];
         auto contiguous_is = [&](const Node& X, const std::vector<int>& want) {
             return !X.leaf && X.fix.empty() && X.legs == want;
         };
@@ -485,7 +498,7 @@ static int compile_plan(qx_ctx* h, const int64_t* order, int64_t n_steps, const 
         std::vector<std::vector<int>> cands = {shared};
         {
             std::vector<int> sB;
-            for (int e : B.legs)
+            for (int e : GB.legs)
                 if (std::find(shared.begin(), shared.end(), e) != shared.end()) sB.push_back(e);
             if (sB != shared) cands.push_back(sB);
         }
@@ -493,31 +506,31 @@ static int compile_plan(qx_ctx* h, const int64_t* order, int64_t n_steps, const 
         best.cost = -1;
         for (auto& S : cands) {
             Choice c{S, true, true, true, true, 0};
-            std::vector<int> ak = freeA, am = S, bk = freeB, bm = S;
+            std::vector<int> ak = fA, am = S, bk = fB, bm = S;
             ak.insert(ak.end(), S.begin(), S.end());
-            am.insert(am.end(), freeA.begin(), freeA.end());
+            am.insert(am.end(), fA.begin(), fA.end());
             bk.insert(bk.end(), S.begin(), S.end());
-            bm.insert(bm.end(), freeB.begin(), freeB.end());
-            if (contiguous_is(A, ak)) { c.pa = false; c.akm = true; }
-            else if (contiguous_is(A, am)) { c.pa = false; c.akm = false; }
-            if (contiguous_is(B, bk)) { c.pb = false; c.bkm = true; }
-            else if (contiguous_is(B, bm)) { c.pb = false; c.bkm = false; }
-            c.cost = (c.pa ? (double)node_entries(A) : 0.0) + (c.pb ? (double)node_entries(B) : 0.0);
+            bm.insert(bm.end(), fB.begin(), fB.end());
+            if (contiguous_is(GA, ak)) { c.pa = false; c.akm = true; }
+            else if (contiguous_is(GA, am)) { c.pa = false; c.akm = false; }
+            if (contiguous_is(GB, bk)) { c.pb = false; c.bkm = true; }
+            else if (contiguous_is(GB, bm)) { c.pb = false; c.bkm = false; }
+            c.cost = (c.pa ? (double)node_entries(GA) : 0.0) + (c.pb ? (double)node_entries(GB) : 0.0);
             if (best.cost < 0 || c.cost < best.cost) best = c;
         }
         Op g{};
         g.type = OP_GEMM;
         g.variant = variant;
         g.step = t;
-        g.mb = (int)freeA.size();
-        g.nb = (int)freeB.size();
+        g.mb = (int)fA.size();
+        g.nb = (int)fB.size();
         g.kb = kb;
         g.a_km = best.akm;
         g.b_km = best.bkm;
         for (int side = 0; side < 2; ++side) {
-            const int nid = side ? b : a;
+            const int nid = side ? gb : ga;
             const bool perm = side ? best.pb : best.pa;
-            const std::vector<int>& fr = side ? freeB : freeA;
+            const std::vector<int>& fr = side ? fB : fA;
             int sid;
             if (perm) {
                 std::vector<int> tl = fr;
@@ -540,10 +553,18 @@ static int compile_plan(qx_ctx* h, const int64_t* order, int64_t n_steps, const 
             }
             (side ? g.sb : g.sa) = sid;
         }
-        std::vector<int> cl = freeA;
-        cl.insert(cl.end(), freeB.begin(), freeB.end());
+        std::vector<int> cl = fA;
+        cl.insert(cl.end(), fB.begin(), fB.end());
         const int st = new_storage(h, (int64_t)1 << cl.size(), variant, t);
         g.dst = st;
+        if (tc_form && g.mb >= 7 && g.nb >= 6 && g.kb >= 5) {
+            // split real parts of A [M][2K] and of the expanded B' [2N][2K], live for this step only
+            const int eb = tc_elem_bytes(tc_form);
+            const int64_t mk = (int64_t)1 << (g.mb + g.kb), nk = (int64_t)1 << (g.nb + g.kb);
+            g.tc = tc_form;
+            g.spa = new_storage(h, tc_parts_a(tc_form) * mk * 2 * eb / 8, variant, t);
+            g.spb = new_storage(h, tc_parts_b(tc_form) * nk * 4 * eb / 8, variant, t);
+        }
         g.flops = 8.0 * std::ldexp(1.0, g.mb + g.kb + g.nb);
         h->ops.push_back(g);
         h->nodes.push_back(contiguous_node(cl, variant, st));
@@ -588,6 +609,8 @@ static int64_t n_open(const qx_ctx* h) { return (int64_t)h->open_wires.size(); }
 
 static void layout(qx_ctx* h, int64_t max_bits, int64_t* fixed_bytes) {
     int64_t off = 0;
+    h->off_err = off;  // device error flag (int)
+    off += 256;
     h->off_leaf = off;
     off += align_up((int64_t)h->leaf_vals.size() * 8, 256);
     h->off_bits = off;
@@ -710,20 +733,59 @@ static int run_op(qx_ctx* h, const Op& op, const ItemCtx& ic, int64_t n_items) {
     float2* dp;
     int64_t dis;
     storage_addr(h, op.dst, &dp, &dis);
-    const int kind = op.type == OP_PERM ? QX_KERNEL_PERMUTE : op.type == OP_SMALL ? QX_KERNEL_SMALL : QX_KERNEL_GEMM;
+    const int kind = op.type == OP_PERM    ? QX_KERNEL_PERMUTE
+                     : op.type == OP_SMALL ? QX_KERNEL_SMALL
+                     : op.tc               ? QX_KERNEL_TC_PREP
+                                           : QX_KERNEL_GEMM;
     size_t slot;
-    cudaError_t e = prof_begin(h, kind, op.flops * (double)n_items, op_bytes(h, op) * (double)n_items, &slot);
+    const double prep_bytes = op.tc ? 8.0 * (double)(h->stor[op.sa].entries + h->stor[op.sb].entries +
+                                                     h->stor[op.spa].entries + h->stor[op.spb].entries)
+                                    : 0.0;
+    cudaError_t e = prof_begin(h, kind, op.tc ? 0.0 : op.flops * (double)n_items,
+                               (op.tc ? prep_bytes : op_bytes(h, op)) * (double)n_items, &slot);
     if (e != cudaSuccess) return fail(h, QX_ECUDA, "profiling event: %s", cudaGetErrorString(e));
     if (op.type == OP_PERM) {
         e = launch_permute(perm_desc(h, op), ic, n_items, dp, dis, h->stream);
     } else if (op.type == OP_SMALL) {
         e = launch_small(small_desc(h, op), ic, n_items, dp, dis, h->stream);
-    } else {
+    } else if (!op.tc) {
         float2 *ap, *bp;
         int64_t ais, bis;
         storage_addr(h, op.sa, &ap, &ais);
         storage_addr(h, op.sb, &bp, &bis);
         e = launch_gemm_c64(ap, ais, op.a_km, bp, bis, op.b_km, dp, dis, op.mb, op.nb, op.kb, n_items, h->stream);
+    } else {
+        TcArgs g{};
+        float2 *ap, *bp, *pa, *pb;
+        int64_t ais, bis, pais, pbis;
+        storage_addr(h, op.sa, &ap, &ais);
+        storage_addr(h, op.sb, &bp, &bis);
+        storage_addr(h, op.spa, &pa, &pais);
+        storage_addr(h, op.spb, &pb, &pbis);
+        g.a = ap;
+        g.a_is = ais;
+        g.a_kmajor = op.a_km;
+        g.b = bp;
+        g.b_is = bis;
+        g.b_kmajor = op.b_km;
+        g.c = dp;
+        g.c_is = dis;
+        g.pa = pa;
+        g.pb = pb;
+        // an item stride of 0 (one item) still needs a valid tensor-map stride
+        g.pa_is_bytes = 8 * (pais ? pais : h->stor[op.spa].entries);
+        g.pb_is_bytes = 8 * (pbis ? pbis : h->stor[op.spb].entries);
+        g.mb = op.mb;
+        g.nb = op.nb;
+        g.kb = op.kb;
+        g.n_items = n_items;
+        g.limit = h->opt.timeout_cycles > 0 ? h->opt.timeout_cycles : 2000000000ll;
+        g.err = (int*)(h->ws + h->off_err);
+        e = launch_tc_prep(op.tc, g, h->stream);
+        if (e == cudaSuccess) e = prof_end(h, slot);
+        if (e == cudaSuccess) e = prof_begin(h, QX_KERNEL_TC_GEMM, op.flops * (double)n_items, op_bytes(h, op) * (double)n_items, &slot);
+        if (e == cudaSuccess) e = launch_tc_gemm(op.tc, g, h->stream);
+        h->last_launches += 2;
     }
     if (e != cudaSuccess) return fail(h, QX_ECUDA, "kernel launch failed: %s", cudaGetErrorString(e));
     e = prof_end(h, slot);
@@ -746,6 +808,7 @@ static int contract_impl(qx_ctx* h, const uint8_t* d_bits, int64_t n_bits, int64
         h->leaves_on_device = true;
     }
     double* acc = (double*)(h->ws + h->off_acc);
+    CUDA_TRY(h, cudaMemsetAsync(h->ws + h->off_err, 0, sizeof(int), h->stream));
     CUDA_TRY(h, cudaMemsetAsync(acc, 0, (size_t)(n_bits * n_o * 32), h->stream));
     ItemCtx ic{};
     ic.n_qubits = h->nq;
@@ -824,7 +887,7 @@ int qx_create(qx_handle* out, int device, void* stream, const qx_options* opt) {
     h->device = device;
     h->stream = (cudaStream_t)stream;
     if (opt) h->opt = *opt;
-    if (h->opt.precision != QX_PREC_C64) {
+    if (h->opt.precision < QX_PREC_C64 || h->opt.precision > QX_PREC_SPLIT_BF16 || h->opt.max_items < 0) {
         delete h;
         return QX_EINVAL;
     }
@@ -846,7 +909,10 @@ const char* qx_last_error(qx_handle h) { return h ? h->err.c_str() : "null handl
 
 int qx_set_options(qx_handle h, const qx_options* opt) {
     if (!h || !opt) return QX_EINVAL;
-    if (opt->precision != QX_PREC_C64) return fail(h, QX_EINVAL, "precision form %d is not available", opt->precision);
+    if (opt->precision < QX_PREC_C64 || opt->precision > QX_PREC_SPLIT_BF16)
+        return fail(h, QX_EINVAL, "precision form %d is not available", opt->precision);
+    if (h->have_plan && opt->precision != h->opt.precision)
+        return fail(h, QX_ESTATE, "set the precision form before qx_set_plan");
     if (opt->max_items < 0) return fail(h, QX_EINVAL, "max_items < 0");
     h->opt = *opt;
     return QX_OK;
@@ -966,7 +1032,7 @@ int qx_contract_slices(qx_handle h, const uint8_t* bits, int64_t n_bits, int64_t
     const size_t out_bytes = (size_t)((n_bits << n_open(h)) * 16);
     CUDA_TRY(h, cudaMemcpyAsync(amps_out, d_amps, out_bytes, cudaMemcpyDeviceToHost, h->stream));
     CUDA_TRY(h, cudaStreamSynchronize(h->stream));
-    return QX_OK;
+    return qx_device_status(h);
 }
 
 int qx_contract(qx_handle h, const uint8_t* bits, int64_t n_bits, double* amps_out) {
@@ -1015,6 +1081,17 @@ int qx_profile_read(qx_handle h, int kind, double* ms, int64_t* launches, double
     return QX_OK;
 }
 
+int qx_device_status(qx_handle h) {
+    if (!h) return QX_EINVAL;
+    if (!h->ws) return QX_OK;
+    int flag = 0;
+    CUDA_TRY(h, cudaSetDevice(h->device));
+    CUDA_TRY(h, cudaMemcpyAsync(&flag, h->ws + h->off_err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    if (flag) return fail(h, flag, "a bounded device wait expired; the result is invalid");
+    return QX_OK;
+}
+
 int qx_last_stats(qx_handle h, double* flops, int64_t* launches, int64_t* batches) {
     if (!h) return QX_EINVAL;
     if (flops) *flops = h->last_flops;
@@ -1042,10 +1119,11 @@ int qx_internal_contract_in(qx_ctx* h, char* buf, int64_t buf_bytes, const uint8
         char* ws;
         int64_t ws_bytes;
         bool ws_owned;
-        int64_t max_bits, off_leaf, off_bits, off_acc, off_amps, off_inv, off_item, items_cap;
+        int64_t max_bits, off_err, off_leaf, off_bits, off_acc, off_amps, off_inv, off_item, items_cap;
         bool leaves_on_device;
-    } const saved = {h->ws,      h->ws_bytes, h->ws_owned, h->max_bits, h->off_leaf,  h->off_bits,
-                     h->off_acc, h->off_amps, h->off_inv,  h->off_item, h->items_cap, h->leaves_on_device};
+    } const saved = {h->ws,       h->ws_bytes, h->ws_owned, h->max_bits, h->off_err,   h->off_leaf,
+                     h->off_bits, h->off_acc,  h->off_amps, h->off_inv,  h->off_item, h->items_cap,
+                     h->leaves_on_device};
     int64_t fixed;
     layout(h, n_bits, &fixed);
     int64_t items = (buf_bytes - fixed) / (h->item_entries * 8);
@@ -1057,6 +1135,7 @@ int qx_internal_contract_in(qx_ctx* h, char* buf, int64_t buf_bytes, const uint8
         h->ws_bytes = saved.ws_bytes;
         h->ws_owned = saved.ws_owned;
         h->max_bits = saved.max_bits;
+        h->off_err = saved.off_err;
         h->off_leaf = saved.off_leaf;
         h->off_bits = saved.off_bits;
         h->off_acc = saved.off_acc;

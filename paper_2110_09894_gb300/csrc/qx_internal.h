@@ -86,6 +86,35 @@ cudaError_t launch_gemm_c64(const float2* a, int64_t a_is, bool a_kmajor, const 
                             bool b_kmajor, float2* c, int64_t c_is, int mb, int nb, int kb, int64_t n_items,
                             cudaStream_t st);
 cudaError_t launch_slice_sum(const SumDesc& d, const ItemCtx& ic, double* acc, cudaStream_t st);
+
+// Tensor-core complex GEMM (qx_tc.cu).  Operands are contiguous complex64
+// per item, [R][K] (kmajor) or [K][R]; pa / pb receive the split real parts
+// (prep), then the tcgen05 kernel writes C [M][N] complex64.
+constexpr int TC_FORM_3XTF32 = 1, TC_FORM_BF16X3 = 2;
+struct TcArgs {
+    const float2* a;
+    int64_t a_is;
+    bool a_kmajor;
+    const float2* b;
+    int64_t b_is;
+    bool b_kmajor;
+    float2* c;
+    int64_t c_is;
+    void* pa;
+    int64_t pa_is_bytes;
+    void* pb;
+    int64_t pb_is_bytes;
+    int mb, nb, kb;
+    int64_t n_items;
+    long long limit;  // clock cycles per bounded wait
+    int* err;         // device error flag (QX_ETIMEOUT on expiry)
+};
+int tc_parts_a(int form);
+int tc_parts_b(int form);
+int tc_elem_bytes(int form);
+int tc_products(int form);
+cudaError_t launch_tc_prep(int form, const TcArgs& g, cudaStream_t st);
+cudaError_t launch_tc_gemm(int form, const TcArgs& g, cudaStream_t st);
 // amps[i] = (sum + compensation) * (scale_re + i scale_im), all in FP64
 cudaError_t launch_finalize(const double* acc, double* amps, int64_t n, double scale_re, double scale_im,
                             cudaStream_t st);

@@ -1,0 +1,468 @@
+// Tensor-core complex GEMM for the large pairwise contraction steps
+// (tcgen05 MMA with TMEM accumulators, operands staged by TMA), sm_103a.
+//
+// The paper maps contractions to matrix multiplications on the GPU
+// (Sec. IV-A); here a complex product C[M][N] = A[M][K] . B[N][K]^T is run as
+// one real product on the tensor cores:
+//   * A's interleaved complex storage, read as floats, already is the real
+//     matrix A_r[M][2K] = (re a_m0, im a_m0, re a_m1, ...);
+//   * B is expanded to B'[2N][2K] with rows 2n = (re b, -im b, ...) and
+//     2n+1 = (im b, re b, ...), so that row m of A_r times row 2n (2n+1) of B'
+//     is the real (imaginary) part of C[m][n];
+//   * the real result C_r[M][2N] is C's interleaved complex storage.
+// Precision forms split each real operand into parts and sum part products
+// in one FP32 TMEM accumulator:
+//   3xTF32:  x = hi + lo (hi = x rounded to TF32); hi.hi + hi.lo + lo.hi
+//   BF16x3:  x = b0 + b1 + b2 (each rounded to BF16 in turn);
+//            b0b0 + b0b1 + b1b0 + b0b2 + b1b1 + b2b0
+// Tile: 128 rows of A x 128 rows of B' per CTA, one 128-byte K slab per
+// pipeline stage, two 128-column TMEM accumulators used in turn.  Warp 0
+// issues TMA, warp 1 owns TMEM and issues the MMAs, warps 2-5 add each stage's
+// TMEM partial into FP32 register totals and write C at the end.  Every mbarrier
+// wait is bounded; on expiry the kernel records QX_ETIMEOUT, waits (bounded)
+// for its own copies, frees TMEM and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstring>
+#include <mutex>
+
+#include "qx.h"
+#include "qx_internal.h"
+
+namespace qx {
+
+constexpr int TC_BM = 128, TC_BN = 128, TC_ROWB = 128, TC_THREADS = 192, TC_SMEM_LIMIT = 196608;
+
+template <int FORM>
+struct TcForm;
+template <>
+struct TcForm<TC_FORM_3XTF32> {
+    using T = float;
+    static constexpr int NPA = 2, NPB = 2, NPROD = 3, EB = 4, FMT = 2, STAGES = 3;
+    static __device__ __forceinline__ int pa(int p) { return p == 2 ? 1 : 0; }
+    static __device__ __forceinline__ int pb(int p) { return p == 1 ? 1 : 0; }
+};
+template <>
+struct TcForm<TC_FORM_BF16X3> {
+    using T = __nv_bfloat16;
+    static constexpr int NPA = 3, NPB = 3, NPROD = 6, EB = 2, FMT = 1, STAGES = 2;
+    // (0,0) (0,1) (1,0) (0,2) (1,1) (2,0)
+    static __device__ __forceinline__ int pa(int p) { return p < 2 ? 0 : p == 2 ? 1 : p == 3 ? 0 : p == 4 ? 1 : 2; }
+    static __device__ __forceinline__ int pb(int p) { return p == 0 ? 0 : p == 1 ? 1 : p == 2 ? 0 : p == 3 ? 2 : p == 4 ? 1 : 0; }
+};
+
+// ------------------------------------------------------------------------------------------------
+// operand preparation (split into parts, expand B)
+// ------------------------------------------------------------------------------------------------
+__device__ __forceinline__ float tf32_rna(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+
+template <int FORM>
+__device__ __forceinline__ void split(float x, typename TcForm<FORM>::T* out, int64_t part_stride) {
+    if constexpr (FORM == TC_FORM_3XTF32) {
+        const float hi = tf32_rna(x);
+        out[0] = hi;
+        out[part_stride] = x - hi;
+    } else {
+        const __nv_bfloat16 b0 = __float2bfloat16_rn(x);
+        const float r1 = x - __bfloat162float(b0);
+        const __nv_bfloat16 b1 = __float2bfloat16_rn(r1);
+        const float r2 = r1 - __bfloat162float(b1);
+        out[0] = b0;
+        out[part_stride] = b1;
+        out[2 * part_stride] = __float2bfloat16_rn(r2);
+    }
+}
+
+// A (complex, [R][K] if kmajor else [K][R]) -> parts [P][R][2K]
+template <int FORM>
+__global__ void k_prep_a(const float2* __restrict__ src, int64_t src_is, bool kmajor, typename TcForm<FORM>::T* dst,
+                         int64_t dst_is_elems, int rb, int kb) {
+    using T = typename TcForm<FORM>::T;
+    const int64_t R = (int64_t)1 << rb, K = (int64_t)1 << kb;
+    const int64_t item = blockIdx.y;
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= R * K) return;
+    const int64_t r = idx >> kb, k = idx & (K - 1);
+    const float2 v = src[item * src_is + (kmajor ? idx : k * R + r)];
+    T* o = dst + item * dst_is_elems + r * 2 * K + 2 * k;
+    const int64_t ps = R * 2 * K;
+    split<FORM>(v.x, o, ps);
+    split<FORM>(v.y, o + 1, ps);
+}
+
+// B (complex, [R][K] if kmajor else [K][R]) -> parts [P][2R][2K]:
+// row 2r = (re, -im) per k, row 2r+1 = (im, re)
+template <int FORM>
+__global__ void k_prep_b(const float2* __restrict__ src, int64_t src_is, bool kmajor, typename TcForm<FORM>::T* dst,
+                         int64_t dst_is_elems, int rb, int kb) {
+    using T = typename TcForm<FORM>::T;
+    const int64_t R = (int64_t)1 << rb, K = (int64_t)1 << kb;
+    const int64_t item = blockIdx.y;
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= R * K) return;
+    const int64_t r = idx >> kb, k = idx & (K - 1);
+    const float2 v = src[item * src_is + (kmajor ? idx : k * R + r)];
+    T* o = dst + item * dst_is_elems + (2 * r) * 2 * K + 2 * k;
+    const int64_t ps = 4 * R * K;
+    split<FORM>(v.x, o, ps);
+    split<FORM>(-v.y, o + 1, ps);
+    split<FORM>(v.y, o + 2 * K, ps);
+    split<FORM>(v.x, o + 2 * K + 1, ps);
+}
+
+// ------------------------------------------------------------------------------------------------
+// PTX wrappers
+// ------------------------------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t s_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t n) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(s_addr(b)), "r"(n) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(s_addr(b)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(s_addr(b)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// bounded wait: false after `limit` cycles, or early once any CTA of the
+// launch has recorded an error (so one expired wait does not make every
+// later CTA wait out its own limit)
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, long long limit, const int* err) {
+    const long long t0 = clock64();
+    uint32_t spins = 0;
+    while (!mbar_try(b, parity)) {
+        if (clock64() - t0 > limit) return false;
+        if ((++spins & 1023) == 0 && *(volatile const int*)err) return false;
+    }
+    return true;
+}
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int c0, int c1, int c2, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+        "[%5];" ::"r"(s_addr(dst)),
+        "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(c2), "r"(s_addr(bar))
+        : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_commit(uint64_t* b) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(s_addr(b))
+                 : "memory");
+}
+// 128-byte-swizzled K-major operand tile: rows of 128 B, 8-row groups 1024 B apart
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFF) >> 4);
+    d |= (uint64_t)1 << 16;            // leading byte offset (unused for swizzled K-major)
+    d |= (uint64_t)(1024 >> 4) << 32;  // stride byte offset between 8-row groups
+    d |= (uint64_t)1 << 46;            // descriptor version
+    d |= (uint64_t)2 << 61;            // 128-byte swizzle
+    return d;
+}
+template <int FORM>
+__device__ __forceinline__ void mma(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
+    if constexpr (FORM == TC_FORM_3XTF32) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\ttcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(
+                tmem),
+            "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+    } else {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\ttcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(
+                tmem),
+            "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+    }
+}
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+          "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+struct TcMaps {
+    CUtensorMap a[3];
+    CUtensorMap b[3];
+};
+
+// ------------------------------------------------------------------------------------------------
+// the GEMM
+// ------------------------------------------------------------------------------------------------
+template <int FORM>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    k_gemm_tc(const __grid_constant__ TcMaps maps, float* __restrict__ C, int64_t c_is, int M, int N2, int K2,
+              int tiles_n, long long limit, int* err) {
+    using F = TcForm<FORM>;
+    constexpr int BK = TC_ROWB / F::EB;                 // K elements per stage
+    constexpr int KSTEP = 32 / F::EB;                   // K elements per MMA (32 bytes)
+    constexpr uint32_t TILE = TC_BM * TC_ROWB;          // bytes of one 128-row part tile
+    constexpr uint32_t STAGE_BYTES = (F::NPA + F::NPB) * TILE;
+    constexpr uint32_t IDESC = (1u << 4) | ((uint32_t)F::FMT << 7) | ((uint32_t)F::FMT << 10) |
+                               ((uint32_t)(TC_BN >> 3) << 17) | ((uint32_t)(TC_BM >> 4) << 24);
+    extern __shared__ uint8_t dyn[];
+    __shared__ uint64_t full[F::STAGES], empty[F::STAGES], tfull[2], tempty[2], drain;
+    __shared__ uint32_t tmem_slot;
+    __shared__ int abort_flag;
+    if (*(volatile const int*)err) return;  // an earlier CTA of this contraction gave up
+    uint8_t* base = (uint8_t*)(((uintptr_t)dyn + 1023) & ~(uintptr_t)1023);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int item = blockIdx.y;
+    const int m0 = (blockIdx.x / tiles_n) * TC_BM;
+    const int n0 = (blockIdx.x % tiles_n) * TC_BN;
+    const int nk = (K2 + BK - 1) / BK;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < F::STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&tfull[b], 1);
+            mbar_init(&tempty[b], 4);  // one arrival per epilogue warp
+        }
+        mbar_init(&drain, 1);
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(s_addr(&tmem_slot)),
+                     "r"(2 * TC_BN)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_slot;
+
+    if (warp == 0 && lane == 0) {
+        // producer
+        int issued = 0;
+        for (int it = 0; it < nk; ++it) {
+            const int s = it % F::STAGES, n = it / F::STAGES;
+            if (!mbar_wait(&empty[s], (n & 1) ^ 1, limit, err) || *(volatile int*)&abort_flag) {
+                atomicExch(&abort_flag, 1);
+                break;
+            }
+            mbar_expect_tx(&full[s], STAGE_BYTES);
+            uint8_t* st = base + s * STAGE_BYTES;
+#pragma unroll
+            for (int p = 0; p < F::NPA; ++p) tma_load_3d(st + p * TILE, &maps.a[p], it * BK, m0, item, &full[s]);
+#pragma unroll
+            for (int p = 0; p < F::NPB; ++p)
+                tma_load_3d(st + (F::NPA + p) * TILE, &maps.b[p], it * BK, n0, item, &full[s]);
+            ++issued;
+        }
+        if (*(volatile int*)&abort_flag) {
+            // let every copy already issued land before the CTA goes away
+            for (int it = (issued > F::STAGES ? issued - F::STAGES : 0); it < issued; ++it)
+                mbar_wait(&full[it % F::STAGES], (it / F::STAGES) & 1, limit, err);
+        }
+    } else if (warp == 1 && lane == 0) {
+        // MMA issuer: stage `it` accumulates (fresh) into TMEM buffer it & 1
+        bool ok = true;
+        for (int it = 0; it < nk && ok; ++it) {
+            const int s = it % F::STAGES, n = it / F::STAGES;
+            const int b = it & 1, u = it >> 1;
+            if (!mbar_wait(&full[s], n & 1, limit, err) ||
+                (u > 0 && !mbar_wait(&tempty[b], (u - 1) & 1, limit, err)) || *(volatile int*)&abort_flag) {
+                atomicExch(&abort_flag, 1);
+                ok = false;
+                break;
+            }
+            tc_fence_after();
+            const uint32_t st = s_addr(base + s * STAGE_BYTES);
+            const uint32_t d = tmem + b * TC_BN;
+#pragma unroll
+            for (int kk = 0; kk < BK / KSTEP; ++kk) {
+#pragma unroll
+                for (int p = 0; p < F::NPROD; ++p) {
+                    const uint64_t ad = sdesc(st + F::pa(p) * TILE + kk * 32);
+                    const uint64_t bd = sdesc(st + (F::NPA + F::pb(p)) * TILE + kk * 32);
+                    mma<FORM>(d, ad, bd, IDESC, (kk | p) != 0);
+                }
+            }
+            tc_commit(&empty[s]);
+            tc_commit(&tfull[b]);
+        }
+        if (!ok) {
+            tc_commit(&drain);
+            mbar_wait(&drain, 0, limit, err);  // MMAs already issued finish before TMEM is freed
+        }
+    } else if (warp >= 2) {
+        // epilogue: TMEM lanes 32 (warp % 4) .. + 31 are rows of the tile.  The
+        // tensor cores' FP32 accumulation drifts toward zero over long sums, so
+        // each stage's partial (<= 24 MMAs) is added to an FP32 total in
+        // registers with round-to-nearest instead of accumulating K in TMEM.
+        const int q = warp & 3;
+        float tot[TC_BN];
+#pragma unroll
+        for (int j = 0; j < TC_BN; ++j) tot[j] = 0.f;
+        bool ok = true;
+        for (int it = 0; it < nk; ++it) {
+            const int b = it & 1, u = it >> 1;
+            if (!mbar_wait(&tfull[b], u & 1, limit, err) || *(volatile int*)&abort_flag) {
+                atomicExch(&abort_flag, 1);
+                ok = false;
+                break;
+            }
+            tc_fence_after();
+#pragma unroll
+            for (int c = 0; c < TC_BN / 32; ++c) {
+                float v[32];
+                tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + b * TC_BN + 32 * c, v);
+#pragma unroll
+                for (int j = 0; j < 32; ++j) tot[32 * c + j] += v[j];
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(s_addr(&tempty[b])) : "memory");
+        }
+        if (ok) {
+            // tiles are whole (rows and columns multiples of 128; see tc_shape_ok)
+            const int row = m0 + 32 * q + lane;
+            float4* d4 = (float4*)(C + (int64_t)item * c_is + (int64_t)row * N2 + n0);
+#pragma unroll
+            for (int j = 0; j < TC_BN / 4; ++j) d4[j] = make_float4(tot[4 * j], tot[4 * j + 1], tot[4 * j + 2], tot[4 * j + 3]);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (abort_flag && threadIdx.x == 0) atomicExch(err, QX_ETIMEOUT);
+    if (warp == 1) {
+        __syncwarp();
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * TC_BN) : "memory");
+    }
+}
+
+// ------------------------------------------------------------------------------------------------
+// host side
+// ------------------------------------------------------------------------------------------------
+static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    });
+    return fn;
+}
+
+template <int FORM>
+static bool make_map(CUtensorMap* m, const void* base, int64_t k2, int64_t rows, int64_t items, int64_t item_bytes) {
+    using F = TcForm<FORM>;
+    auto fn = encode_fn();
+    if (!fn) return false;
+    const cuuint64_t dims[3] = {(cuuint64_t)k2, (cuuint64_t)rows, (cuuint64_t)items};
+    const cuuint64_t strides[2] = {(cuuint64_t)(k2 * F::EB), (cuuint64_t)item_bytes};
+    const cuuint32_t box[3] = {(cuuint32_t)(TC_ROWB / F::EB), (cuuint32_t)TC_BM, 1};
+    const cuuint32_t es[3] = {1, 1, 1};
+    const CUtensorMapDataType dt = F::EB == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+    return fn(m, dt, 3, const_cast<void*>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+              CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+int tc_parts_a(int form) { return form == TC_FORM_3XTF32 ? 2 : 3; }
+int tc_parts_b(int form) { return form == TC_FORM_3XTF32 ? 2 : 3; }
+int tc_elem_bytes(int form) { return form == TC_FORM_3XTF32 ? 4 : 2; }
+int tc_products(int form) { return form == TC_FORM_3XTF32 ? 3 : 6; }
+
+template <int FORM>
+static cudaError_t run_prep(const TcArgs& g, cudaStream_t st) {
+    using F = TcForm<FORM>;
+    using T = typename F::T;
+    const int64_t M = 1ll << g.mb, N = 1ll << g.nb, K = 1ll << g.kb;
+    dim3 grid((unsigned)((M * K + 255) / 256), (unsigned)g.n_items);
+    k_prep_a<FORM><<<grid, 256, 0, st>>>(g.a, g.a_is, g.a_kmajor, (T*)g.pa, g.pa_is_bytes / F::EB, g.mb, g.kb);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    dim3 grid2((unsigned)((N * K + 255) / 256), (unsigned)g.n_items);
+    k_prep_b<FORM><<<grid2, 256, 0, st>>>(g.b, g.b_is, g.b_kmajor, (T*)g.pb, g.pb_is_bytes / F::EB, g.nb, g.kb);
+    return cudaGetLastError();
+}
+
+template <int FORM>
+static cudaError_t run_gemm(const TcArgs& g, cudaStream_t st) {
+    using F = TcForm<FORM>;
+    const int64_t M = 1ll << g.mb, N = 1ll << g.nb, K = 1ll << g.kb;
+    const int64_t pa_part = M * 2 * K, pb_part = 4 * N * K;  // elements per part
+    TcMaps maps;
+    memset(&maps, 0, sizeof maps);
+    for (int p = 0; p < F::NPA; ++p)
+        if (!make_map<FORM>(&maps.a[p], (const char*)g.pa + p * pa_part * F::EB, 2 * K, M, g.n_items, g.pa_is_bytes))
+            return cudaErrorInvalidValue;
+    for (int p = 0; p < F::NPB; ++p)
+        if (!make_map<FORM>(&maps.b[p], (const char*)g.pb + p * pb_part * F::EB, 2 * K, 2 * N, g.n_items,
+                            g.pb_is_bytes))
+            return cudaErrorInvalidValue;
+    const int smem = F::STAGES * (F::NPA + F::NPB) * TC_BM * TC_ROWB + 1024;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    static uint64_t attr_done[4] = {0, 0, 0, 0};  // per device bit
+    static std::mutex mu;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        if (dev < 256 && !((attr_done[dev >> 6] >> (dev & 63)) & 1)) {
+            e = cudaFuncSetAttribute(k_gemm_tc<FORM>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            if (e != cudaSuccess) return e;
+            attr_done[dev >> 6] |= 1ull << (dev & 63);
+        }
+    }
+    const int tiles_m = (int)((M + TC_BM - 1) / TC_BM), tiles_n = (int)((2 * N + TC_BN - 1) / TC_BN);
+    dim3 grid((unsigned)(tiles_m * tiles_n), (unsigned)g.n_items);
+    k_gemm_tc<FORM><<<grid, TC_THREADS, smem, st>>>(maps, (float*)g.c, g.c_is * 2, (int)M, (int)(2 * N), (int)(2 * K),
+                                                   tiles_n, g.limit, g.err);
+    return cudaGetLastError();
+}
+
+static bool tc_shape_ok(const TcArgs& g) {
+    // whole 128 x 128 tiles and whole 128-byte K slabs (see the plan compiler)
+    return g.mb >= 7 && g.nb >= 6 && g.kb >= 5 && g.n_items > 0 && g.n_items <= 65535;
+}
+
+cudaError_t launch_tc_prep(int form, const TcArgs& g, cudaStream_t st) {
+    if (!tc_shape_ok(g)) return cudaErrorInvalidValue;
+    if (form == TC_FORM_3XTF32) return run_prep<TC_FORM_3XTF32>(g, st);
+    if (form == TC_FORM_BF16X3) return run_prep<TC_FORM_BF16X3>(g, st);
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_tc_gemm(int form, const TcArgs& g, cudaStream_t st) {
+    if (!tc_shape_ok(g)) return cudaErrorInvalidValue;
+    if (form == TC_FORM_3XTF32) return run_gemm<TC_FORM_3XTF32>(g, st);
+    if (form == TC_FORM_BF16X3) return run_gemm<TC_FORM_BF16X3>(g, st);
+    return cudaErrorInvalidValue;
+}
+
+static_assert(TcForm<TC_FORM_3XTF32>::STAGES * 4 * TC_BM * TC_ROWB + 1024 <= TC_SMEM_LIMIT + 1024, "smem");
+static_assert(TcForm<TC_FORM_BF16X3>::STAGES * 6 * TC_BM * TC_ROWB + 1024 <= TC_SMEM_LIMIT + 1024, "smem");
+
+}  // namespace qx

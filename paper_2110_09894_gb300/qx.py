@@ -23,9 +23,9 @@ _NAMES = {QX_EINVAL: "QX_EINVAL", QX_ENOMEM: "QX_ENOMEM", QX_ECUDA: "QX_ECUDA", 
 EXPORTS = ("qx_create", "qx_destroy", "qx_last_error", "qx_set_options", "qx_build_network", "qx_network_info",
            "qx_set_plan", "qx_workspace_size", "qx_bind_workspace", "qx_contract", "qx_contract_device",
            "qx_contract_slices", "qx_contract_slices_device", "qx_last_stats", "qx_set_profiling",
-           "qx_profile_read", "qx_contract_device_static")
+           "qx_profile_read", "qx_contract_device_static", "qx_device_status")
 QX_STATIC_SCRATCH_BYTES = 64 << 20
-KERNEL_KINDS = ("permute", "small", "gemm", "sum")
+KERNEL_KINDS = ("permute", "small", "gemm", "sum", "tc_prep", "tc_gemm")
 
 
 class QXError(RuntimeError):
@@ -73,6 +73,7 @@ def load(path=None):
         "qx_last_stats": ([vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64), ctypes.POINTER(i64)],
                           ctypes.c_int),
         "qx_set_profiling": ([vp, ctypes.c_int], ctypes.c_int),
+        "qx_device_status": ([vp], ctypes.c_int),
         "qx_contract_device_static": ([vp, vp, i64, vp], ctypes.c_int),
         "qx_profile_read": ([vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64),
                              ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
@@ -178,6 +179,10 @@ def qx_contract_device_static(h, d_bits_ptr, n_bits, d_amps_ptr):
     """Contract with the library's built-in scratch array: nothing is allocated."""
     _check(h, load().qx_contract_device_static(h, ctypes.c_void_p(int(d_bits_ptr)), int(n_bits),
                                                ctypes.c_void_p(int(d_amps_ptr))))
+
+
+def qx_device_status(h):
+    _check(h, load().qx_device_status(h))
 
 
 def qx_last_stats(h):

@@ -1,0 +1,71 @@
+"""Tensor-core precision forms (tcgen05 3xTF32 and 3-way split BF16) against
+the complex128 oracle, through the C ABI (needs a GPU).
+
+Both compensated forms must meet the same relative l2 tolerance as the plain
+complex64 path; the large workload's long reductions (K up to 2^15) are the
+stress case for FP32 accumulation in TMEM.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from qxgen import workloads as W
+
+from ._util import TOL_C64, grid_case, rel_l2
+
+pytestmark = pytest.mark.gpu
+HERE = os.path.dirname(os.path.abspath(__file__))
+FORMS = [1, 2]  # QX_PREC_3XTF32, QX_PREC_SPLIT_BF16
+
+
+@pytest.fixture(scope="module")
+def qx():
+    from paper_2110_09894_gb300 import build
+    build.build()
+    from paper_2110_09894_gb300 import qx as mod
+    return mod
+
+
+def _tc_launches(qx, c, run):
+    qx.qx_set_profiling(c.h, True)
+    out = run()
+    prof = qx.qx_profile_read(c.h)
+    qx.qx_set_profiling(c.h, False)
+    return out, prof["tc_gemm"]["launches"]
+
+
+@pytest.mark.parametrize("precision", FORMS)
+def test_forms_on_sliced_workload(qx, precision):
+    w = W.sliced()
+    ref = oracle.sv_amplitudes(w.n_qubits, w.gates, w.open_mask, w.bitstrings)
+    c = qx.Contractor(w.n_qubits, w.gates, w.open_mask, w.order, w.sliced, len(w.bitstrings), precision=precision)
+    got, n_tc = _tc_launches(qx, c, lambda: c.contract(w.bitstrings))
+    assert n_tc > 0, "no step ran on the tensor cores"
+    assert rel_l2(got, ref) <= TOL_C64
+    c.close()
+
+
+@pytest.mark.parametrize("precision", FORMS)
+def test_forms_with_open_legs_and_ragged_batches(qx, precision):
+    circ, om, order, sliced, bits = grid_case(4, 5, 10, 64, n_open=3, n_slice=4, n_bits=5)
+    from qxgen import circuits as C
+    recs = C.gates_to_records(circ)
+    ref = oracle.sv_amplitudes(circ.n_qubits, recs, om, bits)
+    c = qx.Contractor(circ.n_qubits, recs, om, order, sliced, len(bits), precision=precision, max_items=7)
+    got = c.contract(bits)
+    assert rel_l2(got, ref) <= TOL_C64
+
+
+@pytest.mark.parametrize("precision", FORMS)
+def test_forms_on_large_workload_32_slices(qx, precision):
+    w = W.large()
+    with open(os.path.join(HERE, "golden", "large_slices0_31.json")) as f:
+        g = json.load(f)
+    ref = np.array(g["re"]) + 1j * np.array(g["im"])
+    c = qx.Contractor(w.n_qubits, w.gates, w.open_mask, w.order, w.sliced, 1, precision=precision)
+    got, n_tc = _tc_launches(qx, c, lambda: c.contract_slices(w.bitstrings, 0, 32)[0])
+    assert n_tc > 0
+    assert rel_l2(got, ref) <= TOL_C64
