@@ -43,6 +43,7 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--max-items", type=int, default=0, help="cap on (slice, bitstring) pairs per batch (0 = fill)")
     p.add_argument("--precision", default="c64", choices=list(PRECISIONS))
+    p.add_argument("--executor", default="auto", choices=["auto", "batched", "persistent"])
     return p.parse_args()
 
 
@@ -228,7 +229,8 @@ def main():
     amps_per_step = n_bits << w.n_open
     with torch.cuda.stream(stream):
         c = qx.Contractor(w.n_qubits, w.gates, w.open_mask, w.order, w.sliced, n_bits, device=local, stream=stream,
-                          max_items=args.max_items, precision=PRECISIONS[args.precision][0])
+                          max_items=args.max_items, precision=PRECISIONS[args.precision][0],
+                          executor={"auto": 0, "batched": 1, "persistent": 2}[args.executor])
         d_bits = torch.from_numpy(bits).to(dev)
         d_amps = torch.empty((n_bits, 1 << w.n_open, 2), dtype=torch.float64, device=dev)
         flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
@@ -350,7 +352,9 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": {"c64": "c64", "3xtf32": "tf32x3", "bf16x3": "bf16x3"}[args.precision],
             "data": "synthetic",
-            "config": config_of(w, {"precision": args.precision + " contraction, FP64 slice sum", "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
+            "config": config_of(w, {"precision": args.precision + " contraction, FP64 slice sum",
+                                    "executor": args.executor,
+                                    "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
                                     "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MiB write); "
                                           f"workspace {ws_gb:.1f} GB",
                                     "batches_per_step": c.stats()["batches"]}),

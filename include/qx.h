@@ -80,7 +80,11 @@ typedef struct {
     int32_t precision;       /* QX_PREC_*                                     */
     int32_t max_items;       /* (slice, bitstring) pairs per batch; 0 = fill  */
     int32_t gemm_min_bits;   /* steps with k, m, n >= this run as GEMM; 0 = 5 */
-    int32_t reserved;
+    int32_t executor;        /* 0 auto (= 1), 1 one launch per step over a
+                                batch of pairs, 2 persistent (one launch, one
+                                pair per CTA at a time; plans without
+                                tensor-core steps), 3 member of a group (see
+                                qx_group_*; contracts only through the group) */
     int64_t timeout_cycles;  /* bound on device spin-waits; 0 = default      */
 } qx_options;
 
@@ -184,6 +188,34 @@ int qx_device_status(qx_handle h);
 #define QX_STATIC_SCRATCH_BYTES (64ll << 20)
 int qx_contract_device_static(qx_handle h, const uint8_t* d_bitstrings, int64_t n_bits, double* d_amps_out);
 
+/* Groups: the pairs of many networks in one persistent launch (uneven
+ * circuits and slice counts side by side; Sec. IV-A's slice and bitstring
+ * levels of parallelism across several circuits).  Every member handle must be
+ * created with executor = 3, have a plan without tensor-core steps and a
+ * bound workspace on the same device; the group uses member 0's stream.
+ *   qx_group_create  takes, per member, device bitstrings (n_bits[i] x
+ *                    n_qubits bytes) and a device output (n_bits[i] x 2^open x
+ *                    {re, im} doubles) that stay fixed for the group's life;
+ *                    ctas_per_sm (0 = 2) sets the persistent grid.  On error
+ *                    *g may still be returned for qx_group_last_error.
+ *   qx_group_bind    takes caller-owned device scratch of at least
+ *                    qx_group_scratch_size bytes, uploads the members' tensors
+ *                    and programs and synchronises the stream.
+ *   qx_group_run     only enqueues: one launch for all members' invariant
+ *                    tensors, one persistent launch for all (slice, bitstring)
+ *                    pairs (largest programs first), one FP64 compensated sum
+ *                    into the outputs.  No allocation, no host copies, no
+ *                    synchronisation, so a CUDA graph can capture it.
+ * A group does not own its members; destroy it before them. */
+typedef struct qx_group* qx_group_t;
+int qx_group_create(qx_group_t* g, qx_handle* hs, int32_t n, const uint8_t* const* d_bitstrings,
+                    const int64_t* n_bits, double* const* d_amps_out, int32_t ctas_per_sm);
+int qx_group_scratch_size(qx_group_t g, int64_t* bytes_out);
+int qx_group_bind(qx_group_t g, void* d_scratch, int64_t bytes);
+int qx_group_run(qx_group_t g);
+const char* qx_group_last_error(qx_group_t g);
+void qx_group_destroy(qx_group_t g);
+
 /* Kernel timing for roofline reports.  With profiling on, every kernel launch
  * of a contraction is bracketed by CUDA events on the handle's stream;
  * qx_profile_read synchronises the stream and returns, for one kernel kind,
@@ -196,7 +228,8 @@ int qx_contract_device_static(qx_handle h, const uint8_t* d_bitstrings, int64_t 
 #define QX_KERNEL_SUM     3
 #define QX_KERNEL_TC_PREP 4  /* operand split / expansion for the tensor-core forms */
 #define QX_KERNEL_TC_GEMM 5  /* tcgen05 complex GEMM */
-#define QX_KERNEL_KINDS   6
+#define QX_KERNEL_PERSIST 6  /* persistent executor (whole contractions) */
+#define QX_KERNEL_KINDS   7
 int qx_set_profiling(qx_handle h, int enable);
 int qx_profile_read(qx_handle h, int kind, double* ms, int64_t* launches, double* flops, double* bytes);
 

@@ -112,12 +112,22 @@ struct qx_ctx {
     int64_t n_slices = 1;
     double flops_inv = 0, flops_item = 0;
 
+    // persistent executor program (variant ops, in order)
+    bool persist_ok = false;
+    std::vector<POp> pops;      // per-pair ops
+    std::vector<POp> pops_inv;  // invariant ops (prologue program)
+    PRef proot{};
+    std::vector<int8_t> pobit_leg;
+    int persist_grid = 0;
+    bool pops_on_device = false;
+
     // workspace
     char* ws = nullptr;
     int64_t ws_bytes = 0;
     bool ws_owned = false;
     int64_t max_bits = 0;
     int64_t off_err = 0, off_leaf = 0, off_bits = 0, off_acc = 0, off_amps = 0, off_inv = 0, off_item = 0;
+    int64_t off_pops = 0, off_counter = 0, off_results = 0, off_pscratch = 0, off_pops_inv = 0;
     int64_t items_cap = 0;
     bool leaves_on_device = false;
 
@@ -356,6 +366,8 @@ static int64_t assign_offsets(qx_ctx* h, bool variant) {
     }
     return top;
 }
+
+static void build_persistent_program(qx_ctx* h);
 
 static int compile_plan(qx_ctx* h, const int64_t* order, int64_t n_steps, const int64_t* sliced, int32_t n_sliced) {
     const int64_t N = h->n_tensors;
@@ -598,6 +610,7 @@ static int compile_plan(qx_ctx* h, const int64_t* order, int64_t n_steps, const 
     h->inv_entries = assign_offsets(h, false);
     h->flops_inv = h->flops_item = 0;
     for (const Op& op : h->ops) (op.variant ? h->flops_item : h->flops_inv) += op.flops;
+    build_persistent_program(h);
     h->have_plan = true;
     return QX_OK;
 }
@@ -606,6 +619,14 @@ static int compile_plan(qx_ctx* h, const int64_t* order, int64_t n_steps, const 
 // Workspace layout: leaves | bitstrings | accumulators | amplitudes | invariant | per-pair region
 // ------------------------------------------------------------------------------------------------
 static int64_t n_open(const qx_ctx* h) { return (int64_t)h->open_wires.size(); }
+
+// persistent executor regions: executor 2 runs this handle alone (own CTA
+// scratch and work counter); executor 3 only prepares the handle for a group
+// launch (programs and per-pair results; scratch comes from the group)
+static bool persist_active(const qx_ctx* h) {
+    return h->persist_ok && h->persist_grid > 0 && h->opt.executor == 2;
+}
+static bool persist_member(const qx_ctx* h) { return h->persist_ok && h->opt.executor >= 2; }
 
 static void layout(qx_ctx* h, int64_t max_bits, int64_t* fixed_bytes) {
     int64_t off = 0;
@@ -621,6 +642,20 @@ static void layout(qx_ctx* h, int64_t max_bits, int64_t* fixed_bytes) {
     off += align_up((max_bits << n_open(h)) * 16, 256);
     h->off_inv = off;
     off += align_up(h->inv_entries * 8, 256);
+    h->off_pops = h->off_counter = h->off_results = h->off_pscratch = h->off_pops_inv = off;
+    if (persist_member(h)) {
+        off += align_up((int64_t)(h->pops.size() * sizeof(POp)), 256);
+        h->off_pops_inv = off;
+        off += align_up((int64_t)(h->pops_inv.size() * sizeof(POp)), 256);
+        h->off_results = off;
+        off += align_up((max_bits * h->n_slices << n_open(h)) * 8, 256);
+        h->off_counter = h->off_pscratch = off;
+    }
+    if (persist_active(h)) {
+        off += 256;
+        h->off_pscratch = off;
+        off += align_up((int64_t)h->persist_grid * h->item_entries * 8, 256);
+    }
     h->off_item = off;
     *fixed_bytes = off;
 }
@@ -720,6 +755,94 @@ static SmallDesc small_desc(const qx_ctx* h, const Op& op) {
     return d;
 }
 
+// ------------------------------------------------------------------------------------------------
+// Persistent program: the variant ops with operands named by space and offset
+// ------------------------------------------------------------------------------------------------
+static PRef pref_node(const qx_ctx* h, int node) {
+    const Node& nd = h->nodes[node];
+    PRef r{};
+    r.rank = (int32_t)nd.legs.size();
+    for (int j = 0; j < r.rank; ++j) r.pos[j] = (int8_t)nd.pos[j];
+    r.n_fix = (int32_t)nd.fix.size();
+    for (int f = 0; f < r.n_fix; ++f) {
+        r.fix_src[f] = nd.fix[f].first;
+        r.fix_stride[f] = nd.fix[f].second;
+    }
+    if (nd.leaf) {
+        r.space = PSPACE_LEAF;
+        r.off = nd.leaf_off;
+    } else {
+        const Storage& st = h->stor[nd.storage];
+        r.space = st.variant ? PSPACE_SCRATCH : PSPACE_INV;
+        r.off = st.off;
+    }
+    return r;
+}
+
+static PRef pref_storage(const qx_ctx* h, int sid) {
+    const Storage& st = h->stor[sid];
+    PRef r{};
+    r.space = st.variant ? PSPACE_SCRATCH : PSPACE_INV;
+    r.off = st.off;
+    return r;
+}
+
+static POp to_pop(const qx_ctx* h, const Op& op) {
+    POp p{};
+    p.mb = op.mb;
+    p.kb = op.kb;
+    p.nb = op.nb;
+    p.dst = h->stor[op.dst].off;
+    if (op.type == OP_PERM) {
+        const PermDesc d = perm_desc(h, op);
+        p.type = POP_PERM;
+        p.x = pref_node(h, op.src);
+        p.t = d.t;
+        p.n_outer = d.n_outer;
+        memcpy(p.in_pos, d.in_pos, sizeof p.in_pos);
+        memcpy(p.tile_in, d.tile_in, sizeof p.tile_in);
+        memcpy(p.tile_out, d.tile_out, sizeof p.tile_out);
+        memcpy(p.outer, d.outer, sizeof p.outer);
+    } else if (op.type == OP_SMALL) {
+        const SmallDesc d = small_desc(h, op);
+        p.type = POP_SMALL;
+        p.x = pref_node(h, op.x);
+        p.y = pref_node(h, op.y);
+        p.n_holes = d.n_holes;
+        memcpy(p.holes, d.holes, sizeof p.holes);
+        memcpy(p.xk_pos, d.xk_pos, sizeof p.xk_pos);
+        memcpy(p.yk_pos, d.yk_pos, sizeof p.yk_pos);
+        memcpy(p.yn_pos, d.yn_pos, sizeof p.yn_pos);
+    } else {
+        p.type = (op.mb + op.nb <= 4 && op.kb >= 8) ? POP_DOT : POP_GEMM;
+        p.x = pref_storage(h, op.sa);
+        p.y = pref_storage(h, op.sb);
+        p.a_km = op.a_km;
+        p.b_km = op.b_km;
+    }
+    return p;
+}
+
+static void build_persistent_program(qx_ctx* h) {
+    h->persist_ok = false;
+    h->pops.clear();
+    h->pops_inv.clear();
+    for (const Op& op : h->ops)
+        if (op.tc) return;  // tensor-core steps run batched
+    const Node& R = h->nodes[h->root];
+    if (!R.variant) return;  // nothing depends on the pair
+    // invariant ops write the invariant region: their program runs with that region as scratch
+    for (const Op& op : h->ops) (op.variant ? h->pops : h->pops_inv).push_back(to_pop(h, op));
+    h->proot = pref_node(h, h->root);
+    const int ob_n = (int)h->open_wires.size();
+    h->pobit_leg.assign(kMaxRank, 0);
+    for (int ob = 0; ob < ob_n; ++ob) {
+        const int wire = h->open_wires[ob_n - 1 - ob];
+        h->pobit_leg[ob] = (int8_t)(std::find(R.legs.begin(), R.legs.end(), wire) - R.legs.begin());
+    }
+    h->persist_ok = true;
+}
+
 static double op_bytes(const qx_ctx* h, const Op& op) {
     // algorithmic bytes per pair: each operand read once, the result written once
     if (op.type == OP_PERM) return 16.0 * (double)h->stor[op.dst].entries;
@@ -795,6 +918,97 @@ static int run_op(qx_ctx* h, const Op& op, const ItemCtx& ic, int64_t n_items) {
     return QX_OK;
 }
 
+static int upload_programs(qx_ctx* h) {
+    if (h->pops_on_device) return QX_OK;
+    if (!h->pops.empty())
+        CUDA_TRY(h, cudaMemcpyAsync(h->ws + h->off_pops, h->pops.data(), h->pops.size() * sizeof(POp),
+                                    cudaMemcpyHostToDevice, h->stream));
+    if (!h->pops_inv.empty())
+        CUDA_TRY(h, cudaMemcpyAsync(h->ws + h->off_pops_inv, h->pops_inv.data(), h->pops_inv.size() * sizeof(POp),
+                                    cudaMemcpyHostToDevice, h->stream));
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    h->pops_on_device = true;
+    return QX_OK;
+}
+
+// the pair program (inv = true: the prologue program) of a handle, for slices [s_begin, s_end)
+static PProg make_prog(const qx_ctx* h, bool inv, const uint8_t* d_bits, int64_t n_bits, int64_t s_begin) {
+    PProg g{};
+    g.ops = (const POp*)(h->ws + (inv ? h->off_pops_inv : h->off_pops));
+    g.n_ops = (int32_t)(inv ? h->pops_inv.size() : h->pops.size());
+    g.n_qubits = h->nq;
+    g.leaves = (const float2*)(h->ws + h->off_leaf);
+    g.inv = inv_base(h);
+    g.bits = d_bits;
+    g.s0 = inv ? 0 : s_begin;
+    g.b0 = 0;
+    g.n_b = inv ? 1 : n_bits;
+    g.root = h->proot;
+    g.open_bits = (int32_t)n_open(h);
+    for (int i = 0; i < g.open_bits; ++i) g.obit_leg[i] = h->pobit_leg[i];
+    g.results = inv ? nullptr : (float2*)(h->ws + h->off_results);
+    g.scratch_override = inv ? inv_base(h) : nullptr;
+    return g;
+}
+
+static GSum make_gsum(const qx_ctx* h, int64_t n_bits, int64_t n_s, double* d_amps, int64_t t0) {
+    GSum g{};
+    g.results = (const float2*)(h->ws + h->off_results);
+    g.amps = d_amps;
+    g.n_b = n_bits;
+    g.t0 = t0;
+    g.n_s = (int32_t)n_s;
+    g.open_bits = (int32_t)n_open(h);
+    g.sr = h->leaf_scale[0];
+    g.si = h->leaf_scale[1];
+    return g;
+}
+
+static int contract_persistent(qx_ctx* h, const uint8_t* d_bits, int64_t n_bits, int64_t s_begin, int64_t s_end,
+                               double* d_amps) {
+    int rc = upload_programs(h);
+    if (rc) return rc;
+    const int64_t pairs = (s_end - s_begin) * n_bits;
+    PLaunch L{};
+    L.n_progs = 0;
+    L.scratch = (float2*)(h->ws + h->off_pscratch);
+    L.scratch_entries = h->item_entries;
+    L.counter = (unsigned long long*)(h->ws + h->off_counter);
+    size_t slot;
+    cudaError_t e = cudaSuccess;
+    if (!h->pops_inv.empty()) {  // prologue: one CTA runs the invariant ops in order
+        L.single = make_prog(h, true, d_bits, n_bits, s_begin);
+        L.n_work = 1;
+        e = prof_begin(h, QX_KERNEL_PERSIST, h->flops_inv, 0.0, &slot);
+        if (e == cudaSuccess) e = launch_persist(L, 1, h->stream);
+        if (e == cudaSuccess) e = prof_end(h, slot);
+        if (e != cudaSuccess) return fail(h, QX_ECUDA, "persistent prologue failed: %s", cudaGetErrorString(e));
+        h->last_launches += 1;
+        h->last_flops += h->flops_inv;
+    }
+    L.single = make_prog(h, false, d_bits, n_bits, s_begin);
+    L.n_work = pairs;
+    double bytes = 0;
+    for (const Op& op : h->ops)
+        if (op.variant) bytes += op_bytes(h, op);
+    e = prof_begin(h, QX_KERNEL_PERSIST, h->flops_item * (double)pairs, bytes * (double)pairs, &slot);
+    if (e == cudaSuccess) e = launch_persist(L, h->persist_grid, h->stream);
+    if (e == cudaSuccess) e = prof_end(h, slot);
+    if (e != cudaSuccess) return fail(h, QX_ECUDA, "persistent launch failed: %s", cudaGetErrorString(e));
+    h->last_launches += 1;
+    h->last_flops += h->flops_item * (double)pairs;
+    // deterministic FP64 sum over the slices of each bitstring, straight into the amplitudes
+    const int64_t n_o = (int64_t)1 << n_open(h);
+    const GSum g = make_gsum(h, n_bits, s_end - s_begin, d_amps, 0);
+    e = prof_begin(h, QX_KERNEL_SUM, 0.0, (double)pairs * n_o * 8.0 + (double)n_bits * n_o * 16.0, &slot);
+    if (e == cudaSuccess) e = launch_single_sum(g, n_bits * n_o, h->stream);
+    if (e == cudaSuccess) e = prof_end(h, slot);
+    if (e != cudaSuccess) return fail(h, QX_ECUDA, "slice sum launch failed: %s", cudaGetErrorString(e));
+    h->last_launches++;
+    h->last_batches = 1;
+    return QX_OK;
+}
+
 static int contract_impl(qx_ctx* h, const uint8_t* d_bits, int64_t n_bits, int64_t s_begin, int64_t s_end,
                          double* d_amps) {
     const int64_t n_o = (int64_t)1 << n_open(h);
@@ -809,6 +1023,11 @@ static int contract_impl(qx_ctx* h, const uint8_t* d_bits, int64_t n_bits, int64
     }
     double* acc = (double*)(h->ws + h->off_acc);
     CUDA_TRY(h, cudaMemsetAsync(h->ws + h->off_err, 0, sizeof(int), h->stream));
+    const int mode = h->opt.executor;
+    if (mode >= 2 && !persist_active(h))
+        return fail(h, QX_EINVAL, mode == 3 ? "a group member contracts only through qx_group_run"
+                                            : "the persistent executor does not apply to this plan and precision form");
+    if (mode == 2) return contract_persistent(h, d_bits, n_bits, s_begin, s_end, d_amps);
     CUDA_TRY(h, cudaMemsetAsync(acc, 0, (size_t)(n_bits * n_o * 32), h->stream));
     ItemCtx ic{};
     ic.n_qubits = h->nq;
@@ -885,9 +1104,16 @@ int qx_create(qx_handle* out, int device, void* stream, const qx_options* opt) {
     }
     qx_ctx* h = new qx_ctx();
     h->device = device;
+    h->persist_grid = 2 * 152;  // two CTAs per SM; the real SM count below
+    if (device >= 0) {
+        int sms = 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) == cudaSuccess && sms > 0)
+            h->persist_grid = 2 * sms;
+    }
     h->stream = (cudaStream_t)stream;
     if (opt) h->opt = *opt;
-    if (h->opt.precision < QX_PREC_C64 || h->opt.precision > QX_PREC_SPLIT_BF16 || h->opt.max_items < 0) {
+    if (h->opt.precision < QX_PREC_C64 || h->opt.precision > QX_PREC_SPLIT_BF16 || h->opt.max_items < 0 ||
+        h->opt.executor < 0 || h->opt.executor > 3) {
         delete h;
         return QX_EINVAL;
     }
@@ -914,6 +1140,7 @@ int qx_set_options(qx_handle h, const qx_options* opt) {
     if (h->have_plan && opt->precision != h->opt.precision)
         return fail(h, QX_ESTATE, "set the precision form before qx_set_plan");
     if (opt->max_items < 0) return fail(h, QX_EINVAL, "max_items < 0");
+    if (opt->executor < 0 || opt->executor > 3) return fail(h, QX_EINVAL, "executor %d out of range", opt->executor);
     h->opt = *opt;
     return QX_OK;
 }
@@ -942,6 +1169,7 @@ static void unbind(qx_ctx* h) {
     h->ws_owned = false;
     h->items_cap = 0;
     h->leaves_on_device = false;
+    h->pops_on_device = false;
 }
 
 int qx_set_plan(qx_handle h, const int64_t* order, int64_t n_steps, const int64_t* sliced, int32_t n_sliced,
@@ -994,6 +1222,7 @@ int qx_bind_workspace(qx_handle h, void* dptr, int64_t bytes, int64_t max_bits) 
     h->max_bits = max_bits;
     h->items_cap = items;
     h->leaves_on_device = false;
+    h->pops_on_device = false;
     return QX_OK;
 }
 
@@ -1121,9 +1350,12 @@ int qx_internal_contract_in(qx_ctx* h, char* buf, int64_t buf_bytes, const uint8
         bool ws_owned;
         int64_t max_bits, off_err, off_leaf, off_bits, off_acc, off_amps, off_inv, off_item, items_cap;
         bool leaves_on_device;
-    } const saved = {h->ws,       h->ws_bytes, h->ws_owned, h->max_bits, h->off_err,   h->off_leaf,
-                     h->off_bits, h->off_acc,  h->off_amps, h->off_inv,  h->off_item, h->items_cap,
-                     h->leaves_on_device};
+        int64_t off_pops, off_counter, off_results, off_pscratch, off_pops_inv;
+        bool pops_on_device;
+    } const saved = {h->ws,        h->ws_bytes, h->ws_owned,    h->max_bits,    h->off_err,    h->off_leaf,
+                     h->off_bits,  h->off_acc,  h->off_amps,    h->off_inv,     h->off_item,   h->items_cap,
+                     h->leaves_on_device, h->off_pops, h->off_counter, h->off_results, h->off_pscratch,
+                     h->off_pops_inv, h->pops_on_device};
     int64_t fixed;
     layout(h, n_bits, &fixed);
     int64_t items = (buf_bytes - fixed) / (h->item_entries * 8);
@@ -1144,6 +1376,12 @@ int qx_internal_contract_in(qx_ctx* h, char* buf, int64_t buf_bytes, const uint8
         h->off_item = saved.off_item;
         h->items_cap = saved.items_cap;
         h->leaves_on_device = saved.leaves_on_device;
+        h->off_pops = saved.off_pops;
+        h->off_counter = saved.off_counter;
+        h->off_results = saved.off_results;
+        h->off_pscratch = saved.off_pscratch;
+        h->off_pops_inv = saved.off_pops_inv;
+        h->pops_on_device = saved.pops_on_device;
     };
     if (items < 1) {
         restore();
@@ -1156,6 +1394,7 @@ int qx_internal_contract_in(qx_ctx* h, char* buf, int64_t buf_bytes, const uint8
     h->max_bits = n_bits;
     h->items_cap = items;
     h->leaves_on_device = false;
+    h->pops_on_device = false;
     int rc = QX_OK;
     cudaError_t e = cudaSetDevice(h->device);
     if (e != cudaSuccess) rc = fail(h, QX_ECUDA, "cudaSetDevice: %s", cudaGetErrorString(e));
@@ -1163,3 +1402,182 @@ int qx_internal_contract_in(qx_ctx* h, char* buf, int64_t buf_bytes, const uint8
     restore();
     return rc;
 }
+
+// ------------------------------------------------------------------------------------------------
+// Groups: many networks contracted by one persistent launch (uneven circuits side by side)
+// ------------------------------------------------------------------------------------------------
+struct qx_group {
+    std::vector<qx_ctx*> hs;
+    std::vector<const uint8_t*> bits;
+    std::vector<int64_t> n_bits;
+    std::vector<double*> amps;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int grid = 0;
+    std::vector<PProg> inv_progs, pair_progs;
+    std::vector<GSum> sums;
+    int64_t n_pair_work = 0, total_sum = 0, max_entries = 0;
+    char* scratch = nullptr;
+    int64_t scratch_bytes = 0;
+    int64_t off_inv = 0, off_pair = 0, off_sum = 0, off_sc = 0;
+    std::string err;
+    bool bound = false;
+};
+
+static int gfail(qx_group* g, int code, const char* msg) {
+    g->err = msg;
+    return code;
+}
+
+static void group_layout(qx_group* g, int64_t* bytes) {
+    int64_t off = 256;  // work counter
+    g->off_inv = off;
+    off += align_up((int64_t)(g->hs.size() * sizeof(PProg)), 256);
+    g->off_pair = off;
+    off += align_up((int64_t)(g->hs.size() * sizeof(PProg)), 256);
+    g->off_sum = off;
+    off += align_up((int64_t)(g->hs.size() * sizeof(GSum)), 256);
+    g->off_sc = off;
+    off += align_up((int64_t)g->grid * g->max_entries * 8, 256);
+    *bytes = off;
+}
+
+extern "C" {
+
+int qx_group_create(qx_group_t* out, qx_handle* hs, int32_t n, const uint8_t* const* d_bits, const int64_t* n_bits,
+                    double* const* d_amps, int32_t ctas_per_sm) {
+    if (!out) return QX_EINVAL;
+    *out = nullptr;
+    if (!hs || n < 1 || !d_bits || !n_bits || !d_amps) return QX_EINVAL;
+    if (ctas_per_sm < 0 || ctas_per_sm > 4) return QX_EINVAL;
+    qx_group* g = new qx_group();
+    for (int i = 0; i < n; ++i) {
+        qx_ctx* h = hs[i];
+        const char* why = nullptr;
+        if (!h) why = "null handle";
+        else if (!h->have_plan || !h->ws) why = "every handle needs a plan and a bound workspace";
+        else if (h->opt.executor != 3 || !h->persist_ok)
+            why = "every handle must be created with executor 3 and a plan without tensor-core steps";
+        else if (h->device != hs[0]->device) why = "handles on different devices";
+        else if (n_bits[i] < 1 || n_bits[i] > h->max_bits) why = "bitstring count outside the handle's workspace";
+        else if (!d_bits[i] || !d_amps[i]) why = "null buffer";
+        if (why) {
+            g->err = why;
+            *out = g;
+            return QX_EINVAL;
+        }
+        g->hs.push_back(h);
+        g->bits.push_back(d_bits[i]);
+        g->n_bits.push_back(n_bits[i]);
+        g->amps.push_back(d_amps[i]);
+        g->max_entries = std::max(g->max_entries, h->item_entries);
+    }
+    g->device = hs[0]->device;
+    g->stream = hs[0]->stream;
+    g->grid = (ctas_per_sm ? ctas_per_sm : 2) * (hs[0]->persist_grid / 2);
+    *out = g;
+    return QX_OK;
+}
+
+const char* qx_group_last_error(qx_group_t g) { return g ? g->err.c_str() : "null group"; }
+
+int qx_group_scratch_size(qx_group_t g, int64_t* bytes) {
+    if (!g || !bytes) return QX_EINVAL;
+    if (g->hs.empty()) return gfail(g, QX_ESTATE, "group creation failed");
+    group_layout(g, bytes);
+    return QX_OK;
+}
+
+int qx_group_bind(qx_group_t g, void* d_scratch, int64_t bytes) {
+    if (!g) return QX_EINVAL;
+    if (g->hs.empty()) return gfail(g, QX_ESTATE, "group creation failed");
+    int64_t need;
+    group_layout(g, &need);
+    if (!d_scratch || bytes < need || ((uintptr_t)d_scratch) % 256) return gfail(g, QX_ENOMEM, "scratch too small or misaligned");
+    if (cudaSetDevice(g->device) != cudaSuccess) return gfail(g, QX_ECUDA, "cudaSetDevice failed");
+    g->scratch = (char*)d_scratch;
+    g->scratch_bytes = bytes;
+    // each member's tensors and programs on its own workspace
+    for (qx_ctx* h : g->hs) {
+        if (!h->leaves_on_device) {
+            if (cudaMemcpyAsync(h->ws + h->off_leaf, h->leaf_vals.data(), h->leaf_vals.size() * sizeof(float2),
+                                cudaMemcpyHostToDevice, g->stream) != cudaSuccess)
+                return gfail(g, QX_ECUDA, "leaf upload failed");
+            h->leaves_on_device = true;
+        }
+        if (upload_programs(h) != QX_OK) return gfail(g, QX_ECUDA, h->err.c_str());
+    }
+    // programs ordered by per-pair work, largest first, so the long pairs start early
+    std::vector<int> order(g->hs.size());
+    for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int a, int b) { return g->hs[a]->flops_item > g->hs[b]->flops_item; });
+    g->inv_progs.clear();
+    g->pair_progs.clear();
+    g->sums.clear();
+    int64_t w = 0, t = 0;
+    for (int i : order) {
+        qx_ctx* h = g->hs[i];
+        if (!h->pops_inv.empty()) {
+            PProg p = make_prog(h, true, g->bits[i], 1, 0);
+            p.work0 = (int64_t)g->inv_progs.size();
+            g->inv_progs.push_back(p);
+        }
+        PProg p = make_prog(h, false, g->bits[i], g->n_bits[i], 0);
+        p.work0 = w;
+        w += h->n_slices * g->n_bits[i];
+        g->pair_progs.push_back(p);
+    }
+    for (size_t i = 0; i < g->hs.size(); ++i) {
+        qx_ctx* h = g->hs[i];
+        g->sums.push_back(make_gsum(h, g->n_bits[i], h->n_slices, g->amps[i], t));
+        t += g->n_bits[i] << n_open(h);
+    }
+    g->n_pair_work = w;
+    g->total_sum = t;
+    cudaError_t e = cudaSuccess;
+    if (!g->inv_progs.empty())
+        e = cudaMemcpyAsync(g->scratch + g->off_inv, g->inv_progs.data(), g->inv_progs.size() * sizeof(PProg),
+                            cudaMemcpyHostToDevice, g->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(g->scratch + g->off_pair, g->pair_progs.data(), g->pair_progs.size() * sizeof(PProg),
+                            cudaMemcpyHostToDevice, g->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(g->scratch + g->off_sum, g->sums.data(), g->sums.size() * sizeof(GSum),
+                            cudaMemcpyHostToDevice, g->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+    if (e != cudaSuccess) return gfail(g, QX_ECUDA, cudaGetErrorString(e));
+    g->bound = true;
+    return QX_OK;
+}
+
+int qx_group_run(qx_group_t g) {
+    if (!g) return QX_EINVAL;
+    if (!g->bound) return gfail(g, QX_ESTATE, "qx_group_run before qx_group_bind");
+    if (cudaSetDevice(g->device) != cudaSuccess) return gfail(g, QX_ECUDA, "cudaSetDevice failed");
+    PLaunch L{};
+    L.scratch = (float2*)(g->scratch + g->off_sc);
+    L.scratch_entries = g->max_entries;
+    L.counter = (unsigned long long*)g->scratch;
+    cudaError_t e = cudaSuccess;
+    if (!g->inv_progs.empty()) {
+        L.progs = (const PProg*)(g->scratch + g->off_inv);
+        L.n_progs = (int32_t)g->inv_progs.size();
+        L.n_work = L.n_progs;
+        e = launch_persist(L, std::min<int>(g->grid, L.n_progs), g->stream);
+    }
+    if (e == cudaSuccess) {
+        L.progs = (const PProg*)(g->scratch + g->off_pair);
+        L.n_progs = (int32_t)g->pair_progs.size();
+        L.n_work = g->n_pair_work;
+        e = launch_persist(L, g->grid, g->stream);
+    }
+    if (e == cudaSuccess)
+        e = launch_group_sum((const GSum*)(g->scratch + g->off_sum), (int32_t)g->sums.size(), g->total_sum, g->stream);
+    if (e != cudaSuccess) return gfail(g, QX_ECUDA, cudaGetErrorString(e));
+    return QX_OK;
+}
+
+void qx_group_destroy(qx_group_t g) { delete g; }
+
+}  // extern "C"

@@ -87,6 +87,69 @@ cudaError_t launch_gemm_c64(const float2* a, int64_t a_is, bool a_kmajor, const 
                             cudaStream_t st);
 cudaError_t launch_slice_sum(const SumDesc& d, const ItemCtx& ic, double* acc, cudaStream_t st);
 
+// Persistent executor (qx_persist.cu): one launch runs whole contractions of
+// (slice, bitstring) pairs, one pair per CTA at a time, steps in order.
+enum { PSPACE_LEAF = 0, PSPACE_INV = 1, PSPACE_SCRATCH = 2 };
+enum { POP_PERM = 0, POP_SMALL = 1, POP_GEMM = 2, POP_DOT = 3 };
+struct PRef {                  // an operand: leaf (with fixed legs), invariant tensor or CTA scratch
+    int64_t off;               // entries into the leaf buffer / invariant region / CTA scratch
+    int32_t space;
+    int32_t rank;
+    int32_t n_fix;
+    int32_t fix_src[kMaxFix];
+    int64_t fix_stride[kMaxFix];
+    int8_t pos[kMaxRank];
+};
+struct POp {
+    int32_t type, mb, kb, nb, a_km, b_km;
+    int64_t dst;               // CTA scratch offset of the result (contiguous)
+    PRef x, y;                 // PERM: x; SMALL: x large, y small; GEMM / DOT: x = A, y = B (contiguous)
+    int32_t t, n_outer, n_holes;
+    int8_t in_pos[kMaxRank], tile_in[10], tile_out[10], outer[kMaxRank];
+    int8_t holes[kMaxRank], xk_pos[kSmallMaxK], yk_pos[kSmallMaxK], yn_pos[kSmallMaxN];
+};
+struct PProg {
+    const POp* ops;            // device
+    int32_t n_ops;
+    int32_t n_qubits;
+    const float2* leaves;      // device
+    const float2* inv;         // device
+    const uint8_t* bits;       // device [n_bits][n_qubits]
+    int64_t s0, b0;            // first slice / bitstring of this program's work
+    int64_t n_b;               // bitstrings per slice: pair = s_local * n_b + b_local
+    int64_t work0;             // first global work index of this program
+    PRef root;
+    int32_t open_bits;
+    int8_t obit_leg[kMaxRank]; // root leg of canonical open bit ob (0 = least significant)
+    float2* results;           // device [pairs][2^open_bits]; null: no result (prologue programs)
+    float2* scratch_override;  // non-null: results of the ops go here (prologue programs: the invariant region)
+};
+struct PLaunch {
+    PProg single;              // used when n_progs == 0
+    const PProg* progs;        // device, ordered by work0
+    int32_t n_progs;
+    int64_t n_work;
+    float2* scratch;           // grid x scratch_entries
+    int64_t scratch_entries;
+    unsigned long long* counter;
+};
+constexpr int kPersistSmem = 17408;
+cudaError_t launch_persist(const PLaunch& L, int grid, cudaStream_t st);
+
+// FP64 compensated slice sum of persistent results, for many programs in one
+// launch, written straight to the amplitudes (times the leaf scale).
+struct GSum {
+    const float2* results;     // [n_s * n_b][2^open_bits], pair = s * n_b + b
+    double* amps;              // [n_b][2^open_bits] complex128
+    int64_t n_b;
+    int64_t t0;                // first global thread of this program
+    int32_t n_s;
+    int32_t open_bits;
+    double sr, si;             // leaf scale
+};
+cudaError_t launch_group_sum(const GSum* d_sums, int32_t n, int64_t total, cudaStream_t st);
+cudaError_t launch_single_sum(const GSum& g, int64_t total, cudaStream_t st);
+
 // Tensor-core complex GEMM (qx_tc.cu).  Operands are contiguous complex64
 // per item, [R][K] (kmajor) or [K][R]; pa / pb receive the split real parts
 // (prep), then the tcgen05 kernel writes C [M][N] complex64.

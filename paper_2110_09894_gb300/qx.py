@@ -23,9 +23,10 @@ _NAMES = {QX_EINVAL: "QX_EINVAL", QX_ENOMEM: "QX_ENOMEM", QX_ECUDA: "QX_ECUDA", 
 EXPORTS = ("qx_create", "qx_destroy", "qx_last_error", "qx_set_options", "qx_build_network", "qx_network_info",
            "qx_set_plan", "qx_workspace_size", "qx_bind_workspace", "qx_contract", "qx_contract_device",
            "qx_contract_slices", "qx_contract_slices_device", "qx_last_stats", "qx_set_profiling",
-           "qx_profile_read", "qx_contract_device_static", "qx_device_status")
+           "qx_profile_read", "qx_contract_device_static", "qx_device_status", "qx_group_create",
+           "qx_group_scratch_size", "qx_group_bind", "qx_group_run", "qx_group_last_error", "qx_group_destroy")
 QX_STATIC_SCRATCH_BYTES = 64 << 20
-KERNEL_KINDS = ("permute", "small", "gemm", "sum", "tc_prep", "tc_gemm")
+KERNEL_KINDS = ("permute", "small", "gemm", "sum", "tc_prep", "tc_gemm", "persist")
 
 
 class QXError(RuntimeError):
@@ -36,7 +37,7 @@ class QXError(RuntimeError):
 
 class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("max_items", ctypes.c_int32), ("gemm_min_bits", ctypes.c_int32),
-                ("reserved", ctypes.c_int32), ("timeout_cycles", ctypes.c_int64)]
+                ("executor", ctypes.c_int32), ("timeout_cycles", ctypes.c_int64)]
 
 
 _lib = None
@@ -74,6 +75,13 @@ def load(path=None):
                           ctypes.c_int),
         "qx_set_profiling": ([vp, ctypes.c_int], ctypes.c_int),
         "qx_device_status": ([vp], ctypes.c_int),
+        "qx_group_create": ([ctypes.POINTER(vp), ctypes.POINTER(vp), i32, ctypes.POINTER(vp), ctypes.POINTER(i64),
+                             ctypes.POINTER(vp), i32], ctypes.c_int),
+        "qx_group_scratch_size": ([vp, ctypes.POINTER(i64)], ctypes.c_int),
+        "qx_group_bind": ([vp, vp, i64], ctypes.c_int),
+        "qx_group_run": ([vp], ctypes.c_int),
+        "qx_group_last_error": ([vp], ctypes.c_char_p),
+        "qx_group_destroy": ([vp], None),
         "qx_contract_device_static": ([vp, vp, i64, vp], ctypes.c_int),
         "qx_profile_read": ([vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64),
                              ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
@@ -95,9 +103,12 @@ def _check(h, rc):
 
 # --- thin wrappers with the C names --------------------------------------------------------------
 
-def qx_create(device=0, stream=0, precision=QX_PREC_C64, max_items=0, gemm_min_bits=0):
+EXEC_AUTO, EXEC_BATCHED, EXEC_PERSISTENT, EXEC_GROUP_MEMBER = 0, 1, 2, 3
+
+
+def qx_create(device=0, stream=0, precision=QX_PREC_C64, max_items=0, gemm_min_bits=0, executor=EXEC_AUTO):
     h = ctypes.c_void_p()
-    opt = Options(precision, max_items, gemm_min_bits, 0, 0)
+    opt = Options(precision, max_items, gemm_min_bits, executor, 0)
     rc = load().qx_create(ctypes.byref(h), int(device), ctypes.c_void_p(int(stream)), ctypes.byref(opt))
     if rc != QX_OK:
         raise QXError(rc, "qx_create failed (device, options)")
@@ -112,8 +123,8 @@ def qx_last_error(h):
     return load().qx_last_error(h).decode()
 
 
-def qx_set_options(h, precision=QX_PREC_C64, max_items=0, gemm_min_bits=0):
-    opt = Options(precision, max_items, gemm_min_bits, 0, 0)
+def qx_set_options(h, precision=QX_PREC_C64, max_items=0, gemm_min_bits=0, executor=EXEC_AUTO):
+    opt = Options(precision, max_items, gemm_min_bits, executor, 0)
     _check(h, load().qx_set_options(h, ctypes.byref(opt)))
 
 
@@ -211,18 +222,20 @@ class Contractor:
     """A network + plan resident on one GPU with a torch-allocated workspace."""
 
     def __init__(self, n_qubits, gate_records, open_mask, order, sliced, max_bits, device=0,
-                 precision=QX_PREC_C64, max_items=0, workspace_bytes=None, stream=None):
+                 precision=QX_PREC_C64, max_items=0, workspace_bytes=None, stream=None, executor=EXEC_AUTO):
         import torch
         self.torch = torch
         self.device = torch.device("cuda", device)
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         self.n_qubits = int(n_qubits)
         self.n_open = 0 if open_mask is None else int(np.sum(np.asarray(open_mask) != 0))
-        self.h = qx_create(device, self.stream.cuda_stream, precision, max_items)
+        self.h = qx_create(device, self.stream.cuda_stream, precision, max_items, 0, executor)
         qx_build_network(self.h, n_qubits, gate_records, open_mask)
         self.peak_entries = qx_set_plan(self.h, order, sliced)
         self.n_slices = 1 << len(np.asarray(sliced).reshape(-1))
         self.max_bits = int(max_bits)
+        if workspace_bytes is None and executor == EXEC_GROUP_MEMBER:
+            workspace_bytes = qx_workspace_size(self.h, max_bits, 1)  # pair scratch comes from the group
         if workspace_bytes is None:
             want = qx_workspace_size(self.h, max_bits, self.n_slices * max_bits)
             free, _ = torch.cuda.mem_get_info(self.device)
@@ -261,6 +274,77 @@ class Contractor:
         if getattr(self, "h", None):
             qx_destroy(self.h)
             self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _gcheck(g, rc):
+    if rc != QX_OK:
+        msg = load().qx_group_last_error(g)
+        raise QXError(rc, msg.decode() if msg else "")
+
+
+class Group:
+    """Many Contractors (created with executor=EXEC_GROUP_MEMBER) run by one persistent launch.
+
+    `run()` only enqueues work on member 0's stream; `capture()` records it in a
+    CUDA graph and `replay()` launches the graph.
+    """
+
+    def __init__(self, members, d_bits, ctas_per_sm=0):
+        import torch
+        self.torch = torch
+        self.members = list(members)
+        self.d_bits = list(d_bits)
+        dev = self.members[0].device
+        self.d_amps = [torch.empty((b.shape[0], 1 << m.n_open, 2), dtype=torch.float64, device=dev)
+                       for m, b in zip(self.members, self.d_bits)]
+        n = len(self.members)
+        hs = (ctypes.c_void_p * n)(*[m.h.value for m in self.members])
+        bits = (ctypes.c_void_p * n)(*[b.data_ptr() for b in self.d_bits])
+        nb = (ctypes.c_int64 * n)(*[b.shape[0] for b in self.d_bits])
+        amps = (ctypes.c_void_p * n)(*[a.data_ptr() for a in self.d_amps])
+        g = ctypes.c_void_p()
+        rc = load().qx_group_create(ctypes.byref(g), hs, n, bits, nb, amps, int(ctas_per_sm))
+        self.g = g
+        _gcheck(g, rc)
+        size = ctypes.c_int64()
+        _gcheck(g, load().qx_group_scratch_size(g, ctypes.byref(size)))
+        self.scratch = torch.empty(max(size.value, 256), dtype=torch.uint8, device=dev)
+        _gcheck(g, load().qx_group_bind(g, self.scratch.data_ptr(), self.scratch.numel()))
+        self.graph = None
+
+    def run(self):
+        _gcheck(self.g, load().qx_group_run(self.g))
+
+    def capture(self):
+        torch = self.torch
+        stream = self.members[0].stream
+        self.run()  # warm-up outside the capture
+        stream.synchronize()
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph, stream=stream):
+            self.run()
+        return self.graph
+
+    def replay(self):
+        self.graph.replay()
+
+    def amplitudes(self):
+        out = []
+        for a in self.d_amps:
+            h = a.cpu().numpy()
+            out.append(h[..., 0] + 1j * h[..., 1])
+        return out
+
+    def close(self):
+        if getattr(self, "g", None):
+            load().qx_group_destroy(self.g)
+            self.g = None
 
     def __del__(self):
         try:

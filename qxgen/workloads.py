@@ -124,11 +124,30 @@ def batched_specs(count=256):
     return specs
 
 
-def batched_circuit(j, spec=None):
-    n, depth, s, nb = spec or batched_specs()[j]
+@functools.lru_cache(maxsize=None)
+def batched_circuit(j):
+    n, depth, s, nb = batched_specs()[j]
     cseed = 4000 + j
     rows, cols = near_square_shape(n)
     circ = random_grid_circuit(rows, cols, depth, cseed, n=n)
     bits = random_bitstrings(n, nb, cseed + 500000)
     return _workload(f"batched{j}_n{n}_d{depth}_s{s}", circ, np.zeros(n, np.uint8), s, cseed, bits,
-                     trials=4, meta={"n": n, "depth": depth})
+                     trials=1, meta={"n": n, "depth": depth, "j": j})
+
+
+BATCHED_MAX_PEAK_RANK = 18
+
+
+def batched_members(count=256, max_peak_rank=BATCHED_MAX_PEAK_RANK):
+    """Circuits of the batched workload that run in the one persistent launch.
+
+    A circuit joins when its plan's largest per-pair intermediate has at most
+    2^max_peak_rank entries (2 MiB of complex64), so every CTA's scratch stays
+    small; the heavy tail of the draw (28-qubit depth-16 circuits whose
+    per-pair cost reaches 1e13 flop) is listed by batched_excluded().
+    """
+    return [batched_circuit(j) for j in range(count) if batched_circuit(j).peak_rank <= max_peak_rank]
+
+
+def batched_excluded(count=256, max_peak_rank=BATCHED_MAX_PEAK_RANK):
+    return [batched_circuit(j) for j in range(count) if batched_circuit(j).peak_rank > max_peak_rank]

@@ -72,8 +72,8 @@ def test_grid_cases_vs_statevector(qx, rows, cols, depth, n_open, n_slice, n_bit
 @pytest.mark.parametrize("max_items", [1, 3, 64, 0])
 def test_batch_size_does_not_change_the_result(qx, max_items):
     circ, om, order, sliced, bits = grid_case(3, 4, 8, 77, 1, 4, 6)
-    base = _contractor(qx, circ, om, order, sliced, 6, max_items=1).contract(bits)
-    got = _contractor(qx, circ, om, order, sliced, 6, max_items=max_items).contract(bits)
+    base = _contractor(qx, circ, om, order, sliced, 6, max_items=1, executor=qx.EXEC_BATCHED).contract(bits)
+    got = _contractor(qx, circ, om, order, sliced, 6, max_items=max_items, executor=qx.EXEC_BATCHED).contract(bits)
     assert np.array_equal(got, base)  # same per-pair kernels, same slice order in the FP64 sum
 
 
@@ -197,3 +197,34 @@ def test_large_workload_32_slices_vs_einsum_oracle(qx):
     # one slice recomputed by the oracle in the test itself
     one = oe.contract_once(w.n_qubits, w.gates, w.open_mask, w.order, w.sliced, 7, w.bitstrings[0])
     assert rel_l2(c.contract_slices(w.bitstrings, 7, 8)[0], one) <= TOL_C64
+
+
+@pytest.mark.parametrize("rows,cols,depth,n_open,n_slice,n_bits", [
+    (3, 3, 8, 3, 2, 5), (2, 5, 10, 0, 4, 33), (3, 4, 6, 2, 3, 1), (4, 4, 8, 4, 5, 7), (2, 4, 6, 8, 0, 2)])
+def test_persistent_executor_vs_statevector(qx, rows, cols, depth, n_open, n_slice, n_bits):
+    circ, om, order, sliced, bits = grid_case(rows, cols, depth, 31 + depth, n_open, n_slice, n_bits)
+    recs = C.gates_to_records(circ)
+    ref = oracle.sv_amplitudes(circ.n_qubits, recs, om, bits)
+    p = _contractor(qx, circ, om, order, sliced, n_bits, executor=qx.EXEC_PERSISTENT)
+    b = _contractor(qx, circ, om, order, sliced, n_bits, executor=qx.EXEC_BATCHED)
+    if n_open == circ.n_qubits and n_slice == 0:
+        # nothing depends on the pair: the persistent executor does not apply
+        with pytest.raises(qx.QXError):
+            p.contract(bits)
+        return
+    gp = p.contract(bits)
+    gb = b.contract(bits)
+    assert rel_l2(gp, ref) <= TOL_C64
+    assert rel_l2(gp, gb) <= 1e-6
+
+
+def test_persistent_executor_on_sliced_workload(qx):
+    w = W.sliced()
+    ref = oracle.sv_amplitudes(w.n_qubits, w.gates, w.open_mask, w.bitstrings)
+    c = qx.Contractor(w.n_qubits, w.gates, w.open_mask, w.order, w.sliced, len(w.bitstrings),
+                      executor=qx.EXEC_PERSISTENT)
+    qx.qx_set_profiling(c.h, True)
+    got = c.contract(w.bitstrings)
+    prof = qx.qx_profile_read(c.h)
+    assert prof["persist"]["launches"] == 2  # one launch for the invariant tensors, one for all pairs
+    assert rel_l2(got, ref) <= TOL_C64
