@@ -228,3 +228,24 @@ def test_persistent_executor_on_sliced_workload(qx):
     prof = qx.qx_profile_read(c.h)
     assert prof["persist"]["launches"] == 2  # one launch for the invariant tensors, one for all pairs
     assert rel_l2(got, ref) <= TOL_C64
+
+
+def test_sharded_slices_single_rank_group(qx):
+    import datetime
+    import socket
+
+    import torch.distributed as dist
+
+    from paper_2110_09894_gb300.dist import sharded_amplitudes
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=0, world_size=1,
+                            timeout=datetime.timedelta(seconds=30))
+    try:
+        circ, om, order, sliced, bits = grid_case(3, 4, 8, 23, 2, 4, 3)
+        c = _contractor(qx, circ, om, order, sliced, 3)
+        got = sharded_amplitudes(c, bits, 0, 1)
+        assert rel_l2(got, c.contract(bits)) < 1e-15
+    finally:
+        dist.destroy_process_group()
