@@ -1,0 +1,266 @@
+"""Continuous-batching amplitude server over resident networks.
+
+Requests (circuit id, bitstrings) arrive over time.  Every circuit keeps its
+network, plan and tensors resident in device memory; the server admits work
+while other work is on the GPU:
+
+* requests for the same circuit that wait together are merged into one
+  contraction (their bitstrings concatenated: the slice-batched executor then
+  runs all their (slice, bitstring) pairs in the same launches);
+* a merged batch runs in slice chunks (``qx_contract_slices_device``) sized to
+  a target amount of work, so a long request never holds the GPU for long and
+  new arrivals start between chunks; chunk results are summed on the host in
+  FP64 with compensation, in slice order;
+* each circuit owns a few execution lanes (a library handle with its own
+  workspace and CUDA stream); lanes are created on demand while the device
+  memory budget allows (admission by memory) and reused afterwards;
+* completion is detected with CUDA events; latency runs from a request's
+  arrival to the host seeing its amplitudes.
+
+The scheduling runs on the host in Python (it only marshals work); every
+contraction step runs in the library's kernels.
+"""
+from __future__ import annotations
+
+import collections
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import qx
+
+
+@dataclass
+class Request:
+    rid: int
+    circuit: int
+    bits: np.ndarray            # [n, n_qubits] uint8
+    arrival: float              # seconds (server clock)
+    done: float = -1.0
+    amps: np.ndarray | None = None
+
+
+@dataclass
+class _Batch:
+    reqs: list
+    bits_host: object           # pinned uint8 tensor
+    bits_dev: object
+    amps_dev: object
+    amps_host: object           # pinned float64 tensor
+    chunks: list                # [(s0, s1)] still to run
+    acc_s: np.ndarray = None    # Neumaier sum over chunks, complex as float64 pairs
+    acc_c: np.ndarray = None
+    event: object = None
+    inflight: tuple = None
+
+
+class _Lane:
+    def __init__(self, circ, dev, precision, max_bits, executor):
+        import torch
+        self.stream = torch.cuda.Stream(dev)
+        self.c = qx.Contractor(circ.n_qubits, circ.gates, circ.open_mask, circ.order, circ.sliced, max_bits,
+                               device=dev.index or 0, precision=precision, stream=self.stream, executor=executor,
+                               workspace_bytes=circ.lane_bytes)
+        self.batch = None
+
+
+@dataclass
+class ServedCircuit:
+    n_qubits: int
+    gates: np.ndarray
+    open_mask: np.ndarray
+    order: list
+    sliced: list
+    flops_per_slice: float
+    n_open: int = 0
+    n_slices: int = 1
+    lane_bytes: int = 0
+    servable: bool = True
+    lanes: list = field(default_factory=list)
+    queue: collections.deque = field(default_factory=collections.deque)
+
+
+class Server:
+    def __init__(self, circuits, device=0, precision=qx.QX_PREC_C64, max_bits=1024, mem_budget=None,
+                 chunk_flops=2e11, max_lanes_per_circuit=2, items_per_lane=4096):
+        import torch
+        self.torch = torch
+        self.dev = torch.device("cuda", device)
+        self.precision = precision
+        self.max_bits = max_bits
+        self.chunk_flops = chunk_flops
+        self.max_lanes = max_lanes_per_circuit
+        free, _ = torch.cuda.mem_get_info(self.dev)
+        self.budget = int(mem_budget if mem_budget is not None else free * 0.7)
+        self.committed = 0
+        self.circuits = []
+        for w in circuits:
+            sc = ServedCircuit(w.n_qubits, w.gates, w.open_mask, w.order, w.sliced, float(w.flops_per_slice),
+                               n_open=int(np.sum(w.open_mask)), n_slices=1 << len(w.sliced))
+            h = qx.qx_create(-1, precision=precision)
+            qx.qx_build_network(h, w.n_qubits, w.gates, w.open_mask)
+            qx.qx_set_plan(h, w.order, w.sliced)
+            # pairs per batch: as many as a lane's share of the budget holds
+            one = qx.qx_workspace_size(h, max_bits, 1)
+            per_pair = max(qx.qx_workspace_size(h, max_bits, 2) - one, 1)
+            fit = (self.budget // 8 - one) // per_pair
+            items = int(max(1, min(items_per_lane, sc.n_slices * max_bits, fit)))
+            sc.lane_bytes = qx.qx_workspace_size(h, max_bits, items)
+            sc.servable = sc.lane_bytes <= self.budget
+            qx.qx_destroy(h)
+            self.circuits.append(sc)
+        self.clock0 = time.perf_counter()
+        self.done = []
+        self.stats = collections.Counter()
+
+    def now(self):
+        return time.perf_counter() - self.clock0
+
+    # -- admission ----------------------------------------------------------------------------------
+    def _free_lane(self, ci):
+        sc = self.circuits[ci]
+        for lane in sc.lanes:
+            if lane.batch is None:
+                return lane
+        if len(sc.lanes) < self.max_lanes and self.committed + sc.lane_bytes <= self.budget:
+            lane = _Lane(sc, self.dev, self.precision, self.max_bits, qx.EXEC_BATCHED)
+            sc.lanes.append(lane)
+            self.committed += sc.lane_bytes
+            self.stats["lanes"] += 1
+            return lane
+        return None
+
+    def submit(self, req: Request):
+        sc = self.circuits[req.circuit]
+        if not sc.servable or len(req.bits) > self.max_bits:
+            self.stats["rejected"] += 1  # needs more device memory than the budget, or too many bitstrings
+            return False
+        sc.queue.append(req)
+        return True
+
+    def _start(self, ci, lane):
+        torch = self.torch
+        sc = self.circuits[ci]
+        reqs, n = [], 0
+        while sc.queue and n + len(sc.queue[0].bits) <= self.max_bits:
+            r = sc.queue.popleft()
+            reqs.append(r)
+            n += len(r.bits)
+        if not reqs:
+            return False
+        bits = np.concatenate([r.bits for r in reqs]).astype(np.uint8)
+        bh = torch.from_numpy(bits).pin_memory()
+        with torch.cuda.stream(lane.stream):
+            bd = bh.to(self.dev, non_blocking=True)
+            ad = torch.empty((n, 1 << sc.n_open, 2), dtype=torch.float64, device=self.dev)
+        ah = torch.empty((n, 1 << sc.n_open, 2), dtype=torch.float64).pin_memory()
+        per_slice = max(sc.flops_per_slice * n, 1.0)
+        step = int(max(1, min(sc.n_slices, self.chunk_flops // per_slice)))
+        chunks = [(s, min(s + step, sc.n_slices)) for s in range(0, sc.n_slices, step)]
+        lane.batch = _Batch(reqs, bh, bd, ad, ah, chunks, np.zeros((n, 1 << sc.n_open, 2)),
+                            np.zeros((n, 1 << sc.n_open, 2)))
+        self.stats["batches"] += 1
+        self.stats["merged_requests"] += len(reqs) - 1
+        self._launch_chunk(lane)
+        return True
+
+    def _launch_chunk(self, lane):
+        torch = self.torch
+        b = lane.batch
+        s0, s1 = b.chunks.pop(0)
+        with torch.cuda.stream(lane.stream):
+            lane.c.contract_device(b.bits_dev, b.amps_dev, s0, s1)
+            b.amps_host.copy_(b.amps_dev, non_blocking=True)
+            b.event = torch.cuda.Event()
+            b.event.record(lane.stream)
+        b.inflight = (s0, s1)
+        self.stats["chunks"] += 1
+
+    def _finish_chunk(self, lane):
+        b = lane.batch
+        x = b.amps_host.numpy()
+        t = b.acc_s + x
+        big = np.abs(b.acc_s) >= np.abs(x)
+        b.acc_c += np.where(big, (b.acc_s - t) + x, (x - t) + b.acc_s)
+        b.acc_s = t
+        if b.chunks:
+            self._launch_chunk(lane)
+            return
+        tot = b.acc_s + b.acc_c
+        amps = tot[..., 0] + 1j * tot[..., 1]
+        t_done = self.now()
+        k = 0
+        for r in b.reqs:
+            r.amps = amps[k:k + len(r.bits)].copy()
+            k += len(r.bits)
+            r.done = t_done
+            self.done.append(r)
+        lane.batch = None
+
+    # -- the loop -----------------------------------------------------------------------------------
+    def poll(self):
+        """Retire finished chunks, start queued work on free lanes; returns True if anything is in flight."""
+        busy = False
+        for sc in self.circuits:
+            for lane in sc.lanes:
+                if lane.batch is not None and lane.batch.event.query():
+                    self._finish_chunk(lane)
+        for ci, sc in enumerate(self.circuits):
+            while sc.queue:
+                lane = self._free_lane(ci)
+                if lane is None or not self._start(ci, lane):
+                    break
+        for sc in self.circuits:
+            busy = busy or any(l.batch is not None for l in sc.lanes) or bool(sc.queue)
+        return busy
+
+    def run(self, requests, deadline=None, idle_sleep=2e-4):
+        """Feed `requests` (sorted by arrival) in real time; returns when all are done or at `deadline`."""
+        i = 0
+        self.clock0 = time.perf_counter()
+        while True:
+            t = self.now()
+            while i < len(requests) and requests[i].arrival <= t:
+                self.submit(requests[i])
+                i += 1
+            busy = self.poll()
+            if i >= len(requests) and not busy:
+                break
+            if deadline is not None and t > deadline:
+                break
+            if not busy:
+                time.sleep(idle_sleep)
+        return self.done
+
+    def close(self):
+        self.torch.cuda.synchronize(self.dev)
+        for sc in self.circuits:
+            for lane in sc.lanes:
+                lane.c.close()
+            sc.lanes.clear()
+
+
+def poisson_requests(n_circuits, n_qubits_of, rate, duration, max_bits, seed):
+    """Seeded Poisson arrivals: exponential gaps of mean 1/rate, circuits and sizes uniform."""
+    from qxgen.circuits import SplitMix64, random_bitstrings
+    rng = SplitMix64(seed)
+    reqs, t, rid = [], 0.0, 0
+    while True:
+        t += -np.log(1.0 - rng.uniform()) / rate
+        if t > duration:
+            break
+        ci = rng.randint(n_circuits)
+        nb = 1 + rng.randint(max_bits)
+        bits = random_bitstrings(n_qubits_of(ci), nb, seed * 7919 + rid)
+        reqs.append(Request(rid, ci, bits, t))
+        rid += 1
+    return reqs
+
+
+def latency_summary(done):
+    lat = np.array([r.done - r.arrival for r in done]) if done else np.zeros(0)
+    amps = sum(r.amps.size for r in done)
+    return {"completed": len(done), "amplitudes": int(amps),
+            "p50_ms": float(np.percentile(lat, 50) * 1e3) if len(lat) else None,
+            "p99_ms": float(np.percentile(lat, 99) * 1e3) if len(lat) else None}

@@ -151,3 +151,21 @@ def batched_members(count=256, max_peak_rank=BATCHED_MAX_PEAK_RANK):
 
 def batched_excluded(count=256, max_peak_rank=BATCHED_MAX_PEAK_RANK):
     return [batched_circuit(j) for j in range(count) if batched_circuit(j).peak_rank > max_peak_rank]
+
+
+def serving_specs(count=32):
+    """Per-circuit (n, depth) draws of the serving workload."""
+    rng = SplitMix64(5000)
+    return [(20 + rng.randint(21), 10 + rng.randint(7)) for _ in range(count)]
+
+
+@functools.lru_cache(maxsize=None)
+def serving_circuit(j, peak_rank=30):
+    """Resident circuit j of the serving workload, sliced until its peak fits 2^peak_rank entries."""
+    n, depth = serving_specs()[j]
+    cseed = 5000 + j
+    rows, cols = near_square_shape(n)
+    circ = random_grid_circuit(rows, cols, depth, cseed, n=n)
+    bits = random_bitstrings(n, 1, cseed + 500000)
+    return _workload(f"serving{j}_n{n}_d{depth}", circ, np.zeros(n, np.uint8), 0, cseed, bits, trials=1,
+                     peak_rank=peak_rank, meta={"n": n, "depth": depth, "j": j})

@@ -1,0 +1,59 @@
+"""Continuous-batching server: every request's amplitudes match the oracle,
+and a request gives the same result alone and in a busy mix (needs a GPU)."""
+import numpy as np
+import pytest
+
+import oracle
+from qxgen import circuits as C
+from qxgen.workloads import _workload
+
+from ._util import TOL_C64, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def serve():
+    from paper_2110_09894_gb300 import build
+    build.build()
+    from paper_2110_09894_gb300 import serve as mod
+    return mod
+
+
+def _circuits():
+    out = []
+    for j, (r, c, d, s) in enumerate([(3, 4, 8, 3), (2, 5, 10, 2), (3, 3, 12, 4), (4, 4, 6, 1)]):
+        circ = C.random_grid_circuit(r, c, d, 800 + j)
+        out.append(_workload(f"srv{j}", circ, np.zeros(circ.n_qubits, np.uint8), s, 800 + j,
+                             np.zeros((1, circ.n_qubits), np.uint8)))
+    return out
+
+
+def test_requests_match_oracle_and_alone_equals_mix(serve):
+    ws = _circuits()
+    reqs = serve.poisson_requests(len(ws), lambda i: ws[i].n_qubits, rate=2000.0, duration=0.05, max_bits=24, seed=5)
+    assert len(reqs) > 20
+    srv = serve.Server(ws, max_bits=96, chunk_flops=2e5, max_lanes_per_circuit=2)
+    done = srv.run(reqs, deadline=120)
+    assert len(done) == len(reqs)
+    assert srv.stats["chunks"] > srv.stats["batches"]  # long batches ran in several slice chunks
+    for r in done:
+        w = ws[r.circuit]
+        ref = oracle.sv_amplitudes(w.n_qubits, w.gates, w.open_mask, r.bits)
+        assert rel_l2(r.amps, ref) <= TOL_C64
+    summary = serve.latency_summary(done)
+    assert summary["completed"] == len(reqs) and summary["p99_ms"] >= summary["p50_ms"] > 0
+    srv.close()
+    # the same request alone on an idle server
+    probe = max(done, key=lambda r: len(r.bits))
+    alone = serve.Server(ws, max_bits=96, chunk_flops=2e5)
+    one = alone.run([serve.Request(0, probe.circuit, probe.bits, 0.0)], deadline=60)
+    assert rel_l2(one[0].amps, probe.amps) <= TOL_C64
+    alone.close()
+
+
+def test_memory_admission_rejects_what_cannot_fit(serve):
+    ws = _circuits()
+    srv = serve.Server(ws, max_bits=8, mem_budget=1 << 10)
+    assert not srv.submit(serve.Request(0, 0, np.zeros((1, ws[0].n_qubits), np.uint8), 0.0))
+    assert srv.stats["rejected"] == 1
