@@ -39,7 +39,9 @@ def parse():
     p.add_argument("--steps", type=int, default=10)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--workload", default="sliced", choices=["small", "sliced", "large"])
+    p.add_argument("--workload", default="sliced", choices=["small", "sliced", "large", "batched", "serving"])
+    p.add_argument("--serve-seconds", type=float, default=20.0, help="arrival window of the serving run")
+    p.add_argument("--serve-rate", type=float, default=200.0, help="mean requests per second (Poisson)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--max-items", type=int, default=0, help="cap on (slice, bitstring) pairs per batch (0 = fill)")
     p.add_argument("--precision", default="c64", choices=list(PRECISIONS))
@@ -200,12 +202,96 @@ def traffic_for(kind):
         return None
 
 
+def group_bench(args):
+    """All member circuits of the uneven batched workload: one captured graph (3 launches) per step."""
+    import torch
+    from paper_2110_09894_gb300 import autotune, qx
+    from paper_2110_09894_gb300 import build as qxbuild
+    qxbuild.build()
+    ws = W.batched_members()
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(dev)
+    cs = [qx.Contractor(w.n_qubits, w.gates, w.open_mask, w.order, w.sliced, len(w.bitstrings),
+                        executor=qx.EXEC_GROUP_MEMBER, stream=stream) for w in ws]
+    bits = [torch.from_numpy(w.bitstrings).to(dev) for w in ws]
+    torch.cuda.synchronize()
+    g, ctas, tune_ms = autotune.tuned_group(cs, bits)
+    g.capture()
+    amps = sum(len(w.bitstrings) << w.n_open for w in ws)
+    flops = sum(float(w.flops_per_slice) * w.n_slices * len(w.bitstrings) for w in ws)
+    for _ in range(args.warmup):
+        g.replay()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    sampler = ClockSampler(0)
+    sampler.start()
+    for i in range(args.steps):
+        ev[i][0].record(stream)
+        g.replay()
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    ms = [a.elapsed_time(b) for a, b in ev]
+    worst = 0.0
+    for w, a in zip(ws[:8], g.amplitudes()[:8]):
+        if w.n_qubits <= 24:
+            import oracle
+            ref = oracle.sv_amplitudes(w.n_qubits, w.gates, w.open_mask, w.bitstrings)
+            worst = max(worst, float(np.linalg.norm(a - ref) / np.linalg.norm(ref)))
+    line = {"metric": "amplitudes/s", "value": amps * len(ms) / (sum(ms) / 1e3), "unit": "amplitudes/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": sum(ms) / len(ms),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c64", "data": "synthetic",
+            "config": {"workload": "batched uneven grid circuits (n 16..28, depth 8..16, S 0..8, 1..64 bitstrings)",
+                       "members": len(ws), "excluded_heavy_tail": len(W.batched_excluded()),
+                       "pairs": int(sum(w.n_slices * len(w.bitstrings) for w in ws)),
+                       "executor": "group: one captured graph = prologue launch + persistent launch + FP64 sum",
+                       "autotuned_ctas_per_sm": ctas, "autotune_ms": tune_ms},
+            "complex_tflops": flops * len(ms) / (sum(ms) / 1e3) / 1e12, "rel_err_first_members": worst,
+            "gpu_launches": 3 * args.steps, "clocks": clocks}
+    print(json.dumps(line), flush=True)
+
+
+def serving_bench(args):
+    """Poisson arrivals on the 32 resident serving circuits; sustained throughput and latency."""
+    import torch
+    from paper_2110_09894_gb300 import build as qxbuild
+    from paper_2110_09894_gb300 import serve
+    qxbuild.build()
+    ws = [W.serving_circuit(j) for j in range(32)]
+    reqs = serve.poisson_requests(len(ws), lambda i: ws[i].n_qubits, args.serve_rate, args.serve_seconds, 1024, 5000)
+    srv = serve.Server(ws, precision=PRECISIONS[args.precision][0], max_bits=1024)
+    sampler = ClockSampler(0)
+    sampler.start()
+    t0 = time.perf_counter()
+    done = srv.run(reqs, deadline=args.serve_seconds + 30.0)
+    wall = time.perf_counter() - t0
+    clocks = sampler.stop()
+    summ = serve.latency_summary(done)
+    offered_amps = sum(r.bits.shape[0] for r in reqs)
+    line = {"metric": "amplitudes/s", "value": summ["amplitudes"] / wall, "unit": "amplitudes/s", "n_gpus": 1,
+            "steps": 1, "warmup": 0, "ms_per_step": wall * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
+            "config": {"workload": "serving: 32 resident grid circuits (n 20..40, depth 10..16, peak <= 2^30)",
+                       "arrivals": f"Poisson {args.serve_rate}/s for {args.serve_seconds} s",
+                       "requests": len(reqs), "offered_amplitudes": offered_amps},
+            "latency_ms": {"p50": summ["p50_ms"], "p99": summ["p99_ms"]}, "completed": summ["completed"],
+            "rejected": srv.stats["rejected"], "rejected_cost": srv.stats["rejected_cost"],
+            "merged_requests": srv.stats["merged_requests"], "max_request_flops": srv.max_request_flops,
+            "chunks": srv.stats["chunks"], "lanes": srv.stats["lanes"], "clocks": clocks}
+    srv.close()
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
-    w = workload(args.workload)
+    if args.impl == "ours" and args.workload == "batched":
+        return group_bench(args)
+    if args.impl == "ours" and args.workload == "serving":
+        return serving_bench(args)
+    w = workload(args.workload) if args.workload in ("small", "sliced", "large") else W.sliced()
     if args.impl == "reference":
         reference_arm(args, w, rank, world)
         return

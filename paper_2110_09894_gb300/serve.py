@@ -15,7 +15,10 @@ while other work is on the GPU:
   workspace and CUDA stream); lanes are created on demand while the device
   memory budget allows (admission by memory) and reused afterwards;
 * completion is detected with CUDA events; latency runs from a request's
-  arrival to the host seeing its amplitudes.
+  arrival to the host seeing its amplitudes;
+* a request is rejected at arrival if its circuit cannot get a lane within
+  the memory budget or if its estimated work (plan flops x slices x
+  bitstrings) exceeds max_request_flops.
 
 The scheduling runs on the host in Python (it only marshals work); every
 contraction step runs in the library's kernels.
@@ -83,7 +86,7 @@ class ServedCircuit:
 
 class Server:
     def __init__(self, circuits, device=0, precision=qx.QX_PREC_C64, max_bits=1024, mem_budget=None,
-                 chunk_flops=2e11, max_lanes_per_circuit=2, items_per_lane=4096):
+                 chunk_flops=2e11, max_lanes_per_circuit=2, items_per_lane=4096, max_request_flops=5e14):
         import torch
         self.torch = torch
         self.dev = torch.device("cuda", device)
@@ -91,6 +94,7 @@ class Server:
         self.max_bits = max_bits
         self.chunk_flops = chunk_flops
         self.max_lanes = max_lanes_per_circuit
+        self.max_request_flops = max_request_flops
         free, _ = torch.cuda.mem_get_info(self.dev)
         self.budget = int(mem_budget if mem_budget is not None else free * 0.7)
         self.committed = 0
@@ -135,6 +139,10 @@ class Server:
         sc = self.circuits[req.circuit]
         if not sc.servable or len(req.bits) > self.max_bits:
             self.stats["rejected"] += 1  # needs more device memory than the budget, or too many bitstrings
+            return False
+        if sc.flops_per_slice * sc.n_slices * len(req.bits) > self.max_request_flops:
+            self.stats["rejected"] += 1  # more work than the server accepts for one request
+            self.stats["rejected_cost"] += 1
             return False
         sc.queue.append(req)
         return True
