@@ -30,7 +30,7 @@ from qxgen import workloads as W  # noqa: E402
 
 L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
 # name -> (C-ABI code, tensor-core products per real MMA, peak ratio to measured BF16)
-PRECISIONS = {"c64": (0, 0, 0.0), "3xtf32": (1, 3, 1.1 / 2.25), "bf16x3": (2, 6, 1.0)}
+PRECISIONS = {"c64": (0, 0, 0.0), "3xtf32": (1, 3, 1.1 / 2.25), "bf16x3": (2, 6, 1.0), "fp16": (3, 1, 1.0)}
 
 
 def parse():
@@ -42,6 +42,7 @@ def parse():
     p.add_argument("--workload", default="sliced", choices=["small", "sliced", "large", "batched", "serving"])
     p.add_argument("--serve-seconds", type=float, default=20.0, help="arrival window of the serving run")
     p.add_argument("--serve-rate", type=float, default=200.0, help="mean requests per second (Poisson)")
+    p.add_argument("--serve-max-flops", type=float, default=5e14, help="largest request the server admits")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--max-items", type=int, default=0, help="cap on (slice, bitstring) pairs per batch (0 = fill)")
     p.add_argument("--precision", default="c64", choices=list(PRECISIONS))
@@ -259,7 +260,8 @@ def serving_bench(args):
     qxbuild.build()
     ws = [W.serving_circuit(j) for j in range(32)]
     reqs = serve.poisson_requests(len(ws), lambda i: ws[i].n_qubits, args.serve_rate, args.serve_seconds, 1024, 5000)
-    srv = serve.Server(ws, precision=PRECISIONS[args.precision][0], max_bits=1024)
+    srv = serve.Server(ws, precision=PRECISIONS[args.precision][0], max_bits=1024,
+                       max_request_flops=args.serve_max_flops)
     sampler = ClockSampler(0)
     sampler.start()
     t0 = time.perf_counter()
@@ -436,7 +438,7 @@ def main():
 
     line = {"metric": "amplitudes/s", "value": value, "unit": "amplitudes/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": {"c64": "c64", "3xtf32": "tf32x3", "bf16x3": "bf16x3"}[args.precision],
+            "vs_baseline": None, "dtype": {"c64": "c64", "3xtf32": "tf32x3", "bf16x3": "bf16x3", "fp16": "fp16"}[args.precision],
             "data": "synthetic",
             "config": config_of(w, {"precision": args.precision + " contraction, FP64 slice sum",
                                     "executor": args.executor,

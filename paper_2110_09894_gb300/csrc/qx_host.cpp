@@ -493,9 +493,10 @@ static int compile_plan(qx_ctx* h, const int64_t* order, int64_t n_steps, const 
 
         // TTGT path: operands as matrices [M][K] / [K][M] and [N][K] / [K][N], C = [M][N].
         // The tensor-core kernel tiles M by 128, so the larger free side becomes M.
-        const int tc_form = h->opt.precision == QX_PREC_3XTF32      ? TC_FORM_3XTF32
-                            : h->opt.precision == QX_PREC_SPLIT_BF16 ? TC_FORM_BF16X3
-                                                                     : 0;
+        const int tc_form = h->opt.precision == QX_PREC_3XTF32       ? TC_FORM_3XTF32
+                            : h->opt.precision == QX_PREC_SPLIT_BF16  ? TC_FORM_BF16X3
+                            : h->opt.precision == QX_PREC_FP16_SCALED ? TC_FORM_FP16
+                                                                      : 0;
         int ga = a, gb = b;
         std::vector<int> fA = freeA, fB = freeB;
         if (tc_form && (int)fA.size() < 7 && (int)fB.size() >= 7) {
@@ -904,6 +905,7 @@ static int run_op(qx_ctx* h, const Op& op, const ItemCtx& ic, int64_t n_items) {
         g.n_items = n_items;
         g.limit = h->opt.timeout_cycles > 0 ? h->opt.timeout_cycles : 2000000000ll;
         g.err = (int*)(h->ws + h->off_err);
+        g.amax = (float*)(h->ws + h->off_err + 16);
         e = launch_tc_prep(op.tc, g, h->stream);
         if (e == cudaSuccess) e = prof_end(h, slot);
         if (e == cudaSuccess) e = prof_begin(h, QX_KERNEL_TC_GEMM, op.flops * (double)n_items, op_bytes(h, op) * (double)n_items, &slot);
@@ -1112,7 +1114,7 @@ int qx_create(qx_handle* out, int device, void* stream, const qx_options* opt) {
     }
     h->stream = (cudaStream_t)stream;
     if (opt) h->opt = *opt;
-    if (h->opt.precision < QX_PREC_C64 || h->opt.precision > QX_PREC_SPLIT_BF16 || h->opt.max_items < 0 ||
+    if (h->opt.precision < QX_PREC_C64 || h->opt.precision > QX_PREC_FP16_SCALED || h->opt.max_items < 0 ||
         h->opt.executor < 0 || h->opt.executor > 3) {
         delete h;
         return QX_EINVAL;
@@ -1135,7 +1137,7 @@ const char* qx_last_error(qx_handle h) { return h ? h->err.c_str() : "null handl
 
 int qx_set_options(qx_handle h, const qx_options* opt) {
     if (!h || !opt) return QX_EINVAL;
-    if (opt->precision < QX_PREC_C64 || opt->precision > QX_PREC_SPLIT_BF16)
+    if (opt->precision < QX_PREC_C64 || opt->precision > QX_PREC_FP16_SCALED)
         return fail(h, QX_EINVAL, "precision form %d is not available", opt->precision);
     if (h->have_plan && opt->precision != h->opt.precision)
         return fail(h, QX_ESTATE, "set the precision form before qx_set_plan");

@@ -53,6 +53,17 @@ struct PermDesc {
     int8_t outer[kMaxRank];
 };
 
+// Address tables of a permutation tile, computed once on the host: entry j
+// of the tile (input order) sits at in_lo[j & 31] + in_hi[j >> 5] from the
+// tile's input base; entry j (output order) goes to out_lo[..] + out_hi[..]
+// from the output base and is read from tile slot map_lo[..] | map_hi[..];
+// outer bit i moves the bases by outer_in[i] / outer_out[i].
+struct PermTables {
+    int64_t in_lo[32], in_hi[32], out_lo[32], out_hi[32];
+    int32_t map_lo[32], map_hi[32];
+    int64_t outer_in[kMaxRank], outer_out[kMaxRank];
+};
+
 // Gather contraction with one small operand Y (<= 2^10 entries):
 //   C[m * 2^nb + n] = sum_k X[m, k] * Y[k, n]
 // m enumerates X's free legs (bit i = i-th lowest free position), k the
@@ -78,6 +89,7 @@ struct SumDesc {
 // Launchers; each returns the launch error (cudaSuccess on success).
 cudaError_t launch_permute(const PermDesc& d, const ItemCtx& ic, int64_t n_items, float2* out,
                            int64_t out_item_stride, cudaStream_t st);
+void perm_tables(const PermDesc& d, PermTables* tb);
 cudaError_t launch_small(const SmallDesc& d, const ItemCtx& ic, int64_t n_items, float2* out,
                          int64_t out_item_stride, cudaStream_t st);
 // Batched complex GEMM, C[M][N] = A . B with A stored [M][K] (a_kmajor) or
@@ -153,7 +165,7 @@ cudaError_t launch_single_sum(const GSum& g, int64_t total, cudaStream_t st);
 // Tensor-core complex GEMM (qx_tc.cu).  Operands are contiguous complex64
 // per item, [R][K] (kmajor) or [K][R]; pa / pb receive the split real parts
 // (prep), then the tcgen05 kernel writes C [M][N] complex64.
-constexpr int TC_FORM_3XTF32 = 1, TC_FORM_BF16X3 = 2;
+constexpr int TC_FORM_3XTF32 = 1, TC_FORM_BF16X3 = 2, TC_FORM_FP16 = 3;
 struct TcArgs {
     const float2* a;
     int64_t a_is;
@@ -171,6 +183,7 @@ struct TcArgs {
     int64_t n_items;
     long long limit;  // clock cycles per bounded wait
     int* err;         // device error flag (QX_ETIMEOUT on expiry)
+    float* amax;      // FP16 form: device max |x| of A and B (2 floats), sets the per-tensor scales
 };
 int tc_parts_a(int form);
 int tc_parts_b(int form);

@@ -9,6 +9,8 @@
 // per-item address offsets here, recombination into the FP64 sum.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "qx_internal.h"
 
 namespace qx {
@@ -46,70 +48,105 @@ __device__ __forceinline__ void cfma(float2& acc, float2 a, float2 b) {
 // ---------------------------------------------------------------------------------------------
 __device__ __forceinline__ int pad32(int j) { return j + (j >> 5); }
 
-__global__ void __launch_bounds__(256) k_permute(const PermDesc d, const ItemCtx ic, float2* __restrict__ out,
-                                                 int64_t out_is) {
-    __shared__ float2 tile[1024 + 32];
-    __shared__ int64_t in_lo[32], in_hi[32], out_lo[32], out_hi[32];
-    __shared__ int map_lo[32], map_hi[32];
-    const int tid = threadIdx.x;
+void perm_tables(const PermDesc& d, PermTables* tb) {
     const int t = d.t;
-    if (tid < 32) {
+    for (int j = 0; j < 32; ++j) {
         int64_t a = 0, b = 0, c = 0, e = 0;
         int ml = 0, mh = 0;
         for (int i = 0; i < 5; ++i) {
-            if ((tid >> i) & 1) {
-                if (i < t) {
-                    a += (int64_t)1 << d.in_pos[d.tile_in[i]];
-                    c += (int64_t)1 << d.tile_out[i];
-                }
-                if (i + 5 < t) {
-                    b += (int64_t)1 << d.in_pos[d.tile_in[i + 5]];
-                    e += (int64_t)1 << d.tile_out[i + 5];
-                }
+            if (!((j >> i) & 1)) continue;
+            if (i < t) {
+                a += (int64_t)1 << d.in_pos[d.tile_in[i]];
+                c += (int64_t)1 << d.tile_out[i];
+            }
+            if (i + 5 < t) {
+                b += (int64_t)1 << d.in_pos[d.tile_in[i + 5]];
+                e += (int64_t)1 << d.tile_out[i + 5];
             }
         }
         // where output-ordered tile bit i sits in the input-ordered tile index
-        for (int i = 0; i < 10 && i < t; ++i) {
+        for (int i = 0; i < t; ++i) {
             int r = 0;
-            for (int j = 0; j < t; ++j)
-                if (d.tile_in[j] == d.tile_out[i]) r = j;
+            for (int k = 0; k < t; ++k)
+                if (d.tile_in[k] == d.tile_out[i]) r = k;
             if (i < 5) {
-                if ((tid >> i) & 1) ml |= 1 << r;
-            } else {
-                if ((tid >> (i - 5)) & 1) mh |= 1 << r;
+                if ((j >> i) & 1) ml |= 1 << r;
+            } else if ((j >> (i - 5)) & 1) {
+                mh |= 1 << r;
             }
         }
-        in_lo[tid] = a;
-        in_hi[tid] = b;
-        out_lo[tid] = c;
-        out_hi[tid] = e;
-        map_lo[tid] = ml;
-        map_hi[tid] = mh;
+        tb->in_lo[j] = a;
+        tb->in_hi[j] = b;
+        tb->out_lo[j] = c;
+        tb->out_hi[j] = e;
+        tb->map_lo[j] = ml;
+        tb->map_hi[j] = mh;
     }
-    const int64_t item = blockIdx.y;
-    const int64_t u = blockIdx.x;
-    int64_t ib = fix_offset(d.in, ic, item);
-    int64_t ob = item * out_is;
-    for (int i = 0; i < d.n_outer; ++i) {
-        if ((u >> i) & 1) {
-            ib += (int64_t)1 << d.in_pos[d.outer[i]];
-            ob += (int64_t)1 << d.outer[i];
+    for (int i = 0; i < kMaxRank; ++i) {
+        tb->outer_in[i] = i < d.n_outer ? (int64_t)1 << d.in_pos[d.outer[i]] : 0;
+        tb->outer_out[i] = i < d.n_outer ? (int64_t)1 << d.outer[i] : 0;
+    }
+}
+
+// Grid-stride over (pair, tile) jobs: the tables are loaded into shared memory
+// once per CTA, each job moves one tile of up to 2^10 entries.
+__global__ void __launch_bounds__(256) k_permute(const PermDesc d, const PermTables tb, const ItemCtx ic,
+                                                 float2* __restrict__ out, int64_t out_is, int64_t n_items) {
+    __shared__ float2 tile[1024 + 32];
+    __shared__ int64_t s_in[64], s_out[64];
+    __shared__ int s_map[64];
+    const int tid = threadIdx.x;
+    if (tid < 32) {
+        s_in[tid] = tb.in_lo[tid];
+        s_in[32 + tid] = tb.in_hi[tid];
+        s_out[tid] = tb.out_lo[tid];
+        s_out[32 + tid] = tb.out_hi[tid];
+        s_map[tid] = tb.map_lo[tid];
+        s_map[32 + tid] = tb.map_hi[tid];
+    }
+    __syncthreads();
+    const int n = 1 << d.t;
+    const int64_t tiles = (int64_t)1 << d.n_outer;
+    const int64_t jobs = tiles * n_items;
+    for (int64_t job = blockIdx.x; job < jobs; job += gridDim.x) {
+        const int64_t item = job >> d.n_outer;
+        uint64_t u = (uint64_t)(job & (tiles - 1));
+        int64_t ib = fix_offset(d.in, ic, item), ob = item * out_is;
+        while (u) {
+            const int i = __ffsll((long long)u) - 1;
+            ib += tb.outer_in[i];
+            ob += tb.outer_out[i];
+            u &= u - 1;
         }
+        const float2* __restrict__ src = d.in.base + ib;
+        for (int j = tid; j < n; j += 256) tile[pad32(j)] = src[s_in[j & 31] + s_in[32 + (j >> 5)]];
+        __syncthreads();
+        float2* __restrict__ dst = out + ob;
+        for (int j = tid; j < n; j += 256) dst[s_out[j & 31] + s_out[32 + (j >> 5)]] = tile[pad32(s_map[j & 31] | s_map[32 + (j >> 5)])];
+        __syncthreads();
     }
-    __syncthreads();
-    const int n = 1 << t;
-    const float2* __restrict__ src = d.in.base + ib;
-    for (int j = tid; j < n; j += blockDim.x) tile[pad32(j)] = src[in_lo[j & 31] + in_hi[j >> 5]];
-    __syncthreads();
-    float2* __restrict__ dst = out + ob;
-    for (int j = tid; j < n; j += blockDim.x) dst[out_lo[j & 31] + out_hi[j >> 5]] = tile[pad32(map_lo[j & 31] | map_hi[j >> 5])];
+}
+
+static int sm_count() {
+    static int n = 0;
+    if (!n) {
+        int dev = 0, v = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0)
+            n = v;
+        else
+            n = 152;
+    }
+    return n;
 }
 
 cudaError_t launch_permute(const PermDesc& d, const ItemCtx& ic, int64_t n_items, float2* out, int64_t out_is,
                            cudaStream_t st) {
     if (n_items <= 0) return cudaSuccess;
-    dim3 grid((unsigned)(1ll << d.n_outer), (unsigned)n_items);
-    k_permute<<<grid, 256, 0, st>>>(d, ic, out, out_is);
+    PermTables tb;
+    perm_tables(d, &tb);
+    const int64_t jobs = ((int64_t)1 << d.n_outer) * n_items;
+    const int64_t grid = std::min<int64_t>(jobs, (int64_t)sm_count() * 8);
+    k_permute<<<(unsigned)grid, 256, 0, st>>>(d, tb, ic, out, out_is, n_items);
     return cudaGetLastError();
 }
 

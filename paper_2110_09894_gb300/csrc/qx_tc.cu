@@ -15,6 +15,7 @@
 //   3xTF32:  x = hi + lo (hi = x rounded to TF32); hi.hi + hi.lo + lo.hi
 //   BF16x3:  x = b0 + b1 + b2 (each rounded to BF16 in turn);
 //            b0b0 + b0b1 + b1b0 + b0b2 + b1b1 + b2b0
+//   FP16:    one product of the operands scaled by powers of two (per tensor)
 // Tile: 128 rows of A x 128 rows of B' per CTA, one 128-byte K slab per
 // pipeline stage, two 128-column TMEM accumulators used in turn.  Warp 0
 // issues TMA, warp 1 owns TMEM and issues the MMAs, warps 2-5 add each stage's
@@ -24,8 +25,10 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstring>
 #include <mutex>
 
@@ -54,6 +57,24 @@ struct TcForm<TC_FORM_BF16X3> {
     static __device__ __forceinline__ int pb(int p) { return p == 0 ? 0 : p == 1 ? 1 : p == 2 ? 0 : p == 3 ? 2 : p == 4 ? 1 : 0; }
 };
 
+template <>
+struct TcForm<TC_FORM_FP16> {
+    using T = __half;
+    static constexpr int NPA = 1, NPB = 1, NPROD = 1, EB = 2, FMT = 0, STAGES = 6;
+    static __device__ __forceinline__ int pa(int) { return 0; }
+    static __device__ __forceinline__ int pb(int) { return 0; }
+};
+
+// FP16 form: a tensor is multiplied by 2^e with e chosen so that its largest
+// magnitude lands just below 2^14 (well inside FP16's range, away from its
+// subnormals); the epilogue divides by both operands' factors.
+__device__ __forceinline__ float fp16_scale(float amax) {
+    if (!(amax > 0.f) || !isfinite(amax)) return 1.f;
+    int ex;
+    frexpf(amax, &ex);  // amax < 2^ex
+    return ldexpf(1.f, 14 - ex);
+}
+
 // ------------------------------------------------------------------------------------------------
 // operand preparation (split into parts, expand B)
 // ------------------------------------------------------------------------------------------------
@@ -64,8 +85,10 @@ __device__ __forceinline__ float tf32_rna(float x) {
 }
 
 template <int FORM>
-__device__ __forceinline__ void split(float x, typename TcForm<FORM>::T* out, int64_t part_stride) {
-    if constexpr (FORM == TC_FORM_3XTF32) {
+__device__ __forceinline__ void split(float x, typename TcForm<FORM>::T* out, int64_t part_stride, float scale) {
+    if constexpr (FORM == TC_FORM_FP16) {
+        out[0] = __float2half_rn(x * scale);
+    } else if constexpr (FORM == TC_FORM_3XTF32) {
         const float hi = tf32_rna(x);
         out[0] = hi;
         out[part_stride] = x - hi;
@@ -83,8 +106,9 @@ __device__ __forceinline__ void split(float x, typename TcForm<FORM>::T* out, in
 // A (complex, [R][K] if kmajor else [K][R]) -> parts [P][R][2K]
 template <int FORM>
 __global__ void k_prep_a(const float2* __restrict__ src, int64_t src_is, bool kmajor, typename TcForm<FORM>::T* dst,
-                         int64_t dst_is_elems, int rb, int kb) {
+                         int64_t dst_is_elems, int rb, int kb, const float* amax) {
     using T = typename TcForm<FORM>::T;
+    const float sc = amax ? fp16_scale(amax[0]) : 1.f;
     const int64_t R = (int64_t)1 << rb, K = (int64_t)1 << kb;
     const int64_t item = blockIdx.y;
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -93,16 +117,17 @@ __global__ void k_prep_a(const float2* __restrict__ src, int64_t src_is, bool km
     const float2 v = src[item * src_is + (kmajor ? idx : k * R + r)];
     T* o = dst + item * dst_is_elems + r * 2 * K + 2 * k;
     const int64_t ps = R * 2 * K;
-    split<FORM>(v.x, o, ps);
-    split<FORM>(v.y, o + 1, ps);
+    split<FORM>(v.x, o, ps, sc);
+    split<FORM>(v.y, o + 1, ps, sc);
 }
 
 // B (complex, [R][K] if kmajor else [K][R]) -> parts [P][2R][2K]:
 // row 2r = (re, -im) per k, row 2r+1 = (im, re)
 template <int FORM>
 __global__ void k_prep_b(const float2* __restrict__ src, int64_t src_is, bool kmajor, typename TcForm<FORM>::T* dst,
-                         int64_t dst_is_elems, int rb, int kb) {
+                         int64_t dst_is_elems, int rb, int kb, const float* amax) {
     using T = typename TcForm<FORM>::T;
+    const float sc = amax ? fp16_scale(amax[1]) : 1.f;
     const int64_t R = (int64_t)1 << rb, K = (int64_t)1 << kb;
     const int64_t item = blockIdx.y;
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -111,10 +136,24 @@ __global__ void k_prep_b(const float2* __restrict__ src, int64_t src_is, bool km
     const float2 v = src[item * src_is + (kmajor ? idx : k * R + r)];
     T* o = dst + item * dst_is_elems + (2 * r) * 2 * K + 2 * k;
     const int64_t ps = 4 * R * K;
-    split<FORM>(v.x, o, ps);
-    split<FORM>(-v.y, o + 1, ps);
-    split<FORM>(v.y, o + 2 * K, ps);
-    split<FORM>(v.x, o + 2 * K + 1, ps);
+    split<FORM>(v.x, o, ps, sc);
+    split<FORM>(-v.y, o + 1, ps, sc);
+    split<FORM>(v.y, o + 2 * K, ps, sc);
+    split<FORM>(v.x, o + 2 * K + 1, ps, sc);
+}
+
+// max |re|, |im| over an operand (all items); non-negative floats order like their bit patterns
+__global__ void k_absmax(const float2* __restrict__ src, int64_t src_is, int64_t per_item, int64_t n_items,
+                         float* out) {
+    float m = 0.f;
+    const int64_t total = per_item * n_items;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t item = i / per_item, e = i - item * per_item;
+        const float2 v = src[item * src_is + e];
+        m = fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y)));
+    }
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax((unsigned int*)out, __float_as_uint(m));
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -212,7 +251,7 @@ struct TcMaps {
 template <int FORM>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_gemm_tc(const __grid_constant__ TcMaps maps, float* __restrict__ C, int64_t c_is, int M, int N2, int K2,
-              int tiles_n, long long limit, int* err) {
+              int tiles_n, long long limit, int* err, const float* amax) {
     using F = TcForm<FORM>;
     constexpr int BK = TC_ROWB / F::EB;                 // K elements per stage
     constexpr int KSTEP = 32 / F::EB;                   // K elements per MMA (32 bytes)
@@ -340,6 +379,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(s_addr(&tempty[b])) : "memory");
         }
         if (ok) {
+            if (amax) {  // undo the FP16 per-tensor scales (powers of two: exact)
+                const float inv = 1.f / (fp16_scale(amax[0]) * fp16_scale(amax[1]));
+#pragma unroll
+                for (int j = 0; j < TC_BN; ++j) tot[j] *= inv;
+            }
             // tiles are whole (rows and columns multiples of 128; see tc_shape_ok)
             const int row = m0 + 32 * q + lane;
             float4* d4 = (float4*)(C + (int64_t)item * c_is + (int64_t)row * N2 + n0);
@@ -383,28 +427,44 @@ static bool make_map(CUtensorMap* m, const void* base, int64_t k2, int64_t rows,
     const cuuint64_t strides[2] = {(cuuint64_t)(k2 * F::EB), (cuuint64_t)item_bytes};
     const cuuint32_t box[3] = {(cuuint32_t)(TC_ROWB / F::EB), (cuuint32_t)TC_BM, 1};
     const cuuint32_t es[3] = {1, 1, 1};
-    const CUtensorMapDataType dt = F::EB == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+    const CUtensorMapDataType dt = F::EB == 4                 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                   : FORM == TC_FORM_FP16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                                          : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
     return fn(m, dt, 3, const_cast<void*>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
               CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-int tc_parts_a(int form) { return form == TC_FORM_3XTF32 ? 2 : 3; }
-int tc_parts_b(int form) { return form == TC_FORM_3XTF32 ? 2 : 3; }
+int tc_parts_a(int form) { return form == TC_FORM_3XTF32 ? 2 : form == TC_FORM_FP16 ? 1 : 3; }
+int tc_parts_b(int form) { return tc_parts_a(form); }
 int tc_elem_bytes(int form) { return form == TC_FORM_3XTF32 ? 4 : 2; }
-int tc_products(int form) { return form == TC_FORM_3XTF32 ? 3 : 6; }
+int tc_products(int form) { return form == TC_FORM_3XTF32 ? 3 : form == TC_FORM_FP16 ? 1 : 6; }
 
 template <int FORM>
 static cudaError_t run_prep(const TcArgs& g, cudaStream_t st) {
     using F = TcForm<FORM>;
     using T = typename F::T;
     const int64_t M = 1ll << g.mb, N = 1ll << g.nb, K = 1ll << g.kb;
+    const float* amax = nullptr;
+    if constexpr (FORM == TC_FORM_FP16) {
+        if (!g.amax) return cudaErrorInvalidValue;
+        cudaError_t e = cudaMemsetAsync(g.amax, 0, 2 * sizeof(float), st);
+        if (e != cudaSuccess) return e;
+        const int64_t na = g.a_is ? g.n_items : 1, nb_ = g.b_is ? g.n_items : 1;
+        k_absmax<<<(unsigned)std::min<int64_t>((M * K * na + 255) / 256, 4096), 256, 0, st>>>(g.a, g.a_is, M * K, na,
+                                                                                               g.amax);
+        k_absmax<<<(unsigned)std::min<int64_t>((N * K * nb_ + 255) / 256, 4096), 256, 0, st>>>(g.b, g.b_is, N * K,
+                                                                                                nb_, g.amax + 1);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        amax = g.amax;
+    }
     dim3 grid((unsigned)((M * K + 255) / 256), (unsigned)g.n_items);
-    k_prep_a<FORM><<<grid, 256, 0, st>>>(g.a, g.a_is, g.a_kmajor, (T*)g.pa, g.pa_is_bytes / F::EB, g.mb, g.kb);
+    k_prep_a<FORM><<<grid, 256, 0, st>>>(g.a, g.a_is, g.a_kmajor, (T*)g.pa, g.pa_is_bytes / F::EB, g.mb, g.kb, amax);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     dim3 grid2((unsigned)((N * K + 255) / 256), (unsigned)g.n_items);
-    k_prep_b<FORM><<<grid2, 256, 0, st>>>(g.b, g.b_is, g.b_kmajor, (T*)g.pb, g.pb_is_bytes / F::EB, g.nb, g.kb);
+    k_prep_b<FORM><<<grid2, 256, 0, st>>>(g.b, g.b_is, g.b_kmajor, (T*)g.pb, g.pb_is_bytes / F::EB, g.nb, g.kb, amax);
     return cudaGetLastError();
 }
 
@@ -439,7 +499,8 @@ static cudaError_t run_gemm(const TcArgs& g, cudaStream_t st) {
     const int tiles_m = (int)((M + TC_BM - 1) / TC_BM), tiles_n = (int)((2 * N + TC_BN - 1) / TC_BN);
     dim3 grid((unsigned)(tiles_m * tiles_n), (unsigned)g.n_items);
     k_gemm_tc<FORM><<<grid, TC_THREADS, smem, st>>>(maps, (float*)g.c, g.c_is * 2, (int)M, (int)(2 * N), (int)(2 * K),
-                                                   tiles_n, g.limit, g.err);
+                                                   tiles_n, g.limit, g.err,
+                                                   FORM == TC_FORM_FP16 ? (const float*)g.amax : nullptr);
     return cudaGetLastError();
 }
 
@@ -452,6 +513,7 @@ cudaError_t launch_tc_prep(int form, const TcArgs& g, cudaStream_t st) {
     if (!tc_shape_ok(g)) return cudaErrorInvalidValue;
     if (form == TC_FORM_3XTF32) return run_prep<TC_FORM_3XTF32>(g, st);
     if (form == TC_FORM_BF16X3) return run_prep<TC_FORM_BF16X3>(g, st);
+    if (form == TC_FORM_FP16) return run_prep<TC_FORM_FP16>(g, st);
     return cudaErrorInvalidValue;
 }
 
@@ -459,10 +521,12 @@ cudaError_t launch_tc_gemm(int form, const TcArgs& g, cudaStream_t st) {
     if (!tc_shape_ok(g)) return cudaErrorInvalidValue;
     if (form == TC_FORM_3XTF32) return run_gemm<TC_FORM_3XTF32>(g, st);
     if (form == TC_FORM_BF16X3) return run_gemm<TC_FORM_BF16X3>(g, st);
+    if (form == TC_FORM_FP16) return run_gemm<TC_FORM_FP16>(g, st);
     return cudaErrorInvalidValue;
 }
 
 static_assert(TcForm<TC_FORM_3XTF32>::STAGES * 4 * TC_BM * TC_ROWB + 1024 <= TC_SMEM_LIMIT + 1024, "smem");
 static_assert(TcForm<TC_FORM_BF16X3>::STAGES * 6 * TC_BM * TC_ROWB + 1024 <= TC_SMEM_LIMIT + 1024, "smem");
+static_assert(TcForm<TC_FORM_FP16>::STAGES * 2 * TC_BM * TC_ROWB + 1024 <= TC_SMEM_LIMIT + 1024, "smem");
 
 }  // namespace qx

@@ -332,7 +332,9 @@ class Group:
         return self.graph
 
     def replay(self):
-        self.graph.replay()
+        # a CUDA graph replays into the current stream: make it the members' stream
+        with self.torch.cuda.stream(self.members[0].stream):
+            self.graph.replay()
 
     def amplitudes(self):
         out = []

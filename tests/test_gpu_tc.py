@@ -69,3 +69,17 @@ def test_forms_on_large_workload_32_slices(qx, precision):
     got, n_tc = _tc_launches(qx, c, lambda: c.contract_slices(w.bitstrings, 0, 32)[0])
     assert n_tc > 0
     assert rel_l2(got, ref) <= TOL_C64
+
+
+def test_fp16_scaled_form_runs_on_tensor_cores_and_reports_its_error(qx, capsys):
+    """FP16 with per-tensor power-of-two scales: its error is reported, not held to 1e-5."""
+    w = W.sliced()
+    ref = oracle.sv_amplitudes(w.n_qubits, w.gates, w.open_mask, w.bitstrings)
+    c = qx.Contractor(w.n_qubits, w.gates, w.open_mask, w.order, w.sliced, len(w.bitstrings),
+                      precision=qx.QX_PREC_FP16_SCALED)
+    got, n_tc = _tc_launches(qx, c, lambda: c.contract(w.bitstrings))
+    err = rel_l2(got, ref)
+    with capsys.disabled():
+        print(f"\nFP16-scaled relative l2 error on the 4x5 depth-12 workload: {err:.3e}")
+    assert n_tc > 0
+    assert err < 2e-2  # ~2^-11 per element over a few tensor-core steps; a sanity bound only
