@@ -201,9 +201,81 @@ __global__ void __launch_bounds__(256) k_small(const SmallDesc d, const ItemCtx 
     }
 }
 
+// Flat variant for small per-pair tensors (2^mb < 256): one thread per
+// (pair, m) across the whole batch, the small operand read through L1 with
+// per-pair offsets (its few entries are shared by the threads of a pair).
+template <int KB, int NB>
+__global__ void __launch_bounds__(256) k_small_flat(const SmallDesc d, const ItemCtx ic, float2* __restrict__ out,
+                                                    int64_t out_is, int64_t n_items) {
+    __shared__ int64_t yrel[(1 << KB) << NB];
+    __shared__ int64_t kofs[1 << KB];
+    if (threadIdx.x < ((1 << KB) << NB)) {
+        const int kk = threadIdx.x >> NB, n = threadIdx.x & ((1 << NB) - 1);
+        int64_t a = 0;
+        for (int i = 0; i < KB; ++i)
+            if ((kk >> i) & 1) a += (int64_t)1 << d.yk_pos[i];
+        for (int i = 0; i < NB; ++i)
+            if ((n >> i) & 1) a += (int64_t)1 << d.yn_pos[i];
+        yrel[threadIdx.x] = a;
+    }
+    if (threadIdx.x < (1 << KB)) {
+        int64_t a = 0;
+        for (int i = 0; i < KB; ++i)
+            if ((threadIdx.x >> i) & 1) a += (int64_t)1 << d.xk_pos[i];
+        kofs[threadIdx.x] = a;
+    }
+    __syncthreads();
+    const int64_t total = n_items << d.mb;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t item = t >> d.mb, m = t & (((int64_t)1 << d.mb) - 1);
+        int64_t xa = m;
+        for (int h = 0; h < d.n_holes; ++h) {
+            const int p = d.holes[h];
+            xa = ((xa >> p) << (p + 1)) | (xa & (((int64_t)1 << p) - 1));
+        }
+        const float2* __restrict__ xp = d.x.base + fix_offset(d.x, ic, item) + xa;
+        const float2* __restrict__ yp = d.y.base + fix_offset(d.y, ic, item);
+        float2 a[1 << KB];
+#pragma unroll
+        for (int kk = 0; kk < (1 << KB); ++kk) a[kk] = xp[kofs[kk]];
+        float2* __restrict__ cp = out + item * out_is + (m << NB);
+#pragma unroll
+        for (int n = 0; n < (1 << NB); ++n) {
+            float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int kk = 0; kk < (1 << KB); ++kk) cfma(acc, a[kk], __ldg(yp + yrel[(kk << NB) + n]));
+            cp[n] = acc;
+        }
+    }
+}
+
+template <int KB>
+static cudaError_t small_flat_nb(const SmallDesc& d, const ItemCtx& ic, int64_t n_items, float2* out, int64_t out_is,
+                                 cudaStream_t st, unsigned grid) {
+    switch (d.nb) {
+        case 0: k_small_flat<KB, 0><<<grid, 256, 0, st>>>(d, ic, out, out_is, n_items); break;
+        case 1: k_small_flat<KB, 1><<<grid, 256, 0, st>>>(d, ic, out, out_is, n_items); break;
+        case 2: k_small_flat<KB, 2><<<grid, 256, 0, st>>>(d, ic, out, out_is, n_items); break;
+        default: k_small_flat<KB, 3><<<grid, 256, 0, st>>>(d, ic, out, out_is, n_items); break;
+    }
+    return cudaGetLastError();
+}
+
+static int sm_count();
+
 cudaError_t launch_small(const SmallDesc& d, const ItemCtx& ic, int64_t n_items, float2* out, int64_t out_is,
                          cudaStream_t st) {
     if (n_items <= 0) return cudaSuccess;
+    if (d.mb < 8 && d.kb <= 3 && d.nb <= 3) {
+        const int64_t total = n_items << d.mb;
+        const unsigned grid = (unsigned)std::min<int64_t>((total + 255) / 256, (int64_t)sm_count() * 16);
+        switch (d.kb) {
+            case 0: return small_flat_nb<0>(d, ic, n_items, out, out_is, st, grid);
+            case 1: return small_flat_nb<1>(d, ic, n_items, out, out_is, st, grid);
+            case 2: return small_flat_nb<2>(d, ic, n_items, out, out_is, st, grid);
+            default: return small_flat_nb<3>(d, ic, n_items, out, out_is, st, grid);
+        }
+    }
     const int64_t m = (int64_t)1 << d.mb;
     dim3 grid((unsigned)((m + 255) / 256), (unsigned)n_items);
     const int threads = m < 256 ? (int)((m + 31) / 32 * 32) : 256;
@@ -235,13 +307,14 @@ constexpr int GBK = 16;
 constexpr int GFOLD = 4;  // stages per partial
 
 template <int BM, int BN>
-__global__ void __launch_bounds__(256) k_gemm_c64(const float2* __restrict__ A, int64_t a_is, bool akm,
+__global__ void __launch_bounds__(256, (BM * BN >= 8192 ? 1 : 2)) k_gemm_c64(const float2* __restrict__ A, int64_t a_is, bool akm,
                                                   const float2* __restrict__ B, int64_t b_is, bool bkm,
                                                   float2* __restrict__ C, int64_t c_is, int mb, int nb, int kb,
                                                   int tiles_n) {
     constexpr int TM = BM / 16, TN = BN / 16, LA = BM * GBK / 256, LB = BN * GBK / 256;
-    __shared__ float2 As[2][GBK][BM + 1];
-    __shared__ float2 Bs[2][GBK][BN + 1];
+    extern __shared__ float2 gsm[];  // As[2][GBK][BM + 1], then Bs[2][GBK][BN + 1]
+    float2(*As)[GBK][BM + 1] = (float2(*)[GBK][BM + 1])gsm;
+    float2(*Bs)[GBK][BN + 1] = (float2(*)[GBK][BN + 1])(gsm + 2 * GBK * (BM + 1));
     const int64_t M = (int64_t)1 << mb, N = (int64_t)1 << nb, K = (int64_t)1 << kb;
     const int64_t item = blockIdx.y;
     const int64_t m0 = (int64_t)(blockIdx.x / tiles_n) * BM;
@@ -386,7 +459,15 @@ __global__ void __launch_bounds__(256) k_dot_c64(const float2* __restrict__ A, i
 template <int BM, int BN>
 static void gemm_tile(dim3 grid, cudaStream_t st, const float2* a, int64_t a_is, bool akm, const float2* b,
                       int64_t b_is, bool bkm, float2* c, int64_t c_is, int mb, int nb, int kb, int tn) {
-    k_gemm_c64<BM, BN><<<grid, 256, 0, st>>>(a, a_is, akm, b, b_is, bkm, c, c_is, mb, nb, kb, tn);
+    constexpr int smem = 2 * GBK * (BM + 1 + BN + 1) * (int)sizeof(float2);
+    if (smem > 48 * 1024) {
+        static int done = 0;  // opt in to more than 48 KB of dynamic shared memory (once)
+        if (!done) {
+            cudaFuncSetAttribute(k_gemm_c64<BM, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            done = 1;
+        }
+    }
+    k_gemm_c64<BM, BN><<<grid, 256, smem, st>>>(a, a_is, akm, b, b_is, bkm, c, c_is, mb, nb, kb, tn);
 }
 
 cudaError_t launch_gemm_c64(const float2* a, int64_t a_is, bool a_kmajor, const float2* b, int64_t b_is,
@@ -407,7 +488,7 @@ cudaError_t launch_gemm_c64(const float2* a, int64_t a_is, bool a_kmajor, const 
 #undef QX_DOT_CASE
         return cudaErrorInvalidValue;
     }
-    const int bmb = mb >= 6 ? 6 : mb >= 5 ? 5 : 4;  // tile edge 64 / 32 / 16 complex
+    const int bmb = mb >= 7 && nb >= 6 ? 7 : mb >= 6 ? 6 : mb >= 5 ? 5 : 4;  // tile edge 128 / 64 / 32 / 16
     const int bnb = nb >= 6 ? 6 : nb >= 5 ? 5 : 4;
     const int64_t tm = ((1ll << mb) + (1 << bmb) - 1) >> bmb, tn = ((1ll << nb) + (1 << bnb) - 1) >> bnb;
     dim3 grid((unsigned)(tm * tn), (unsigned)n_items);
@@ -417,6 +498,7 @@ cudaError_t launch_gemm_c64(const float2* a, int64_t a_is, bool a_kmajor, const 
                                       (int)tn);                                                       \
         return cudaGetLastError();                                                                    \
     }
+    QX_GEMM_CASE(7, 6)
     QX_GEMM_CASE(6, 6) QX_GEMM_CASE(6, 5) QX_GEMM_CASE(6, 4)
     QX_GEMM_CASE(5, 6) QX_GEMM_CASE(5, 5) QX_GEMM_CASE(5, 4)
     QX_GEMM_CASE(4, 6) QX_GEMM_CASE(4, 5) QX_GEMM_CASE(4, 4)
