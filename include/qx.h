@@ -152,6 +152,14 @@ int qx_contract_slices(qx_handle h, const uint8_t* bitstrings, int64_t n_bits, i
 int qx_contract_slices_device(qx_handle h, const uint8_t* d_bitstrings, int64_t n_bits, int64_t s_begin,
                               int64_t s_end, double* d_amps_out);
 
+/* Graph replay (on by default): a call of qx_contract / qx_contract_device /
+ * qx_contract_slices[_device] that repeats the previous call's device
+ * buffers, bitstring count and slice range is captured once as a CUDA graph
+ * and replayed afterwards (the contents of the buffers may change; the
+ * pointers and sizes may not).  Not used on the legacy default stream or
+ * while profiling.  enable = 0 turns it off and drops the captured graph. */
+int qx_set_graphs(qx_handle h, int enable);
+
 /* Statistics of the last contraction (host values, any pointer may be NULL):
  * algorithmic complex flops (8 M K N per step, per pair), kernel launches,
  * batches. */

@@ -135,6 +135,18 @@ struct qx_ctx {
     double last_flops = 0;
     int64_t last_launches = 0, last_batches = 0;
 
+    // CUDA graph of a repeated contraction (same buffers, sizes and slice range)
+    bool graphs = true;
+    struct {
+        const uint8_t* bits = nullptr;
+        double* amps = nullptr;
+        int64_t n_bits = -1, s0 = -1, s1 = -1;
+        int seen = 0;
+        cudaGraphExec_t exec = nullptr;
+        double flops = 0;
+        int64_t launches = 0, batches = 0;
+    } gc;
+
     // profiling: an event pair around every launch, folded per kernel kind on read
     bool profiling = false;
     std::vector<cudaEvent_t> ev_pool;
@@ -146,6 +158,15 @@ struct qx_ctx {
 };
 
 static int fail(qx_ctx* h, int code, const char* fmt, ...);
+static void drop_graph(qx_ctx* h) {
+    if (h->gc.exec) cudaGraphExecDestroy(h->gc.exec);
+    h->gc.exec = nullptr;
+    h->gc.seen = 0;
+    h->gc.bits = nullptr;
+    h->gc.amps = nullptr;
+    h->gc.n_bits = h->gc.s0 = h->gc.s1 = -1;
+}
+
 
 static cudaError_t prof_begin(qx_ctx* h, int kind, double flops, double bytes, size_t* slot) {
     *slot = SIZE_MAX;
@@ -515,6 +536,12 @@ static int compile_plan(qx_ctx* h, const int64_t* order, int64_t n_steps, const 
                 if (std::find(shared.begin(), shared.end(), e) != shared.end()) sB.push_back(e);
             if (sB != shared) cands.push_back(sB);
         }
+        // The direct 3xTF32 kernel splits operands in shared memory and reads them K-major through TMA;
+        // the prep-based kernel streams pre-split parts (about (40 M + 72 N) K extra bytes) but leaves
+        // shared-memory bandwidth to the MMAs.  Measured on GB300: direct wins for the short products of
+        // small per-pair tensors (M or N <= 256), the prep-based kernel for large tensors.
+        const bool direct = tc_form == TC_FORM_3XTF32 && (int)fA.size() >= 7 && (int)fB.size() >= 6 && kb >= 4 &&
+                            ((int)fA.size() <= 8 || (int)fB.size() <= 8);
         Choice best{};
         best.cost = -1;
         for (auto& S : cands) {
@@ -528,6 +555,8 @@ static int compile_plan(qx_ctx* h, const int64_t* order, int64_t n_steps, const 
             else if (contiguous_is(GA, am)) { c.pa = false; c.akm = false; }
             if (contiguous_is(GB, bk)) { c.pb = false; c.bkm = true; }
             else if (contiguous_is(GB, bm)) { c.pb = false; c.bkm = false; }
+            if (direct && !c.akm) c.pa = c.akm = true;
+            if (direct && !c.bkm) c.pb = c.bkm = true;
             c.cost = (c.pa ? (double)node_entries(GA) : 0.0) + (c.pb ? (double)node_entries(GB) : 0.0);
             if (best.cost < 0 || c.cost < best.cost) best = c;
         }
@@ -570,7 +599,9 @@ static int compile_plan(qx_ctx* h, const int64_t* order, int64_t n_steps, const 
         cl.insert(cl.end(), fB.begin(), fB.end());
         const int st = new_storage(h, (int64_t)1 << cl.size(), variant, t);
         g.dst = st;
-        if (tc_form && g.mb >= 7 && g.nb >= 6 && g.kb >= 5) {
+        if (direct) {
+            g.tc = TC_FORM_3XTF32_DIRECT;
+        } else if (tc_form && g.mb >= 7 && g.nb >= 6 && g.kb >= 5) {
             // split real parts of A [M][2K] and of the expanded B' [2N][2K], live for this step only
             const int eb = tc_elem_bytes(tc_form);
             const int64_t mk = (int64_t)1 << (g.mb + g.kb), nk = (int64_t)1 << (g.nb + g.kb);
@@ -857,16 +888,18 @@ static int run_op(qx_ctx* h, const Op& op, const ItemCtx& ic, int64_t n_items) {
     float2* dp;
     int64_t dis;
     storage_addr(h, op.dst, &dp, &dis);
+    const bool direct = op.tc == TC_FORM_3XTF32_DIRECT, prep = op.tc && !direct;
     const int kind = op.type == OP_PERM    ? QX_KERNEL_PERMUTE
                      : op.type == OP_SMALL ? QX_KERNEL_SMALL
-                     : op.tc               ? QX_KERNEL_TC_PREP
+                     : direct              ? QX_KERNEL_TC_GEMM
+                     : prep                ? QX_KERNEL_TC_PREP
                                            : QX_KERNEL_GEMM;
     size_t slot;
-    const double prep_bytes = op.tc ? 8.0 * (double)(h->stor[op.sa].entries + h->stor[op.sb].entries +
-                                                     h->stor[op.spa].entries + h->stor[op.spb].entries)
-                                    : 0.0;
-    cudaError_t e = prof_begin(h, kind, op.tc ? 0.0 : op.flops * (double)n_items,
-                               (op.tc ? prep_bytes : op_bytes(h, op)) * (double)n_items, &slot);
+    const double prep_bytes = prep ? 8.0 * (double)(h->stor[op.sa].entries + h->stor[op.sb].entries +
+                                                    h->stor[op.spa].entries + h->stor[op.spb].entries)
+                                   : 0.0;
+    cudaError_t e = prof_begin(h, kind, prep ? 0.0 : op.flops * (double)n_items,
+                               (prep ? prep_bytes : op_bytes(h, op)) * (double)n_items, &slot);
     if (e != cudaSuccess) return fail(h, QX_ECUDA, "profiling event: %s", cudaGetErrorString(e));
     if (op.type == OP_PERM) {
         e = launch_permute(perm_desc(h, op), ic, n_items, dp, dis, h->stream);
@@ -878,6 +911,27 @@ static int run_op(qx_ctx* h, const Op& op, const ItemCtx& ic, int64_t n_items) {
         storage_addr(h, op.sa, &ap, &ais);
         storage_addr(h, op.sb, &bp, &bis);
         e = launch_gemm_c64(ap, ais, op.a_km, bp, bis, op.b_km, dp, dis, op.mb, op.nb, op.kb, n_items, h->stream);
+    } else if (op.tc == TC_FORM_3XTF32_DIRECT) {
+        TcArgs g{};
+        float2 *ap, *bp;
+        int64_t ais, bis;
+        storage_addr(h, op.sa, &ap, &ais);
+        storage_addr(h, op.sb, &bp, &bis);
+        g.a = ap;
+        g.a_is = ais;
+        g.a_kmajor = op.a_km;
+        g.b = bp;
+        g.b_is = bis;
+        g.b_kmajor = op.b_km;
+        g.c = dp;
+        g.c_is = dis;
+        g.mb = op.mb;
+        g.nb = op.nb;
+        g.kb = op.kb;
+        g.n_items = n_items;
+        g.limit = h->opt.timeout_cycles > 0 ? h->opt.timeout_cycles : 2000000000ll;
+        g.err = (int*)(h->ws + h->off_err);
+        e = launch_tc2_gemm(g, h->stream);
     } else {
         TcArgs g{};
         float2 *ap, *bp, *pa, *pb;
@@ -1092,6 +1146,56 @@ static int contract_impl(qx_ctx* h, const uint8_t* d_bits, int64_t n_bits, int64
     return QX_OK;
 }
 
+// Repeated calls with the same buffers, sizes and slice range replay a CUDA graph of the whole
+// contraction (hundreds of short launches become one graph launch).  The first such call runs
+// eagerly (it also uploads tensors and programs), the second captures and launches the graph.
+static int contract_graph(qx_ctx* h, const uint8_t* d_bits, int64_t n_bits, int64_t s0, int64_t s1, double* d_amps) {
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (h->stream) CUDA_TRY(h, cudaStreamIsCapturing(h->stream, &cap));
+    // the caller may be capturing this stream into a graph of its own: then just enqueue
+    const bool usable = h->graphs && !h->profiling && h->stream != nullptr && cap == cudaStreamCaptureStatusNone;
+    if (!usable) return contract_impl(h, d_bits, n_bits, s0, s1, d_amps);
+    const bool same = h->gc.bits == d_bits && h->gc.amps == d_amps && h->gc.n_bits == n_bits && h->gc.s0 == s0 &&
+                      h->gc.s1 == s1;
+    if (same && h->gc.exec) {
+        CUDA_TRY(h, cudaGraphLaunch(h->gc.exec, h->stream));
+        h->last_flops = h->gc.flops;
+        h->last_launches = h->gc.launches;
+        h->last_batches = h->gc.batches;
+        return QX_OK;
+    }
+    if (!same) {
+        drop_graph(h);
+        h->gc.bits = d_bits;
+        h->gc.amps = d_amps;
+        h->gc.n_bits = n_bits;
+        h->gc.s0 = s0;
+        h->gc.s1 = s1;
+        return contract_impl(h, d_bits, n_bits, s0, s1, d_amps);
+    }
+    cudaGraph_t graph = nullptr;
+    CUDA_TRY(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+    int rc = contract_impl(h, d_bits, n_bits, s0, s1, d_amps);
+    cudaError_t e = cudaStreamEndCapture(h->stream, &graph);
+    if (rc) {
+        if (graph) cudaGraphDestroy(graph);
+        h->graphs = false;  // this plan needs host work inside a contraction: stay eager
+        return rc;
+    }
+    if (e != cudaSuccess) return fail(h, QX_ECUDA, "graph capture: %s", cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&h->gc.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        h->gc.exec = nullptr;
+        return fail(h, QX_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+    }
+    h->gc.flops = h->last_flops;
+    h->gc.launches = h->last_launches;
+    h->gc.batches = h->last_batches;
+    CUDA_TRY(h, cudaGraphLaunch(h->gc.exec, h->stream));
+    return QX_OK;
+}
+
 // ------------------------------------------------------------------------------------------------
 // C ABI
 // ------------------------------------------------------------------------------------------------
@@ -1125,6 +1229,7 @@ int qx_create(qx_handle* out, int device, void* stream, const qx_options* opt) {
 
 void qx_destroy(qx_handle h) {
     if (!h) return;
+    drop_graph(h);
     for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
     if (h->ws_owned && h->ws) {
         cudaSetDevice(h->device);
@@ -1162,6 +1267,7 @@ int qx_network_info(qx_handle h, int64_t* n_tensors, int64_t* n_bonds) {
 }
 
 static void unbind(qx_ctx* h) {
+    drop_graph(h);
     if (h->ws_owned && h->ws) {
         cudaSetDevice(h->device);
         cudaFree(h->ws);
@@ -1258,7 +1364,7 @@ int qx_contract_slices(qx_handle h, const uint8_t* bits, int64_t n_bits, int64_t
     uint8_t* d_bits = (uint8_t*)(h->ws + h->off_bits);
     double* d_amps = (double*)(h->ws + h->off_amps);
     CUDA_TRY(h, cudaMemcpyAsync(d_bits, bits, (size_t)(n_bits * h->nq), cudaMemcpyHostToDevice, h->stream));
-    rc = contract_impl(h, d_bits, n_bits, s_begin, s_end, d_amps);
+    rc = contract_graph(h, d_bits, n_bits, s_begin, s_end, d_amps);
     if (rc) return rc;
     const size_t out_bytes = (size_t)((n_bits << n_open(h)) * 16);
     CUDA_TRY(h, cudaMemcpyAsync(amps_out, d_amps, out_bytes, cudaMemcpyDeviceToHost, h->stream));
@@ -1280,12 +1386,19 @@ int qx_contract_slices_device(qx_handle h, const uint8_t* d_bits, int64_t n_bits
     if (rc) return rc;
     if (!d_bits || !d_amps) return fail(h, QX_EINVAL, "null buffer");
     CUDA_TRY(h, cudaSetDevice(h->device));
-    return contract_impl(h, d_bits, n_bits, s_begin, s_end, d_amps);
+    return contract_graph(h, d_bits, n_bits, s_begin, s_end, d_amps);
 }
 
 int qx_contract_device(qx_handle h, const uint8_t* d_bits, int64_t n_bits, double* d_amps) {
     if (!h) return QX_EINVAL;
     return qx_contract_slices_device(h, d_bits, n_bits, 0, h->n_slices, d_amps);
+}
+
+int qx_set_graphs(qx_handle h, int enable) {
+    if (!h) return QX_EINVAL;
+    drop_graph(h);
+    h->graphs = enable != 0;
+    return QX_OK;
 }
 
 int qx_set_profiling(qx_handle h, int enable) {

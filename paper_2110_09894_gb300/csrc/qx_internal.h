@@ -166,6 +166,7 @@ cudaError_t launch_single_sum(const GSum& g, int64_t total, cudaStream_t st);
 // per item, [R][K] (kmajor) or [K][R]; pa / pb receive the split real parts
 // (prep), then the tcgen05 kernel writes C [M][N] complex64.
 constexpr int TC_FORM_3XTF32 = 1, TC_FORM_BF16X3 = 2, TC_FORM_FP16 = 3;
+constexpr int TC_FORM_3XTF32_DIRECT = 4;  // 3xTF32 split in shared memory (launch_tc2_gemm)
 struct TcArgs {
     const float2* a;
     int64_t a_is;
@@ -191,6 +192,8 @@ int tc_elem_bytes(int form);
 int tc_products(int form);
 cudaError_t launch_tc_prep(int form, const TcArgs& g, cudaStream_t st);
 cudaError_t launch_tc_gemm(int form, const TcArgs& g, cudaStream_t st);
+// 3xTF32 directly on the complex64 operands (split in shared memory; no pa / pb)
+cudaError_t launch_tc2_gemm(const TcArgs& g, cudaStream_t st);
 // amps[i] = (sum + compensation) * (scale_re + i scale_im), all in FP64
 cudaError_t launch_finalize(const double* acc, double* amps, int64_t n, double scale_re, double scale_im,
                             cudaStream_t st);

@@ -159,7 +159,7 @@ cudaError_t launch_permute(const PermDesc& d, const ItemCtx& ic, int64_t n_items
 template <int KB>
 __global__ void __launch_bounds__(256) k_small(const SmallDesc d, const ItemCtx ic, float2* __restrict__ out,
                                                int64_t out_is) {
-    __shared__ float2 ys[1 << (kSmallMaxK + kSmallMaxN)];
+    extern __shared__ float2 ys[];  // the small operand (2^(kb + nb) entries), then the output stage
     __shared__ int64_t kofs[1 << kSmallMaxK];
     const int64_t item = blockIdx.y;
     const int nb = d.nb;
@@ -181,70 +181,105 @@ __global__ void __launch_bounds__(256) k_small(const SmallDesc d, const ItemCtx 
         kofs[threadIdx.x] = a;
     }
     __syncthreads();
+    const int64_t M = (int64_t)1 << d.mb;
     const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (m >= ((int64_t)1 << d.mb)) return;
-    int64_t xa = m;
-    for (int h = 0; h < d.n_holes; ++h) {
-        const int p = d.holes[h];
-        xa = ((xa >> p) << (p + 1)) | (xa & (((int64_t)1 << p) - 1));
-    }
-    const float2* __restrict__ xp = d.x.base + fix_offset(d.x, ic, item) + xa;
-    float2 a[1 << KB];
-#pragma unroll
-    for (int kk = 0; kk < (1 << KB); ++kk) a[kk] = xp[kofs[kk]];
-    float2* __restrict__ cp = out + item * out_is + (m << nb);
-    for (int n = 0; n < nn; ++n) {
-        float2 acc = make_float2(0.f, 0.f);
-#pragma unroll
-        for (int kk = 0; kk < (1 << KB); ++kk) cfma(acc, a[kk], ys[kk * nn + n]);
-        cp[n] = acc;
-    }
-}
-
-// Flat variant for small per-pair tensors (2^mb < 256): one thread per
-// (pair, m) across the whole batch, the small operand read through L1 with
-// per-pair offsets (its few entries are shared by the threads of a pair).
-template <int KB, int NB>
-__global__ void __launch_bounds__(256) k_small_flat(const SmallDesc d, const ItemCtx ic, float2* __restrict__ out,
-                                                    int64_t out_is, int64_t n_items) {
-    __shared__ int64_t yrel[(1 << KB) << NB];
-    __shared__ int64_t kofs[1 << KB];
-    if (threadIdx.x < ((1 << KB) << NB)) {
-        const int kk = threadIdx.x >> NB, n = threadIdx.x & ((1 << NB) - 1);
-        int64_t a = 0;
-        for (int i = 0; i < KB; ++i)
-            if ((kk >> i) & 1) a += (int64_t)1 << d.yk_pos[i];
-        for (int i = 0; i < NB; ++i)
-            if ((n >> i) & 1) a += (int64_t)1 << d.yn_pos[i];
-        yrel[threadIdx.x] = a;
-    }
-    if (threadIdx.x < (1 << KB)) {
-        int64_t a = 0;
-        for (int i = 0; i < KB; ++i)
-            if ((threadIdx.x >> i) & 1) a += (int64_t)1 << d.xk_pos[i];
-        kofs[threadIdx.x] = a;
-    }
-    __syncthreads();
-    const int64_t total = n_items << d.mb;
-    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t item = t >> d.mb, m = t & (((int64_t)1 << d.mb) - 1);
+    // outputs of the CTA's rows form one block: stage them (row stride nn + 1) and store coalesced
+    float2* stage = ys + (1 << (kSmallMaxK + kSmallMaxN));
+    const bool staged = nb <= 4 && blockDim.x == 256;
+    if (m < M) {
         int64_t xa = m;
         for (int h = 0; h < d.n_holes; ++h) {
             const int p = d.holes[h];
             xa = ((xa >> p) << (p + 1)) | (xa & (((int64_t)1 << p) - 1));
         }
         const float2* __restrict__ xp = d.x.base + fix_offset(d.x, ic, item) + xa;
-        const float2* __restrict__ yp = d.y.base + fix_offset(d.y, ic, item);
         float2 a[1 << KB];
 #pragma unroll
         for (int kk = 0; kk < (1 << KB); ++kk) a[kk] = xp[kofs[kk]];
-        float2* __restrict__ cp = out + item * out_is + (m << NB);
-#pragma unroll
-        for (int n = 0; n < (1 << NB); ++n) {
+        float2* __restrict__ cp = out + item * out_is + (m << nb);
+        for (int n = 0; n < nn; ++n) {
             float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
-            for (int kk = 0; kk < (1 << KB); ++kk) cfma(acc, a[kk], __ldg(yp + yrel[(kk << NB) + n]));
-            cp[n] = acc;
+            for (int kk = 0; kk < (1 << KB); ++kk) cfma(acc, a[kk], ys[kk * nn + n]);
+            if (staged) stage[threadIdx.x * (nn + 1) + n] = acc;
+            else cp[n] = acc;
+        }
+    }
+    if (!staged) return;
+    __syncthreads();
+    const int64_t r0 = (int64_t)blockIdx.x * blockDim.x;
+    const int64_t cnt = (M - r0 < 256 ? M - r0 : 256) * nn;
+    float2* __restrict__ dst = out + item * out_is + (r0 << nb);
+    for (int i = threadIdx.x; i < cnt; i += 256) dst[i] = stage[(i >> nb) * (nn + 1) + (i & (nn - 1))];
+}
+
+// Flat variant for small per-pair tensors (2^mb < 256): one thread per
+// (pair, m) across the whole batch, the small operand read through L1 with
+// per-pair offsets (its entries are shared by the threads of a pair).  The
+// 256 threads of a CTA own 256 consecutive (pair, m), whose outputs form one
+// contiguous block: they are staged in shared memory (row stride 2^NB + 1
+// against bank conflicts) and stored coalesced.
+template <int KB, int NB>
+__global__ void __launch_bounds__(256) k_small_flat(const SmallDesc d, const ItemCtx ic, float2* __restrict__ out,
+                                                    int64_t out_is, int64_t n_items) {
+    constexpr int NN = 1 << NB, STAGE = NB <= 4;
+    __shared__ int64_t yrel[(1 << KB) << NB];
+    __shared__ int64_t kofs[1 << KB];
+    __shared__ float2 stage[STAGE ? 256 * (NN + 1) : 1];
+    for (int i = threadIdx.x; i < ((1 << KB) << NB); i += blockDim.x) {
+        const int kk = i >> NB, n = i & (NN - 1);
+        int64_t a = 0;
+        for (int b = 0; b < KB; ++b)
+            if ((kk >> b) & 1) a += (int64_t)1 << d.yk_pos[b];
+        for (int b = 0; b < NB; ++b)
+            if ((n >> b) & 1) a += (int64_t)1 << d.yn_pos[b];
+        yrel[i] = a;
+    }
+    if (threadIdx.x < (1 << KB)) {
+        int64_t a = 0;
+        for (int b = 0; b < KB; ++b)
+            if ((threadIdx.x >> b) & 1) a += (int64_t)1 << d.xk_pos[b];
+        kofs[threadIdx.x] = a;
+    }
+    __syncthreads();
+    const int64_t total = n_items << d.mb;
+    for (int64_t t0 = (int64_t)blockIdx.x * 256; t0 < total; t0 += (int64_t)gridDim.x * 256) {
+        const int64_t t = t0 + threadIdx.x;
+        float2 res[NN];
+        if (t < total) {
+            const int64_t item = t >> d.mb, m = t & (((int64_t)1 << d.mb) - 1);
+            int64_t xa = m;
+            for (int h = 0; h < d.n_holes; ++h) {
+                const int p = d.holes[h];
+                xa = ((xa >> p) << (p + 1)) | (xa & (((int64_t)1 << p) - 1));
+            }
+            const float2* __restrict__ xp = d.x.base + fix_offset(d.x, ic, item) + xa;
+            const float2* __restrict__ yp = d.y.base + fix_offset(d.y, ic, item);
+            float2 a[1 << KB];
+#pragma unroll
+            for (int kk = 0; kk < (1 << KB); ++kk) a[kk] = xp[kofs[kk]];
+#pragma unroll
+            for (int n = 0; n < NN; ++n) {
+                float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int kk = 0; kk < (1 << KB); ++kk) cfma(acc, a[kk], __ldg(yp + yrel[(kk << NB) + n]));
+                res[n] = acc;
+            }
+            if (!STAGE) {
+                float2* __restrict__ cp = out + item * out_is + (m << NB);
+#pragma unroll
+                for (int n = 0; n < NN; ++n) cp[n] = res[n];
+            }
+        }
+        if (STAGE) {
+            // outputs of (pair, m) = t sit at t * NN (out_is = 2^(mb + NB)): one block per CTA
+#pragma unroll
+            for (int n = 0; n < NN; ++n) stage[threadIdx.x * (NN + 1) + n] = res[n];
+            __syncthreads();
+            const int64_t cnt = (total - t0 < 256 ? total - t0 : 256) * NN;
+            float2* __restrict__ dst = out + t0 * NN;
+            for (int i = threadIdx.x; i < cnt; i += 256) dst[i] = stage[(i / NN) * (NN + 1) + (i % NN)];
+            __syncthreads();
         }
     }
 }
@@ -256,7 +291,9 @@ static cudaError_t small_flat_nb(const SmallDesc& d, const ItemCtx& ic, int64_t 
         case 0: k_small_flat<KB, 0><<<grid, 256, 0, st>>>(d, ic, out, out_is, n_items); break;
         case 1: k_small_flat<KB, 1><<<grid, 256, 0, st>>>(d, ic, out, out_is, n_items); break;
         case 2: k_small_flat<KB, 2><<<grid, 256, 0, st>>>(d, ic, out, out_is, n_items); break;
-        default: k_small_flat<KB, 3><<<grid, 256, 0, st>>>(d, ic, out, out_is, n_items); break;
+        case 3: k_small_flat<KB, 3><<<grid, 256, 0, st>>>(d, ic, out, out_is, n_items); break;
+        case 4: k_small_flat<KB, 4><<<grid, 256, 0, st>>>(d, ic, out, out_is, n_items); break;
+        default: k_small_flat<KB, 5><<<grid, 256, 0, st>>>(d, ic, out, out_is, n_items); break;
     }
     return cudaGetLastError();
 }
@@ -266,26 +303,29 @@ static int sm_count();
 cudaError_t launch_small(const SmallDesc& d, const ItemCtx& ic, int64_t n_items, float2* out, int64_t out_is,
                          cudaStream_t st) {
     if (n_items <= 0) return cudaSuccess;
-    if (d.mb < 8 && d.kb <= 3 && d.nb <= 3) {
+    if (d.mb < 8) {  // flat: short per-pair rows
         const int64_t total = n_items << d.mb;
         const unsigned grid = (unsigned)std::min<int64_t>((total + 255) / 256, (int64_t)sm_count() * 16);
         switch (d.kb) {
             case 0: return small_flat_nb<0>(d, ic, n_items, out, out_is, st, grid);
             case 1: return small_flat_nb<1>(d, ic, n_items, out, out_is, st, grid);
             case 2: return small_flat_nb<2>(d, ic, n_items, out, out_is, st, grid);
-            default: return small_flat_nb<3>(d, ic, n_items, out, out_is, st, grid);
+            case 3: return small_flat_nb<3>(d, ic, n_items, out, out_is, st, grid);
+            case 4: return small_flat_nb<4>(d, ic, n_items, out, out_is, st, grid);
+            default: return small_flat_nb<5>(d, ic, n_items, out, out_is, st, grid);
         }
     }
     const int64_t m = (int64_t)1 << d.mb;
     dim3 grid((unsigned)((m + 255) / 256), (unsigned)n_items);
     const int threads = m < 256 ? (int)((m + 31) / 32 * 32) : 256;
+    const size_t smem = sizeof(float2) * ((1 << (kSmallMaxK + kSmallMaxN)) + (d.nb <= 4 ? 256 * ((1 << d.nb) + 1) : 0));
     switch (d.kb) {
-        case 0: k_small<0><<<grid, threads, 0, st>>>(d, ic, out, out_is); break;
-        case 1: k_small<1><<<grid, threads, 0, st>>>(d, ic, out, out_is); break;
-        case 2: k_small<2><<<grid, threads, 0, st>>>(d, ic, out, out_is); break;
-        case 3: k_small<3><<<grid, threads, 0, st>>>(d, ic, out, out_is); break;
-        case 4: k_small<4><<<grid, threads, 0, st>>>(d, ic, out, out_is); break;
-        case 5: k_small<5><<<grid, threads, 0, st>>>(d, ic, out, out_is); break;
+        case 0: k_small<0><<<grid, threads, smem, st>>>(d, ic, out, out_is); break;
+        case 1: k_small<1><<<grid, threads, smem, st>>>(d, ic, out, out_is); break;
+        case 2: k_small<2><<<grid, threads, smem, st>>>(d, ic, out, out_is); break;
+        case 3: k_small<3><<<grid, threads, smem, st>>>(d, ic, out, out_is); break;
+        case 4: k_small<4><<<grid, threads, smem, st>>>(d, ic, out, out_is); break;
+        case 5: k_small<5><<<grid, threads, smem, st>>>(d, ic, out, out_is); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

@@ -402,6 +402,229 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 }
 
 // ------------------------------------------------------------------------------------------------
+// 3xTF32 straight from the complex64 operands: TMA brings raw 128-byte K slabs
+// of A (128 rows) and of B (64 complex rows) into shared memory, where the
+// epilogue warps split A into hi (in place) and lo, and build both parts of the
+// expanded B' (rows 2n = (re, -im), 2n+1 = (im, re)) before the MMAs run.  An
+// elementwise map keeps the 128-byte swizzle, so A's parts sit at the same
+// offsets as the raw data; B' row r puts chunk j at (j ^ (r % 8)).  This
+// removes the separate split pass and its HBM traffic.
+// Warps: 0 TMA, 1 TMEM + MMA, 2..9 convert the next stage and drain TMEM
+// (warp w reads TMEM lanes 32 (w % 4), columns 64 ((w - 2) / 4) .. + 63).
+// ------------------------------------------------------------------------------------------------
+constexpr int TC2_THREADS = 320, TC2_STAGES = 3;
+constexpr uint32_t TC2_A = 16384, TC2_BRAW = 8192, TC2_STAGE = 4 * TC2_A + TC2_BRAW;  // raw/hi A, lo A, raw B, B'hi, B'lo
+constexpr uint32_t TC2_OFF_ALO = TC2_A, TC2_OFF_BRAW = 2 * TC2_A, TC2_OFF_BHI = 2 * TC2_A + TC2_BRAW,
+                   TC2_OFF_BLO = 3 * TC2_A + TC2_BRAW;
+
+__device__ __forceinline__ void split4(float4 v, float4& hi, float4& lo) {
+    hi = make_float4(tf32_rna(v.x), tf32_rna(v.y), tf32_rna(v.z), tf32_rna(v.w));
+    lo = make_float4(v.x - hi.x, v.y - hi.y, v.z - hi.z, v.w - hi.w);
+}
+
+// convert stage `st` (raw A, raw B landed) with the 256 converter threads ct = 0..255
+__device__ __forceinline__ void tc2_convert(uint8_t* st, int ct) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {  // A: 1024 float4, elementwise, same offsets
+        const int c = ct + 256 * i;
+        float4* a = (float4*)(st) + c;
+        float4 hi, lo;
+        split4(*a, hi, lo);
+        *a = hi;
+        ((float4*)(st + TC2_OFF_ALO))[c] = lo;
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {  // B: 64 rows x 8 chunks of 16 bytes
+        const int c = ct + 256 * i;
+        const int n = c >> 3, j = c & 7;
+        const float4 v = *(const float4*)(st + TC2_OFF_BRAW + n * 128 + ((j ^ (n & 7)) << 4));
+        const float4 r0 = make_float4(v.x, -v.y, v.z, -v.w);  // row 2n: re, -im
+        const float4 r1 = make_float4(v.y, v.x, v.w, v.z);    // row 2n+1: im, re
+        const int ra = 2 * n, rb = 2 * n + 1;
+        const uint32_t oa = ra * 128 + ((j ^ (ra & 7)) << 4), ob = rb * 128 + ((j ^ (rb & 7)) << 4);
+        float4 hi, lo;
+        split4(r0, hi, lo);
+        *(float4*)(st + TC2_OFF_BHI + oa) = hi;
+        *(float4*)(st + TC2_OFF_BLO + oa) = lo;
+        split4(r1, hi, lo);
+        *(float4*)(st + TC2_OFF_BHI + ob) = hi;
+        *(float4*)(st + TC2_OFF_BLO + ob) = lo;
+    }
+}
+
+__global__ void __launch_bounds__(TC2_THREADS, 1)
+    k_gemm_tc2(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
+               float* __restrict__ C, int64_t c_is, int M, int N2, int K2, int tiles_n, int tiles, int64_t n_items,
+               int a_bcast, int b_bcast, long long limit, int* err) {
+    // persistent over (pair, tile) jobs: job = blockIdx.x + t * gridDim.x; the
+    // k-stages of successive jobs form one sequence g = t * nk + it, so the
+    // pipeline stays full across tile boundaries
+    constexpr int BK = 32;  // TF32 elements per stage (one 128-byte slab)
+    constexpr uint32_t IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(TC_BN >> 3) << 17) |
+                               ((uint32_t)(TC_BM >> 4) << 24);
+    extern __shared__ uint8_t dyn[];
+    __shared__ uint64_t full[TC2_STAGES], conv[TC2_STAGES], empty[TC2_STAGES], tfull[2], tempty[2], drain;
+    __shared__ uint32_t tmem_slot;
+    __shared__ int abort_flag;
+    if (*(volatile const int*)err) return;
+    uint8_t* base = (uint8_t*)(((uintptr_t)dyn + 1023) & ~(uintptr_t)1023);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nk = K2 / BK;
+    const int64_t jobs = (int64_t)tiles * n_items;
+    const int64_t my_jobs = jobs > blockIdx.x ? (jobs - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    const int64_t total = my_jobs * nk;
+    auto job_of = [&](int64_t t, int64_t* item, int* m0, int* n0) {
+        const int64_t j = blockIdx.x + t * (int64_t)gridDim.x;
+        *item = j / tiles;
+        const int tile = (int)(j % tiles);
+        *m0 = (tile / tiles_n) * TC_BM;
+        *n0 = (tile % tiles_n) * TC_BN;  // row of B'; raw B row n0 / 2
+    };
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < TC2_STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&conv[s], 8);
+            mbar_init(&empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&tfull[b], 1);
+            mbar_init(&tempty[b], 8);
+        }
+        mbar_init(&drain, 1);
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(s_addr(&tmem_slot)),
+                     "r"(2 * TC_BN)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_slot;
+
+    if (warp == 0 && lane == 0) {
+        int64_t issued = 0;
+        for (int64_t g = 0; g < total; ++g) {
+            const int s = (int)(g % TC2_STAGES);
+            const int64_t n = g / TC2_STAGES;
+            if (!mbar_wait(&empty[s], (uint32_t)((n & 1) ^ 1), limit, err) || *(volatile int*)&abort_flag) {
+                atomicExch(&abort_flag, 1);
+                break;
+            }
+            int64_t item;
+            int m0, n0;
+            job_of(g / nk, &item, &m0, &n0);
+            const int it = (int)(g % nk);
+            mbar_expect_tx(&full[s], TC2_A + TC2_BRAW);
+            uint8_t* st = base + s * TC2_STAGE;
+            tma_load_3d(st, &mapA, it * BK, m0, a_bcast ? 0 : (int)item, &full[s]);
+            tma_load_3d(st + TC2_OFF_BRAW, &mapB, it * BK, n0 >> 1, b_bcast ? 0 : (int)item, &full[s]);
+            ++issued;
+        }
+        if (*(volatile int*)&abort_flag) {
+            for (int64_t g = (issued > TC2_STAGES ? issued - TC2_STAGES : 0); g < issued; ++g)
+                mbar_wait(&full[g % TC2_STAGES], (uint32_t)((g / TC2_STAGES) & 1), limit, err);
+        }
+    } else if (warp == 1 && lane == 0) {
+        bool ok = true;
+        for (int64_t g = 0; g < total && ok; ++g) {
+            const int s = (int)(g % TC2_STAGES);
+            const int64_t n = g / TC2_STAGES;
+            const int b = (int)(g & 1);
+            const int64_t u = g >> 1;
+            if (!mbar_wait(&conv[s], (uint32_t)(n & 1), limit, err) ||
+                (u > 0 && !mbar_wait(&tempty[b], (uint32_t)((u - 1) & 1), limit, err)) || *(volatile int*)&abort_flag) {
+                atomicExch(&abort_flag, 1);
+                ok = false;
+                break;
+            }
+            tc_fence_after();
+            const uint32_t st = s_addr(base + s * TC2_STAGE);
+            const uint32_t d = tmem + b * TC_BN;
+#pragma unroll
+            for (int kk = 0; kk < BK / 8; ++kk) {
+                const uint64_t ahi = sdesc(st + kk * 32), alo = sdesc(st + TC2_OFF_ALO + kk * 32);
+                const uint64_t bhi = sdesc(st + TC2_OFF_BHI + kk * 32), blo = sdesc(st + TC2_OFF_BLO + kk * 32);
+                mma<TC_FORM_3XTF32>(d, ahi, bhi, IDESC, kk != 0);
+                mma<TC_FORM_3XTF32>(d, ahi, blo, IDESC, 1);
+                mma<TC_FORM_3XTF32>(d, alo, bhi, IDESC, 1);
+            }
+            tc_commit(&empty[s]);
+            tc_commit(&tfull[b]);
+        }
+        if (!ok) {
+            tc_commit(&drain);
+            mbar_wait(&drain, 0, limit, err);
+        }
+    } else if (warp >= 2) {
+        const int ct = threadIdx.x - 64;  // converter thread 0..255
+        const int q = warp & 3, half = (warp - 2) >> 2;
+        float tot[TC_BN / 2];
+#pragma unroll
+        for (int j = 0; j < TC_BN / 2; ++j) tot[j] = 0.f;
+        bool ok = true;
+        // stage 0 is converted before the loop; step g converts stage g + 1, then drains stage g
+        for (int64_t g = -1; g < total && ok; ++g) {
+            const int64_t nx = g + 1;
+            if (nx < total) {
+                const int s = (int)(nx % TC2_STAGES);
+                if (!mbar_wait(&full[s], (uint32_t)((nx / TC2_STAGES) & 1), limit, err) || *(volatile int*)&abort_flag) {
+                    atomicExch(&abort_flag, 1);
+                    ok = false;
+                    break;
+                }
+                tc2_convert(base + s * TC2_STAGE, ct);
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic writes -> tensor core
+                __syncwarp();
+                if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(s_addr(&conv[s])) : "memory");
+            }
+            if (g < 0) continue;
+            const int b = (int)(g & 1);
+            const int64_t u = g >> 1;
+            if (!mbar_wait(&tfull[b], (uint32_t)(u & 1), limit, err) || *(volatile int*)&abort_flag) {
+                atomicExch(&abort_flag, 1);
+                ok = false;
+                break;
+            }
+            tc_fence_after();
+#pragma unroll
+            for (int c = 0; c < TC_BN / 64; ++c) {
+                float v[32];
+                tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + b * TC_BN + 64 * half + 32 * c, v);
+#pragma unroll
+                for (int j = 0; j < 32; ++j) tot[32 * c + j] += v[j];
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(s_addr(&tempty[b])) : "memory");
+            if (g % nk == nk - 1) {  // last stage of a job: write its tile, start the next total
+                int64_t item;
+                int m0, n0;
+                job_of(g / nk, &item, &m0, &n0);
+                const int row = m0 + 32 * q + lane;
+                float4* d4 = (float4*)(C + item * c_is + (int64_t)row * N2 + n0 + 64 * half);
+#pragma unroll
+                for (int j = 0; j < TC_BN / 8; ++j) {
+                    d4[j] = make_float4(tot[4 * j], tot[4 * j + 1], tot[4 * j + 2], tot[4 * j + 3]);
+                    tot[4 * j] = tot[4 * j + 1] = tot[4 * j + 2] = tot[4 * j + 3] = 0.f;
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (abort_flag && threadIdx.x == 0) atomicExch(err, QX_ETIMEOUT);
+    if (warp == 1) {
+        __syncwarp();
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * TC_BN) : "memory");
+    }
+}
+
+// ------------------------------------------------------------------------------------------------
 // host side
 // ------------------------------------------------------------------------------------------------
 static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
@@ -504,6 +727,52 @@ static cudaError_t run_gemm(const TcArgs& g, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+static bool map_raw(CUtensorMap* m, const void* base, int64_t k2, int64_t rows, int64_t items, int64_t item_bytes,
+                    int box_rows) {
+    auto fn = encode_fn();
+    if (!fn) return false;
+    const cuuint64_t dims[3] = {(cuuint64_t)k2, (cuuint64_t)rows, (cuuint64_t)items};
+    const cuuint64_t strides[2] = {(cuuint64_t)(k2 * 4), (cuuint64_t)item_bytes};
+    const cuuint32_t box[3] = {32, (cuuint32_t)box_rows, 1};
+    const cuuint32_t es[3] = {1, 1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void*>(base), dims, strides, box, es,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+cudaError_t launch_tc2_gemm(const TcArgs& g, cudaStream_t st) {
+    if (!(g.mb >= 7 && g.nb >= 6 && g.kb >= 4 && g.n_items > 0 && g.n_items <= 65535)) return cudaErrorInvalidValue;
+    if (!g.a_kmajor || !g.b_kmajor) return cudaErrorInvalidValue;
+    const int64_t M = 1ll << g.mb, N = 1ll << g.nb, K = 1ll << g.kb;
+    const bool abc = g.a_is == 0, bbc = g.b_is == 0;
+    CUtensorMap ma, mb;
+    if (!map_raw(&ma, g.a, 2 * K, M, abc ? 1 : g.n_items, abc ? M * K * 8 : g.a_is * 8, TC_BM) ||
+        !map_raw(&mb, g.b, 2 * K, N, bbc ? 1 : g.n_items, bbc ? N * K * 8 : g.b_is * 8, TC_BN / 2))
+        return cudaErrorInvalidValue;
+    const int smem = TC2_STAGES * TC2_STAGE + 1024;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    static uint64_t done[4] = {0, 0, 0, 0};
+    static std::mutex mu;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        if (dev < 256 && !((done[dev >> 6] >> (dev & 63)) & 1)) {
+            e = cudaFuncSetAttribute(k_gemm_tc2, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            if (e != cudaSuccess) return e;
+            done[dev >> 6] |= 1ull << (dev & 63);
+        }
+    }
+    const int tiles_m = (int)(M / TC_BM), tiles_n = (int)(2 * N / TC_BN);
+    int sms = 152;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 152;
+    const int64_t jobs = (int64_t)tiles_m * tiles_n * g.n_items;
+    const unsigned grid = (unsigned)std::min<int64_t>(jobs, sms);  // one CTA per SM (shared memory)
+    k_gemm_tc2<<<grid, TC2_THREADS, smem, st>>>(ma, mb, (float*)g.c, g.c_is * 2, (int)M, (int)(2 * N), (int)(2 * K),
+                                                tiles_n, tiles_m * tiles_n, g.n_items, abc, bbc, g.limit, g.err);
+    return cudaGetLastError();
+}
+
 static bool tc_shape_ok(const TcArgs& g) {
     // whole 128 x 128 tiles and whole 128-byte K slabs (see the plan compiler)
     return g.mb >= 7 && g.nb >= 6 && g.kb >= 5 && g.n_items > 0 && g.n_items <= 65535;
@@ -528,5 +797,6 @@ cudaError_t launch_tc_gemm(int form, const TcArgs& g, cudaStream_t st) {
 static_assert(TcForm<TC_FORM_3XTF32>::STAGES * 4 * TC_BM * TC_ROWB + 1024 <= TC_SMEM_LIMIT + 1024, "smem");
 static_assert(TcForm<TC_FORM_BF16X3>::STAGES * 6 * TC_BM * TC_ROWB + 1024 <= TC_SMEM_LIMIT + 1024, "smem");
 static_assert(TcForm<TC_FORM_FP16>::STAGES * 2 * TC_BM * TC_ROWB + 1024 <= TC_SMEM_LIMIT + 1024, "smem");
+static_assert(TC2_STAGES * TC2_STAGE + 1024 <= 227 * 1024, "smem");
 
 }  // namespace qx

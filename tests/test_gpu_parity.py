@@ -249,3 +249,29 @@ def test_sharded_slices_single_rank_group(qx):
         assert rel_l2(got, c.contract(bits)) < 1e-15
     finally:
         dist.destroy_process_group()
+
+
+def test_graph_replay_matches_eager_and_follows_new_data(qx):
+    import torch
+    circ, om, order, sliced, bits = grid_case(3, 4, 8, 44, 1, 3, 6)
+    c = _contractor(qx, circ, om, order, sliced, 6)
+    d_bits = torch.from_numpy(bits).cuda()
+    out = torch.empty((6, 2, 2), dtype=torch.float64, device="cuda")
+    runs = []
+    for _ in range(3):  # eager, capture + launch, replay
+        c.contract_device(d_bits, out)
+        torch.cuda.synchronize()
+        runs.append(out.cpu().numpy().copy())
+    assert np.array_equal(runs[0], runs[1]) and np.array_equal(runs[1], runs[2])
+    # new bitstrings in the same buffer: the replayed graph reads them
+    bits2 = C.random_bitstrings(circ.n_qubits, 6, 99)
+    d_bits.copy_(torch.from_numpy(bits2))
+    c.contract_device(d_bits, out)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy()
+    ref = oracle.sv_amplitudes(circ.n_qubits, C.gates_to_records(circ), om, bits2)
+    assert rel_l2(got[..., 0] + 1j * got[..., 1], ref) <= TOL_C64
+    qx.qx_set_graphs(c.h, False)
+    c.contract_device(d_bits, out)
+    torch.cuda.synchronize()
+    assert np.array_equal(out.cpu().numpy(), got)
