@@ -164,7 +164,7 @@ def reference_arm(args, w, rank, world):
     amps_per_step = (ns / w.n_slices) * (1 << w.n_open)
     value = amps_per_step * len(times) / sum(times)
     sample = f"1 bitstring x {ns} of {w.n_slices} slices per step (complex128 numpy plan einsum)"
-    line = {"impl": "reference", "metric": "amplitudes/s", "value": value, "unit": "amplitudes/s", "n_gpus": 0,
+    line = {"impl": "reference", "metric": "amplitudes/s", "value": value, "unit": "amplitudes/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
             "config": config_of(w, {"sample": sample}),

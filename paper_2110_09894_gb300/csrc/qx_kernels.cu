@@ -412,8 +412,10 @@ __global__ void __launch_bounds__(256, (BM * BN >= 8192 ? 1 : 2)) k_gemm_c64(con
     for (int64_t k0 = 0; k0 < K; k0 += GBK) {
         const bool more = k0 + GBK < K;
         if (more) gload(k0 + GBK);
+        const int kl = K < GBK ? (int)K : GBK;  // products with K < 16 skip the zero-filled rows
 #pragma unroll
         for (int kk = 0; kk < GBK; ++kk) {
+            if (kk >= kl) break;
             float2 a[TM], b[TN];
 #pragma unroll
             for (int i = 0; i < TM; ++i) a[i] = As[buf][kk][ty + 16 * i];

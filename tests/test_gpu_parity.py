@@ -275,3 +275,34 @@ def test_graph_replay_matches_eager_and_follows_new_data(qx):
     c.contract_device(d_bits, out)
     torch.cuda.synchronize()
     assert np.array_equal(out.cpu().numpy(), got)
+
+
+def test_edge_cases(qx):
+    # no bitstrings
+    circ, om, order, sliced, bits = grid_case(2, 3, 4, 61, 1, 2, 3)
+    c = _contractor(qx, circ, om, order, sliced, 3)
+    with pytest.raises(qx.QXError) as e:
+        c.contract(np.zeros((0, circ.n_qubits), np.uint8))
+    assert e.value.code == qx.QX_EINVAL
+    # bytes at open qubits are ignored
+    b2 = bits.copy()
+    b2[:, -1] ^= 1
+    assert np.array_equal(c.contract(bits), c.contract(b2))
+    # disconnected network: two qubits without a two-qubit gate (outer product step)
+    d = C.Circuit(2)
+    d.append((0,), C.SQRT_X)
+    d.append((1,), C.SQRT_W)
+    from qxgen.workloads import make_plan
+    om2 = np.array([0, 1], np.uint8)
+    order2, sliced2, _, _ = make_plan(d, om2, 0, 3)
+    cc = _contractor(qx, d, om2, order2, sliced2, 2)
+    bb = np.array([[0, 0], [1, 0]], np.uint8)
+    got = cc.contract(bb)
+    ref = oracle.sv_amplitudes(2, C.gates_to_records(d), om2, bb)
+    assert rel_l2(got, ref) <= TOL_C64
+    # every qubit closed but the plan slices the only bond of a one-gate circuit
+    e1 = C.Circuit(1)
+    e1.append((0,), C.SQRT_Y)
+    ce = _contractor(qx, e1, np.zeros(1, np.uint8), [(0, 1), (2, 3)], [0], 2)
+    got = ce.contract(np.array([[0], [1]], np.uint8))[:, 0]
+    assert np.allclose(got, C.SQRT_Y[:, 0], atol=1e-7)
