@@ -540,7 +540,7 @@ static int compile_plan(qx_ctx* h, const int64_t* order, int64_t n_steps, const 
         // the prep-based kernel streams pre-split parts (about (40 M + 72 N) K extra bytes) but leaves
         // shared-memory bandwidth to the MMAs.  Measured on GB300: direct wins for the short products of
         // small per-pair tensors (M or N <= 256), the prep-based kernel for large tensors.
-        const bool direct = tc_form == TC_FORM_3XTF32 && (int)fA.size() >= 7 && (int)fB.size() >= 6 && kb >= 4 &&
+        const bool direct = tc_form == TC_FORM_3XTF32 && (int)fA.size() >= 7 && (int)fB.size() >= 5 && kb >= 4 &&
                             ((int)fA.size() <= 8 || (int)fB.size() <= 8);
         Choice best{};
         best.cost = -1;

@@ -412,10 +412,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 // Warps: 0 TMA, 1 TMEM + MMA, 2..9 convert the next stage and drain TMEM
 // (warp w reads TMEM lanes 32 (w % 4), columns 64 ((w - 2) / 4) .. + 63).
 // ------------------------------------------------------------------------------------------------
-constexpr int TC2_THREADS = 320, TC2_STAGES = 3;
-constexpr uint32_t TC2_A = 16384, TC2_BRAW = 8192, TC2_STAGE = 4 * TC2_A + TC2_BRAW;  // raw/hi A, lo A, raw B, B'hi, B'lo
-constexpr uint32_t TC2_OFF_ALO = TC2_A, TC2_OFF_BRAW = 2 * TC2_A, TC2_OFF_BHI = 2 * TC2_A + TC2_BRAW,
-                   TC2_OFF_BLO = 3 * TC2_A + TC2_BRAW;
+constexpr int TC2_THREADS = 320;
+// stage layout for a B' tile of BN rows: raw/hi A (16 KB), lo A (16 KB), raw B (BN/2 rows), B'hi, B'lo (BN rows)
+template <int BN>
+struct Tc2 {
+    static constexpr uint32_t A = 16384, BRAW = (BN / 2) * 128, BP = BN * 128;
+    static constexpr uint32_t OFF_ALO = A, OFF_BRAW = 2 * A, OFF_BHI = 2 * A + BRAW, OFF_BLO = 2 * A + BRAW + BP;
+    static constexpr uint32_t STAGE = 2 * A + BRAW + 2 * BP;
+    static constexpr int STAGES = BN == 128 ? 3 : 4;
+};
 
 __device__ __forceinline__ void split4(float4 v, float4& hi, float4& lo) {
     hi = make_float4(tf32_rna(v.x), tf32_rna(v.y), tf32_rna(v.z), tf32_rna(v.w));
@@ -423,7 +428,9 @@ __device__ __forceinline__ void split4(float4 v, float4& hi, float4& lo) {
 }
 
 // convert stage `st` (raw A, raw B landed) with the 256 converter threads ct = 0..255
+template <int BN>
 __device__ __forceinline__ void tc2_convert(uint8_t* st, int ct) {
+    using L = Tc2<BN>;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {  // A: 1024 float4, elementwise, same offsets
         const int c = ct + 256 * i;
@@ -431,27 +438,28 @@ __device__ __forceinline__ void tc2_convert(uint8_t* st, int ct) {
         float4 hi, lo;
         split4(*a, hi, lo);
         *a = hi;
-        ((float4*)(st + TC2_OFF_ALO))[c] = lo;
+        ((float4*)(st + L::OFF_ALO))[c] = lo;
     }
 #pragma unroll
-    for (int i = 0; i < 2; ++i) {  // B: 64 rows x 8 chunks of 16 bytes
+    for (int i = 0; i < BN / 64; ++i) {  // B: BN/2 rows x 8 chunks of 16 bytes
         const int c = ct + 256 * i;
         const int n = c >> 3, j = c & 7;
-        const float4 v = *(const float4*)(st + TC2_OFF_BRAW + n * 128 + ((j ^ (n & 7)) << 4));
+        const float4 v = *(const float4*)(st + L::OFF_BRAW + n * 128 + ((j ^ (n & 7)) << 4));
         const float4 r0 = make_float4(v.x, -v.y, v.z, -v.w);  // row 2n: re, -im
         const float4 r1 = make_float4(v.y, v.x, v.w, v.z);    // row 2n+1: im, re
         const int ra = 2 * n, rb = 2 * n + 1;
         const uint32_t oa = ra * 128 + ((j ^ (ra & 7)) << 4), ob = rb * 128 + ((j ^ (rb & 7)) << 4);
         float4 hi, lo;
         split4(r0, hi, lo);
-        *(float4*)(st + TC2_OFF_BHI + oa) = hi;
-        *(float4*)(st + TC2_OFF_BLO + oa) = lo;
+        *(float4*)(st + L::OFF_BHI + oa) = hi;
+        *(float4*)(st + L::OFF_BLO + oa) = lo;
         split4(r1, hi, lo);
-        *(float4*)(st + TC2_OFF_BHI + ob) = hi;
-        *(float4*)(st + TC2_OFF_BLO + ob) = lo;
+        *(float4*)(st + L::OFF_BHI + ob) = hi;
+        *(float4*)(st + L::OFF_BLO + ob) = lo;
     }
 }
 
+template <int BN>
 __global__ void __launch_bounds__(TC2_THREADS, 1)
     k_gemm_tc2(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                float* __restrict__ C, int64_t c_is, int M, int N2, int K2, int tiles_n, int tiles, int64_t n_items,
@@ -459,8 +467,10 @@ __global__ void __launch_bounds__(TC2_THREADS, 1)
     // persistent over (pair, tile) jobs: job = blockIdx.x + t * gridDim.x; the
     // k-stages of successive jobs form one sequence g = t * nk + it, so the
     // pipeline stays full across tile boundaries
+    using L = Tc2<BN>;
     constexpr int BK = 32;  // TF32 elements per stage (one 128-byte slab)
-    constexpr uint32_t IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(TC_BN >> 3) << 17) |
+    constexpr int TC2_STAGES = L::STAGES;
+    constexpr uint32_t IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(BN >> 3) << 17) |
                                ((uint32_t)(TC_BM >> 4) << 24);
     extern __shared__ uint8_t dyn[];
     __shared__ uint64_t full[TC2_STAGES], conv[TC2_STAGES], empty[TC2_STAGES], tfull[2], tempty[2], drain;
@@ -478,7 +488,7 @@ __global__ void __launch_bounds__(TC2_THREADS, 1)
         *item = j / tiles;
         const int tile = (int)(j % tiles);
         *m0 = (tile / tiles_n) * TC_BM;
-        *n0 = (tile % tiles_n) * TC_BN;  // row of B'; raw B row n0 / 2
+        *n0 = (tile % tiles_n) * BN;  // row of B'; raw B row n0 / 2
     };
     if (threadIdx.x == 0) {
         for (int s = 0; s < TC2_STAGES; ++s) {
@@ -496,7 +506,7 @@ __global__ void __launch_bounds__(TC2_THREADS, 1)
     }
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(s_addr(&tmem_slot)),
-                     "r"(2 * TC_BN)
+                     "r"(2 * BN)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -518,10 +528,10 @@ __global__ void __launch_bounds__(TC2_THREADS, 1)
             int m0, n0;
             job_of(g / nk, &item, &m0, &n0);
             const int it = (int)(g % nk);
-            mbar_expect_tx(&full[s], TC2_A + TC2_BRAW);
-            uint8_t* st = base + s * TC2_STAGE;
+            mbar_expect_tx(&full[s], L::A + L::BRAW);
+            uint8_t* st = base + s * L::STAGE;
             tma_load_3d(st, &mapA, it * BK, m0, a_bcast ? 0 : (int)item, &full[s]);
-            tma_load_3d(st + TC2_OFF_BRAW, &mapB, it * BK, n0 >> 1, b_bcast ? 0 : (int)item, &full[s]);
+            tma_load_3d(st + L::OFF_BRAW, &mapB, it * BK, n0 >> 1, b_bcast ? 0 : (int)item, &full[s]);
             ++issued;
         }
         if (*(volatile int*)&abort_flag) {
@@ -542,12 +552,12 @@ __global__ void __launch_bounds__(TC2_THREADS, 1)
                 break;
             }
             tc_fence_after();
-            const uint32_t st = s_addr(base + s * TC2_STAGE);
-            const uint32_t d = tmem + b * TC_BN;
+            const uint32_t st = s_addr(base + s * L::STAGE);
+            const uint32_t d = tmem + b * BN;
 #pragma unroll
             for (int kk = 0; kk < BK / 8; ++kk) {
-                const uint64_t ahi = sdesc(st + kk * 32), alo = sdesc(st + TC2_OFF_ALO + kk * 32);
-                const uint64_t bhi = sdesc(st + TC2_OFF_BHI + kk * 32), blo = sdesc(st + TC2_OFF_BLO + kk * 32);
+                const uint64_t ahi = sdesc(st + kk * 32), alo = sdesc(st + L::OFF_ALO + kk * 32);
+                const uint64_t bhi = sdesc(st + L::OFF_BHI + kk * 32), blo = sdesc(st + L::OFF_BLO + kk * 32);
                 mma<TC_FORM_3XTF32>(d, ahi, bhi, IDESC, kk != 0);
                 mma<TC_FORM_3XTF32>(d, ahi, blo, IDESC, 1);
                 mma<TC_FORM_3XTF32>(d, alo, bhi, IDESC, 1);
@@ -562,9 +572,9 @@ __global__ void __launch_bounds__(TC2_THREADS, 1)
     } else if (warp >= 2) {
         const int ct = threadIdx.x - 64;  // converter thread 0..255
         const int q = warp & 3, half = (warp - 2) >> 2;
-        float tot[TC_BN / 2];
+        float tot[BN / 2];
 #pragma unroll
-        for (int j = 0; j < TC_BN / 2; ++j) tot[j] = 0.f;
+        for (int j = 0; j < BN / 2; ++j) tot[j] = 0.f;
         bool ok = true;
         // stage 0 is converted before the loop; step g converts stage g + 1, then drains stage g
         for (int64_t g = -1; g < total && ok; ++g) {
@@ -576,7 +586,7 @@ __global__ void __launch_bounds__(TC2_THREADS, 1)
                     ok = false;
                     break;
                 }
-                tc2_convert(base + s * TC2_STAGE, ct);
+                tc2_convert<BN>(base + s * L::STAGE, ct);
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic writes -> tensor core
                 __syncwarp();
                 if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(s_addr(&conv[s])) : "memory");
@@ -591,9 +601,9 @@ __global__ void __launch_bounds__(TC2_THREADS, 1)
             }
             tc_fence_after();
 #pragma unroll
-            for (int c = 0; c < TC_BN / 64; ++c) {
+            for (int c = 0; c < BN / 64; ++c) {
                 float v[32];
-                tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + b * TC_BN + 64 * half + 32 * c, v);
+                tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + b * BN + (BN / 2) * half + 32 * c, v);
 #pragma unroll
                 for (int j = 0; j < 32; ++j) tot[32 * c + j] += v[j];
             }
@@ -605,9 +615,9 @@ __global__ void __launch_bounds__(TC2_THREADS, 1)
                 int m0, n0;
                 job_of(g / nk, &item, &m0, &n0);
                 const int row = m0 + 32 * q + lane;
-                float4* d4 = (float4*)(C + item * c_is + (int64_t)row * N2 + n0 + 64 * half);
+                float4* d4 = (float4*)(C + item * c_is + (int64_t)row * N2 + n0 + (BN / 2) * half);
 #pragma unroll
-                for (int j = 0; j < TC_BN / 8; ++j) {
+                for (int j = 0; j < BN / 8; ++j) {
                     d4[j] = make_float4(tot[4 * j], tot[4 * j + 1], tot[4 * j + 2], tot[4 * j + 3]);
                     tot[4 * j] = tot[4 * j + 1] = tot[4 * j + 2] = tot[4 * j + 3] = 0.f;
                 }
@@ -620,7 +630,7 @@ __global__ void __launch_bounds__(TC2_THREADS, 1)
     if (warp == 1) {
         __syncwarp();
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * TC_BN) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * BN) : "memory");
     }
 }
 
@@ -740,16 +750,16 @@ static bool map_raw(CUtensorMap* m, const void* base, int64_t k2, int64_t rows, 
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-cudaError_t launch_tc2_gemm(const TcArgs& g, cudaStream_t st) {
-    if (!(g.mb >= 7 && g.nb >= 6 && g.kb >= 4 && g.n_items > 0 && g.n_items <= 65535)) return cudaErrorInvalidValue;
-    if (!g.a_kmajor || !g.b_kmajor) return cudaErrorInvalidValue;
+template <int BN>
+static cudaError_t run_tc2(const TcArgs& g, cudaStream_t st) {
+    using L = Tc2<BN>;
     const int64_t M = 1ll << g.mb, N = 1ll << g.nb, K = 1ll << g.kb;
     const bool abc = g.a_is == 0, bbc = g.b_is == 0;
     CUtensorMap ma, mb;
     if (!map_raw(&ma, g.a, 2 * K, M, abc ? 1 : g.n_items, abc ? M * K * 8 : g.a_is * 8, TC_BM) ||
-        !map_raw(&mb, g.b, 2 * K, N, bbc ? 1 : g.n_items, bbc ? N * K * 8 : g.b_is * 8, TC_BN / 2))
+        !map_raw(&mb, g.b, 2 * K, N, bbc ? 1 : g.n_items, bbc ? N * K * 8 : g.b_is * 8, BN / 2))
         return cudaErrorInvalidValue;
-    const int smem = TC2_STAGES * TC2_STAGE + 1024;
+    const int smem = L::STAGES * L::STAGE + 1024;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
@@ -758,19 +768,26 @@ cudaError_t launch_tc2_gemm(const TcArgs& g, cudaStream_t st) {
     {
         std::lock_guard<std::mutex> lk(mu);
         if (dev < 256 && !((done[dev >> 6] >> (dev & 63)) & 1)) {
-            e = cudaFuncSetAttribute(k_gemm_tc2, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            e = cudaFuncSetAttribute(k_gemm_tc2<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
             if (e != cudaSuccess) return e;
             done[dev >> 6] |= 1ull << (dev & 63);
         }
     }
-    const int tiles_m = (int)(M / TC_BM), tiles_n = (int)(2 * N / TC_BN);
+    const int tiles_m = (int)(M / TC_BM), tiles_n = (int)(2 * N / BN);
     int sms = 152;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 152;
     const int64_t jobs = (int64_t)tiles_m * tiles_n * g.n_items;
     const unsigned grid = (unsigned)std::min<int64_t>(jobs, sms);  // one CTA per SM (shared memory)
-    k_gemm_tc2<<<grid, TC2_THREADS, smem, st>>>(ma, mb, (float*)g.c, g.c_is * 2, (int)M, (int)(2 * N), (int)(2 * K),
-                                                tiles_n, tiles_m * tiles_n, g.n_items, abc, bbc, g.limit, g.err);
+    k_gemm_tc2<BN><<<grid, TC2_THREADS, smem, st>>>(ma, mb, (float*)g.c, g.c_is * 2, (int)M, (int)(2 * N),
+                                                    (int)(2 * K), tiles_n, tiles_m * tiles_n, g.n_items, abc, bbc,
+                                                    g.limit, g.err);
     return cudaGetLastError();
+}
+
+cudaError_t launch_tc2_gemm(const TcArgs& g, cudaStream_t st) {
+    if (!(g.mb >= 7 && g.nb >= 5 && g.kb >= 4 && g.n_items > 0 && g.n_items <= 65535)) return cudaErrorInvalidValue;
+    if (!g.a_kmajor || !g.b_kmajor) return cudaErrorInvalidValue;
+    return g.nb >= 6 ? run_tc2<128>(g, st) : run_tc2<64>(g, st);
 }
 
 static bool tc_shape_ok(const TcArgs& g) {
@@ -797,6 +814,7 @@ cudaError_t launch_tc_gemm(int form, const TcArgs& g, cudaStream_t st) {
 static_assert(TcForm<TC_FORM_3XTF32>::STAGES * 4 * TC_BM * TC_ROWB + 1024 <= TC_SMEM_LIMIT + 1024, "smem");
 static_assert(TcForm<TC_FORM_BF16X3>::STAGES * 6 * TC_BM * TC_ROWB + 1024 <= TC_SMEM_LIMIT + 1024, "smem");
 static_assert(TcForm<TC_FORM_FP16>::STAGES * 2 * TC_BM * TC_ROWB + 1024 <= TC_SMEM_LIMIT + 1024, "smem");
-static_assert(TC2_STAGES * TC2_STAGE + 1024 <= 227 * 1024, "smem");
+static_assert(Tc2<128>::STAGES * Tc2<128>::STAGE + 1024 <= 227 * 1024, "smem");
+static_assert(Tc2<64>::STAGES * Tc2<64>::STAGE + 1024 <= 227 * 1024, "smem");
 
 }  // namespace qx
