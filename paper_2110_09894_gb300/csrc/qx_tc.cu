@@ -409,10 +409,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 // elementwise map keeps the 128-byte swizzle, so A's parts sit at the same
 // offsets as the raw data; B' row r puts chunk j at (j ^ (r % 8)).  This
 // removes the separate split pass and its HBM traffic.
-// Warps: 0 TMA, 1 TMEM + MMA, 2..9 convert the next stage and drain TMEM
-// (warp w reads TMEM lanes 32 (w % 4), columns 64 ((w - 2) / 4) .. + 63).
+// Warps: 0 TMA, 1 TMEM + MMA, 2..9 drain TMEM (warp w reads TMEM lanes
+// 32 (w % 4) and half of the columns), 10..13 convert stages ahead of the MMAs.
 // ------------------------------------------------------------------------------------------------
-constexpr int TC2_THREADS = 320;
+constexpr int TC2_THREADS = 448, TC2_CONV = 128;  // warps 0 TMA, 1 MMA, 2-9 drain, 10-13 convert
 // stage layout for a B' tile of BN rows: raw/hi A (16 KB), lo A (16 KB), raw B (BN/2 rows), B'hi, B'lo (BN rows)
 template <int BN>
 struct Tc2 {
@@ -427,13 +427,13 @@ __device__ __forceinline__ void split4(float4 v, float4& hi, float4& lo) {
     lo = make_float4(v.x - hi.x, v.y - hi.y, v.z - hi.z, v.w - hi.w);
 }
 
-// convert stage `st` (raw A, raw B landed) with the 256 converter threads ct = 0..255
+// convert stage `st` (raw A, raw B landed) with the converter threads ct = 0 .. TC2_CONV - 1
 template <int BN>
 __device__ __forceinline__ void tc2_convert(uint8_t* st, int ct) {
     using L = Tc2<BN>;
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {  // A: 1024 float4, elementwise, same offsets
-        const int c = ct + 256 * i;
+    for (int i = 0; i < 1024 / TC2_CONV; ++i) {  // A: 1024 float4, elementwise, same offsets
+        const int c = ct + TC2_CONV * i;
         float4* a = (float4*)(st) + c;
         float4 hi, lo;
         split4(*a, hi, lo);
@@ -441,8 +441,8 @@ __device__ __forceinline__ void tc2_convert(uint8_t* st, int ct) {
         ((float4*)(st + L::OFF_ALO))[c] = lo;
     }
 #pragma unroll
-    for (int i = 0; i < BN / 64; ++i) {  // B: BN/2 rows x 8 chunks of 16 bytes
-        const int c = ct + 256 * i;
+    for (int i = 0; i < (BN / 2) * 8 / TC2_CONV; ++i) {  // B: BN/2 rows x 8 chunks of 16 bytes
+        const int c = ct + TC2_CONV * i;
         const int n = c >> 3, j = c & 7;
         const float4 v = *(const float4*)(st + L::OFF_BRAW + n * 128 + ((j ^ (n & 7)) << 4));
         const float4 r0 = make_float4(v.x, -v.y, v.z, -v.w);  // row 2n: re, -im
@@ -493,7 +493,7 @@ __global__ void __launch_bounds__(TC2_THREADS, 1)
     if (threadIdx.x == 0) {
         for (int s = 0; s < TC2_STAGES; ++s) {
             mbar_init(&full[s], 1);
-            mbar_init(&conv[s], 8);
+            mbar_init(&conv[s], TC2_CONV / 32);
             mbar_init(&empty[s], 1);
         }
         for (int b = 0; b < 2; ++b) {
@@ -569,34 +569,31 @@ __global__ void __launch_bounds__(TC2_THREADS, 1)
             tc_commit(&drain);
             mbar_wait(&drain, 0, limit, err);
         }
+    } else if (warp >= 10) {
+        // converters: split each landed stage in place / into the part tiles, ahead of the MMAs
+        const int ct = threadIdx.x - 320;
+        for (int64_t g = 0; g < total; ++g) {
+            const int s = (int)(g % TC2_STAGES);
+            if (!mbar_wait(&full[s], (uint32_t)((g / TC2_STAGES) & 1), limit, err) || *(volatile int*)&abort_flag) {
+                atomicExch(&abort_flag, 1);
+                break;
+            }
+            tc2_convert<BN>(base + s * L::STAGE, ct);
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic writes -> tensor core
+            __syncwarp();
+            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(s_addr(&conv[s])) : "memory");
+        }
     } else if (warp >= 2) {
-        const int ct = threadIdx.x - 64;  // converter thread 0..255
+        // drain: TMEM lanes 32 (warp % 4), columns (BN / 2) ((warp - 2) / 4) .. + BN / 2 - 1
         const int q = warp & 3, half = (warp - 2) >> 2;
         float tot[BN / 2];
 #pragma unroll
         for (int j = 0; j < BN / 2; ++j) tot[j] = 0.f;
-        bool ok = true;
-        // stage 0 is converted before the loop; step g converts stage g + 1, then drains stage g
-        for (int64_t g = -1; g < total && ok; ++g) {
-            const int64_t nx = g + 1;
-            if (nx < total) {
-                const int s = (int)(nx % TC2_STAGES);
-                if (!mbar_wait(&full[s], (uint32_t)((nx / TC2_STAGES) & 1), limit, err) || *(volatile int*)&abort_flag) {
-                    atomicExch(&abort_flag, 1);
-                    ok = false;
-                    break;
-                }
-                tc2_convert<BN>(base + s * L::STAGE, ct);
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic writes -> tensor core
-                __syncwarp();
-                if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(s_addr(&conv[s])) : "memory");
-            }
-            if (g < 0) continue;
+        for (int64_t g = 0; g < total; ++g) {
             const int b = (int)(g & 1);
             const int64_t u = g >> 1;
             if (!mbar_wait(&tfull[b], (uint32_t)(u & 1), limit, err) || *(volatile int*)&abort_flag) {
                 atomicExch(&abort_flag, 1);
-                ok = false;
                 break;
             }
             tc_fence_after();
