@@ -160,6 +160,12 @@ int qx_contract_slices_device(qx_handle h, const uint8_t* d_bitstrings, int64_t 
  * while profiling.  enable = 0 turns it off and drops the captured graph. */
 int qx_set_graphs(qx_handle h, int enable);
 
+/* A text listing of the compiled plan, one line per kernel launch of a
+ * contraction (kind, whether it runs per pair or once, M/K/N bits, operand
+ * layouts).  Writes at most len bytes (NUL-terminated) to buf; *needed (may be
+ * NULL) receives the full size.  Works on host-only handles. */
+int qx_describe_plan(qx_handle h, char* buf, int64_t len, int64_t* needed);
+
 /* Statistics of the last contraction (host values, any pointer may be NULL):
  * algorithmic complex flops (8 M K N per step, per pair), kernel launches,
  * batches. */

@@ -1394,6 +1394,36 @@ int qx_contract_device(qx_handle h, const uint8_t* d_bits, int64_t n_bits, doubl
     return qx_contract_slices_device(h, d_bits, n_bits, 0, h->n_slices, d_amps);
 }
 
+int qx_describe_plan(qx_handle h, char* buf, int64_t len, int64_t* needed) {
+    if (!h) return QX_EINVAL;
+    if (!h->have_plan) return fail(h, QX_ESTATE, "no plan");
+    std::string out;
+    char line[256];
+    for (size_t i = 0; i < h->ops.size(); ++i) {
+        const Op& op = h->ops[i];
+        const char* kind = op.type == OP_PERM    ? "permute"
+                           : op.type == OP_SMALL ? "gather"
+                           : op.tc == TC_FORM_3XTF32_DIRECT ? "tc_direct"
+                           : op.tc                          ? "tc_prep"
+                                                            : "gemm";
+        if (op.type == OP_PERM)
+            snprintf(line, sizeof line, "%zu step=%lld %s %s rank=%zu\n", i, (long long)op.step, kind,
+                     op.variant ? "pair" : "shared", op.target_legs.size());
+        else
+            snprintf(line, sizeof line, "%zu step=%lld %s %s m=%d k=%d n=%d a_kmajor=%d b_kmajor=%d\n", i,
+                     (long long)op.step, kind, op.variant ? "pair" : "shared", op.mb, op.kb, op.nb, (int)op.a_km,
+                     (int)op.b_km);
+        out += line;
+    }
+    if (needed) *needed = (int64_t)out.size() + 1;
+    if (buf && len > 0) {
+        const size_t n = std::min<size_t>(out.size(), (size_t)len - 1);
+        memcpy(buf, out.data(), n);
+        buf[n] = 0;
+    }
+    return QX_OK;
+}
+
 int qx_set_graphs(qx_handle h, int enable) {
     if (!h) return QX_EINVAL;
     drop_graph(h);

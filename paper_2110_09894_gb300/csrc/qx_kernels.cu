@@ -303,7 +303,9 @@ static int sm_count();
 cudaError_t launch_small(const SmallDesc& d, const ItemCtx& ic, int64_t n_items, float2* out, int64_t out_is,
                          cudaStream_t st) {
     if (n_items <= 0) return cudaSuccess;
-    if (d.mb < 8) {  // flat: short per-pair rows
+    // flat: short per-pair rows with a small operand light enough to read through L1 per thread;
+    // a larger small operand is better staged once per CTA in shared memory (per-pair kernel)
+    if (d.mb < 8 && d.kb + d.nb <= 6) {
         const int64_t total = n_items << d.mb;
         const unsigned grid = (unsigned)std::min<int64_t>((total + 255) / 256, (int64_t)sm_count() * 16);
         switch (d.kb) {

@@ -25,7 +25,7 @@ EXPORTS = ("qx_create", "qx_destroy", "qx_last_error", "qx_set_options", "qx_bui
            "qx_contract_slices", "qx_contract_slices_device", "qx_last_stats", "qx_set_profiling",
            "qx_profile_read", "qx_contract_device_static", "qx_device_status", "qx_group_create",
            "qx_group_scratch_size", "qx_group_bind", "qx_group_run", "qx_group_last_error", "qx_group_destroy",
-           "qx_set_graphs")
+           "qx_set_graphs", "qx_describe_plan")
 QX_STATIC_SCRATCH_BYTES = 64 << 20
 KERNEL_KINDS = ("permute", "small", "gemm", "sum", "tc_prep", "tc_gemm", "persist")
 
@@ -77,6 +77,7 @@ def load(path=None):
         "qx_set_profiling": ([vp, ctypes.c_int], ctypes.c_int),
         "qx_device_status": ([vp], ctypes.c_int),
         "qx_set_graphs": ([vp, ctypes.c_int], ctypes.c_int),
+        "qx_describe_plan": ([vp, ctypes.c_char_p, i64, ctypes.POINTER(i64)], ctypes.c_int),
         "qx_group_create": ([ctypes.POINTER(vp), ctypes.POINTER(vp), i32, ctypes.POINTER(vp), ctypes.POINTER(i64),
                              ctypes.POINTER(vp), i32], ctypes.c_int),
         "qx_group_scratch_size": ([vp, ctypes.POINTER(i64)], ctypes.c_int),
@@ -192,6 +193,14 @@ def qx_contract_device_static(h, d_bits_ptr, n_bits, d_amps_ptr):
     """Contract with the library's built-in scratch array: nothing is allocated."""
     _check(h, load().qx_contract_device_static(h, ctypes.c_void_p(int(d_bits_ptr)), int(n_bits),
                                                ctypes.c_void_p(int(d_amps_ptr))))
+
+
+def qx_describe_plan(h):
+    need = ctypes.c_int64()
+    _check(h, load().qx_describe_plan(h, None, 0, ctypes.byref(need)))
+    buf = ctypes.create_string_buffer(need.value)
+    _check(h, load().qx_describe_plan(h, buf, need.value, None))
+    return buf.value.decode()
 
 
 def qx_set_graphs(h, enable):
