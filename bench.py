@@ -48,6 +48,8 @@ def parse():
     p.add_argument("--precision", default="3xtf32", choices=list(PRECISIONS),
                    help="contraction form (3xtf32 and bf16x3 meet the 1e-5 tolerance; fp16 is reported)")
     p.add_argument("--executor", default="auto", choices=["auto", "batched", "persistent"])
+    p.add_argument("--streams", type=int, default=8,
+                   help="streams the batched executor issues independent steps on (1 = in plan order)")
     return p.parse_args()
 
 
@@ -320,6 +322,7 @@ def main():
         c = qx.Contractor(w.n_qubits, w.gates, w.open_mask, w.order, w.sliced, n_bits, device=local, stream=stream,
                           max_items=args.max_items, precision=PRECISIONS[args.precision][0],
                           executor={"auto": 0, "batched": 1, "persistent": 2}[args.executor])
+        qx.qx_set_streams(c.h, args.streams)
         d_bits = torch.from_numpy(bits).to(dev)
         d_amps = torch.empty((n_bits, 1 << w.n_open, 2), dtype=torch.float64, device=dev)
         flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
@@ -369,6 +372,7 @@ def main():
             c64 = qx.Contractor(w.n_qubits, w.gates, w.open_mask, w.order, w.sliced, n_bits, device=local,
                                 stream=stream, max_items=args.max_items, precision=0,
                                 executor={"auto": 0, "batched": 1, "persistent": 2}[args.executor])
+            qx.qx_set_streams(c64.h, args.streams)
             d64 = torch.empty_like(d_amps)
         for _ in range(args.warmup):
             c64.contract_device(d_bits, d64)
@@ -470,7 +474,7 @@ def main():
             "vs_baseline": None, "dtype": {"c64": "c64", "3xtf32": "tf32x3", "bf16x3": "bf16x3", "fp16": "fp16"}[args.precision],
             "data": "synthetic",
             "config": config_of(w, {"precision": args.precision + " contraction, FP64 slice sum",
-                                    "executor": args.executor,
+                                    "executor": args.executor, "streams": args.streams,
                                     "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
                                     "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MiB write); "
                                           f"workspace {ws_gb:.1f} GB",

@@ -160,6 +160,23 @@ int qx_contract_slices_device(qx_handle h, const uint8_t* d_bitstrings, int64_t 
  * while profiling.  enable = 0 turns it off and drops the captured graph. */
 int qx_set_graphs(qx_handle h, int enable);
 
+/* Concurrent issue of independent contraction steps (the paper has no
+ * counterpart; Sec. IV-A's levels of parallelism stop at one contraction per
+ * GPU kernel).  The plan compiler records, for every kernel launch, the
+ * earlier launches it must follow: those writing what it reads, reading or
+ * writing what it writes (storages of dead tensors are reused).  The batched
+ * executor then issues launches over n_streams streams: the handle's own
+ * stream plus n_streams - 1 streams the handle creates on its device, with
+ * event waits for the dependencies, and joins them back into the handle's
+ * stream before the slice sum of every batch, so the call stays ordered on
+ * the handle's stream as before.  Results are bit-identical for every
+ * n_streams (each launch computes the same values; only the overlap of
+ * independent launches changes).  n_streams = 1 issues everything on the
+ * handle's stream in plan order.  Default 8; range 1 .. 32 (QX_EINVAL
+ * otherwise).  Profiling runs everything on the handle's stream.  Drops a
+ * captured graph. */
+int qx_set_streams(qx_handle h, int32_t n_streams);
+
 /* A text listing of the compiled plan, one line per kernel launch of a
  * contraction (kind, whether it runs per pair or once, M/K/N bits, operand
  * layouts).  Writes at most len bytes (NUL-terminated) to buf; *needed (may be

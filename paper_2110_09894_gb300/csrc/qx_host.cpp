@@ -67,6 +67,7 @@ struct Op {
     // OP_SMALL: x, y nodes
     int x = -1, y = -1;
     std::vector<int> shared;
+    std::vector<int> fy;    // Y's free legs in the order they take in the product
     // OP_GEMM: operand storages, shapes
     int sa = -1, sb = -1;
     bool a_km = true, b_km = true;
@@ -146,6 +147,16 @@ struct qx_ctx {
         double flops = 0;
         int64_t launches = 0, batches = 0;
     } gc;
+
+    // Concurrent issue: op j follows the earlier ops in deps[j] (data and space-reuse hazards), so
+    // independent branches of the contraction tree run side by side on the handle's extra streams
+    // (their order in a captured graph becomes graph edges).  n_streams 1: all on `stream`, in order.
+    int n_streams = 8;
+    std::vector<std::vector<int>> deps;
+    std::vector<cudaStream_t> dstreams;
+    std::vector<cudaEvent_t> op_ev;    // one per op
+    std::vector<cudaEvent_t> join_ev;  // one per extra stream
+    cudaEvent_t fork_ev = nullptr;
 
     // profiling: an event pair around every launch, folded per kernel kind on read
     bool profiling = false;
@@ -390,6 +401,55 @@ static int64_t assign_offsets(qx_ctx* h, bool variant) {
 
 static void build_persistent_program(qx_ctx* h);
 
+// Storages an op reads and writes (leaves are read-only and not listed), and whether it uses the
+// per-tensor scale words of the workspace (prep-based tensor-core steps).
+static void op_access(const qx_ctx* h, const Op& op, std::vector<int>* rd, std::vector<int>* wr, bool* scale) {
+    auto node_st = [&](int node) { return h->nodes[node].leaf ? -1 : h->nodes[node].storage; };
+    std::vector<int> r;
+    if (op.type == OP_PERM) r = {node_st(op.src)};
+    else if (op.type == OP_SMALL) r = {node_st(op.x), node_st(op.y)};
+    else r = {op.sa, op.sb};
+    rd->clear();
+    for (int x : r)
+        if (x >= 0) rd->push_back(x);
+    *wr = {op.dst};
+    if (op.spa >= 0) wr->push_back(op.spa);  // split parts: written by the prep, read by the GEMM
+    if (op.spb >= 0) wr->push_back(op.spb);
+    *scale = op.type == OP_GEMM && op.tc && op.tc != TC_FORM_3XTF32_DIRECT;
+}
+
+// Hazards between ops, in plan order: op j follows op i < j when j reads storage that i writes,
+// writes storage that i reads, or writes storage that i writes.  Storages of the same region
+// (per-pair or invariant) conflict when their entry ranges overlap, since the liveness allocator
+// gives the space of dead tensors to later ones.  Ops using the scale words follow one another.
+static void compute_deps(qx_ctx* h) {
+    const size_t n = h->ops.size();
+    std::vector<std::vector<int>> rd(n), wr(n);
+    std::vector<char> scale(n, 0);
+    for (size_t j = 0; j < n; ++j) {
+        bool sc;
+        op_access(h, h->ops[j], &rd[j], &wr[j], &sc);
+        scale[j] = sc;
+    }
+    auto overlap = [&](int a, int b) {
+        const Storage& A = h->stor[a];
+        const Storage& B = h->stor[b];
+        if (A.variant != B.variant) return false;
+        return A.off < B.off + align_up(B.entries, kAlignEntries) && B.off < A.off + align_up(A.entries, kAlignEntries);
+    };
+    auto any = [&](const std::vector<int>& x, const std::vector<int>& y) {
+        for (int a : x)
+            for (int b : y)
+                if (overlap(a, b)) return true;
+        return false;
+    };
+    h->deps.assign(n, {});
+    for (size_t j = 0; j < n; ++j)
+        for (size_t i = 0; i < j; ++i)
+            if ((scale[i] && scale[j]) || any(wr[i], rd[j]) || any(rd[i], wr[j]) || any(wr[i], wr[j]))
+                h->deps[j].push_back((int)i);
+}
+
 static int compile_plan(qx_ctx* h, const int64_t* order, int64_t n_steps, const int64_t* sliced, int32_t n_sliced) {
     const int64_t N = h->n_tensors;
     if (n_steps != N - 1)
@@ -440,16 +500,104 @@ static int compile_plan(qx_ctx* h, const int64_t* order, int64_t n_steps, const 
         }
         h->nodes.push_back(nd);
     }
+    // Leg sets, closed-output status and consuming step of every node, known before any layout is
+    // chosen, so that a step can lay out its product the way the step that consumes it reads it.
     std::vector<char> used(N + n_steps, 0);
-    const int gemm_bits = h->opt.gemm_min_bits > 0 ? h->opt.gemm_min_bits : 5;
-    h->peak_entries = 1;
+    std::vector<std::vector<int>> lset(N + n_steps);
+    std::vector<char> lone(N + n_steps, 0);
+    std::vector<int64_t> consumer(N + n_steps, -1);
+    for (int64_t t = 0; t < N; ++t) {
+        lset[t] = h->nodes[t].legs;
+        lone[t] = h->nodes[t].const_one;
+    }
     for (int64_t t = 0; t < n_steps; ++t) {
         const int64_t ia = order[2 * t], ib = order[2 * t + 1];
         if (ia < 0 || ib < 0 || ia >= N + t || ib >= N + t || ia == ib || used[ia] || used[ib])
             return fail(h, QX_EINVAL, "plan step %lld uses an invalid or consumed id (%lld, %lld)", (long long)t,
                         (long long)ia, (long long)ib);
         used[ia] = used[ib] = 1;
-        const int a = (int)ia, b = (int)ib;
+        consumer[ia] = consumer[ib] = t;
+        if (lone[ia] || lone[ib]) {
+            lset[N + t] = lone[ia] ? lset[ib] : lset[ia];
+            lone[N + t] = lone[ia] && lone[ib];
+            continue;
+        }
+        for (int e : lset[ia])
+            if (std::find(lset[ib].begin(), lset[ib].end(), e) == lset[ib].end()) lset[N + t].push_back(e);
+        for (int e : lset[ib])
+            if (std::find(lset[ia].begin(), lset[ia].end(), e) == lset[ia].end()) lset[N + t].push_back(e);
+    }
+    const int gemm_bits = h->opt.gemm_min_bits > 0 ? h->opt.gemm_min_bits : 5;
+    auto has = [](const std::vector<int>& v, int e) { return std::find(v.begin(), v.end(), e) != v.end(); };
+    // Legs of node x that the GEMM consuming it contracts (empty when no GEMM step consumes x: the root,
+    // or a gather step, which reads its operands at any strides).  Re-labelling steps are followed.
+    // *other is the node x is contracted with.
+    auto next_shared = [&](int64_t x, int64_t* other) {
+        std::vector<int> s2;
+        int64_t c = consumer[x];
+        while (c >= 0 && (lone[order[2 * c]] || lone[order[2 * c + 1]])) {
+            x = N + c;
+            c = consumer[x];
+        }
+        if (c < 0) return s2;
+        const int64_t d = order[2 * c] == x ? order[2 * c + 1] : order[2 * c];
+        *other = d;
+        for (int e : lset[x])
+            if (has(lset[d], e)) s2.push_back(e);
+        const int k2 = (int)s2.size(), fx = (int)(lset[x].size() - k2), fd = (int)(lset[d].size() - k2);
+        const bool big = k2 >= gemm_bits && fx >= gemm_bits && fd >= gemm_bits;
+        const bool small = (lset[x].size() <= 10 && k2 <= kSmallMaxK && fx <= kSmallMaxN) ||
+                           (lset[d].size() <= 10 && k2 <= kSmallMaxK && fd <= kSmallMaxN);
+        if (small && !big) s2.clear();
+        return s2;
+    };
+    // The product of step t is stored as [f1 | f2].  Where a block's legs can be put in any order at no
+    // cost (the operand is permuted anyway, or the kernel addresses it per bit), order them to leave the
+    // legs that the next GEMM contracts at the end of the product (read K-major there, no permute),
+    // else at its start (M-major).
+    auto lay_out = [&](int64_t t, std::vector<int>& f1, bool r1, std::vector<int>& f2, bool r2) {
+        int64_t d = -1;
+        const std::vector<int> s2 = next_shared(N + t, &d);
+        if (s2.empty()) return;
+        // a block's contracted legs follow the partner's stored order when the partner exists
+        auto rank_in_d = [&](int e) {
+            if (d < 0 || d >= N + t) return 0;
+            const auto& dl = h->nodes[d].legs;
+            return (int)(std::find(dl.begin(), dl.end(), e) - dl.begin());
+        };
+        auto arrange = [&](std::vector<int>& blk, bool last) {
+            std::vector<int> in, out;
+            for (int e : blk) (has(s2, e) ? in : out).push_back(e);
+            std::stable_sort(in.begin(), in.end(), [&](int x, int y) { return rank_in_d(x) < rank_in_d(y); });
+            blk = last ? out : in;
+            const std::vector<int>& tail = last ? in : out;
+            blk.insert(blk.end(), tail.begin(), tail.end());
+        };
+        auto count_in = [&](const std::vector<int>& blk) {
+            int n = 0;
+            for (int e : blk) n += has(s2, e);
+            return n;
+        };
+        auto edge_ok = [&](const std::vector<int>& blk, bool last) {  // s2 legs already at that end
+            const int n = count_in(blk), m = (int)blk.size();
+            for (int i = 0; i < n; ++i)
+                if (!has(s2, blk[last ? m - 1 - i : i])) return false;
+            return true;
+        };
+        const int i1 = count_in(f1), i2 = count_in(f2);
+        if (i1 == 0 && (r2 || edge_ok(f2, true))) {
+            if (r2) arrange(f2, true);
+        } else if (i2 == (int)f2.size() && i1 > 0 && (r1 || edge_ok(f1, true))) {
+            if (r1) arrange(f1, true);
+        } else if (i2 == 0 && (r1 || edge_ok(f1, false))) {
+            if (r1) arrange(f1, false);
+        } else if (i1 == (int)f1.size() && i2 > 0 && (r2 || edge_ok(f2, false))) {
+            if (r2) arrange(f2, false);
+        }
+    };
+    h->peak_entries = 1;
+    for (int64_t t = 0; t < n_steps; ++t) {
+        const int a = (int)order[2 * t], b = (int)order[2 * t + 1];
         const Node A = h->nodes[a], B = h->nodes[b];
         if (A.const_one || B.const_one) {  // contracting with a closed output is a re-labelling
             Node c = A.const_one ? B : A;
@@ -492,11 +640,13 @@ static int compile_plan(qx_ctx* h, const int64_t* order, int64_t n_steps, const 
                 if (std::find(shared.begin(), shared.end(), e) == shared.end()) fx.push_back(e);
             for (int e : Y.legs)
                 if (std::find(shared.begin(), shared.end(), e) == shared.end()) fy.push_back(e);
+            lay_out(t, fx, false, fy, true);
             std::vector<int> cl = fx;
             cl.insert(cl.end(), fy.begin(), fy.end());
             const int st = new_storage(h, (int64_t)1 << cl.size(), variant, t);
             Op op{};
             op.type = OP_SMALL;
+            op.fy = fy;
             op.variant = variant;
             op.step = t;
             op.x = xn;
@@ -529,12 +679,15 @@ static int compile_plan(qx_ctx* h, const int64_t* order, int64_t n_steps, const 
             return !X.leaf && X.fix.empty() && X.legs == want;
         };
         struct Choice { std::vector<int> S; bool pa, pb, akm, bkm; double cost; };
-        std::vector<std::vector<int>> cands = {shared};
+        // the contracted legs in either operand's stored order
+        std::vector<std::vector<int>> cands(1);
+        for (int e : GA.legs)
+            if (has(shared, e)) cands[0].push_back(e);
         {
             std::vector<int> sB;
             for (int e : GB.legs)
-                if (std::find(shared.begin(), shared.end(), e) != shared.end()) sB.push_back(e);
-            if (sB != shared) cands.push_back(sB);
+                if (has(shared, e)) sB.push_back(e);
+            if (sB != cands[0]) cands.push_back(sB);
         }
         // The direct 3xTF32 kernel splits operands in shared memory and reads them K-major through TMA;
         // the prep-based kernel streams pre-split parts (about (40 M + 72 N) K extra bytes) but leaves
@@ -560,6 +713,7 @@ static int compile_plan(qx_ctx* h, const int64_t* order, int64_t n_steps, const 
             c.cost = (c.pa ? (double)node_entries(GA) : 0.0) + (c.pb ? (double)node_entries(GB) : 0.0);
             if (best.cost < 0 || c.cost < best.cost) best = c;
         }
+        lay_out(t, fA, best.pa, fB, best.pb);
         Op g{};
         g.type = OP_GEMM;
         g.variant = variant;
@@ -642,6 +796,7 @@ static int compile_plan(qx_ctx* h, const int64_t* order, int64_t n_steps, const 
     h->inv_entries = assign_offsets(h, false);
     h->flops_inv = h->flops_item = 0;
     for (const Op& op : h->ops) (op.variant ? h->flops_item : h->flops_inv) += op.flops;
+    compute_deps(h);
     build_persistent_program(h);
     h->have_plan = true;
     return QX_OK;
@@ -780,10 +935,10 @@ static SmallDesc small_desc(const qx_ctx* h, const Op& op) {
         d.xk_pos[i] = (int8_t)X.pos[std::find(X.legs.begin(), X.legs.end(), e) - X.legs.begin()];
         d.yk_pos[i] = (int8_t)Y.pos[std::find(Y.legs.begin(), Y.legs.end(), e) - Y.legs.begin()];
     }
-    std::vector<int> fy;
-    for (size_t j = 0; j < Y.legs.size(); ++j)
-        if (std::find(op.shared.begin(), op.shared.end(), Y.legs[j]) == op.shared.end()) fy.push_back((int)j);
-    for (int i = 0; i < op.nb; ++i) d.yn_pos[i] = (int8_t)Y.pos[fy[op.nb - 1 - i]];
+    for (int i = 0; i < op.nb; ++i) {
+        const int e = op.fy[op.nb - 1 - i];
+        d.yn_pos[i] = (int8_t)Y.pos[std::find(Y.legs.begin(), Y.legs.end(), e) - Y.legs.begin()];
+    }
     return d;
 }
 
@@ -884,7 +1039,7 @@ static double op_bytes(const qx_ctx* h, const Op& op) {
     return c + 8.0 * (double)(h->stor[op.sa].entries + h->stor[op.sb].entries);
 }
 
-static int run_op(qx_ctx* h, const Op& op, const ItemCtx& ic, int64_t n_items) {
+static int run_op(qx_ctx* h, const Op& op, const ItemCtx& ic, int64_t n_items, cudaStream_t st) {
     float2* dp;
     int64_t dis;
     storage_addr(h, op.dst, &dp, &dis);
@@ -902,15 +1057,15 @@ static int run_op(qx_ctx* h, const Op& op, const ItemCtx& ic, int64_t n_items) {
                                (prep ? prep_bytes : op_bytes(h, op)) * (double)n_items, &slot);
     if (e != cudaSuccess) return fail(h, QX_ECUDA, "profiling event: %s", cudaGetErrorString(e));
     if (op.type == OP_PERM) {
-        e = launch_permute(perm_desc(h, op), ic, n_items, dp, dis, h->stream);
+        e = launch_permute(perm_desc(h, op), ic, n_items, dp, dis, st);
     } else if (op.type == OP_SMALL) {
-        e = launch_small(small_desc(h, op), ic, n_items, dp, dis, h->stream);
+        e = launch_small(small_desc(h, op), ic, n_items, dp, dis, st);
     } else if (!op.tc) {
         float2 *ap, *bp;
         int64_t ais, bis;
         storage_addr(h, op.sa, &ap, &ais);
         storage_addr(h, op.sb, &bp, &bis);
-        e = launch_gemm_c64(ap, ais, op.a_km, bp, bis, op.b_km, dp, dis, op.mb, op.nb, op.kb, n_items, h->stream);
+        e = launch_gemm_c64(ap, ais, op.a_km, bp, bis, op.b_km, dp, dis, op.mb, op.nb, op.kb, n_items, st);
     } else if (op.tc == TC_FORM_3XTF32_DIRECT) {
         TcArgs g{};
         float2 *ap, *bp;
@@ -931,7 +1086,7 @@ static int run_op(qx_ctx* h, const Op& op, const ItemCtx& ic, int64_t n_items) {
         g.n_items = n_items;
         g.limit = h->opt.timeout_cycles > 0 ? h->opt.timeout_cycles : 2000000000ll;
         g.err = (int*)(h->ws + h->off_err);
-        e = launch_tc2_gemm(g, h->stream);
+        e = launch_tc2_gemm(g, st);
     } else {
         TcArgs g{};
         float2 *ap, *bp, *pa, *pb;
@@ -960,10 +1115,10 @@ static int run_op(qx_ctx* h, const Op& op, const ItemCtx& ic, int64_t n_items) {
         g.limit = h->opt.timeout_cycles > 0 ? h->opt.timeout_cycles : 2000000000ll;
         g.err = (int*)(h->ws + h->off_err);
         g.amax = (float*)(h->ws + h->off_err + 16);
-        e = launch_tc_prep(op.tc, g, h->stream);
+        e = launch_tc_prep(op.tc, g, st);
         if (e == cudaSuccess) e = prof_end(h, slot);
         if (e == cudaSuccess) e = prof_begin(h, QX_KERNEL_TC_GEMM, op.flops * (double)n_items, op_bytes(h, op) * (double)n_items, &slot);
-        if (e == cudaSuccess) e = launch_tc_gemm(op.tc, g, h->stream);
+        if (e == cudaSuccess) e = launch_tc_gemm(op.tc, g, st);
         h->last_launches += 2;
     }
     if (e != cudaSuccess) return fail(h, QX_ECUDA, "kernel launch failed: %s", cudaGetErrorString(e));
@@ -1065,6 +1220,93 @@ static int contract_persistent(qx_ctx* h, const uint8_t* d_bits, int64_t n_bits,
     return QX_OK;
 }
 
+// Issues the ops of one batch over the handle's streams.  An op goes to the stream whose last op
+// is one of its dependencies (the chain continues without a wait), else to the stream idle the
+// longest; it waits on the event of its latest dependency on every other stream.  Streams join the
+// handle's stream lazily at first use and all rejoin it at the end.  With one stream, or while
+// profiling (events around each launch on the handle's stream), everything runs on that stream.
+struct Dag {
+    qx_ctx* h;
+    bool on = false;
+    std::vector<int> stream_of, last_on;  // per op: stream this batch (-1 none); per stream: last op
+    std::vector<std::vector<int>> seen;   // seen[s][t]: latest op of stream t that stream s waited for
+    std::vector<char> forked;
+    explicit Dag(qx_ctx* hh) : h(hh) {}
+    int init() {
+        on = h->n_streams > 1 && !h->profiling && !h->ops.empty();
+        if (!on) return QX_OK;
+        const int S = h->n_streams - 1;  // extra streams next to the handle's own
+        while ((int)h->dstreams.size() < S) {
+            cudaStream_t st;
+            CUDA_TRY(h, cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+            h->dstreams.push_back(st);
+            cudaEvent_t e;
+            CUDA_TRY(h, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+            h->join_ev.push_back(e);
+        }
+        if (!h->fork_ev) CUDA_TRY(h, cudaEventCreateWithFlags(&h->fork_ev, cudaEventDisableTiming));
+        while (h->op_ev.size() < h->ops.size()) {
+            cudaEvent_t e;
+            CUDA_TRY(h, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+            h->op_ev.push_back(e);
+        }
+        return QX_OK;
+    }
+    cudaStream_t stream(int s) const { return s == 0 ? h->stream : h->dstreams[s - 1]; }
+    int fork() {
+        if (!on) return QX_OK;
+        const int S = h->n_streams;
+        stream_of.assign(h->ops.size(), -1);
+        last_on.assign(S, -1);
+        seen.assign(S, std::vector<int>(S, -1));
+        forked.assign(S, 0);
+        forked[0] = 1;
+        CUDA_TRY(h, cudaEventRecord(h->fork_ev, h->stream));
+        return QX_OK;
+    }
+    int issue(int j, const ItemCtx& ic, int64_t n_items) {
+        if (!on) return run_op(h, h->ops[j], ic, n_items, h->stream);
+        const int S = h->n_streams;
+        int s = -1;
+        for (int i : h->deps[j]) {
+            const int t = stream_of[i];
+            if (t >= 0 && last_on[t] == i && (s < 0 || i > last_on[s])) s = t;
+        }
+        if (s < 0)
+            for (int t = 0; t < S; ++t)
+                if (s < 0 || last_on[t] < last_on[s]) s = t;
+        if (!forked[s]) {
+            CUDA_TRY(h, cudaStreamWaitEvent(stream(s), h->fork_ev, 0));
+            forked[s] = 1;
+        }
+        std::vector<int> latest(S, -1);
+        for (int i : h->deps[j]) {
+            const int t = stream_of[i];
+            if (t >= 0 && t != s) latest[t] = std::max(latest[t], i);
+        }
+        for (int t = 0; t < S; ++t)
+            if (latest[t] > seen[s][t]) {
+                CUDA_TRY(h, cudaStreamWaitEvent(stream(s), h->op_ev[latest[t]], 0));
+                seen[s][t] = latest[t];
+            }
+        int rc = run_op(h, h->ops[j], ic, n_items, stream(s));
+        if (rc) return rc;
+        CUDA_TRY(h, cudaEventRecord(h->op_ev[j], stream(s)));
+        stream_of[j] = s;
+        last_on[s] = j;
+        return QX_OK;
+    }
+    int join() {
+        if (!on) return QX_OK;
+        for (int s = 1; s < h->n_streams; ++s)
+            if (forked[s]) {
+                CUDA_TRY(h, cudaEventRecord(h->join_ev[s - 1], stream(s)));
+                CUDA_TRY(h, cudaStreamWaitEvent(h->stream, h->join_ev[s - 1], 0));
+            }
+        return QX_OK;
+    }
+};
+
 static int contract_impl(qx_ctx* h, const uint8_t* d_bits, int64_t n_bits, int64_t s_begin, int64_t s_end,
                          double* d_amps) {
     const int64_t n_o = (int64_t)1 << n_open(h);
@@ -1090,12 +1332,10 @@ static int contract_impl(qx_ctx* h, const uint8_t* d_bits, int64_t n_bits, int64
     ic.bits = d_bits;
     ic.n_b = 1;
     ic.n_items = 1;
-    // prologue: everything that no slice or bitstring touches
-    for (const Op& op : h->ops)
-        if (!op.variant) {
-            int rc = run_op(h, op, ic, 1);
-            if (rc) return rc;
-        }
+    const ItemCtx ic_inv = ic;
+    Dag dag(h);
+    int rc = dag.init();
+    if (rc) return rc;
     // batches of (slice, bitstring) pairs
     int64_t nb_batch, ns_batch;
     if (h->items_cap >= n_bits) {
@@ -1116,6 +1356,10 @@ static int contract_impl(qx_ctx* h, const uint8_t* d_bits, int64_t n_bits, int64
             sd.obit_pos[ob] = (int8_t)R.pos[j];
         }
     }
+    // The prologue (everything that no slice or bitstring touches) is issued together with the first
+    // batch of (slice, bitstring) pairs, so independent branches of both overlap; every batch ends with
+    // all streams joined before its slice sum, and the next batch reuses the per-pair space.
+    bool prologue = true;
     for (int64_t s0 = s_begin; s0 < s_end; s0 += ns_batch) {
         const int64_t ns = std::min(ns_batch, s_end - s0);
         for (int64_t b0 = 0; b0 < n_bits; b0 += nb_batch) {
@@ -1124,11 +1368,14 @@ static int contract_impl(qx_ctx* h, const uint8_t* d_bits, int64_t n_bits, int64
             ic.b0 = b0;
             ic.n_b = (int32_t)nb;
             ic.n_items = ns * nb;
-            for (const Op& op : h->ops)
-                if (op.variant) {
-                    int rc = run_op(h, op, ic, ic.n_items);
-                    if (rc) return rc;
-                }
+            if ((rc = dag.fork())) return rc;
+            for (size_t j = 0; j < h->ops.size(); ++j) {
+                const Op& op = h->ops[j];
+                if (!op.variant && !prologue) continue;
+                if ((rc = dag.issue((int)j, op.variant ? ic : ic_inv, op.variant ? ic.n_items : 1))) return rc;
+            }
+            prologue = false;
+            if ((rc = dag.join())) return rc;
             sd.n_s = (int32_t)ns;
             size_t slot;
             const double sum_bytes = (double)(ns * nb << sd.open_bits) * 8.0 + (double)(nb << sd.open_bits) * 64.0;
@@ -1231,6 +1478,10 @@ void qx_destroy(qx_handle h) {
     if (!h) return;
     drop_graph(h);
     for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
+    for (cudaEvent_t e : h->op_ev) cudaEventDestroy(e);
+    for (cudaEvent_t e : h->join_ev) cudaEventDestroy(e);
+    if (h->fork_ev) cudaEventDestroy(h->fork_ev);
+    for (cudaStream_t st : h->dstreams) cudaStreamDestroy(st);
     if (h->ws_owned && h->ws) {
         cudaSetDevice(h->device);
         cudaFree(h->ws);
@@ -1414,6 +1665,29 @@ int qx_describe_plan(qx_handle h, char* buf, int64_t len, int64_t* needed) {
                      (long long)op.step, kind, op.variant ? "pair" : "shared", op.mb, op.kb, op.nb, (int)op.a_km,
                      (int)op.b_km);
         out += line;
+        // storages as region:offset+entries (entries rounded up as allocated), then the dependencies
+        std::vector<int> rd, wr;
+        bool sc;
+        op_access(h, op, &rd, &wr, &sc);
+        for (int pass = 0; pass < 2; ++pass) {
+            out.pop_back();
+            out += pass ? " writes=" : " reads=";
+            const std::vector<int>& v = pass ? wr : rd;
+            for (size_t k = 0; k < v.size(); ++k) {
+                const Storage& st = h->stor[v[k]];
+                snprintf(line, sizeof line, "%s%s:%lld+%lld", k ? "," : "", st.variant ? "pair" : "shared",
+                         (long long)st.off, (long long)align_up(st.entries, kAlignEntries));
+                out += line;
+            }
+            out += "\n";
+        }
+        out.pop_back();
+        out += sc ? " scale=1 after=" : " scale=0 after=";
+        for (size_t k = 0; k < h->deps[i].size(); ++k) {
+            snprintf(line, sizeof line, "%s%d", k ? "," : "", h->deps[i][k]);
+            out += line;
+        }
+        out += "\n";
     }
     if (needed) *needed = (int64_t)out.size() + 1;
     if (buf && len > 0) {
@@ -1428,6 +1702,14 @@ int qx_set_graphs(qx_handle h, int enable) {
     if (!h) return QX_EINVAL;
     drop_graph(h);
     h->graphs = enable != 0;
+    return QX_OK;
+}
+
+int qx_set_streams(qx_handle h, int32_t n_streams) {
+    if (!h) return QX_EINVAL;
+    if (n_streams < 1 || n_streams > 32) return fail(h, QX_EINVAL, "n_streams %d out of range [1, 32]", n_streams);
+    drop_graph(h);
+    h->n_streams = n_streams;
     return QX_OK;
 }
 

@@ -108,22 +108,49 @@ __global__ void __launch_bounds__(256) k_permute(const PermDesc d, const PermTab
     const int n = 1 << d.t;
     const int64_t tiles = (int64_t)1 << d.n_outer;
     const int64_t jobs = tiles * n_items;
-    for (int64_t job = blockIdx.x; job < jobs; job += gridDim.x) {
+    // input and output bases of a job (pair, tile of the outer bits)
+    auto bases = [&](int64_t job, int64_t* ib, int64_t* ob) {
         const int64_t item = job >> d.n_outer;
         uint64_t u = (uint64_t)(job & (tiles - 1));
-        int64_t ib = fix_offset(d.in, ic, item), ob = item * out_is;
+        *ib = fix_offset(d.in, ic, item);
+        *ob = item * out_is;
         while (u) {
             const int i = __ffsll((long long)u) - 1;
-            ib += tb.outer_in[i];
-            ob += tb.outer_out[i];
+            *ib += tb.outer_in[i];
+            *ob += tb.outer_out[i];
             u &= u - 1;
         }
+    };
+    // software pipeline: the next job's tile is loaded into registers while the current one is
+    // stored, so every thread keeps up to four loads in flight during its stores
+    float2 v[4];
+    auto load = [&](int64_t job) {
+        int64_t ib, ob;
+        bases(job, &ib, &ob);
         const float2* __restrict__ src = d.in.base + ib;
-        for (int j = tid; j < n; j += 256) tile[pad32(j)] = src[s_in[j & 31] + s_in[32 + (j >> 5)]];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int j = tid + 256 * k;
+            if (j < n) v[k] = src[s_in[j & 31] + s_in[32 + (j >> 5)]];
+        }
+    };
+    int64_t job = blockIdx.x;
+    if (job < jobs) load(job);
+    while (job < jobs) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int j = tid + 256 * k;
+            if (j < n) tile[pad32(j)] = v[k];
+        }
         __syncthreads();
+        int64_t ib, ob;
+        bases(job, &ib, &ob);
+        const int64_t next = job + gridDim.x;
+        if (next < jobs) load(next);
         float2* __restrict__ dst = out + ob;
         for (int j = tid; j < n; j += 256) dst[s_out[j & 31] + s_out[32 + (j >> 5)]] = tile[pad32(s_map[j & 31] | s_map[32 + (j >> 5)])];
         __syncthreads();
+        job = next;
     }
 }
 

@@ -25,7 +25,7 @@ EXPORTS = ("qx_create", "qx_destroy", "qx_last_error", "qx_set_options", "qx_bui
            "qx_contract_slices", "qx_contract_slices_device", "qx_last_stats", "qx_set_profiling",
            "qx_profile_read", "qx_contract_device_static", "qx_device_status", "qx_group_create",
            "qx_group_scratch_size", "qx_group_bind", "qx_group_run", "qx_group_last_error", "qx_group_destroy",
-           "qx_set_graphs", "qx_describe_plan")
+           "qx_set_graphs", "qx_set_streams", "qx_describe_plan")
 QX_STATIC_SCRATCH_BYTES = 64 << 20
 KERNEL_KINDS = ("permute", "small", "gemm", "sum", "tc_prep", "tc_gemm", "persist")
 
@@ -77,6 +77,7 @@ def load(path=None):
         "qx_set_profiling": ([vp, ctypes.c_int], ctypes.c_int),
         "qx_device_status": ([vp], ctypes.c_int),
         "qx_set_graphs": ([vp, ctypes.c_int], ctypes.c_int),
+        "qx_set_streams": ([vp, i32], ctypes.c_int),
         "qx_describe_plan": ([vp, ctypes.c_char_p, i64, ctypes.POINTER(i64)], ctypes.c_int),
         "qx_group_create": ([ctypes.POINTER(vp), ctypes.POINTER(vp), i32, ctypes.POINTER(vp), ctypes.POINTER(i64),
                              ctypes.POINTER(vp), i32], ctypes.c_int),
@@ -205,6 +206,10 @@ def qx_describe_plan(h):
 
 def qx_set_graphs(h, enable):
     _check(h, load().qx_set_graphs(h, 1 if enable else 0))
+
+
+def qx_set_streams(h, n_streams):
+    _check(h, load().qx_set_streams(h, int(n_streams)))
 
 
 def qx_device_status(h):

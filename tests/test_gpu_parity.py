@@ -277,6 +277,50 @@ def test_graph_replay_matches_eager_and_follows_new_data(qx):
     assert np.array_equal(out.cpu().numpy(), got)
 
 
+@pytest.mark.parametrize("precision", [0, 1, 2, 3])
+def test_concurrent_issue_is_bit_identical_to_in_order(qx, precision):
+    """Steps issued over several streams along the dependency lists give the same bits as in order."""
+    import torch
+    w = W.sliced()
+    st = torch.cuda.Stream()
+    runs = {}
+    for n_streams, max_items in ((1, 0), (8, 0), (3, 0), (1, 1000), (8, 1000)):
+        c = qx.Contractor(w.n_qubits, w.gates, w.open_mask, w.order, w.sliced, len(w.bitstrings),
+                          precision=precision, max_items=max_items, stream=st)
+        qx.qx_set_streams(c.h, n_streams)
+        d_bits = torch.from_numpy(w.bitstrings).cuda()
+        out = torch.empty((len(w.bitstrings), 1, 2), dtype=torch.float64, device="cuda")
+        got = []
+        for _ in range(3):  # eager, graph capture + launch, replay
+            with torch.cuda.stream(st):
+                c.contract_device(d_bits, out)
+            st.synchronize()
+            got.append(out.cpu().numpy().copy())
+        assert np.array_equal(got[0], got[1]) and np.array_equal(got[1], got[2])
+        if max_items:
+            assert c.stats()["batches"] > 1
+        runs[(n_streams, max_items)] = got[0]
+        c.close()
+    assert np.array_equal(runs[(8, 0)], runs[(1, 0)])
+    assert np.array_equal(runs[(3, 0)], runs[(1, 0)])
+    assert np.array_equal(runs[(8, 1000)], runs[(1, 1000)])
+    if precision <= 2:
+        ref = oracle.sv_amplitudes(w.n_qubits, w.gates, w.open_mask, w.bitstrings)
+        got = runs[(8, 0)][..., 0] + 1j * runs[(8, 0)][..., 1]
+        assert rel_l2(got, ref) <= TOL_C64
+
+
+def test_stream_count_is_checked(qx):
+    circ, om, order, sliced, bits = grid_case(3, 3, 6, 5, 1, 1, 2)
+    c = _contractor(qx, circ, om, order, sliced, 2)
+    for bad in (0, 33, -1):
+        with pytest.raises(qx.QXError):
+            qx.qx_set_streams(c.h, bad)
+    qx.qx_set_streams(c.h, 32)
+    ref = oracle.sv_amplitudes(circ.n_qubits, C.gates_to_records(circ), om, bits)
+    assert rel_l2(c.contract(bits), ref) <= TOL_C64
+
+
 def test_edge_cases(qx):
     # no bitstrings
     circ, om, order, sliced, bits = grid_case(2, 3, 4, 61, 1, 2, 3)
