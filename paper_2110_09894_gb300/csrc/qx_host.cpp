@@ -878,7 +878,8 @@ static Operand node_operand(const qx_ctx* h, int node) {
     return op;
 }
 
-static PermDesc perm_desc(const qx_ctx* h, const Op& op) {
+// lo: lowest input positions and output bits the tile must hold; max_t: tile bits
+static PermDesc perm_desc(const qx_ctx* h, const Op& op, int lo = kPermLoBits, int max_t = kPermTileBits) {
     PermDesc d{};
     d.in = node_operand(h, op.src);
     const Node& X = h->nodes[op.src];
@@ -889,7 +890,7 @@ static PermDesc perm_desc(const qx_ctx* h, const Op& op) {
         const int j = (int)(std::find(X.legs.begin(), X.legs.end(), leg) - X.legs.begin());
         d.in_pos[ob] = (int8_t)X.pos[j];
     }
-    const int L = std::min(5, r);
+    const int L = std::min(lo, r);
     std::vector<char> in_tile(r, 0);
     for (int ob = 0; ob < L; ++ob) in_tile[ob] = 1;
     std::vector<int> by_in(r);
@@ -898,7 +899,7 @@ static PermDesc perm_desc(const qx_ctx* h, const Op& op) {
     for (int i = 0; i < L; ++i) in_tile[by_in[i]] = 1;
     int t = 0;
     for (int ob = 0; ob < r; ++ob) t += in_tile[ob];
-    for (int ob = 0; ob < r && t < std::min(r, 10); ++ob)
+    for (int ob = 0; ob < r && t < std::min(r, max_t); ++ob)
         if (!in_tile[ob]) { in_tile[ob] = 1; ++t; }
     d.t = t;
     int k = 0;
@@ -981,7 +982,7 @@ static POp to_pop(const qx_ctx* h, const Op& op) {
     p.nb = op.nb;
     p.dst = h->stor[op.dst].off;
     if (op.type == OP_PERM) {
-        const PermDesc d = perm_desc(h, op);
+        const PermDesc d = perm_desc(h, op, 5, 10);  // the persistent kernel's tiles: 2^10 entries, 5 + 5 bits
         p.type = POP_PERM;
         p.x = pref_node(h, op.src);
         p.t = d.t;

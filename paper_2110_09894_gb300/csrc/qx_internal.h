@@ -39,28 +39,31 @@ struct Operand {
 };
 
 // Bit permutation out[y] = in[x]: output bit ob (0 = least significant) is
-// taken from input address position in_pos[ob].  The tile holds `t` bits:
-// tile_in lists them (as output-bit ids) by increasing input position,
-// tile_out by increasing output bit; `outer` lists the remaining output bits.
+// taken from input address position in_pos[ob].  The tile holds `t` bits
+// (at most kPermTileBits): tile_in lists them (as output-bit ids) by
+// increasing input position, tile_out by increasing output bit; `outer` lists
+// the remaining output bits.
+constexpr int kPermTileBits = 12;  // batched kernel: 2^12-entry tiles, 6 + 6 index bits
+constexpr int kPermLoBits = 6;
 struct PermDesc {
     Operand in;
     int32_t rank;
     int32_t t;
     int32_t n_outer;
     int8_t in_pos[kMaxRank];
-    int8_t tile_in[10];
-    int8_t tile_out[10];
+    int8_t tile_in[kPermTileBits];
+    int8_t tile_out[kPermTileBits];
     int8_t outer[kMaxRank];
 };
 
 // Address tables of a permutation tile, computed once on the host: entry j
-// of the tile (input order) sits at in_lo[j & 31] + in_hi[j >> 5] from the
+// of the tile (input order) sits at in_lo[j & 63] + in_hi[j >> 6] from the
 // tile's input base; entry j (output order) goes to out_lo[..] + out_hi[..]
 // from the output base and is read from tile slot map_lo[..] | map_hi[..];
 // outer bit i moves the bases by outer_in[i] / outer_out[i].
 struct PermTables {
-    int64_t in_lo[32], in_hi[32], out_lo[32], out_hi[32];
-    int32_t map_lo[32], map_hi[32];
+    int64_t in_lo[64], in_hi[64], out_lo[64], out_hi[64];
+    int32_t map_lo[64], map_hi[64];
     int64_t outer_in[kMaxRank], outer_out[kMaxRank];
 };
 

@@ -41,27 +41,29 @@ __device__ __forceinline__ void cfma(float2& acc, float2 a, float2 b) {
 }
 
 // ---------------------------------------------------------------------------------------------
-// Bit permutation through a shared-memory tile.  Reads walk the tile in input
-// order (the lowest input positions vary fastest, so warps read contiguous
-// runs) and writes walk it in output order (contiguous runs again); the tile
-// holds up to 2^10 entries with one float2 of padding per 32.
+// Bit permutation through a shared-memory tile of up to 2^12 entries.  The
+// tile spans the 6 lowest input positions and the 6 lowest output bits (plus
+// more output bits up to 12), so reads walk it in input order in contiguous
+// runs of 64 entries (512 bytes) and writes walk it in output order in runs of
+// 64 again; one float2 of padding per 32 entries.
 // ---------------------------------------------------------------------------------------------
 __device__ __forceinline__ int pad32(int j) { return j + (j >> 5); }
 
 void perm_tables(const PermDesc& d, PermTables* tb) {
+    constexpr int LO = kPermLoBits;
     const int t = d.t;
-    for (int j = 0; j < 32; ++j) {
+    for (int j = 0; j < (1 << LO); ++j) {
         int64_t a = 0, b = 0, c = 0, e = 0;
         int ml = 0, mh = 0;
-        for (int i = 0; i < 5; ++i) {
+        for (int i = 0; i < LO; ++i) {
             if (!((j >> i) & 1)) continue;
             if (i < t) {
                 a += (int64_t)1 << d.in_pos[d.tile_in[i]];
                 c += (int64_t)1 << d.tile_out[i];
             }
-            if (i + 5 < t) {
-                b += (int64_t)1 << d.in_pos[d.tile_in[i + 5]];
-                e += (int64_t)1 << d.tile_out[i + 5];
+            if (i + LO < t) {
+                b += (int64_t)1 << d.in_pos[d.tile_in[i + LO]];
+                e += (int64_t)1 << d.tile_out[i + LO];
             }
         }
         // where output-ordered tile bit i sits in the input-ordered tile index
@@ -69,9 +71,9 @@ void perm_tables(const PermDesc& d, PermTables* tb) {
             int r = 0;
             for (int k = 0; k < t; ++k)
                 if (d.tile_in[k] == d.tile_out[i]) r = k;
-            if (i < 5) {
+            if (i < LO) {
                 if ((j >> i) & 1) ml |= 1 << r;
-            } else if ((j >> (i - 5)) & 1) {
+            } else if ((j >> (i - LO)) & 1) {
                 mh |= 1 << r;
             }
         }
@@ -89,20 +91,24 @@ void perm_tables(const PermDesc& d, PermTables* tb) {
 }
 
 // Grid-stride over (pair, tile) jobs: the tables are loaded into shared memory
-// once per CTA, each job moves one tile of up to 2^10 entries.
-__global__ void __launch_bounds__(256) k_permute(const PermDesc d, const PermTables tb, const ItemCtx ic,
-                                                 float2* __restrict__ out, int64_t out_is, int64_t n_items) {
-    __shared__ float2 tile[1024 + 32];
-    __shared__ int64_t s_in[64], s_out[64];
-    __shared__ int s_map[64];
+// once per CTA, each job moves one tile.  Software pipeline: the next job's
+// tile is loaded into registers while the current one is stored, so every
+// thread keeps its loads in flight during its stores.
+constexpr int kPermThreads = 256, kPermPer = (1 << kPermTileBits) / kPermThreads;
+__global__ void __launch_bounds__(kPermThreads, 4) k_permute(const PermDesc d, const PermTables tb, const ItemCtx ic,
+                                                          float2* __restrict__ out, int64_t out_is, int64_t n_items) {
+    constexpr int LO = kPermLoBits, LM = (1 << LO) - 1;
+    __shared__ float2 tile[(1 << kPermTileBits) + (1 << kPermTileBits) / 32];
+    __shared__ int64_t s_in[128], s_out[128];
+    __shared__ int s_map[128];
     const int tid = threadIdx.x;
-    if (tid < 32) {
+    if (tid < 64) {
         s_in[tid] = tb.in_lo[tid];
-        s_in[32 + tid] = tb.in_hi[tid];
+        s_in[64 + tid] = tb.in_hi[tid];
         s_out[tid] = tb.out_lo[tid];
-        s_out[32 + tid] = tb.out_hi[tid];
+        s_out[64 + tid] = tb.out_hi[tid];
         s_map[tid] = tb.map_lo[tid];
-        s_map[32 + tid] = tb.map_hi[tid];
+        s_map[64 + tid] = tb.map_hi[tid];
     }
     __syncthreads();
     const int n = 1 << d.t;
@@ -121,25 +127,23 @@ __global__ void __launch_bounds__(256) k_permute(const PermDesc d, const PermTab
             u &= u - 1;
         }
     };
-    // software pipeline: the next job's tile is loaded into registers while the current one is
-    // stored, so every thread keeps up to four loads in flight during its stores
-    float2 v[4];
+    float2 v[kPermPer];
     auto load = [&](int64_t job) {
         int64_t ib, ob;
         bases(job, &ib, &ob);
         const float2* __restrict__ src = d.in.base + ib;
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const int j = tid + 256 * k;
-            if (j < n) v[k] = src[s_in[j & 31] + s_in[32 + (j >> 5)]];
+        for (int k = 0; k < kPermPer; ++k) {
+            const int j = tid + kPermThreads * k;
+            if (j < n) v[k] = src[s_in[j & LM] + s_in[64 + (j >> LO)]];
         }
     };
     int64_t job = blockIdx.x;
     if (job < jobs) load(job);
     while (job < jobs) {
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const int j = tid + 256 * k;
+        for (int k = 0; k < kPermPer; ++k) {
+            const int j = tid + kPermThreads * k;
             if (j < n) tile[pad32(j)] = v[k];
         }
         __syncthreads();
@@ -148,7 +152,8 @@ __global__ void __launch_bounds__(256) k_permute(const PermDesc d, const PermTab
         const int64_t next = job + gridDim.x;
         if (next < jobs) load(next);
         float2* __restrict__ dst = out + ob;
-        for (int j = tid; j < n; j += 256) dst[s_out[j & 31] + s_out[32 + (j >> 5)]] = tile[pad32(s_map[j & 31] | s_map[32 + (j >> 5)])];
+        for (int j = tid; j < n; j += kPermThreads)
+            dst[s_out[j & LM] + s_out[64 + (j >> LO)]] = tile[pad32(s_map[j & LM] | s_map[64 + (j >> LO)])];
         __syncthreads();
         job = next;
     }
@@ -172,8 +177,9 @@ cudaError_t launch_permute(const PermDesc& d, const ItemCtx& ic, int64_t n_items
     PermTables tb;
     perm_tables(d, &tb);
     const int64_t jobs = ((int64_t)1 << d.n_outer) * n_items;
-    const int64_t grid = std::min<int64_t>(jobs, (int64_t)sm_count() * 8);
-    k_permute<<<(unsigned)grid, 256, 0, st>>>(d, tb, ic, out, out_is, n_items);
+    if (d.t > kPermTileBits) return cudaErrorInvalidValue;
+    const int64_t grid = std::min<int64_t>(jobs, (int64_t)sm_count() * 4);  // 4 resident CTAs per SM (registers)
+    k_permute<<<(unsigned)grid, kPermThreads, 0, st>>>(d, tb, ic, out, out_is, n_items);
     return cudaGetLastError();
 }
 
