@@ -201,6 +201,25 @@ __device__ __forceinline__ void tc_commit(uint64_t* b) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(s_addr(b))
                  : "memory");
 }
+// In-register transpose of a 32 x 32 block held one row per lane (a[i] = element (lane, i)):
+// afterwards a[i] = element (i, lane).  Stage s swaps bit s of the lane index with bit s of the
+// register index through one exchange with lane ^ s per register pair.
+__device__ __forceinline__ void transpose32(float* a, int lane) {
+#pragma unroll
+    for (int s = 16; s >= 1; s >>= 1) {
+        const bool up = (lane & s) != 0;
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+            if (i & s) continue;
+            const int j = i | s;
+            const float send = up ? a[i] : a[j];
+            const float recv = __shfl_xor_sync(0xffffffffu, send, s);
+            if (up) a[i] = recv;
+            else a[j] = recv;
+        }
+    }
+}
+
 // 128-byte-swizzled K-major operand tile: rows of 128 B, 8-row groups 1024 B apart
 __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
     uint64_t d = 0;
@@ -385,10 +404,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 for (int j = 0; j < TC_BN; ++j) tot[j] *= inv;
             }
             // tiles are whole (rows and columns multiples of 128; see tc_shape_ok)
-            const int row = m0 + 32 * q + lane;
-            float4* d4 = (float4*)(C + (int64_t)item * c_is + (int64_t)row * N2 + n0);
+            float* cb = C + (int64_t)item * c_is + (int64_t)(m0 + 32 * q) * N2 + n0 + lane;
 #pragma unroll
-            for (int j = 0; j < TC_BN / 4; ++j) d4[j] = make_float4(tot[4 * j], tot[4 * j + 1], tot[4 * j + 2], tot[4 * j + 3]);
+            for (int b32 = 0; b32 < TC_BN / 32; ++b32) {
+                transpose32(tot + 32 * b32, lane);
+#pragma unroll
+                for (int r = 0; r < 32; ++r) cb[(int64_t)r * N2 + 32 * b32] = tot[32 * b32 + r];
+            }
         }
     }
     tc_fence_before();
@@ -611,12 +633,15 @@ __global__ void __launch_bounds__(TC2_THREADS, 1)
                 int64_t item;
                 int m0, n0;
                 job_of(g / nk, &item, &m0, &n0);
-                const int row = m0 + 32 * q + lane;
-                float4* d4 = (float4*)(C + item * c_is + (int64_t)row * N2 + n0 + (BN / 2) * half);
+                float* cb = C + item * c_is + (int64_t)(m0 + 32 * q) * N2 + n0 + (BN / 2) * half + lane;
 #pragma unroll
-                for (int j = 0; j < BN / 8; ++j) {
-                    d4[j] = make_float4(tot[4 * j], tot[4 * j + 1], tot[4 * j + 2], tot[4 * j + 3]);
-                    tot[4 * j] = tot[4 * j + 1] = tot[4 * j + 2] = tot[4 * j + 3] = 0.f;
+                for (int b32 = 0; b32 < BN / 64; ++b32) {
+                    transpose32(tot + 32 * b32, lane);
+#pragma unroll
+                    for (int r = 0; r < 32; ++r) {
+                        cb[(int64_t)r * N2 + 32 * b32] = tot[32 * b32 + r];
+                        tot[32 * b32 + r] = 0.f;
+                    }
                 }
             }
         }
