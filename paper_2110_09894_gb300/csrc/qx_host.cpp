@@ -68,6 +68,9 @@ struct Op {
     int x = -1, y = -1;
     std::vector<int> shared;
     std::vector<int> fy;    // Y's free legs in the order they take in the product
+    // output position of each bit of the kernel's natural product index (columns low, then rows);
+    // empty: the natural layout
+    std::vector<int8_t> out_pos;
     // OP_GEMM: operand storages, shapes
     int sa = -1, sb = -1;
     bool a_km = true, b_km = true;
@@ -152,6 +155,7 @@ struct qx_ctx {
     // independent branches of the contraction tree run side by side on the handle's extra streams
     // (their order in a captured graph becomes graph edges).  n_streams 1: all on `stream`, in order.
     int n_streams = 8;
+    bool fuse_layouts = true;  // products stored in the layout their consuming GEMM reads (batched executor)
     std::vector<std::vector<int>> deps;
     std::vector<cudaStream_t> dstreams;
     std::vector<cudaEvent_t> op_ev;    // one per op
@@ -532,7 +536,20 @@ static int compile_plan(qx_ctx* h, const int64_t* order, int64_t n_steps, const 
     // Legs of node x that the GEMM consuming it contracts (empty when no GEMM step consumes x: the root,
     // or a gather step, which reads its operands at any strides).  Re-labelling steps are followed.
     // *other is the node x is contracted with.
-    auto next_shared = [&](int64_t x, int64_t* other) {
+    const int plan_tc = h->opt.precision == QX_PREC_3XTF32       ? TC_FORM_3XTF32
+                        : h->opt.precision == QX_PREC_SPLIT_BF16  ? TC_FORM_BF16X3
+                        : h->opt.precision == QX_PREC_FP16_SCALED ? TC_FORM_FP16
+                                                                  : 0;
+    // the tensor-core kernels take products with these free / shared bits; both read their operands
+    // K-major (the direct kernel through TMA, the prep-based one best: an M-major operand makes its
+    // split pass a transpose)
+    auto tc_shape = [&](int fa, int fb, int kb) {
+        if (plan_tc && fa < 7 && fb >= 7) std::swap(fa, fb);
+        const bool direct = plan_tc == TC_FORM_3XTF32 && fa >= 7 && fb >= 5 && kb >= 4 && (fa <= 8 || fb <= 8);
+        return direct || (plan_tc && fa >= 7 && fb >= 6 && kb >= 5);
+    };
+    // *kmajor_only: the consuming GEMM runs on a tensor-core kernel
+    auto next_shared = [&](int64_t x, int64_t* other, bool* kmajor_only = nullptr) {
         std::vector<int> s2;
         int64_t c = consumer[x];
         while (c >= 0 && (lone[order[2 * c]] || lone[order[2 * c + 1]])) {
@@ -549,6 +566,7 @@ static int compile_plan(qx_ctx* h, const int64_t* order, int64_t n_steps, const 
         const bool small = (lset[x].size() <= 10 && k2 <= kSmallMaxK && fx <= kSmallMaxN) ||
                            (lset[d].size() <= 10 && k2 <= kSmallMaxK && fd <= kSmallMaxN);
         if (small && !big) s2.clear();
+        if (kmajor_only) *kmajor_only = order[2 * c] == x ? tc_shape(fx, fd, k2) : tc_shape(fd, fx, k2);
         return s2;
     };
     // The product of step t is stored as [f1 | f2].  Where a block's legs can be put in any order at no
@@ -594,6 +612,139 @@ static int compile_plan(qx_ctx* h, const int64_t* order, int64_t n_steps, const 
         } else if (i1 == (int)f1.size() && i2 > 0 && (r2 || edge_ok(f2, false))) {
             if (r2) arrange(f2, false);
         }
+    };
+    // A product with natural index [R | Cl] (row legs, then column legs, most significant first) can
+    // be written by its kernel straight into another leg order D, when D's lowest L positions hold the
+    // lowest L bits of one side (the kernel's lanes run along that side, so each store run stays
+    // whole); modes lists the (side is rows, L) pairs the kernel supports, best first.  A side whose
+    // order is free (rR / rC: its operand is permuted anyway, or addressed per bit) may be reordered
+    // to make this work.  D is the order the consuming GEMM reads without a permute: [free' | S2]
+    // (K-major), or [S2 | free'] (M-major) unless that GEMM runs on the direct kernel.  Returns D
+    // (empty: keep the natural layout) and updates R / Cl where their order was chosen here.
+    auto fused_layout = [&](int64_t t, std::vector<int>& R, bool rR, std::vector<int>& Cl, bool rC,
+                            std::initializer_list<std::pair<bool, int>> modes) -> std::vector<int> {
+        if (!h->fuse_layouts || h->opt.executor >= 2) return {};  // the persistent kernels store natural layouts
+        int64_t d = -1;
+        bool konly = false;
+        const std::vector<int> s2 = next_shared(N + t, &d, &konly);
+        if (s2.empty()) return {};
+        const int k = (int)s2.size();
+        // S2 order (lowest first) of a partner that is stored already in a layout the consumer reads
+        std::vector<int> fixed;
+        if (d >= 0 && d < N + t) {
+            const Node& P = h->nodes[d];
+            if (!P.leaf && P.fix.empty()) {
+                const int r = (int)P.legs.size();
+                bool suf = true, pre = true;
+                for (int i = 0; i < k; ++i) {
+                    suf = suf && has(s2, P.legs[r - 1 - i]);
+                    pre = pre && has(s2, P.legs[i]);
+                }
+                if (suf)
+                    for (int i = 0; i < k; ++i) fixed.push_back(P.legs[r - 1 - i]);
+                else if (pre && !konly)
+                    for (int i = 0; i < k; ++i) fixed.push_back(P.legs[k - 1 - i]);
+            }
+        }
+        for (int kmaj = 1; kmaj >= (konly ? 1 : 0); --kmaj) {
+            for (const auto& md : modes) {
+                std::vector<int> X = md.first ? R : Cl;
+                const bool rx = md.first ? rR : rC;
+                const int L = md.second;
+                if ((int)X.size() < L) continue;
+                std::vector<int> low;  // the side's lowest L legs, lowest first
+                std::vector<int> s2low, freelow;
+                if (kmaj) {
+                    // lowest positions: S2 (all of it if k < L, then free legs of X)
+                    std::vector<int> want;
+                    if (!fixed.empty()) {
+                        want.assign(fixed.begin(), fixed.begin() + std::min(k, L));
+                    } else {
+                        for (auto it = X.rbegin(); it != X.rend() && (int)want.size() < std::min(k, L); ++it)
+                            if (has(s2, *it)) want.push_back(*it);
+                        if ((int)want.size() < std::min(k, L)) continue;
+                    }
+                    bool ok = true;
+                    for (int e : want) ok = ok && has(X, e);
+                    if (!ok) continue;
+                    if (rx) {
+                        low = want;
+                        for (auto it = X.rbegin(); it != X.rend() && (int)low.size() < L; ++it)
+                            if (!has(s2, *it)) low.push_back(*it);
+                        if ((int)low.size() < L) continue;
+                    } else {
+                        low.assign(X.rbegin(), X.rbegin() + L);
+                        for (int i = 0; i < (int)want.size(); ++i) ok = ok && low[i] == want[i];
+                        for (int i = (int)want.size(); i < L; ++i) ok = ok && !has(s2, low[i]);
+                        if (!ok) continue;
+                    }
+                    if (!fixed.empty()) {
+                        s2low = fixed;
+                    } else {
+                        s2low.assign(low.begin(), low.begin() + std::min(k, L));
+                        std::vector<int> nat = R;
+                        nat.insert(nat.end(), Cl.begin(), Cl.end());
+                        for (auto it = nat.rbegin(); it != nat.rend(); ++it)
+                            if (has(s2, *it) && !has(s2low, *it)) s2low.push_back(*it);
+                    }
+                    if (k < L) freelow.assign(low.begin() + k, low.end());
+                } else {
+                    // lowest positions: free legs of X; S2 on top
+                    if (rx) {
+                        for (auto it = X.rbegin(); it != X.rend() && (int)low.size() < L; ++it)
+                            if (!has(s2, *it)) low.push_back(*it);
+                        if ((int)low.size() < L) continue;
+                    } else {
+                        low.assign(X.rbegin(), X.rbegin() + L);
+                        bool ok = true;
+                        for (int e : low) ok = ok && !has(s2, e);
+                        if (!ok) continue;
+                    }
+                    freelow = low;
+                    if (!fixed.empty()) {
+                        s2low = fixed;
+                    } else {
+                        std::vector<int> nat = R;
+                        nat.insert(nat.end(), Cl.begin(), Cl.end());
+                        for (auto it = nat.rbegin(); it != nat.rend(); ++it)
+                            if (has(s2, *it)) s2low.push_back(*it);
+                    }
+                }
+                // the chosen side order: its other legs keep their order, `low` at the bottom
+                if (rx) {
+                    std::vector<int> nx;
+                    for (int e : X)
+                        if (!has(low, e)) nx.push_back(e);
+                    for (auto it = low.rbegin(); it != low.rend(); ++it) nx.push_back(*it);
+                    (md.first ? R : Cl) = nx;
+                }
+                std::vector<int> nat = R;
+                nat.insert(nat.end(), Cl.begin(), Cl.end());
+                std::vector<int> D;
+                if (kmaj) {
+                    for (int e : nat)
+                        if (!has(s2, e) && !has(freelow, e)) D.push_back(e);
+                    for (auto it = freelow.rbegin(); it != freelow.rend(); ++it) D.push_back(*it);
+                    for (auto it = s2low.rbegin(); it != s2low.rend(); ++it) D.push_back(*it);
+                } else {
+                    for (auto it = s2low.rbegin(); it != s2low.rend(); ++it) D.push_back(*it);
+                    for (int e : nat)
+                        if (!has(s2, e) && !has(freelow, e)) D.push_back(e);
+                    for (auto it = freelow.rbegin(); it != freelow.rend(); ++it) D.push_back(*it);
+                }
+                return D == nat ? std::vector<int>{} : D;
+            }
+        }
+        return {};
+    };
+    // output position of every natural bit (columns low, then rows) of [R | Cl] stored as D
+    auto out_positions = [&](const std::vector<int>& R, const std::vector<int>& Cl, const std::vector<int>& D) {
+        std::vector<int8_t> pos;
+        const int r = (int)D.size();
+        auto at = [&](int e) { return (int8_t)(r - 1 - (int)(std::find(D.begin(), D.end(), e) - D.begin())); };
+        for (auto it = Cl.rbegin(); it != Cl.rend(); ++it) pos.push_back(at(*it));
+        for (auto it = R.rbegin(); it != R.rend(); ++it) pos.push_back(at(*it));
+        return pos;
     };
     h->peak_entries = 1;
     for (int64_t t = 0; t < n_steps; ++t) {
@@ -641,12 +792,18 @@ static int compile_plan(qx_ctx* h, const int64_t* order, int64_t n_steps, const 
             for (int e : Y.legs)
                 if (std::find(shared.begin(), shared.end(), e) == shared.end()) fy.push_back(e);
             lay_out(t, fx, false, fy, true);
+            // gathers: lanes run along rows (X's free index); a thread's own outputs along Y's columns
+            const std::vector<int> D = fused_layout(t, fx, false, fy, true, {{true, 4}, {false, 2}, {true, 2}});
             std::vector<int> cl = fx;
             cl.insert(cl.end(), fy.begin(), fy.end());
             const int st = new_storage(h, (int64_t)1 << cl.size(), variant, t);
             Op op{};
             op.type = OP_SMALL;
             op.fy = fy;
+            if (!D.empty()) {
+                op.out_pos = out_positions(fx, fy, D);
+                cl = D;
+            }
             op.variant = variant;
             op.step = t;
             op.x = xn;
@@ -714,6 +871,16 @@ static int compile_plan(qx_ctx* h, const int64_t* order, int64_t n_steps, const 
             if (best.cost < 0 || c.cost < best.cost) best = c;
         }
         lay_out(t, fA, best.pa, fB, best.pb);
+        // the SIMT GEMM places its product with whole 128-byte runs along columns (16 complex); the
+        // tensor-core kernels and the dot kernel store their natural layout (measured on GB300: placed
+        // tensor-core stores and shorter SIMT runs cost more than the permutes they save)
+        std::vector<int> D;
+        {
+            const int mb = (int)fA.size(), nb = (int)fB.size();
+            const bool dot = mb + nb <= 4 && kb >= 8;
+            const bool tc = direct || (tc_form && mb >= 7 && nb >= 6 && kb >= 5);
+            if (!tc && !dot) D = fused_layout(t, fA, best.pa, fB, best.pb, {{false, 4}});
+        }
         Op g{};
         g.type = OP_GEMM;
         g.variant = variant;
@@ -753,6 +920,10 @@ static int compile_plan(qx_ctx* h, const int64_t* order, int64_t n_steps, const 
         cl.insert(cl.end(), fB.begin(), fB.end());
         const int st = new_storage(h, (int64_t)1 << cl.size(), variant, t);
         g.dst = st;
+        if (!D.empty()) {
+            g.out_pos = out_positions(fA, fB, D);
+            cl = D;
+        }
         if (direct) {
             g.tc = TC_FORM_3XTF32_DIRECT;
         } else if (tc_form && g.mb >= 7 && g.nb >= 6 && g.kb >= 5) {
@@ -915,6 +1086,13 @@ static PermDesc perm_desc(const qx_ctx* h, const Op& op, int lo = kPermLoBits, i
     return d;
 }
 
+static OutMap out_map(const Op& op) {
+    OutMap m{};
+    m.on = !op.out_pos.empty();
+    for (size_t i = 0; i < op.out_pos.size() && i < (size_t)kMaxRank; ++i) m.pos[i] = op.out_pos[i];
+    return m;
+}
+
 static SmallDesc small_desc(const qx_ctx* h, const Op& op) {
     SmallDesc d{};
     d.x = node_operand(h, op.x);
@@ -940,6 +1118,7 @@ static SmallDesc small_desc(const qx_ctx* h, const Op& op) {
         const int e = op.fy[op.nb - 1 - i];
         d.yn_pos[i] = (int8_t)Y.pos[std::find(Y.legs.begin(), Y.legs.end(), e) - Y.legs.begin()];
     }
+    d.om = out_map(op);
     return d;
 }
 
@@ -1016,7 +1195,7 @@ static void build_persistent_program(qx_ctx* h) {
     h->pops.clear();
     h->pops_inv.clear();
     for (const Op& op : h->ops)
-        if (op.tc) return;  // tensor-core steps run batched
+        if (op.tc || !op.out_pos.empty()) return;  // tensor-core steps and placed products run batched
     const Node& R = h->nodes[h->root];
     if (!R.variant) return;  // nothing depends on the pair
     // invariant ops write the invariant region: their program runs with that region as scratch
@@ -1066,7 +1245,8 @@ static int run_op(qx_ctx* h, const Op& op, const ItemCtx& ic, int64_t n_items, c
         int64_t ais, bis;
         storage_addr(h, op.sa, &ap, &ais);
         storage_addr(h, op.sb, &bp, &bis);
-        e = launch_gemm_c64(ap, ais, op.a_km, bp, bis, op.b_km, dp, dis, op.mb, op.nb, op.kb, n_items, st);
+        const OutMap om = out_map(op);
+        e = launch_gemm_c64(ap, ais, op.a_km, bp, bis, op.b_km, dp, dis, op.mb, op.nb, op.kb, n_items, st, &om);
     } else if (op.tc == TC_FORM_3XTF32_DIRECT) {
         TcArgs g{};
         float2 *ap, *bp;
@@ -1662,9 +1842,9 @@ int qx_describe_plan(qx_handle h, char* buf, int64_t len, int64_t* needed) {
             snprintf(line, sizeof line, "%zu step=%lld %s %s rank=%zu\n", i, (long long)op.step, kind,
                      op.variant ? "pair" : "shared", op.target_legs.size());
         else
-            snprintf(line, sizeof line, "%zu step=%lld %s %s m=%d k=%d n=%d a_kmajor=%d b_kmajor=%d\n", i,
+            snprintf(line, sizeof line, "%zu step=%lld %s %s m=%d k=%d n=%d a_kmajor=%d b_kmajor=%d scatter=%d\n", i,
                      (long long)op.step, kind, op.variant ? "pair" : "shared", op.mb, op.kb, op.nb, (int)op.a_km,
-                     (int)op.b_km);
+                     (int)op.b_km, (int)!op.out_pos.empty());
         out += line;
         // storages as region:offset+entries (entries rounded up as allocated), then the dependencies
         std::vector<int> rd, wr;

@@ -71,6 +71,15 @@ struct PermTables {
 //   C[m * 2^nb + n] = sum_k X[m, k] * Y[k, n]
 // m enumerates X's free legs (bit i = i-th lowest free position), k the
 // shared legs, n Y's free legs (in Y's leg order, last leg = bit 0).
+// Placement of a product in memory: bit i of the kernel's natural product index (the column bits
+// first, bit 0 lowest, then the row bits) goes to address position pos[i].  on = 0: the natural
+// row-major layout.  Chosen by the plan compiler so that the next GEMM reads the product without a
+// permute; the lowest positions always come from the side the kernel's lanes run along.
+struct OutMap {
+    int8_t pos[kMaxRank];
+    int32_t on;
+};
+
 struct SmallDesc {
     Operand x, y;
     int32_t mb, kb, nb;
@@ -79,6 +88,7 @@ struct SmallDesc {
     int8_t xk_pos[kSmallMaxK]; // X position of shared bit i of k
     int8_t yk_pos[kSmallMaxK]; // Y position of shared bit i of k
     int8_t yn_pos[kSmallMaxN]; // Y position of bit i of n
+    OutMap om;                 // product placement (natural bits: n, then m)
 };
 
 // Cross-slice FP64 compensated sum of the root tensor into accumulators.
@@ -99,7 +109,7 @@ cudaError_t launch_small(const SmallDesc& d, const ItemCtx& ic, int64_t n_items,
 // [K][M], B stored [N][K] (b_kmajor) or [K][N]; M = 2^mb etc.
 cudaError_t launch_gemm_c64(const float2* a, int64_t a_is, bool a_kmajor, const float2* b, int64_t b_is,
                             bool b_kmajor, float2* c, int64_t c_is, int mb, int nb, int kb, int64_t n_items,
-                            cudaStream_t st);
+                            cudaStream_t st, const OutMap* om = nullptr);
 cudaError_t launch_slice_sum(const SumDesc& d, const ItemCtx& ic, double* acc, cudaStream_t st);
 
 // Persistent executor (qx_persist.cu): one launch runs whole contractions of

@@ -10,6 +10,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <mutex>
 
 #include "qx_internal.h"
 
@@ -25,6 +26,17 @@ __device__ __forceinline__ int64_t fix_offset(const Operand& op, const ItemCtx& 
             const int64_t v = src >= 0 ? ((s >> src) & 1) : (int64_t)(ic.bits[b * ic.n_qubits + (-src - 1)] & 1);
             off += v * op.fix_stride[f];
         }
+    }
+    return off;
+}
+
+// address offset of the set bits of v placed at positions pos[0..] (bit b of v -> 2^pos[b])
+__device__ __forceinline__ int64_t place_bits(int64_t v, const int8_t* pos) {
+    int64_t off = 0;
+    while (v) {
+        const int b = __ffsll((long long)v) - 1;
+        off += (int64_t)1 << pos[b];
+        v &= v - 1;
     }
     return off;
 }
@@ -190,13 +202,19 @@ cudaError_t launch_permute(const PermDesc& d, const ItemCtx& ic, int64_t n_items
 // outputs C[m, n].  Used for the many steps that absorb a gate-sized tensor.
 // ---------------------------------------------------------------------------------------------
 template <int KB>
-__global__ void __launch_bounds__(256) k_small(const SmallDesc d, const ItemCtx ic, float2* __restrict__ out,
+__global__ void __launch_bounds__(256) k_small(const __grid_constant__ SmallDesc d, const ItemCtx ic, float2* __restrict__ out,
                                                int64_t out_is) {
     extern __shared__ float2 ys[];  // the small operand (2^(kb + nb) entries), then the output stage
     __shared__ int64_t kofs[1 << kSmallMaxK];
+    __shared__ int64_t cofs[1 << kSmallMaxN];  // placed product: offset of each column n
+    __shared__ int8_t rpos[kMaxRank];          // placed product: position of each row bit
     const int64_t item = blockIdx.y;
     const int nb = d.nb;
     const int nn = 1 << nb;
+    if (d.om.on) {
+        for (int n = threadIdx.x; n < nn; n += blockDim.x) cofs[n] = place_bits(n, d.om.pos);
+        for (int b = threadIdx.x; b < d.mb; b += blockDim.x) rpos[b] = d.om.pos[nb + b];
+    }
     const int64_t yoff = fix_offset(d.y, ic, item);
     for (int idx = threadIdx.x; idx < ((1 << KB) << nb); idx += blockDim.x) {
         const int kk = idx >> nb, n = idx & (nn - 1);
@@ -218,7 +236,7 @@ __global__ void __launch_bounds__(256) k_small(const SmallDesc d, const ItemCtx 
     const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     // outputs of the CTA's rows form one block: stage them (row stride nn + 1) and store coalesced
     float2* stage = ys + (1 << (kSmallMaxK + kSmallMaxN));
-    const bool staged = nb <= 4 && blockDim.x == 256;
+    const bool staged = !d.om.on && nb <= 4 && blockDim.x == 256;
     if (m < M) {
         int64_t xa = m;
         for (int h = 0; h < d.n_holes; ++h) {
@@ -229,13 +247,13 @@ __global__ void __launch_bounds__(256) k_small(const SmallDesc d, const ItemCtx 
         float2 a[1 << KB];
 #pragma unroll
         for (int kk = 0; kk < (1 << KB); ++kk) a[kk] = xp[kofs[kk]];
-        float2* __restrict__ cp = out + item * out_is + (m << nb);
+        float2* __restrict__ cp = out + item * out_is + (d.om.on ? place_bits(m, rpos) : (m << nb));
         for (int n = 0; n < nn; ++n) {
             float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
             for (int kk = 0; kk < (1 << KB); ++kk) cfma(acc, a[kk], ys[kk * nn + n]);
             if (staged) stage[threadIdx.x * (nn + 1) + n] = acc;
-            else cp[n] = acc;
+            else cp[d.om.on ? cofs[n] : n] = acc;
         }
     }
     if (!staged) return;
@@ -253,12 +271,19 @@ __global__ void __launch_bounds__(256) k_small(const SmallDesc d, const ItemCtx 
 // contiguous block: they are staged in shared memory (row stride 2^NB + 1
 // against bank conflicts) and stored coalesced.
 template <int KB, int NB>
-__global__ void __launch_bounds__(256) k_small_flat(const SmallDesc d, const ItemCtx ic, float2* __restrict__ out,
+__global__ void __launch_bounds__(256) k_small_flat(const __grid_constant__ SmallDesc d, const ItemCtx ic, float2* __restrict__ out,
                                                     int64_t out_is, int64_t n_items) {
     constexpr int NN = 1 << NB, STAGE = NB <= 4;
     __shared__ int64_t yrel[(1 << KB) << NB];
     __shared__ int64_t kofs[1 << KB];
     __shared__ float2 stage[STAGE ? 256 * (NN + 1) : 1];
+    __shared__ int64_t cofs[NN];      // placed product: offset of each column n
+    __shared__ int8_t rpos[kMaxRank];  // placed product: position of each row bit
+    const bool staged = STAGE && !d.om.on;
+    if (d.om.on) {
+        for (int n = threadIdx.x; n < NN; n += blockDim.x) cofs[n] = place_bits(n, d.om.pos);
+        for (int b = threadIdx.x; b < d.mb; b += blockDim.x) rpos[b] = d.om.pos[NB + b];
+    }
     for (int i = threadIdx.x; i < ((1 << KB) << NB); i += blockDim.x) {
         const int kk = i >> NB, n = i & (NN - 1);
         int64_t a = 0;
@@ -298,13 +323,13 @@ __global__ void __launch_bounds__(256) k_small_flat(const SmallDesc d, const Ite
                 for (int kk = 0; kk < (1 << KB); ++kk) cfma(acc, a[kk], __ldg(yp + yrel[(kk << NB) + n]));
                 res[n] = acc;
             }
-            if (!STAGE) {
-                float2* __restrict__ cp = out + item * out_is + (m << NB);
+            if (!staged) {
+                float2* __restrict__ cp = out + item * out_is + (d.om.on ? place_bits(m, rpos) : (m << NB));
 #pragma unroll
-                for (int n = 0; n < NN; ++n) cp[n] = res[n];
+                for (int n = 0; n < NN; ++n) cp[d.om.on ? cofs[n] : n] = res[n];
             }
         }
-        if (STAGE) {
+        if (staged) {
             // outputs of (pair, m) = t sit at t * NN (out_is = 2^(mb + NB)): one block per CTA
 #pragma unroll
             for (int n = 0; n < NN; ++n) stage[threadIdx.x * (NN + 1) + n] = res[n];
@@ -385,7 +410,7 @@ template <int BM, int BN>
 __global__ void __launch_bounds__(256, (BM * BN >= 8192 ? 1 : 2)) k_gemm_c64(const float2* __restrict__ A, int64_t a_is, bool akm,
                                                   const float2* __restrict__ B, int64_t b_is, bool bkm,
                                                   float2* __restrict__ C, int64_t c_is, int mb, int nb, int kb,
-                                                  int tiles_n) {
+                                                  int tiles_n, const __grid_constant__ OutMap om) {
     constexpr int TM = BM / 16, TN = BN / 16, LA = BM * GBK / 256, LB = BN * GBK / 256;
     extern __shared__ float2 gsm[];  // As[2][GBK][BM + 1], then Bs[2][GBK][BN + 1]
     float2(*As)[GBK][BM + 1] = (float2(*)[GBK][BM + 1])gsm;
@@ -477,6 +502,21 @@ __global__ void __launch_bounds__(256, (BM * BN >= 8192 ? 1 : 2)) k_gemm_c64(con
         buf ^= 1;
     }
     float2* Cp = C + item * c_is;
+    if (om.on) {  // placed product: row and column offsets from the bit map (columns stay lane-contiguous)
+        int64_t co[TN];
+#pragma unroll
+        for (int j = 0; j < TN; ++j) co[j] = place_bits(n0 + tx + 16 * j, om.pos);
+#pragma unroll
+        for (int i = 0; i < TM; ++i) {
+            const int64_t gm = m0 + ty + 16 * i;
+            if (gm >= M) continue;
+            const int64_t ro = place_bits(gm, om.pos + nb);
+#pragma unroll
+            for (int j = 0; j < TN; ++j)
+                if (n0 + tx + 16 * j < N) Cp[ro + co[j]] = tot[i][j];
+        }
+        return;
+    }
 #pragma unroll
     for (int i = 0; i < TM; ++i) {
         const int64_t gm = m0 + ty + 16 * i;
@@ -535,23 +575,33 @@ __global__ void __launch_bounds__(256) k_dot_c64(const float2* __restrict__ A, i
 
 template <int BM, int BN>
 static void gemm_tile(dim3 grid, cudaStream_t st, const float2* a, int64_t a_is, bool akm, const float2* b,
-                      int64_t b_is, bool bkm, float2* c, int64_t c_is, int mb, int nb, int kb, int tn) {
+                      int64_t b_is, bool bkm, float2* c, int64_t c_is, int mb, int nb, int kb, int tn,
+                      const OutMap& om) {
     constexpr int smem = 2 * GBK * (BM + 1 + BN + 1) * (int)sizeof(float2);
     if (smem > 48 * 1024) {
-        static int done = 0;  // opt in to more than 48 KB of dynamic shared memory (once)
-        if (!done) {
-            cudaFuncSetAttribute(k_gemm_c64<BM, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-            done = 1;
+        // opt in to more than 48 KB of dynamic shared memory, once per device
+        static uint64_t done[4] = {0, 0, 0, 0};
+        static std::mutex mu;
+        int dev = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess && dev >= 0 && dev < 256) {
+            std::lock_guard<std::mutex> lk(mu);
+            if (!((done[dev >> 6] >> (dev & 63)) & 1) &&
+                cudaFuncSetAttribute(k_gemm_c64<BM, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) ==
+                    cudaSuccess)
+                done[dev >> 6] |= 1ull << (dev & 63);
         }
     }
-    k_gemm_c64<BM, BN><<<grid, 256, smem, st>>>(a, a_is, akm, b, b_is, bkm, c, c_is, mb, nb, kb, tn);
+    k_gemm_c64<BM, BN><<<grid, 256, smem, st>>>(a, a_is, akm, b, b_is, bkm, c, c_is, mb, nb, kb, tn, om);
 }
 
 cudaError_t launch_gemm_c64(const float2* a, int64_t a_is, bool a_kmajor, const float2* b, int64_t b_is,
                             bool b_kmajor, float2* c, int64_t c_is, int mb, int nb, int kb, int64_t n_items,
-                            cudaStream_t st) {
+                            cudaStream_t st, const OutMap* omp) {
     if (n_items <= 0) return cudaSuccess;
+    OutMap om{};
+    if (omp) om = *omp;
     if (mb + nb <= 4 && kb >= 8) {
+        if (om.on) return cudaErrorInvalidValue;  // the dot kernel writes the natural layout only
         dim3 grid((unsigned)n_items);
 #define QX_DOT_CASE(X, Y)                                                                                   \
     if (mb == X && nb == Y) {                                                                               \
@@ -572,7 +622,7 @@ cudaError_t launch_gemm_c64(const float2* a, int64_t a_is, bool a_kmajor, const 
 #define QX_GEMM_CASE(X, Y)                                                                            \
     if (bmb == X && bnb == Y) {                                                                       \
         gemm_tile<(1 << X), (1 << Y)>(grid, st, a, a_is, a_kmajor, b, b_is, b_kmajor, c, c_is, mb, nb, kb, \
-                                      (int)tn);                                                       \
+                                      (int)tn, om);                                                   \
         return cudaGetLastError();                                                                    \
     }
     QX_GEMM_CASE(7, 6)
