@@ -204,7 +204,8 @@ cudaError_t launch_permute(const PermDesc& d, const ItemCtx& ic, int64_t n_items
 template <int KB>
 __global__ void __launch_bounds__(256) k_small(const __grid_constant__ SmallDesc d, const ItemCtx ic, float2* __restrict__ out,
                                                int64_t out_is) {
-    extern __shared__ float2 ys[];  // the small operand (2^(kb + nb) entries), then the output stage
+    extern __shared__ float4 small_dyn[];  // 16-byte aligned
+    float2* ys = (float2*)small_dyn;        // the small operand (2^(kb + nb) entries), then the output stage
     __shared__ int64_t kofs[1 << kSmallMaxK];
     __shared__ int64_t cofs[1 << kSmallMaxN];  // placed product: offset of each column n
     __shared__ int8_t rpos[kMaxRank];          // placed product: position of each row bit
@@ -248,12 +249,33 @@ __global__ void __launch_bounds__(256) k_small(const __grid_constant__ SmallDesc
 #pragma unroll
         for (int kk = 0; kk < (1 << KB); ++kk) a[kk] = xp[kofs[kk]];
         float2* __restrict__ cp = out + item * out_is + (d.om.on ? place_bits(m, rpos) : (m << nb));
-        for (int n = 0; n < nn; ++n) {
+        if (nn >= 2) {
+            // two outputs per pass: their Y entries are adjacent, one 16-byte shared load per k
+            const float4* __restrict__ ys4 = (const float4*)ys;
+            for (int n = 0; n < nn; n += 2) {
+                float2 acc0 = make_float2(0.f, 0.f), acc1 = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int kk = 0; kk < (1 << KB); ++kk) {
+                    const float4 y = ys4[(kk * nn + n) >> 1];
+                    cfma(acc0, a[kk], make_float2(y.x, y.y));
+                    cfma(acc1, a[kk], make_float2(y.z, y.w));
+                }
+                if (staged) {
+                    stage[threadIdx.x * (nn + 1) + n] = acc0;
+                    stage[threadIdx.x * (nn + 1) + n + 1] = acc1;
+                } else if (d.om.on) {
+                    cp[cofs[n]] = acc0;
+                    cp[cofs[n + 1]] = acc1;
+                } else {
+                    *(float4*)(cp + n) = make_float4(acc0.x, acc0.y, acc1.x, acc1.y);
+                }
+            }
+        } else {
             float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
-            for (int kk = 0; kk < (1 << KB); ++kk) cfma(acc, a[kk], ys[kk * nn + n]);
-            if (staged) stage[threadIdx.x * (nn + 1) + n] = acc;
-            else cp[d.om.on ? cofs[n] : n] = acc;
+            for (int kk = 0; kk < (1 << KB); ++kk) cfma(acc, a[kk], ys[kk]);
+            if (staged) stage[threadIdx.x * (nn + 1)] = acc;
+            else cp[d.om.on ? cofs[0] : 0] = acc;
         }
     }
     if (!staged) return;

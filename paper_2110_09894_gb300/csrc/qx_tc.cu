@@ -180,6 +180,7 @@ __device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t parity) {
 // launch has recorded an error (so one expired wait does not make every
 // later CTA wait out its own limit)
 __device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, long long limit, const int* err) {
+    if (mbar_try(b, parity)) return true;  // the common case: no clock read (it costs hundreds of cycles)
     const long long t0 = clock64();
     uint32_t spins = 0;
     while (!mbar_try(b, parity)) {
@@ -244,6 +245,24 @@ __device__ __forceinline__ void mma(uint32_t tmem, uint64_t ad, uint64_t bd, uin
             "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
     }
 }
+// tcgen05.st of 16 32-bit columns starting at taddr for this thread's TMEM lane (not waited)
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const float* v) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16};" ::"r"(taddr),
+        "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])), "r"(__float_as_uint(v[3])),
+        "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])), "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])),
+        "r"(__float_as_uint(v[8])), "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])), "r"(__float_as_uint(v[11])),
+        "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])), "r"(__float_as_uint(v[14])),
+        "r"(__float_as_uint(v[15]))
+        : "memory");
+}
+// 3xTF32 product with the A operand read from TMEM (row i in lane i, K along columns)
+__device__ __forceinline__ void mma_tf32_ta(uint32_t d, uint32_t a_tmem, uint64_t bd, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\ttcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n\t}\n" ::"r"(d),
+        "r"(a_tmem), "l"(bd), "r"(idesc), "r"(acc));
+}
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
     uint32_t r[32];
     asm volatile(
@@ -279,7 +298,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     constexpr uint32_t IDESC = (1u << 4) | ((uint32_t)F::FMT << 7) | ((uint32_t)F::FMT << 10) |
                                ((uint32_t)(TC_BN >> 3) << 17) | ((uint32_t)(TC_BM >> 4) << 24);
     extern __shared__ uint8_t dyn[];
-    __shared__ uint64_t full[F::STAGES], empty[F::STAGES], tfull[2], tempty[2], drain;
+    constexpr int NTB = 4;  // TMEM accumulator buffers (4 x 128 columns: all of TMEM)
+    __shared__ uint64_t full[F::STAGES], empty[F::STAGES], tfull[NTB], tempty[NTB], drain;
     __shared__ uint32_t tmem_slot;
     __shared__ int abort_flag;
     if (*(volatile const int*)err) return;  // an earlier CTA of this contraction gave up
@@ -295,7 +315,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
-        for (int b = 0; b < 2; ++b) {
+        for (int b = 0; b < NTB; ++b) {
             mbar_init(&tfull[b], 1);
             mbar_init(&tempty[b], 4);  // one arrival per epilogue warp
         }
@@ -305,7 +325,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     }
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(s_addr(&tmem_slot)),
-                     "r"(2 * TC_BN)
+                     "r"(NTB * TC_BN)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -338,11 +358,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 mbar_wait(&full[it % F::STAGES], (it / F::STAGES) & 1, limit, err);
         }
     } else if (warp == 1 && lane == 0) {
-        // MMA issuer: stage `it` accumulates (fresh) into TMEM buffer it & 1
+        // MMA issuer: stage `it` accumulates (fresh) into TMEM buffer it % NTB
         bool ok = true;
         for (int it = 0; it < nk && ok; ++it) {
             const int s = it % F::STAGES, n = it / F::STAGES;
-            const int b = it & 1, u = it >> 1;
+            const int b = it % NTB, u = it / NTB;
             if (!mbar_wait(&full[s], n & 1, limit, err) ||
                 (u > 0 && !mbar_wait(&tempty[b], (u - 1) & 1, limit, err)) || *(volatile int*)&abort_flag) {
                 atomicExch(&abort_flag, 1);
@@ -379,7 +399,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         for (int j = 0; j < TC_BN; ++j) tot[j] = 0.f;
         bool ok = true;
         for (int it = 0; it < nk; ++it) {
-            const int b = it & 1, u = it >> 1;
+            const int b = it % NTB, u = it / NTB;
             if (!mbar_wait(&tfull[b], u & 1, limit, err) || *(volatile int*)&abort_flag) {
                 atomicExch(&abort_flag, 1);
                 ok = false;
@@ -419,29 +439,41 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     if (warp == 1) {
         __syncwarp();
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * TC_BN) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(NTB * TC_BN) : "memory");
     }
 }
 
 // ------------------------------------------------------------------------------------------------
 // 3xTF32 straight from the complex64 operands: TMA brings raw 128-byte K slabs
-// of A (128 rows) and of B (64 complex rows) into shared memory, where the
-// epilogue warps split A into hi (in place) and lo, and build both parts of the
-// expanded B' (rows 2n = (re, -im), 2n+1 = (im, re)) before the MMAs run.  An
-// elementwise map keeps the 128-byte swizzle, so A's parts sit at the same
-// offsets as the raw data; B' row r puts chunk j at (j ^ (r % 8)).  This
-// removes the separate split pass and its HBM traffic.
+// of A (128 rows) and of B (BN/2 complex rows) into landing slots.  Converter
+// warps split A into hi and lo and store both into TMEM (row = lane), and build
+// both parts of the expanded B' (rows 2n = (re, -im), 2n+1 = (im, re)) in an
+// MMA slot in shared memory; the MMAs read A from TMEM and B' through
+// descriptors.  Keeping A out of shared memory halves the tensor core's
+// shared-memory reads, which with the split traffic bound this kernel; B' row
+// r puts chunk j at (j ^ (r % 8)), the 128-byte swizzle.  No separate split
+// pass, no extra HBM traffic.
 // Warps: 0 TMA, 1 TMEM + MMA, 2..9 drain TMEM (warp w reads TMEM lanes
-// 32 (w % 4) and half of the columns), 10..13 convert stages ahead of the MMAs.
+// 32 (w % 4) and half of the columns), 10..13 convert slabs ahead of the MMAs
+// (warp w writes the A rows of TMEM lanes 32 (w % 4)).
 // ------------------------------------------------------------------------------------------------
-constexpr int TC2_THREADS = 448, TC2_CONV = 128;  // warps 0 TMA, 1 MMA, 2-9 drain, 10-13 convert
-// stage layout for a B' tile of BN rows: raw/hi A (16 KB), lo A (16 KB), raw B (BN/2 rows), B'hi, B'lo (BN rows)
+// warps 0 TMA, 1 and 14 MMA (even / odd stages), 2-9 drain, 10-13 convert
+constexpr int TC2_THREADS = 480, TC2_CONV = 128;
+// Two rings.  Landing slots take the raw TMA slabs: A (16 KB, 128 rows) and B (BN/2 complex
+// rows).  MMA slots hold what the tensor core reads: B' hi and B' lo (BN rows each) in shared
+// memory, A hi and A lo (2 x 32 columns) in TMEM after the NTB accumulator buffers.  A landing
+// slot is free again as soon as it is converted, so several slabs per SM stay in flight while the
+// tensor core works on earlier ones.
 template <int BN>
 struct Tc2 {
     static constexpr uint32_t A = 16384, BRAW = (BN / 2) * 128, BP = BN * 128;
-    static constexpr uint32_t OFF_ALO = A, OFF_BRAW = 2 * A, OFF_BHI = 2 * A + BRAW, OFF_BLO = 2 * A + BRAW + BP;
-    static constexpr uint32_t STAGE = 2 * A + BRAW + 2 * BP;
-    static constexpr int STAGES = BN == 128 ? 3 : 4;
+    static constexpr uint32_t LAND = A + BRAW;          // landing slot: raw A, raw B
+    static constexpr uint32_t OFF_BLO = BP, MSLOT = 2 * BP;  // MMA slot: B' hi, B' lo
+    static constexpr int NL = BN == 128 ? 5 : 8, NM = BN == 128 ? 3 : 4;
+    static constexpr uint32_t SMEM = NL * LAND + NM * MSLOT;  // slots are multiples of 1024 bytes
+    static constexpr int NTB = 2;                      // accumulator buffers
+    static constexpr uint32_t ACOL = NTB * BN;         // first TMEM column of the A parts (64 per MMA slot)
+    static constexpr uint32_t TMEM_COLS = 512;
 };
 
 __device__ __forceinline__ void split4(float4 v, float4& hi, float4& lo) {
@@ -449,36 +481,48 @@ __device__ __forceinline__ void split4(float4 v, float4& hi, float4& lo) {
     lo = make_float4(v.x - hi.x, v.y - hi.y, v.z - hi.z, v.w - hi.w);
 }
 
-// convert stage `st` (raw A, raw B landed) with the converter threads ct = 0 .. TC2_CONV - 1
+// Convert a landed slab pair (`land`) into an MMA slot (`ms`, TMEM columns ahi / ahi + 32) with the
+// converter warps: thread (quarter qq, lane) splits row 32 qq + lane of A into TMEM (row = lane),
+// then the threads ct = 0 .. TC2_CONV - 1 build B' hi / lo in shared memory.
 template <int BN>
-__device__ __forceinline__ void tc2_convert(uint8_t* st, int ct) {
+__device__ __forceinline__ void tc2_convert(const uint8_t* land, uint8_t* ms, int ct, uint32_t tmem, int qq,
+                                            int lane, uint32_t ahi) {
     using L = Tc2<BN>;
+    const int r = 32 * qq + lane;
+    const uint32_t lanes = (uint32_t)(32 * qq) << 16;
 #pragma unroll
-    for (int i = 0; i < 1024 / TC2_CONV; ++i) {  // A: 1024 float4, elementwise, same offsets
-        const int c = ct + TC2_CONV * i;
-        float4* a = (float4*)(st) + c;
-        float4 hi, lo;
-        split4(*a, hi, lo);
-        *a = hi;
-        ((float4*)(st + L::OFF_ALO))[c] = lo;
+    for (int h = 0; h < 2; ++h) {  // 16 columns (four 16-byte chunks) at a time
+        float hi[16], lo[16];
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj) {
+            const int j = 4 * h + jj;
+            const float4 v = *(const float4*)(land + r * 128 + ((j ^ (r & 7)) << 4));
+            float4 vh, vl;
+            split4(v, vh, vl);
+            hi[4 * jj] = vh.x; hi[4 * jj + 1] = vh.y; hi[4 * jj + 2] = vh.z; hi[4 * jj + 3] = vh.w;
+            lo[4 * jj] = vl.x; lo[4 * jj + 1] = vl.y; lo[4 * jj + 2] = vl.z; lo[4 * jj + 3] = vl.w;
+        }
+        tmem_st16(tmem + lanes + ahi + 16 * h, hi);
+        tmem_st16(tmem + lanes + ahi + 32 + 16 * h, lo);
     }
 #pragma unroll
     for (int i = 0; i < (BN / 2) * 8 / TC2_CONV; ++i) {  // B: BN/2 rows x 8 chunks of 16 bytes
         const int c = ct + TC2_CONV * i;
         const int n = c >> 3, j = c & 7;
-        const float4 v = *(const float4*)(st + L::OFF_BRAW + n * 128 + ((j ^ (n & 7)) << 4));
+        const float4 v = *(const float4*)(land + L::A + n * 128 + ((j ^ (n & 7)) << 4));
         const float4 r0 = make_float4(v.x, -v.y, v.z, -v.w);  // row 2n: re, -im
         const float4 r1 = make_float4(v.y, v.x, v.w, v.z);    // row 2n+1: im, re
         const int ra = 2 * n, rb = 2 * n + 1;
         const uint32_t oa = ra * 128 + ((j ^ (ra & 7)) << 4), ob = rb * 128 + ((j ^ (rb & 7)) << 4);
         float4 hi, lo;
         split4(r0, hi, lo);
-        *(float4*)(st + L::OFF_BHI + oa) = hi;
-        *(float4*)(st + L::OFF_BLO + oa) = lo;
+        *(float4*)(ms + oa) = hi;
+        *(float4*)(ms + L::OFF_BLO + oa) = lo;
         split4(r1, hi, lo);
-        *(float4*)(st + L::OFF_BHI + ob) = hi;
-        *(float4*)(st + L::OFF_BLO + ob) = lo;
+        *(float4*)(ms + ob) = hi;
+        *(float4*)(ms + L::OFF_BLO + ob) = lo;
     }
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 }
 
 template <int BN>
@@ -487,19 +531,21 @@ __global__ void __launch_bounds__(TC2_THREADS, 1)
                float* __restrict__ C, int64_t c_is, int M, int N2, int K2, int tiles_n, int tiles, int64_t n_items,
                int a_bcast, int b_bcast, long long limit, int* err) {
     // persistent over (pair, tile) jobs: job = blockIdx.x + t * gridDim.x; the
-    // k-stages of successive jobs form one sequence g = t * nk + it, so the
-    // pipeline stays full across tile boundaries
+    // k-stages of successive jobs form one sequence g = t * nk + it, so both
+    // rings stay full across tile boundaries
     using L = Tc2<BN>;
     constexpr int BK = 32;  // TF32 elements per stage (one 128-byte slab)
-    constexpr int TC2_STAGES = L::STAGES;
+    constexpr int NL = L::NL, NM = L::NM, NTB = L::NTB;
     constexpr uint32_t IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(BN >> 3) << 17) |
                                ((uint32_t)(TC_BM >> 4) << 24);
     extern __shared__ uint8_t dyn[];
-    __shared__ uint64_t full[TC2_STAGES], conv[TC2_STAGES], empty[TC2_STAGES], tfull[2], tempty[2], drain;
+    __shared__ uint64_t full[NL], lfree[NL], mfull[NM], mfree[NM], tfull[NTB], tempty[NTB], drain[2];
     __shared__ uint32_t tmem_slot;
     __shared__ int abort_flag;
     if (*(volatile const int*)err) return;
     uint8_t* base = (uint8_t*)(((uintptr_t)dyn + 1023) & ~(uintptr_t)1023);
+    auto land = [&](int l) { return base + l * L::LAND; };
+    auto mslot = [&](int m) { return base + NL * L::LAND + m * L::MSLOT; };
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nk = K2 / BK;
     const int64_t jobs = (int64_t)tiles * n_items;
@@ -513,22 +559,26 @@ __global__ void __launch_bounds__(TC2_THREADS, 1)
         *n0 = (tile % tiles_n) * BN;  // row of B'; raw B row n0 / 2
     };
     if (threadIdx.x == 0) {
-        for (int s = 0; s < TC2_STAGES; ++s) {
+        for (int s = 0; s < NL; ++s) {
             mbar_init(&full[s], 1);
-            mbar_init(&conv[s], TC2_CONV / 32);
-            mbar_init(&empty[s], 1);
+            mbar_init(&lfree[s], TC2_CONV / 32);
         }
-        for (int b = 0; b < 2; ++b) {
+        for (int s = 0; s < NM; ++s) {
+            mbar_init(&mfull[s], TC2_CONV / 32);
+            mbar_init(&mfree[s], 1);
+        }
+        for (int b = 0; b < NTB; ++b) {
             mbar_init(&tfull[b], 1);
             mbar_init(&tempty[b], 8);
         }
-        mbar_init(&drain, 1);
+        mbar_init(&drain[0], 1);
+        mbar_init(&drain[1], 1);
         abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(s_addr(&tmem_slot)),
-                     "r"(2 * BN)
+                     "r"(L::TMEM_COLS)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -540,9 +590,8 @@ __global__ void __launch_bounds__(TC2_THREADS, 1)
     if (warp == 0 && lane == 0) {
         int64_t issued = 0;
         for (int64_t g = 0; g < total; ++g) {
-            const int s = (int)(g % TC2_STAGES);
-            const int64_t n = g / TC2_STAGES;
-            if (!mbar_wait(&empty[s], (uint32_t)((n & 1) ^ 1), limit, err) || *(volatile int*)&abort_flag) {
+            const int l = (int)(g % NL);
+            if (!mbar_wait(&lfree[l], (uint32_t)(((g / NL) & 1) ^ 1), limit, err) || *(volatile int*)&abort_flag) {
                 atomicExch(&abort_flag, 1);
                 break;
             }
@@ -550,70 +599,79 @@ __global__ void __launch_bounds__(TC2_THREADS, 1)
             int m0, n0;
             job_of(g / nk, &item, &m0, &n0);
             const int it = (int)(g % nk);
-            mbar_expect_tx(&full[s], L::A + L::BRAW);
-            uint8_t* st = base + s * L::STAGE;
-            tma_load_3d(st, &mapA, it * BK, m0, a_bcast ? 0 : (int)item, &full[s]);
-            tma_load_3d(st + L::OFF_BRAW, &mapB, it * BK, n0 >> 1, b_bcast ? 0 : (int)item, &full[s]);
+            mbar_expect_tx(&full[l], L::LAND);  // raw A and raw B
+            tma_load_3d(land(l), &mapA, it * BK, m0, a_bcast ? 0 : (int)item, &full[l]);
+            tma_load_3d(land(l) + L::A, &mapB, it * BK, n0 >> 1, b_bcast ? 0 : (int)item, &full[l]);
             ++issued;
         }
-        if (*(volatile int*)&abort_flag) {
-            for (int64_t g = (issued > TC2_STAGES ? issued - TC2_STAGES : 0); g < issued; ++g)
-                mbar_wait(&full[g % TC2_STAGES], (uint32_t)((g / TC2_STAGES) & 1), limit, err);
+        if (*(volatile int*)&abort_flag) {  // let the copies in flight land before the CTA exits
+            for (int64_t g = (issued > NL ? issued - NL : 0); g < issued; ++g)
+                mbar_wait(&full[g % NL], (uint32_t)((g / NL) & 1), limit, err);
         }
-    } else if (warp == 1 && lane == 0) {
+    } else if ((warp == 1 || warp == 14) && lane == 0) {
+        // two issuers, even and odd stages: while one waits for its next stage (barrier waits, fence,
+        // commits cost about as much as issuing the stage's MMAs), the other keeps the tensor pipe busy;
+        // stage g accumulates into TMEM buffer g % 2, i.e. each issuer owns one buffer
+        const int who = warp == 1 ? 0 : 1;
         bool ok = true;
-        for (int64_t g = 0; g < total && ok; ++g) {
-            const int s = (int)(g % TC2_STAGES);
-            const int64_t n = g / TC2_STAGES;
-            const int b = (int)(g & 1);
-            const int64_t u = g >> 1;
-            if (!mbar_wait(&conv[s], (uint32_t)(n & 1), limit, err) ||
+        for (int64_t g = who; g < total && ok; g += 2) {
+            const int m = (int)(g % NM);
+            const int b = (int)(g % NTB);
+            const int64_t u = g / NTB;
+            if (!mbar_wait(&mfull[m], (uint32_t)((g / NM) & 1), limit, err) ||
                 (u > 0 && !mbar_wait(&tempty[b], (uint32_t)((u - 1) & 1), limit, err)) || *(volatile int*)&abort_flag) {
                 atomicExch(&abort_flag, 1);
                 ok = false;
                 break;
             }
             tc_fence_after();
-            const uint32_t st = s_addr(base + s * L::STAGE);
+            const uint32_t st = s_addr(mslot(m));
             const uint32_t d = tmem + b * BN;
 #pragma unroll
             for (int kk = 0; kk < BK / 8; ++kk) {
-                const uint64_t ahi = sdesc(st + kk * 32), alo = sdesc(st + L::OFF_ALO + kk * 32);
-                const uint64_t bhi = sdesc(st + L::OFF_BHI + kk * 32), blo = sdesc(st + L::OFF_BLO + kk * 32);
-                mma<TC_FORM_3XTF32>(d, ahi, bhi, IDESC, kk != 0);
-                mma<TC_FORM_3XTF32>(d, ahi, blo, IDESC, 1);
-                mma<TC_FORM_3XTF32>(d, alo, bhi, IDESC, 1);
+                const uint32_t ahi = tmem + L::ACOL + 64 * m + 8 * kk, alo = ahi + 32;
+                const uint64_t bhi = sdesc(st + kk * 32), blo = sdesc(st + L::OFF_BLO + kk * 32);
+                mma_tf32_ta(d, ahi, bhi, IDESC, kk != 0);
+                mma_tf32_ta(d, ahi, blo, IDESC, 1);
+                mma_tf32_ta(d, alo, bhi, IDESC, 1);
             }
-            tc_commit(&empty[s]);
+            tc_commit(&mfree[m]);
             tc_commit(&tfull[b]);
         }
-        if (!ok) {
-            tc_commit(&drain);
-            mbar_wait(&drain, 0, limit, err);
+        if (!ok) {  // the MMAs this thread issued finish before TMEM is freed
+            tc_commit(&drain[who]);
+            mbar_wait(&drain[who], 0, limit, err);
         }
-    } else if (warp >= 10) {
-        // converters: split each landed stage in place / into the part tiles, ahead of the MMAs
+    } else if (warp >= 10 && warp <= 13) {
+        // converters: landing slot -> MMA slot, ahead of the MMAs; warp w writes the A rows of TMEM
+        // lanes 32 (w % 4)
         const int ct = threadIdx.x - 320;
         for (int64_t g = 0; g < total; ++g) {
-            const int s = (int)(g % TC2_STAGES);
-            if (!mbar_wait(&full[s], (uint32_t)((g / TC2_STAGES) & 1), limit, err) || *(volatile int*)&abort_flag) {
+            const int l = (int)(g % NL), m = (int)(g % NM);
+            if (!mbar_wait(&full[l], (uint32_t)((g / NL) & 1), limit, err) ||
+                !mbar_wait(&mfree[m], (uint32_t)(((g / NM) & 1) ^ 1), limit, err) || *(volatile int*)&abort_flag) {
                 atomicExch(&abort_flag, 1);
                 break;
             }
-            tc2_convert<BN>(base + s * L::STAGE, ct);
+            tc_fence_after();  // the MMAs that last read this MMA slot have completed (mfree)
+            tc2_convert<BN>(land(l), mslot(m), ct, tmem, warp & 3, lane, L::ACOL + 64 * m);
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic writes -> tensor core
+            tc_fence_before();
             __syncwarp();
-            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(s_addr(&conv[s])) : "memory");
+            if (lane == 0) {
+                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(s_addr(&lfree[l])) : "memory");
+                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(s_addr(&mfull[m])) : "memory");
+            }
         }
-    } else if (warp >= 2) {
+    } else if (warp >= 2 && warp <= 9) {
         // drain: TMEM lanes 32 (warp % 4), columns (BN / 2) ((warp - 2) / 4) .. + BN / 2 - 1
         const int q = warp & 3, half = (warp - 2) >> 2;
         float tot[BN / 2];
 #pragma unroll
         for (int j = 0; j < BN / 2; ++j) tot[j] = 0.f;
         for (int64_t g = 0; g < total; ++g) {
-            const int b = (int)(g & 1);
-            const int64_t u = g >> 1;
+            const int b = (int)(g % NTB);
+            const int64_t u = g / NTB;
             if (!mbar_wait(&tfull[b], (uint32_t)(u & 1), limit, err) || *(volatile int*)&abort_flag) {
                 atomicExch(&abort_flag, 1);
                 break;
@@ -633,6 +691,8 @@ __global__ void __launch_bounds__(TC2_THREADS, 1)
                 int64_t item;
                 int m0, n0;
                 job_of(g / nk, &item, &m0, &n0);
+                // lane r holds row 32 q + r; each 32-column block is transposed across the warp so
+                // that every store writes 128 contiguous bytes of one row
                 float* cb = C + item * c_is + (int64_t)(m0 + 32 * q) * N2 + n0 + (BN / 2) * half + lane;
 #pragma unroll
                 for (int b32 = 0; b32 < BN / 64; ++b32) {
@@ -652,7 +712,7 @@ __global__ void __launch_bounds__(TC2_THREADS, 1)
     if (warp == 1) {
         __syncwarp();
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * BN) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(L::TMEM_COLS) : "memory");
     }
 }
 
@@ -781,7 +841,7 @@ static cudaError_t run_tc2(const TcArgs& g, cudaStream_t st) {
     if (!map_raw(&ma, g.a, 2 * K, M, abc ? 1 : g.n_items, abc ? M * K * 8 : g.a_is * 8, TC_BM) ||
         !map_raw(&mb, g.b, 2 * K, N, bbc ? 1 : g.n_items, bbc ? N * K * 8 : g.b_is * 8, BN / 2))
         return cudaErrorInvalidValue;
-    const int smem = L::STAGES * L::STAGE + 1024;
+    const int smem = (int)L::SMEM + 1024;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
@@ -836,7 +896,9 @@ cudaError_t launch_tc_gemm(int form, const TcArgs& g, cudaStream_t st) {
 static_assert(TcForm<TC_FORM_3XTF32>::STAGES * 4 * TC_BM * TC_ROWB + 1024 <= TC_SMEM_LIMIT + 1024, "smem");
 static_assert(TcForm<TC_FORM_BF16X3>::STAGES * 6 * TC_BM * TC_ROWB + 1024 <= TC_SMEM_LIMIT + 1024, "smem");
 static_assert(TcForm<TC_FORM_FP16>::STAGES * 2 * TC_BM * TC_ROWB + 1024 <= TC_SMEM_LIMIT + 1024, "smem");
-static_assert(Tc2<128>::STAGES * Tc2<128>::STAGE + 1024 <= 227 * 1024, "smem");
-static_assert(Tc2<64>::STAGES * Tc2<64>::STAGE + 1024 <= 227 * 1024, "smem");
+static_assert(Tc2<128>::SMEM + 1024 <= 227 * 1024 - 512, "smem");
+static_assert(Tc2<64>::SMEM + 1024 <= 227 * 1024 - 512, "smem");
+static_assert(Tc2<128>::ACOL + Tc2<128>::NM * 64 <= Tc2<128>::TMEM_COLS, "tmem");
+static_assert(Tc2<64>::ACOL + Tc2<64>::NM * 64 <= Tc2<64>::TMEM_COLS, "tmem");
 
 }  // namespace qx
