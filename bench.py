@@ -427,28 +427,39 @@ def main():
     dom = max(prof, key=lambda k: prof[k]["ms"])
     d = prof[dom]
     avg_ms = d["ms"] / max(d["launches"], 1)
+    # the binding roofline of the dominant kernel: its algorithmic bytes at the measured HBM bandwidth
+    # or its operations at the unit's peak, whichever takes longer for the same work
+    hbm_peak = pk["hbm_gbs"]
+    t_bytes = d["bytes"] / (hbm_peak * 1e9)
     if dom == "tc_gemm":
         code, products, ratio = PRECISIONS[args.precision]
         peak = pk["bf16_tflops"] * ratio
-        achieved = d["flops"] * products / (d["ms"] / 1e3) / 1e12  # issued real tensor flops
-        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "peak_source": f"bf16_tflops ({pk_src}, burst) x {ratio:.3f} nominal {args.precision} ratio",
-                "issued_products": products}
+        ops = d["flops"] * products  # issued real tensor flops
+        comp = {"bound": "tensor", "peak": peak, "unit": "TFLOP/s", "issued_products": products,
+                "peak_source": f"bf16_tflops ({pk_src}, burst) x {ratio:.3f} nominal {args.precision} ratio"}
     elif dom == "gemm":
         clk = pk.get("sm_max_mhz", 2070.0)
         n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
         peak = n_sm * 128 * 2 * clk * 1e6 / 1e12  # FP32 FMA lanes x 2 flops x clock
-        achieved = d["flops"] / (d["ms"] / 1e3) / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+        ops = d["flops"]
+        comp = {"bound": "alu", "peak": peak, "unit": "TFLOP/s",
                 "peak_source": f"{n_sm} SMs x 128 FP32 lanes x 2 x {clk:.0f} MHz (max clock)"}
     else:
-        peak = pk["hbm_gbs"]
+        ops, comp = 0.0, None
+    if comp is not None and ops / (comp["peak"] * 1e12) >= t_bytes:
+        achieved = ops / (d["ms"] / 1e3) / 1e12
+        roof = dict(comp, achieved=achieved, frac=achieved / comp["peak"],
+                    algorithmic_per_launch=ops / max(d["launches"], 1),
+                    other_bound={"bound": "hbm", "frac": d["bytes"] / (d["ms"] / 1e3) / 1e9 / hbm_peak})
+    else:
         achieved = d["bytes"] / (d["ms"] / 1e3) / 1e9
-        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "peak_source": f"hbm_gbs ({pk_src})"}
+        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
+                "peak_source": f"hbm_gbs ({pk_src})", "algorithmic_per_launch": d["bytes"] / max(d["launches"], 1)}
+        if comp is not None:
+            roof["other_bound"] = {"bound": comp["bound"],
+                                   "frac": ops / (d["ms"] / 1e3) / 1e12 / comp["peak"]}
     traffic = traffic_for(dom)
     roof.update({"kernel": dom, "traffic": traffic, "avg_launch_ms": avg_ms,
-                 "algorithmic_per_launch": (d["flops"] if dom == "gemm" else d["bytes"]) / max(d["launches"], 1),
                  "share_of_kernel_time": d["ms"] / max(sum(v["ms"] for v in prof.values()), 1e-12)})
     kernels = {k: {"ms_per_step": v["ms"] / args.steps, "launches_per_step": v["launches"] / args.steps,
                    "tflops": v["flops"] / max(v["ms"], 1e-12) / 1e9, "gbs": v["bytes"] / max(v["ms"], 1e-12) / 1e6}

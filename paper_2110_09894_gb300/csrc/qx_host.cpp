@@ -1210,13 +1210,16 @@ static void build_persistent_program(qx_ctx* h) {
     h->persist_ok = true;
 }
 
-static double op_bytes(const qx_ctx* h, const Op& op) {
-    // algorithmic bytes per pair: each operand read once, the result written once
-    if (op.type == OP_PERM) return 16.0 * (double)h->stor[op.dst].entries;
-    const double c = 8.0 * (double)h->stor[op.dst].entries;
-    if (op.type == OP_SMALL)
-        return c + 8.0 * (double)(node_entries(h->nodes[op.x]) + node_entries(h->nodes[op.y]));
-    return c + 8.0 * (double)(h->stor[op.sa].entries + h->stor[op.sb].entries);
+static double op_bytes(const qx_ctx* h, const Op& op, int64_t n_items) {
+    // algorithmic bytes of one launch over n_items pairs: each operand read once (a tensor shared by
+    // all pairs once per launch), the result written once per pair
+    const double n = (double)n_items;
+    auto node_b = [&](int node) { return 8.0 * (double)node_entries(h->nodes[node]) * (h->nodes[node].variant ? n : 1.0); };
+    auto stor_b = [&](int sid) { return 8.0 * (double)h->stor[sid].entries * (h->stor[sid].variant ? n : 1.0); };
+    const double c = stor_b(op.dst);
+    if (op.type == OP_PERM) return c + node_b(op.src);
+    if (op.type == OP_SMALL) return c + node_b(op.x) + node_b(op.y);
+    return c + stor_b(op.sa) + stor_b(op.sb);
 }
 
 static int run_op(qx_ctx* h, const Op& op, const ItemCtx& ic, int64_t n_items, cudaStream_t st) {
@@ -1230,11 +1233,11 @@ static int run_op(qx_ctx* h, const Op& op, const ItemCtx& ic, int64_t n_items, c
                      : prep                ? QX_KERNEL_TC_PREP
                                            : QX_KERNEL_GEMM;
     size_t slot;
-    const double prep_bytes = prep ? 8.0 * (double)(h->stor[op.sa].entries + h->stor[op.sb].entries +
-                                                    h->stor[op.spa].entries + h->stor[op.spb].entries)
-                                   : 0.0;
+    const double n = (double)n_items;
+    auto stor_b = [&](int sid) { return 8.0 * (double)h->stor[sid].entries * (h->stor[sid].variant ? n : 1.0); };
+    const double prep_bytes = prep ? stor_b(op.sa) + stor_b(op.sb) + stor_b(op.spa) + stor_b(op.spb) : 0.0;
     cudaError_t e = prof_begin(h, kind, prep ? 0.0 : op.flops * (double)n_items,
-                               (prep ? prep_bytes : op_bytes(h, op)) * (double)n_items, &slot);
+                               prep ? prep_bytes : op_bytes(h, op, n_items), &slot);
     if (e != cudaSuccess) return fail(h, QX_ECUDA, "profiling event: %s", cudaGetErrorString(e));
     if (op.type == OP_PERM) {
         e = launch_permute(perm_desc(h, op), ic, n_items, dp, dis, st);
@@ -1298,7 +1301,7 @@ static int run_op(qx_ctx* h, const Op& op, const ItemCtx& ic, int64_t n_items, c
         g.amax = (float*)(h->ws + h->off_err + 16);
         e = launch_tc_prep(op.tc, g, st);
         if (e == cudaSuccess) e = prof_end(h, slot);
-        if (e == cudaSuccess) e = prof_begin(h, QX_KERNEL_TC_GEMM, op.flops * (double)n_items, op_bytes(h, op) * (double)n_items, &slot);
+        if (e == cudaSuccess) e = prof_begin(h, QX_KERNEL_TC_GEMM, op.flops * (double)n_items, op_bytes(h, op, n_items), &slot);
         if (e == cudaSuccess) e = launch_tc_gemm(op.tc, g, st);
         h->last_launches += 2;
     }
@@ -1382,8 +1385,8 @@ static int contract_persistent(qx_ctx* h, const uint8_t* d_bits, int64_t n_bits,
     L.n_work = pairs;
     double bytes = 0;
     for (const Op& op : h->ops)
-        if (op.variant) bytes += op_bytes(h, op);
-    e = prof_begin(h, QX_KERNEL_PERSIST, h->flops_item * (double)pairs, bytes * (double)pairs, &slot);
+        if (op.variant) bytes += op_bytes(h, op, pairs);
+    e = prof_begin(h, QX_KERNEL_PERSIST, h->flops_item * (double)pairs, bytes, &slot);
     if (e == cudaSuccess) e = launch_persist(L, h->persist_grid, h->stream);
     if (e == cudaSuccess) e = prof_end(h, slot);
     if (e != cudaSuccess) return fail(h, QX_ECUDA, "persistent launch failed: %s", cudaGetErrorString(e));

@@ -203,28 +203,36 @@ cudaError_t launch_permute(const PermDesc& d, const ItemCtx& ic, int64_t n_items
 // ---------------------------------------------------------------------------------------------
 template <int KB>
 __global__ void __launch_bounds__(256) k_small(const __grid_constant__ SmallDesc d, const ItemCtx ic, float2* __restrict__ out,
-                                               int64_t out_is) {
+                                               int64_t out_is, int64_t n_items, int ppc, int y_shared) {
+    // A CTA owns 256 rows of one pair (ppc = 1), or ppc whole pairs of 2^mb < 256 rows each, whose
+    // products are then contiguous (out_is = 2^(mb + nb)).  The small operand of each of its pairs
+    // (one copy when every pair reads the same one) is staged in shared memory, then the output stage.
     extern __shared__ float4 small_dyn[];  // 16-byte aligned
-    float2* ys = (float2*)small_dyn;        // the small operand (2^(kb + nb) entries), then the output stage
+    float2* ys = (float2*)small_dyn;
     __shared__ int64_t kofs[1 << kSmallMaxK];
     __shared__ int64_t cofs[1 << kSmallMaxN];  // placed product: offset of each column n
     __shared__ int8_t rpos[kMaxRank];          // placed product: position of each row bit
-    const int64_t item = blockIdx.y;
     const int nb = d.nb;
     const int nn = 1 << nb;
+    const int yn = (1 << KB) << nb;   // entries of one small operand
+    const int yst = (yn + 1) & ~1;    // its stride in shared memory (even: 16-byte aligned pairs)
+    const int ny = y_shared ? 1 : ppc;
+    const int64_t M = (int64_t)1 << d.mb;
+    const int64_t item0 = (int64_t)blockIdx.y * ppc;
     if (d.om.on) {
         for (int n = threadIdx.x; n < nn; n += blockDim.x) cofs[n] = place_bits(n, d.om.pos);
         for (int b = threadIdx.x; b < d.mb; b += blockDim.x) rpos[b] = d.om.pos[nb + b];
     }
-    const int64_t yoff = fix_offset(d.y, ic, item);
-    for (int idx = threadIdx.x; idx < ((1 << KB) << nb); idx += blockDim.x) {
-        const int kk = idx >> nb, n = idx & (nn - 1);
-        int64_t a = yoff;
+    for (int idx = threadIdx.x; idx < ny * yn; idx += blockDim.x) {
+        const int p = idx / yn, e = idx - p * yn;
+        if (item0 + p >= n_items) continue;
+        const int kk = e >> nb, n = e & (nn - 1);
+        int64_t a = fix_offset(d.y, ic, item0 + p);
         for (int i = 0; i < KB; ++i)
             if ((kk >> i) & 1) a += (int64_t)1 << d.yk_pos[i];
         for (int i = 0; i < nb; ++i)
             if ((n >> i) & 1) a += (int64_t)1 << d.yn_pos[i];
-        ys[idx] = d.y.base[a];
+        ys[p * yst + e] = d.y.base[a];
     }
     if (threadIdx.x < (1 << KB)) {
         int64_t a = 0;
@@ -233,16 +241,18 @@ __global__ void __launch_bounds__(256) k_small(const __grid_constant__ SmallDesc
         kofs[threadIdx.x] = a;
     }
     __syncthreads();
-    const int64_t M = (int64_t)1 << d.mb;
-    const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int p = ppc > 1 ? (int)(threadIdx.x >> d.mb) : 0;
+    const int64_t item = item0 + p;
+    const int64_t m = ppc > 1 ? (int64_t)(threadIdx.x & (M - 1)) : (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const float2* __restrict__ yp = ys + (y_shared ? 0 : p * yst);
     // outputs of the CTA's rows form one block: stage them (row stride nn + 1) and store coalesced
-    float2* stage = ys + (1 << (kSmallMaxK + kSmallMaxN));
+    float2* stage = ys + ny * yst;
     const bool staged = !d.om.on && nb <= 4 && blockDim.x == 256;
-    if (m < M) {
+    if (m < M && item < n_items) {
         int64_t xa = m;
         for (int h = 0; h < d.n_holes; ++h) {
-            const int p = d.holes[h];
-            xa = ((xa >> p) << (p + 1)) | (xa & (((int64_t)1 << p) - 1));
+            const int q = d.holes[h];
+            xa = ((xa >> q) << (q + 1)) | (xa & (((int64_t)1 << q) - 1));
         }
         const float2* __restrict__ xp = d.x.base + fix_offset(d.x, ic, item) + xa;
         float2 a[1 << KB];
@@ -251,7 +261,7 @@ __global__ void __launch_bounds__(256) k_small(const __grid_constant__ SmallDesc
         float2* __restrict__ cp = out + item * out_is + (d.om.on ? place_bits(m, rpos) : (m << nb));
         if (nn >= 2) {
             // two outputs per pass: their Y entries are adjacent, one 16-byte shared load per k
-            const float4* __restrict__ ys4 = (const float4*)ys;
+            const float4* __restrict__ ys4 = (const float4*)yp;
             for (int n = 0; n < nn; n += 2) {
                 float2 acc0 = make_float2(0.f, 0.f), acc1 = make_float2(0.f, 0.f);
 #pragma unroll
@@ -273,16 +283,26 @@ __global__ void __launch_bounds__(256) k_small(const __grid_constant__ SmallDesc
         } else {
             float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
-            for (int kk = 0; kk < (1 << KB); ++kk) cfma(acc, a[kk], ys[kk]);
+            for (int kk = 0; kk < (1 << KB); ++kk) cfma(acc, a[kk], yp[kk]);
             if (staged) stage[threadIdx.x * (nn + 1)] = acc;
             else cp[d.om.on ? cofs[0] : 0] = acc;
         }
     }
     if (!staged) return;
     __syncthreads();
-    const int64_t r0 = (int64_t)blockIdx.x * blockDim.x;
-    const int64_t cnt = (M - r0 < 256 ? M - r0 : 256) * nn;
-    float2* __restrict__ dst = out + item * out_is + (r0 << nb);
+    // the block: rows r0 .. of pair item0 (ppc = 1), or every row of pairs item0 .. (ppc > 1)
+    int64_t rows;
+    float2* __restrict__ dst;
+    if (ppc > 1) {
+        const int64_t np = n_items - item0 < ppc ? n_items - item0 : ppc;
+        rows = np * M;
+        dst = out + item0 * out_is;
+    } else {
+        const int64_t r0 = (int64_t)blockIdx.x * blockDim.x;
+        rows = M - r0 < 256 ? M - r0 : 256;
+        dst = out + item0 * out_is + (r0 << nb);
+    }
+    const int64_t cnt = rows * nn;
     for (int i = threadIdx.x; i < cnt; i += 256) dst[i] = stage[(i >> nb) * (nn + 1) + (i & (nn - 1))];
 }
 
@@ -397,17 +417,27 @@ cudaError_t launch_small(const SmallDesc& d, const ItemCtx& ic, int64_t n_items,
             default: return small_flat_nb<5>(d, ic, n_items, out, out_is, st, grid);
         }
     }
+    // pairs of fewer than 256 rows share a CTA (their products contiguous), within 1536 staged
+    // small-operand entries so that with the output stage the CTA stays under 48 KB
     const int64_t m = (int64_t)1 << d.mb;
-    dim3 grid((unsigned)((m + 255) / 256), (unsigned)n_items);
-    const int threads = m < 256 ? (int)((m + 31) / 32 * 32) : 256;
-    const size_t smem = sizeof(float2) * ((1 << (kSmallMaxK + kSmallMaxN)) + (d.nb <= 4 ? 256 * ((1 << d.nb) + 1) : 0));
+    const int yst = (((1 << d.kb) << d.nb) + 1) & ~1;
+    const int y_shared = d.y.item_stride == 0 && d.y.n_fix == 0;
+    int ppc = 1;
+    if (m < 256 && (out_is == (m << d.nb) || n_items == 1)) {
+        ppc = (int)(256 / m);
+        while (ppc > 1 && !y_shared && ppc * yst > 1536) ppc >>= 1;
+    }
+    const int threads = ppc > 1 ? (int)(ppc * m) : (m < 256 ? (int)((m + 31) / 32 * 32) : 256);
+    const bool staged = !d.om.on && d.nb <= 4 && threads == 256;
+    dim3 grid(ppc > 1 ? 1u : (unsigned)((m + 255) / 256), (unsigned)((n_items + ppc - 1) / ppc));
+    const size_t smem = sizeof(float2) * ((size_t)(y_shared ? 1 : ppc) * yst + (staged ? 256 * ((1 << d.nb) + 1) : 0));
     switch (d.kb) {
-        case 0: k_small<0><<<grid, threads, smem, st>>>(d, ic, out, out_is); break;
-        case 1: k_small<1><<<grid, threads, smem, st>>>(d, ic, out, out_is); break;
-        case 2: k_small<2><<<grid, threads, smem, st>>>(d, ic, out, out_is); break;
-        case 3: k_small<3><<<grid, threads, smem, st>>>(d, ic, out, out_is); break;
-        case 4: k_small<4><<<grid, threads, smem, st>>>(d, ic, out, out_is); break;
-        case 5: k_small<5><<<grid, threads, smem, st>>>(d, ic, out, out_is); break;
+        case 0: k_small<0><<<grid, threads, smem, st>>>(d, ic, out, out_is, n_items, ppc, y_shared); break;
+        case 1: k_small<1><<<grid, threads, smem, st>>>(d, ic, out, out_is, n_items, ppc, y_shared); break;
+        case 2: k_small<2><<<grid, threads, smem, st>>>(d, ic, out, out_is, n_items, ppc, y_shared); break;
+        case 3: k_small<3><<<grid, threads, smem, st>>>(d, ic, out, out_is, n_items, ppc, y_shared); break;
+        case 4: k_small<4><<<grid, threads, smem, st>>>(d, ic, out, out_is, n_items, ppc, y_shared); break;
+        case 5: k_small<5><<<grid, threads, smem, st>>>(d, ic, out, out_is, n_items, ppc, y_shared); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
