@@ -260,7 +260,8 @@ void qx_group_destroy(qx_group_t g);
 #define QX_KERNEL_TC_PREP 4  /* operand split / expansion for the tensor-core forms */
 #define QX_KERNEL_TC_GEMM 5  /* tcgen05 complex GEMM */
 #define QX_KERNEL_PERSIST 6  /* persistent executor (whole contractions) */
-#define QX_KERNEL_KINDS   7
+#define QX_KERNEL_WAVE    7  /* batched executor: a level of small invariant steps, one CTA each */
+#define QX_KERNEL_KINDS   8
 int qx_set_profiling(qx_handle h, int enable);
 int qx_profile_read(qx_handle h, int kind, double* ms, int64_t* launches, double* flops, double* bytes);
 

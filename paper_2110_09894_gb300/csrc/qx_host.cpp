@@ -125,13 +125,24 @@ struct qx_ctx {
     int persist_grid = 0;
     bool pops_on_device = false;
 
+    // batched executor prologue in waves: the invariant steps by dependency level, one launch per
+    // level, one CTA per step (only when every invariant step is small)
+    bool wave_ok = false;
+    std::vector<POp> wave_ops;          // one per invariant op, grouped by level
+    std::vector<int32_t> wave_idx;      // 0 .. n-1 (positions into wave_ops)
+    std::vector<int32_t> wave_start;    // level L: wave_ops[wave_start[L] .. wave_start[L + 1])
+    std::vector<int> wave_of;           // per op: its level, -1 if not in a wave
+    std::vector<double> wave_flops, wave_bytes;
+    bool waves_on_device = false;
+    std::vector<cudaEvent_t> wave_ev;
+
     // workspace
     char* ws = nullptr;
     int64_t ws_bytes = 0;
     bool ws_owned = false;
     int64_t max_bits = 0;
     int64_t off_err = 0, off_leaf = 0, off_bits = 0, off_acc = 0, off_amps = 0, off_inv = 0, off_item = 0;
-    int64_t off_pops = 0, off_counter = 0, off_results = 0, off_pscratch = 0, off_pops_inv = 0;
+    int64_t off_pops = 0, off_counter = 0, off_results = 0, off_pscratch = 0, off_pops_inv = 0, off_wave = 0;
     int64_t items_cap = 0;
     bool leaves_on_device = false;
 
@@ -404,6 +415,7 @@ static int64_t assign_offsets(qx_ctx* h, bool variant) {
 }
 
 static void build_persistent_program(qx_ctx* h);
+static void build_waves(qx_ctx* h);
 
 // Storages an op reads and writes (leaves are read-only and not listed), and whether it uses the
 // per-tensor scale words of the workspace (prep-based tensor-core steps).
@@ -793,7 +805,8 @@ static int compile_plan(qx_ctx* h, const int64_t* order, int64_t n_steps, const 
                 if (std::find(shared.begin(), shared.end(), e) == shared.end()) fy.push_back(e);
             lay_out(t, fx, false, fy, true);
             // gathers: lanes run along rows (X's free index); a thread's own outputs along Y's columns
-            const std::vector<int> D = fused_layout(t, fx, false, fy, true, {{true, 4}, {false, 2}, {true, 2}});
+            const std::vector<int> D =
+                variant ? fused_layout(t, fx, false, fy, true, {{true, 4}, {false, 2}, {true, 2}}) : std::vector<int>{};
             std::vector<int> cl = fx;
             cl.insert(cl.end(), fy.begin(), fy.end());
             const int st = new_storage(h, (int64_t)1 << cl.size(), variant, t);
@@ -879,7 +892,7 @@ static int compile_plan(qx_ctx* h, const int64_t* order, int64_t n_steps, const 
             const int mb = (int)fA.size(), nb = (int)fB.size();
             const bool dot = mb + nb <= 4 && kb >= 8;
             const bool tc = direct || (tc_form && mb >= 7 && nb >= 6 && kb >= 5);
-            if (!tc && !dot) D = fused_layout(t, fA, best.pa, fB, best.pb, {{false, 4}});
+            if (!tc && !dot && variant) D = fused_layout(t, fA, best.pa, fB, best.pb, {{false, 4}});
         }
         Op g{};
         g.type = OP_GEMM;
@@ -969,6 +982,7 @@ static int compile_plan(qx_ctx* h, const int64_t* order, int64_t n_steps, const 
     for (const Op& op : h->ops) (op.variant ? h->flops_item : h->flops_inv) += op.flops;
     compute_deps(h);
     build_persistent_program(h);
+    build_waves(h);
     h->have_plan = true;
     return QX_OK;
 }
@@ -1014,6 +1028,10 @@ static void layout(qx_ctx* h, int64_t max_bits, int64_t* fixed_bytes) {
         h->off_pscratch = off;
         off += align_up((int64_t)h->persist_grid * h->item_entries * 8, 256);
     }
+    h->off_wave = off;  // wave programs: the POps, then their index list
+    if (h->wave_ok)
+        off += align_up((int64_t)(h->wave_ops.size() * sizeof(POp)), 256) +
+               align_up((int64_t)(h->wave_idx.size() * sizeof(int32_t)), 256);
     h->off_item = off;
     *fixed_bytes = off;
 }
@@ -1208,6 +1226,61 @@ static void build_persistent_program(qx_ctx* h) {
         h->pobit_leg[ob] = (int8_t)(std::find(R.legs.begin(), R.legs.end(), wire) - R.legs.begin());
     }
     h->persist_ok = true;
+}
+
+static double op_bytes(const qx_ctx* h, const Op& op, int64_t n_items);
+
+// The invariant steps grouped by dependency level (the dependency lists include space reuse, so the
+// steps of one level never touch the same storage).  Used when every invariant step is small enough
+// for one CTA: at most 2^12 entries in and out, no tensor cores, natural layouts.
+static void build_waves(qx_ctx* h) {
+    h->wave_ok = false;
+    h->wave_ops.clear();
+    h->wave_idx.clear();
+    h->wave_start.clear();
+    h->wave_flops.clear();
+    h->wave_bytes.clear();
+    h->wave_of.assign(h->ops.size(), -1);
+    if (h->opt.executor >= 2) return;  // the persistent executors run their own prologue program
+    constexpr int64_t kWaveEntries = 4096;
+    std::vector<int> inv;
+    for (size_t j = 0; j < h->ops.size(); ++j) {
+        const Op& op = h->ops[j];
+        if (op.variant) continue;
+        if (op.tc || !op.out_pos.empty() || h->stor[op.dst].entries > kWaveEntries) return;
+        auto small_node = [&](int n) { return node_entries(h->nodes[n]) <= kWaveEntries; };
+        if (op.type == OP_PERM && !small_node(op.src)) return;
+        if (op.type == OP_SMALL && !(small_node(op.x) && small_node(op.y))) return;
+        if (op.type == OP_GEMM &&
+            !(h->stor[op.sa].entries <= kWaveEntries && h->stor[op.sb].entries <= kWaveEntries))
+            return;
+        inv.push_back((int)j);
+    }
+    if (inv.empty()) return;
+    int levels = 0;
+    for (int j : inv) {
+        int lv = 0;
+        for (int i : h->deps[j])
+            if (!h->ops[i].variant) lv = std::max(lv, h->wave_of[i] + 1);
+        h->wave_of[j] = lv;
+        levels = std::max(levels, lv + 1);
+    }
+    h->wave_start.assign(levels + 1, 0);
+    h->wave_flops.assign(levels, 0.0);
+    h->wave_bytes.assign(levels, 0.0);
+    for (int L = 0; L < levels; ++L) {
+        h->wave_start[L] = (int32_t)h->wave_ops.size();
+        for (int j : inv)
+            if (h->wave_of[j] == L) {
+                h->wave_ops.push_back(to_pop(h, h->ops[j]));
+                h->wave_flops[L] += h->ops[j].flops;
+                h->wave_bytes[L] += op_bytes(h, h->ops[j], 1);
+            }
+    }
+    h->wave_start[levels] = (int32_t)h->wave_ops.size();
+    h->wave_idx.resize(h->wave_ops.size());
+    for (size_t i = 0; i < h->wave_idx.size(); ++i) h->wave_idx[i] = (int32_t)i;
+    h->wave_ok = true;
 }
 
 static double op_bytes(const qx_ctx* h, const Op& op, int64_t n_items) {
@@ -1415,6 +1488,8 @@ struct Dag {
     std::vector<int> stream_of, last_on;  // per op: stream this batch (-1 none); per stream: last op
     std::vector<std::vector<int>> seen;   // seen[s][t]: latest op of stream t that stream s waited for
     std::vector<char> forked;
+    std::vector<int> wave_seen;          // per stream: highest prologue level waited for
+    bool waves_now = false;              // the prologue levels were launched in this batch
     explicit Dag(qx_ctx* hh) : h(hh) {}
     int init() {
         on = h->n_streams > 1 && !h->profiling && !h->ops.empty();
@@ -1434,6 +1509,50 @@ struct Dag {
             CUDA_TRY(h, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
             h->op_ev.push_back(e);
         }
+        while (h->wave_ok && h->wave_ev.size() + 1 < h->wave_start.size()) {
+            cudaEvent_t e;
+            CUDA_TRY(h, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+            h->wave_ev.push_back(e);
+        }
+        return QX_OK;
+    }
+    // the invariant steps, one launch per dependency level, on the handle's stream
+    int waves(const uint8_t* d_bits) {
+        if (!h->wave_ok) return QX_OK;
+        const size_t n = h->wave_ops.size();
+        char* wbase = h->ws + h->off_wave;
+        const int32_t* idx = (const int32_t*)(wbase + align_up((int64_t)(n * sizeof(POp)), 256));
+        if (!h->waves_on_device) {
+            CUDA_TRY(h, cudaMemcpyAsync(wbase, h->wave_ops.data(), n * sizeof(POp), cudaMemcpyHostToDevice, h->stream));
+            CUDA_TRY(h, cudaMemcpyAsync((void*)idx, h->wave_idx.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice,
+                                        h->stream));
+            CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+            h->waves_on_device = true;
+        }
+        PProg prog{};
+        prog.ops = (const POp*)wbase;
+        prog.n_ops = (int32_t)n;
+        prog.n_qubits = h->nq;
+        prog.leaves = (const float2*)(h->ws + h->off_leaf);
+        prog.inv = inv_base(h);
+        prog.bits = d_bits;
+        prog.n_b = 1;
+        prog.scratch_override = inv_base(h);
+        const int levels = (int)h->wave_start.size() - 1;
+        for (int L = 0; L < levels; ++L) {
+            size_t slot;
+            cudaError_t e = prof_begin(h, QX_KERNEL_WAVE, h->wave_flops[L], h->wave_bytes[L], &slot);
+            if (e == cudaSuccess)
+                e = launch_wave(prog.ops, idx + h->wave_start[L], h->wave_start[L + 1] - h->wave_start[L], prog,
+                                h->stream);
+            if (e == cudaSuccess) e = prof_end(h, slot);
+            if (e == cudaSuccess && on) e = cudaEventRecord(h->wave_ev[L], h->stream);
+            if (e != cudaSuccess) return fail(h, QX_ECUDA, "prologue wave launch failed: %s", cudaGetErrorString(e));
+            h->last_launches++;
+            h->last_flops += h->wave_flops[L];
+        }
+        waves_now = true;
+        if (on) last_on[0] = INT32_MAX / 2;  // per-pair steps go to the other streams first
         return QX_OK;
     }
     cudaStream_t stream(int s) const { return s == 0 ? h->stream : h->dstreams[s - 1]; }
@@ -1445,14 +1564,21 @@ struct Dag {
         seen.assign(S, std::vector<int>(S, -1));
         forked.assign(S, 0);
         forked[0] = 1;
+        wave_seen.assign(S, -1);
+        waves_now = false;
         CUDA_TRY(h, cudaEventRecord(h->fork_ev, h->stream));
         return QX_OK;
     }
     int issue(int j, const ItemCtx& ic, int64_t n_items) {
+        if (h->wave_ok && h->wave_of[j] >= 0) return QX_OK;  // ran in a prologue level
         if (!on) return run_op(h, h->ops[j], ic, n_items, h->stream);
         const int S = h->n_streams;
-        int s = -1;
+        int s = -1, wneed = -1;
         for (int i : h->deps[j]) {
+            if (h->wave_ok && h->wave_of[i] >= 0) {
+                if (waves_now) wneed = std::max(wneed, h->wave_of[i]);
+                continue;
+            }
             const int t = stream_of[i];
             if (t >= 0 && last_on[t] == i && (s < 0 || i > last_on[s])) s = t;
         }
@@ -1463,8 +1589,13 @@ struct Dag {
             CUDA_TRY(h, cudaStreamWaitEvent(stream(s), h->fork_ev, 0));
             forked[s] = 1;
         }
+        if (wneed >= 0 && s != 0 && wave_seen[s] < wneed) {
+            CUDA_TRY(h, cudaStreamWaitEvent(stream(s), h->wave_ev[wneed], 0));
+            wave_seen[s] = wneed;
+        }
         std::vector<int> latest(S, -1);
         for (int i : h->deps[j]) {
+            if (h->wave_ok && h->wave_of[i] >= 0) continue;
             const int t = stream_of[i];
             if (t >= 0 && t != s) latest[t] = std::max(latest[t], i);
         }
@@ -1553,6 +1684,7 @@ static int contract_impl(qx_ctx* h, const uint8_t* d_bits, int64_t n_bits, int64
             ic.n_b = (int32_t)nb;
             ic.n_items = ns * nb;
             if ((rc = dag.fork())) return rc;
+            if (prologue && (rc = dag.waves(d_bits))) return rc;
             for (size_t j = 0; j < h->ops.size(); ++j) {
                 const Op& op = h->ops[j];
                 if (!op.variant && !prologue) continue;
@@ -1664,6 +1796,7 @@ void qx_destroy(qx_handle h) {
     for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
     for (cudaEvent_t e : h->op_ev) cudaEventDestroy(e);
     for (cudaEvent_t e : h->join_ev) cudaEventDestroy(e);
+    for (cudaEvent_t e : h->wave_ev) cudaEventDestroy(e);
     if (h->fork_ev) cudaEventDestroy(h->fork_ev);
     for (cudaStream_t st : h->dstreams) cudaStreamDestroy(st);
     if (h->ws_owned && h->ws) {
@@ -1713,6 +1846,7 @@ static void unbind(qx_ctx* h) {
     h->items_cap = 0;
     h->leaves_on_device = false;
     h->pops_on_device = false;
+    h->waves_on_device = false;
 }
 
 int qx_set_plan(qx_handle h, const int64_t* order, int64_t n_steps, const int64_t* sliced, int32_t n_sliced,
@@ -1766,6 +1900,7 @@ int qx_bind_workspace(qx_handle h, void* dptr, int64_t bytes, int64_t max_bits) 
     h->items_cap = items;
     h->leaves_on_device = false;
     h->pops_on_device = false;
+    h->waves_on_device = false;
     return QX_OK;
 }
 
@@ -1961,12 +2096,12 @@ int qx_internal_contract_in(qx_ctx* h, char* buf, int64_t buf_bytes, const uint8
         bool ws_owned;
         int64_t max_bits, off_err, off_leaf, off_bits, off_acc, off_amps, off_inv, off_item, items_cap;
         bool leaves_on_device;
-        int64_t off_pops, off_counter, off_results, off_pscratch, off_pops_inv;
-        bool pops_on_device;
+        int64_t off_pops, off_counter, off_results, off_pscratch, off_pops_inv, off_wave;
+        bool pops_on_device, waves_on_device;
     } const saved = {h->ws,        h->ws_bytes, h->ws_owned,    h->max_bits,    h->off_err,    h->off_leaf,
                      h->off_bits,  h->off_acc,  h->off_amps,    h->off_inv,     h->off_item,   h->items_cap,
                      h->leaves_on_device, h->off_pops, h->off_counter, h->off_results, h->off_pscratch,
-                     h->off_pops_inv, h->pops_on_device};
+                     h->off_pops_inv, h->off_wave, h->pops_on_device, h->waves_on_device};
     int64_t fixed;
     layout(h, n_bits, &fixed);
     int64_t items = (buf_bytes - fixed) / (h->item_entries * 8);
@@ -1993,6 +2128,8 @@ int qx_internal_contract_in(qx_ctx* h, char* buf, int64_t buf_bytes, const uint8
         h->off_pscratch = saved.off_pscratch;
         h->off_pops_inv = saved.off_pops_inv;
         h->pops_on_device = saved.pops_on_device;
+        h->off_wave = saved.off_wave;
+        h->waves_on_device = saved.waves_on_device;
     };
     if (items < 1) {
         restore();
@@ -2006,6 +2143,7 @@ int qx_internal_contract_in(qx_ctx* h, char* buf, int64_t buf_bytes, const uint8
     h->items_cap = items;
     h->leaves_on_device = false;
     h->pops_on_device = false;
+    h->waves_on_device = false;
     int rc = QX_OK;
     cudaError_t e = cudaSetDevice(h->device);
     if (e != cudaSuccess) rc = fail(h, QX_ECUDA, "cudaSetDevice: %s", cudaGetErrorString(e));

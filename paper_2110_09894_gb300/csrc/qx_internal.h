@@ -160,6 +160,8 @@ struct PLaunch {
 };
 constexpr int kPersistSmem = 17408;
 cudaError_t launch_persist(const PLaunch& L, int grid, cudaStream_t st);
+// one launch of n independent invariant steps: CTA i runs ops[idx[i]] (device arrays)
+cudaError_t launch_wave(const POp* ops, const int32_t* idx, int n, const PProg& prog, cudaStream_t st);
 
 // FP64 compensated slice sum of persistent results, for many programs in one
 // launch, written straight to the amplitudes (times the leaf scale).

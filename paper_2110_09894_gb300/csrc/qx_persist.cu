@@ -379,6 +379,34 @@ cudaError_t launch_group_sum(const GSum* d_sums, int32_t n, int64_t total, cudaS
     return cudaGetLastError();
 }
 
+// ---- a wave of invariant steps in one launch ---------------------------------------------------
+// The steps that no slice or bitstring touches are mostly tiny (gate-sized tensors).  Grouped by
+// dependency level, the steps of a level are independent: CTA i runs step idx[i] with the code of
+// the persistent kernel, its operands in the leaf buffer or the invariant region and its result in
+// the invariant region (the program's scratch).
+__global__ void __launch_bounds__(256, 2) k_wave(const POp* __restrict__ ops, const int32_t* __restrict__ idx,
+                                                 const PProg prog) {
+    extern __shared__ float2 psm[];
+    const POp& op = ops[idx[blockIdx.x]];
+    PairCtx c;
+    c.s = 0;
+    c.bits = prog.bits;
+    c.scratch = prog.scratch_override;
+    c.prog = &prog;
+    switch (op.type) {
+        case POP_PERM: exec_perm(op, c, psm); break;
+        case POP_SMALL: exec_small(op, c, psm); break;
+        case POP_GEMM: exec_gemm(op, c, psm); break;
+        default: exec_dot(op, c, psm); break;
+    }
+}
+
+cudaError_t launch_wave(const POp* ops, const int32_t* idx, int n, const PProg& prog, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    k_wave<<<n, 256, kPersistSmem, st>>>(ops, idx, prog);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_persist(const PLaunch& L, int grid, cudaStream_t st) {
     if (L.n_work <= 0) return cudaSuccess;
     cudaError_t e = cudaMemsetAsync(L.counter, 0, sizeof(unsigned long long), st);
