@@ -189,7 +189,7 @@ def peaks():
 
 
 def traffic_for(kind):
-    """Per-launch DRAM bytes of a kernel kind from the committed ncu summary, if still current."""
+    """Per-launch DRAM bytes of a kernel kind from the committed ncu summary, if its source is unchanged."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
@@ -197,11 +197,14 @@ def traffic_for(kind):
         with open(p) as f:
             d = json.load(f)
         import hashlib
-        src = os.path.join(ROOT, "paper_2110_09894_gb300", "csrc", d.get("source", ""))
+        k = d.get("kernels", {}).get(kind)
+        if not k:
+            return None
+        src = os.path.join(ROOT, "paper_2110_09894_gb300", "csrc", k.get("source", ""))
         with open(src, "rb") as f:
-            if hashlib.sha256(f.read()).hexdigest() != d.get("source_sha256"):
+            if hashlib.sha256(f.read()).hexdigest() != k.get("source_sha256"):
                 return None
-        return d.get("kernels", {}).get(kind, {}).get("dram_bytes_per_launch")
+        return k.get("dram_bytes_per_launch")
     except (OSError, ValueError):
         return None
 
