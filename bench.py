@@ -141,6 +141,22 @@ def cpu_oracle_sample(w, n_slices_sample):
     return amps / dt, dt
 
 
+def cpu_model():
+    """The host CPU as /proc/cpuinfo names it (model name on x86; implementer / part ids on Arm)."""
+    try:
+        with open("/proc/cpuinfo") as f:
+            info = f.read()
+    except OSError:
+        return None
+    for key in ("model name", "Model name"):
+        for ln in info.splitlines():
+            if ln.startswith(key):
+                return ln.split(":", 1)[1].strip()
+    impl = sorted({ln.split(":", 1)[1].strip() for ln in info.splitlines() if ln.startswith("CPU implementer")})
+    part = sorted({ln.split(":", 1)[1].strip() for ln in info.splitlines() if ln.startswith("CPU part")})
+    return f"Arm implementer {','.join(impl)} part {','.join(part)}" if part else None
+
+
 def cpu_threads():
     try:
         return len(os.sched_getaffinity(0))
@@ -170,7 +186,8 @@ def reference_arm(args, w, rank, world):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
             "config": config_of(w, {"sample": sample}),
-            "cpu_baseline": {"value": value, "unit": "amplitudes/s", "cores": cpu_threads(), "kind": "oracle",
+            "cpu_baseline": {"value": value, "unit": "amplitudes/s", "cores": cpu_threads(), "cpu": cpu_model(),
+                             "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": "amplitudes/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -321,6 +338,15 @@ def main():
     bits = rank_bits(w, rank)
     n_bits = len(bits)
     amps_per_step = n_bits << w.n_open
+    # host-side build and plan compile, timed apart from the contraction (a host-only handle)
+    t0 = time.perf_counter()
+    hh = qx.qx_create(-1, precision=PRECISIONS[args.precision][0])
+    qx.qx_build_network(hh, w.n_qubits, w.gates, w.open_mask)
+    t1 = time.perf_counter()
+    qx.qx_set_plan(hh, w.order, w.sliced)
+    t2 = time.perf_counter()
+    qx.qx_destroy(hh)
+    host_ms = {"build_network": 1e3 * (t1 - t0), "set_plan": 1e3 * (t2 - t1)}
     with torch.cuda.stream(stream):
         c = qx.Contractor(w.n_qubits, w.gates, w.open_mask, w.order, w.sliced, n_bits, device=local, stream=stream,
                           max_items=args.max_items, precision=PRECISIONS[args.precision][0],
@@ -473,7 +499,8 @@ def main():
         ns = sample_slices(w)
         v, dt = cpu_oracle_sample(w, ns)
         cpu = {"value": v, "unit": "amplitudes/s", "cores": cpu_threads(), "kind": "oracle",
-               "sample": f"1 bitstring x {ns} of {w.n_slices} slices, complex128 numpy plan einsum, {dt:.1f} s"}
+               "sample": f"1 bitstring x {ns} of {w.n_slices} slices, complex128 numpy plan einsum, {dt:.1f} s",
+               "cpu": cpu_model()}
         if w.n_qubits <= 26:
             import oracle
             t0 = time.perf_counter()
@@ -493,6 +520,7 @@ def main():
                                     "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MiB write); "
                                           f"workspace {ws_gb:.1f} GB",
                                     "batches_per_step": c.stats()["batches"]}),
+            "ms_per_step_median": float(np.median(step_ms)), "host_ms": host_ms,
             "complex_tflops": tflops, "vs_plain_c64": vs_c64, "flops_per_step_algorithmic": flops_alg,
             "flops_per_step_executed": flops_exec,
             "latency_ms": {"p50": 1e3 * float(np.percentile(lat, 50)), "p99": 1e3 * float(np.percentile(lat, 99))},

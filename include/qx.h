@@ -152,6 +152,22 @@ int qx_contract_slices(qx_handle h, const uint8_t* bitstrings, int64_t n_bits, i
 int qx_contract_slices_device(qx_handle h, const uint8_t* d_bitstrings, int64_t n_bits, int64_t s_begin,
                               int64_t s_end, double* d_amps_out);
 
+/* Asynchronous requests for serving (the paper states the problem as a batch
+ * call; the request loop of the serving workload needs to overlap requests).
+ * qx_submit enqueues what qx_contract_slices_device does (device bitstrings
+ * d_bitstrings [n_bits][n_qubits], slices [s_begin, s_end), FP64 partial sums
+ * into d_amps_out [n_bits][2^n_open][2]) on the handle's stream, then, when
+ * h_amps_out is not NULL, a device-to-host copy of those amplitudes into it
+ * (pinned host memory for the copy to be asynchronous), and records a
+ * completion event; it returns at once with *req_out, a request number that
+ * increases per handle.  The buffers must stay valid until the request is
+ * done.  qx_poll sets *done = 1 once everything of request req has finished
+ * (then the number is forgotten) and 0 while it runs; unknown numbers give
+ * QX_EINVAL.  A device-side timeout shows in qx_device_status. */
+int qx_submit(qx_handle h, const uint8_t* d_bitstrings, int64_t n_bits, int64_t s_begin, int64_t s_end,
+              double* d_amps_out, double* h_amps_out, int64_t* req_out);
+int qx_poll(qx_handle h, int64_t req, int32_t* done);
+
 /* Graph replay (on by default): a call of qx_contract / qx_contract_device /
  * qx_contract_slices[_device] that repeats the previous call's device
  * buffers, bitstring count and slice range is captured once as a CUDA graph

@@ -165,6 +165,11 @@ struct qx_ctx {
     // Concurrent issue: op j follows the earlier ops in deps[j] (data and space-reuse hazards), so
     // independent branches of the contraction tree run side by side on the handle's extra streams
     // (their order in a captured graph becomes graph edges).  n_streams 1: all on `stream`, in order.
+    // asynchronous requests (qx_submit / qx_poll): completion events by request number
+    std::map<int64_t, cudaEvent_t> reqs;
+    std::vector<cudaEvent_t> req_pool;
+    int64_t next_req = 1;
+
     int n_streams = 8;
     bool fuse_layouts = true;  // products stored in the layout their consuming GEMM reads (batched executor)
     std::vector<std::vector<int>> deps;
@@ -1797,6 +1802,8 @@ void qx_destroy(qx_handle h) {
     for (cudaEvent_t e : h->op_ev) cudaEventDestroy(e);
     for (cudaEvent_t e : h->join_ev) cudaEventDestroy(e);
     for (cudaEvent_t e : h->wave_ev) cudaEventDestroy(e);
+    for (auto& kv : h->reqs) cudaEventDestroy(kv.second);
+    for (cudaEvent_t e : h->req_pool) cudaEventDestroy(e);
     if (h->fork_ev) cudaEventDestroy(h->fork_ev);
     for (cudaStream_t st : h->dstreams) cudaStreamDestroy(st);
     if (h->ws_owned && h->ws) {
@@ -1957,6 +1964,48 @@ int qx_contract_slices_device(qx_handle h, const uint8_t* d_bits, int64_t n_bits
     if (!d_bits || !d_amps) return fail(h, QX_EINVAL, "null buffer");
     CUDA_TRY(h, cudaSetDevice(h->device));
     return contract_graph(h, d_bits, n_bits, s_begin, s_end, d_amps);
+}
+
+int qx_submit(qx_handle h, const uint8_t* d_bits, int64_t n_bits, int64_t s_begin, int64_t s_end, double* d_amps,
+              double* h_amps, int64_t* req_out) {
+    if (!h || !req_out) return QX_EINVAL;
+    int rc = qx_contract_slices_device(h, d_bits, n_bits, s_begin, s_end, d_amps);
+    if (rc) return rc;
+    if (h_amps)
+        CUDA_TRY(h, cudaMemcpyAsync(h_amps, d_amps, (size_t)(n_bits << n_open(h)) * 16, cudaMemcpyDeviceToHost,
+                                    h->stream));
+    cudaEvent_t e;
+    if (!h->req_pool.empty()) {
+        e = h->req_pool.back();
+        h->req_pool.pop_back();
+    } else {
+        CUDA_TRY(h, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    }
+    cudaError_t r = cudaEventRecord(e, h->stream);
+    if (r != cudaSuccess) {
+        h->req_pool.push_back(e);
+        return fail(h, QX_ECUDA, "request event: %s", cudaGetErrorString(r));
+    }
+    const int64_t id = h->next_req++;
+    h->reqs[id] = e;
+    *req_out = id;
+    return QX_OK;
+}
+
+int qx_poll(qx_handle h, int64_t req, int32_t* done) {
+    if (!h || !done) return QX_EINVAL;
+    auto it = h->reqs.find(req);
+    if (it == h->reqs.end()) return fail(h, QX_EINVAL, "request %lld is unknown or was reported done", (long long)req);
+    const cudaError_t r = cudaEventQuery(it->second);
+    if (r == cudaErrorNotReady) {
+        *done = 0;
+        return QX_OK;
+    }
+    h->req_pool.push_back(it->second);
+    h->reqs.erase(it);
+    if (r != cudaSuccess) return fail(h, QX_ECUDA, "request %lld: %s", (long long)req, cudaGetErrorString(r));
+    *done = 1;
+    return QX_OK;
 }
 
 int qx_contract_device(qx_handle h, const uint8_t* d_bits, int64_t n_bits, double* d_amps) {

@@ -254,8 +254,7 @@ __device__ __forceinline__ void tmem_st16(uint32_t taddr, const float* v) {
         "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])), "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])),
         "r"(__float_as_uint(v[8])), "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])), "r"(__float_as_uint(v[11])),
         "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])), "r"(__float_as_uint(v[14])),
-        "r"(__float_as_uint(v[15]))
-        : "memory");
+        "r"(__float_as_uint(v[15])));
 }
 // 3xTF32 product with the A operand read from TMEM (row i in lane i, K along columns)
 __device__ __forceinline__ void mma_tf32_ta(uint32_t d, uint32_t a_tmem, uint64_t bd, uint32_t idesc, uint32_t acc) {
@@ -490,15 +489,25 @@ __device__ __forceinline__ void tc2_convert(const uint8_t* land, uint8_t* ms, in
     using L = Tc2<BN>;
     const int r = 32 * qq + lane;
     const uint32_t lanes = (uint32_t)(32 * qq) << 16;
+    // every shared-memory load of the slab first (A row and B chunks), then the splits and stores:
+    // the loads overlap instead of waiting behind each other's stores
+    constexpr int NBC = (BN / 2) * 8 / TC2_CONV;
+    float4 va[8], vb[NBC];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) va[j] = *(const float4*)(land + r * 128 + ((j ^ (r & 7)) << 4));
+#pragma unroll
+    for (int i = 0; i < NBC; ++i) {
+        const int c = ct + TC2_CONV * i;
+        const int n = c >> 3, j = c & 7;
+        vb[i] = *(const float4*)(land + L::A + n * 128 + ((j ^ (n & 7)) << 4));
+    }
 #pragma unroll
     for (int h = 0; h < 2; ++h) {  // 16 columns (four 16-byte chunks) at a time
         float hi[16], lo[16];
 #pragma unroll
         for (int jj = 0; jj < 4; ++jj) {
-            const int j = 4 * h + jj;
-            const float4 v = *(const float4*)(land + r * 128 + ((j ^ (r & 7)) << 4));
             float4 vh, vl;
-            split4(v, vh, vl);
+            split4(va[4 * h + jj], vh, vl);
             hi[4 * jj] = vh.x; hi[4 * jj + 1] = vh.y; hi[4 * jj + 2] = vh.z; hi[4 * jj + 3] = vh.w;
             lo[4 * jj] = vl.x; lo[4 * jj + 1] = vl.y; lo[4 * jj + 2] = vl.z; lo[4 * jj + 3] = vl.w;
         }
@@ -506,10 +515,10 @@ __device__ __forceinline__ void tc2_convert(const uint8_t* land, uint8_t* ms, in
         tmem_st16(tmem + lanes + ahi + 32 + 16 * h, lo);
     }
 #pragma unroll
-    for (int i = 0; i < (BN / 2) * 8 / TC2_CONV; ++i) {  // B: BN/2 rows x 8 chunks of 16 bytes
+    for (int i = 0; i < NBC; ++i) {  // B: BN/2 rows x 8 chunks of 16 bytes
         const int c = ct + TC2_CONV * i;
         const int n = c >> 3, j = c & 7;
-        const float4 v = *(const float4*)(land + L::A + n * 128 + ((j ^ (n & 7)) << 4));
+        const float4 v = vb[i];
         const float4 r0 = make_float4(v.x, -v.y, v.z, -v.w);  // row 2n: re, -im
         const float4 r1 = make_float4(v.y, v.x, v.w, v.z);    // row 2n+1: im, re
         const int ra = 2 * n, rb = 2 * n + 1;

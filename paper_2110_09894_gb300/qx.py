@@ -25,7 +25,7 @@ EXPORTS = ("qx_create", "qx_destroy", "qx_last_error", "qx_set_options", "qx_bui
            "qx_contract_slices", "qx_contract_slices_device", "qx_last_stats", "qx_set_profiling",
            "qx_profile_read", "qx_contract_device_static", "qx_device_status", "qx_group_create",
            "qx_group_scratch_size", "qx_group_bind", "qx_group_run", "qx_group_last_error", "qx_group_destroy",
-           "qx_set_graphs", "qx_set_streams", "qx_describe_plan")
+           "qx_set_graphs", "qx_set_streams", "qx_describe_plan", "qx_submit", "qx_poll")
 QX_STATIC_SCRATCH_BYTES = 64 << 20
 KERNEL_KINDS = ("permute", "small", "gemm", "sum", "tc_prep", "tc_gemm", "persist", "wave")
 
@@ -78,6 +78,8 @@ def load(path=None):
         "qx_device_status": ([vp], ctypes.c_int),
         "qx_set_graphs": ([vp, ctypes.c_int], ctypes.c_int),
         "qx_set_streams": ([vp, i32], ctypes.c_int),
+        "qx_submit": ([vp, vp, i64, i64, i64, vp, vp, ctypes.POINTER(i64)], ctypes.c_int),
+        "qx_poll": ([vp, i64, ctypes.POINTER(i32)], ctypes.c_int),
         "qx_describe_plan": ([vp, ctypes.c_char_p, i64, ctypes.POINTER(i64)], ctypes.c_int),
         "qx_group_create": ([ctypes.POINTER(vp), ctypes.POINTER(vp), i32, ctypes.POINTER(vp), ctypes.POINTER(i64),
                              ctypes.POINTER(vp), i32], ctypes.c_int),
@@ -206,6 +208,22 @@ def qx_describe_plan(h):
 
 def qx_set_graphs(h, enable):
     _check(h, load().qx_set_graphs(h, 1 if enable else 0))
+
+
+def qx_submit(h, d_bits_ptr, n_bits, s_begin, s_end, d_amps_ptr, h_amps_ptr=None):
+    """Enqueue a slice-range contraction (device buffers; optional pinned host copy); returns the request."""
+    req = ctypes.c_int64()
+    _check(h, load().qx_submit(h, ctypes.c_void_p(int(d_bits_ptr)), int(n_bits), int(s_begin), int(s_end),
+                               ctypes.c_void_p(int(d_amps_ptr)),
+                               ctypes.c_void_p(int(h_amps_ptr)) if h_amps_ptr else None, ctypes.byref(req)))
+    return req.value
+
+
+def qx_poll(h, req):
+    """True once request `req` has finished (reported once), False while it runs."""
+    done = ctypes.c_int32()
+    _check(h, load().qx_poll(h, int(req), ctypes.byref(done)))
+    return bool(done.value)
 
 
 def qx_set_streams(h, n_streams):

@@ -14,8 +14,10 @@ while other work is on the GPU:
 * each circuit owns a few execution lanes (a library handle with its own
   workspace and CUDA stream); lanes are created on demand while the device
   memory budget allows (admission by memory) and reused afterwards;
-* completion is detected with CUDA events; latency runs from a request's
-  arrival to the host seeing its amplitudes;
+* each chunk is one asynchronous request of the library (``qx_submit``: the
+  contraction and the copy of its amplitudes to pinned host memory on the
+  lane's stream); completion is polled with ``qx_poll``; latency runs from a
+  request's arrival to the host seeing its amplitudes;
 * a request is rejected at arrival if its circuit cannot get a lane within
   the memory budget or if its estimated work (plan flops x slices x
   bitstrings) exceeds max_request_flops.
@@ -54,7 +56,7 @@ class _Batch:
     chunks: list                # [(s0, s1)] still to run
     acc_s: np.ndarray = None    # Neumaier sum over chunks, complex as float64 pairs
     acc_c: np.ndarray = None
-    event: object = None
+    req: int = 0                # library request number of the chunk in flight
     inflight: tuple = None
 
 
@@ -174,14 +176,10 @@ class Server:
         return True
 
     def _launch_chunk(self, lane):
-        torch = self.torch
         b = lane.batch
         s0, s1 = b.chunks.pop(0)
-        with torch.cuda.stream(lane.stream):
-            lane.c.contract_device(b.bits_dev, b.amps_dev, s0, s1)
-            b.amps_host.copy_(b.amps_dev, non_blocking=True)
-            b.event = torch.cuda.Event()
-            b.event.record(lane.stream)
+        b.req = qx.qx_submit(lane.c.h, b.bits_dev.data_ptr(), b.bits_dev.shape[0], s0, s1, b.amps_dev.data_ptr(),
+                             b.amps_host.data_ptr())
         b.inflight = (s0, s1)
         self.stats["chunks"] += 1
 
@@ -212,7 +210,7 @@ class Server:
         busy = False
         for sc in self.circuits:
             for lane in sc.lanes:
-                if lane.batch is not None and lane.batch.event.query():
+                if lane.batch is not None and qx.qx_poll(lane.c.h, lane.batch.req):
                     self._finish_chunk(lane)
         for ci, sc in enumerate(self.circuits):
             while sc.queue:

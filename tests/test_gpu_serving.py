@@ -57,3 +57,41 @@ def test_memory_admission_rejects_what_cannot_fit(serve):
     srv = serve.Server(ws, max_bits=8, mem_budget=1 << 10)
     assert not srv.submit(serve.Request(0, 0, np.zeros((1, ws[0].n_qubits), np.uint8), 0.0))
     assert srv.stats["rejected"] == 1
+
+
+def test_submit_and_poll_requests(serve):
+    """qx_submit enqueues without waiting; qx_poll reports each request once, with the same bits as the
+    blocking slice-range call; unknown request numbers are an error."""
+    import time
+
+    import torch
+
+    from paper_2110_09894_gb300 import qx
+    from tests._util import grid_case
+    circ, om, order, sliced, bits = grid_case(3, 4, 8, 61, 1, 3, 5)
+    st = torch.cuda.Stream()
+    c = qx.Contractor(circ.n_qubits, C.gates_to_records(circ), om, order, sliced, 5, stream=st)
+    ref = c.contract_slices(bits, 2, 7)
+    d_bits = torch.from_numpy(bits).cuda()
+    outs, reqs = [], []
+    for k in range(3):
+        d_amps = torch.empty((5, 2, 2), dtype=torch.float64, device="cuda")
+        h_amps = torch.empty((5, 2, 2), dtype=torch.float64).pin_memory()
+        reqs.append(qx.qx_submit(c.h, d_bits.data_ptr(), 5, 2, 7, d_amps.data_ptr(), h_amps.data_ptr()))
+        outs.append((d_amps, h_amps))
+    assert reqs == sorted(reqs) and len(set(reqs)) == 3
+    pending, t0 = set(reqs), time.time()
+    while pending and time.time() - t0 < 60:
+        for r in list(pending):
+            if qx.qx_poll(c.h, r):
+                pending.discard(r)
+    assert not pending
+    for d_amps, h_amps in outs:
+        got = h_amps.numpy()
+        assert np.array_equal(got[..., 0] + 1j * got[..., 1], ref)
+        assert np.array_equal(d_amps.cpu().numpy(), got)
+    with pytest.raises(qx.QXError):
+        qx.qx_poll(c.h, reqs[0])  # reported already
+    with pytest.raises(qx.QXError):
+        qx.qx_poll(c.h, 10 ** 9)
+    qx.qx_device_status(c.h)

@@ -250,3 +250,19 @@ def test_planted_dropped_compensation_is_caught(monkeypatch):
     for x in xs:
         acc.add(np.array([x]))
     assert acc.value()[0] != math.fsum(xs)
+
+
+def test_porter_thomas_second_moment_of_deep_random_circuits():
+    """Deep random circuits scramble: p = 2^n |amp|^2 over all x has mean 1 (unitarity) and second
+    moment near 2 (the exponential law of Porter and Thomas); shallow ones are far from it."""
+    n = 16
+    zero = np.zeros((1, n), np.uint8)
+    moments = {}
+    for depth in (2, 16):
+        circ = C.random_grid_circuit(4, 4, depth, 4242)
+        a = oracle.sv_amplitudes(n, C.gates_to_records(circ), np.ones(n, np.uint8), zero).reshape(-1)
+        p = (1 << n) * np.abs(a) ** 2
+        assert abs(p.mean() - 1.0) < 1e-10
+        moments[depth] = float((p ** 2).mean())
+    assert abs(moments[16] - 2.0) < 0.1
+    assert moments[2] > 3.0
