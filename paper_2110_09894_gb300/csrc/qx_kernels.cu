@@ -625,6 +625,40 @@ __global__ void __launch_bounds__(256) k_dot_c64(const float2* __restrict__ A, i
     if (tid < MN) C[item * c_is + tid] = red[tid][0];
 }
 
+// Products with K <= 4 (k <= 2 shared bits): each output reads K entries of A and K of B, so the
+// work is writing C.  Threads run along the columns n (whole rows per store, or whole runs of the
+// placed columns), each keeps its column of B in registers and walks rows; the A entries of a row
+// are the same for the threads of a warp (N >= 32).
+template <int KB>
+__global__ void __launch_bounds__(256) k_gemm_smallk(const float2* __restrict__ A, int64_t a_is, bool akm,
+                                                    const float2* __restrict__ B, int64_t b_is, bool bkm,
+                                                    float2* __restrict__ C, int64_t c_is, int mb, int nb,
+                                                    int rows_per_cta, const __grid_constant__ OutMap om) {
+    constexpr int K = 1 << KB;
+    const int64_t item = blockIdx.y;
+    const int64_t M = (int64_t)1 << mb, N = (int64_t)1 << nb;
+    const int width = N < 256 ? (int)N : 256;            // columns per row pass
+    const int passes = 256 / width;                      // rows per pass
+    const int64_t col_blocks = N / width;
+    const int64_t cb = blockIdx.x % col_blocks, rb = blockIdx.x / col_blocks;
+    const int64_t n = cb * width + (threadIdx.x % width);
+    const int64_t r0 = rb * rows_per_cta + threadIdx.x / width;
+    const int64_t r1 = (rb + 1) * rows_per_cta < M ? (rb + 1) * rows_per_cta : M;
+    const float2* __restrict__ Ap = A + item * a_is;
+    const float2* __restrict__ Bp = B + item * b_is;
+    float2 b[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) b[k] = bkm ? Bp[n * K + k] : Bp[(int64_t)k * N + n];
+    float2* __restrict__ Cp = C + item * c_is;
+    const int64_t co = om.on ? place_bits(n, om.pos) : n;
+    for (int64_t r = r0; r < r1; r += passes) {
+        float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int k = 0; k < K; ++k) cfma(acc, akm ? Ap[r * K + k] : Ap[(int64_t)k * M + r], b[k]);
+        Cp[(om.on ? place_bits(r, om.pos + nb) : r * N) + co] = acc;
+    }
+}
+
 template <int BM, int BN>
 static void gemm_tile(dim3 grid, cudaStream_t st, const float2* a, int64_t a_is, bool akm, const float2* b,
                       int64_t b_is, bool bkm, float2* c, int64_t c_is, int mb, int nb, int kb, int tn,
@@ -652,6 +686,20 @@ cudaError_t launch_gemm_c64(const float2* a, int64_t a_is, bool a_kmajor, const 
     if (n_items <= 0) return cudaSuccess;
     OutMap om{};
     if (omp) om = *omp;
+    if (kb <= 2 && nb >= 5) {
+        // about 4096 outputs per CTA
+        const int64_t M = (int64_t)1 << mb, N = (int64_t)1 << nb;
+        const int64_t width = N < 256 ? N : 256;
+        const int64_t rows = std::max<int64_t>(256 / width, std::min<int64_t>(M, 4096 / width));
+        const int64_t blocks = ((M + rows - 1) / rows) * (N / width);
+        dim3 grid((unsigned)blocks, (unsigned)n_items);
+        switch (kb) {
+            case 0: k_gemm_smallk<0><<<grid, 256, 0, st>>>(a, a_is, a_kmajor, b, b_is, b_kmajor, c, c_is, mb, nb, (int)rows, om); break;
+            case 1: k_gemm_smallk<1><<<grid, 256, 0, st>>>(a, a_is, a_kmajor, b, b_is, b_kmajor, c, c_is, mb, nb, (int)rows, om); break;
+            default: k_gemm_smallk<2><<<grid, 256, 0, st>>>(a, a_is, a_kmajor, b, b_is, b_kmajor, c, c_is, mb, nb, (int)rows, om); break;
+        }
+        return cudaGetLastError();
+    }
     if (mb + nb <= 4 && kb >= 8) {
         if (om.on) return cudaErrorInvalidValue;  // the dot kernel writes the natural layout only
         dim3 grid((unsigned)n_items);
