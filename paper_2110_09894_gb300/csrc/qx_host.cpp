@@ -71,6 +71,11 @@ struct Op {
     // output position of each bit of the kernel's natural product index (columns low, then rows);
     // empty: the natural layout
     std::vector<int8_t> out_pos;
+    // a step contracting every leg with one operand in another order: that operand (perm_src) is
+    // read through the permutation to perm_legs (the other operand's order) inside the dot kernel
+    bool dot_perm = false;
+    int perm_src = -1;
+    std::vector<int> perm_legs;
     // OP_GEMM: operand storages, shapes
     int sa = -1, sb = -1;
     bool a_km = true, b_km = true;
@@ -429,6 +434,7 @@ static void op_access(const qx_ctx* h, const Op& op, std::vector<int>* rd, std::
     std::vector<int> r;
     if (op.type == OP_PERM) r = {node_st(op.src)};
     else if (op.type == OP_SMALL) r = {node_st(op.x), node_st(op.y)};
+    else if (op.dot_perm) r = {op.sa, node_st(op.perm_src)};
     else r = {op.sa, op.sb};
     rd->clear();
     for (int x : r)
@@ -908,11 +914,20 @@ static int compile_plan(qx_ctx* h, const int64_t* order, int64_t n_steps, const 
         g.kb = kb;
         g.a_km = best.akm;
         g.b_km = best.bkm;
+        // a full contraction (scalar per pair) with exactly one operand to permute: the dot kernel
+        // reads that operand through the permutation instead (no permuted copy in HBM)
+        const bool fuse_dot = fA.empty() && fB.empty() && kb >= 8 && best.pa != best.pb && h->opt.executor < 2;
         for (int side = 0; side < 2; ++side) {
             const int nid = side ? gb : ga;
             const bool perm = side ? best.pb : best.pa;
             const std::vector<int>& fr = side ? fB : fA;
             int sid;
+            if (perm && fuse_dot) {
+                g.dot_perm = true;
+                g.perm_src = nid;
+                g.perm_legs = best.S;
+                continue;
+            }
             if (perm) {
                 std::vector<int> tl = fr;
                 tl.insert(tl.end(), best.S.begin(), best.S.end());
@@ -934,6 +949,7 @@ static int compile_plan(qx_ctx* h, const int64_t* order, int64_t n_steps, const 
             }
             (side ? g.sb : g.sa) = sid;
         }
+        if (g.dot_perm && g.sa < 0) std::swap(g.sa, g.sb);  // the stored operand is A
         std::vector<int> cl = fA;
         cl.insert(cl.end(), fB.begin(), fB.end());
         const int st = new_storage(h, (int64_t)1 << cl.size(), variant, t);
@@ -977,7 +993,8 @@ static int compile_plan(qx_ctx* h, const int64_t* order, int64_t n_steps, const 
         if (op.type == OP_SMALL) { keep(op.x); keep(op.y); }
         if (op.type == OP_GEMM) {
             if (!h->stor[op.sa].variant) h->stor[op.sa].last = kLive;
-            if (!h->stor[op.sb].variant) h->stor[op.sb].last = kLive;
+            if (op.dot_perm) keep(op.perm_src);
+            else if (!h->stor[op.sb].variant) h->stor[op.sb].last = kLive;
         }
     }
     if (!R.variant && R.storage >= 0) h->stor[R.storage].last = kLive;
@@ -1218,7 +1235,7 @@ static void build_persistent_program(qx_ctx* h) {
     h->pops.clear();
     h->pops_inv.clear();
     for (const Op& op : h->ops)
-        if (op.tc || !op.out_pos.empty()) return;  // tensor-core steps and placed products run batched
+        if (op.tc || !op.out_pos.empty() || op.dot_perm) return;  // these run batched only
     const Node& R = h->nodes[h->root];
     if (!R.variant) return;  // nothing depends on the pair
     // invariant ops write the invariant region: their program runs with that region as scratch
@@ -1252,7 +1269,7 @@ static void build_waves(qx_ctx* h) {
     for (size_t j = 0; j < h->ops.size(); ++j) {
         const Op& op = h->ops[j];
         if (op.variant) continue;
-        if (op.tc || !op.out_pos.empty() || h->stor[op.dst].entries > kWaveEntries) return;
+        if (op.tc || !op.out_pos.empty() || op.dot_perm || h->stor[op.dst].entries > kWaveEntries) return;
         auto small_node = [&](int n) { return node_entries(h->nodes[n]) <= kWaveEntries; };
         if (op.type == OP_PERM && !small_node(op.src)) return;
         if (op.type == OP_SMALL && !(small_node(op.x) && small_node(op.y))) return;
@@ -1297,6 +1314,7 @@ static double op_bytes(const qx_ctx* h, const Op& op, int64_t n_items) {
     const double c = stor_b(op.dst);
     if (op.type == OP_PERM) return c + node_b(op.src);
     if (op.type == OP_SMALL) return c + node_b(op.x) + node_b(op.y);
+    if (op.dot_perm) return c + stor_b(op.sa) + node_b(op.perm_src);
     return c + stor_b(op.sa) + stor_b(op.sb);
 }
 
@@ -1321,6 +1339,15 @@ static int run_op(qx_ctx* h, const Op& op, const ItemCtx& ic, int64_t n_items, c
         e = launch_permute(perm_desc(h, op), ic, n_items, dp, dis, st);
     } else if (op.type == OP_SMALL) {
         e = launch_small(small_desc(h, op), ic, n_items, dp, dis, st);
+    } else if (op.dot_perm) {
+        float2* ap;
+        int64_t ais;
+        storage_addr(h, op.sa, &ap, &ais);
+        Op pv{};
+        pv.type = OP_PERM;
+        pv.src = op.perm_src;
+        pv.target_legs = op.perm_legs;
+        e = launch_dot_perm(perm_desc(h, pv), ic, n_items, ap, ais, dp, dis, st);
     } else if (!op.tc) {
         float2 *ap, *bp;
         int64_t ais, bis;
@@ -2022,6 +2049,7 @@ int qx_describe_plan(qx_handle h, char* buf, int64_t len, int64_t* needed) {
         const Op& op = h->ops[i];
         const char* kind = op.type == OP_PERM    ? "permute"
                            : op.type == OP_SMALL ? "gather"
+                           : op.dot_perm                    ? "dot_perm"
                            : op.tc == TC_FORM_3XTF32_DIRECT ? "tc_direct"
                            : op.tc                          ? "tc_prep"
                                                             : "gemm";

@@ -103,6 +103,9 @@ struct SumDesc {
 cudaError_t launch_permute(const PermDesc& d, const ItemCtx& ic, int64_t n_items, float2* out,
                            int64_t out_item_stride, cudaStream_t st);
 void perm_tables(const PermDesc& d, PermTables* tb);
+// per pair C = sum_k A[k] B[p(k)]: B = d.in read through the permutation d, A in the target order
+cudaError_t launch_dot_perm(const PermDesc& d, const ItemCtx& ic, int64_t n_items, const float2* a, int64_t a_is,
+                            float2* c, int64_t c_is, cudaStream_t st);
 cudaError_t launch_small(const SmallDesc& d, const ItemCtx& ic, int64_t n_items, float2* out,
                          int64_t out_item_stride, cudaStream_t st);
 // Batched complex GEMM, C[M][N] = A . B with A stored [M][K] (a_kmajor) or

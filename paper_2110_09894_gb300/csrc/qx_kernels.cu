@@ -625,6 +625,71 @@ __global__ void __launch_bounds__(256) k_dot_c64(const float2* __restrict__ A, i
     if (tid < MN) C[item * c_is + tid] = red[tid][0];
 }
 
+// A step that contracts every leg with one operand stored in another leg order: per pair
+// C = sum_k A[k] B[p(k)], B read through the permutation's tiles (as k_permute: a tile in input
+// order into shared memory, then walked in A's order), so the permuted copy of B never goes to HBM.
+// One CTA per pair; per-thread FP32 partials, then a fixed-order tree.
+__global__ void __launch_bounds__(256) k_dot_perm(const PermDesc d, const PermTables tb, const ItemCtx ic,
+                                                  const float2* __restrict__ A, int64_t a_is, float2* __restrict__ C,
+                                                  int64_t c_is) {
+    constexpr int LO = kPermLoBits, LM = (1 << LO) - 1;
+    __shared__ float2 tile[(1 << kPermTileBits) + (1 << kPermTileBits) / 32];
+    __shared__ int64_t s_in[128], s_out[128];
+    __shared__ int s_map[128];
+    __shared__ float2 red[256];
+    const int tid = threadIdx.x;
+    if (tid < 64) {
+        s_in[tid] = tb.in_lo[tid];
+        s_in[64 + tid] = tb.in_hi[tid];
+        s_out[tid] = tb.out_lo[tid];
+        s_out[64 + tid] = tb.out_hi[tid];
+        s_map[tid] = tb.map_lo[tid];
+        s_map[64 + tid] = tb.map_hi[tid];
+    }
+    __syncthreads();
+    const int64_t item = blockIdx.x;
+    const int n = 1 << d.t;
+    const int64_t tiles = (int64_t)1 << d.n_outer;
+    const int64_t ibase = fix_offset(d.in, ic, item);
+    const float2* __restrict__ Ap = A + item * a_is;
+    float2 acc = make_float2(0.f, 0.f);
+    for (int64_t tj = 0; tj < tiles; ++tj) {
+        int64_t ib = ibase, ob = 0;
+        uint64_t u = (uint64_t)tj;
+        while (u) {
+            const int i = __ffsll((long long)u) - 1;
+            ib += tb.outer_in[i];
+            ob += tb.outer_out[i];
+            u &= u - 1;
+        }
+        for (int j = tid; j < n; j += 256) tile[pad32(j)] = d.in.base[ib + s_in[j & LM] + s_in[64 + (j >> LO)]];
+        __syncthreads();
+        for (int j = tid; j < n; j += 256)
+            cfma(acc, Ap[ob + s_out[j & LM] + s_out[64 + (j >> LO)]], tile[pad32(s_map[j & LM] | s_map[64 + (j >> LO)])]);
+        __syncthreads();
+    }
+    red[tid] = acc;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (tid < w) {
+            red[tid].x += red[tid + w].x;
+            red[tid].y += red[tid + w].y;
+        }
+        __syncthreads();
+    }
+    if (tid == 0) C[item * c_is] = red[0];
+}
+
+cudaError_t launch_dot_perm(const PermDesc& d, const ItemCtx& ic, int64_t n_items, const float2* a, int64_t a_is,
+                            float2* c, int64_t c_is, cudaStream_t st) {
+    if (n_items <= 0) return cudaSuccess;
+    if (d.t > kPermTileBits || n_items > 0x7fffffffll) return cudaErrorInvalidValue;
+    PermTables tb;
+    perm_tables(d, &tb);
+    k_dot_perm<<<(unsigned)n_items, 256, 0, st>>>(d, tb, ic, a, a_is, c, c_is);
+    return cudaGetLastError();
+}
+
 // Products with K <= 4 (k <= 2 shared bits): each output reads K entries of A and K of B, so the
 // work is writing C.  Threads run along the columns n (whole rows per store, or whole runs of the
 // placed columns), each keeps its column of B in registers and walks rows; the A entries of a row
