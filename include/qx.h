@@ -84,7 +84,12 @@ typedef struct {
                                 batch of pairs, 2 persistent (one launch, one
                                 pair per CTA at a time; plans without
                                 tensor-core steps), 3 member of a group (see
-                                qx_group_*; contracts only through the group) */
+                                qx_group_*; contracts only through the group).
+                                Read by qx_set_plan: plans compiled for 0 / 1
+                                may store products in the layout the next
+                                GEMM reads and fuse the last permute into the
+                                dot, which only the batched launches do, so
+                                set 2 or 3 before qx_set_plan */
     int64_t timeout_cycles;  /* bound on device spin-waits; 0 = default      */
 } qx_options;
 
