@@ -2061,6 +2061,16 @@ int qx_describe_plan(qx_handle h, char* buf, int64_t len, int64_t* needed) {
                      (long long)op.step, kind, op.variant ? "pair" : "shared", op.mb, op.kb, op.nb, (int)op.a_km,
                      (int)op.b_km, (int)!op.out_pos.empty());
         out += line;
+        if (op.type == OP_SMALL) {  // address positions in X of the contracted legs
+            const SmallDesc sd = small_desc(h, op);
+            out.pop_back();
+            out += " xk=";
+            for (int i = 0; i < op.kb; ++i) {
+                snprintf(line, sizeof line, "%s%d", i ? "," : "", (int)sd.xk_pos[i]);
+                out += line;
+            }
+            out += "\n";
+        }
         // storages as region:offset+entries (entries rounded up as allocated), then the dependencies
         std::vector<int> rd, wr;
         bool sc;
