@@ -7,6 +7,8 @@ shares no code with the CUDA path.
 * ``statevector`` / ``sv_amplitudes``: state-vector evolution in C (Sec. II).
 * ``einsum.amplitudes``: plan-following pairwise contraction with slicing
   (Sec. II closing of outputs, Sec. III-A order and Eq. 2 slicing), numpy.
+* ``sampler.esup_run``: empirical-supremum rejection sampling of output
+  bitstrings from candidate amplitudes (Sec. III-B), plain Python.
 """
 from __future__ import annotations
 
@@ -18,6 +20,7 @@ import threading
 import numpy as np
 
 from . import einsum  # noqa: F401
+from . import sampler  # noqa: F401
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_HERE, "_build", "libqxoracle.so")

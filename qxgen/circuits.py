@@ -190,6 +190,36 @@ def random_bitstrings(n_qubits: int, count: int, seed: int) -> np.ndarray:
     return out
 
 
+def splitmix64_stream(seed: int, count: int) -> np.ndarray:
+    """The first `count` splitmix64 outputs of `seed`, vectorised.
+
+    Output k (k = 1, 2, ...) is the finaliser applied to seed + k * gamma, so
+    the stream is the one SplitMix64(seed).next_u64() produces.
+    """
+    k = np.arange(1, count + 1, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        z = np.uint64(seed & MASK64) + k * np.uint64(0x9E3779B97F4A7C15)
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+    return z ^ (z >> np.uint64(31))
+
+
+def sampler_draws(n_qubits: int, count: int, seed: int):
+    """Uniform candidate bitstrings and uniforms for a rejection sampler.
+
+    Output 2i of the splitmix64 stream gives candidate i (its top n_qubits
+    bits, qubit 0 the most significant) and output 2i+1 its uniform in
+    [0, 1) (top 53 bits).  Returns (bitstrings uint8 [count][n_qubits],
+    candidate indices int64 [count], uniforms float64 [count]).
+    """
+    z = splitmix64_stream(seed, 2 * count).reshape(count, 2) if count else np.zeros((0, 2), np.uint64)
+    idx = (z[:, 0] >> np.uint64(64 - n_qubits)).astype(np.int64)
+    shifts = np.arange(n_qubits - 1, -1, -1, dtype=np.int64)
+    bits = ((idx[:, None] >> shifts[None, :]) & 1).astype(np.uint8)
+    u = (z[:, 1] >> np.uint64(11)).astype(np.float64) * (1.0 / (1 << 53))
+    return bits, idx, u
+
+
 def ghz_circuit(n: int) -> Circuit:
     """H on qubit 0 followed by the CNOT chain (0,1), (1,2), ..."""
     c = Circuit(n)
