@@ -39,7 +39,9 @@ def parse():
     p.add_argument("--steps", type=int, default=10)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--workload", default="sliced", choices=["small", "sliced", "large", "batched", "serving"])
+    p.add_argument("--workload", default="sliced", choices=["small", "sliced", "large", "batched", "serving", "sampling"])
+    p.add_argument("--sample-batch", type=int, default=1024, help="candidates per contraction when sampling")
+    p.add_argument("--samples-per-step", type=int, default=256)
     p.add_argument("--serve-seconds", type=float, default=20.0, help="arrival window of the serving run")
     p.add_argument("--serve-rate", type=float, default=200.0, help="mean requests per second (Poisson)")
     p.add_argument("--serve-max-flops", type=float, default=5e14, help="largest request the server admits")
@@ -325,6 +327,45 @@ def serving_bench(args):
     print(json.dumps(line), flush=True)
 
 
+def sampling_bench(args):
+    """Output bitstrings of the 20-qubit sliced workload by empirical-supremum rejection sampling (Sec. III-B)."""
+    import torch
+    from paper_2110_09894_gb300 import build as qxbuild
+    from paper_2110_09894_gb300 import qx
+    from paper_2110_09894_gb300.sampler import ESupSampler
+    qxbuild.build()
+    w = W.sliced()
+    c = qx.Contractor(w.n_qubits, w.gates, w.open_mask, w.order, w.sliced, args.sample_batch,
+                      precision=PRECISIONS[args.precision][0])
+    s = ESupSampler(c, seed=1, warmup=2 * args.sample_batch)
+    per = args.samples_per_step
+    for _ in range(max(args.warmup, 3)):
+        s.sample(per)
+    it0, con0 = s.iterations, s.contracted
+    sampler = ClockSampler(0)
+    sampler.start()
+    times = []
+    for _ in range(args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        x = s.sample(per)  # synchronous: counts come back to the host every call
+        times.append(time.perf_counter() - t0)
+        assert x.shape == (per, w.n_qubits)
+    clocks = sampler.stop()
+    total = sum(times)
+    line = {"metric": "samples/s", "value": per * args.steps / total, "unit": "samples/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": total / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": args.precision,
+            "data": "synthetic",
+            "config": {"workload": "sampling: grid 4x5 depth 12, 6 sliced bonds (64 slices), uniform candidates",
+                       "samples_per_step": per, "candidates_per_contraction": s.batch,
+                       "warmup_iterations": 2 * args.sample_batch},
+            "candidates_per_sample": (s.iterations - it0) / (per * args.steps),
+            "amplitudes_per_s": (s.contracted - con0) / total, "bound_m": s.m, "clocks": clocks}
+    c.close()
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -334,6 +375,8 @@ def main():
         return group_bench(args)
     if args.impl == "ours" and args.workload == "serving":
         return serving_bench(args)
+    if args.impl == "ours" and args.workload == "sampling":
+        return sampling_bench(args)
     w = workload(args.workload) if args.workload in ("small", "sliced", "large") else W.sliced()
     if args.impl == "reference":
         reference_arm(args, w, rank, world)

@@ -240,6 +240,52 @@ int qx_device_status(qx_handle h);
 #define QX_STATIC_SCRATCH_BYTES (64ll << 20)
 int qx_contract_device_static(qx_handle h, const uint8_t* d_bitstrings, int64_t n_bits, double* d_amps_out);
 
+/* Empirical-supremum rejection sampling of output bitstrings (Sec. III-B;
+ * the method of Caffo, Booth and Davison, 2002).  Target law p(x) =
+ * |<x|C|0>|^2 over the N = 2^n_qubits bitstrings, uniform proposal, density
+ * ratio w(x) = p(x) N.  Iteration i takes candidate X_i and uniform U_i
+ * (both drawn by the caller, so the run is reproducible), accepts X_i when
+ * U_i * M < w(X_i) (FP64, the test U < w / M without a division, p = re*re
+ * + im*im rounded term by term, M the bound BEFORE this iteration), then
+ * sets M = max(M, w(X_i)); a NaN w is never accepted and never raises M.
+ * Iterations i < n_warmup only move M.  The run stops right after its
+ * max_out-th acceptance (later candidates are not consumed and do not touch
+ * M) or when the candidates run out.  A fresh run starts with *m_inout = 1;
+ * to continue a run, pass back the returned bound, the candidates from
+ * *n_consumed on, and the warm-up still left.  Results are exactly those of
+ * the one-at-a-time algorithm (the batch is scanned on the GPU: a prefix
+ * maximum and a stream compaction).
+ *
+ * qx_esup_accept takes the candidates' amplitudes:
+ *   d_amps      device, n_cand x {re, im} doubles (amplitude of candidate i)
+ *   d_uniforms  device, n_cand doubles
+ *   n_qubits    N = 2^n_qubits, 1 .. 62
+ *   d_accepted  device, room for min(max_out, n_cand) int64: the accepted
+ *               iterations' indices in [0, n_cand), increasing
+ *   m_inout, n_accepted, n_consumed: host values
+ * It runs on the handle's stream and synchronises it (the counts come back
+ * to the host).  Needs no network, plan or workspace.
+ *
+ * qx_esup_sample first contracts the candidates with the handle's network,
+ * plan and bound workspace (every qubit closed, else QX_EINVAL), in pieces
+ * of at most the workspace's bitstring count, then runs the tests of each
+ * piece, stopping early once max_out are accepted:
+ *   d_candidates  device, n_cand x n_qubits bytes of 0/1 (not validated)
+ *   d_amps        device, n_cand x {re, im} doubles, receives the
+ *                 amplitudes of the pieces contracted (all of
+ *                 [0, *n_consumed) at least)
+ * Other arguments as above.  QX_ESTATE without a network, plan or
+ * workspace; QX_ETIMEOUT if a bounded device wait expired.
+ *
+ * Both: n_cand == 0 or max_out == 0 consumes nothing (M unchanged);
+ * negative counts and NULL pointers give QX_EINVAL. */
+int qx_esup_accept(qx_handle h, const double* d_amps, const double* d_uniforms, int64_t n_cand, int32_t n_qubits,
+                   int64_t n_warmup, int64_t max_out, double* m_inout, int64_t* d_accepted, int64_t* n_accepted,
+                   int64_t* n_consumed);
+int qx_esup_sample(qx_handle h, const uint8_t* d_candidates, const double* d_uniforms, int64_t n_cand,
+                   int64_t n_warmup, int64_t max_out, double* m_inout, double* d_amps, int64_t* d_accepted,
+                   int64_t* n_accepted, int64_t* n_consumed);
+
 /* Groups: the pairs of many networks in one persistent launch (uneven
  * circuits and slice counts side by side; Sec. IV-A's slice and bitstring
  * levels of parallelism across several circuits).  Every member handle must be

@@ -91,6 +91,7 @@ struct Op {
 struct qx_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
+    void* d_small = nullptr;  // 256 device bytes for small results (sampler counts), allocated on first use
     qx_options opt{};
     std::string err;
 
@@ -1837,6 +1838,10 @@ void qx_destroy(qx_handle h) {
         cudaSetDevice(h->device);
         cudaFree(h->ws);
     }
+    if (h->d_small) {
+        cudaSetDevice(h->device);
+        cudaFree(h->d_small);
+    }
     delete h;
 }
 
@@ -2170,6 +2175,24 @@ int qx_last_stats(qx_handle h, double* flops, int64_t* launches, int64_t* batche
 int qx_internal_device(const qx_ctx* h) { return h->device; }
 
 int qx_internal_fail(qx_ctx* h, int code, const char* msg) { return fail(h, code, "%s", msg); }
+
+cudaStream_t qx_internal_stream(const qx_ctx* h) { return h->stream; }
+
+void* qx_internal_small(qx_ctx* h) {
+    if (!h->d_small && cudaMalloc(&h->d_small, 256) != cudaSuccess) {
+        h->d_small = nullptr;
+        cudaGetLastError();
+    }
+    return h->d_small;
+}
+
+int qx_internal_shape(const qx_ctx* h, int* n_qubits, int64_t* n_open_out, int64_t* max_bits, int* ready) {
+    *n_qubits = h->have_net ? h->nq : 0;
+    *n_open_out = h->have_net ? n_open(h) : 0;
+    *max_bits = h->ws ? h->max_bits : 0;
+    *ready = h->have_plan && h->ws != nullptr;
+    return QX_OK;
+}
 
 int qx_internal_contract_in(qx_ctx* h, char* buf, int64_t buf_bytes, const uint8_t* d_bits, int64_t n_bits,
                             double* d_amps) {

@@ -227,3 +227,10 @@ int qx_internal_contract_in(qx_ctx* h, char* buf, int64_t buf_bytes, const uint8
                             double* d_amps);
 int qx_internal_device(const qx_ctx* h);
 int qx_internal_fail(qx_ctx* h, int code, const char* msg);
+cudaStream_t qx_internal_stream(const qx_ctx* h);
+// 256 bytes of device memory owned by the handle (NULL if the allocation fails)
+void* qx_internal_small(qx_ctx* h);
+// qubits and open outputs of the built network (0 without one), the
+// bitstrings per call the bound workspace takes (0 unbound), and whether a
+// plan and a workspace are both in place
+int qx_internal_shape(const qx_ctx* h, int* n_qubits, int64_t* n_open, int64_t* max_bits, int* ready);

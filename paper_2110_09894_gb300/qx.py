@@ -25,7 +25,8 @@ EXPORTS = ("qx_create", "qx_destroy", "qx_last_error", "qx_set_options", "qx_bui
            "qx_contract_slices", "qx_contract_slices_device", "qx_last_stats", "qx_set_profiling",
            "qx_profile_read", "qx_contract_device_static", "qx_device_status", "qx_group_create",
            "qx_group_scratch_size", "qx_group_bind", "qx_group_run", "qx_group_last_error", "qx_group_destroy",
-           "qx_set_graphs", "qx_set_streams", "qx_describe_plan", "qx_submit", "qx_poll")
+           "qx_set_graphs", "qx_set_streams", "qx_describe_plan", "qx_submit", "qx_poll", "qx_esup_accept",
+           "qx_esup_sample")
 QX_STATIC_SCRATCH_BYTES = 64 << 20
 KERNEL_KINDS = ("permute", "small", "gemm", "sum", "tc_prep", "tc_gemm", "persist", "wave")
 
@@ -89,6 +90,10 @@ def load(path=None):
         "qx_group_last_error": ([vp], ctypes.c_char_p),
         "qx_group_destroy": ([vp], None),
         "qx_contract_device_static": ([vp, vp, i64, vp], ctypes.c_int),
+        "qx_esup_accept": ([vp, vp, vp, i64, i32, i64, i64, ctypes.POINTER(ctypes.c_double), vp,
+                            ctypes.POINTER(i64), ctypes.POINTER(i64)], ctypes.c_int),
+        "qx_esup_sample": ([vp, vp, vp, i64, i64, i64, ctypes.POINTER(ctypes.c_double), vp, vp,
+                            ctypes.POINTER(i64), ctypes.POINTER(i64)], ctypes.c_int),
         "qx_profile_read": ([vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64),
                              ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     }
@@ -196,6 +201,29 @@ def qx_contract_device_static(h, d_bits_ptr, n_bits, d_amps_ptr):
     """Contract with the library's built-in scratch array: nothing is allocated."""
     _check(h, load().qx_contract_device_static(h, ctypes.c_void_p(int(d_bits_ptr)), int(n_bits),
                                                ctypes.c_void_p(int(d_amps_ptr))))
+
+
+def qx_esup_accept(h, d_amps_ptr, d_uniforms_ptr, n_cand, n_qubits, n_warmup, max_out, m, d_accepted_ptr):
+    """Rejection tests of the empirical-supremum sampler over given amplitudes.
+
+    Returns (accepted count, iterations consumed, bound M after them)."""
+    mm, na, nc = ctypes.c_double(m), ctypes.c_int64(), ctypes.c_int64()
+    _check(h, load().qx_esup_accept(h, ctypes.c_void_p(int(d_amps_ptr)), ctypes.c_void_p(int(d_uniforms_ptr)),
+                                    int(n_cand), int(n_qubits), int(n_warmup), int(max_out), ctypes.byref(mm),
+                                    ctypes.c_void_p(int(d_accepted_ptr)), ctypes.byref(na), ctypes.byref(nc)))
+    return na.value, nc.value, mm.value
+
+
+def qx_esup_sample(h, d_cand_ptr, d_uniforms_ptr, n_cand, n_warmup, max_out, m, d_amps_ptr, d_accepted_ptr):
+    """Contract the candidates, then run the sampler's tests over them.
+
+    Returns (accepted count, iterations consumed, bound M after them)."""
+    mm, na, nc = ctypes.c_double(m), ctypes.c_int64(), ctypes.c_int64()
+    _check(h, load().qx_esup_sample(h, ctypes.c_void_p(int(d_cand_ptr)), ctypes.c_void_p(int(d_uniforms_ptr)),
+                                    int(n_cand), int(n_warmup), int(max_out), ctypes.byref(mm),
+                                    ctypes.c_void_p(int(d_amps_ptr)), ctypes.c_void_p(int(d_accepted_ptr)),
+                                    ctypes.byref(na), ctypes.byref(nc)))
+    return na.value, nc.value, mm.value
 
 
 def qx_describe_plan(h):

@@ -138,3 +138,22 @@ def test_state_errors(qx):
 def test_missing_library_fails_loudly(qx, tmp_path):
     with pytest.raises(ImportError):
         qx.load(str(tmp_path / "libqx.so"))
+
+
+def test_sampler_argument_checks_on_host_only_handle(qx):
+    h = qx.qx_create(device=-1)
+    # nothing to consume: no device work, bound unchanged
+    assert qx.qx_esup_accept(h, 0, 0, 0, 10, 0, 5, 2.5, 0) == (0, 0, 2.5)
+    for args in [(0, 0, -1, 10, 0, 5, 1.0, 0), (0, 0, 4, 0, 0, 5, 1.0, 0), (0, 0, 4, 63, 0, 5, 1.0, 0),
+                 (0, 0, 4, 10, -2, 5, 1.0, 0), (0, 0, 4, 10, 0, 5, 1.0, 0)]:
+        with pytest.raises(qx.QXError) as e:
+            qx.qx_esup_accept(h, *args)
+        assert e.value.code == qx.QX_EINVAL
+    with pytest.raises(qx.QXError) as e:  # no network yet
+        qx.qx_esup_sample(h, 0, 0, 4, 0, 5, 1.0, 0, 0)
+    assert e.value.code == qx.QX_ESTATE
+    qx.qx_build_network(h, 3, C.gates_to_records(C.ghz_circuit(3)), np.array([0, 0, 1], np.uint8))
+    with pytest.raises(qx.QXError) as e:  # an open qubit
+        qx.qx_esup_sample(h, 0, 0, 4, 0, 5, 1.0, 0, 0)
+    assert e.value.code == qx.QX_EINVAL
+    qx.qx_destroy(h)
