@@ -91,6 +91,15 @@ typedef struct {
                                 dot, which only the batched launches do, so
                                 set 2 or 3 before qx_set_plan */
     int64_t timeout_cycles;  /* bound on device spin-waits; 0 = default      */
+    int32_t no_slice_level;  /* read by qx_set_plan.  0 (default): with
+                                executor 0 / 1, intermediates that depend on
+                                the slice but on no output bit are computed
+                                once per slice and shared by the slice's
+                                bitstrings; 1: once per (slice, bitstring)
+                                pair, as executors 2 and 3 always do.  The
+                                amplitudes agree to FP32 rounding (launches
+                                over fewer items may pick other tiles). */
+    int32_t pad;
 } qx_options;
 
 /* Create a handle on CUDA device `device`; `cuda_stream` is a cudaStream_t

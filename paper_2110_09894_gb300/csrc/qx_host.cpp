@@ -41,7 +41,8 @@ struct Node {
     std::vector<int> pos;   // address bit of each leg
     std::vector<std::pair<int32_t, int64_t>> fix;  // (source, stride) of fixed legs
     bool const_one = false;
-    bool variant = false;
+    bool variant = false;   // level > 0
+    int level = 0;          // 0: invariant, 1: depends on the slice only, 2: on the bitstring (and slice)
     bool leaf = false;
     int64_t leaf_off = 0;   // entries into the leaf buffer
     int storage = -1;       // intermediate storage id
@@ -50,7 +51,8 @@ struct Node {
 
 struct Storage {
     int64_t entries = 0;
-    bool variant = false;
+    bool variant = false;   // level > 0
+    int level = 0;          // region: 0 invariant, 1 per slice, 2 per pair
     int64_t def = 0, last = 0;
     int64_t off = 0;        // entries within its region (per pair for the item region)
 };
@@ -59,7 +61,8 @@ enum OpType { OP_PERM, OP_SMALL, OP_GEMM };
 
 struct Op {
     OpType type;
-    bool variant;
+    bool variant;           // level > 0
+    int level = 0;          // runs once (0), per slice (1) or per pair (2)
     int64_t step;
     // OP_PERM: node -> storage
     int src = -1;
@@ -118,9 +121,10 @@ struct qx_ctx {
     int root = -1;
     int64_t peak_entries = 0;
     int64_t item_entries = 0;  // per pair
+    int64_t slice_entries = 0; // per slice (intermediates that no output bit touches)
     int64_t inv_entries = 0;
     int64_t n_slices = 1;
-    double flops_inv = 0, flops_item = 0;
+    double flops_inv = 0, flops_slice = 0, flops_item = 0;
 
     // persistent executor program (variant ops, in order)
     bool persist_ok = false;
@@ -148,6 +152,7 @@ struct qx_ctx {
     bool ws_owned = false;
     int64_t max_bits = 0;
     int64_t off_err = 0, off_leaf = 0, off_bits = 0, off_acc = 0, off_amps = 0, off_inv = 0, off_item = 0;
+    int64_t off_slice = 0, slices_cap = 0;  // per-slice region: room for slices_cap slices
     int64_t off_pops = 0, off_counter = 0, off_results = 0, off_pscratch = 0, off_pops_inv = 0, off_wave = 0;
     int64_t items_cap = 0;
     bool leaves_on_device = false;
@@ -366,10 +371,11 @@ static Operand make_operand(const qx_ctx* h, int node) {
 
 static int64_t node_entries(const Node& n) { return (int64_t)1 << n.legs.size(); }
 
-static int new_storage(qx_ctx* h, int64_t entries, bool variant, int64_t def) {
+static int new_storage(qx_ctx* h, int64_t entries, int level, int64_t def) {
     Storage s;
     s.entries = entries;
-    s.variant = variant;
+    s.variant = level > 0;
+    s.level = level;
     s.def = def;
     s.last = def;
     h->stor.push_back(s);
@@ -381,23 +387,24 @@ static void use_node(qx_ctx* h, int node, int64_t step) {
     if (nd.storage >= 0) h->stor[nd.storage].last = std::max(h->stor[nd.storage].last, step);
 }
 
-static Node contiguous_node(const std::vector<int>& legs, bool variant, int storage) {
+static Node contiguous_node(const std::vector<int>& legs, int level, int storage) {
     Node n;
     n.legs = legs;
     const int r = (int)legs.size();
     n.pos.resize(r);
     for (int j = 0; j < r; ++j) n.pos[j] = r - 1 - j;
-    n.variant = variant;
+    n.variant = level > 0;
+    n.level = level;
     n.storage = storage;
     n.under_rank = r;
     return n;
 }
 
 // First-fit offsets for storages of one region (intervals [def, last] inclusive).
-static int64_t assign_offsets(qx_ctx* h, bool variant) {
+static int64_t assign_offsets(qx_ctx* h, int level) {
     std::vector<int> ids;
     for (int i = 0; i < (int)h->stor.size(); ++i)
-        if (h->stor[i].variant == variant) ids.push_back(i);
+        if (h->stor[i].level == level) ids.push_back(i);
     std::sort(ids.begin(), ids.end(), [&](int a, int b) {
         if (h->stor[a].def != h->stor[b].def) return h->stor[a].def < h->stor[b].def;
         return a < b;
@@ -448,7 +455,7 @@ static void op_access(const qx_ctx* h, const Op& op, std::vector<int>* rd, std::
 
 // Hazards between ops, in plan order: op j follows op i < j when j reads storage that i writes,
 // writes storage that i reads, or writes storage that i writes.  Storages of the same region
-// (per-pair or invariant) conflict when their entry ranges overlap, since the liveness allocator
+// (per-pair, per-slice or invariant) conflict when their entry ranges overlap, since the liveness allocator
 // gives the space of dead tensors to later ones.  Ops using the scale words follow one another.
 static void compute_deps(qx_ctx* h) {
     const size_t n = h->ops.size();
@@ -462,7 +469,7 @@ static void compute_deps(qx_ctx* h) {
     auto overlap = [&](int a, int b) {
         const Storage& A = h->stor[a];
         const Storage& B = h->stor[b];
-        if (A.variant != B.variant) return false;
+        if (A.level != B.level) return false;
         return A.off < B.off + align_up(B.entries, kAlignEntries) && B.off < A.off + align_up(A.entries, kAlignEntries);
     };
     auto any = [&](const std::vector<int>& x, const std::vector<int>& y) {
@@ -484,6 +491,9 @@ static int compile_plan(qx_ctx* h, const int64_t* order, int64_t n_steps, const 
         return fail(h, QX_EINVAL, "plan has %lld steps, a full contraction of %lld tensors needs %lld",
                     (long long)n_steps, (long long)N, (long long)(N - 1));
     if (n_sliced < 0 || n_sliced > 40) return fail(h, QX_EINVAL, "n_sliced %d out of range [0, 40]", n_sliced);
+    // Intermediates that depend on the slice but on no output bit are computed once per slice and
+    // shared by every bitstring of it (batched executor only).
+    const bool slice_level = h->opt.executor < 2 && !h->opt.no_slice_level;
     std::vector<int> fixsrc(h->n_bonds, INT32_MIN);  // source of each fixed bond
     for (int j = 0; j < n_sliced; ++j) {
         const int64_t e = sliced[j];
@@ -524,7 +534,12 @@ static int compile_plan(qx_ctx* h, const int64_t* order, int64_t n_steps, const 
                     nd.pos.push_back(p);
                 }
             }
-            nd.variant = !nd.fix.empty();
+            // a fixed output leg makes a leaf depend on the bitstring, a sliced leg on the slice; with
+            // the slice level off (persistent executors) anything fixed is per pair
+            bool by_bits = false;
+            for (auto& f : nd.fix) by_bits |= f.first < 0;
+            nd.level = nd.fix.empty() ? 0 : (by_bits || !slice_level) ? 2 : 1;
+            nd.variant = nd.level > 0;
         }
         h->nodes.push_back(nd);
     }
@@ -789,7 +804,8 @@ static int compile_plan(qx_ctx* h, const int64_t* order, int64_t n_steps, const 
         for (int e : B.legs)
             if (std::find(A.legs.begin(), A.legs.end(), e) == A.legs.end()) freeB.push_back(e);
         const int kb = (int)shared.size();
-        const bool variant = A.variant || B.variant;
+        const int level = std::max(A.level, B.level);
+        const bool variant = level > 0;
         const int rc = (int)(freeA.size() + freeB.size());
         if (rc > kMaxRank) return fail(h, QX_EINVAL, "step %lld: intermediate rank %d too large", (long long)t, rc);
         h->peak_entries = std::max(h->peak_entries, (int64_t)1 << rc);
@@ -821,7 +837,7 @@ static int compile_plan(qx_ctx* h, const int64_t* order, int64_t n_steps, const 
                 variant ? fused_layout(t, fx, false, fy, true, {{true, 4}, {false, 2}, {true, 2}}) : std::vector<int>{};
             std::vector<int> cl = fx;
             cl.insert(cl.end(), fy.begin(), fy.end());
-            const int st = new_storage(h, (int64_t)1 << cl.size(), variant, t);
+            const int st = new_storage(h, (int64_t)1 << cl.size(), level, t);
             Op op{};
             op.type = OP_SMALL;
             op.fy = fy;
@@ -830,6 +846,7 @@ static int compile_plan(qx_ctx* h, const int64_t* order, int64_t n_steps, const 
                 cl = D;
             }
             op.variant = variant;
+            op.level = level;
             op.step = t;
             op.x = xn;
             op.y = yn;
@@ -840,7 +857,7 @@ static int compile_plan(qx_ctx* h, const int64_t* order, int64_t n_steps, const 
             op.nb = (int)fy.size();
             op.flops = 8.0 * std::ldexp(1.0, op.mb + op.kb + op.nb);
             h->ops.push_back(op);
-            h->nodes.push_back(contiguous_node(cl, variant, st));
+            h->nodes.push_back(contiguous_node(cl, level, st));
             continue;
         }
 
@@ -909,6 +926,7 @@ static int compile_plan(qx_ctx* h, const int64_t* order, int64_t n_steps, const 
         Op g{};
         g.type = OP_GEMM;
         g.variant = variant;
+        g.level = level;
         g.step = t;
         g.mb = (int)fA.size();
         g.nb = (int)fB.size();
@@ -933,13 +951,15 @@ static int compile_plan(qx_ctx* h, const int64_t* order, int64_t n_steps, const 
                 std::vector<int> tl = fr;
                 tl.insert(tl.end(), best.S.begin(), best.S.end());
                 const Node& X = h->nodes[nid];
-                // an invariant operand of a per-pair step is permuted once in the prologue and kept
-                const bool keep = !X.variant && variant;
-                sid = new_storage(h, node_entries(X), X.variant, t);
+                // an operand of a lower level is permuted at its own level (an invariant one once in the
+                // prologue, and kept; a per-slice one once per slice)
+                const bool keep = X.level == 0 && variant;
+                sid = new_storage(h, node_entries(X), X.level, t);
                 if (keep) h->stor[sid].last = kLive;
                 Op p{};
                 p.type = OP_PERM;
                 p.variant = X.variant;
+                p.level = X.level;
                 p.step = t;
                 p.src = nid;
                 p.target_legs = tl;
@@ -953,7 +973,7 @@ static int compile_plan(qx_ctx* h, const int64_t* order, int64_t n_steps, const 
         if (g.dot_perm && g.sa < 0) std::swap(g.sa, g.sb);  // the stored operand is A
         std::vector<int> cl = fA;
         cl.insert(cl.end(), fB.begin(), fB.end());
-        const int st = new_storage(h, (int64_t)1 << cl.size(), variant, t);
+        const int st = new_storage(h, (int64_t)1 << cl.size(), level, t);
         g.dst = st;
         if (!D.empty()) {
             g.out_pos = out_positions(fA, fB, D);
@@ -966,12 +986,12 @@ static int compile_plan(qx_ctx* h, const int64_t* order, int64_t n_steps, const 
             const int eb = tc_elem_bytes(tc_form);
             const int64_t mk = (int64_t)1 << (g.mb + g.kb), nk = (int64_t)1 << (g.nb + g.kb);
             g.tc = tc_form;
-            g.spa = new_storage(h, tc_parts_a(tc_form) * mk * 2 * eb / 8, variant, t);
-            g.spb = new_storage(h, tc_parts_b(tc_form) * nk * 4 * eb / 8, variant, t);
+            g.spa = new_storage(h, tc_parts_a(tc_form) * mk * 2 * eb / 8, level, t);
+            g.spb = new_storage(h, tc_parts_b(tc_form) * nk * 4 * eb / 8, level, t);
         }
         g.flops = 8.0 * std::ldexp(1.0, g.mb + g.kb + g.nb);
         h->ops.push_back(g);
-        h->nodes.push_back(contiguous_node(cl, variant, st));
+        h->nodes.push_back(contiguous_node(cl, level, st));
     }
     h->root = (int)h->nodes.size() - 1;
     const Node& R = h->nodes[h->root];
@@ -999,10 +1019,11 @@ static int compile_plan(qx_ctx* h, const int64_t* order, int64_t n_steps, const 
         }
     }
     if (!R.variant && R.storage >= 0) h->stor[R.storage].last = kLive;
-    h->item_entries = std::max<int64_t>(assign_offsets(h, true), kAlignEntries);
-    h->inv_entries = assign_offsets(h, false);
-    h->flops_inv = h->flops_item = 0;
-    for (const Op& op : h->ops) (op.variant ? h->flops_item : h->flops_inv) += op.flops;
+    h->item_entries = std::max<int64_t>(assign_offsets(h, 2), kAlignEntries);
+    h->slice_entries = assign_offsets(h, 1);
+    h->inv_entries = assign_offsets(h, 0);
+    h->flops_inv = h->flops_slice = h->flops_item = 0;
+    for (const Op& op : h->ops) (op.level == 2 ? h->flops_item : op.level == 1 ? h->flops_slice : h->flops_inv) += op.flops;
     compute_deps(h);
     build_persistent_program(h);
     build_waves(h);
@@ -1011,7 +1032,8 @@ static int compile_plan(qx_ctx* h, const int64_t* order, int64_t n_steps, const 
 }
 
 // ------------------------------------------------------------------------------------------------
-// Workspace layout: leaves | bitstrings | accumulators | amplitudes | invariant | per-pair region
+// Workspace layout: leaves | bitstrings | accumulators | amplitudes | invariant | programs |
+// per-slice region | per-pair region
 // ------------------------------------------------------------------------------------------------
 static int64_t n_open(const qx_ctx* h) { return (int64_t)h->open_wires.size(); }
 
@@ -1055,18 +1077,52 @@ static void layout(qx_ctx* h, int64_t max_bits, int64_t* fixed_bytes) {
     if (h->wave_ok)
         off += align_up((int64_t)(h->wave_ops.size() * sizeof(POp)), 256) +
                align_up((int64_t)(h->wave_idx.size() * sizeof(int32_t)), 256);
-    h->off_item = off;
+    h->off_slice = h->off_item = off;
     *fixed_bytes = off;
 }
 
+// Split the bytes after the fixed part between the per-slice and the per-pair region: as many
+// (slice, bitstring) pairs per batch as fit, with room for the slices such a batch can span.
+// Returns false when not even one pair (and its slice) fits.
+static bool fit_regions(const qx_ctx* h, int64_t avail, int64_t max_bits, int64_t* items_out, int64_t* slices_out) {
+    const int64_t per_item = h->item_entries * 8, per_slice = h->slice_entries * 8;
+    auto cap = [&](int64_t v) {
+        if (h->opt.max_items > 0) v = std::min<int64_t>(v, h->opt.max_items);
+        v = std::min<int64_t>(v, kMaxBatchItems);
+        return std::min<int64_t>(v, h->n_slices * max_bits);
+    };
+    if (avail <= 0) return false;
+    // a batch spans at most as many slices as it has pairs
+    int64_t items = cap(avail / (per_item + per_slice));
+    if (items < 1) return false;
+    const int64_t slices = per_slice ? std::min<int64_t>(h->n_slices, items) : 0;
+    const int64_t rest = avail - align_up(slices * per_slice, 256);
+    items = std::max<int64_t>(items, cap(rest / per_item));
+    *items_out = items;
+    *slices_out = slices;
+    return true;
+}
+
+// Region offsets for a workspace whose fixed part ends at `fixed`.
+static void place_regions(qx_ctx* h, int64_t fixed, int64_t items, int64_t slices) {
+    h->off_slice = fixed;
+    h->off_item = fixed + align_up(slices * h->slice_entries * 8, 256);
+    h->items_cap = items;
+    h->slices_cap = slices;
+}
+
 static float2* item_base(const qx_ctx* h) { return (float2*)(h->ws + h->off_item); }
+static float2* slice_base(const qx_ctx* h) { return (float2*)(h->ws + h->off_slice); }
 static float2* inv_base(const qx_ctx* h) { return (float2*)(h->ws + h->off_inv); }
 
 // device address and item stride of a storage
 static void storage_addr(const qx_ctx* h, int sid, float2** p, int64_t* is) {
     const Storage& s = h->stor[sid];
-    if (s.variant) {
+    if (s.level == 2) {
         *p = item_base(h) + s.off * h->items_cap;
+        *is = s.entries;
+    } else if (s.level == 1) {
+        *p = slice_base(h) + s.off * h->slices_cap;
         *is = s.entries;
     } else {
         *p = inv_base(h) + s.off;
@@ -1086,6 +1142,7 @@ static Operand node_operand(const qx_ctx* h, int node) {
         storage_addr(h, nd.storage, &p, &is);
         op.base = p;
         op.item_stride = is;
+        op.per_slice = h->stor[nd.storage].level == 1;
     }
     return op;
 }
@@ -1236,7 +1293,7 @@ static void build_persistent_program(qx_ctx* h) {
     h->pops.clear();
     h->pops_inv.clear();
     for (const Op& op : h->ops)
-        if (op.tc || !op.out_pos.empty() || op.dot_perm) return;  // these run batched only
+        if (op.tc || !op.out_pos.empty() || op.dot_perm || op.level == 1) return;  // these run batched only
     const Node& R = h->nodes[h->root];
     if (!R.variant) return;  // nothing depends on the pair
     // invariant ops write the invariant region: their program runs with that region as scratch
@@ -1251,7 +1308,7 @@ static void build_persistent_program(qx_ctx* h) {
     h->persist_ok = true;
 }
 
-static double op_bytes(const qx_ctx* h, const Op& op, int64_t n_items);
+static double op_bytes(const qx_ctx* h, const Op& op, int64_t n_items, int64_t n_b = 1);
 
 // The invariant steps grouped by dependency level (the dependency lists include space reuse, so the
 // steps of one level never touch the same storage).  Used when every invariant step is small enough
@@ -1306,12 +1363,21 @@ static void build_waves(qx_ctx* h) {
     h->wave_ok = true;
 }
 
-static double op_bytes(const qx_ctx* h, const Op& op, int64_t n_items) {
-    // algorithmic bytes of one launch over n_items pairs: each operand read once (a tensor shared by
-    // all pairs once per launch), the result written once per pair
-    const double n = (double)n_items;
-    auto node_b = [&](int node) { return 8.0 * (double)node_entries(h->nodes[node]) * (h->nodes[node].variant ? n : 1.0); };
-    auto stor_b = [&](int sid) { return 8.0 * (double)h->stor[sid].entries * (h->stor[sid].variant ? n : 1.0); };
+// how many distinct copies of a tensor of level `level` a launch of op over n_items items (n_b
+// bitstrings per slice) reads or writes
+static double copies(const Op& op, int level, int64_t n_items, int64_t n_b) {
+    if (level == 0) return 1.0;
+    if (level == 1 && op.level == 2) return (double)((n_items + n_b - 1) / n_b);
+    return (double)n_items;
+}
+
+static double op_bytes(const qx_ctx* h, const Op& op, int64_t n_items, int64_t n_b) {
+    // algorithmic bytes of one launch over n_items items: each operand read once (a tensor shared by
+    // several items once per launch), the result written once per item
+    auto node_b = [&](int node) {
+        return 8.0 * (double)node_entries(h->nodes[node]) * copies(op, h->nodes[node].level, n_items, n_b);
+    };
+    auto stor_b = [&](int sid) { return 8.0 * (double)h->stor[sid].entries * copies(op, h->stor[sid].level, n_items, n_b); };
     const double c = stor_b(op.dst);
     if (op.type == OP_PERM) return c + node_b(op.src);
     if (op.type == OP_SMALL) return c + node_b(op.x) + node_b(op.y);
@@ -1330,11 +1396,17 @@ static int run_op(qx_ctx* h, const Op& op, const ItemCtx& ic, int64_t n_items, c
                      : prep                ? QX_KERNEL_TC_PREP
                                            : QX_KERNEL_GEMM;
     size_t slot;
-    const double n = (double)n_items;
-    auto stor_b = [&](int sid) { return 8.0 * (double)h->stor[sid].entries * (h->stor[sid].variant ? n : 1.0); };
-    const double prep_bytes = prep ? stor_b(op.sa) + stor_b(op.sb) + stor_b(op.spa) + stor_b(op.spb) : 0.0;
+    // item i of a per-pair launch reads a per-slice operand at its slice i / n_b
+    const int64_t n_b = op.level == 2 ? ic.n_b : 1;
+    auto div = [&](int sid) { return h->stor[sid].level == 1 && op.level == 2 ? (int)n_b : 1; };
+    auto stor_b = [&](int sid) { return 8.0 * (double)h->stor[sid].entries * copies(op, h->stor[sid].level, n_items, n_b); };
+    // the split parts hold one copy per distinct operand item
+    const double prep_bytes = prep ? stor_b(op.sa) + stor_b(op.sb) + 8.0 * (double)h->stor[op.spa].entries *
+                                                                          copies(op, h->stor[op.sa].level, n_items, n_b) +
+                                         8.0 * (double)h->stor[op.spb].entries * copies(op, h->stor[op.sb].level, n_items, n_b)
+                                   : 0.0;
     cudaError_t e = prof_begin(h, kind, prep ? 0.0 : op.flops * (double)n_items,
-                               prep ? prep_bytes : op_bytes(h, op, n_items), &slot);
+                               prep ? prep_bytes : op_bytes(h, op, n_items, n_b), &slot);
     if (e != cudaSuccess) return fail(h, QX_ECUDA, "profiling event: %s", cudaGetErrorString(e));
     if (op.type == OP_PERM) {
         e = launch_permute(perm_desc(h, op), ic, n_items, dp, dis, st);
@@ -1348,14 +1420,15 @@ static int run_op(qx_ctx* h, const Op& op, const ItemCtx& ic, int64_t n_items, c
         pv.type = OP_PERM;
         pv.src = op.perm_src;
         pv.target_legs = op.perm_legs;
-        e = launch_dot_perm(perm_desc(h, pv), ic, n_items, ap, ais, dp, dis, st);
+        e = launch_dot_perm(perm_desc(h, pv), ic, n_items, ap, ais, dp, dis, st, div(op.sa));
     } else if (!op.tc) {
         float2 *ap, *bp;
         int64_t ais, bis;
         storage_addr(h, op.sa, &ap, &ais);
         storage_addr(h, op.sb, &bp, &bis);
         const OutMap om = out_map(op);
-        e = launch_gemm_c64(ap, ais, op.a_km, bp, bis, op.b_km, dp, dis, op.mb, op.nb, op.kb, n_items, st, &om);
+        e = launch_gemm_c64(ap, ais, op.a_km, bp, bis, op.b_km, dp, dis, op.mb, op.nb, op.kb, n_items, st, &om,
+                            div(op.sa), div(op.sb));
     } else if (op.tc == TC_FORM_3XTF32_DIRECT) {
         TcArgs g{};
         float2 *ap, *bp;
@@ -1374,6 +1447,8 @@ static int run_op(qx_ctx* h, const Op& op, const ItemCtx& ic, int64_t n_items, c
         g.nb = op.nb;
         g.kb = op.kb;
         g.n_items = n_items;
+        g.a_div = div(op.sa);
+        g.b_div = div(op.sb);
         g.limit = h->opt.timeout_cycles > 0 ? h->opt.timeout_cycles : 2000000000ll;
         g.err = (int*)(h->ws + h->off_err);
         e = launch_tc2_gemm(g, st);
@@ -1402,12 +1477,15 @@ static int run_op(qx_ctx* h, const Op& op, const ItemCtx& ic, int64_t n_items, c
         g.nb = op.nb;
         g.kb = op.kb;
         g.n_items = n_items;
+        g.a_div = div(op.sa);
+        g.b_div = div(op.sb);
         g.limit = h->opt.timeout_cycles > 0 ? h->opt.timeout_cycles : 2000000000ll;
         g.err = (int*)(h->ws + h->off_err);
         g.amax = (float*)(h->ws + h->off_err + 16);
         e = launch_tc_prep(op.tc, g, st);
         if (e == cudaSuccess) e = prof_end(h, slot);
-        if (e == cudaSuccess) e = prof_begin(h, QX_KERNEL_TC_GEMM, op.flops * (double)n_items, op_bytes(h, op, n_items), &slot);
+        if (e == cudaSuccess)
+            e = prof_begin(h, QX_KERNEL_TC_GEMM, op.flops * (double)n_items, op_bytes(h, op, n_items, n_b), &slot);
         if (e == cudaSuccess) e = launch_tc_gemm(op.tc, g, st);
         h->last_launches += 2;
     }
@@ -1693,6 +1771,7 @@ static int contract_impl(qx_ctx* h, const uint8_t* d_bits, int64_t n_bits, int64
         nb_batch = h->items_cap;
         ns_batch = 1;
     }
+    if (h->slice_entries) ns_batch = std::max<int64_t>(1, std::min<int64_t>(ns_batch, h->slices_cap));
     SumDesc sd{};
     sd.root = node_operand(h, h->root);
     sd.open_bits = (int32_t)n_open(h);
@@ -1706,7 +1785,9 @@ static int contract_impl(qx_ctx* h, const uint8_t* d_bits, int64_t n_bits, int64
     }
     // The prologue (everything that no slice or bitstring touches) is issued together with the first
     // batch of (slice, bitstring) pairs, so independent branches of both overlap; every batch ends with
-    // all streams joined before its slice sum, and the next batch reuses the per-pair space.
+    // all streams joined before its slice sum, and the next batch reuses the per-slice and per-pair
+    // space.  Steps that no output bit touches run once per slice of the batch (one item per slice),
+    // the others once per pair.
     bool prologue = true;
     for (int64_t s0 = s_begin; s0 < s_end; s0 += ns_batch) {
         const int64_t ns = std::min(ns_batch, s_end - s0);
@@ -1718,10 +1799,14 @@ static int contract_impl(qx_ctx* h, const uint8_t* d_bits, int64_t n_bits, int64
             ic.n_items = ns * nb;
             if ((rc = dag.fork())) return rc;
             if (prologue && (rc = dag.waves(d_bits))) return rc;
+            ItemCtx ic_s = ic;
+            ic_s.n_b = 1;
+            ic_s.n_items = ns;
             for (size_t j = 0; j < h->ops.size(); ++j) {
                 const Op& op = h->ops[j];
                 if (!op.variant && !prologue) continue;
-                if ((rc = dag.issue((int)j, op.variant ? ic : ic_inv, op.variant ? ic.n_items : 1))) return rc;
+                const ItemCtx& c = op.level == 2 ? ic : op.level == 1 ? ic_s : ic_inv;
+                if ((rc = dag.issue((int)j, c, c.n_items))) return rc;
             }
             prologue = false;
             if ((rc = dag.join())) return rc;
@@ -1815,7 +1900,7 @@ int qx_create(qx_handle* out, int device, void* stream, const qx_options* opt) {
     h->stream = (cudaStream_t)stream;
     if (opt) h->opt = *opt;
     if (h->opt.precision < QX_PREC_C64 || h->opt.precision > QX_PREC_FP16_SCALED || h->opt.max_items < 0 ||
-        h->opt.executor < 0 || h->opt.executor > 3) {
+        h->opt.executor < 0 || h->opt.executor > 3 || h->opt.no_slice_level < 0 || h->opt.no_slice_level > 1) {
         delete h;
         return QX_EINVAL;
     }
@@ -1855,6 +1940,7 @@ int qx_set_options(qx_handle h, const qx_options* opt) {
         return fail(h, QX_ESTATE, "set the precision form before qx_set_plan");
     if (opt->max_items < 0) return fail(h, QX_EINVAL, "max_items < 0");
     if (opt->executor < 0 || opt->executor > 3) return fail(h, QX_EINVAL, "executor %d out of range", opt->executor);
+    if (opt->no_slice_level < 0 || opt->no_slice_level > 1) return fail(h, QX_EINVAL, "no_slice_level must be 0 or 1");
     h->opt = *opt;
     return QX_OK;
 }
@@ -1908,7 +1994,8 @@ int qx_workspace_size(qx_handle h, int64_t max_bits, int64_t items, int64_t* byt
     if (items < 1) items = 1;
     int64_t fixed;
     layout(h, max_bits, &fixed);
-    *bytes_out = fixed + items * h->item_entries * 8;
+    const int64_t slices = h->slice_entries ? std::min<int64_t>(h->n_slices, items) : 0;
+    *bytes_out = fixed + align_up(slices * h->slice_entries * 8, 256) + items * h->item_entries * 8;
     return QX_OK;
 }
 
@@ -1919,15 +2006,11 @@ int qx_bind_workspace(qx_handle h, void* dptr, int64_t bytes, int64_t max_bits) 
     if (max_bits < 1) return fail(h, QX_EINVAL, "max_bits < 1");
     if (((uintptr_t)dptr) % 256) return fail(h, QX_EINVAL, "workspace must be 256-byte aligned");
     unbind(h);
-    int64_t fixed;
+    int64_t fixed, items = 0, slices = 0;
     layout(h, max_bits, &fixed);
-    int64_t items = (bytes - fixed) / (h->item_entries * 8);
-    if (h->opt.max_items > 0) items = std::min<int64_t>(items, h->opt.max_items);
-    items = std::min<int64_t>(items, kMaxBatchItems);
-    items = std::min<int64_t>(items, h->n_slices * max_bits);
-    if (items < 1)
+    if (!fit_regions(h, bytes - fixed, max_bits, &items, &slices))
         return fail(h, QX_ENOMEM, "workspace of %lld bytes holds no (slice, bitstring) pair; need %lld", (long long)bytes,
-                    (long long)(fixed + h->item_entries * 8));
+                    (long long)(fixed + 256 + (h->item_entries + h->slice_entries) * 8));
     CUDA_TRY(h, cudaSetDevice(h->device));
     if (!dptr) {
         CUDA_TRY(h, cudaMalloc(&dptr, (size_t)bytes));
@@ -1936,7 +2019,7 @@ int qx_bind_workspace(qx_handle h, void* dptr, int64_t bytes, int64_t max_bits) 
     h->ws = (char*)dptr;
     h->ws_bytes = bytes;
     h->max_bits = max_bits;
-    h->items_cap = items;
+    place_regions(h, fixed, items, slices);
     h->leaves_on_device = false;
     h->pops_on_device = false;
     h->waves_on_device = false;
@@ -2060,10 +2143,10 @@ int qx_describe_plan(qx_handle h, char* buf, int64_t len, int64_t* needed) {
                                                             : "gemm";
         if (op.type == OP_PERM)
             snprintf(line, sizeof line, "%zu step=%lld %s %s rank=%zu\n", i, (long long)op.step, kind,
-                     op.variant ? "pair" : "shared", op.target_legs.size());
+                     op.level == 2 ? "pair" : op.level == 1 ? "slice" : "shared", op.target_legs.size());
         else
             snprintf(line, sizeof line, "%zu step=%lld %s %s m=%d k=%d n=%d a_kmajor=%d b_kmajor=%d scatter=%d\n", i,
-                     (long long)op.step, kind, op.variant ? "pair" : "shared", op.mb, op.kb, op.nb, (int)op.a_km,
+                     (long long)op.step, kind, op.level == 2 ? "pair" : op.level == 1 ? "slice" : "shared", op.mb, op.kb, op.nb, (int)op.a_km,
                      (int)op.b_km, (int)!op.out_pos.empty());
         out += line;
         if (op.type == OP_SMALL) {  // address positions in X of the contracted legs
@@ -2086,7 +2169,7 @@ int qx_describe_plan(qx_handle h, char* buf, int64_t len, int64_t* needed) {
             const std::vector<int>& v = pass ? wr : rd;
             for (size_t k = 0; k < v.size(); ++k) {
                 const Storage& st = h->stor[v[k]];
-                snprintf(line, sizeof line, "%s%s:%lld+%lld", k ? "," : "", st.variant ? "pair" : "shared",
+                snprintf(line, sizeof line, "%s%s:%lld+%lld", k ? "," : "", st.level == 2 ? "pair" : st.level == 1 ? "slice" : "shared",
                          (long long)st.off, (long long)align_up(st.entries, kAlignEntries));
                 out += line;
             }
@@ -2204,20 +2287,18 @@ int qx_internal_contract_in(qx_ctx* h, char* buf, int64_t buf_bytes, const uint8
         char* ws;
         int64_t ws_bytes;
         bool ws_owned;
-        int64_t max_bits, off_err, off_leaf, off_bits, off_acc, off_amps, off_inv, off_item, items_cap;
+        int64_t max_bits, off_err, off_leaf, off_bits, off_acc, off_amps, off_inv, off_item, items_cap, off_slice,
+            slices_cap;
         bool leaves_on_device;
         int64_t off_pops, off_counter, off_results, off_pscratch, off_pops_inv, off_wave;
         bool pops_on_device, waves_on_device;
     } const saved = {h->ws,        h->ws_bytes, h->ws_owned,    h->max_bits,    h->off_err,    h->off_leaf,
                      h->off_bits,  h->off_acc,  h->off_amps,    h->off_inv,     h->off_item,   h->items_cap,
-                     h->leaves_on_device, h->off_pops, h->off_counter, h->off_results, h->off_pscratch,
+                     h->off_slice, h->slices_cap, h->leaves_on_device, h->off_pops, h->off_counter, h->off_results, h->off_pscratch,
                      h->off_pops_inv, h->off_wave, h->pops_on_device, h->waves_on_device};
-    int64_t fixed;
+    int64_t fixed, items = 0, slices = 0;
     layout(h, n_bits, &fixed);
-    int64_t items = (buf_bytes - fixed) / (h->item_entries * 8);
-    if (h->opt.max_items > 0) items = std::min<int64_t>(items, h->opt.max_items);
-    items = std::min<int64_t>(items, kMaxBatchItems);
-    items = std::min<int64_t>(items, h->n_slices * n_bits);
+    const bool fits = fit_regions(h, buf_bytes - fixed, n_bits, &items, &slices);
     auto restore = [&]() {
         h->ws = saved.ws;
         h->ws_bytes = saved.ws_bytes;
@@ -2231,6 +2312,8 @@ int qx_internal_contract_in(qx_ctx* h, char* buf, int64_t buf_bytes, const uint8
         h->off_inv = saved.off_inv;
         h->off_item = saved.off_item;
         h->items_cap = saved.items_cap;
+        h->off_slice = saved.off_slice;
+        h->slices_cap = saved.slices_cap;
         h->leaves_on_device = saved.leaves_on_device;
         h->off_pops = saved.off_pops;
         h->off_counter = saved.off_counter;
@@ -2241,16 +2324,17 @@ int qx_internal_contract_in(qx_ctx* h, char* buf, int64_t buf_bytes, const uint8
         h->off_wave = saved.off_wave;
         h->waves_on_device = saved.waves_on_device;
     };
-    if (items < 1) {
+    if (!fits) {
         restore();
         return fail(h, QX_ENOMEM, "this plan and %lld bitstrings need %lld bytes of scratch; %lld are available",
-                    (long long)n_bits, (long long)(fixed + h->item_entries * 8), (long long)buf_bytes);
+                    (long long)n_bits, (long long)(fixed + 256 + (h->item_entries + h->slice_entries) * 8),
+                    (long long)buf_bytes);
     }
     h->ws = buf;
     h->ws_bytes = buf_bytes;
     h->ws_owned = false;
     h->max_bits = n_bits;
-    h->items_cap = items;
+    place_regions(h, fixed, items, slices);
     h->leaves_on_device = false;
     h->pops_on_device = false;
     h->waves_on_device = false;

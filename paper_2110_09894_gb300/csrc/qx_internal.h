@@ -24,7 +24,9 @@ struct ItemCtx {
 };
 
 // Address of entry (leg bits) of an operand for item i:
-//   base + i * item_stride + sum_f value_f * fix_stride[f] + sum_j bit_j << pos[j]
+//   base + i' * item_stride + sum_f value_f * fix_stride[f] + sum_j bit_j << pos[j]
+// where i' = i, or i / n_b (the item's slice within the batch) for a per-slice
+// tensor read by per-pair work (per_slice = 1; in launches over slices n_b = 1).
 // value_f is bit fix_src[f] of the slice index (fix_src >= 0) or the byte of
 // output qubit -(fix_src+1) of the bitstring (fix_src < 0).  Leg 0 is the
 // most significant; positions are strictly decreasing in leg order.
@@ -33,6 +35,8 @@ struct Operand {
     int64_t item_stride;
     int32_t n_fix;
     int32_t rank;
+    int32_t per_slice;
+    int32_t pad;
     int32_t fix_src[kMaxFix];
     int64_t fix_stride[kMaxFix];
     int8_t pos[kMaxRank];
@@ -104,15 +108,17 @@ cudaError_t launch_permute(const PermDesc& d, const ItemCtx& ic, int64_t n_items
                            int64_t out_item_stride, cudaStream_t st);
 void perm_tables(const PermDesc& d, PermTables* tb);
 // per pair C = sum_k A[k] B[p(k)]: B = d.in read through the permutation d, A in the target order
+// a_div / b_div: item i reads operand item i / div (n_b for a per-slice tensor
+// read by per-pair work, else 1)
 cudaError_t launch_dot_perm(const PermDesc& d, const ItemCtx& ic, int64_t n_items, const float2* a, int64_t a_is,
-                            float2* c, int64_t c_is, cudaStream_t st);
+                            float2* c, int64_t c_is, cudaStream_t st, int a_div = 1);
 cudaError_t launch_small(const SmallDesc& d, const ItemCtx& ic, int64_t n_items, float2* out,
                          int64_t out_item_stride, cudaStream_t st);
 // Batched complex GEMM, C[M][N] = A . B with A stored [M][K] (a_kmajor) or
 // [K][M], B stored [N][K] (b_kmajor) or [K][N]; M = 2^mb etc.
 cudaError_t launch_gemm_c64(const float2* a, int64_t a_is, bool a_kmajor, const float2* b, int64_t b_is,
                             bool b_kmajor, float2* c, int64_t c_is, int mb, int nb, int kb, int64_t n_items,
-                            cudaStream_t st, const OutMap* om = nullptr);
+                            cudaStream_t st, const OutMap* om = nullptr, int a_div = 1, int b_div = 1);
 cudaError_t launch_slice_sum(const SumDesc& d, const ItemCtx& ic, double* acc, cudaStream_t st);
 
 // Persistent executor (qx_persist.cu): one launch runs whole contractions of
@@ -200,6 +206,7 @@ struct TcArgs {
     int64_t pb_is_bytes;
     int mb, nb, kb;
     int64_t n_items;
+    int a_div, b_div;  // item i reads operand item i / div (0 taken as 1); ignored for an item stride of 0
     long long limit;  // clock cycles per bounded wait
     int* err;         // device error flag (QX_ETIMEOUT on expiry)
     float* amax;      // FP16 form: device max |x| of A and B (2 floats), sets the per-tensor scales

@@ -17,7 +17,7 @@
 namespace qx {
 
 __device__ __forceinline__ int64_t fix_offset(const Operand& op, const ItemCtx& ic, int64_t item) {
-    int64_t off = item * op.item_stride;
+    int64_t off = (op.per_slice ? item / ic.n_b : item) * op.item_stride;
     if (op.n_fix) {
         const int64_t s = ic.s0 + item / ic.n_b;
         const int64_t b = ic.b0 + item % ic.n_b;
@@ -462,7 +462,8 @@ template <int BM, int BN>
 __global__ void __launch_bounds__(256, (BM * BN >= 8192 ? 1 : 2)) k_gemm_c64(const float2* __restrict__ A, int64_t a_is, bool akm,
                                                   const float2* __restrict__ B, int64_t b_is, bool bkm,
                                                   float2* __restrict__ C, int64_t c_is, int mb, int nb, int kb,
-                                                  int tiles_n, const __grid_constant__ OutMap om) {
+                                                  int tiles_n, const __grid_constant__ OutMap om, int a_div,
+                                                  int b_div) {
     constexpr int TM = BM / 16, TN = BN / 16, LA = BM * GBK / 256, LB = BN * GBK / 256;
     extern __shared__ float2 gsm[];  // As[2][GBK][BM + 1], then Bs[2][GBK][BN + 1]
     float2(*As)[GBK][BM + 1] = (float2(*)[GBK][BM + 1])gsm;
@@ -471,8 +472,8 @@ __global__ void __launch_bounds__(256, (BM * BN >= 8192 ? 1 : 2)) k_gemm_c64(con
     const int64_t item = blockIdx.y;
     const int64_t m0 = (int64_t)(blockIdx.x / tiles_n) * BM;
     const int64_t n0 = (int64_t)(blockIdx.x % tiles_n) * BN;
-    const float2* Ap = A + item * a_is;
-    const float2* Bp = B + item * b_is;
+    const float2* Ap = A + (item / a_div) * a_is;
+    const float2* Bp = B + (item / b_div) * b_is;
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
     const float2 zero = make_float2(0.f, 0.f);
     float2 ra[LA], rb[LB];
@@ -587,13 +588,13 @@ __global__ void __launch_bounds__(256, (BM * BN >= 8192 ? 1 : 2)) k_gemm_c64(con
 template <int MB, int NB>
 __global__ void __launch_bounds__(256) k_dot_c64(const float2* __restrict__ A, int64_t a_is, bool akm,
                                                  const float2* __restrict__ B, int64_t b_is, bool bkm,
-                                                 float2* __restrict__ C, int64_t c_is, int kb) {
+                                                 float2* __restrict__ C, int64_t c_is, int kb, int a_div, int b_div) {
     constexpr int M = 1 << MB, N = 1 << NB, MN = M * N;
     __shared__ float2 red[MN][256];
     const int64_t K = (int64_t)1 << kb;
     const int64_t item = blockIdx.x;
-    const float2* Ap = A + item * a_is;
-    const float2* Bp = B + item * b_is;
+    const float2* Ap = A + (item / a_div) * a_is;
+    const float2* Bp = B + (item / b_div) * b_is;
     const int tid = threadIdx.x;
     float2 acc[MN];
 #pragma unroll
@@ -631,7 +632,7 @@ __global__ void __launch_bounds__(256) k_dot_c64(const float2* __restrict__ A, i
 // One CTA per pair; per-thread FP32 partials, then a fixed-order tree.
 __global__ void __launch_bounds__(256) k_dot_perm(const PermDesc d, const PermTables tb, const ItemCtx ic,
                                                   const float2* __restrict__ A, int64_t a_is, float2* __restrict__ C,
-                                                  int64_t c_is) {
+                                                  int64_t c_is, int a_div) {
     constexpr int LO = kPermLoBits, LM = (1 << LO) - 1;
     __shared__ float2 tile[(1 << kPermTileBits) + (1 << kPermTileBits) / 32];
     __shared__ int64_t s_in[128], s_out[128];
@@ -651,7 +652,7 @@ __global__ void __launch_bounds__(256) k_dot_perm(const PermDesc d, const PermTa
     const int n = 1 << d.t;
     const int64_t tiles = (int64_t)1 << d.n_outer;
     const int64_t ibase = fix_offset(d.in, ic, item);
-    const float2* __restrict__ Ap = A + item * a_is;
+    const float2* __restrict__ Ap = A + (item / a_div) * a_is;
     float2 acc = make_float2(0.f, 0.f);
     for (int64_t tj = 0; tj < tiles; ++tj) {
         int64_t ib = ibase, ob = 0;
@@ -681,12 +682,12 @@ __global__ void __launch_bounds__(256) k_dot_perm(const PermDesc d, const PermTa
 }
 
 cudaError_t launch_dot_perm(const PermDesc& d, const ItemCtx& ic, int64_t n_items, const float2* a, int64_t a_is,
-                            float2* c, int64_t c_is, cudaStream_t st) {
+                            float2* c, int64_t c_is, cudaStream_t st, int a_div) {
     if (n_items <= 0) return cudaSuccess;
-    if (d.t > kPermTileBits || n_items > 0x7fffffffll) return cudaErrorInvalidValue;
+    if (d.t > kPermTileBits || n_items > 0x7fffffffll || a_div < 1) return cudaErrorInvalidValue;
     PermTables tb;
     perm_tables(d, &tb);
-    k_dot_perm<<<(unsigned)n_items, 256, 0, st>>>(d, tb, ic, a, a_is, c, c_is);
+    k_dot_perm<<<(unsigned)n_items, 256, 0, st>>>(d, tb, ic, a, a_is, c, c_is, a_div);
     return cudaGetLastError();
 }
 
@@ -698,7 +699,8 @@ template <int KB>
 __global__ void __launch_bounds__(256) k_gemm_smallk(const float2* __restrict__ A, int64_t a_is, bool akm,
                                                     const float2* __restrict__ B, int64_t b_is, bool bkm,
                                                     float2* __restrict__ C, int64_t c_is, int mb, int nb,
-                                                    int rows_per_cta, const __grid_constant__ OutMap om) {
+                                                    int rows_per_cta, const __grid_constant__ OutMap om, int a_div,
+                                                    int b_div) {
     constexpr int K = 1 << KB;
     const int64_t item = blockIdx.y;
     const int64_t M = (int64_t)1 << mb, N = (int64_t)1 << nb;
@@ -709,8 +711,8 @@ __global__ void __launch_bounds__(256) k_gemm_smallk(const float2* __restrict__ 
     const int64_t n = cb * width + (threadIdx.x % width);
     const int64_t r0 = rb * rows_per_cta + threadIdx.x / width;
     const int64_t r1 = (rb + 1) * rows_per_cta < M ? (rb + 1) * rows_per_cta : M;
-    const float2* __restrict__ Ap = A + item * a_is;
-    const float2* __restrict__ Bp = B + item * b_is;
+    const float2* __restrict__ Ap = A + (item / a_div) * a_is;
+    const float2* __restrict__ Bp = B + (item / b_div) * b_is;
     float2 b[K];
 #pragma unroll
     for (int k = 0; k < K; ++k) b[k] = bkm ? Bp[n * K + k] : Bp[(int64_t)k * N + n];
@@ -727,7 +729,7 @@ __global__ void __launch_bounds__(256) k_gemm_smallk(const float2* __restrict__ 
 template <int BM, int BN>
 static void gemm_tile(dim3 grid, cudaStream_t st, const float2* a, int64_t a_is, bool akm, const float2* b,
                       int64_t b_is, bool bkm, float2* c, int64_t c_is, int mb, int nb, int kb, int tn,
-                      const OutMap& om) {
+                      const OutMap& om, int a_div, int b_div) {
     constexpr int smem = 2 * GBK * (BM + 1 + BN + 1) * (int)sizeof(float2);
     if (smem > 48 * 1024) {
         // opt in to more than 48 KB of dynamic shared memory, once per device
@@ -742,13 +744,15 @@ static void gemm_tile(dim3 grid, cudaStream_t st, const float2* a, int64_t a_is,
                 done[dev >> 6] |= 1ull << (dev & 63);
         }
     }
-    k_gemm_c64<BM, BN><<<grid, 256, smem, st>>>(a, a_is, akm, b, b_is, bkm, c, c_is, mb, nb, kb, tn, om);
+    k_gemm_c64<BM, BN><<<grid, 256, smem, st>>>(a, a_is, akm, b, b_is, bkm, c, c_is, mb, nb, kb, tn, om, a_div,
+                                                b_div);
 }
 
 cudaError_t launch_gemm_c64(const float2* a, int64_t a_is, bool a_kmajor, const float2* b, int64_t b_is,
                             bool b_kmajor, float2* c, int64_t c_is, int mb, int nb, int kb, int64_t n_items,
-                            cudaStream_t st, const OutMap* omp) {
+                            cudaStream_t st, const OutMap* omp, int a_div, int b_div) {
     if (n_items <= 0) return cudaSuccess;
+    if (a_div < 1 || b_div < 1) return cudaErrorInvalidValue;
     OutMap om{};
     if (omp) om = *omp;
     if (kb <= 2 && nb >= 5) {
@@ -759,9 +763,9 @@ cudaError_t launch_gemm_c64(const float2* a, int64_t a_is, bool a_kmajor, const 
         const int64_t blocks = ((M + rows - 1) / rows) * (N / width);
         dim3 grid((unsigned)blocks, (unsigned)n_items);
         switch (kb) {
-            case 0: k_gemm_smallk<0><<<grid, 256, 0, st>>>(a, a_is, a_kmajor, b, b_is, b_kmajor, c, c_is, mb, nb, (int)rows, om); break;
-            case 1: k_gemm_smallk<1><<<grid, 256, 0, st>>>(a, a_is, a_kmajor, b, b_is, b_kmajor, c, c_is, mb, nb, (int)rows, om); break;
-            default: k_gemm_smallk<2><<<grid, 256, 0, st>>>(a, a_is, a_kmajor, b, b_is, b_kmajor, c, c_is, mb, nb, (int)rows, om); break;
+            case 0: k_gemm_smallk<0><<<grid, 256, 0, st>>>(a, a_is, a_kmajor, b, b_is, b_kmajor, c, c_is, mb, nb, (int)rows, om, a_div, b_div); break;
+            case 1: k_gemm_smallk<1><<<grid, 256, 0, st>>>(a, a_is, a_kmajor, b, b_is, b_kmajor, c, c_is, mb, nb, (int)rows, om, a_div, b_div); break;
+            default: k_gemm_smallk<2><<<grid, 256, 0, st>>>(a, a_is, a_kmajor, b, b_is, b_kmajor, c, c_is, mb, nb, (int)rows, om, a_div, b_div); break;
         }
         return cudaGetLastError();
     }
@@ -770,7 +774,7 @@ cudaError_t launch_gemm_c64(const float2* a, int64_t a_is, bool a_kmajor, const 
         dim3 grid((unsigned)n_items);
 #define QX_DOT_CASE(X, Y)                                                                                   \
     if (mb == X && nb == Y) {                                                                               \
-        k_dot_c64<X, Y><<<grid, 256, 0, st>>>(a, a_is, a_kmajor, b, b_is, b_kmajor, c, c_is, kb);          \
+        k_dot_c64<X, Y><<<grid, 256, 0, st>>>(a, a_is, a_kmajor, b, b_is, b_kmajor, c, c_is, kb, a_div, b_div); \
         return cudaGetLastError();                                                                          \
     }
         QX_DOT_CASE(0, 0) QX_DOT_CASE(0, 1) QX_DOT_CASE(0, 2) QX_DOT_CASE(0, 3) QX_DOT_CASE(0, 4)
@@ -787,7 +791,7 @@ cudaError_t launch_gemm_c64(const float2* a, int64_t a_is, bool a_kmajor, const 
 #define QX_GEMM_CASE(X, Y)                                                                            \
     if (bmb == X && bnb == Y) {                                                                       \
         gemm_tile<(1 << X), (1 << Y)>(grid, st, a, a_is, a_kmajor, b, b_is, b_kmajor, c, c_is, mb, nb, kb, \
-                                      (int)tn, om);                                                   \
+                                      (int)tn, om, a_div, b_div);                                     \
         return cudaGetLastError();                                                                    \
     }
     QX_GEMM_CASE(7, 6)

@@ -29,6 +29,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <climits>
 #include <cstring>
 #include <mutex>
 
@@ -288,7 +289,7 @@ struct TcMaps {
 template <int FORM>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_gemm_tc(const __grid_constant__ TcMaps maps, float* __restrict__ C, int64_t c_is, int M, int N2, int K2,
-              int tiles_n, long long limit, int* err, const float* amax) {
+              int tiles_n, long long limit, int* err, const float* amax, int a_div, int b_div) {
     using F = TcForm<FORM>;
     constexpr int BK = TC_ROWB / F::EB;                 // K elements per stage
     constexpr int KSTEP = 32 / F::EB;                   // K elements per MMA (32 bytes)
@@ -345,10 +346,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             mbar_expect_tx(&full[s], STAGE_BYTES);
             uint8_t* st = base + s * STAGE_BYTES;
 #pragma unroll
-            for (int p = 0; p < F::NPA; ++p) tma_load_3d(st + p * TILE, &maps.a[p], it * BK, m0, item, &full[s]);
+            for (int p = 0; p < F::NPA; ++p)
+                tma_load_3d(st + p * TILE, &maps.a[p], it * BK, m0, item / a_div, &full[s]);
 #pragma unroll
             for (int p = 0; p < F::NPB; ++p)
-                tma_load_3d(st + (F::NPA + p) * TILE, &maps.b[p], it * BK, n0, item, &full[s]);
+                tma_load_3d(st + (F::NPA + p) * TILE, &maps.b[p], it * BK, n0, item / b_div, &full[s]);
             ++issued;
         }
         if (*(volatile int*)&abort_flag) {
@@ -538,7 +540,7 @@ template <int BN>
 __global__ void __launch_bounds__(TC2_THREADS, 1)
     k_gemm_tc2(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                float* __restrict__ C, int64_t c_is, int M, int N2, int K2, int tiles_n, int tiles, int64_t n_items,
-               int a_bcast, int b_bcast, long long limit, int* err) {
+               int a_div, int b_div, long long limit, int* err) {
     // persistent over (pair, tile) jobs: job = blockIdx.x + t * gridDim.x; the
     // k-stages of successive jobs form one sequence g = t * nk + it, so both
     // rings stay full across tile boundaries
@@ -609,8 +611,8 @@ __global__ void __launch_bounds__(TC2_THREADS, 1)
             job_of(g / nk, &item, &m0, &n0);
             const int it = (int)(g % nk);
             mbar_expect_tx(&full[l], L::LAND);  // raw A and raw B
-            tma_load_3d(land(l), &mapA, it * BK, m0, a_bcast ? 0 : (int)item, &full[l]);
-            tma_load_3d(land(l) + L::A, &mapB, it * BK, n0 >> 1, b_bcast ? 0 : (int)item, &full[l]);
+            tma_load_3d(land(l), &mapA, it * BK, m0, (int)(item / a_div), &full[l]);
+            tma_load_3d(land(l) + L::A, &mapB, it * BK, n0 >> 1, (int)(item / b_div), &full[l]);
             ++issued;
         }
         if (*(volatile int*)&abort_flag) {  // let the copies in flight land before the CTA exits
@@ -759,6 +761,16 @@ static bool make_map(CUtensorMap* m, const void* base, int64_t k2, int64_t rows,
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// Items of an operand a launch reads: one for an item stride of 0 (the same
+// tensor for every item), n_items / div otherwise; and the divisor the kernel
+// applies to its item index (INT_MAX turns every index into item 0).
+static int64_t distinct_items(int64_t is, int div, int64_t n_items) {
+    if (!is) return 1;
+    div = div < 1 ? 1 : div;
+    return (n_items + div - 1) / div;
+}
+static int item_div(int64_t is, int div) { return !is ? INT_MAX : div < 1 ? 1 : div; }
+
 int tc_parts_a(int form) { return form == TC_FORM_3XTF32 ? 2 : form == TC_FORM_FP16 ? 1 : 3; }
 int tc_parts_b(int form) { return tc_parts_a(form); }
 int tc_elem_bytes(int form) { return form == TC_FORM_3XTF32 ? 4 : 2; }
@@ -774,7 +786,7 @@ static cudaError_t run_prep(const TcArgs& g, cudaStream_t st) {
         if (!g.amax) return cudaErrorInvalidValue;
         cudaError_t e = cudaMemsetAsync(g.amax, 0, 2 * sizeof(float), st);
         if (e != cudaSuccess) return e;
-        const int64_t na = g.a_is ? g.n_items : 1, nb_ = g.b_is ? g.n_items : 1;
+        const int64_t na = distinct_items(g.a_is, g.a_div, g.n_items), nb_ = distinct_items(g.b_is, g.b_div, g.n_items);
         k_absmax<<<(unsigned)std::min<int64_t>((M * K * na + 255) / 256, 4096), 256, 0, st>>>(g.a, g.a_is, M * K, na,
                                                                                                g.amax);
         k_absmax<<<(unsigned)std::min<int64_t>((N * K * nb_ + 255) / 256, 4096), 256, 0, st>>>(g.b, g.b_is, N * K,
@@ -783,11 +795,12 @@ static cudaError_t run_prep(const TcArgs& g, cudaStream_t st) {
         if (e != cudaSuccess) return e;
         amax = g.amax;
     }
-    dim3 grid((unsigned)((M * K + 255) / 256), (unsigned)g.n_items);
+    // each distinct operand item is split once
+    dim3 grid((unsigned)((M * K + 255) / 256), (unsigned)distinct_items(g.a_is, g.a_div, g.n_items));
     k_prep_a<FORM><<<grid, 256, 0, st>>>(g.a, g.a_is, g.a_kmajor, (T*)g.pa, g.pa_is_bytes / F::EB, g.mb, g.kb, amax);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    dim3 grid2((unsigned)((N * K + 255) / 256), (unsigned)g.n_items);
+    dim3 grid2((unsigned)((N * K + 255) / 256), (unsigned)distinct_items(g.b_is, g.b_div, g.n_items));
     k_prep_b<FORM><<<grid2, 256, 0, st>>>(g.b, g.b_is, g.b_kmajor, (T*)g.pb, g.pb_is_bytes / F::EB, g.nb, g.kb, amax);
     return cudaGetLastError();
 }
@@ -800,11 +813,12 @@ static cudaError_t run_gemm(const TcArgs& g, cudaStream_t st) {
     TcMaps maps;
     memset(&maps, 0, sizeof maps);
     for (int p = 0; p < F::NPA; ++p)
-        if (!make_map<FORM>(&maps.a[p], (const char*)g.pa + p * pa_part * F::EB, 2 * K, M, g.n_items, g.pa_is_bytes))
+        if (!make_map<FORM>(&maps.a[p], (const char*)g.pa + p * pa_part * F::EB, 2 * K, M,
+                            distinct_items(g.a_is, g.a_div, g.n_items), g.pa_is_bytes))
             return cudaErrorInvalidValue;
     for (int p = 0; p < F::NPB; ++p)
-        if (!make_map<FORM>(&maps.b[p], (const char*)g.pb + p * pb_part * F::EB, 2 * K, 2 * N, g.n_items,
-                            g.pb_is_bytes))
+        if (!make_map<FORM>(&maps.b[p], (const char*)g.pb + p * pb_part * F::EB, 2 * K, 2 * N,
+                            distinct_items(g.b_is, g.b_div, g.n_items), g.pb_is_bytes))
             return cudaErrorInvalidValue;
     const int smem = F::STAGES * (F::NPA + F::NPB) * TC_BM * TC_ROWB + 1024;
     int dev = 0;
@@ -824,7 +838,8 @@ static cudaError_t run_gemm(const TcArgs& g, cudaStream_t st) {
     dim3 grid((unsigned)(tiles_m * tiles_n), (unsigned)g.n_items);
     k_gemm_tc<FORM><<<grid, TC_THREADS, smem, st>>>(maps, (float*)g.c, g.c_is * 2, (int)M, (int)(2 * N), (int)(2 * K),
                                                    tiles_n, g.limit, g.err,
-                                                   FORM == TC_FORM_FP16 ? (const float*)g.amax : nullptr);
+                                                   FORM == TC_FORM_FP16 ? (const float*)g.amax : nullptr,
+                                                   item_div(g.a_is, g.a_div), item_div(g.b_is, g.b_div));
     return cudaGetLastError();
 }
 
@@ -847,8 +862,8 @@ static cudaError_t run_tc2(const TcArgs& g, cudaStream_t st) {
     const int64_t M = 1ll << g.mb, N = 1ll << g.nb, K = 1ll << g.kb;
     const bool abc = g.a_is == 0, bbc = g.b_is == 0;
     CUtensorMap ma, mb;
-    if (!map_raw(&ma, g.a, 2 * K, M, abc ? 1 : g.n_items, abc ? M * K * 8 : g.a_is * 8, TC_BM) ||
-        !map_raw(&mb, g.b, 2 * K, N, bbc ? 1 : g.n_items, bbc ? N * K * 8 : g.b_is * 8, BN / 2))
+    if (!map_raw(&ma, g.a, 2 * K, M, distinct_items(g.a_is, g.a_div, g.n_items), abc ? M * K * 8 : g.a_is * 8, TC_BM) ||
+        !map_raw(&mb, g.b, 2 * K, N, distinct_items(g.b_is, g.b_div, g.n_items), bbc ? N * K * 8 : g.b_is * 8, BN / 2))
         return cudaErrorInvalidValue;
     const int smem = (int)L::SMEM + 1024;
     int dev = 0;
@@ -870,8 +885,9 @@ static cudaError_t run_tc2(const TcArgs& g, cudaStream_t st) {
     const int64_t jobs = (int64_t)tiles_m * tiles_n * g.n_items;
     const unsigned grid = (unsigned)std::min<int64_t>(jobs, sms);  // one CTA per SM (shared memory)
     k_gemm_tc2<BN><<<grid, TC2_THREADS, smem, st>>>(ma, mb, (float*)g.c, g.c_is * 2, (int)M, (int)(2 * N),
-                                                    (int)(2 * K), tiles_n, tiles_m * tiles_n, g.n_items, abc, bbc,
-                                                    g.limit, g.err);
+                                                    (int)(2 * K), tiles_n, tiles_m * tiles_n, g.n_items,
+                                                    item_div(g.a_is, g.a_div), item_div(g.b_is, g.b_div), g.limit,
+                                                    g.err);
     return cudaGetLastError();
 }
 

@@ -39,7 +39,8 @@ class QXError(RuntimeError):
 
 class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("max_items", ctypes.c_int32), ("gemm_min_bits", ctypes.c_int32),
-                ("executor", ctypes.c_int32), ("timeout_cycles", ctypes.c_int64)]
+                ("executor", ctypes.c_int32), ("timeout_cycles", ctypes.c_int64), ("no_slice_level", ctypes.c_int32),
+                ("pad", ctypes.c_int32)]
 
 
 _lib = None
@@ -117,9 +118,10 @@ def _check(h, rc):
 EXEC_AUTO, EXEC_BATCHED, EXEC_PERSISTENT, EXEC_GROUP_MEMBER = 0, 1, 2, 3
 
 
-def qx_create(device=0, stream=0, precision=QX_PREC_C64, max_items=0, gemm_min_bits=0, executor=EXEC_AUTO):
+def qx_create(device=0, stream=0, precision=QX_PREC_C64, max_items=0, gemm_min_bits=0, executor=EXEC_AUTO,
+              no_slice_level=0):
     h = ctypes.c_void_p()
-    opt = Options(precision, max_items, gemm_min_bits, executor, 0)
+    opt = Options(precision, max_items, gemm_min_bits, executor, 0, int(no_slice_level), 0)
     rc = load().qx_create(ctypes.byref(h), int(device), ctypes.c_void_p(int(stream)), ctypes.byref(opt))
     if rc != QX_OK:
         raise QXError(rc, "qx_create failed (device, options)")
@@ -134,8 +136,8 @@ def qx_last_error(h):
     return load().qx_last_error(h).decode()
 
 
-def qx_set_options(h, precision=QX_PREC_C64, max_items=0, gemm_min_bits=0, executor=EXEC_AUTO):
-    opt = Options(precision, max_items, gemm_min_bits, executor, 0)
+def qx_set_options(h, precision=QX_PREC_C64, max_items=0, gemm_min_bits=0, executor=EXEC_AUTO, no_slice_level=0):
+    opt = Options(precision, max_items, gemm_min_bits, executor, 0, int(no_slice_level), 0)
     _check(h, load().qx_set_options(h, ctypes.byref(opt)))
 
 
@@ -288,14 +290,15 @@ class Contractor:
     """A network + plan resident on one GPU with a torch-allocated workspace."""
 
     def __init__(self, n_qubits, gate_records, open_mask, order, sliced, max_bits, device=0,
-                 precision=QX_PREC_C64, max_items=0, workspace_bytes=None, stream=None, executor=EXEC_AUTO):
+                 precision=QX_PREC_C64, max_items=0, workspace_bytes=None, stream=None, executor=EXEC_AUTO,
+                 no_slice_level=0):
         import torch
         self.torch = torch
         self.device = torch.device("cuda", device)
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         self.n_qubits = int(n_qubits)
         self.n_open = 0 if open_mask is None else int(np.sum(np.asarray(open_mask) != 0))
-        self.h = qx_create(device, self.stream.cuda_stream, precision, max_items, 0, executor)
+        self.h = qx_create(device, self.stream.cuda_stream, precision, max_items, 0, executor, no_slice_level)
         qx_build_network(self.h, n_qubits, gate_records, open_mask)
         self.peak_entries = qx_set_plan(self.h, order, sliced)
         self.n_slices = 1 << len(np.asarray(sliced).reshape(-1))

@@ -310,6 +310,43 @@ def test_concurrent_issue_is_bit_identical_to_in_order(qx, precision):
         assert rel_l2(got, ref) <= TOL_C64
 
 
+@pytest.mark.parametrize("precision", [0, 1, 2, 3])
+def test_slice_level_is_bit_identical_to_per_pair(qx, precision):
+    """Steps that no output bit touches, run once per slice and read by every bitstring of the slice,
+    give the bits the per-pair execution gives (same kernels, same operands), with less work."""
+    import torch
+    w = W.sliced()
+    d_bits = torch.from_numpy(w.bitstrings).cuda()
+    runs, flops = {}, {}
+    for off, max_items in ((0, 0), (1, 0), (0, 700), (0, 100)):
+        c = qx.Contractor(w.n_qubits, w.gates, w.open_mask, w.order, w.sliced, len(w.bitstrings),
+                          precision=precision, max_items=max_items, no_slice_level=off)
+        out = c.contract_device(d_bits)
+        torch.cuda.synchronize()
+        runs[(off, max_items)] = out.cpu().numpy()
+        flops[(off, max_items)] = c.stats()["flops"]
+        c.close()
+    assert np.array_equal(runs[(0, 0)], runs[(1, 0)])
+    assert np.array_equal(runs[(0, 700)], runs[(1, 0)])  # 2 slices per batch
+    assert np.array_equal(runs[(0, 100)], runs[(1, 0)])  # fewer pairs per batch than bitstrings
+    assert flops[(0, 0)] < 0.5 * flops[(1, 0)]
+
+
+@pytest.mark.parametrize("rows,cols,depth,n_open,n_slice,n_bits,max_items", [
+    (3, 4, 8, 1, 4, 6, 7), (3, 4, 8, 1, 4, 6, 13), (4, 4, 8, 0, 5, 9, 0), (3, 3, 8, 9, 3, 2, 0),
+    (2, 5, 10, 2, 4, 33, 50)])
+def test_slice_level_vs_statevector(qx, rows, cols, depth, n_open, n_slice, n_bits, max_items):
+    # ragged batches: a batch may hold one slice and part of the bitstrings, several slices, or (all
+    # qubits open) no output bit at all, so the root itself is per slice
+    circ, om, order, sliced, bits = grid_case(rows, cols, depth, 90 + depth + n_bits, n_open, n_slice, n_bits)
+    ref = oracle.sv_amplitudes(circ.n_qubits, C.gates_to_records(circ), om, bits)
+    for prec in (0, 1):
+        c = _contractor(qx, circ, om, order, sliced, n_bits, precision=prec, max_items=max_items)
+        got = c.contract(bits)
+        assert rel_l2(got, ref) <= TOL_C64
+        c.close()
+
+
 def test_stream_count_is_checked(qx):
     circ, om, order, sliced, bits = grid_case(3, 3, 6, 5, 1, 1, 2)
     c = _contractor(qx, circ, om, order, sliced, 2)

@@ -97,3 +97,37 @@ def test_dependency_check_catches_a_missing_edge():
     ops[j]["deps"] = ops[j]["deps"][:-1]
     with pytest.raises(AssertionError):
         _check(ops)
+
+
+def test_per_slice_launches_read_no_per_pair_storage():
+    """Steps that no output bit touches run once per slice: they may read invariant and per-slice
+    tensors only, and every per-pair launch comes after the per-slice launches it reads."""
+    from paper_2110_09894_gb300 import qx
+    w = W.sliced()
+    lines = _plan_lines(qx, w.n_qubits, w.gates, w.open_mask, w.order, w.sliced, 1)
+    ops = _parse(lines)
+    levels = [line.split()[3] for line in lines]
+    assert levels.count("slice") >= 5 and levels.count("pair") >= 5
+    for j, (op, lv) in enumerate(zip(ops, levels)):
+        for space, _, _ in op["w"]:
+            assert space == {"shared": "shared", "slice": "slice", "pair": "pair"}[lv]
+        if lv != "pair":
+            assert all(space != "pair" for space, _, _ in op["r"])
+        if lv == "shared":
+            assert all(space == "shared" for space, _, _ in op["r"])
+    _check(ops)
+
+
+def test_per_slice_level_shrinks_work_and_workspace():
+    from paper_2110_09894_gb300 import qx
+    w = W.sliced()
+    got = {}
+    for off in (0, 1):
+        h = qx.qx_create(-1, precision=1, no_slice_level=off)
+        qx.qx_build_network(h, w.n_qubits, w.gates, w.open_mask)
+        qx.qx_set_plan(h, w.order, w.sliced)
+        got[off] = qx.qx_workspace_size(h, len(w.bitstrings), w.n_slices * len(w.bitstrings))
+        qx.qx_destroy(h)
+    assert got[0] < 0.6 * got[1]
+    with pytest.raises(qx.QXError):
+        qx.qx_create(-1, no_slice_level=2)
