@@ -487,7 +487,7 @@ __device__ __forceinline__ void split4(float4 v, float4& hi, float4& lo) {
 // then the threads ct = 0 .. TC2_CONV - 1 build B' hi / lo in shared memory.
 template <int BN>
 __device__ __forceinline__ void tc2_convert(const uint8_t* land, uint8_t* ms, int ct, uint32_t tmem, int qq,
-                                            int lane, uint32_t ahi) {
+                                            int lane, uint32_t ahi, bool with_a) {
     using L = Tc2<BN>;
     const int r = 32 * qq + lane;
     const uint32_t lanes = (uint32_t)(32 * qq) << 16;
@@ -495,8 +495,10 @@ __device__ __forceinline__ void tc2_convert(const uint8_t* land, uint8_t* ms, in
     // the loads overlap instead of waiting behind each other's stores
     constexpr int NBC = (BN / 2) * 8 / TC2_CONV;
     float4 va[8], vb[NBC];
+    if (with_a) {
 #pragma unroll
-    for (int j = 0; j < 8; ++j) va[j] = *(const float4*)(land + r * 128 + ((j ^ (r & 7)) << 4));
+        for (int j = 0; j < 8; ++j) va[j] = *(const float4*)(land + r * 128 + ((j ^ (r & 7)) << 4));
+    }
 #pragma unroll
     for (int i = 0; i < NBC; ++i) {
         const int c = ct + TC2_CONV * i;
@@ -504,7 +506,7 @@ __device__ __forceinline__ void tc2_convert(const uint8_t* land, uint8_t* ms, in
         vb[i] = *(const float4*)(land + L::A + n * 128 + ((j ^ (n & 7)) << 4));
     }
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {  // 16 columns (four 16-byte chunks) at a time
+    for (int h = 0; h < 2 && with_a; ++h) {  // 16 columns (four 16-byte chunks) at a time
         float hi[16], lo[16];
 #pragma unroll
         for (int jj = 0; jj < 4; ++jj) {
@@ -540,10 +542,14 @@ template <int BN>
 __global__ void __launch_bounds__(TC2_THREADS, 1)
     k_gemm_tc2(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                float* __restrict__ C, int64_t c_is, int M, int N2, int K2, int tiles_n, int tiles, int64_t n_items,
-               int a_div, int b_div, long long limit, int* err) {
+               int a_div, int b_div, int keep_a, long long limit, int* err) {
     // persistent over (pair, tile) jobs: job = blockIdx.x + t * gridDim.x; the
     // k-stages of successive jobs form one sequence g = t * nk + it, so both
-    // rings stay full across tile boundaries
+    // rings stay full across tile boundaries.
+    // keep_a (A shared by the a_div items of a slice, all of A's k-stages fit in TMEM after the
+    // accumulators): A is split into TMEM at columns ACOL + 64 it for stage it, and a job whose A
+    // (slice, m tile) is the one its CTA's previous job used loads and splits only B.  The job order
+    // stays the same, so neighbouring CTAs still work on neighbouring items.
     using L = Tc2<BN>;
     constexpr int BK = 32;  // TF32 elements per stage (one 128-byte slab)
     constexpr int NL = L::NL, NM = L::NM, NTB = L::NTB;
@@ -562,13 +568,18 @@ __global__ void __launch_bounds__(TC2_THREADS, 1)
     const int64_t jobs = (int64_t)tiles * n_items;
     const int64_t my_jobs = jobs > blockIdx.x ? (jobs - 1 - blockIdx.x) / gridDim.x + 1 : 0;
     const int64_t total = my_jobs * nk;
-    auto job_of = [&](int64_t t, int64_t* item, int* m0, int* n0) {
+    // job t of this CTA: its item, tile origin and the key of its A (its A item and m tile)
+    auto job_of = [&](int64_t t, int64_t* item, int* m0, int* n0, int64_t* akey) {
         const int64_t j = blockIdx.x + t * (int64_t)gridDim.x;
         *item = j / tiles;
         const int tile = (int)(j % tiles);
         *m0 = (tile / tiles_n) * TC_BM;
         *n0 = (tile % tiles_n) * BN;  // row of B'; raw B row n0 / 2
+        *akey = (*item / a_div) * (tiles / tiles_n) + tile / tiles_n;
     };
+    // Every role walks the stages g = 0, 1, ... with counters (ring slot and its phase, stage within
+    // the job, job) advanced by one step at a time: 64-bit divisions per stage would cost more
+    // cycles than a stage's MMAs.  A job is decoded (job_of) once, at its first or last stage.
     if (threadIdx.x == 0) {
         for (int s = 0; s < NL; ++s) {
             mbar_init(&full[s], 1);
@@ -599,21 +610,34 @@ __global__ void __launch_bounds__(TC2_THREADS, 1)
     const uint32_t tmem = tmem_slot;
 
     if (warp == 0 && lane == 0) {
-        int64_t issued = 0;
+        int64_t issued = 0, t = 0, item = 0, akey = 0, prev_key = -1;
+        int l = 0, it = 0, m0 = 0, n0 = 0, ia = 0, ib = 0;
+        uint32_t lph = 0;
+        bool with_a = true;
         for (int64_t g = 0; g < total; ++g) {
-            const int l = (int)(g % NL);
-            if (!mbar_wait(&lfree[l], (uint32_t)(((g / NL) & 1) ^ 1), limit, err) || *(volatile int*)&abort_flag) {
+            if (!mbar_wait(&lfree[l], lph ^ 1u, limit, err) || *(volatile int*)&abort_flag) {
                 atomicExch(&abort_flag, 1);
                 break;
             }
-            int64_t item;
-            int m0, n0;
-            job_of(g / nk, &item, &m0, &n0);
-            const int it = (int)(g % nk);
-            mbar_expect_tx(&full[l], L::LAND);  // raw A and raw B
-            tma_load_3d(land(l), &mapA, it * BK, m0, (int)(item / a_div), &full[l]);
-            tma_load_3d(land(l) + L::A, &mapB, it * BK, n0 >> 1, (int)(item / b_div), &full[l]);
+            if (it == 0) {
+                job_of(t, &item, &m0, &n0, &akey);
+                with_a = !keep_a || akey != prev_key;
+                prev_key = akey;
+                ia = (int)(item / a_div);
+                ib = (int)(item / b_div);
+            }
+            mbar_expect_tx(&full[l], with_a ? L::LAND : L::BRAW);  // raw A (unless kept) and raw B
+            if (with_a) tma_load_3d(land(l), &mapA, it * BK, m0, ia, &full[l]);
+            tma_load_3d(land(l) + L::A, &mapB, it * BK, n0 >> 1, ib, &full[l]);
             ++issued;
+            if (++it == nk) {
+                it = 0;
+                ++t;
+            }
+            if (++l == NL) {
+                l = 0;
+                lph ^= 1u;
+            }
         }
         if (*(volatile int*)&abort_flag) {  // let the copies in flight land before the CTA exits
             for (int64_t g = (issued > NL ? issued - NL : 0); g < issued; ++g)
@@ -624,12 +648,14 @@ __global__ void __launch_bounds__(TC2_THREADS, 1)
         // commits cost about as much as issuing the stage's MMAs), the other keeps the tensor pipe busy;
         // stage g accumulates into TMEM buffer g % 2, i.e. each issuer owns one buffer
         const int who = warp == 1 ? 0 : 1;
+        static_assert(NTB == 2 && NM > 2, "issuer g owns accumulator buffer g % 2 and steps two MMA slots");
+        const int b = who;
         bool ok = true;
-        for (int64_t g = who; g < total && ok; g += 2) {
-            const int m = (int)(g % NM);
-            const int b = (int)(g % NTB);
-            const int64_t u = g / NTB;
-            if (!mbar_wait(&mfull[m], (uint32_t)((g / NM) & 1), limit, err) ||
+        int m = who, it = who % nk;
+        uint32_t mph = 0;
+        int64_t u = 0;  // g / NTB
+        for (int64_t g = who; g < total && ok; g += 2, ++u) {
+            if (!mbar_wait(&mfull[m], mph, limit, err) ||
                 (u > 0 && !mbar_wait(&tempty[b], (uint32_t)((u - 1) & 1), limit, err)) || *(volatile int*)&abort_flag) {
                 atomicExch(&abort_flag, 1);
                 ok = false;
@@ -638,9 +664,10 @@ __global__ void __launch_bounds__(TC2_THREADS, 1)
             tc_fence_after();
             const uint32_t st = s_addr(mslot(m));
             const uint32_t d = tmem + b * BN;
+            const uint32_t acol = L::ACOL + 64 * (uint32_t)(keep_a ? it : m);
 #pragma unroll
             for (int kk = 0; kk < BK / 8; ++kk) {
-                const uint32_t ahi = tmem + L::ACOL + 64 * m + 8 * kk, alo = ahi + 32;
+                const uint32_t ahi = tmem + acol + 8 * kk, alo = ahi + 32;
                 const uint64_t bhi = sdesc(st + kk * 32), blo = sdesc(st + L::OFF_BLO + kk * 32);
                 mma_tf32_ta(d, ahi, bhi, IDESC, kk != 0);
                 mma_tf32_ta(d, ahi, blo, IDESC, 1);
@@ -648,6 +675,13 @@ __global__ void __launch_bounds__(TC2_THREADS, 1)
             }
             tc_commit(&mfree[m]);
             tc_commit(&tfull[b]);
+            m += 2;
+            if (m >= NM) {
+                m -= NM;
+                mph ^= 1u;
+            }
+            it += 2;
+            while (it >= nk) it -= nk;
         }
         if (!ok) {  // the MMAs this thread issued finish before TMEM is freed
             tc_commit(&drain[who]);
@@ -657,21 +691,56 @@ __global__ void __launch_bounds__(TC2_THREADS, 1)
         // converters: landing slot -> MMA slot, ahead of the MMAs; warp w writes the A rows of TMEM
         // lanes 32 (w % 4)
         const int ct = threadIdx.x - 320;
+        int l = 0, m = 0, it = 0;
+        uint32_t lph = 0, mph = 0;
+        int64_t t = 0, prev_key = -1;
+        bool with_a = true;
         for (int64_t g = 0; g < total; ++g) {
-            const int l = (int)(g % NL), m = (int)(g % NM);
-            if (!mbar_wait(&full[l], (uint32_t)((g / NL) & 1), limit, err) ||
-                !mbar_wait(&mfree[m], (uint32_t)(((g / NM) & 1) ^ 1), limit, err) || *(volatile int*)&abort_flag) {
+            if (!mbar_wait(&full[l], lph, limit, err) || !mbar_wait(&mfree[m], mph ^ 1u, limit, err) ||
+                *(volatile int*)&abort_flag) {
                 atomicExch(&abort_flag, 1);
                 break;
             }
+            if (keep_a && it == 0) {
+                int64_t item, akey;
+                int m0, n0;
+                job_of(t, &item, &m0, &n0, &akey);
+                with_a = akey != prev_key;
+                prev_key = akey;
+                if (with_a && g > 0) {
+                    // a new A overwrites the kept one: every MMA of the earlier stages must be done
+                    // (each stage's commit to its accumulator buffer covers the MMAs its issuer issued
+                    // before it)
+                    bool ok = true;
+                    for (int64_t p = g - 1; p >= 0 && p >= g - 2 && ok; --p)
+                        ok = mbar_wait(&tfull[p & 1], (uint32_t)((p >> 1) & 1), limit, err);
+                    if (!ok) {
+                        atomicExch(&abort_flag, 1);
+                        break;
+                    }
+                }
+            }
             tc_fence_after();  // the MMAs that last read this MMA slot have completed (mfree)
-            tc2_convert<BN>(land(l), mslot(m), ct, tmem, warp & 3, lane, L::ACOL + 64 * m);
+            tc2_convert<BN>(land(l), mslot(m), ct, tmem, warp & 3, lane,
+                            L::ACOL + 64 * (uint32_t)(keep_a ? it : m), with_a);
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic writes -> tensor core
             tc_fence_before();
             __syncwarp();
             if (lane == 0) {
                 asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(s_addr(&lfree[l])) : "memory");
                 asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(s_addr(&mfull[m])) : "memory");
+            }
+            if (++it == nk) {
+                it = 0;
+                ++t;
+            }
+            if (++l == NL) {
+                l = 0;
+                lph ^= 1u;
+            }
+            if (++m == NM) {
+                m = 0;
+                mph ^= 1u;
             }
         }
     } else if (warp >= 2 && warp <= 9) {
@@ -680,39 +749,44 @@ __global__ void __launch_bounds__(TC2_THREADS, 1)
         float tot[BN / 2];
 #pragma unroll
         for (int j = 0; j < BN / 2; ++j) tot[j] = 0.f;
-        for (int64_t g = 0; g < total; ++g) {
-            const int b = (int)(g % NTB);
-            const int64_t u = g / NTB;
-            if (!mbar_wait(&tfull[b], (uint32_t)(u & 1), limit, err) || *(volatile int*)&abort_flag) {
-                atomicExch(&abort_flag, 1);
-                break;
+        int64_t g = 0;
+        for (int64_t t = 0; t < my_jobs; ++t) {
+            bool ok = true;
+            for (int it = 0; it < nk; ++it, ++g) {
+                const int b = (int)(g & 1);
+                if (!mbar_wait(&tfull[b], (uint32_t)((g >> 1) & 1), limit, err) || *(volatile int*)&abort_flag) {
+                    atomicExch(&abort_flag, 1);
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+#pragma unroll
+                for (int c = 0; c < BN / 64; ++c) {
+                    float v[32];
+                    tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + b * BN + (BN / 2) * half + 32 * c, v);
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) tot[32 * c + j] += v[j];
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0)
+                    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(s_addr(&tempty[b])) : "memory");
             }
-            tc_fence_after();
+            if (!ok) break;
+            // the job's last stage is in: write its tile, start the next total
+            int64_t item, akey;
+            int m0, n0;
+            job_of(t, &item, &m0, &n0, &akey);
+            // lane r holds row 32 q + r; each 32-column block is transposed across the warp so
+            // that every store writes 128 contiguous bytes of one row
+            float* cb = C + item * c_is + (int64_t)(m0 + 32 * q) * N2 + n0 + (BN / 2) * half + lane;
 #pragma unroll
-            for (int c = 0; c < BN / 64; ++c) {
-                float v[32];
-                tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + b * BN + (BN / 2) * half + 32 * c, v);
+            for (int b32 = 0; b32 < BN / 64; ++b32) {
+                transpose32(tot + 32 * b32, lane);
 #pragma unroll
-                for (int j = 0; j < 32; ++j) tot[32 * c + j] += v[j];
-            }
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(s_addr(&tempty[b])) : "memory");
-            if (g % nk == nk - 1) {  // last stage of a job: write its tile, start the next total
-                int64_t item;
-                int m0, n0;
-                job_of(g / nk, &item, &m0, &n0);
-                // lane r holds row 32 q + r; each 32-column block is transposed across the warp so
-                // that every store writes 128 contiguous bytes of one row
-                float* cb = C + item * c_is + (int64_t)(m0 + 32 * q) * N2 + n0 + (BN / 2) * half + lane;
-#pragma unroll
-                for (int b32 = 0; b32 < BN / 64; ++b32) {
-                    transpose32(tot + 32 * b32, lane);
-#pragma unroll
-                    for (int r = 0; r < 32; ++r) {
-                        cb[(int64_t)r * N2 + 32 * b32] = tot[32 * b32 + r];
-                        tot[32 * b32 + r] = 0.f;
-                    }
+                for (int r = 0; r < 32; ++r) {
+                    cb[(int64_t)r * N2 + 32 * b32] = tot[32 * b32 + r];
+                    tot[32 * b32 + r] = 0.f;
                 }
             }
         }
@@ -884,10 +958,14 @@ static cudaError_t run_tc2(const TcArgs& g, cudaStream_t st) {
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 152;
     const int64_t jobs = (int64_t)tiles_m * tiles_n * g.n_items;
     const unsigned grid = (unsigned)std::min<int64_t>(jobs, sms);  // one CTA per SM (shared memory)
+    // A shared by the items of a slice, and all of its k-stages fit in TMEM after the accumulators:
+    // keep it across the jobs of a CTA
+    const int nk = (int)(2 * K / 32);
+    const int keep_a = g.a_is && g.a_div > 1 && L::ACOL + 64 * nk <= L::TMEM_COLS;
     k_gemm_tc2<BN><<<grid, TC2_THREADS, smem, st>>>(ma, mb, (float*)g.c, g.c_is * 2, (int)M, (int)(2 * N),
                                                     (int)(2 * K), tiles_n, tiles_m * tiles_n, g.n_items,
-                                                    item_div(g.a_is, g.a_div), item_div(g.b_is, g.b_div), g.limit,
-                                                    g.err);
+                                                    item_div(g.a_is, g.a_div), item_div(g.b_is, g.b_div), keep_a,
+                                                    g.limit, g.err);
     return cudaGetLastError();
 }
 
