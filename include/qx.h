@@ -190,6 +190,20 @@ int qx_poll(qx_handle h, int64_t req, int32_t* done);
  * while profiling.  enable = 0 turns it off and drops the captured graph. */
 int qx_set_graphs(qx_handle h, int enable);
 
+/* Memoised invariant intermediates (the checkpoint reuse the paper's outlook
+ * proposes, after Pan et al. 2021: parts of the contraction that no sliced
+ * bond and no output bit touch are the same for every slice and every
+ * bitstring, so they can be kept between samples).  enable = 1: the first
+ * contraction after this call (or after a new plan or workspace) computes
+ * them into the bound workspace as usual, later calls of the batched
+ * executor skip those steps and read the kept tensors.  Same amplitudes
+ * (the kept tensors are the ones the skipped steps would write again).
+ * enable = 0 (default): every call computes them.  qx_contract_device_static
+ * always computes them.  A device timeout reported by qx_device_status
+ * drops the kept tensors.  Drops a captured graph.  QX_EINVAL unless enable
+ * is 0 or 1. */
+int qx_set_memo(qx_handle h, int enable);
+
 /* Concurrent issue of independent contraction steps (the paper has no
  * counterpart; Sec. IV-A's levels of parallelism stop at one contraction per
  * GPU kernel).  The plan compiler records, for every kernel launch, the

@@ -163,6 +163,8 @@ struct qx_ctx {
 
     // CUDA graph of a repeated contraction (same buffers, sizes and slice range)
     bool graphs = true;
+    bool memo = false;       // keep the invariant intermediates across calls (qx_set_memo)
+    bool inv_ready = false;  // the bound workspace holds them
     struct {
         const uint8_t* bits = nullptr;
         double* amps = nullptr;
@@ -1788,7 +1790,8 @@ static int contract_impl(qx_ctx* h, const uint8_t* d_bits, int64_t n_bits, int64
     // all streams joined before its slice sum, and the next batch reuses the per-slice and per-pair
     // space.  Steps that no output bit touches run once per slice of the batch (one item per slice),
     // the others once per pair.
-    bool prologue = true;
+    // with qx_set_memo, the invariant intermediates of an earlier call are still in the workspace
+    bool prologue = !(h->memo && h->inv_ready);
     for (int64_t s0 = s_begin; s0 < s_end; s0 += ns_batch) {
         const int64_t ns = std::min(ns_batch, s_end - s0);
         for (int64_t b0 = 0; b0 < n_bits; b0 += nb_batch) {
@@ -1824,6 +1827,7 @@ static int contract_impl(qx_ctx* h, const uint8_t* d_bits, int64_t n_bits, int64
     cudaError_t e = launch_finalize(acc, d_amps, n_bits * n_o, h->leaf_scale[0], h->leaf_scale[1], h->stream);
     if (e != cudaSuccess) return fail(h, QX_ECUDA, "finalize launch failed: %s", cudaGetErrorString(e));
     h->last_launches++;
+    if (h->memo) h->inv_ready = true;
     return QX_OK;
 }
 
@@ -1972,6 +1976,7 @@ static void unbind(qx_ctx* h) {
     h->leaves_on_device = false;
     h->pops_on_device = false;
     h->waves_on_device = false;
+    h->inv_ready = false;
 }
 
 int qx_set_plan(qx_handle h, const int64_t* order, int64_t n_steps, const int64_t* sliced, int32_t n_sliced,
@@ -2199,6 +2204,15 @@ int qx_set_graphs(qx_handle h, int enable) {
     return QX_OK;
 }
 
+int qx_set_memo(qx_handle h, int enable) {
+    if (!h) return QX_EINVAL;
+    if (enable != 0 && enable != 1) return fail(h, QX_EINVAL, "enable must be 0 or 1");
+    drop_graph(h);
+    h->memo = enable != 0;
+    h->inv_ready = false;
+    return QX_OK;
+}
+
 int qx_set_streams(qx_handle h, int32_t n_streams) {
     if (!h) return QX_EINVAL;
     if (n_streams < 1 || n_streams > 32) return fail(h, QX_EINVAL, "n_streams %d out of range [1, 32]", n_streams);
@@ -2238,7 +2252,10 @@ int qx_device_status(qx_handle h) {
     CUDA_TRY(h, cudaSetDevice(h->device));
     CUDA_TRY(h, cudaMemcpyAsync(&flag, h->ws + h->off_err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     CUDA_TRY(h, cudaStreamSynchronize(h->stream));
-    if (flag) return fail(h, flag, "a bounded device wait expired; the result is invalid");
+    if (flag) {
+        h->inv_ready = false;  // the kept intermediates may be incomplete
+        return fail(h, flag, "a bounded device wait expired; the result is invalid");
+    }
     return QX_OK;
 }
 
@@ -2291,11 +2308,11 @@ int qx_internal_contract_in(qx_ctx* h, char* buf, int64_t buf_bytes, const uint8
             slices_cap;
         bool leaves_on_device;
         int64_t off_pops, off_counter, off_results, off_pscratch, off_pops_inv, off_wave;
-        bool pops_on_device, waves_on_device;
+        bool pops_on_device, waves_on_device, inv_ready;
     } const saved = {h->ws,        h->ws_bytes, h->ws_owned,    h->max_bits,    h->off_err,    h->off_leaf,
                      h->off_bits,  h->off_acc,  h->off_amps,    h->off_inv,     h->off_item,   h->items_cap,
                      h->off_slice, h->slices_cap, h->leaves_on_device, h->off_pops, h->off_counter, h->off_results, h->off_pscratch,
-                     h->off_pops_inv, h->off_wave, h->pops_on_device, h->waves_on_device};
+                     h->off_pops_inv, h->off_wave, h->pops_on_device, h->waves_on_device, h->inv_ready};
     int64_t fixed, items = 0, slices = 0;
     layout(h, n_bits, &fixed);
     const bool fits = fit_regions(h, buf_bytes - fixed, n_bits, &items, &slices);
@@ -2323,6 +2340,7 @@ int qx_internal_contract_in(qx_ctx* h, char* buf, int64_t buf_bytes, const uint8
         h->pops_on_device = saved.pops_on_device;
         h->off_wave = saved.off_wave;
         h->waves_on_device = saved.waves_on_device;
+        h->inv_ready = saved.inv_ready;
     };
     if (!fits) {
         restore();
@@ -2338,6 +2356,7 @@ int qx_internal_contract_in(qx_ctx* h, char* buf, int64_t buf_bytes, const uint8
     h->leaves_on_device = false;
     h->pops_on_device = false;
     h->waves_on_device = false;
+    h->inv_ready = false;  // the shared scratch array holds whatever the last call left
     int rc = QX_OK;
     cudaError_t e = cudaSetDevice(h->device);
     if (e != cudaSuccess) rc = fail(h, QX_ECUDA, "cudaSetDevice: %s", cudaGetErrorString(e));

@@ -17,10 +17,14 @@
 namespace qx {
 
 __device__ __forceinline__ int64_t fix_offset(const Operand& op, const ItemCtx& ic, int64_t item) {
-    int64_t off = (op.per_slice ? item / ic.n_b : item) * op.item_stride;
+    // the items of one launch number fewer than 2^16 (kMaxBatchItems): one 32-bit division splits an
+    // item into its slice and bitstring within the batch
+    const uint32_t i32 = (uint32_t)item, nb = (uint32_t)ic.n_b;
+    const uint32_t sl = (op.per_slice || op.n_fix) ? i32 / nb : 0u;
+    int64_t off = (int64_t)(op.per_slice ? sl : i32) * op.item_stride;
     if (op.n_fix) {
-        const int64_t s = ic.s0 + item / ic.n_b;
-        const int64_t b = ic.b0 + item % ic.n_b;
+        const int64_t s = ic.s0 + sl;
+        const int64_t b = ic.b0 + (i32 - sl * nb);
         for (int f = 0; f < op.n_fix; ++f) {
             const int src = op.fix_src[f];
             const int64_t v = src >= 0 ? ((s >> src) & 1) : (int64_t)(ic.bits[b * ic.n_qubits + (-src - 1)] & 1);
@@ -186,6 +190,7 @@ static int sm_count() {
 cudaError_t launch_permute(const PermDesc& d, const ItemCtx& ic, int64_t n_items, float2* out, int64_t out_is,
                            cudaStream_t st) {
     if (n_items <= 0) return cudaSuccess;
+    if (n_items > kMaxBatchItems || ic.n_items > kMaxBatchItems) return cudaErrorInvalidValue;  // fix_offset
     PermTables tb;
     perm_tables(d, &tb);
     const int64_t jobs = ((int64_t)1 << d.n_outer) * n_items;
@@ -403,6 +408,7 @@ static int sm_count();
 cudaError_t launch_small(const SmallDesc& d, const ItemCtx& ic, int64_t n_items, float2* out, int64_t out_is,
                          cudaStream_t st) {
     if (n_items <= 0) return cudaSuccess;
+    if (n_items > kMaxBatchItems || ic.n_items > kMaxBatchItems) return cudaErrorInvalidValue;  // fix_offset
     // flat: short per-pair rows with a small operand light enough to read through L1 per thread;
     // a larger small operand is better staged once per CTA in shared memory (per-pair kernel)
     if (d.mb < 8 && d.kb + d.nb <= 6) {
@@ -663,10 +669,28 @@ __global__ void __launch_bounds__(256) k_dot_perm(const PermDesc d, const PermTa
             ob += tb.outer_out[i];
             u &= u - 1;
         }
-        for (int j = tid; j < n; j += 256) tile[pad32(j)] = d.in.base[ib + s_in[j & LM] + s_in[64 + (j >> LO)]];
+        // every load of the tile (both operands) is issued before any is used
+        constexpr int PER = (1 << kPermTileBits) / 256;
+        float2 v[PER], a[PER];
+#pragma unroll
+        for (int k = 0; k < PER; ++k) {
+            const int j = tid + 256 * k;
+            if (j < n) {
+                v[k] = d.in.base[ib + s_in[j & LM] + s_in[64 + (j >> LO)]];
+                a[k] = Ap[ob + s_out[j & LM] + s_out[64 + (j >> LO)]];
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < PER; ++k) {
+            const int j = tid + 256 * k;
+            if (j < n) tile[pad32(j)] = v[k];
+        }
         __syncthreads();
-        for (int j = tid; j < n; j += 256)
-            cfma(acc, Ap[ob + s_out[j & LM] + s_out[64 + (j >> LO)]], tile[pad32(s_map[j & LM] | s_map[64 + (j >> LO)])]);
+#pragma unroll
+        for (int k = 0; k < PER; ++k) {
+            const int j = tid + 256 * k;
+            if (j < n) cfma(acc, a[k], tile[pad32(s_map[j & LM] | s_map[64 + (j >> LO)])]);
+        }
         __syncthreads();
     }
     red[tid] = acc;
@@ -684,7 +708,8 @@ __global__ void __launch_bounds__(256) k_dot_perm(const PermDesc d, const PermTa
 cudaError_t launch_dot_perm(const PermDesc& d, const ItemCtx& ic, int64_t n_items, const float2* a, int64_t a_is,
                             float2* c, int64_t c_is, cudaStream_t st, int a_div) {
     if (n_items <= 0) return cudaSuccess;
-    if (d.t > kPermTileBits || n_items > 0x7fffffffll || a_div < 1) return cudaErrorInvalidValue;
+    if (d.t > kPermTileBits || n_items > kMaxBatchItems || ic.n_items > kMaxBatchItems || a_div < 1)
+        return cudaErrorInvalidValue;
     PermTables tb;
     perm_tables(d, &tb);
     k_dot_perm<<<(unsigned)n_items, 256, 0, st>>>(d, tb, ic, a, a_is, c, c_is, a_div);
@@ -840,6 +865,7 @@ __global__ void k_slice_sum(const SumDesc d, const ItemCtx ic, double* __restric
 cudaError_t launch_slice_sum(const SumDesc& d, const ItemCtx& ic, double* acc, cudaStream_t st) {
     const int64_t n = (int64_t)ic.n_b << d.open_bits;
     if (n <= 0) return cudaSuccess;
+    if (ic.n_items > kMaxBatchItems) return cudaErrorInvalidValue;  // fix_offset
     k_slice_sum<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(d, ic, acc);
     return cudaGetLastError();
 }

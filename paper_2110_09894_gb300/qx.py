@@ -26,7 +26,7 @@ EXPORTS = ("qx_create", "qx_destroy", "qx_last_error", "qx_set_options", "qx_bui
            "qx_profile_read", "qx_contract_device_static", "qx_device_status", "qx_group_create",
            "qx_group_scratch_size", "qx_group_bind", "qx_group_run", "qx_group_last_error", "qx_group_destroy",
            "qx_set_graphs", "qx_set_streams", "qx_describe_plan", "qx_submit", "qx_poll", "qx_esup_accept",
-           "qx_esup_sample")
+           "qx_esup_sample", "qx_set_memo")
 QX_STATIC_SCRATCH_BYTES = 64 << 20
 KERNEL_KINDS = ("permute", "small", "gemm", "sum", "tc_prep", "tc_gemm", "persist", "wave")
 
@@ -79,6 +79,7 @@ def load(path=None):
         "qx_set_profiling": ([vp, ctypes.c_int], ctypes.c_int),
         "qx_device_status": ([vp], ctypes.c_int),
         "qx_set_graphs": ([vp, ctypes.c_int], ctypes.c_int),
+        "qx_set_memo": ([vp, ctypes.c_int], ctypes.c_int),
         "qx_set_streams": ([vp, i32], ctypes.c_int),
         "qx_submit": ([vp, vp, i64, i64, i64, vp, vp, ctypes.POINTER(i64)], ctypes.c_int),
         "qx_poll": ([vp, i64, ctypes.POINTER(i32)], ctypes.c_int),
@@ -238,6 +239,11 @@ def qx_describe_plan(h):
 
 def qx_set_graphs(h, enable):
     _check(h, load().qx_set_graphs(h, 1 if enable else 0))
+
+
+def qx_set_memo(h, enable):
+    """Keep the invariant intermediates in the workspace across calls (enable) or recompute them."""
+    _check(h, load().qx_set_memo(h, int(enable)))
 
 
 def qx_submit(h, d_bits_ptr, n_bits, s_begin, s_end, d_amps_ptr, h_amps_ptr=None):

@@ -29,14 +29,17 @@ class ESupSampler:
     [count]) supplies the random numbers; by default a numpy PCG64 generator
     seeded with ``seed`` draws uniform bits and uniforms in [0, 1).
     ``batch`` candidates go to the GPU per call (default: the contractor's
-    bitstring capacity).
+    bitstring capacity).  ``memo`` switches on qx_set_memo for the
+    contractor: the steps that no slice and no output bit touch run once.
     """
 
     def __init__(self, contractor: qx.Contractor, seed: int = 0, warmup: int = 1000, batch: int | None = None,
-                 draw=None):
+                 draw=None, memo: bool = True):
         if contractor.n_open:
             raise ValueError("sampling needs every qubit closed")
         self.c = contractor
+        if memo:  # the invariant intermediates are computed once for all batches of candidates
+            qx.qx_set_memo(contractor.h, 1)
         self.torch = contractor.torch
         self.n_qubits = contractor.n_qubits
         # one contraction piece per batch, so every candidate of a batch has its amplitude

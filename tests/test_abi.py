@@ -157,3 +157,13 @@ def test_sampler_argument_checks_on_host_only_handle(qx):
         qx.qx_esup_sample(h, 0, 0, 4, 0, 5, 1.0, 0, 0)
     assert e.value.code == qx.QX_EINVAL
     qx.qx_destroy(h)
+
+
+def test_memo_switch_on_host_only_handle(qx):
+    h = qx.qx_create(device=-1)
+    qx.qx_set_memo(h, 1)
+    qx.qx_set_memo(h, 0)
+    with pytest.raises(qx.QXError) as e:
+        qx.qx_set_memo(h, 2)
+    assert e.value.code == qx.QX_EINVAL
+    qx.qx_destroy(h)

@@ -347,6 +347,40 @@ def test_slice_level_vs_statevector(qx, rows, cols, depth, n_open, n_slice, n_bi
         c.close()
 
 
+def test_memoised_invariants_give_the_same_bits(qx):
+    """qx_set_memo: later calls skip the invariant steps and read the kept tensors; new bitstrings,
+    graph replay and the static-scratch entry point in between all give the bits of fresh calls."""
+    import torch
+    w = W.sliced()
+    bits_a = torch.from_numpy(w.bitstrings).cuda()
+    bits_b = torch.from_numpy(C.random_bitstrings(w.n_qubits, len(w.bitstrings), 4242)).cuda()
+    fresh = qx.Contractor(w.n_qubits, w.gates, w.open_mask, w.order, w.sliced, len(w.bitstrings), precision=1)
+    want_a = fresh.contract_device(bits_a).cpu().numpy()
+    want_b = fresh.contract_device(bits_b).cpu().numpy()
+    full_flops = fresh.stats()["flops"]
+    fresh.close()
+    c = qx.Contractor(w.n_qubits, w.gates, w.open_mask, w.order, w.sliced, len(w.bitstrings), precision=1)
+    qx.qx_set_memo(c.h, 1)
+    out = torch.empty((len(w.bitstrings), 1, 2), dtype=torch.float64, device="cuda")
+    for i in range(4):  # eager with the invariant steps, eager without, graph capture, replay
+        c.contract_device(bits_a, out)
+        torch.cuda.synchronize()
+        assert np.array_equal(out.cpu().numpy(), want_a), i
+        if i == 1:
+            assert c.stats()["flops"] < full_flops
+    assert np.array_equal(c.contract_device(bits_b).cpu().numpy(), want_b)
+    d_static = torch.empty_like(out)
+    qx.qx_contract_device_static(c.h, bits_b.data_ptr(), len(w.bitstrings), d_static.data_ptr())
+    torch.cuda.synchronize()
+    assert np.array_equal(d_static.cpu().numpy(), want_b)
+    c.contract_device(bits_a, out)
+    torch.cuda.synchronize()
+    assert np.array_equal(out.cpu().numpy(), want_a)
+    with pytest.raises(qx.QXError):
+        qx.qx_set_memo(c.h, 2)
+    c.close()
+
+
 def test_stream_count_is_checked(qx):
     circ, om, order, sliced, bits = grid_case(3, 3, 6, 5, 1, 1, 2)
     c = _contractor(qx, circ, om, order, sliced, 2)
