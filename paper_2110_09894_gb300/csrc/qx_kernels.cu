@@ -669,28 +669,10 @@ __global__ void __launch_bounds__(256) k_dot_perm(const PermDesc d, const PermTa
             ob += tb.outer_out[i];
             u &= u - 1;
         }
-        // every load of the tile (both operands) is issued before any is used
-        constexpr int PER = (1 << kPermTileBits) / 256;
-        float2 v[PER], a[PER];
-#pragma unroll
-        for (int k = 0; k < PER; ++k) {
-            const int j = tid + 256 * k;
-            if (j < n) {
-                v[k] = d.in.base[ib + s_in[j & LM] + s_in[64 + (j >> LO)]];
-                a[k] = Ap[ob + s_out[j & LM] + s_out[64 + (j >> LO)]];
-            }
-        }
-#pragma unroll
-        for (int k = 0; k < PER; ++k) {
-            const int j = tid + 256 * k;
-            if (j < n) tile[pad32(j)] = v[k];
-        }
+        for (int j = tid; j < n; j += 256) tile[pad32(j)] = d.in.base[ib + s_in[j & LM] + s_in[64 + (j >> LO)]];
         __syncthreads();
-#pragma unroll
-        for (int k = 0; k < PER; ++k) {
-            const int j = tid + 256 * k;
-            if (j < n) cfma(acc, a[k], tile[pad32(s_map[j & LM] | s_map[64 + (j >> LO)])]);
-        }
+        for (int j = tid; j < n; j += 256)
+            cfma(acc, Ap[ob + s_out[j & LM] + s_out[64 + (j >> LO)]], tile[pad32(s_map[j & LM] | s_map[64 + (j >> LO)])]);
         __syncthreads();
     }
     red[tid] = acc;

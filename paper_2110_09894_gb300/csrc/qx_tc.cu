@@ -203,19 +203,23 @@ __device__ __forceinline__ void tc_commit(uint64_t* b) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(s_addr(b))
                  : "memory");
 }
-// In-register transpose of a 32 x 32 block held one row per lane (a[i] = element (lane, i)):
-// afterwards a[i] = element (i, lane).  Stage s swaps bit s of the lane index with bit s of the
-// register index through one exchange with lane ^ s per register pair.
-__device__ __forceinline__ void transpose32(float* a, int lane) {
+// Partial in-register transpose of a 32 x 32 block held one row per lane (a[i] = element (lane, i)):
+// register index bits 2..4 trade places with lane bits 0..2, one exchange with lane ^ 2^t per
+// register pair for t = 0, 1, 2.  Afterwards a[4 r + c] of lane l is element (8 (l >> 3) + r,
+// 4 (l & 7) + c): each register quad is four consecutive columns of one row, so one 16-byte store
+// per quad from the 32 lanes writes four whole 128-byte row runs (three exchange rounds and eight
+// stores instead of five rounds and 32 stores of a full transpose).
+__device__ __forceinline__ void transpose_q4(float* a, int lane) {
 #pragma unroll
-    for (int s = 16; s >= 1; s >>= 1) {
-        const bool up = (lane & s) != 0;
+    for (int t = 0; t < 3; ++t) {
+        const int p = 2 + t;
+        const bool up = (lane >> t) & 1;
 #pragma unroll
         for (int i = 0; i < 32; ++i) {
-            if (i & s) continue;
-            const int j = i | s;
+            if ((i >> p) & 1) continue;
+            const int j = i | (1 << p);
             const float send = up ? a[i] : a[j];
-            const float recv = __shfl_xor_sync(0xffffffffu, send, s);
+            const float recv = __shfl_xor_sync(0xffffffffu, send, 1 << t);
             if (up) a[i] = recv;
             else a[j] = recv;
         }
@@ -425,12 +429,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 for (int j = 0; j < TC_BN; ++j) tot[j] *= inv;
             }
             // tiles are whole (rows and columns multiples of 128; see tc_shape_ok)
-            float* cb = C + (int64_t)item * c_is + (int64_t)(m0 + 32 * q) * N2 + n0 + lane;
+            float* cb = C + (int64_t)item * c_is + (int64_t)(m0 + 32 * q + ((lane >> 3) << 3)) * N2 + n0 +
+                        ((lane & 7) << 2);
 #pragma unroll
             for (int b32 = 0; b32 < TC_BN / 32; ++b32) {
-                transpose32(tot + 32 * b32, lane);
+                float* t = tot + 32 * b32;
+                transpose_q4(t, lane);
 #pragma unroll
-                for (int r = 0; r < 32; ++r) cb[(int64_t)r * N2 + 32 * b32] = tot[32 * b32 + r];
+                for (int r = 0; r < 8; ++r)
+                    *(float4*)(cb + (int64_t)r * N2 + 32 * b32) = make_float4(t[4 * r], t[4 * r + 1], t[4 * r + 2], t[4 * r + 3]);
             }
         }
     }
@@ -777,16 +784,19 @@ __global__ void __launch_bounds__(TC2_THREADS, 1)
             int64_t item, akey;
             int m0, n0;
             job_of(t, &item, &m0, &n0, &akey);
-            // lane r holds row 32 q + r; each 32-column block is transposed across the warp so
-            // that every store writes 128 contiguous bytes of one row
-            float* cb = C + item * c_is + (int64_t)(m0 + 32 * q) * N2 + n0 + (BN / 2) * half + lane;
+            // lane r holds row 32 q + r; each 32-column block is partly transposed across the warp so
+            // that every 16-byte store instruction writes whole 128-byte runs of four rows
+            float* cb = C + item * c_is + (int64_t)(m0 + 32 * q + ((lane >> 3) << 3)) * N2 + n0 + (BN / 2) * half +
+                        ((lane & 7) << 2);
 #pragma unroll
             for (int b32 = 0; b32 < BN / 64; ++b32) {
-                transpose32(tot + 32 * b32, lane);
+                float* t = tot + 32 * b32;
+                transpose_q4(t, lane);
 #pragma unroll
-                for (int r = 0; r < 32; ++r) {
-                    cb[(int64_t)r * N2 + 32 * b32] = tot[32 * b32 + r];
-                    tot[32 * b32 + r] = 0.f;
+                for (int r = 0; r < 8; ++r) {
+                    *(float4*)(cb + (int64_t)r * N2 + 32 * b32) =
+                        make_float4(t[4 * r], t[4 * r + 1], t[4 * r + 2], t[4 * r + 3]);
+                    t[4 * r] = t[4 * r + 1] = t[4 * r + 2] = t[4 * r + 3] = 0.f;
                 }
             }
         }
