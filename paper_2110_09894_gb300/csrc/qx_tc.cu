@@ -549,7 +549,7 @@ template <int BN>
 __global__ void __launch_bounds__(TC2_THREADS, 1)
     k_gemm_tc2(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                float* __restrict__ C, int64_t c_is, int M, int N2, int K2, int tiles_n, int tiles, int64_t n_items,
-               int a_div, int b_div, int keep_a, long long limit, int* err) {
+               int a_div, int b_div, int keep_a, int pack2, long long limit, int* err) {
     // persistent over (pair, tile) jobs: job = blockIdx.x + t * gridDim.x; the
     // k-stages of successive jobs form one sequence g = t * nk + it, so both
     // rings stay full across tile boundaries.
@@ -557,6 +557,9 @@ __global__ void __launch_bounds__(TC2_THREADS, 1)
     // accumulators): A is split into TMEM at columns ACOL + 64 it for stage it, and a job whose A
     // (slice, m tile) is the one its CTA's previous job used loads and splits only B.  The job order
     // stays the same, so neighbouring CTAs still work on neighbouring items.
+    // pack2 (N = BN / 4 complex per item, B dense per item, both items of a job on the same A): a job
+    // covers items 2 i and 2 i + 1 side by side, B's rows of both come in one TMA box (B read as one
+    // [items x N][2K] matrix), and drain half h writes item 2 i + h.
     using L = Tc2<BN>;
     constexpr int BK = 32;  // TF32 elements per stage (one 128-byte slab)
     constexpr int NL = L::NL, NM = L::NM, NTB = L::NTB;
@@ -578,7 +581,7 @@ __global__ void __launch_bounds__(TC2_THREADS, 1)
     // job t of this CTA: its item, tile origin and the key of its A (its A item and m tile)
     auto job_of = [&](int64_t t, int64_t* item, int* m0, int* n0, int64_t* akey) {
         const int64_t j = blockIdx.x + t * (int64_t)gridDim.x;
-        *item = j / tiles;
+        *item = pack2 ? 2 * (j / tiles) : j / tiles;
         const int tile = (int)(j % tiles);
         *m0 = (tile / tiles_n) * TC_BM;
         *n0 = (tile % tiles_n) * BN;  // row of B'; raw B row n0 / 2
@@ -635,7 +638,8 @@ __global__ void __launch_bounds__(TC2_THREADS, 1)
             }
             mbar_expect_tx(&full[l], with_a ? L::LAND : L::BRAW);  // raw A (unless kept) and raw B
             if (with_a) tma_load_3d(land(l), &mapA, it * BK, m0, ia, &full[l]);
-            tma_load_3d(land(l) + L::A, &mapB, it * BK, n0 >> 1, ib, &full[l]);
+            if (pack2) tma_load_3d(land(l) + L::A, &mapB, it * BK, (int)item * (BN / 4), 0, &full[l]);
+            else tma_load_3d(land(l) + L::A, &mapB, it * BK, n0 >> 1, ib, &full[l]);
             ++issued;
             if (++it == nk) {
                 it = 0;
@@ -786,8 +790,8 @@ __global__ void __launch_bounds__(TC2_THREADS, 1)
             job_of(t, &item, &m0, &n0, &akey);
             // lane r holds row 32 q + r; each 32-column block is partly transposed across the warp so
             // that every 16-byte store instruction writes whole 128-byte runs of four rows
-            float* cb = C + item * c_is + (int64_t)(m0 + 32 * q + ((lane >> 3) << 3)) * N2 + n0 + (BN / 2) * half +
-                        ((lane & 7) << 2);
+            float* cb = (pack2 ? C + (item + half) * c_is : C + item * c_is + n0 + (BN / 2) * half) +
+                        (int64_t)(m0 + 32 * q + ((lane >> 3) << 3)) * N2 + ((lane & 7) << 2);
 #pragma unroll
             for (int b32 = 0; b32 < BN / 64; ++b32) {
                 float* t = tot + 32 * b32;
@@ -941,13 +945,16 @@ static bool map_raw(CUtensorMap* m, const void* base, int64_t k2, int64_t rows, 
 }
 
 template <int BN>
-static cudaError_t run_tc2(const TcArgs& g, cudaStream_t st) {
+static cudaError_t run_tc2(const TcArgs& g, cudaStream_t st, bool pack2 = false) {
     using L = Tc2<BN>;
     const int64_t M = 1ll << g.mb, N = 1ll << g.nb, K = 1ll << g.kb;
     const bool abc = g.a_is == 0, bbc = g.b_is == 0;
     CUtensorMap ma, mb;
-    if (!map_raw(&ma, g.a, 2 * K, M, distinct_items(g.a_is, g.a_div, g.n_items), abc ? M * K * 8 : g.a_is * 8, TC_BM) ||
-        !map_raw(&mb, g.b, 2 * K, N, distinct_items(g.b_is, g.b_div, g.n_items), bbc ? N * K * 8 : g.b_is * 8, BN / 2))
+    if (!map_raw(&ma, g.a, 2 * K, M, distinct_items(g.a_is, g.a_div, g.n_items), abc ? M * K * 8 : g.a_is * 8, TC_BM))
+        return cudaErrorInvalidValue;
+    if (pack2 ? !map_raw(&mb, g.b, 2 * K, N * g.n_items, 1, N * g.n_items * K * 8, BN / 2)
+              : !map_raw(&mb, g.b, 2 * K, N, distinct_items(g.b_is, g.b_div, g.n_items), bbc ? N * K * 8 : g.b_is * 8,
+                         BN / 2))
         return cudaErrorInvalidValue;
     const int smem = (int)L::SMEM + 1024;
     int dev = 0;
@@ -963,25 +970,32 @@ static cudaError_t run_tc2(const TcArgs& g, cudaStream_t st) {
             done[dev >> 6] |= 1ull << (dev & 63);
         }
     }
-    const int tiles_m = (int)(M / TC_BM), tiles_n = (int)(2 * N / BN);
+    const int tiles_m = (int)(M / TC_BM), tiles_n = pack2 ? 1 : (int)(2 * N / BN);
     int sms = 152;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 152;
-    const int64_t jobs = (int64_t)tiles_m * tiles_n * g.n_items;
+    const int64_t job_items = pack2 ? g.n_items / 2 : g.n_items;  // a packed job covers two items
+    const int64_t jobs = (int64_t)tiles_m * tiles_n * job_items;
     const unsigned grid = (unsigned)std::min<int64_t>(jobs, sms);  // one CTA per SM (shared memory)
     // A shared by the items of a slice, and all of its k-stages fit in TMEM after the accumulators:
     // keep it across the jobs of a CTA
     const int nk = (int)(2 * K / 32);
     const int keep_a = g.a_is && g.a_div > 1 && L::ACOL + 64 * nk <= L::TMEM_COLS;
     k_gemm_tc2<BN><<<grid, TC2_THREADS, smem, st>>>(ma, mb, (float*)g.c, g.c_is * 2, (int)M, (int)(2 * N),
-                                                    (int)(2 * K), tiles_n, tiles_m * tiles_n, g.n_items,
+                                                    (int)(2 * K), tiles_n, tiles_m * tiles_n, job_items,
                                                     item_div(g.a_is, g.a_div), item_div(g.b_is, g.b_div), keep_a,
-                                                    g.limit, g.err);
+                                                    pack2 ? 1 : 0, g.limit, g.err);
     return cudaGetLastError();
 }
 
 cudaError_t launch_tc2_gemm(const TcArgs& g, cudaStream_t st) {
     if (!(g.mb >= 7 && g.nb >= 5 && g.kb >= 4 && g.n_items > 0 && g.n_items <= 65535)) return cudaErrorInvalidValue;
     if (!g.a_kmajor || !g.b_kmajor) return cudaErrorInvalidValue;
+    // N = 32 complex per item: two items per 128-column tile when their B rows are contiguous and
+    // they read the same A (shared, or per slice with an even number of items per slice)
+    const int64_t NK = (1ll << g.nb) * (1ll << g.kb);
+    const bool pack2 = g.nb == 5 && g.b_is == NK && g.b_div <= 1 && g.n_items % 2 == 0 &&
+                       (g.a_is == 0 || (g.a_div > 1 && g.a_div % 2 == 0));
+    if (pack2) return run_tc2<128>(g, st, true);
     return g.nb >= 6 ? run_tc2<128>(g, st) : run_tc2<64>(g, st);
 }
 
