@@ -19,6 +19,7 @@
 #include <cstdint>
 #include <cstdio>
 #include <cstring>
+#include <functional>
 #include <limits>
 #include <map>
 #include <string>
@@ -140,7 +141,7 @@ struct qx_ctx {
     bool wave_ok = false;
     std::vector<POp> wave_ops;          // one per invariant op, grouped by level
     std::vector<int32_t> wave_idx;      // 0 .. n-1 (positions into wave_ops)
-    std::vector<int32_t> wave_start;    // level L: wave_ops[wave_start[L] .. wave_start[L + 1])
+    std::vector<int32_t> wave_start;    // chain c: wave_ops[wave_start[c] .. wave_start[c + 1])
     std::vector<int> wave_of;           // per op: its level, -1 if not in a wave
     std::vector<double> wave_flops, wave_bytes;
     bool waves_on_device = false;
@@ -1023,6 +1024,19 @@ static int compile_plan(qx_ctx* h, const int64_t* order, int64_t n_steps, const 
     if (!R.variant && R.storage >= 0) h->stor[R.storage].last = kLive;
     h->item_entries = std::max<int64_t>(assign_offsets(h, 2), kAlignEntries);
     h->slice_entries = assign_offsets(h, 1);
+    if (h->opt.executor < 2) {
+        // a small invariant region gets no reuse: then the only hazards between invariant steps are
+        // their data dependencies, which form trees the prologue runs one CTA per tree
+        int64_t tot = 0;
+        for (const Storage& st : h->stor)
+            if (st.level == 0) tot += align_up(st.entries, kAlignEntries);
+        if (tot <= ((int64_t)1 << 22))
+            for (Storage& st : h->stor)
+                if (st.level == 0) {
+                    st.def = 0;
+                    st.last = kLive;
+                }
+    }
     h->inv_entries = assign_offsets(h, 0);
     h->flops_inv = h->flops_slice = h->flops_item = 0;
     for (const Op& op : h->ops) (op.level == 2 ? h->flops_item : op.level == 1 ? h->flops_slice : h->flops_inv) += op.flops;
@@ -1075,10 +1089,11 @@ static void layout(qx_ctx* h, int64_t max_bits, int64_t* fixed_bytes) {
         h->off_pscratch = off;
         off += align_up((int64_t)h->persist_grid * h->item_entries * 8, 256);
     }
-    h->off_wave = off;  // wave programs: the POps, then their index list
+    h->off_wave = off;  // prologue programs: the POps, their index list, the chain boundaries
     if (h->wave_ok)
         off += align_up((int64_t)(h->wave_ops.size() * sizeof(POp)), 256) +
-               align_up((int64_t)(h->wave_idx.size() * sizeof(int32_t)), 256);
+               align_up((int64_t)(h->wave_idx.size() * sizeof(int32_t)), 256) +
+               align_up((int64_t)(h->wave_start.size() * sizeof(int32_t)), 256);
     h->off_slice = h->off_item = off;
     *fixed_bytes = off;
 }
@@ -1339,27 +1354,38 @@ static void build_waves(qx_ctx* h) {
         inv.push_back((int)j);
     }
     if (inv.empty()) return;
-    int levels = 0;
-    for (int j : inv) {
-        int lv = 0;
+    // chains: invariant steps joined by a dependency (data, or space reuse when the region is
+    // reused) go to one chain, which one CTA runs in plan order; different chains touch no common
+    // storage, so the CTAs need no synchronisation
+    std::vector<int> root(h->ops.size());
+    for (size_t j = 0; j < root.size(); ++j) root[j] = (int)j;
+    std::function<int(int)> find = [&](int x) { return root[x] == x ? x : root[x] = find(root[x]); };
+    for (int j : inv)
         for (int i : h->deps[j])
-            if (!h->ops[i].variant) lv = std::max(lv, h->wave_of[i] + 1);
-        h->wave_of[j] = lv;
-        levels = std::max(levels, lv + 1);
+            if (!h->ops[i].variant) root[find(i)] = find(j);
+    std::vector<int> chain_of(h->ops.size(), -1), order;
+    for (int j : inv) {
+        const int r = find(j);
+        if (chain_of[r] < 0) {
+            chain_of[r] = (int)order.size();
+            order.push_back(r);
+        }
     }
-    h->wave_start.assign(levels + 1, 0);
-    h->wave_flops.assign(levels, 0.0);
-    h->wave_bytes.assign(levels, 0.0);
-    for (int L = 0; L < levels; ++L) {
-        h->wave_start[L] = (int32_t)h->wave_ops.size();
+    const int n_chains = (int)order.size();
+    h->wave_start.assign(n_chains + 1, 0);
+    h->wave_flops.assign(1, 0.0);
+    h->wave_bytes.assign(1, 0.0);
+    for (int c = 0; c < n_chains; ++c) {
+        h->wave_start[c] = (int32_t)h->wave_ops.size();
         for (int j : inv)
-            if (h->wave_of[j] == L) {
+            if (chain_of[find(j)] == c) {
+                h->wave_of[j] = 0;  // one launch: every dependant waits for its end
                 h->wave_ops.push_back(to_pop(h, h->ops[j]));
-                h->wave_flops[L] += h->ops[j].flops;
-                h->wave_bytes[L] += op_bytes(h, h->ops[j], 1);
+                h->wave_flops[0] += h->ops[j].flops;
+                h->wave_bytes[0] += op_bytes(h, h->ops[j], 1);
             }
     }
-    h->wave_start[levels] = (int32_t)h->wave_ops.size();
+    h->wave_start[n_chains] = (int32_t)h->wave_ops.size();
     h->wave_idx.resize(h->wave_ops.size());
     for (size_t i = 0; i < h->wave_idx.size(); ++i) h->wave_idx[i] = (int32_t)i;
     h->wave_ok = true;
@@ -1622,23 +1648,26 @@ struct Dag {
             CUDA_TRY(h, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
             h->op_ev.push_back(e);
         }
-        while (h->wave_ok && h->wave_ev.size() + 1 < h->wave_start.size()) {
+        while (h->wave_ok && h->wave_ev.empty()) {
             cudaEvent_t e;
             CUDA_TRY(h, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
             h->wave_ev.push_back(e);
         }
         return QX_OK;
     }
-    // the invariant steps, one launch per dependency level, on the handle's stream
+    // the invariant steps, one launch on the handle's stream: one CTA per chain
     int waves(const uint8_t* d_bits) {
         if (!h->wave_ok) return QX_OK;
-        const size_t n = h->wave_ops.size();
+        const size_t n = h->wave_ops.size(), nc = h->wave_start.size() - 1;
         char* wbase = h->ws + h->off_wave;
         const int32_t* idx = (const int32_t*)(wbase + align_up((int64_t)(n * sizeof(POp)), 256));
+        const int32_t* starts = idx + align_up((int64_t)(n * sizeof(int32_t)), 256) / (int64_t)sizeof(int32_t);
         if (!h->waves_on_device) {
             CUDA_TRY(h, cudaMemcpyAsync(wbase, h->wave_ops.data(), n * sizeof(POp), cudaMemcpyHostToDevice, h->stream));
             CUDA_TRY(h, cudaMemcpyAsync((void*)idx, h->wave_idx.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice,
                                         h->stream));
+            CUDA_TRY(h, cudaMemcpyAsync((void*)starts, h->wave_start.data(), (nc + 1) * sizeof(int32_t),
+                                        cudaMemcpyHostToDevice, h->stream));
             CUDA_TRY(h, cudaStreamSynchronize(h->stream));
             h->waves_on_device = true;
         }
@@ -1651,19 +1680,14 @@ struct Dag {
         prog.bits = d_bits;
         prog.n_b = 1;
         prog.scratch_override = inv_base(h);
-        const int levels = (int)h->wave_start.size() - 1;
-        for (int L = 0; L < levels; ++L) {
-            size_t slot;
-            cudaError_t e = prof_begin(h, QX_KERNEL_WAVE, h->wave_flops[L], h->wave_bytes[L], &slot);
-            if (e == cudaSuccess)
-                e = launch_wave(prog.ops, idx + h->wave_start[L], h->wave_start[L + 1] - h->wave_start[L], prog,
-                                h->stream);
-            if (e == cudaSuccess) e = prof_end(h, slot);
-            if (e == cudaSuccess && on) e = cudaEventRecord(h->wave_ev[L], h->stream);
-            if (e != cudaSuccess) return fail(h, QX_ECUDA, "prologue wave launch failed: %s", cudaGetErrorString(e));
-            h->last_launches++;
-            h->last_flops += h->wave_flops[L];
-        }
+        size_t slot;
+        cudaError_t e = prof_begin(h, QX_KERNEL_WAVE, h->wave_flops[0], h->wave_bytes[0], &slot);
+        if (e == cudaSuccess) e = launch_chains(prog.ops, idx, starts, (int)nc, prog, h->stream);
+        if (e == cudaSuccess) e = prof_end(h, slot);
+        if (e == cudaSuccess && on) e = cudaEventRecord(h->wave_ev[0], h->stream);
+        if (e != cudaSuccess) return fail(h, QX_ECUDA, "prologue launch failed: %s", cudaGetErrorString(e));
+        h->last_launches++;
+        h->last_flops += h->wave_flops[0];
         waves_now = true;
         if (on) last_on[0] = INT32_MAX / 2;  // per-pair steps go to the other streams first
         return QX_OK;

@@ -401,6 +401,36 @@ __global__ void __launch_bounds__(256, 2) k_wave(const POp* __restrict__ ops, co
     }
 }
 
+// The prologue as chains: CTA c runs its chain of invariant steps in order; different chains
+// share no storage, so no CTA waits for another.
+__global__ void __launch_bounds__(256, 2) k_chain(const POp* __restrict__ ops, const int32_t* __restrict__ idx,
+                                                  const int32_t* __restrict__ starts, const PProg prog) {
+    extern __shared__ float2 psm[];
+    PairCtx c;
+    c.s = 0;
+    c.bits = prog.bits;
+    c.scratch = prog.scratch_override;
+    c.prog = &prog;
+    const int i1 = starts[blockIdx.x + 1];
+    for (int i = starts[blockIdx.x]; i < i1; ++i) {
+        const POp& op = ops[idx[i]];
+        switch (op.type) {
+            case POP_PERM: exec_perm(op, c, psm); break;
+            case POP_SMALL: exec_small(op, c, psm); break;
+            case POP_GEMM: exec_gemm(op, c, psm); break;
+            default: exec_dot(op, c, psm); break;
+        }
+        __syncthreads();  // this step's results (global and shared) before the next step reads them
+    }
+}
+
+cudaError_t launch_chains(const POp* ops, const int32_t* idx, const int32_t* starts, int n_chains, const PProg& prog,
+                          cudaStream_t st) {
+    if (n_chains <= 0) return cudaSuccess;
+    k_chain<<<n_chains, 256, kPersistSmem, st>>>(ops, idx, starts, prog);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_wave(const POp* ops, const int32_t* idx, int n, const PProg& prog, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
     k_wave<<<n, 256, kPersistSmem, st>>>(ops, idx, prog);
