@@ -344,14 +344,15 @@ void qx_group_destroy(qx_group_t g);
  * per pair) and algorithmic bytes (operands read once, result written once)
  * since profiling was last switched.  qx_set_profiling resets the totals. */
 #define QX_KERNEL_PERMUTE 0
-#define QX_KERNEL_SMALL   1
+#define QX_KERNEL_SMALL   1  /* gathers, small operand staged in shared memory (k_small) */
 #define QX_KERNEL_GEMM    2
 #define QX_KERNEL_SUM     3
 #define QX_KERNEL_TC_PREP 4  /* operand split / expansion for the tensor-core forms */
 #define QX_KERNEL_TC_GEMM 5  /* tcgen05 complex GEMM */
 #define QX_KERNEL_PERSIST 6  /* persistent executor (whole contractions) */
-#define QX_KERNEL_WAVE    7  /* batched executor: a level of small invariant steps, one CTA each */
-#define QX_KERNEL_KINDS   8
+#define QX_KERNEL_WAVE    7  /* batched executor: the small invariant steps, one CTA per chain */
+#define QX_KERNEL_SMALL_FLAT 8  /* gathers of short per-pair rows, one thread per row (k_small_flat) */
+#define QX_KERNEL_KINDS   9
 int qx_set_profiling(qx_handle h, int enable);
 int qx_profile_read(qx_handle h, int kind, double* ms, int64_t* launches, double* flops, double* bytes);
 

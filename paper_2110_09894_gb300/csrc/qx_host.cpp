@@ -1418,8 +1418,10 @@ static int run_op(qx_ctx* h, const Op& op, const ItemCtx& ic, int64_t n_items, c
     int64_t dis;
     storage_addr(h, op.dst, &dp, &dis);
     const bool direct = op.tc == TC_FORM_3XTF32_DIRECT, prep = op.tc && !direct;
+    SmallDesc sdesc{};
+    if (op.type == OP_SMALL) sdesc = small_desc(h, op);
     const int kind = op.type == OP_PERM    ? QX_KERNEL_PERMUTE
-                     : op.type == OP_SMALL ? QX_KERNEL_SMALL
+                     : op.type == OP_SMALL ? (small_is_flat(sdesc) ? QX_KERNEL_SMALL_FLAT : QX_KERNEL_SMALL)
                      : direct              ? QX_KERNEL_TC_GEMM
                      : prep                ? QX_KERNEL_TC_PREP
                                            : QX_KERNEL_GEMM;
@@ -1439,7 +1441,7 @@ static int run_op(qx_ctx* h, const Op& op, const ItemCtx& ic, int64_t n_items, c
     if (op.type == OP_PERM) {
         e = launch_permute(perm_desc(h, op), ic, n_items, dp, dis, st);
     } else if (op.type == OP_SMALL) {
-        e = launch_small(small_desc(h, op), ic, n_items, dp, dis, st);
+        e = launch_small(sdesc, ic, n_items, dp, dis, st);
     } else if (op.dot_perm) {
         float2* ap;
         int64_t ais;

@@ -112,6 +112,9 @@ void perm_tables(const PermDesc& d, PermTables* tb);
 // read by per-pair work, else 1)
 cudaError_t launch_dot_perm(const PermDesc& d, const ItemCtx& ic, int64_t n_items, const float2* a, int64_t a_is,
                             float2* c, int64_t c_is, cudaStream_t st, int a_div = 1);
+// whether launch_small runs this gather as k_small_flat (short per-pair rows, small operand read
+// through L1) rather than k_small (small operand staged in shared memory)
+bool small_is_flat(const SmallDesc& d);
 cudaError_t launch_small(const SmallDesc& d, const ItemCtx& ic, int64_t n_items, float2* out,
                          int64_t out_item_stride, cudaStream_t st);
 // Batched complex GEMM, C[M][N] = A . B with A stored [M][K] (a_kmajor) or

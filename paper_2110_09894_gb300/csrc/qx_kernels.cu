@@ -405,13 +405,15 @@ static cudaError_t small_flat_nb(const SmallDesc& d, const ItemCtx& ic, int64_t 
 
 static int sm_count();
 
+bool small_is_flat(const SmallDesc& d) { return d.mb < 8 && d.kb + d.nb <= 6; }
+
 cudaError_t launch_small(const SmallDesc& d, const ItemCtx& ic, int64_t n_items, float2* out, int64_t out_is,
                          cudaStream_t st) {
     if (n_items <= 0) return cudaSuccess;
     if (n_items > kMaxBatchItems || ic.n_items > kMaxBatchItems) return cudaErrorInvalidValue;  // fix_offset
     // flat: short per-pair rows with a small operand light enough to read through L1 per thread;
     // a larger small operand is better staged once per CTA in shared memory (per-pair kernel)
-    if (d.mb < 8 && d.kb + d.nb <= 6) {
+    if (small_is_flat(d)) {
         const int64_t total = n_items << d.mb;
         const unsigned grid = (unsigned)std::min<int64_t>((total + 255) / 256, (int64_t)sm_count() * 16);
         switch (d.kb) {

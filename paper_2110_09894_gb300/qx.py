@@ -28,7 +28,7 @@ EXPORTS = ("qx_create", "qx_destroy", "qx_last_error", "qx_set_options", "qx_bui
            "qx_set_graphs", "qx_set_streams", "qx_describe_plan", "qx_submit", "qx_poll", "qx_esup_accept",
            "qx_esup_sample", "qx_set_memo")
 QX_STATIC_SCRATCH_BYTES = 64 << 20
-KERNEL_KINDS = ("permute", "small", "gemm", "sum", "tc_prep", "tc_gemm", "persist", "wave")
+KERNEL_KINDS = ("permute", "small", "gemm", "sum", "tc_prep", "tc_gemm", "persist", "wave", "small_flat")
 
 
 class QXError(RuntimeError):
