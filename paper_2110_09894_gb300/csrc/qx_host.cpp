@@ -142,7 +142,8 @@ struct qx_ctx {
     std::vector<POp> wave_ops;          // one per invariant op, grouped by level
     std::vector<int32_t> wave_idx;      // 0 .. n-1 (positions into wave_ops)
     std::vector<int32_t> wave_start;    // chain c: wave_ops[wave_start[c] .. wave_start[c + 1])
-    std::vector<int> wave_of;           // per op: its level, -1 if not in a wave
+    std::vector<int> wave_of;           // per op: 0 if the prologue launch runs it, else -1
+    std::vector<int> chain_of_op;       // per op: its prologue chain, -1 if none
     std::vector<double> wave_flops, wave_bytes;
     bool waves_on_device = false;
     std::vector<cudaEvent_t> wave_ev;
@@ -1338,6 +1339,7 @@ static void build_waves(qx_ctx* h) {
     h->wave_flops.clear();
     h->wave_bytes.clear();
     h->wave_of.assign(h->ops.size(), -1);
+    h->chain_of_op.assign(h->ops.size(), -1);
     if (h->opt.executor >= 2) return;  // the persistent executors run their own prologue program
     constexpr int64_t kWaveEntries = 4096;
     std::vector<int> inv;
@@ -1380,6 +1382,7 @@ static void build_waves(qx_ctx* h) {
         for (int j : inv)
             if (chain_of[find(j)] == c) {
                 h->wave_of[j] = 0;  // one launch: every dependant waits for its end
+                h->chain_of_op[j] = c;
                 h->wave_ops.push_back(to_pop(h, h->ops[j]));
                 h->wave_flops[0] += h->ops[j].flops;
                 h->wave_bytes[0] += op_bytes(h, h->ops[j], 1);
@@ -2210,6 +2213,10 @@ int qx_describe_plan(qx_handle h, char* buf, int64_t len, int64_t* needed) {
         out += sc ? " scale=1 after=" : " scale=0 after=";
         for (size_t k = 0; k < h->deps[i].size(); ++k) {
             snprintf(line, sizeof line, "%s%d", k ? "," : "", h->deps[i][k]);
+            out += line;
+        }
+        if (h->wave_ok && h->chain_of_op[i] >= 0) {  // run by the prologue launch, in this chain
+            snprintf(line, sizeof line, " chain=%d", h->chain_of_op[i]);
             out += line;
         }
         out += "\n";

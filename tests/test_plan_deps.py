@@ -131,3 +131,54 @@ def test_per_slice_level_shrinks_work_and_workspace():
     assert got[0] < 0.6 * got[1]
     with pytest.raises(qx.QXError):
         qx.qx_create(-1, no_slice_level=2)
+
+
+def _chains(lines):
+    out = []
+    for line in lines:
+        m = re.search(r" chain=(\d+)", line)
+        out.append(int(m.group(1)) if m else -1)
+    return out
+
+
+def _check_chains(ops, chains):
+    """Prologue chains run on different CTAs with no synchronisation: steps of different chains must
+    touch no common storage where either writes, and a step's dependencies on other prologue steps
+    must sit in its own chain (which runs them earlier, in plan order)."""
+    for j, cj in enumerate(chains):
+        if cj < 0:
+            continue
+        for i in ops[j]["deps"]:
+            if chains[i] >= 0:
+                assert chains[i] == cj, f"step {j} (chain {cj}) depends on step {i} of chain {chains[i]}"
+        for i in range(j):
+            ci = chains[i]
+            if ci < 0 or ci == cj:
+                continue
+            oi, oj = ops[i], ops[j]
+            assert not (_overlap(oi["w"], oj["r"]) or _overlap(oi["r"], oj["w"]) or _overlap(oi["w"], oj["w"])), \
+                f"steps {i} (chain {ci}) and {j} (chain {cj}) share storage"
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_prologue_chains_share_no_storage(precision):
+    from paper_2110_09894_gb300 import qx
+    w = W.sliced()
+    lines = _plan_lines(qx, w.n_qubits, w.gates, w.open_mask, w.order, w.sliced, precision)
+    ops, chains = _parse(lines), _chains(lines)
+    levels = [line.split()[3] for line in lines]
+    # every invariant step of this plan is small: all of them run in the one prologue launch
+    assert all((c >= 0) == (lv == "shared") for c, lv in zip(chains, levels))
+    assert len(set(c for c in chains if c >= 0)) > 10
+    _check_chains(ops, chains)
+
+
+def test_chain_check_catches_a_step_in_the_wrong_chain():
+    from paper_2110_09894_gb300 import qx
+    w = W.sliced()
+    lines = _plan_lines(qx, w.n_qubits, w.gates, w.open_mask, w.order, w.sliced, 0)
+    ops, chains = _parse(lines), _chains(lines)
+    j = next(j for j in range(len(ops)) if chains[j] >= 0 and any(chains[i] >= 0 for i in ops[j]["deps"]))
+    chains[j] = max(chains) + 1
+    with pytest.raises(AssertionError):
+        _check_chains(ops, chains)
