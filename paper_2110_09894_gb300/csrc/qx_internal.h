@@ -173,7 +173,6 @@ struct PLaunch {
 constexpr int kPersistSmem = 17408;
 cudaError_t launch_persist(const PLaunch& L, int grid, cudaStream_t st);
 // one launch of n independent invariant steps: CTA i runs ops[idx[i]] (device arrays)
-cudaError_t launch_wave(const POp* ops, const int32_t* idx, int n, const PProg& prog, cudaStream_t st);
 // n_chains CTAs; CTA c runs ops[idx[starts[c]]], ops[idx[starts[c] + 1]], ... up to starts[c + 1], in
 // order, with a block barrier between steps (device arrays idx and starts)
 cudaError_t launch_chains(const POp* ops, const int32_t* idx, const int32_t* starts, int n_chains, const PProg& prog,

@@ -379,30 +379,11 @@ cudaError_t launch_group_sum(const GSum* d_sums, int32_t n, int64_t total, cudaS
     return cudaGetLastError();
 }
 
-// ---- a wave of invariant steps in one launch ---------------------------------------------------
-// The steps that no slice or bitstring touches are mostly tiny (gate-sized tensors).  Grouped by
-// dependency level, the steps of a level are independent: CTA i runs step idx[i] with the code of
-// the persistent kernel, its operands in the leaf buffer or the invariant region and its result in
-// the invariant region (the program's scratch).
-__global__ void __launch_bounds__(256, 2) k_wave(const POp* __restrict__ ops, const int32_t* __restrict__ idx,
-                                                 const PProg prog) {
-    extern __shared__ float2 psm[];
-    const POp& op = ops[idx[blockIdx.x]];
-    PairCtx c;
-    c.s = 0;
-    c.bits = prog.bits;
-    c.scratch = prog.scratch_override;
-    c.prog = &prog;
-    switch (op.type) {
-        case POP_PERM: exec_perm(op, c, psm); break;
-        case POP_SMALL: exec_small(op, c, psm); break;
-        case POP_GEMM: exec_gemm(op, c, psm); break;
-        default: exec_dot(op, c, psm); break;
-    }
-}
-
-// The prologue as chains: CTA c runs its chain of invariant steps in order; different chains
-// share no storage, so no CTA waits for another.
+// ---- the invariant steps in one launch -----------------------------------------------------------
+// The steps that no slice or bitstring touches are mostly tiny (gate-sized tensors).  The plan
+// compiler splits them into chains that share no storage (their dependency trees, with the
+// invariant region given no reuse): CTA c runs the steps of chain c in plan order with the code of
+// the persistent executor, a block barrier between steps, and waits for no other CTA.
 __global__ void __launch_bounds__(256, 2) k_chain(const POp* __restrict__ ops, const int32_t* __restrict__ idx,
                                                   const int32_t* __restrict__ starts, const PProg prog) {
     extern __shared__ float2 psm[];
@@ -428,12 +409,6 @@ cudaError_t launch_chains(const POp* ops, const int32_t* idx, const int32_t* sta
                           cudaStream_t st) {
     if (n_chains <= 0) return cudaSuccess;
     k_chain<<<n_chains, 256, kPersistSmem, st>>>(ops, idx, starts, prog);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_wave(const POp* ops, const int32_t* idx, int n, const PProg& prog, cudaStream_t st) {
-    if (n <= 0) return cudaSuccess;
-    k_wave<<<n, 256, kPersistSmem, st>>>(ops, idx, prog);
     return cudaGetLastError();
 }
 
