@@ -13,7 +13,8 @@ while other work is on the GPU:
   FP64 with compensation, in slice order;
 * each circuit owns a few execution lanes (a library handle with its own
   workspace and CUDA stream); lanes are created on demand while the device
-  memory budget allows (admission by memory) and reused afterwards;
+  memory budget allows (admission by memory) and reused afterwards; a lane
+  keeps its circuit's invariant intermediates across requests (qx_set_memo);
 * each chunk is one asynchronous request of the library (``qx_submit``: the
   contraction and the copy of its amplitudes to pinned host memory on the
   lane's stream); completion is polled with ``qx_poll``; latency runs from a
@@ -67,6 +68,8 @@ class _Lane:
         self.c = qx.Contractor(circ.n_qubits, circ.gates, circ.open_mask, circ.order, circ.sliced, max_bits,
                                device=dev.index or 0, precision=precision, stream=self.stream, executor=executor,
                                workspace_bytes=circ.lane_bytes)
+        # every request of the lane's circuit reads the same invariant intermediates: keep them
+        qx.qx_set_memo(self.c.h, 1)
         self.batch = None
 
 
