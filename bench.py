@@ -50,6 +50,9 @@ def parse():
     p.add_argument("--precision", default="3xtf32", choices=list(PRECISIONS),
                    help="contraction form (3xtf32 and bf16x3 meet the 1e-5 tolerance; fp16 is reported)")
     p.add_argument("--executor", default="auto", choices=["auto", "batched", "persistent"])
+    p.add_argument("--plan", default="default", choices=["default", "level-aware"],
+                   help="sliced workload plan: seeded greedy + tree trimming, or the candidate that executes the "
+                        "fewest flops per call with the per-slice level")
     p.add_argument("--no-slice-level", action="store_true",
                    help="compute bitstring-independent intermediates per (slice, bitstring) pair, not per slice")
     p.add_argument("--streams", type=int, default=8,
@@ -57,7 +60,9 @@ def parse():
     return p.parse_args()
 
 
-def workload(name):
+def workload(name, plan="default"):
+    if name == "sliced" and plan == "level-aware":
+        return W.sliced_level_aware()
     return {"small": W.small, "sliced": W.sliced, "large": W.large}[name]()
 
 
@@ -72,7 +77,7 @@ def config_of(w, extra=None):
            "grid": f"{w.circuit.rows}x{w.circuit.cols}", "sliced_bonds": len(w.sliced), "slices": w.n_slices,
            "bitstrings_per_gpu": int(len(w.bitstrings)), "open_qubits": w.n_open,
            "amplitudes_per_gpu": int(len(w.bitstrings)) << w.n_open, "peak_entries": 1 << w.peak_rank,
-           "plan": "seeded greedy (order) + tree trimming (slices)", "precision": None}
+           "plan": w.meta.get("plan", "seeded greedy (order) + tree trimming (slices)"), "precision": None}
     cfg.update(extra or {})
     return cfg
 
@@ -379,7 +384,7 @@ def main():
         return serving_bench(args)
     if args.impl == "ours" and args.workload == "sampling":
         return sampling_bench(args)
-    w = workload(args.workload) if args.workload in ("small", "sliced", "large") else W.sliced()
+    w = workload(args.workload, args.plan) if args.workload in ("small", "sliced", "large") else W.sliced()
     if args.impl == "reference":
         reference_arm(args, w, rank, world)
         return

@@ -211,3 +211,70 @@ def randomized_greedy(legs, trials, seed, n_slice=0, open_edges=(), settings=((1
         if best is None or key < best[0]:
             best = (key, order, sliced)
     return best[1], best[2]
+
+
+def executed_cost(legs, order, sliced, n_outputs, n_bits):
+    """Flops one contraction call executes when steps run at their dependence level.
+
+    A step that no sliced bond and no output bit reaches runs once, one that a
+    sliced bond reaches but no output bit runs once per slice, the others once
+    per (slice, bitstring) pair (n_bits bitstrings per call); a step is reached
+    by a fixed bond when any leaf below it touches that bond.  The last
+    n_outputs tensors are the closed outputs <x_q|: their bonds are fixed, and
+    absorbing one is a relabelling with no flops.  A step costs 8 M K N over
+    its unfixed bonds.
+    """
+    sl = frozenset(sliced)
+    first_out = len(legs) - n_outputs
+    out_wires = frozenset(e for t in range(first_out, len(legs)) for e in legs[t])
+    fixed = sl | out_wires
+    sets = [frozenset(l) for l in legs]
+    # a fixed bond is read as an address offset on every leaf it touches, so a leaf on a closed
+    # output wire depends on the bitstring, one on a sliced bond on the slice
+    by_slice = [bool(sl & sets[t]) for t in range(len(legs))]
+    by_bits = [bool(out_wires & sets[t]) for t in range(len(legs))]
+    n_slices = 1 << len(sl)
+    total = 0
+    for a, b in order:
+        sa, sb = sets[a] - fixed, sets[b] - fixed
+        shared = sa & sb
+        closing = (a >= first_out and a < len(legs)) or (b >= first_out and b < len(legs))
+        flops = 0 if closing else 8 * (1 << (len(sa - shared) + len(shared) + len(sb - shared)))
+        s_dep, b_dep = by_slice[a] or by_slice[b], by_bits[a] or by_bits[b]
+        total += flops * (n_slices * n_bits if b_dep else n_slices if s_dep else 1)
+        sets.append(sets[a] ^ sets[b])
+        by_slice.append(s_dep)
+        by_bits.append(b_dep)
+    return total
+
+
+def level_aware_plan(legs, trials, seed, n_slice, open_edges, n_outputs, n_bits, max_peak=None,
+                     settings=((1.0, 0.6), (0.75, 0.3), (0.75, 0.6), (0.5, 0.6), (0.25, 0.3), (1.0, 1.0),
+                               (1.0, 0.2))):
+    """Seeded greedy orders, each sliced by tree trimming, ranked by executed_cost.
+
+    Same candidates as randomized_greedy (Gumbel-perturbed greedy orders under
+    several (alpha, temperature) settings, plus the deterministic greedy
+    order), but every one is sliced and the plan that executes the fewest
+    flops per call of n_bits bitstrings wins (ties: smaller peak, earlier
+    candidate), among those whose largest intermediate has at most max_peak
+    legs.  Returns (order, sliced, executed flops, peak rank).
+    """
+    rng = SplitMix64(seed)
+    orders = [_greedy(legs)]
+    for alpha, temp in settings:
+        for _ in range(trials):
+            orders.append(_greedy(legs, rng, temp, alpha))
+    best = None
+    for k, order in enumerate(orders):
+        sliced = tree_trim_slices(legs, order, n_slice, seed + k, open_edges) if n_slice else []
+        peak, _ = plan_cost(legs, order, sliced)
+        if max_peak is not None and peak > max_peak:
+            continue
+        ex = executed_cost(legs, order, sliced, n_outputs, n_bits)
+        key = (ex, peak, k)
+        if best is None or key < best[0]:
+            best = (key, order, sliced)
+    if best is None:
+        raise ValueError("no candidate plan within max_peak")
+    return best[1], best[2], best[0][0], best[0][1]

@@ -24,7 +24,7 @@ import numpy as np
 
 from .circuits import (Circuit, SplitMix64, gates_to_records, near_square_shape, random_bitstrings,
                        random_grid_circuit)
-from .plan import (greedy_order, network_legs, plan_cost, randomized_greedy, tree_trim_slices)
+from .plan import (greedy_order, level_aware_plan, network_legs, plan_cost, randomized_greedy, tree_trim_slices)
 
 
 @dataclass
@@ -99,6 +99,26 @@ def sliced():
     circ = random_grid_circuit(4, 5, 12, cseed)
     bits = random_bitstrings(20, 256, cseed + 500000)
     return _workload("grid4x5_d12_s6_amp256", circ, np.zeros(20, np.uint8), 6, cseed, bits)
+
+
+@functools.lru_cache(maxsize=None)
+def sliced_level_aware():
+    """The sliced workload's circuit, bitstrings and slice count with a plan chosen for the levels the
+    executor runs steps at: seeded greedy candidates, each sliced by tree trimming, ranked by the flops
+    one call of 256 bitstrings executes (executed_cost), peak kept at the default plan's 2^14."""
+    cseed = 2001
+    circ = random_grid_circuit(4, 5, 12, cseed)
+    bits = random_bitstrings(20, 256, cseed + 500000)
+    om = np.zeros(20, np.uint8)
+    legs, _, open_edges = network_legs(20, [g.qubits for g in circ.gates], om)
+    n_out = 20 - len(open_edges)
+    no_slice = list(open_edges) + [legs[t][0] for t in range(len(legs) - n_out, len(legs))]
+    order, sliced, executed, peak = level_aware_plan(legs, 40, cseed + 700000, 6, no_slice, n_out, len(bits),
+                                                     max_peak=14)
+    flops = plan_cost(legs, order, sliced)[1]
+    return Workload("grid4x5_d12_s6_amp256_levelplan", circ, om, order, sliced, bits, peak, flops,
+                    {"plan": "seeded greedy candidates ranked by executed flops per call (level-aware)",
+                     "executed_flops": executed})
 
 
 @functools.lru_cache(maxsize=None)

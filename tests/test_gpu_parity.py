@@ -381,6 +381,18 @@ def test_memoised_invariants_give_the_same_bits(qx):
     c.close()
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_level_aware_plan_vs_statevector(qx, precision):
+    # the sliced workload's circuit under the plan chosen for executed flops per call
+    w = W.sliced_level_aware()
+    c = qx.Contractor(w.n_qubits, w.gates, w.open_mask, w.order, w.sliced, len(w.bitstrings), precision=precision)
+    got = c.contract(w.bitstrings)
+    ref = oracle.sv_amplitudes(w.n_qubits, w.gates, w.open_mask, w.bitstrings)
+    assert rel_l2(got, ref) <= TOL_C64
+    assert c.stats()["flops"] == w.meta["executed_flops"]
+    c.close()
+
+
 def test_stream_count_is_checked(qx):
     circ, om, order, sliced, bits = grid_case(3, 3, 6, 5, 1, 1, 2)
     c = _contractor(qx, circ, om, order, sliced, 2)

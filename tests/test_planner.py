@@ -1,0 +1,75 @@
+"""The level-aware plan choice (host logic, no GPU).
+
+executed_cost models what the batched executor runs per call: invariant steps
+once, per-slice steps once per slice, the rest per (slice, bitstring) pair.
+It is checked against the library's own compiled plan (the step sizes and
+levels qx_describe_plan lists, an independent computation in the C++ plan
+compiler), and the plan it selects is checked to compute the right amplitude
+with the einsum oracle against the state vector.
+"""
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import einsum as oe
+from qxgen import workloads as W
+from qxgen.plan import executed_cost, network_legs
+
+
+def _legs(w):
+    legs, _, open_edges = network_legs(w.n_qubits, [g.qubits for g in w.circuit.gates], w.open_mask)
+    return legs, w.n_qubits - len(open_edges)
+
+
+def _library_executed(qx, w, n_bits):
+    h = qx.qx_create(-1, precision=1)
+    try:
+        qx.qx_build_network(h, w.n_qubits, w.gates, w.open_mask)
+        qx.qx_set_plan(h, w.order, w.sliced)
+        total = 0
+        for line in qx.qx_describe_plan(h).splitlines():
+            f = line.split()
+            m = re.search(r" m=(\d+) k=(\d+) n=(\d+)", line)
+            if not m:
+                continue  # permutes move data only
+            flops = 8 * (1 << (int(m.group(1)) + int(m.group(2)) + int(m.group(3))))
+            mult = {"pair": w.n_slices * n_bits, "slice": w.n_slices, "shared": 1}[f[3]]
+            total += flops * mult
+        return total
+    finally:
+        qx.qx_destroy(h)
+
+
+@pytest.fixture(scope="module")
+def qx():
+    from paper_2110_09894_gb300 import build
+    build.build()
+    from paper_2110_09894_gb300 import qx as mod
+    return mod
+
+
+@pytest.mark.parametrize("name", ["sliced", "sliced_level_aware"])
+def test_executed_cost_matches_the_compiled_plan(qx, name):
+    w = getattr(W, name)()
+    legs, n_out = _legs(w)
+    assert executed_cost(legs, w.order, w.sliced, n_out, 256) == _library_executed(qx, w, 256)
+
+
+def test_level_aware_plan_executes_less_at_the_same_peak():
+    base, lvl = W.sliced(), W.sliced_level_aware()
+    legs, n_out = _legs(base)
+    e0 = executed_cost(legs, base.order, base.sliced, n_out, 256)
+    e1 = executed_cost(legs, lvl.order, lvl.sliced, n_out, 256)
+    assert e1 < 0.6 * e0
+    assert lvl.peak_rank <= base.peak_rank and len(lvl.sliced) == len(base.sliced)
+    assert e1 == lvl.meta["executed_flops"]
+
+
+def test_level_aware_plan_gives_the_state_vector_amplitude():
+    w = W.sliced_level_aware()
+    bits = w.bitstrings[:1]
+    got = oe.amplitudes(w.n_qubits, w.gates, w.open_mask, w.order, w.sliced, bits)
+    ref = oracle.sv_amplitudes(w.n_qubits, w.gates, w.open_mask, bits)
+    assert np.allclose(got, ref, rtol=1e-10, atol=1e-13)
