@@ -136,10 +136,10 @@ struct qx_ctx {
     int persist_grid = 0;
     bool pops_on_device = false;
 
-    // batched executor prologue in waves: the invariant steps by dependency level, one launch per
-    // level, one CTA per step (only when every invariant step is small)
+    // batched executor prologue: the invariant steps as chains that share no storage, one launch,
+    // one CTA per chain (only when every invariant step is small)
     bool wave_ok = false;
-    std::vector<POp> wave_ops;          // one per invariant op, grouped by level
+    std::vector<POp> wave_ops;          // one per invariant op, grouped by chain
     std::vector<int32_t> wave_idx;      // 0 .. n-1 (positions into wave_ops)
     std::vector<int32_t> wave_start;    // chain c: wave_ops[wave_start[c] .. wave_start[c + 1])
     std::vector<int> wave_of;           // per op: 0 if the prologue launch runs it, else -1
@@ -1328,9 +1328,10 @@ static void build_persistent_program(qx_ctx* h) {
 
 static double op_bytes(const qx_ctx* h, const Op& op, int64_t n_items, int64_t n_b = 1);
 
-// The invariant steps grouped by dependency level (the dependency lists include space reuse, so the
-// steps of one level never touch the same storage).  Used when every invariant step is small enough
-// for one CTA: at most 2^12 entries in and out, no tensor cores, natural layouts.
+// The invariant steps grouped into chains for the one prologue launch: steps joined by a dependency
+// (data, or space reuse where the invariant region reuses space) share a chain, which one CTA runs in
+// plan order.  Used when every invariant step is small enough for one CTA: at most 2^12 entries in
+// and out, no tensor cores, natural layouts.
 static void build_waves(qx_ctx* h) {
     h->wave_ok = false;
     h->wave_ops.clear();
@@ -1632,8 +1633,8 @@ struct Dag {
     std::vector<int> stream_of, last_on;  // per op: stream this batch (-1 none); per stream: last op
     std::vector<std::vector<int>> seen;   // seen[s][t]: latest op of stream t that stream s waited for
     std::vector<char> forked;
-    std::vector<int> wave_seen;          // per stream: highest prologue level waited for
-    bool waves_now = false;              // the prologue levels were launched in this batch
+    std::vector<int> wave_seen;          // per stream: 0 once it waited for the prologue launch
+    bool waves_now = false;              // the prologue launch was issued in this batch
     explicit Dag(qx_ctx* hh) : h(hh) {}
     int init() {
         on = h->n_streams > 1 && !h->profiling && !h->ops.empty();
@@ -1712,7 +1713,7 @@ struct Dag {
         return QX_OK;
     }
     int issue(int j, const ItemCtx& ic, int64_t n_items) {
-        if (h->wave_ok && h->wave_of[j] >= 0) return QX_OK;  // ran in a prologue level
+        if (h->wave_ok && h->wave_of[j] >= 0) return QX_OK;  // ran in the prologue launch
         if (!on) return run_op(h, h->ops[j], ic, n_items, h->stream);
         const int S = h->n_streams;
         int s = -1, wneed = -1;
