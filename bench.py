@@ -50,7 +50,7 @@ def parse():
     p.add_argument("--precision", default="3xtf32", choices=list(PRECISIONS),
                    help="contraction form (3xtf32 and bf16x3 meet the 1e-5 tolerance; fp16 is reported)")
     p.add_argument("--executor", default="auto", choices=["auto", "batched", "persistent"])
-    p.add_argument("--plan", default="default", choices=["default", "level-aware"],
+    p.add_argument("--plan", default="default", choices=["default", "level-aware", "checkpoint"],
                    help="sliced workload plan: seeded greedy + tree trimming, or the candidate that executes the "
                         "fewest flops per call with the per-slice level")
     p.add_argument("--no-slice-level", action="store_true",
@@ -63,6 +63,8 @@ def parse():
 def workload(name, plan="default"):
     if name == "sliced" and plan == "level-aware":
         return W.sliced_level_aware()
+    if name == "sliced" and plan == "checkpoint":
+        return W.sliced_checkpoint()
     return {"small": W.small, "sliced": W.sliced, "large": W.large}[name]()
 
 

@@ -1,0 +1,39 @@
+"""Write the stored plans of qxgen/plans/ (plans are inputs; the paper keeps them in files).
+
+    python -m qxgen.make_plans
+
+grid4x5_d12_s6_checkpoint.json: the 20-qubit sliced circuit (4x5 grid, depth
+12, six sliced bonds, 256 bitstrings) under the level-aware plan improved by
+local search (20000 seeded tree rotations), which about 25 s of host time
+finds; the workload loads it instead of searching again.
+"""
+import json
+import os
+
+from . import workloads as W
+from .plan import local_search_plan, network_legs
+
+HERE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "plans")
+
+
+def checkpoint_plan():
+    base = W.sliced_level_aware()
+    circ = base.circuit
+    legs, _, open_edges = network_legs(circ.n_qubits, [g.qubits for g in circ.gates], base.open_mask)
+    n_out = circ.n_qubits - len(open_edges)
+    order, executed, accepted = local_search_plan(legs, base.order, base.sliced, n_out, len(base.bitstrings),
+                                                  max_peak=14, iters=20000, seed=11)
+    return {"circuit_sha256": W.circuit_digest(circ), "order": [list(p) for p in order],
+            "sliced": [int(e) for e in base.sliced], "executed_flops": int(executed),
+            "n_bits": int(len(base.bitstrings)), "max_peak": 14,
+            "made_by": "level_aware_plan (40 trials per setting, seed 702001) + local_search_plan "
+                       "(20000 rotations, seed 11)"}
+
+
+if __name__ == "__main__":
+    os.makedirs(HERE, exist_ok=True)
+    d = checkpoint_plan()
+    path = os.path.join(HERE, "grid4x5_d12_s6_checkpoint.json")
+    with open(path, "w") as f:
+        json.dump(d, f)
+    print(path, d["executed_flops"])

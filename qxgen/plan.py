@@ -278,3 +278,58 @@ def level_aware_plan(legs, trials, seed, n_slice, open_edges, n_outputs, n_bits,
     if best is None:
         raise ValueError("no candidate plan within max_peak")
     return best[1], best[2], best[0][0], best[0][1]
+
+
+def _order_to_tree(n_leaves, order):
+    return {n_leaves + t: (a, b) for t, (a, b) in enumerate(order)}, n_leaves + len(order) - 1
+
+
+def _tree_to_order(n_leaves, children, root):
+    """SSA order of a contraction tree: children before parents, left subtree first."""
+    order, new_id = [], {}
+    stack = [(root, False)]
+    while stack:
+        node, done = stack.pop()
+        if node < n_leaves:
+            continue
+        a, b = children[node]
+        if done:
+            order.append((new_id.get(a, a), new_id.get(b, b)))
+            new_id[node] = n_leaves + len(order) - 1
+        else:
+            stack.append((node, True))
+            stack.append((b, False))
+            stack.append((a, False))
+    return order
+
+
+def local_search_plan(legs, order, sliced, n_outputs, n_bits, max_peak, iters, seed):
+    """Local optimisation of a plan (the paper's outlook cites local optimisation of contraction
+    plans): seeded random rotations of the contraction tree, ((A, B), C) -> ((A, C), B), each kept
+    when the plan executes fewer flops per call (executed_cost) with every intermediate within
+    max_peak legs; the sliced bonds stay as given.  Returns (order, executed flops, accepted moves).
+    """
+    n = len(legs)
+    children, root = _order_to_tree(n, order)
+    internal = sorted(children)
+    best = executed_cost(legs, order, sliced, n_outputs, n_bits)
+    rng = SplitMix64(seed)
+    accepted = 0
+    for _ in range(iters):
+        p = internal[rng.randint(len(internal))]
+        a, b = children[p]
+        x, y = (a, b) if rng.randint(2) == 0 else (b, a)  # x: the child to open, y: its sibling
+        if x < n:
+            continue
+        xa, xb = children[x]
+        keep, move = (xa, xb) if rng.randint(2) == 0 else (xb, xa)
+        old_p, old_x = children[p], children[x]
+        children[x], children[p] = (keep, y), (x, move)
+        cand = _tree_to_order(n, children, root)
+        ok = plan_cost(legs, cand, sliced)[0] <= max_peak
+        cost = executed_cost(legs, cand, sliced, n_outputs, n_bits) if ok else None
+        if cost is not None and cost < best:
+            best, accepted = cost, accepted + 1
+        else:
+            children[p], children[x] = old_p, old_x
+    return _tree_to_order(n, children, root), best, accepted

@@ -24,7 +24,8 @@ import numpy as np
 
 from .circuits import (Circuit, SplitMix64, gates_to_records, near_square_shape, random_bitstrings,
                        random_grid_circuit)
-from .plan import (greedy_order, level_aware_plan, network_legs, plan_cost, randomized_greedy, tree_trim_slices)
+from .plan import (executed_cost, greedy_order, level_aware_plan, network_legs, plan_cost, randomized_greedy,
+                   tree_trim_slices)
 
 
 @dataclass
@@ -118,6 +119,41 @@ def sliced_level_aware():
     flops = plan_cost(legs, order, sliced)[1]
     return Workload("grid4x5_d12_s6_amp256_levelplan", circ, om, order, sliced, bits, peak, flops,
                     {"plan": "seeded greedy candidates ranked by executed flops per call (level-aware)",
+                     "executed_flops": executed})
+
+
+def circuit_digest(circ: Circuit) -> str:
+    """sha256 of a circuit's gate records (identifies the circuit a stored plan was made for)."""
+    import hashlib
+    return hashlib.sha256(np.ascontiguousarray(gates_to_records(circ)).tobytes()).hexdigest()
+
+
+@functools.lru_cache(maxsize=None)
+def sliced_checkpoint():
+    """The sliced workload's circuit, bitstrings and slice count under the stored checkpoint plan
+    (qxgen/plans/grid4x5_d12_s6_checkpoint.json, written by qxgen.make_plans): the level-aware plan
+    improved by local search, so that each slice's environment is contracted once and every bitstring
+    adds little work."""
+    import json
+    import os
+    cseed = 2001
+    circ = random_grid_circuit(4, 5, 12, cseed)
+    bits = random_bitstrings(20, 256, cseed + 500000)
+    om = np.zeros(20, np.uint8)
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "plans", "grid4x5_d12_s6_checkpoint.json")
+    with open(path) as f:
+        d = json.load(f)
+    if d["circuit_sha256"] != circuit_digest(circ):
+        raise ValueError("stored plan was made for another circuit")
+    order = [tuple(p) for p in d["order"]]
+    sliced = list(d["sliced"])
+    legs, _, open_edges = network_legs(20, [g.qubits for g in circ.gates], om)
+    peak, flops = plan_cost(legs, order, sliced)
+    executed = executed_cost(legs, order, sliced, 20 - len(open_edges), len(bits))
+    if executed != d["executed_flops"] or peak > d["max_peak"]:
+        raise ValueError("stored plan does not match its recorded cost")
+    return Workload("grid4x5_d12_s6_amp256_checkpoint", circ, om, order, sliced, bits, peak, flops,
+                    {"plan": "level-aware plan + local search (stored; checkpoint per slice)",
                      "executed_flops": executed})
 
 

@@ -382,9 +382,10 @@ def test_memoised_invariants_give_the_same_bits(qx):
 
 
 @pytest.mark.parametrize("precision", [0, 1])
-def test_level_aware_plan_vs_statevector(qx, precision):
-    # the sliced workload's circuit under the plan chosen for executed flops per call
-    w = W.sliced_level_aware()
+@pytest.mark.parametrize("plan", ["sliced_level_aware", "sliced_checkpoint"])
+def test_level_aware_plan_vs_statevector(qx, precision, plan):
+    # the sliced workload's circuit under the plans chosen for executed flops per call
+    w = getattr(W, plan)()
     c = qx.Contractor(w.n_qubits, w.gates, w.open_mask, w.order, w.sliced, len(w.bitstrings), precision=precision)
     got = c.contract(w.bitstrings)
     ref = oracle.sv_amplitudes(w.n_qubits, w.gates, w.open_mask, w.bitstrings)

@@ -50,7 +50,7 @@ def qx():
     return mod
 
 
-@pytest.mark.parametrize("name", ["sliced", "sliced_level_aware"])
+@pytest.mark.parametrize("name", ["sliced", "sliced_level_aware", "sliced_checkpoint"])
 def test_executed_cost_matches_the_compiled_plan(qx, name):
     w = getattr(W, name)()
     legs, n_out = _legs(w)
@@ -72,4 +72,37 @@ def test_level_aware_plan_gives_the_state_vector_amplitude():
     bits = w.bitstrings[:1]
     got = oe.amplitudes(w.n_qubits, w.gates, w.open_mask, w.order, w.sliced, bits)
     ref = oracle.sv_amplitudes(w.n_qubits, w.gates, w.open_mask, bits)
+    assert np.allclose(got, ref, rtol=1e-10, atol=1e-13)
+
+
+def test_checkpoint_plan_executes_a_fraction_at_the_same_peak():
+    # the stored plan (level-aware choice improved by local search): each slice's environment is
+    # contracted once, every bitstring adds little
+    base, ck = W.sliced(), W.sliced_checkpoint()
+    legs, n_out = _legs(base)
+    assert ck.peak_rank <= base.peak_rank and list(ck.sliced) and len(ck.sliced) == len(base.sliced)
+    assert executed_cost(legs, ck.order, ck.sliced, n_out, 256) < 0.05 * executed_cost(legs, base.order, base.sliced,
+                                                                                        n_out, 256)
+
+
+def test_checkpoint_plan_gives_the_state_vector_amplitude():
+    w = W.sliced_checkpoint()
+    bits = w.bitstrings[:2]
+    got = oe.amplitudes(w.n_qubits, w.gates, w.open_mask, w.order, w.sliced, bits)
+    ref = oracle.sv_amplitudes(w.n_qubits, w.gates, w.open_mask, bits)
+    assert np.allclose(got, ref, rtol=1e-10, atol=1e-13)
+
+
+def test_tree_rotation_round_trip_and_local_search_only_improves():
+    from qxgen.plan import _order_to_tree, _tree_to_order, local_search_plan
+    w = W.small()
+    legs, n_out = _legs(w)
+    ch, root = _order_to_tree(len(legs), w.order)
+    order = _tree_to_order(len(legs), ch, root)
+    assert executed_cost(legs, order, w.sliced, n_out, 16) == executed_cost(legs, w.order, w.sliced, n_out, 16)
+    o2, cost, _ = local_search_plan(legs, w.order, w.sliced, n_out, 16, max_peak=w.peak_rank, iters=300, seed=3)
+    assert cost <= executed_cost(legs, w.order, w.sliced, n_out, 16)
+    assert cost == executed_cost(legs, o2, w.sliced, n_out, 16)
+    got = oe.amplitudes(w.n_qubits, w.gates, w.open_mask, o2, w.sliced, w.bitstrings[:3])
+    ref = oracle.sv_amplitudes(w.n_qubits, w.gates, w.open_mask, w.bitstrings[:3])
     assert np.allclose(got, ref, rtol=1e-10, atol=1e-13)
