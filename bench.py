@@ -3,7 +3,9 @@
 
 Default workload: the 20-qubit 4x5 grid circuit of depth 12 with 6 sliced
 bonds (64 slices, each contracted and summed in FP64) for 256 random
-bitstrings, complex64.  One step = one full contraction of that workload
+bitstrings, complex64, under the level-aware plan (the seeded greedy
+candidate that executes the fewest flops per call; `--plan greedy` gives the
+seeded greedy order).  One step = one full contraction of that workload
 (every slice for every bitstring) from device-resident bitstrings to
 device-resident complex128 amplitudes.
 
@@ -50,9 +52,10 @@ def parse():
     p.add_argument("--precision", default="3xtf32", choices=list(PRECISIONS),
                    help="contraction form (3xtf32 and bf16x3 meet the 1e-5 tolerance; fp16 is reported)")
     p.add_argument("--executor", default="auto", choices=["auto", "batched", "persistent"])
-    p.add_argument("--plan", default="default", choices=["default", "level-aware", "checkpoint"],
-                   help="sliced workload plan: seeded greedy + tree trimming, or the candidate that executes the "
-                        "fewest flops per call with the per-slice level")
+    p.add_argument("--plan", default="level-aware", choices=["level-aware", "greedy", "checkpoint"],
+                   help="plan of the sliced workload: the seeded greedy candidate that executes the fewest flops "
+                        "per call (default), the seeded greedy order of the workload definition, or the stored "
+                        "level-aware plan improved by local search")
     p.add_argument("--no-slice-level", action="store_true",
                    help="compute bitstring-independent intermediates per (slice, bitstring) pair, not per slice")
     p.add_argument("--streams", type=int, default=8,
@@ -60,7 +63,7 @@ def parse():
     return p.parse_args()
 
 
-def workload(name, plan="default"):
+def workload(name, plan="level-aware"):
     if name == "sliced" and plan == "level-aware":
         return W.sliced_level_aware()
     if name == "sliced" and plan == "checkpoint":
@@ -366,7 +369,8 @@ def sampling_bench(args):
             "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": total / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": args.precision,
             "data": "synthetic",
-            "config": {"workload": "sampling: grid 4x5 depth 12, 6 sliced bonds (64 slices), uniform candidates",
+            "config": {"workload": "sampling: grid 4x5 depth 12, 6 sliced bonds (64 slices, seeded greedy plan), "
+                                   "uniform candidates",
                        "samples_per_step": per, "candidates_per_contraction": s.batch,
                        "warmup_iterations": 2 * args.sample_batch},
             "candidates_per_sample": (s.iterations - it0) / (per * args.steps),
