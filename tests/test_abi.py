@@ -167,3 +167,19 @@ def test_memo_switch_on_host_only_handle(qx):
         qx.qx_set_memo(h, 2)
     assert e.value.code == qx.QX_EINVAL
     qx.qx_destroy(h)
+
+
+def test_workspace_grows_with_items_and_holds_the_slice_region(qx):
+    from qxgen import workloads as W
+    w = W.sliced()
+    sizes = {}
+    for off in (0, 1):
+        h = qx.qx_create(-1, precision=1, no_slice_level=off)
+        qx.qx_build_network(h, w.n_qubits, w.gates, w.open_mask)
+        qx.qx_set_plan(h, w.order, w.sliced)
+        sizes[off] = [qx.qx_workspace_size(h, 256, it) for it in (1, 64, 256, 4096)]
+        qx.qx_destroy(h)
+    for v in sizes.values():
+        assert all(a < b for a, b in zip(v, v[1:]))
+    # with the per-slice level, one pair needs its per-pair part and one slice's per-slice part
+    assert sizes[0][0] != sizes[1][0]

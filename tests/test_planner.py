@@ -106,3 +106,22 @@ def test_tree_rotation_round_trip_and_local_search_only_improves():
     got = oe.amplitudes(w.n_qubits, w.gates, w.open_mask, o2, w.sliced, w.bitstrings[:3])
     ref = oracle.sv_amplitudes(w.n_qubits, w.gates, w.open_mask, w.bitstrings[:3])
     assert np.allclose(got, ref, rtol=1e-10, atol=1e-13)
+
+
+def test_local_search_is_deterministic_for_a_seed():
+    from qxgen.plan import local_search_plan
+    w = W.small()
+    legs, n_out = _legs(w)
+    a = local_search_plan(legs, w.order, w.sliced, n_out, 16, max_peak=w.peak_rank, iters=200, seed=5)
+    b = local_search_plan(legs, w.order, w.sliced, n_out, 16, max_peak=w.peak_rank, iters=200, seed=5)
+    assert a == b
+
+
+def test_stored_plan_is_checked_against_its_circuit(monkeypatch):
+    W.sliced_checkpoint.cache_clear()
+    monkeypatch.setattr(W, "circuit_digest", lambda circ: "0" * 64)
+    with pytest.raises(ValueError):
+        W.sliced_checkpoint()
+    monkeypatch.undo()
+    W.sliced_checkpoint.cache_clear()
+    assert W.sliced_checkpoint().meta["executed_flops"] > 0
