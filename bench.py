@@ -1,13 +1,15 @@
 #!/usr/bin/env python
 """Throughput of sliced circuit tensor-network contraction on GB300.
 
-Default workload: the 20-qubit 4x5 grid circuit of depth 12 with 6 sliced
-bonds (64 slices, each contracted and summed in FP64) for 256 random
-bitstrings, complex64, under the level-aware plan (the seeded greedy
-candidate that executes the fewest flops per call; `--plan greedy` gives the
-seeded greedy order).  One step = one full contraction of that workload
-(every slice for every bitstring) from device-resident bitstrings to
-device-resident complex128 amplitudes.
+Default workload: the 36-qubit 6x6 grid circuit of depth 14 with qubits
+30..35 left open (64 amplitudes per contraction) and 10 sliced bonds (1024
+slices, each contracted and summed in FP64), in the 3xTF32 tensor-core form
+with the plain complex64 form and the split-BF16 and FP16-scaled forms timed
+beside it, under its stored local-search plan (`--plan greedy` gives the
+seeded greedy order).  `--workload sliced` runs the 20-qubit 4x5 grid circuit
+of depth 12 with 6 sliced bonds for 256 random bitstrings.  One step = one
+full contraction of the workload (every slice for every bitstring) from
+device-resident bitstrings to device-resident complex128 amplitudes.
 
 Prints one JSON line (rank 0).  `--impl reference` times the CPU oracle on a
 bounded sample of the same workload instead.  Under torchrun each rank
@@ -41,7 +43,7 @@ def parse():
     p.add_argument("--steps", type=int, default=10)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--workload", default="sliced", choices=["small", "sliced", "large", "batched", "serving", "sampling"])
+    p.add_argument("--workload", default="large", choices=["small", "sliced", "large", "batched", "serving", "sampling"])
     p.add_argument("--sample-batch", type=int, default=1024, help="candidates per contraction when sampling")
     p.add_argument("--samples-per-step", type=int, default=256)
     p.add_argument("--serve-seconds", type=float, default=20.0, help="arrival window of the serving run")
@@ -52,10 +54,15 @@ def parse():
     p.add_argument("--precision", default="3xtf32", choices=list(PRECISIONS),
                    help="contraction form (3xtf32 and bf16x3 meet the 1e-5 tolerance; fp16 is reported)")
     p.add_argument("--executor", default="auto", choices=["auto", "batched", "persistent"])
-    p.add_argument("--plan", default="level-aware", choices=["level-aware", "greedy", "checkpoint"],
-                   help="plan of the sliced workload: the seeded greedy candidate that executes the fewest flops "
-                        "per call (default), the seeded greedy order of the workload definition, or the stored "
+    p.add_argument("--plan", default="auto", choices=["auto", "level-aware", "greedy", "checkpoint", "local-search"],
+                   help="auto: the large workload's stored local-search plan, the sliced workload's level-aware "
+                        "plan (the seeded greedy candidate that executes the fewest flops per call); greedy: the "
+                        "seeded greedy order of the workload definition; checkpoint: the sliced workload's stored "
                         "level-aware plan improved by local search")
+    p.add_argument("--no-forms", action="store_true", help="skip timing the other tensor-core forms beside")
+    p.add_argument("--workspace-gb", type=float, default=-1.0,
+                   help="device workspace of each form (the same for all, so batches match); "
+                        "-1: 48 GB for the large workload, else what one call needs up to 60%% of free memory")
     p.add_argument("--no-slice-level", action="store_true",
                    help="compute bitstring-independent intermediates per (slice, bitstring) pair, not per slice")
     p.add_argument("--streams", type=int, default=8,
@@ -63,11 +70,13 @@ def parse():
     return p.parse_args()
 
 
-def workload(name, plan="level-aware"):
-    if name == "sliced" and plan == "level-aware":
+def workload(name, plan="auto"):
+    if name == "sliced" and plan in ("auto", "level-aware"):
         return W.sliced_level_aware()
     if name == "sliced" and plan == "checkpoint":
         return W.sliced_checkpoint()
+    if name == "large" and plan in ("auto", "local-search"):
+        return W.large_local_search()
     return {"small": W.small, "sliced": W.sliced, "large": W.large}[name]()
 
 
@@ -421,11 +430,18 @@ def main():
     t2 = time.perf_counter()
     qx.qx_destroy(hh)
     host_ms = {"build_network": 1e3 * (t1 - t0), "set_plan": 1e3 * (t2 - t1)}
+    ws_bytes = None
+    if args.workspace_gb > 0 or (args.workspace_gb < 0 and args.workload == "large"):
+        ws_bytes = int((args.workspace_gb if args.workspace_gb > 0 else 48.0) * 1e9)
+
+    def contractor(precision):
+        return qx.Contractor(w.n_qubits, w.gates, w.open_mask, w.order, w.sliced, n_bits, device=local, stream=stream,
+                             max_items=args.max_items, precision=precision, workspace_bytes=ws_bytes,
+                             executor={"auto": 0, "batched": 1, "persistent": 2}[args.executor],
+                             no_slice_level=int(args.no_slice_level))
+
     with torch.cuda.stream(stream):
-        c = qx.Contractor(w.n_qubits, w.gates, w.open_mask, w.order, w.sliced, n_bits, device=local, stream=stream,
-                          max_items=args.max_items, precision=PRECISIONS[args.precision][0],
-                          executor={"auto": 0, "batched": 1, "persistent": 2}[args.executor],
-                          no_slice_level=int(args.no_slice_level))
+        c = contractor(PRECISIONS[args.precision][0])
         qx.qx_set_streams(c.h, args.streams)
         d_bits = torch.from_numpy(bits).to(dev)
         d_amps = torch.empty((n_bits, 1 << w.n_open, 2), dtype=torch.float64, device=dev)
@@ -490,35 +506,54 @@ def main():
             "what": "invariant intermediates (no sliced bond, no output bit) kept from the first call"}
     qx.qx_set_memo(c.h, 0)
 
-    # the same steps in the plain complex64 form, for the forms' speed-up
-    vs_c64 = None
-    if args.precision != "c64":
+    def as_complex(t):
+        x = t.cpu().numpy()
+        return x[..., 0] + 1j * x[..., 1]
+
+    def time_form(precision):
+        """The same steps in another form (same workspace size, so the same batches): ms per step and
+        the device amplitudes of its last step."""
         with torch.cuda.stream(stream):
-            c64 = qx.Contractor(w.n_qubits, w.gates, w.open_mask, w.order, w.sliced, n_bits, device=local,
-                                stream=stream, max_items=args.max_items, precision=0,
-                                executor={"auto": 0, "batched": 1, "persistent": 2}[args.executor],
-                                no_slice_level=int(args.no_slice_level))
-            qx.qx_set_streams(c64.h, args.streams)
-            d64 = torch.empty_like(d_amps)
+            cf = contractor(precision)
+            qx.qx_set_streams(cf.h, args.streams)
+            out = torch.empty_like(d_amps)
         for _ in range(args.warmup):
-            c64.contract_device(d_bits, d64)
-        ev64 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+            cf.contract_device(d_bits, out)
+        evf = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
         barrier()
         for i in range(args.steps):
             with torch.cuda.stream(stream):
                 flush.fill_(i & 0xFF)
-            ev64[i][0].record(stream)
-            c64.contract_device(d_bits, d64)
-            ev64[i][1].record(stream)
+            evf[i][0].record(stream)
+            cf.contract_device(d_bits, out)
+            evf[i][1].record(stream)
         barrier()
-        ms64 = sum(a.elapsed_time(b) for a, b in ev64) / args.steps
-        a = d_amps.cpu().numpy()
-        b = d64.cpu().numpy()
-        a, b = a[..., 0] + 1j * a[..., 1], b[..., 0] + 1j * b[..., 1]
+        qx.qx_device_status(cf.h)
+        msf = sum(a.elapsed_time(b) for a, b in evf) / args.steps
+        cf.close()
+        del cf
+        return msf, as_complex(out)
+
+    # the same steps in the plain complex64 form, for the forms' speed-up
+    vs_c64 = None
+    a_main = as_complex(d_amps)
+    a64 = None
+    if args.precision != "c64":
+        ms64, a64 = time_form(0)
         vs_c64 = {"c64_ms_per_step": ms64, "speedup": ms64 / ms_per_step,
-                  "rel_diff_to_c64": float(np.linalg.norm(a - b) / np.linalg.norm(b))}
-        c64.close()
-        del d64
+                  "rel_diff_to_c64": float(np.linalg.norm(a_main - a64) / np.linalg.norm(a64))}
+    # the other tensor-core forms beside (the large workload runs all three against plain complex64)
+    forms = None
+    if args.workload == "large" and not args.no_forms:
+        forms = {}
+        for name in ("3xtf32", "bf16x3", "fp16"):
+            if name == args.precision:
+                continue
+            msf, af = time_form(PRECISIONS[name][0])
+            forms[name] = {"ms_per_step": msf, "value": amps_per_step / (msf / 1e3),
+                           "speedup_vs_c64": (vs_c64["c64_ms_per_step"] / msf) if vs_c64 else None,
+                           "rel_diff_to_c64": float(np.linalg.norm(af - a64) / np.linalg.norm(a64))
+                           if a64 is not None else None}
 
     # per-kernel event timing over K more steps on the same stream
     qx.qx_set_profiling(c.h, True)
@@ -591,6 +626,22 @@ def main():
                    "tflops": v["flops"] / max(v["ms"], 1e-12) / 1e9, "gbs": v["bytes"] / max(v["ms"], 1e-12) / 1e6}
                for k, v in prof.items()}
 
+    # parity of this launch configuration: the large workload's slices 0..31 against the complex128
+    # oracle's partial sum stored by tests/golden/make_large_golden.py (which calls only the oracle)
+    parity = None
+    if args.workload == "large":
+        gname = "large_ls_slices0_31.json" if w.name.endswith("_ls") else "large_slices0_31.json"
+        gpath = os.path.join(ROOT, "tests", "golden", gname)
+        if os.path.exists(gpath):
+            with open(gpath) as f:
+                g = json.load(f)
+            ref = np.array(g["re"]) + 1j * np.array(g["im"])
+            got = c.contract_slices(bits[:1], 0, 32)[0]
+            rms = float(np.sqrt(np.mean(np.abs(ref) ** 2)))
+            parity = {"vs": f"complex128 einsum oracle, slices 0..31 ({gname})",
+                      "rel_l2": float(np.linalg.norm(got - ref) / np.linalg.norm(ref)),
+                      "max_elem_over_rms": float(np.max(np.abs(got - ref)) / rms), "tolerance": 1e-5}
+
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
         ns = sample_slices(w)
@@ -620,7 +671,8 @@ def main():
                                           f"workspace {ws_gb:.1f} GB",
                                     "batches_per_step": c.stats()["batches"]}),
             "ms_per_step_median": float(np.median(step_ms)), "host_ms": host_ms,
-            "complex_tflops_executed": tflops, "memoised_invariants": memo, "vs_plain_c64": vs_c64, "flops_per_step_algorithmic": flops_alg,
+            "complex_tflops_executed": tflops, "memoised_invariants": memo, "vs_plain_c64": vs_c64,
+            "other_forms": forms, "parity": parity, "flops_per_step_algorithmic": flops_alg,
             "flops_per_step_executed": flops_exec,
             "latency_ms": {"p50": 1e3 * float(np.percentile(lat, 50)), "p99": 1e3 * float(np.percentile(lat, 99))},
             "roofline": roof, "kernels": kernels, "cpu_baseline": cpu,

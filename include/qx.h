@@ -90,7 +90,11 @@ typedef struct {
                                 GEMM reads and fuse the last permute into the
                                 dot, which only the batched launches do, so
                                 set 2 or 3 before qx_set_plan */
-    int64_t timeout_cycles;  /* bound on device spin-waits; 0 = default      */
+    int64_t timeout_cycles;  /* bound on each device spin-wait, in SM clock
+                                cycles; 0 = default (2e9).  An expired wait
+                                makes the call report QX_ETIMEOUT (through
+                                qx_device_status for the enqueue-only calls);
+                                a new value drops a captured graph */
     int32_t no_slice_level;  /* read by qx_set_plan.  0 (default): with
                                 executor 0 / 1, intermediates that depend on
                                 the slice but on no output bit are computed
@@ -250,6 +254,14 @@ int qx_device_status(qx_handle h);
  * device output (n_bits x 2^n_open x {re, im} doubles); work is enqueued on
  * the handle's stream, as for qx_contract_device, and gives the same
  * amplitudes.
+ *   - Each call first copies the network's tensors and the compiled programs
+ *     from host memory into the array and synchronises the handle's stream
+ *     (the array may hold another plan's data), so the call returns only once
+ *     earlier work on that stream is done; the contraction itself is then
+ *     enqueued.
+ *   - A bounded device wait that expires is reported by the next
+ *     qx_device_status on this handle (QX_ETIMEOUT), as for
+ *     qx_contract_device.
  *   - The first call on each device also looks up the array's device address
  *     (once per device); make that first call before any stream capture.
  *   - QX_ENOMEM when the network's tensors, n_bits bitstrings, their

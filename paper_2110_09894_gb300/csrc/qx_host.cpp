@@ -167,6 +167,7 @@ struct qx_ctx {
     bool graphs = true;
     bool memo = false;       // keep the invariant intermediates across calls (qx_set_memo)
     bool inv_ready = false;  // the bound workspace holds them
+    char* static_err = nullptr;  // error flag of the last static-scratch call, until qx_device_status reads it
     struct {
         const uint8_t* bits = nullptr;
         double* amps = nullptr;
@@ -1976,6 +1977,7 @@ int qx_set_options(qx_handle h, const qx_options* opt) {
     if (opt->executor < 0 || opt->executor > 3) return fail(h, QX_EINVAL, "executor %d out of range", opt->executor);
     if (opt->no_slice_level < 0 || opt->no_slice_level > 1) return fail(h, QX_EINVAL, "no_slice_level must be 0 or 1");
     h->opt = *opt;
+    drop_graph(h);  // a captured graph holds the old options' launch parameters (e.g. the wait limit)
     return QX_OK;
 }
 
@@ -2281,15 +2283,21 @@ int qx_profile_read(qx_handle h, int kind, double* ms, int64_t* launches, double
 
 int qx_device_status(qx_handle h) {
     if (!h) return QX_EINVAL;
-    if (!h->ws) return QX_OK;
-    int flag = 0;
+    if (!h->ws && !h->static_err) return QX_OK;
+    int flag = 0, sflag = 0;
     CUDA_TRY(h, cudaSetDevice(h->device));
-    CUDA_TRY(h, cudaMemcpyAsync(&flag, h->ws + h->off_err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    if (h->ws)
+        CUDA_TRY(h, cudaMemcpyAsync(&flag, h->ws + h->off_err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    // the flag of a static-scratch call lives in the shared array, not in the handle's workspace
+    if (h->static_err)
+        CUDA_TRY(h, cudaMemcpyAsync(&sflag, h->static_err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    h->static_err = nullptr;
     if (flag) {
         h->inv_ready = false;  // the kept intermediates may be incomplete
         return fail(h, flag, "a bounded device wait expired; the result is invalid");
     }
+    if (sflag) return fail(h, sflag, "a bounded device wait expired in a static-scratch call; the result is invalid");
     return QX_OK;
 }
 
@@ -2395,6 +2403,7 @@ int qx_internal_contract_in(qx_ctx* h, char* buf, int64_t buf_bytes, const uint8
     cudaError_t e = cudaSetDevice(h->device);
     if (e != cudaSuccess) rc = fail(h, QX_ECUDA, "cudaSetDevice: %s", cudaGetErrorString(e));
     if (rc == QX_OK) rc = contract_impl(h, d_bits, n_bits, 0, h->n_slices, d_amps);
+    if (rc == QX_OK) h->static_err = buf + h->off_err;  // read by the next qx_device_status
     restore();
     return rc;
 }

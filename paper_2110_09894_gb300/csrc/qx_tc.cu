@@ -190,6 +190,17 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, long lon
     }
     return true;
 }
+// Wait for asynchronous work this CTA issued itself (TMA copies into its shared memory, MMAs into
+// its TMEM) before it exits or frees TMEM.  Issued copies and MMAs always complete, so this wait is
+// neither cut short by the launch-wide error flag nor by the caller's limit, which may be tiny: only
+// by a fixed bound of about two seconds, so that even a stuck unit cannot keep the CTA forever.
+constexpr long long kIssuedWaitCycles = 1ll << 32;
+__device__ __forceinline__ void mbar_wait_issued(uint64_t* b, uint32_t parity) {
+    if (mbar_try(b, parity)) return;
+    const long long t0 = clock64();
+    while (!mbar_try(b, parity))
+        if (clock64() - t0 > kIssuedWaitCycles) return;
+}
 __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int c0, int c1, int c2, uint64_t* bar) {
     asm volatile(
         "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
@@ -357,11 +368,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 tma_load_3d(st + (F::NPA + p) * TILE, &maps.b[p], it * BK, n0, item / b_div, &full[s]);
             ++issued;
         }
-        if (*(volatile int*)&abort_flag) {
-            // let every copy already issued land before the CTA goes away
-            for (int it = (issued > F::STAGES ? issued - F::STAGES : 0); it < issued; ++it)
-                mbar_wait(&full[it % F::STAGES], (it / F::STAGES) & 1, limit, err);
-        }
+        // every copy issued lands before the CTA goes away (immediate unless a wait gave up: the
+        // consumers then did not see every stage)
+        for (int it = (issued > F::STAGES ? issued - F::STAGES : 0); it < issued; ++it)
+            mbar_wait_issued(&full[it % F::STAGES], (it / F::STAGES) & 1);
     } else if (warp == 1 && lane == 0) {
         // MMA issuer: stage `it` accumulates (fresh) into TMEM buffer it % NTB
         bool ok = true;
@@ -389,10 +399,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             tc_commit(&empty[s]);
             tc_commit(&tfull[b]);
         }
-        if (!ok) {
-            tc_commit(&drain);
-            mbar_wait(&drain, 0, limit, err);  // MMAs already issued finish before TMEM is freed
-        }
+        // the MMAs this thread issued finish before TMEM is freed, also when the epilogue warps gave
+        // up and stopped waiting for them
+        tc_commit(&drain);
+        mbar_wait_issued(&drain, 0);
     } else if (warp >= 2) {
         // epilogue: TMEM lanes 32 (warp % 4) .. + 31 are rows of the tile.  The
         // tensor cores' FP32 accumulation drifts toward zero over long sums, so
@@ -650,10 +660,9 @@ __global__ void __launch_bounds__(TC2_THREADS, 1)
                 lph ^= 1u;
             }
         }
-        if (*(volatile int*)&abort_flag) {  // let the copies in flight land before the CTA exits
-            for (int64_t g = (issued > NL ? issued - NL : 0); g < issued; ++g)
-                mbar_wait(&full[g % NL], (uint32_t)((g / NL) & 1), limit, err);
-        }
+        // the copies in flight land before the CTA exits (immediate unless a wait gave up)
+        for (int64_t g = (issued > NL ? issued - NL : 0); g < issued; ++g)
+            mbar_wait_issued(&full[g % NL], (uint32_t)((g / NL) & 1));
     } else if ((warp == 1 || warp == 14) && lane == 0) {
         // two issuers, even and odd stages: while one waits for its next stage (barrier waits, fence,
         // commits cost about as much as issuing the stage's MMAs), the other keeps the tensor pipe busy;
@@ -694,10 +703,10 @@ __global__ void __launch_bounds__(TC2_THREADS, 1)
             it += 2;
             while (it >= nk) it -= nk;
         }
-        if (!ok) {  // the MMAs this thread issued finish before TMEM is freed
-            tc_commit(&drain[who]);
-            mbar_wait(&drain[who], 0, limit, err);
-        }
+        // the MMAs this thread issued finish before TMEM is freed, also when the drain or converter
+        // warps gave up and stopped waiting for them
+        tc_commit(&drain[who]);
+        mbar_wait_issued(&drain[who], 0);
     } else if (warp >= 10 && warp <= 13) {
         // converters: landing slot -> MMA slot, ahead of the MMAs; warp w writes the A rows of TMEM
         // lanes 32 (w % 4)

@@ -120,9 +120,9 @@ EXEC_AUTO, EXEC_BATCHED, EXEC_PERSISTENT, EXEC_GROUP_MEMBER = 0, 1, 2, 3
 
 
 def qx_create(device=0, stream=0, precision=QX_PREC_C64, max_items=0, gemm_min_bits=0, executor=EXEC_AUTO,
-              no_slice_level=0):
+              no_slice_level=0, timeout_cycles=0):
     h = ctypes.c_void_p()
-    opt = Options(precision, max_items, gemm_min_bits, executor, 0, int(no_slice_level), 0)
+    opt = Options(precision, max_items, gemm_min_bits, executor, int(timeout_cycles), int(no_slice_level), 0)
     rc = load().qx_create(ctypes.byref(h), int(device), ctypes.c_void_p(int(stream)), ctypes.byref(opt))
     if rc != QX_OK:
         raise QXError(rc, "qx_create failed (device, options)")
@@ -137,8 +137,9 @@ def qx_last_error(h):
     return load().qx_last_error(h).decode()
 
 
-def qx_set_options(h, precision=QX_PREC_C64, max_items=0, gemm_min_bits=0, executor=EXEC_AUTO, no_slice_level=0):
-    opt = Options(precision, max_items, gemm_min_bits, executor, 0, int(no_slice_level), 0)
+def qx_set_options(h, precision=QX_PREC_C64, max_items=0, gemm_min_bits=0, executor=EXEC_AUTO, no_slice_level=0,
+                   timeout_cycles=0):
+    opt = Options(precision, max_items, gemm_min_bits, executor, int(timeout_cycles), int(no_slice_level), 0)
     _check(h, load().qx_set_options(h, ctypes.byref(opt)))
 
 

@@ -157,6 +157,43 @@ def sliced_checkpoint():
                      "executed_flops": executed})
 
 
+def _load_stored_plan(fname, circ, open_mask, n_bits):
+    """A plan stored in qxgen/plans/ (written by qxgen.make_plans), checked against the circuit it was
+    made for and its recorded executed cost; returns (order, sliced, peak rank, flops per slice,
+    executed flops per call, the record)."""
+    import json
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "plans", fname)
+    with open(path) as f:
+        d = json.load(f)
+    if d["circuit_sha256"] != circuit_digest(circ):
+        raise ValueError("stored plan was made for another circuit")
+    order = [tuple(p) for p in d["order"]]
+    sliced = list(d["sliced"])
+    n = circ.n_qubits
+    legs, _, open_edges = network_legs(n, [g.qubits for g in circ.gates], open_mask)
+    peak, flops = plan_cost(legs, order, sliced)
+    executed = executed_cost(legs, order, sliced, n - len(open_edges), n_bits)
+    if executed != d["executed_flops"] or peak > d["max_peak"]:
+        raise ValueError("stored plan does not match its recorded cost")
+    return order, sliced, peak, flops, executed, d
+
+
+@functools.lru_cache(maxsize=None)
+def large_local_search():
+    """The large workload (6x6 depth 14, qubits 30..35 open, the same 10 sliced bonds and bitstring)
+    under its seeded plan improved by local search (qxgen/plans/grid6x6_d14_s10_open6_ls.json):
+    the same 1024 slices, far fewer flops per slice, peak still <= 2^28 entries."""
+    base = large()
+    order, sliced, peak, flops, executed, d = _load_stored_plan("grid6x6_d14_s10_open6_ls.json", base.circuit,
+                                                                base.open_mask, len(base.bitstrings))
+    if sliced != list(base.sliced):
+        raise ValueError("stored plan slices other bonds than the workload")
+    return Workload("grid6x6_d14_s10_open6_ls", base.circuit, base.open_mask, order, sliced, base.bitstrings, peak,
+                    flops, {"plan": "seeded greedy + tree trimming, then local search (stored)",
+                            "executed_flops": executed, "made_by": d["made_by"]})
+
+
 @functools.lru_cache(maxsize=None)
 def large():
     cseed = 3001

@@ -1,4 +1,7 @@
 """Shared helpers for the tests: tolerances and small workload builders."""
+import json
+import os
+
 import numpy as np
 
 from qxgen import circuits as C
@@ -11,10 +14,41 @@ from qxgen.workloads import make_plan
 TOL_C64 = 1e-5
 
 
+# Element-wise: the largest error of any single amplitude, relative to the rms magnitude of the
+# oracle's amplitudes in the same request (a relative error per amplitude is unstable for random-
+# circuit amplitudes near zero, Porter-Thomas); the same 1e-5 acceptance level.  An error confined
+# to a few amplitudes, which the l2 norm over the request could hide, fails this bound.
+TOL_ELEM = 1e-5
+
+
 def rel_l2(a, ref):
     a = np.asarray(a).reshape(-1)
     ref = np.asarray(ref).reshape(-1)
     return float(np.linalg.norm(a - ref) / max(np.linalg.norm(ref), 1e-300))
+
+
+def max_elem(a, ref):
+    """max_i |a_i - ref_i| / rms_i |ref_i|."""
+    a = np.asarray(a).reshape(-1)
+    ref = np.asarray(ref).reshape(-1)
+    rms = np.sqrt(np.mean(np.abs(ref) ** 2)) if ref.size else 0.0
+    return float(np.max(np.abs(a - ref)) / max(rms, 1e-300)) if ref.size else 0.0
+
+
+def _log(kind, l2, el):
+    path = os.environ.get("QX_PARITY_LOG")
+    if path:
+        with open(path, "a") as f:
+            f.write(json.dumps({"test": os.environ.get("PYTEST_CURRENT_TEST", "").split(" ")[0], "kind": kind,
+                                "rel_l2": l2, "max_elem": el}) + "\n")
+
+
+def assert_parity(a, ref, tol=TOL_C64, tol_elem=TOL_ELEM, what=""):
+    """Both parity bounds of a request: relative l2 over its amplitudes and the element-wise bound."""
+    l2, el = rel_l2(a, ref), max_elem(a, ref)
+    _log(what, l2, el)
+    assert l2 <= tol, f"{what} relative l2 error {l2:.3e} > {tol:.0e}"
+    assert el <= tol_elem, f"{what} largest element error {el:.3e} x rms > {tol_elem:.0e}"
 
 
 def grid_case(rows, cols, depth, seed, n_open=0, n_slice=0, n_bits=8, trials=0):
@@ -26,3 +60,25 @@ def grid_case(rows, cols, depth, seed, n_open=0, n_slice=0, n_bits=8, trials=0):
     order, sliced, peak, flops = make_plan(circ, om, n_slice, seed + 700000, trials)
     bits = C.random_bitstrings(n, n_bits, seed + 500000)
     return circ, om, order, sliced, bits
+
+
+def cancelling_slices_case():
+    """A 2-qubit network whose four slice results are X, 1, -X, -1 (X = 2^60, slice order), all exact
+    in FP32: their exact sum is 0, a plain running FP64 sum in slice order gives -1 (X + 1 rounds to X),
+    a compensated one gives 0.  Gates need not be unitary for the method (explicit matrices).
+
+    Bonds: 0, 1 inputs; 2 (qubit 0) and 3 (qubit 1) between the two layers of gates (sliced);
+    4, 5 the final wires.  Slice s sets bond 2 to bit 0 of s and bond 3 to bit 1.
+    """
+    from qxgen.plan import greedy_order, network_legs
+    X = 2.0 ** 60
+    circ = C.Circuit(2)
+    circ.append([0], [[X, 0], [1, 0]])
+    circ.append([1], [[1, 0], [-1, 0]])
+    circ.append([0], [[1, 1], [0, 0]])
+    circ.append([1], [[1, 1], [0, 0]])
+    om = np.zeros(2, np.uint8)
+    legs, _, _ = network_legs(2, [g.qubits for g in circ.gates], om)
+    order = greedy_order(legs)
+    bits = np.zeros((1, 2), np.uint8)
+    return circ, om, order, [2, 3], bits

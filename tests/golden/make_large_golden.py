@@ -1,12 +1,15 @@
 """Write the oracle's partial sum over slices 0..31 of the 6x6 depth-14 workload.
 
 Calls only the oracle (complex128 plan einsum, compensated slice sum) on the
-seeded workload from qxgen.workloads.large(); about 30 s of CPU per slice
-group of 8 on a few cores.  Output: large_slices0_31.json next to this file,
-with a digest of the plan so a changed planner is detected instead of
-silently compared against stale values.
+seeded workload: `greedy` follows qxgen.workloads.large() (its seeded greedy
+order; several minutes of CPU) into large_slices0_31.json, `ls` follows
+qxgen.workloads.large_local_search() (the stored local-search order of the
+same sliced bonds; about a minute) into large_ls_slices0_31.json.  Each file
+carries a digest of its plan so a changed planner is detected instead of
+silently compared against stale values.  The two orders contract the same 32
+sub-networks (Eq. 2), so the two files agree to complex128 rounding.
 
-    python tests/golden/make_large_golden.py
+    python tests/golden/make_large_golden.py [greedy] [ls]
 """
 import hashlib
 import json
@@ -31,8 +34,8 @@ def plan_digest(w):
     return h.hexdigest()
 
 
-def main(n_slices=32):
-    w = workloads.large()
+def main(which="greedy", n_slices=32):
+    w = workloads.large() if which == "greedy" else workloads.large_local_search()
     amps = einsum.amplitudes(w.n_qubits, w.gates, w.open_mask, w.order, w.sliced, w.bitstrings,
                              slices=range(n_slices))
     out = {
@@ -44,9 +47,11 @@ def main(n_slices=32):
         "im": amps[0].imag.tolist(),
         "source": "oracle.einsum.amplitudes (complex128, Neumaier slice sum)",
     }
-    with open(os.path.join(HERE, f"large_slices0_{n_slices - 1}.json"), "w") as f:
+    name = f"large_slices0_{n_slices - 1}.json" if which == "greedy" else f"large_ls_slices0_{n_slices - 1}.json"
+    with open(os.path.join(HERE, name), "w") as f:
         json.dump(out, f, indent=1)
 
 
 if __name__ == "__main__":
-    main()
+    for which in sys.argv[1:] or ["greedy", "ls"]:
+        main(which)

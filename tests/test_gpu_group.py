@@ -9,7 +9,7 @@ import pytest
 import oracle
 from qxgen import workloads as W
 
-from ._util import TOL_C64, rel_l2
+from ._util import assert_parity
 
 pytestmark = pytest.mark.gpu
 
@@ -55,7 +55,7 @@ def test_group_matches_statevectors(qx):
     got = g.amplitudes()
     for w, a in zip(ws, got):
         ref = oracle.sv_amplitudes(w.n_qubits, w.gates, w.open_mask, w.bitstrings)
-        assert rel_l2(a, ref) <= TOL_C64, w.name
+        assert_parity(a, ref, what=w.name)
 
 
 def test_group_graph_replay_reproduces_the_run(qx):
@@ -103,4 +103,4 @@ def test_autotuner_picks_and_caches(qx, tmp_path, monkeypatch):
     torch.cuda.synchronize()
     for w, a in zip(ws, g.amplitudes()):
         ref = oracle.sv_amplitudes(w.n_qubits, w.gates, w.open_mask, w.bitstrings)
-        assert rel_l2(a, ref) <= TOL_C64
+        assert_parity(a, ref)

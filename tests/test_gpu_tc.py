@@ -14,7 +14,7 @@ import pytest
 import oracle
 from qxgen import workloads as W
 
-from ._util import TOL_C64, grid_case, rel_l2
+from ._util import assert_parity, grid_case, rel_l2
 
 pytestmark = pytest.mark.gpu
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -44,7 +44,7 @@ def test_forms_on_sliced_workload(qx, precision):
     c = qx.Contractor(w.n_qubits, w.gates, w.open_mask, w.order, w.sliced, len(w.bitstrings), precision=precision)
     got, n_tc = _tc_launches(qx, c, lambda: c.contract(w.bitstrings))
     assert n_tc > 0, "no step ran on the tensor cores"
-    assert rel_l2(got, ref) <= TOL_C64
+    assert_parity(got, ref)
     c.close()
 
 
@@ -56,19 +56,21 @@ def test_forms_with_open_legs_and_ragged_batches(qx, precision):
     ref = oracle.sv_amplitudes(circ.n_qubits, recs, om, bits)
     c = qx.Contractor(circ.n_qubits, recs, om, order, sliced, len(bits), precision=precision, max_items=7)
     got = c.contract(bits)
-    assert rel_l2(got, ref) <= TOL_C64
+    assert_parity(got, ref)
 
 
+@pytest.mark.parametrize("plan", ["greedy", "local-search"])
 @pytest.mark.parametrize("precision", FORMS)
-def test_forms_on_large_workload_32_slices(qx, precision):
-    w = W.large()
-    with open(os.path.join(HERE, "golden", "large_slices0_31.json")) as f:
+def test_forms_on_large_workload_32_slices(qx, precision, plan):
+    w = W.large() if plan == "greedy" else W.large_local_search()
+    name = "large_slices0_31.json" if plan == "greedy" else "large_ls_slices0_31.json"
+    with open(os.path.join(HERE, "golden", name)) as f:
         g = json.load(f)
     ref = np.array(g["re"]) + 1j * np.array(g["im"])
     c = qx.Contractor(w.n_qubits, w.gates, w.open_mask, w.order, w.sliced, 1, precision=precision)
     got, n_tc = _tc_launches(qx, c, lambda: c.contract_slices(w.bitstrings, 0, 32)[0])
     assert n_tc > 0
-    assert rel_l2(got, ref) <= TOL_C64
+    assert_parity(got, ref)
 
 
 def test_fp16_scaled_form_runs_on_tensor_cores_and_reports_its_error(qx, capsys):

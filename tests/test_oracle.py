@@ -266,3 +266,22 @@ def test_porter_thomas_second_moment_of_deep_random_circuits():
         moments[depth] = float((p ** 2).mean())
     assert abs(moments[16] - 2.0) < 0.1
     assert moments[2] > 3.0
+
+
+def test_cancelling_slices_need_the_compensated_sum():
+    """The case that pins the device's compensated slice sum: per-slice values X, 1, -X, -1 in slice
+    order (checked through the oracle one slice at a time); a plain FP64 running sum gives -1, the
+    oracle's compensated sum and math.fsum give the exact 0."""
+    from ._util import cancelling_slices_case
+    circ, om, order, sliced, bits = cancelling_slices_case()
+    recs = C.gates_to_records(circ)
+    per = [oe.amplitudes(2, recs, om, order, sliced, bits, slices=[s])[0, 0] for s in range(4)]
+    X = 2.0 ** 60
+    assert [p.real for p in per] == [X, 1.0, -X, -1.0] and all(p.imag == 0 for p in per)
+    naive = 0.0
+    for p in per:
+        naive += p.real
+    assert naive == -1.0
+    assert math.fsum(p.real for p in per) == 0.0
+    assert oe.amplitudes(2, recs, om, order, sliced, bits)[0, 0] == 0.0
+    assert oracle.sv_amplitudes(2, recs, om, bits)[0, 0] == 0.0

@@ -125,3 +125,20 @@ def test_stored_plan_is_checked_against_its_circuit(monkeypatch):
     monkeypatch.undo()
     W.sliced_checkpoint.cache_clear()
     assert W.sliced_checkpoint().meta["executed_flops"] > 0
+
+
+def test_large_local_search_plan_keeps_the_slices_and_its_golden_agrees():
+    """The stored local-search plan of the large workload slices the same bonds and stays within the
+    2^28 peak; the oracle's 32-slice partial sums under the two orders (two golden files written by
+    tests/golden/make_large_golden.py) agree to complex128 rounding: the order changes only the
+    rounding (Sec. III-A), slicing fixes which sub-networks are summed (Eq. 2)."""
+    import json
+    import os
+    w0, w1 = W.large(), W.large_local_search()
+    assert w1.sliced == list(w0.sliced) and w1.peak_rank <= 28
+    assert w1.meta["executed_flops"] < executed_cost(*_legs(w0)[:1], w0.order, w0.sliced, _legs(w0)[1], 1) / 10
+    here = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+    g = [json.load(open(os.path.join(here, n))) for n in ("large_slices0_31.json", "large_ls_slices0_31.json")]
+    a, b = (np.array(x["re"]) + 1j * np.array(x["im"]) for x in g)
+    assert g[0]["bitstring"] == g[1]["bitstring"]
+    assert np.linalg.norm(a - b) / np.linalg.norm(a) < 1e-12
