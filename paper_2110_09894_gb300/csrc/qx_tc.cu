@@ -415,7 +415,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         bool ok = true;
         for (int it = 0; it < nk; ++it) {
             const int b = it % NTB, u = it / NTB;
-            if (!mbar_wait(&tfull[b], u & 1, limit, err) || *(volatile int*)&abort_flag) {
+            // one decision per warp: the TMEM loads below are warp-wide (.sync.aligned)
+            const bool go = mbar_wait(&tfull[b], u & 1, limit, err) && !*(volatile int*)&abort_flag;
+            if (!__all_sync(0xffffffffu, go)) {
                 atomicExch(&abort_flag, 1);
                 ok = false;
                 break;
@@ -716,8 +718,10 @@ __global__ void __launch_bounds__(TC2_THREADS, 1)
         int64_t t = 0, prev_key = -1;
         bool with_a = true;
         for (int64_t g = 0; g < total; ++g) {
-            if (!mbar_wait(&full[l], lph, limit, err) || !mbar_wait(&mfree[m], mph ^ 1u, limit, err) ||
-                *(volatile int*)&abort_flag) {
+            // one decision per warp: the TMEM stores of the conversion are warp-wide (.sync.aligned)
+            const bool go = mbar_wait(&full[l], lph, limit, err) && mbar_wait(&mfree[m], mph ^ 1u, limit, err) &&
+                            !*(volatile int*)&abort_flag;
+            if (!__all_sync(0xffffffffu, go)) {
                 atomicExch(&abort_flag, 1);
                 break;
             }
@@ -734,7 +738,7 @@ __global__ void __launch_bounds__(TC2_THREADS, 1)
                     bool ok = true;
                     for (int64_t p = g - 1; p >= 0 && p >= g - 2 && ok; --p)
                         ok = mbar_wait(&tfull[p & 1], (uint32_t)((p >> 1) & 1), limit, err);
-                    if (!ok) {
+                    if (!__all_sync(0xffffffffu, ok)) {
                         atomicExch(&abort_flag, 1);
                         break;
                     }
@@ -774,7 +778,10 @@ __global__ void __launch_bounds__(TC2_THREADS, 1)
             bool ok = true;
             for (int it = 0; it < nk; ++it, ++g) {
                 const int b = (int)(g & 1);
-                if (!mbar_wait(&tfull[b], (uint32_t)((g >> 1) & 1), limit, err) || *(volatile int*)&abort_flag) {
+                // one decision per warp: the TMEM loads below are warp-wide (.sync.aligned)
+                const bool go = mbar_wait(&tfull[b], (uint32_t)((g >> 1) & 1), limit, err) &&
+                                !*(volatile int*)&abort_flag;
+                if (!__all_sync(0xffffffffu, go)) {
                     atomicExch(&abort_flag, 1);
                     ok = false;
                     break;
