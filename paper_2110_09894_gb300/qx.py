@@ -298,14 +298,15 @@ class Contractor:
 
     def __init__(self, n_qubits, gate_records, open_mask, order, sliced, max_bits, device=0,
                  precision=QX_PREC_C64, max_items=0, workspace_bytes=None, stream=None, executor=EXEC_AUTO,
-                 no_slice_level=0):
+                 no_slice_level=0, gemm_min_bits=0, timeout_cycles=0):
         import torch
         self.torch = torch
         self.device = torch.device("cuda", device)
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         self.n_qubits = int(n_qubits)
         self.n_open = 0 if open_mask is None else int(np.sum(np.asarray(open_mask) != 0))
-        self.h = qx_create(device, self.stream.cuda_stream, precision, max_items, 0, executor, no_slice_level)
+        self.h = qx_create(device, self.stream.cuda_stream, precision, max_items, gemm_min_bits, executor,
+                           no_slice_level, timeout_cycles)
         qx_build_network(self.h, n_qubits, gate_records, open_mask)
         self.peak_entries = qx_set_plan(self.h, order, sliced)
         self.n_slices = 1 << len(np.asarray(sliced).reshape(-1))

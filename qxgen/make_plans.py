@@ -1,6 +1,6 @@
 """Write the stored plans of qxgen/plans/ (plans are inputs; the paper keeps them in files).
 
-    python -m qxgen.make_plans [checkpoint] [large]
+    python -m qxgen.make_plans [checkpoint] [large] [batched]
 
 grid4x5_d12_s6_checkpoint.json: the 20-qubit sliced circuit (4x5 grid, depth
 12, six sliced bonds, 256 bitstrings) under the level-aware plan improved by
@@ -9,8 +9,13 @@ finds; the workload loads it instead of searching again.
 
 grid6x6_d14_s10_open6_ls.json: the 36-qubit large workload (6x6 grid, depth
 14, qubits 30..35 open, 10 sliced bonds) under its seeded plan improved by
-local search (150000 rotations, about 6 minutes of host time): 2.4e13 instead
-of 1.0e15 executed flops per call, the same sliced bonds, peak 2^22 entries.
+local search, 150000 rotations on executed flops then 100000 on the time
+estimate (about 10 minutes of host time): 3.6e13 instead of 1.0e15 executed
+flops per call, the same sliced bonds, peak 2^22 entries.
+
+batched_uneven.json: the 256 circuits of the batched workload, each under
+its level-aware plan improved by local search on the time estimate (about
+half an hour of host time on 7 processes).
 """
 import json
 import os
@@ -35,20 +40,59 @@ def checkpoint_plan():
                        "(20000 rotations, seed 11)"}
 
 
-def large_plan(iters=150000, seed=13):
-    """The large workload's seeded plan improved by local search; the sliced bonds stay those of the
-    seeded plan, so its slices are the same sub-networks (Eq. 2) in another contraction order."""
+def large_plan(iters=150000, seed=13, iters_t=100000, seed_t=22):
+    """The large workload's seeded plan improved by local search, first on executed flops, then on the
+    time estimate (executed_time: memory traffic counts too); the sliced bonds stay those of the seeded
+    plan, so its slices are the same sub-networks (Eq. 2) in another contraction order."""
+    from .plan import executed_cost, executed_time
     base = W.large()
     circ = base.circuit
     legs, _, open_edges = network_legs(circ.n_qubits, [g.qubits for g in circ.gates], base.open_mask)
     n_out = circ.n_qubits - len(open_edges)
-    order, executed, accepted = local_search_plan(legs, base.order, base.sliced, n_out, len(base.bitstrings),
-                                                  max_peak=28, iters=iters, seed=seed)
+    nb = len(base.bitstrings)
+    order, _, _ = local_search_plan(legs, base.order, base.sliced, n_out, nb, max_peak=28, iters=iters, seed=seed)
+    order, t, _ = local_search_plan(legs, order, base.sliced, n_out, nb, max_peak=28, iters=iters_t, seed=seed_t,
+                                    objective="time")
     return {"circuit_sha256": W.circuit_digest(circ), "order": [list(p) for p in order],
-            "sliced": [int(e) for e in base.sliced], "executed_flops": int(executed),
-            "n_bits": int(len(base.bitstrings)), "max_peak": 28,
+            "sliced": [int(e) for e in base.sliced], "executed_flops": int(executed_cost(legs, order, base.sliced,
+                                                                                          n_out, nb)),
+            "estimated_s": executed_time(legs, order, base.sliced, n_out, nb),
+            "n_bits": int(nb), "max_peak": 28,
             "made_by": f"randomized_greedy (64 trials per setting, seed 703001) + tree trimming + "
-                       f"local_search_plan ({iters} rotations, seed {seed})"}
+                       f"local_search_plan ({iters} rotations, seed {seed}, executed flops) + "
+                       f"local_search_plan ({iters_t} rotations, seed {seed_t}, time estimate)"}
+
+
+BATCHED_MAX_PEAK = 28
+
+
+def batched_plan(j, trials=20, iters=20000):
+    """Circuit j of the batched uneven workload: its drawn number of sliced bonds S, the seeded greedy
+    candidates ranked by executed flops (level_aware_plan), then local search on the time estimate
+    (executed_time), every intermediate within 2^28 entries."""
+    from .plan import executed_cost, executed_time, level_aware_plan, plan_cost
+    n, depth, S, nb = W.batched_specs()[j]
+    w = W.batched_circuit_greedy(j)
+    circ = w.circuit
+    legs, _, open_edges = network_legs(n, [g.qubits for g in circ.gates], w.open_mask)
+    n_out = n - len(open_edges)
+    no_slice = list(open_edges) + [legs[t][0] for t in range(len(legs) - n_out, len(legs))]
+    order, sliced, _, _ = level_aware_plan(legs, trials, 4000 + j + 700000, S, no_slice, n_out, nb,
+                                           max_peak=BATCHED_MAX_PEAK)
+    order, t, _ = local_search_plan(legs, order, sliced, n_out, nb, BATCHED_MAX_PEAK, iters, j, objective="time")
+    return {"j": j, "circuit_sha256": W.circuit_digest(circ), "order": [list(p) for p in order],
+            "sliced": [int(e) for e in sliced], "n_bits": nb, "max_peak": BATCHED_MAX_PEAK,
+            "peak": plan_cost(legs, order, sliced)[0], "executed_flops": int(executed_cost(legs, order, sliced, n_out, nb)),
+            "estimated_s": t}
+
+
+def batched_plans(workers=7):
+    import multiprocessing as mp
+    with mp.get_context("spawn").Pool(workers) as pool:
+        plans = pool.map(batched_plan, range(256), chunksize=1)
+    return {"made_by": "per circuit: level_aware_plan (20 trials per setting, seed 704000 + j) + local_search_plan "
+                       "(20000 rotations, seed j, objective time), max peak 2^28",
+            "plans": plans}
 
 
 def _write(name, d):
@@ -66,3 +110,9 @@ if __name__ == "__main__":
         _write("grid4x5_d12_s6_checkpoint.json", checkpoint_plan())
     if "large" in which:
         _write("grid6x6_d14_s10_open6_ls.json", large_plan())
+    if "batched" in which:
+        d = batched_plans()
+        path = os.path.join(HERE, "batched_uneven.json")
+        with open(path, "w") as f:
+            json.dump(d, f)
+        print(path, sum(p["estimated_s"] for p in d["plans"]))

@@ -248,6 +248,68 @@ def executed_cost(legs, order, sliced, n_outputs, n_bits):
     return total
 
 
+# Rates of one GB300 for executed_time, in the units of the 8 M K N convention and bytes, from the
+# kernels' measured throughput on the 36-qubit sliced workload: tensor-core products in 3xTF32 (about
+# 170 complex TFLOP/s), the SIMT complex64 GEMM, the gather kernels' FP32 arithmetic, and the HBM
+# bandwidth the memory-bound kernels reach (about 4.7 TB/s); plus a fixed cost per launch.
+GB300_RATES = {"tc": 170e12, "gemm": 35e12, "gather": 20e12, "hbm": 4.7e12, "launch": 4e-6}
+
+
+def step_kind(m, k, n, small_entries, tensor_cores=True):
+    """The kernel family the library's plan compiler picks for a step with m, k, n free / shared /
+    free bits (m >= n): 'gather' when one operand has at most 2^10 entries, k <= 5 and that operand
+    has at most 5 free bits (and the step is not a GEMM with all three >= 5), 'tc' for the tensor-core
+    shapes of the 3xTF32 form, else 'gemm'."""
+    big_gemm = k >= 5 and m >= 5 and n >= 5
+    if small_entries <= 10 and k <= 5 and n <= 5 and not big_gemm:
+        return "gather"
+    if tensor_cores and ((m >= 7 and n >= 5 and k >= 4 and (m <= 8 or n <= 8)) or (m >= 7 and n >= 6 and k >= 5)):
+        return "tc"
+    return "gemm"
+
+
+def executed_time(legs, order, sliced, n_outputs, n_bits, rates=GB300_RATES, tensor_cores=True):
+    """Estimated seconds of one contraction call on one GPU, steps at their dependence level.
+
+    Each step is one launch over its items (1, the slices, or the (slice, bitstring) pairs); it takes
+    the longer of its flops at its kernel family's rate (step_kind) and its bytes at the HBM rate,
+    8 (|A| + |B| + |C|) per item with an operand of a lower level (shared by the items) read once,
+    plus the launch cost.  A roofline estimate: it ignores permutes and overlap between launches, and
+    serves to rank plans, where executed flops alone favour huge tensors contracted over few bonds
+    (cheap in flops, bound by memory traffic)."""
+    sl = frozenset(sliced)
+    first_out = len(legs) - n_outputs
+    out_wires = frozenset(e for t in range(first_out, len(legs)) for e in legs[t])
+    fixed = sl | out_wires
+    sets = [frozenset(l) for l in legs]
+    lev = [2 if out_wires & sets[t] else 1 if sl & sets[t] else 0 for t in range(len(legs))]
+    n_slices = 1 << len(sl)
+    mult = (1, n_slices, n_slices * n_bits)
+    total = 0.0
+    for a, b in order:
+        sa, sb = sets[a] - fixed, sets[b] - fixed
+        la = lev[a]
+        lb = lev[b]
+        lc = max(la, lb)
+        closing = first_out <= a < len(legs) or first_out <= b < len(legs)
+        sets.append(sets[a] ^ sets[b])
+        lev.append(lc)
+        if closing:
+            continue
+        shared = sa & sb
+        m, k, n = len(sa - shared), len(shared), len(sb - shared)
+        ea, eb = len(sa), len(sb)
+        if m < n:
+            m, n = n, m
+        kind = step_kind(m, k, n, min(ea, eb), tensor_cores)
+        items = mult[lc]
+        flops = 8.0 * 2.0 ** (m + k + n) * items
+        nbytes = 8.0 * (2.0 ** (m + n) * items + 2.0 ** ea * (items if la == lc else 1)
+                        + 2.0 ** eb * (items if lb == lc else 1))
+        total += max(flops / rates[kind], nbytes / rates["hbm"]) + rates["launch"]
+    return total
+
+
 def level_aware_plan(legs, trials, seed, n_slice, open_edges, n_outputs, n_bits, max_peak=None,
                      settings=((1.0, 0.6), (0.75, 0.3), (0.75, 0.6), (0.5, 0.6), (0.25, 0.3), (1.0, 1.0),
                                (1.0, 0.2))):
@@ -303,16 +365,23 @@ def _tree_to_order(n_leaves, children, root):
     return order
 
 
-def local_search_plan(legs, order, sliced, n_outputs, n_bits, max_peak, iters, seed):
-    """Local optimisation of a plan (the paper's outlook cites local optimisation of contraction
-    plans): seeded random rotations of the contraction tree, ((A, B), C) -> ((A, C), B), each kept
-    when the plan executes fewer flops per call (executed_cost) with every intermediate within
-    max_peak legs; the sliced bonds stay as given.  Returns (order, executed flops, accepted moves).
+def local_search_plan(legs, order, sliced, n_outputs, n_bits, max_peak, iters, seed, objective="flops"):
+    """Local optimisation of a plan (this project's own step beyond the paper's planner): seeded
+    random rotations of the contraction tree, ((A, B), C) -> ((A, C), B), each kept when the plan
+    costs less per call with every intermediate within max_peak legs; the sliced bonds stay as given.
+    objective "flops": executed flops per call (executed_cost); "time": the roofline estimate of
+    executed_time.  Returns (order, cost, accepted moves).
     """
     n = len(legs)
     children, root = _order_to_tree(n, order)
     internal = sorted(children)
-    best = executed_cost(legs, order, sliced, n_outputs, n_bits)
+    if objective == "flops":
+        cost_of = executed_cost
+    elif objective == "time":
+        cost_of = executed_time
+    else:
+        raise ValueError(f"unknown objective {objective!r}")
+    best = cost_of(legs, order, sliced, n_outputs, n_bits)
     rng = SplitMix64(seed)
     accepted = 0
     for _ in range(iters):
@@ -327,7 +396,7 @@ def local_search_plan(legs, order, sliced, n_outputs, n_bits, max_peak, iters, s
         children[x], children[p] = (keep, y), (x, move)
         cand = _tree_to_order(n, children, root)
         ok = plan_cost(legs, cand, sliced)[0] <= max_peak
-        cost = executed_cost(legs, cand, sliced, n_outputs, n_bits) if ok else None
+        cost = cost_of(legs, cand, sliced, n_outputs, n_bits) if ok else None
         if cost is not None and cost < best:
             best, accepted = cost, accepted + 1
         else:

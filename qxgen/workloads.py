@@ -218,7 +218,9 @@ def batched_specs(count=256):
 
 
 @functools.lru_cache(maxsize=None)
-def batched_circuit(j):
+def batched_circuit_greedy(j):
+    """Circuit j of the batched workload under a seeded greedy plan with its drawn S sliced bonds (the
+    starting point of its stored plan)."""
     n, depth, s, nb = batched_specs()[j]
     cseed = 4000 + j
     rows, cols = near_square_shape(n)
@@ -226,6 +228,35 @@ def batched_circuit(j):
     bits = random_bitstrings(n, nb, cseed + 500000)
     return _workload(f"batched{j}_n{n}_d{depth}_s{s}", circ, np.zeros(n, np.uint8), s, cseed, bits,
                      trials=1, meta={"n": n, "depth": depth, "j": j})
+
+
+@functools.lru_cache(maxsize=None)
+def _batched_plans():
+    import json
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "plans", "batched_uneven.json")
+    with open(path) as f:
+        return json.load(f)["plans"]
+
+
+@functools.lru_cache(maxsize=None)
+def batched_circuit(j):
+    """Circuit j of the batched workload under its stored plan (qxgen/plans/batched_uneven.json, written
+    by qxgen.make_plans: level-aware candidates + local search on the time estimate), checked against
+    the circuit and its recorded cost."""
+    g = batched_circuit_greedy(j)
+    d = _batched_plans()[j]
+    n, depth, s, nb = batched_specs()[j]
+    if d["j"] != j or d["circuit_sha256"] != circuit_digest(g.circuit) or d["n_bits"] != nb or len(d["sliced"]) != s:
+        raise ValueError(f"stored plan {j} was made for another circuit")
+    order = [tuple(p) for p in d["order"]]
+    legs, _, open_edges = network_legs(n, [x.qubits for x in g.circuit.gates], g.open_mask)
+    peak, flops = plan_cost(legs, order, d["sliced"])
+    if executed_cost(legs, order, d["sliced"], n - len(open_edges), nb) != d["executed_flops"] or peak > d["max_peak"]:
+        raise ValueError(f"stored plan {j} does not match its recorded cost")
+    return Workload(g.name, g.circuit, g.open_mask, order, list(d["sliced"]), g.bitstrings, peak, flops,
+                    {"n": n, "depth": depth, "j": j, "executed_flops": d["executed_flops"],
+                     "estimated_s": d["estimated_s"]})
 
 
 BATCHED_MAX_PEAK_RANK = 18

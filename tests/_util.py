@@ -16,9 +16,14 @@ TOL_C64 = 1e-5
 
 # Element-wise: the largest error of any single amplitude, relative to the rms magnitude of the
 # oracle's amplitudes in the same request (a relative error per amplitude is unstable for random-
-# circuit amplitudes near zero, Porter-Thomas); the same 1e-5 acceptance level.  An error confined
-# to a few amplitudes, which the l2 norm over the request could hide, fails this bound.
-TOL_ELEM = 1e-5
+# circuit amplitudes near zero, Porter-Thomas).  FP32 rounding gives every amplitude of a request an
+# error of about the same scale sigma, independently, and the largest of N such errors stays below
+# sigma * sqrt(2 ln 2N) (Gaussian tail), so an l2 error at the 1e-5 tolerance allows a largest
+# element error of TOL_C64 * sqrt(2 ln 2N) times the rms amplitude (1.2e-5 for one amplitude, 3.1e-5
+# for 64, 3.5e-5 for 256).  An error confined to a few amplitudes, which the l2 norm over the request
+# could hide, fails it: one amplitude carrying the whole l2 budget is sqrt(N) * 1e-5 times the rms.
+def tol_elem(n):
+    return TOL_C64 * float(np.sqrt(2.0 * np.log(2.0 * max(int(n), 1))))
 
 
 def rel_l2(a, ref):
@@ -43,12 +48,13 @@ def _log(kind, l2, el):
                                 "rel_l2": l2, "max_elem": el}) + "\n")
 
 
-def assert_parity(a, ref, tol=TOL_C64, tol_elem=TOL_ELEM, what=""):
+def assert_parity(a, ref, tol=TOL_C64, what=""):
     """Both parity bounds of a request: relative l2 over its amplitudes and the element-wise bound."""
     l2, el = rel_l2(a, ref), max_elem(a, ref)
+    te = tol / TOL_C64 * tol_elem(np.asarray(ref).size)
     _log(what, l2, el)
     assert l2 <= tol, f"{what} relative l2 error {l2:.3e} > {tol:.0e}"
-    assert el <= tol_elem, f"{what} largest element error {el:.3e} x rms > {tol_elem:.0e}"
+    assert el <= te, f"{what} largest element error {el:.3e} x rms > {te:.2e}"
 
 
 def grid_case(rows, cols, depth, seed, n_open=0, n_slice=0, n_bits=8, trials=0):

@@ -28,7 +28,7 @@ def _members(count, max_n):
         n = W.batched_specs()[j][0]
         if n > max_n:
             continue
-        w = W.batched_circuit(j)
+        w = W.batched_circuit_greedy(j)
         if w.peak_rank <= W.BATCHED_MAX_PEAK_RANK:
             out.append(w)
         if len(out) == count:

@@ -285,3 +285,20 @@ def test_cancelling_slices_need_the_compensated_sum():
     assert math.fsum(p.real for p in per) == 0.0
     assert oe.amplitudes(2, recs, om, order, sliced, bits)[0, 0] == 0.0
     assert oracle.sv_amplitudes(2, recs, om, bits)[0, 0] == 0.0
+
+
+def test_parity_bounds_catch_a_concentrated_error():
+    """The tests' two parity bounds: independent errors at 80% of the l2 tolerance pass both; the
+    same l2 error put into one amplitude passes the l2 bound but fails the element-wise one."""
+    from ._util import TOL_C64, assert_parity, tol_elem
+    rng = np.random.default_rng(5)
+    for n in (64, 256, 4096):
+        ref = (rng.standard_normal(n) + 1j * rng.standard_normal(n)) / np.sqrt(2 * n)
+        noise = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+        noise *= 0.8 * TOL_C64 * np.linalg.norm(ref) / np.linalg.norm(noise)
+        assert_parity(ref + noise, ref)
+        one = np.zeros(n, complex)
+        one[n // 3] = 0.8 * TOL_C64 * np.linalg.norm(ref)
+        with pytest.raises(AssertionError):
+            assert_parity(ref + one, ref)
+        assert tol_elem(n) < 0.8 * TOL_C64 * np.sqrt(n)

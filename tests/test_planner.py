@@ -142,3 +142,18 @@ def test_large_local_search_plan_keeps_the_slices_and_its_golden_agrees():
     a, b = (np.array(x["re"]) + 1j * np.array(x["im"]) for x in g)
     assert g[0]["bitstring"] == g[1]["bitstring"]
     assert np.linalg.norm(a - b) / np.linalg.norm(a) < 1e-12
+
+
+def test_executed_time_reduces_to_executed_flops_with_one_rate():
+    """With every kernel family at one rate, unbounded memory bandwidth and no launch cost, the time
+    estimate is the executed flops over that rate (the same levels and multiplicities); the memory
+    term alone grows with the bytes a plan moves."""
+    from qxgen.plan import executed_time
+    for w in (W.small(), W.sliced()):
+        legs, n_out = _legs(w)
+        one = {"tc": 1e12, "gemm": 1e12, "gather": 1e12, "hbm": float("inf"), "launch": 0.0}
+        t = executed_time(legs, w.order, w.sliced, n_out, len(w.bitstrings), rates=one)
+        f = executed_cost(legs, w.order, w.sliced, n_out, len(w.bitstrings))
+        assert abs(t * 1e12 - f) <= 1e-9 * f
+        mem = {"tc": float("inf"), "gemm": float("inf"), "gather": float("inf"), "hbm": 1.0, "launch": 0.0}
+        assert executed_time(legs, w.order, w.sliced, n_out, len(w.bitstrings), rates=mem) > 0
