@@ -60,6 +60,9 @@ def parse():
                         "seeded greedy order of the workload definition; checkpoint: the sliced workload's stored "
                         "level-aware plan improved by local search")
     p.add_argument("--no-forms", action="store_true", help="skip timing the other tensor-core forms beside")
+    p.add_argument("--slices", type=int, default=0,
+                   help="contract only slices 0..S-1 per step (a smaller case of the same launches, for profiling; "
+                        "the workload name then says so); 0 = all")
     p.add_argument("--workspace-gb", type=float, default=-1.0,
                    help="device workspace of each form (the same for all, so batches match); "
                         "-1: 48 GB for the large workload, else what one call needs up to 60%% of free memory")
@@ -421,7 +424,10 @@ def main():
     stream = torch.cuda.Stream(dev)
     bits = rank_bits(w, rank)
     n_bits = len(bits)
-    amps_per_step = n_bits << w.n_open
+    # --slices S: a smaller case of the same launches (slices 0..S-1 of every bitstring, for profiling);
+    # a step then yields S / n_slices of each amplitude, counted as that fraction
+    s_end = min(args.slices, w.n_slices) if args.slices > 0 else w.n_slices
+    amps_per_step = (n_bits << w.n_open) * s_end / w.n_slices
     # host-side build and plan compile, timed apart from the contraction (a host-only handle)
     t0 = time.perf_counter()
     hh = qx.qx_create(-1, precision=PRECISIONS[args.precision][0])
@@ -455,7 +461,7 @@ def main():
         torch.cuda.synchronize(dev)
 
     for _ in range(args.warmup):
-        c.contract_device(d_bits, d_amps)
+        c.contract_device(d_bits, d_amps, s_end=s_end)
     stream.synchronize()
     launches_per_step = c.stats()["launches"]
     flops_exec = c.stats()["flops"]
@@ -469,7 +475,7 @@ def main():
         with torch.cuda.stream(stream):
             flush.fill_(i & 0xFF)  # evict L2 between timed steps (outside the events)
         ev[i][0].record(stream)
-        c.contract_device(d_bits, d_amps)
+        c.contract_device(d_bits, d_amps, s_end=s_end)
         ev[i][1].record(stream)
     barrier()
     t_wall = time.perf_counter() - t_wall
@@ -491,14 +497,14 @@ def main():
     # sampler or a server pays per call once the circuit is resident; reported beside, not as value
     qx.qx_set_memo(c.h, 1)
     for _ in range(2):  # computes and keeps them, then captures the graph without those steps
-        c.contract_device(d_bits, d_amps)
+        c.contract_device(d_bits, d_amps, s_end=s_end)
     evm = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     barrier()
     for i in range(args.steps):
         with torch.cuda.stream(stream):
             flush.fill_(i & 0xFF)
         evm[i][0].record(stream)
-        c.contract_device(d_bits, d_amps)
+        c.contract_device(d_bits, d_amps, s_end=s_end)
         evm[i][1].record(stream)
     barrier()
     memo_ms = sum(a.elapsed_time(b) for a, b in evm) / args.steps
@@ -519,14 +525,14 @@ def main():
             qx.qx_set_streams(cf.h, args.streams)
             out = torch.empty_like(d_amps)
         for _ in range(args.warmup):
-            cf.contract_device(d_bits, out)
+            cf.contract_device(d_bits, out, s_end=s_end)
         evf = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
         barrier()
         for i in range(args.steps):
             with torch.cuda.stream(stream):
                 flush.fill_(i & 0xFF)
             evf[i][0].record(stream)
-            cf.contract_device(d_bits, out)
+            cf.contract_device(d_bits, out, s_end=s_end)
             evf[i][1].record(stream)
         barrier()
         qx.qx_device_status(cf.h)
@@ -559,20 +565,26 @@ def main():
     # per-kernel event timing over K more steps on the same stream
     qx.qx_set_profiling(c.h, True)
     for _ in range(args.steps):
-        c.contract_device(d_bits, d_amps)
+        c.contract_device(d_bits, d_amps, s_end=s_end)
     prof = qx.qx_profile_read(c.h)
     qx.qx_set_profiling(c.h, False)
 
     # end to end through the public host API: pinned bitstrings in, pinned amplitudes out
     h_bits = torch.from_numpy(bits).pin_memory()
     h_amps = torch.empty((n_bits, 1 << w.n_open, 2), dtype=torch.float64).pin_memory()
-    c.contract_host_ptr(h_bits.data_ptr(), n_bits, h_amps.data_ptr())
+    def contract_host():
+        if s_end == w.n_slices:
+            c.contract_host_ptr(h_bits.data_ptr(), n_bits, h_amps.data_ptr())
+        else:
+            c.contract_slices_host_ptr(h_bits.data_ptr(), n_bits, 0, s_end, h_amps.data_ptr())
+
+    contract_host()
     barrier()
     lat = []
     t_e2e = time.perf_counter()
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        c.contract_host_ptr(h_bits.data_ptr(), n_bits, h_amps.data_ptr())
+        contract_host()
         lat.append(time.perf_counter() - t0)
     barrier()
     t_e2e = time.perf_counter() - t_e2e
@@ -593,7 +605,7 @@ def main():
     # or its operations at the unit's peak, whichever takes longer for the same work
     hbm_peak = pk["hbm_gbs"]
     t_bytes = d["bytes"] / (hbm_peak * 1e9)
-    if dom == "tc_gemm":
+    if dom in ("tc_gemm", "tc_direct"):
         code, products, ratio = PRECISIONS[args.precision]
         peak = pk["bf16_tflops"] * ratio
         ops = d["flops"] * products  # issued real tensor flops
@@ -665,7 +677,8 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": {"c64": "c64", "3xtf32": "tf32x3", "bf16x3": "bf16x3", "fp16": "fp16"}[args.precision],
             "data": "synthetic",
-            "config": config_of(w, {"precision": args.precision + " contraction, FP64 slice sum",
+            "config": config_of(w, {"workload": w.name + (f"_slices0-{s_end - 1}" if s_end < w.n_slices else ""),
+                                    "precision": args.precision + " contraction, FP64 slice sum",
                                     "executor": args.executor, "streams": args.streams,
                                     "bitstring_independent_steps": "per pair" if args.no_slice_level else "per slice",
                                     "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",

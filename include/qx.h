@@ -186,6 +186,25 @@ int qx_submit(qx_handle h, const uint8_t* d_bitstrings, int64_t n_bits, int64_t 
               double* d_amps_out, double* h_amps_out, int64_t* req_out);
 int qx_poll(qx_handle h, int64_t req, int32_t* done);
 
+/* One sum over all slices (Eq. 2) submitted in parts, so that a server can
+ * interleave other work between the parts of a long request: as qx_submit,
+ * but the FP64 compensated accumulators of the handle carry the running sum
+ * from one part to the next, so the parts add exactly as one call over their
+ * slices would (the same per-slice results, summed in the same slice order).
+ *   first != 0  starts a new sum (clears the accumulators); first == 0
+ *               continues the handle's open sum: d_bitstrings and n_bits must
+ *               be those of its first part and s_begin the s_end of its last
+ *               part, else QX_ESTATE;
+ *   last != 0   ends the sum: the amplitudes are written to d_amps_out (and
+ *               copied to h_amps_out when it is not NULL); parts with
+ *               last == 0 write nothing to either buffer.
+ * The completion event of every part is polled with qx_poll.  Any other
+ * contraction on the handle ends an open sum (its parts must be submitted
+ * again from first != 0).  The batched executor only (executor 0 or 1; else
+ * QX_EINVAL). */
+int qx_submit_part(qx_handle h, const uint8_t* d_bitstrings, int64_t n_bits, int64_t s_begin, int64_t s_end,
+                   int32_t first, int32_t last, double* d_amps_out, double* h_amps_out, int64_t* req_out);
+
 /* Graph replay (on by default): a call of qx_contract / qx_contract_device /
  * qx_contract_slices[_device] that repeats the previous call's device
  * buffers, bitstring count and slice range is captured once as a CUDA graph
@@ -360,11 +379,12 @@ void qx_group_destroy(qx_group_t g);
 #define QX_KERNEL_GEMM    2
 #define QX_KERNEL_SUM     3
 #define QX_KERNEL_TC_PREP 4  /* operand split / expansion for the tensor-core forms */
-#define QX_KERNEL_TC_GEMM 5  /* tcgen05 complex GEMM */
+#define QX_KERNEL_TC_GEMM 5  /* tcgen05 complex GEMM on pre-split operands (k_gemm_tc) */
 #define QX_KERNEL_PERSIST 6  /* persistent executor (whole contractions) */
 #define QX_KERNEL_WAVE    7  /* batched executor: the small invariant steps, one CTA per chain */
 #define QX_KERNEL_SMALL_FLAT 8  /* gathers of short per-pair rows, one thread per row (k_small_flat) */
-#define QX_KERNEL_KINDS   9
+#define QX_KERNEL_TC_DIRECT 9  /* tcgen05 3xTF32 GEMM splitting raw complex64 slabs itself (k_gemm_tc2) */
+#define QX_KERNEL_KINDS   10
 int qx_set_profiling(qx_handle h, int enable);
 int qx_profile_read(qx_handle h, int kind, double* ms, int64_t* launches, double* flops, double* bytes);
 

@@ -168,10 +168,17 @@ struct qx_ctx {
     bool memo = false;       // keep the invariant intermediates across calls (qx_set_memo)
     bool inv_ready = false;  // the bound workspace holds them
     char* static_err = nullptr;  // error flag of the last static-scratch call, until qx_device_status reads it
+    // Parts of one compensated slice sum (qx_submit_part): the next contraction clears the FP64
+    // accumulators first (part_clear) and writes the amplitudes at the end (part_final); a sum left
+    // open continues at slice part_next with the same bitstrings.
+    bool part_clear = true, part_final = true, part_open = false;
+    const uint8_t* part_bits = nullptr;
+    int64_t part_nbits = 0, part_next = 0;
     struct {
         const uint8_t* bits = nullptr;
         double* amps = nullptr;
         int64_t n_bits = -1, s0 = -1, s1 = -1;
+        bool clear = true, final_ = true;
         int seen = 0;
         cudaGraphExec_t exec = nullptr;
         double flops = 0;
@@ -1427,7 +1434,7 @@ static int run_op(qx_ctx* h, const Op& op, const ItemCtx& ic, int64_t n_items, c
     if (op.type == OP_SMALL) sdesc = small_desc(h, op);
     const int kind = op.type == OP_PERM    ? QX_KERNEL_PERMUTE
                      : op.type == OP_SMALL ? (small_is_flat(sdesc) ? QX_KERNEL_SMALL_FLAT : QX_KERNEL_SMALL)
-                     : direct              ? QX_KERNEL_TC_GEMM
+                     : direct              ? QX_KERNEL_TC_DIRECT
                      : prep                ? QX_KERNEL_TC_PREP
                                            : QX_KERNEL_GEMM;
     size_t slot;
@@ -1772,6 +1779,7 @@ static int contract_impl(qx_ctx* h, const uint8_t* d_bits, int64_t n_bits, int64
     h->last_flops = 0;
     h->last_launches = 0;
     h->last_batches = 0;
+    if (h->part_clear) h->part_open = false;  // any whole contraction ends an open sum of parts
     if (!h->leaves_on_device) {
         CUDA_TRY(h, cudaMemcpyAsync(h->ws + h->off_leaf, h->leaf_vals.data(), h->leaf_vals.size() * sizeof(float2),
                                     cudaMemcpyHostToDevice, h->stream));
@@ -1784,8 +1792,12 @@ static int contract_impl(qx_ctx* h, const uint8_t* d_bits, int64_t n_bits, int64
     if (mode >= 2 && !persist_active(h))
         return fail(h, QX_EINVAL, mode == 3 ? "a group member contracts only through qx_group_run"
                                             : "the persistent executor does not apply to this plan and precision form");
-    if (mode == 2) return contract_persistent(h, d_bits, n_bits, s_begin, s_end, d_amps);
-    CUDA_TRY(h, cudaMemsetAsync(acc, 0, (size_t)(n_bits * n_o * 32), h->stream));
+    if (mode == 2) {
+        if (!h->part_clear || !h->part_final)
+            return fail(h, QX_EINVAL, "parts of a slice sum need the batched executor");
+        return contract_persistent(h, d_bits, n_bits, s_begin, s_end, d_amps);
+    }
+    if (h->part_clear) CUDA_TRY(h, cudaMemsetAsync(acc, 0, (size_t)(n_bits * n_o * 32), h->stream));
     ItemCtx ic{};
     ic.n_qubits = h->nq;
     ic.bits = d_bits;
@@ -1855,9 +1867,11 @@ static int contract_impl(qx_ctx* h, const uint8_t* d_bits, int64_t n_bits, int64
             h->last_batches++;
         }
     }
-    cudaError_t e = launch_finalize(acc, d_amps, n_bits * n_o, h->leaf_scale[0], h->leaf_scale[1], h->stream);
-    if (e != cudaSuccess) return fail(h, QX_ECUDA, "finalize launch failed: %s", cudaGetErrorString(e));
-    h->last_launches++;
+    if (h->part_final) {
+        cudaError_t e = launch_finalize(acc, d_amps, n_bits * n_o, h->leaf_scale[0], h->leaf_scale[1], h->stream);
+        if (e != cudaSuccess) return fail(h, QX_ECUDA, "finalize launch failed: %s", cudaGetErrorString(e));
+        h->last_launches++;
+    }
     if (h->memo) h->inv_ready = true;
     return QX_OK;
 }
@@ -1872,7 +1886,7 @@ static int contract_graph(qx_ctx* h, const uint8_t* d_bits, int64_t n_bits, int6
     const bool usable = h->graphs && !h->profiling && h->stream != nullptr && cap == cudaStreamCaptureStatusNone;
     if (!usable) return contract_impl(h, d_bits, n_bits, s0, s1, d_amps);
     const bool same = h->gc.bits == d_bits && h->gc.amps == d_amps && h->gc.n_bits == n_bits && h->gc.s0 == s0 &&
-                      h->gc.s1 == s1;
+                      h->gc.s1 == s1 && h->gc.clear == h->part_clear && h->gc.final_ == h->part_final;
     if (same && h->gc.exec) {
         CUDA_TRY(h, cudaGraphLaunch(h->gc.exec, h->stream));
         h->last_flops = h->gc.flops;
@@ -1887,6 +1901,8 @@ static int contract_graph(qx_ctx* h, const uint8_t* d_bits, int64_t n_bits, int6
         h->gc.n_bits = n_bits;
         h->gc.s0 = s0;
         h->gc.s1 = s1;
+        h->gc.clear = h->part_clear;
+        h->gc.final_ = h->part_final;
         return contract_impl(h, d_bits, n_bits, s0, s1, d_amps);
     }
     cudaGraph_t graph = nullptr;
@@ -2118,14 +2134,7 @@ int qx_contract_slices_device(qx_handle h, const uint8_t* d_bits, int64_t n_bits
     return contract_graph(h, d_bits, n_bits, s_begin, s_end, d_amps);
 }
 
-int qx_submit(qx_handle h, const uint8_t* d_bits, int64_t n_bits, int64_t s_begin, int64_t s_end, double* d_amps,
-              double* h_amps, int64_t* req_out) {
-    if (!h || !req_out) return QX_EINVAL;
-    int rc = qx_contract_slices_device(h, d_bits, n_bits, s_begin, s_end, d_amps);
-    if (rc) return rc;
-    if (h_amps)
-        CUDA_TRY(h, cudaMemcpyAsync(h_amps, d_amps, (size_t)(n_bits << n_open(h)) * 16, cudaMemcpyDeviceToHost,
-                                    h->stream));
+static int enqueue_request(qx_ctx* h, int64_t* req_out) {
     cudaEvent_t e;
     if (!h->req_pool.empty()) {
         e = h->req_pool.back();
@@ -2142,6 +2151,48 @@ int qx_submit(qx_handle h, const uint8_t* d_bits, int64_t n_bits, int64_t s_begi
     h->reqs[id] = e;
     *req_out = id;
     return QX_OK;
+}
+
+int qx_submit_part(qx_handle h, const uint8_t* d_bits, int64_t n_bits, int64_t s_begin, int64_t s_end,
+                   int32_t first, int32_t last, double* d_amps, double* h_amps, int64_t* req_out) {
+    if (!h || !req_out) return QX_EINVAL;
+    int rc = check_ready(h, n_bits);
+    if (rc) return rc;
+    rc = check_range(h, s_begin, s_end);
+    if (rc) return rc;
+    if (!d_bits || !d_amps) return fail(h, QX_EINVAL, "null buffer");
+    if (h->opt.executor == 2) return fail(h, QX_EINVAL, "parts of a slice sum need the batched executor");
+    if (!first && (!h->part_open || d_bits != h->part_bits || n_bits != h->part_nbits || s_begin != h->part_next))
+        return fail(h, QX_ESTATE, "a continuing part must follow the open sum's last part: same bitstrings, slices "
+                                  "from %lld", (long long)(h->part_open ? h->part_next : -1));
+    CUDA_TRY(h, cudaSetDevice(h->device));
+    h->part_clear = first != 0;
+    h->part_final = last != 0;
+    rc = contract_graph(h, d_bits, n_bits, s_begin, s_end, d_amps);
+    h->part_clear = h->part_final = true;
+    if (rc) {
+        h->part_open = false;
+        return rc;
+    }
+    h->part_open = !last;
+    h->part_bits = d_bits;
+    h->part_nbits = n_bits;
+    h->part_next = s_end;
+    if (last && h_amps)
+        CUDA_TRY(h, cudaMemcpyAsync(h_amps, d_amps, (size_t)(n_bits << n_open(h)) * 16, cudaMemcpyDeviceToHost,
+                                    h->stream));
+    return enqueue_request(h, req_out);
+}
+
+int qx_submit(qx_handle h, const uint8_t* d_bits, int64_t n_bits, int64_t s_begin, int64_t s_end, double* d_amps,
+              double* h_amps, int64_t* req_out) {
+    if (!h || !req_out) return QX_EINVAL;
+    int rc = qx_contract_slices_device(h, d_bits, n_bits, s_begin, s_end, d_amps);
+    if (rc) return rc;
+    if (h_amps)
+        CUDA_TRY(h, cudaMemcpyAsync(h_amps, d_amps, (size_t)(n_bits << n_open(h)) * 16, cudaMemcpyDeviceToHost,
+                                    h->stream));
+    return enqueue_request(h, req_out);
 }
 
 int qx_poll(qx_handle h, int64_t req, int32_t* done) {

@@ -387,13 +387,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             tc_fence_after();
             const uint32_t st = s_addr(base + s * STAGE_BYTES);
             const uint32_t d = tmem + b * TC_BN;
+            // the smallest part products first, the main one (p = 0) last: each MMA joins the FP32
+            // accumulator with a truncated alignment, so correction terms summed while it is still
+            // small keep their bits, and only the main product's MMAs add at full magnitude
 #pragma unroll
-            for (int kk = 0; kk < BK / KSTEP; ++kk) {
+            for (int p = F::NPROD - 1; p >= 0; --p) {
 #pragma unroll
-                for (int p = 0; p < F::NPROD; ++p) {
+                for (int kk = 0; kk < BK / KSTEP; ++kk) {
                     const uint64_t ad = sdesc(st + F::pa(p) * TILE + kk * 32);
                     const uint64_t bd = sdesc(st + (F::NPA + F::pb(p)) * TILE + kk * 32);
-                    mma<FORM>(d, ad, bd, IDESC, (kk | p) != 0);
+                    mma<FORM>(d, ad, bd, IDESC, (p != F::NPROD - 1 || kk != 0) ? 1u : 0u);
                 }
             }
             tc_commit(&empty[s]);
@@ -687,14 +690,18 @@ __global__ void __launch_bounds__(TC2_THREADS, 1)
             const uint32_t st = s_addr(mslot(m));
             const uint32_t d = tmem + b * BN;
             const uint32_t acol = L::ACOL + 64 * (uint32_t)(keep_a ? it : m);
+            // the correction products first, the main one last (see k_gemm_tc: each MMA joins the FP32
+            // accumulator with a truncated alignment)
 #pragma unroll
             for (int kk = 0; kk < BK / 8; ++kk) {
                 const uint32_t ahi = tmem + acol + 8 * kk, alo = ahi + 32;
                 const uint64_t bhi = sdesc(st + kk * 32), blo = sdesc(st + L::OFF_BLO + kk * 32);
-                mma_tf32_ta(d, ahi, bhi, IDESC, kk != 0);
-                mma_tf32_ta(d, ahi, blo, IDESC, 1);
+                mma_tf32_ta(d, ahi, blo, IDESC, kk != 0);
                 mma_tf32_ta(d, alo, bhi, IDESC, 1);
             }
+#pragma unroll
+            for (int kk = 0; kk < BK / 8; ++kk)
+                mma_tf32_ta(d, tmem + acol + 8 * kk, sdesc(st + kk * 32), IDESC, 1);
             tc_commit(&mfree[m]);
             tc_commit(&tfull[b]);
             m += 2;

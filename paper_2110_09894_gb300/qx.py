@@ -26,9 +26,9 @@ EXPORTS = ("qx_create", "qx_destroy", "qx_last_error", "qx_set_options", "qx_bui
            "qx_profile_read", "qx_contract_device_static", "qx_device_status", "qx_group_create",
            "qx_group_scratch_size", "qx_group_bind", "qx_group_run", "qx_group_last_error", "qx_group_destroy",
            "qx_set_graphs", "qx_set_streams", "qx_describe_plan", "qx_submit", "qx_poll", "qx_esup_accept",
-           "qx_esup_sample", "qx_set_memo")
+           "qx_esup_sample", "qx_set_memo", "qx_submit_part")
 QX_STATIC_SCRATCH_BYTES = 64 << 20
-KERNEL_KINDS = ("permute", "small", "gemm", "sum", "tc_prep", "tc_gemm", "persist", "wave", "small_flat")
+KERNEL_KINDS = ("permute", "small", "gemm", "sum", "tc_prep", "tc_gemm", "persist", "wave", "small_flat", "tc_direct")
 
 
 class QXError(RuntimeError):
@@ -83,6 +83,7 @@ def load(path=None):
         "qx_set_streams": ([vp, i32], ctypes.c_int),
         "qx_submit": ([vp, vp, i64, i64, i64, vp, vp, ctypes.POINTER(i64)], ctypes.c_int),
         "qx_poll": ([vp, i64, ctypes.POINTER(i32)], ctypes.c_int),
+        "qx_submit_part": ([vp, vp, i64, i64, i64, i32, i32, vp, vp, ctypes.POINTER(i64)], ctypes.c_int),
         "qx_describe_plan": ([vp, ctypes.c_char_p, i64, ctypes.POINTER(i64)], ctypes.c_int),
         "qx_group_create": ([ctypes.POINTER(vp), ctypes.POINTER(vp), i32, ctypes.POINTER(vp), ctypes.POINTER(i64),
                              ctypes.POINTER(vp), i32], ctypes.c_int),
@@ -256,6 +257,15 @@ def qx_submit(h, d_bits_ptr, n_bits, s_begin, s_end, d_amps_ptr, h_amps_ptr=None
     return req.value
 
 
+def qx_submit_part(h, d_bits_ptr, n_bits, s_begin, s_end, first, last, d_amps_ptr, h_amps_ptr=None):
+    """Enqueue one part of a slice sum (the accumulators carry over between parts); returns the request."""
+    req = ctypes.c_int64()
+    _check(h, load().qx_submit_part(h, ctypes.c_void_p(int(d_bits_ptr)), int(n_bits), int(s_begin), int(s_end),
+                                    int(bool(first)), int(bool(last)), ctypes.c_void_p(int(d_amps_ptr)),
+                                    ctypes.c_void_p(int(h_amps_ptr)) if h_amps_ptr else None, ctypes.byref(req)))
+    return req.value
+
+
 def qx_poll(h, req):
     """True once request `req` has finished (reported once), False while it runs."""
     done = ctypes.c_int32()
@@ -329,6 +339,11 @@ class Contractor:
         """qx_contract on raw host pointers (e.g. pinned buffers); synchronises."""
         _check(self.h, load().qx_contract(self.h, ctypes.c_void_p(int(bits_ptr)), int(n_bits),
                                           ctypes.c_void_p(int(amps_ptr))))
+
+    def contract_slices_host_ptr(self, bits_ptr, n_bits, s_begin, s_end, amps_ptr):
+        """qx_contract_slices on raw host pointers (e.g. pinned buffers); synchronises."""
+        _check(self.h, load().qx_contract_slices(self.h, ctypes.c_void_p(int(bits_ptr)), int(n_bits), int(s_begin),
+                                                 int(s_end), ctypes.c_void_p(int(amps_ptr))))
 
     def contract_slices(self, bitstrings, s_begin, s_end):
         """Partial sum over slices [s_begin, s_end) (host in, host out)."""

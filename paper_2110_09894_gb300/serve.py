@@ -7,18 +7,20 @@ while other work is on the GPU:
 * requests for the same circuit that wait together are merged into one
   contraction (their bitstrings concatenated: the slice-batched executor then
   runs all their (slice, bitstring) pairs in the same launches);
-* a merged batch runs in slice chunks (``qx_contract_slices_device``) sized to
-  a target amount of work, so a long request never holds the GPU for long and
-  new arrivals start between chunks; chunk results are summed on the host in
-  FP64 with compensation, in slice order;
+* a merged batch runs in slice chunks sized to a target amount of work, so a
+  long request never holds the GPU for long and new arrivals start between
+  chunks; the chunks are parts of one sum in the library (``qx_submit_part``):
+  the lane's FP64 compensated accumulators carry from chunk to chunk on the
+  device, so a chunked request gets the same sum, in the same slice order, as
+  one call over all slices (Eq. 2);
 * each circuit owns a few execution lanes (a library handle with its own
   workspace and CUDA stream); lanes are created on demand while the device
   memory budget allows (admission by memory) and reused afterwards; a lane
   keeps its circuit's invariant intermediates across requests (qx_set_memo);
-* each chunk is one asynchronous request of the library (``qx_submit``: the
-  contraction and the copy of its amplitudes to pinned host memory on the
-  lane's stream); completion is polled with ``qx_poll``; latency runs from a
-  request's arrival to the host seeing its amplitudes;
+* each chunk is one asynchronous request of the library (the contraction of
+  its slices, and for the last chunk the copy of the amplitudes to pinned
+  host memory, on the lane's stream); completion is polled with ``qx_poll``;
+  latency runs from a request's arrival to the host seeing its amplitudes;
 * a request is rejected at arrival if its circuit cannot get a lane within
   the memory budget or if its estimated work (plan flops x slices x
   bitstrings) exceeds max_request_flops.
@@ -55,8 +57,7 @@ class _Batch:
     amps_dev: object
     amps_host: object           # pinned float64 tensor
     chunks: list                # [(s0, s1)] still to run
-    acc_s: np.ndarray = None    # Neumaier sum over chunks, complex as float64 pairs
-    acc_c: np.ndarray = None
+    first: bool = True          # the next chunk starts the sum
     req: int = 0                # library request number of the chunk in flight
     inflight: tuple = None
 
@@ -171,8 +172,7 @@ class Server:
         per_slice = max(sc.flops_per_slice * n, 1.0)
         step = int(max(1, min(sc.n_slices, self.chunk_flops // per_slice)))
         chunks = [(s, min(s + step, sc.n_slices)) for s in range(0, sc.n_slices, step)]
-        lane.batch = _Batch(reqs, bh, bd, ad, ah, chunks, np.zeros((n, 1 << sc.n_open, 2)),
-                            np.zeros((n, 1 << sc.n_open, 2)))
+        lane.batch = _Batch(reqs, bh, bd, ad, ah, chunks)
         self.stats["batches"] += 1
         self.stats["merged_requests"] += len(reqs) - 1
         self._launch_chunk(lane)
@@ -181,22 +181,19 @@ class Server:
     def _launch_chunk(self, lane):
         b = lane.batch
         s0, s1 = b.chunks.pop(0)
-        b.req = qx.qx_submit(lane.c.h, b.bits_dev.data_ptr(), b.bits_dev.shape[0], s0, s1, b.amps_dev.data_ptr(),
-                             b.amps_host.data_ptr())
+        last = not b.chunks
+        b.req = qx.qx_submit_part(lane.c.h, b.bits_dev.data_ptr(), b.bits_dev.shape[0], s0, s1, b.first, last,
+                                  b.amps_dev.data_ptr(), b.amps_host.data_ptr() if last else None)
+        b.first = False
         b.inflight = (s0, s1)
         self.stats["chunks"] += 1
 
     def _finish_chunk(self, lane):
         b = lane.batch
-        x = b.amps_host.numpy()
-        t = b.acc_s + x
-        big = np.abs(b.acc_s) >= np.abs(x)
-        b.acc_c += np.where(big, (b.acc_s - t) + x, (x - t) + b.acc_s)
-        b.acc_s = t
         if b.chunks:
             self._launch_chunk(lane)
             return
-        tot = b.acc_s + b.acc_c
+        tot = b.amps_host.numpy()
         amps = tot[..., 0] + 1j * tot[..., 1]
         t_done = self.now()
         k = 0

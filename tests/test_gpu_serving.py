@@ -95,3 +95,50 @@ def test_submit_and_poll_requests(serve):
     with pytest.raises(qx.QXError):
         qx.qx_poll(c.h, 10 ** 9)
     qx.qx_device_status(c.h)
+
+
+def test_parts_of_a_slice_sum_add_like_one_call(serve):
+    """qx_submit_part: the FP64 compensated accumulators carry over on the device from part to part, so
+    a sum over all slices submitted in parts equals the one-call sum (same per-slice results, same slice
+    order); a continuing part that does not follow the open sum is refused."""
+    import time
+
+    import torch
+
+    from paper_2110_09894_gb300 import qx
+    from tests._util import grid_case
+    circ, om, order, sliced, bits = grid_case(3, 4, 8, 62, 1, 4, 6)
+    st = torch.cuda.Stream()
+    c = qx.Contractor(circ.n_qubits, C.gates_to_records(circ), om, order, sliced, 6, stream=st,
+                      executor=qx.EXEC_BATCHED)
+    whole = c.contract(bits)
+    ref = oracle.sv_amplitudes(circ.n_qubits, C.gates_to_records(circ), om, bits)
+    assert_parity(whole, ref)
+    d_bits = torch.from_numpy(bits).cuda()
+    d_amps = torch.full((6, 2, 2), float("nan"), dtype=torch.float64, device="cuda")
+    h_amps = torch.full((6, 2, 2), float("nan"), dtype=torch.float64).pin_memory()
+    parts = [(0, 3), (3, 4), (4, 11), (11, 16)]
+    reqs = []
+    for k, (s0, s1) in enumerate(parts):
+        reqs.append(qx.qx_submit_part(c.h, d_bits.data_ptr(), 6, s0, s1, k == 0, k == len(parts) - 1,
+                                      d_amps.data_ptr(), h_amps.data_ptr()))
+        if k == 1:  # parts before the last write nothing
+            st.synchronize()
+            assert np.all(np.isnan(h_amps.numpy()))
+    t0 = time.time()
+    while reqs and time.time() - t0 < 60:
+        reqs = [r for r in reqs if not qx.qx_poll(c.h, r)]
+    assert not reqs
+    got = h_amps.numpy()
+    got = got[..., 0] + 1j * got[..., 1]
+    assert np.array_equal(got, whole)
+    with pytest.raises(qx.QXError) as e:  # no open sum to continue
+        qx.qx_submit_part(c.h, d_bits.data_ptr(), 6, 16, 16 + 0, False, True, d_amps.data_ptr())
+    r = qx.qx_submit_part(c.h, d_bits.data_ptr(), 6, 0, 5, True, False, d_amps.data_ptr())
+    with pytest.raises(qx.QXError) as e:  # skips slices 5..6
+        qx.qx_submit_part(c.h, d_bits.data_ptr(), 6, 7, 16, False, True, d_amps.data_ptr())
+    assert e.value.code == qx.QX_ESTATE
+    qx.qx_device_status(c.h)
+    while not qx.qx_poll(c.h, r):
+        pass
+    c.close()
