@@ -272,51 +272,96 @@ def traffic_for(kind, workload_name):
 
 
 def group_bench(args):
-    """All member circuits of the uneven batched workload: one captured graph (3 launches) per step."""
+    """All 256 circuits of the uneven batched workload in one captured CUDA graph per step: the light ones
+    (intermediates within a CTA's scratch) in the persistent launch, the heavy ones on the batched
+    executor, with the autotuned tile family and slice-batch size of each heavy member."""
     import torch
-    from paper_2110_09894_gb300 import autotune, qx
+    from paper_2110_09894_gb300 import autotune
     from paper_2110_09894_gb300 import build as qxbuild
+    from paper_2110_09894_gb300.batch import UnevenBatch
     qxbuild.build()
     ws = W.batched_members()
-    dev = torch.device("cuda", 0)
-    stream = torch.cuda.Stream(dev)
-    cs = [qx.Contractor(w.n_qubits, w.gates, w.open_mask, w.order, w.sliced, len(w.bitstrings),
-                        executor=qx.EXEC_GROUP_MEMBER, stream=stream) for w in ws]
-    bits = [torch.from_numpy(w.bitstrings).to(dev) for w in ws]
-    torch.cuda.synchronize()
-    g, ctas, tune_ms = autotune.tuned_group(cs, bits)
-    g.capture()
+    prec = PRECISIONS[args.precision][0]
+    t0 = time.perf_counter()
+    b, choice, tune_ms = autotune.tuned_uneven(ws, precision=prec)
+    tune_s = time.perf_counter() - t0
+    b.capture()
+    eager = b.amplitudes()
+    launches = 3 * (b.group is not None) + sum(c.stats()["launches"] for c in b.heavy_members.values())
+    flops = sum(float(c.stats()["flops"]) for c in b.heavy_members.values()) + \
+        sum(float(ws[i].flops_per_slice) * ws[i].n_slices * len(ws[i].bitstrings) for i in b.light)
     amps = sum(len(w.bitstrings) << w.n_open for w in ws)
-    flops = sum(float(w.flops_per_slice) * w.n_slices * len(w.bitstrings) for w in ws)
-    for _ in range(args.warmup):
-        g.replay()
-    torch.cuda.synchronize()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+
+    def timed(batch):
+        for _ in range(args.warmup):
+            batch.replay()
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        for i in range(args.steps):
+            with torch.cuda.stream(batch.stream):
+                flush.fill_(i & 0xFF)
+            ev[i][0].record(batch.stream)
+            batch.replay()
+            ev[i][1].record(batch.stream)
+        torch.cuda.synchronize()
+        batch.check()
+        return [a.elapsed_time(c) for a, c in ev]
+
     sampler = ClockSampler(0)
     sampler.start()
-    for i in range(args.steps):
-        ev[i][0].record(stream)
-        g.replay()
-        ev[i][1].record(stream)
-    torch.cuda.synchronize()
+    ms = timed(b)
     clocks = sampler.stop()
-    ms = [a.elapsed_time(b) for a, b in ev]
-    worst = 0.0
-    for w, a in zip(ws[:8], g.amplitudes()[:8]):
-        if w.n_qubits <= 24:
-            import oracle
-            ref = oracle.sv_amplitudes(w.n_qubits, w.gates, w.open_mask, w.bitstrings)
-            worst = max(worst, float(np.linalg.norm(a - ref) / np.linalg.norm(ref)))
+    got = b.amplitudes()
+    replay_equal = all(np.array_equal(a, c) for a, c in zip(eager, got))
+    # parity of every member against its complex128 state vector (stored by tests/golden/make_batched_golden.py)
+    parity = None
+    gpath = os.path.join(ROOT, "tests", "golden", "batched_statevector.json")
+    if os.path.exists(gpath):
+        with open(gpath) as f:
+            recs = {r["j"]: r for r in json.load(f)["circuits"]}
+        worst_l2 = worst_el = 0.0
+        checked = 0
+        for w, a in zip(ws, got):
+            r = recs.get(w.meta["j"])
+            if r is None:
+                continue
+            ref = (np.array(r["re"]) + 1j * np.array(r["im"])).reshape(a.shape)
+            worst_l2 = max(worst_l2, float(np.linalg.norm(a - ref) / np.linalg.norm(ref)))
+            worst_el = max(worst_el, float(np.max(np.abs(a - ref)) / np.sqrt(np.mean(np.abs(ref) ** 2))))
+            checked += 1
+        parity = {"vs": "complex128 state vectors (batched_statevector.json)", "members_checked": checked,
+                  "worst_rel_l2": worst_l2, "worst_max_elem_over_rms": worst_el}
+    # the same members in plain complex64 (heavy members on the SIMT kernels), same settings
+    vs_c64 = None
+    if prec != 0:
+        b64 = UnevenBatch(ws, precision=0, ctas_per_sm=choice["ctas_per_sm"],
+                          settings={int(i): s for i, s in choice["settings"].items()})
+        b64.capture()
+        ms64 = timed(b64)
+        a64 = b64.amplitudes()
+        vs_c64 = {"c64_ms_per_step": sum(ms64) / len(ms64), "speedup": sum(ms64) / sum(ms),
+                  "worst_rel_diff_to_c64": max(float(np.linalg.norm(x - y) / np.linalg.norm(y))
+                                               for x, y in zip(got, a64))}
+        b64.close()
+    n_light, n_heavy = len(b.light), len(b.heavy)
     line = {"metric": "amplitudes/s", "value": amps * len(ms) / (sum(ms) / 1e3), "unit": "amplitudes/s",
             "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": sum(ms) / len(ms),
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c64", "data": "synthetic",
-            "config": {"workload": "batched uneven grid circuits (n 16..28, depth 8..16, S 0..8, 1..64 bitstrings)",
-                       "members": len(ws), "excluded_heavy_tail": len(W.batched_excluded()),
-                       "pairs": int(sum(w.n_slices * len(w.bitstrings) for w in ws)),
-                       "executor": "group: one captured graph = prologue launch + persistent launch + FP64 sum",
-                       "autotuned_ctas_per_sm": ctas, "autotune_ms": tune_ms},
-            "complex_tflops": flops * len(ms) / (sum(ms) / 1e3) / 1e12, "rel_err_first_members": worst,
-            "gpu_launches": 3 * args.steps, "clocks": clocks}
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": {"c64": "c64", "3xtf32": "tf32x3", "bf16x3": "bf16x3", "fp16": "fp16"}[args.precision],
+            "data": "synthetic",
+            "config": {"workload": "batched uneven grid circuits (256: n 16..28, depth 8..16, S 0..8, 1..64 "
+                                   "bitstrings)", "members": len(ws), "light_persistent": n_light,
+                       "heavy_batched": n_heavy, "pairs": int(sum(w.n_slices * len(w.bitstrings) for w in ws)),
+                       "amplitudes": int(amps),
+                       "executor": "one captured CUDA graph per step: persistent launch (light members, complex64) "
+                                   "+ batched launches of the heavy members (" + args.precision + ")",
+                       "autotuned": {"ctas_per_sm": choice["ctas_per_sm"], "heavy_settings": choice["settings"]},
+                       "autotune_s": tune_s, "l2": "flushed between timed steps"},
+            "complex_tflops_executed": flops * len(ms) / (sum(ms) / 1e3) / 1e12, "parity": parity,
+            "graph_replay_equals_eager_run": replay_equal, "vs_plain_c64": vs_c64,
+            "gpu_launches": int(launches * args.steps), "clocks": clocks}
+    b.close()
     print(json.dumps(line), flush=True)
 
 

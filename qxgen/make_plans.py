@@ -1,6 +1,6 @@
 """Write the stored plans of qxgen/plans/ (plans are inputs; the paper keeps them in files).
 
-    python -m qxgen.make_plans [checkpoint] [large] [batched]
+    python -m qxgen.make_plans [checkpoint] [large] [batched] [serving]
 
 grid4x5_d12_s6_checkpoint.json: the 20-qubit sliced circuit (4x5 grid, depth
 12, six sliced bonds, 256 bitstrings) under the level-aware plan improved by
@@ -16,6 +16,11 @@ flops per call, the same sliced bonds, peak 2^22 entries.
 batched_uneven.json: the 256 circuits of the batched workload, each under
 its level-aware plan improved by local search on the time estimate (about
 half an hour of host time on 7 processes).
+
+serving.json: the 32 resident circuits of the serving workload, each under
+the seeded greedy candidate that, sliced until its intermediates fit 2^30
+entries, has the smallest time estimate for 256 bitstrings, improved by
+local search on that estimate.
 """
 import json
 import os
@@ -95,6 +100,40 @@ def batched_plans(workers=7):
             "plans": plans}
 
 
+SERVING_MAX_PEAK = 30  # 2^30 complex64 entries = 8 GB per intermediate
+SERVING_PLAN_BITS = 256  # bitstrings per call the serving plans are ranked for
+
+
+def serving_plan(j, trials=10, iters=5000):
+    """Resident circuit j of the serving workload: seeded greedy candidates, each sliced by tree trimming
+    until every intermediate fits 2^30 entries, ranked by the time estimate of a call of 256 bitstrings
+    (fitted_plan), then local search on that estimate."""
+    from .plan import executed_cost, executed_time, fitted_plan, plan_cost
+    import numpy as np
+    _, circ, _ = W.serving_base(j)
+    n = circ.n_qubits
+    legs, _, open_edges = network_legs(n, [g.qubits for g in circ.gates], np.zeros(n, np.uint8))
+    n_out = n - len(open_edges)
+    no_slice = list(open_edges) + [legs[t][0] for t in range(len(legs) - n_out, len(legs))]
+    nb = SERVING_PLAN_BITS
+    order, sliced, _ = fitted_plan(legs, trials, 5000 + j + 700000, no_slice, n_out, nb, SERVING_MAX_PEAK)
+    order, t, _ = local_search_plan(legs, order, sliced, n_out, nb, SERVING_MAX_PEAK, iters, j, objective="time")
+    return {"j": j, "circuit_sha256": W.circuit_digest(circ), "order": [list(p) for p in order],
+            "sliced": [int(e) for e in sliced], "n_bits": nb, "max_peak": SERVING_MAX_PEAK,
+            "peak": plan_cost(legs, order, sliced)[0],
+            "executed_flops": int(executed_cost(legs, order, sliced, n_out, nb)), "estimated_s": t,
+            "estimated_s_1bit": executed_time(legs, order, sliced, n_out, 1)}
+
+
+def serving_plans(workers=7):
+    import multiprocessing as mp
+    with mp.get_context("spawn").Pool(workers) as pool:
+        plans = pool.map(serving_plan, range(32), chunksize=1)
+    return {"made_by": "per circuit: fitted_plan (10 trials per setting, seed 705000 + j, sliced to 2^30 entries, "
+                       "ranked for 256 bitstrings), then local_search_plan (5000 rotations, seed j, objective time)",
+            "plans": plans}
+
+
 def _write(name, d):
     path = os.path.join(HERE, name)
     with open(path, "w") as f:
@@ -110,6 +149,12 @@ if __name__ == "__main__":
         _write("grid4x5_d12_s6_checkpoint.json", checkpoint_plan())
     if "large" in which:
         _write("grid6x6_d14_s10_open6_ls.json", large_plan())
+    if "serving" in which:
+        d = serving_plans()
+        path = os.path.join(HERE, "serving.json")
+        with open(path, "w") as f:
+            json.dump(d, f)
+        print(path, [round(p["estimated_s"], 3) for p in d["plans"]])
     if "batched" in which:
         d = batched_plans()
         path = os.path.join(HERE, "batched_uneven.json")

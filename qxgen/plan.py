@@ -342,6 +342,29 @@ def level_aware_plan(legs, trials, seed, n_slice, open_edges, n_outputs, n_bits,
     return best[1], best[2], best[0][0], best[0][1]
 
 
+def fitted_plan(legs, trials, seed, open_edges, n_outputs, n_bits, max_peak,
+                settings=((1.0, 0.6), (0.75, 0.3), (0.75, 0.6), (0.5, 0.6), (0.25, 0.3), (1.0, 1.0), (1.0, 0.2))):
+    """Seeded greedy candidates (as level_aware_plan), each sliced by tree trimming with as few bonds as
+    keep every intermediate within max_peak legs (Sec. III-A: slicing trades memory for more
+    contractions); the candidate with the smallest executed_time for n_bits bitstrings wins (ties: fewer
+    sliced bonds, earlier candidate).  Returns (order, sliced, estimated seconds)."""
+    rng = SplitMix64(seed)
+    orders = [_greedy(legs)]
+    for alpha, temp in settings:
+        for _ in range(trials):
+            orders.append(_greedy(legs, rng, temp, alpha))
+    best = None
+    for k, order in enumerate(orders):
+        sliced = []
+        while plan_cost(legs, order, sliced)[0] > max_peak:
+            sliced = tree_trim_slices(legs, order, len(sliced) + 1, seed + k, open_edges)
+        t = executed_time(legs, order, sliced, n_outputs, n_bits)
+        key = (t, len(sliced), k)
+        if best is None or key < best[0]:
+            best = (key, order, sliced)
+    return best[1], best[2], best[0][0]
+
+
 def _order_to_tree(n_leaves, order):
     return {n_leaves + t: (a, b) for t, (a, b) in enumerate(order)}, n_leaves + len(order) - 1
 

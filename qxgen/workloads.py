@@ -11,7 +11,7 @@ circuits on qubit grids (Sec. IV-B); these seeded circuits stand in for them.
 * large:   6x6 grid, depth 14, 10 sliced bonds (1024 slices), qubits 30..35
            left open (64 amplitudes per contraction), peak <= 2^28 entries.
 * batched: 256 circuits, n ~ U{16..28} on near-square grids, depth ~ U{8..16},
-           S ~ U{0..8}, 1..64 bitstrings each.
+           S ~ U{0..8}, 1..64 bitstrings each, every one under its stored plan.
 * serving: 32 circuits, n ~ U{20..40}, depth ~ U{10..16}, plans sliced until
            the peak intermediate fits 8 GB of complex64 (2^30 entries).
 """
@@ -259,22 +259,9 @@ def batched_circuit(j):
                      "estimated_s": d["estimated_s"]})
 
 
-BATCHED_MAX_PEAK_RANK = 18
-
-
-def batched_members(count=256, max_peak_rank=BATCHED_MAX_PEAK_RANK):
-    """Circuits of the batched workload that run in the one persistent launch.
-
-    A circuit joins when its plan's largest per-pair intermediate has at most
-    2^max_peak_rank entries (2 MiB of complex64), so every CTA's scratch stays
-    small; the heavy tail of the draw (28-qubit depth-16 circuits whose
-    per-pair cost reaches 1e13 flop) is listed by batched_excluded().
-    """
-    return [batched_circuit(j) for j in range(count) if batched_circuit(j).peak_rank <= max_peak_rank]
-
-
-def batched_excluded(count=256, max_peak_rank=BATCHED_MAX_PEAK_RANK):
-    return [batched_circuit(j) for j in range(count) if batched_circuit(j).peak_rank > max_peak_rank]
+def batched_members(count=256):
+    """All circuits of the batched workload under their stored plans."""
+    return [batched_circuit(j) for j in range(count)]
 
 
 def serving_specs(count=32):
@@ -283,13 +270,50 @@ def serving_specs(count=32):
     return [(20 + rng.randint(21), 10 + rng.randint(7)) for _ in range(count)]
 
 
-@functools.lru_cache(maxsize=None)
-def serving_circuit(j, peak_rank=30):
-    """Resident circuit j of the serving workload, sliced until its peak fits 2^peak_rank entries."""
+def serving_base(j):
+    """(name, circuit, bitstring) of resident circuit j of the serving workload (no plan)."""
     n, depth = serving_specs()[j]
     cseed = 5000 + j
     rows, cols = near_square_shape(n)
     circ = random_grid_circuit(rows, cols, depth, cseed, n=n)
-    bits = random_bitstrings(n, 1, cseed + 500000)
-    return _workload(f"serving{j}_n{n}_d{depth}", circ, np.zeros(n, np.uint8), 0, cseed, bits, trials=1,
+    return f"serving{j}_n{n}_d{depth}", circ, random_bitstrings(n, 1, cseed + 500000)
+
+
+@functools.lru_cache(maxsize=None)
+def serving_circuit_greedy(j, peak_rank=30):
+    """Resident circuit j of the serving workload under a seeded greedy plan, sliced until its peak fits
+    2^peak_rank entries."""
+    name, circ, bits = serving_base(j)
+    n, depth = serving_specs()[j]
+    return _workload(name, circ, np.zeros(n, np.uint8), 0, 5000 + j, bits, trials=1,
                      peak_rank=peak_rank, meta={"n": n, "depth": depth, "j": j})
+
+
+@functools.lru_cache(maxsize=None)
+def _serving_plans():
+    import json
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "plans", "serving.json")
+    with open(path) as f:
+        return json.load(f)["plans"]
+
+
+@functools.lru_cache(maxsize=None)
+def serving_circuit(j):
+    """Resident circuit j of the serving workload under its stored plan (qxgen/plans/serving.json,
+    written by qxgen.make_plans), checked against the circuit and its recorded cost."""
+    name, circ, bits = serving_base(j)
+    d = _serving_plans()[j]
+    n, depth = serving_specs()[j]
+    om = np.zeros(n, np.uint8)
+    if d["j"] != j or d["circuit_sha256"] != circuit_digest(circ):
+        raise ValueError(f"stored serving plan {j} was made for another circuit")
+    order = [tuple(p) for p in d["order"]]
+    legs, _, open_edges = network_legs(n, [x.qubits for x in circ.gates], om)
+    peak, flops = plan_cost(legs, order, d["sliced"])
+    if executed_cost(legs, order, d["sliced"], n - len(open_edges), d["n_bits"]) != d["executed_flops"] or \
+            peak > d["max_peak"]:
+        raise ValueError(f"stored serving plan {j} does not match its recorded cost")
+    return Workload(name, circ, om, order, list(d["sliced"]), bits, peak, flops,
+                    {"n": n, "depth": depth, "j": j, "executed_flops_256": d["executed_flops"],
+                     "estimated_s_256": d["estimated_s"], "estimated_s_1": d["estimated_s_1bit"]})

@@ -1,8 +1,16 @@
-"""Uneven circuits in one persistent launch (group API), through the C ABI.
+"""Uneven circuits in one captured CUDA graph (needs a GPU).
 
-Every member circuit is checked against its own CPU state vector; the
-captured CUDA graph must reproduce the direct run exactly.
+All 256 circuits of the batched workload, each under its stored plan: the
+light ones in the persistent group launch of the C ABI, the heavy ones on the
+batched executor in 3xTF32, enqueued on one stream and captured as one graph.
+Every member is checked against its complex128 state vector (stored by
+tests/golden/make_batched_golden.py, which calls only the oracle); the graph
+replay must reproduce the eager run exactly.  Smaller group cases check the
+persistent launch on its own and the autotuners.
 """
+import json
+import os
+
 import numpy as np
 import pytest
 
@@ -12,6 +20,7 @@ from qxgen import workloads as W
 from ._util import assert_parity
 
 pytestmark = pytest.mark.gpu
+HERE = os.path.dirname(os.path.abspath(__file__))
 
 
 @pytest.fixture(scope="module")
@@ -22,14 +31,15 @@ def qx():
     return mod
 
 
-def _members(count, max_n):
+def _members(count, max_n, max_peak=18):
+    """Light members (persistent-launch sized) of the batched workload with at most max_n qubits."""
     out = []
     for j in range(256):
         n = W.batched_specs()[j][0]
         if n > max_n:
             continue
-        w = W.batched_circuit_greedy(j)
-        if w.peak_rank <= W.BATCHED_MAX_PEAK_RANK:
+        w = W.batched_circuit(j)
+        if w.peak_rank <= max_peak:
             out.append(w)
         if len(out) == count:
             break
@@ -44,6 +54,33 @@ def _group(qx, ws, ctas_per_sm=0):
     bits = [torch.from_numpy(w.bitstrings).cuda() for w in ws]
     torch.cuda.synchronize()
     return qx.Group(cs, bits, ctas_per_sm), cs
+
+
+def test_all_256_members_in_one_graph_vs_statevectors(qx):
+    import torch
+    from paper_2110_09894_gb300.batch import UnevenBatch
+    from tests.golden.make_batched_golden import case_digest
+    with open(os.path.join(HERE, "golden", "batched_statevector.json")) as f:
+        recs = {r["j"]: r for r in json.load(f)["circuits"]}
+    ws = W.batched_members()
+    assert len(ws) == 256 and len(recs) == 256
+    b = UnevenBatch(ws, precision=qx.QX_PREC_3XTF32)
+    assert b.light and b.heavy  # both kinds of member are in the batch
+    b.capture()
+    eager = b.amplitudes()
+    for a in b.d_amps:
+        a.zero_()
+    b.replay()
+    torch.cuda.synchronize()
+    b.check()
+    got = b.amplitudes()
+    for w, a, e in zip(ws, got, eager):
+        assert np.array_equal(a, e), w.name
+        r = recs[w.meta["j"]]
+        assert r["digest"] == case_digest(w), f"{w.name}: circuit changed; regenerate the golden file"
+        ref = (np.array(r["re"]) + 1j * np.array(r["im"])).reshape(a.shape)
+        assert_parity(a, ref, what=w.name)
+    b.close()
 
 
 def test_group_matches_statevectors(qx):
@@ -104,3 +141,30 @@ def test_autotuner_picks_and_caches(qx, tmp_path, monkeypatch):
     for w, a in zip(ws, g.amplitudes()):
         ref = oracle.sv_amplitudes(w.n_qubits, w.gates, w.open_mask, w.bitstrings)
         assert_parity(a, ref)
+
+
+def test_uneven_autotuner_picks_settings_and_caches(qx, tmp_path, monkeypatch):
+    """Tile family and slice-batch size of heavy members, persistent grid of light ones: every choice is
+    timed, cached, and gives amplitudes within the tolerance of the state vector."""
+    import torch
+    from paper_2110_09894_gb300 import autotune
+    monkeypatch.setattr(autotune, "CACHE", str(tmp_path / "tune.json"))
+    light = _members(3, 18)
+    heavy = [w for w in (W.batched_circuit(j) for j in range(256))
+             if w.peak_rank > 18 and w.n_qubits <= 22][:2]
+    assert len(heavy) == 2
+    ws = light + heavy
+    b, choice, ms = autotune.tuned_uneven(ws, precision=qx.QX_PREC_3XTF32, ctas_candidates=(1, 2),
+                                          heavy_settings=autotune.HEAVY_SETTINGS[:3], min_share=0.0)
+    assert choice["ctas_per_sm"] in (1, 2) and set(ms["light_ctas_per_sm"]) == {"1", "2"}
+    assert all(f"heavy{i}" in ms for i in b.heavy)
+    b2, choice2, _ = autotune.tuned_uneven(ws, precision=qx.QX_PREC_3XTF32)  # from the cache, no timing
+    assert choice2 == choice
+    b.capture()
+    b.replay()
+    torch.cuda.synchronize()
+    for w, a in zip(ws, b.amplitudes()):
+        ref = oracle.sv_amplitudes(w.n_qubits, w.gates, w.open_mask, w.bitstrings)
+        assert_parity(a, ref, what=w.name)
+    b.close()
+    b2.close()

@@ -142,3 +142,45 @@ def test_parts_of_a_slice_sum_add_like_one_call(serve):
     while not qx.qx_poll(c.h, r):
         pass
     c.close()
+
+
+def _mirror(rows, cols, depth, seed, n_slice):
+    """U U^dagger on a rows x cols grid: amp(x) = 1 for x = 0...0 and 0 for every other x, exactly."""
+    from qxgen.workloads import make_plan
+    u = C.random_grid_circuit(rows, cols, depth, seed)
+    m = u.then(u.inverse())
+    om = np.zeros(m.n_qubits, np.uint8)
+    order, sliced, peak, flops = make_plan(m, om, n_slice, seed + 700000, trials=2)
+    from qxgen.workloads import Workload
+    return Workload(f"mirror{rows}x{cols}_d{depth}x2", m, om, order, sliced, np.zeros((1, m.n_qubits), np.uint8),
+                    peak, flops)
+
+
+def test_serving_circuits_of_the_workload_and_mirror_pins(serve):
+    """Requests on two resident circuits of the serving workload (20 qubits, their stored plans) against
+    the state vector, and on 36- and 40-qubit mirror circuits, whose amplitudes are known exactly (1 at
+    0...0, 0 elsewhere), in one busy mix: each result also equals the same request served alone."""
+    from qxgen import workloads as W
+    ws = [W.serving_circuit(7), W.serving_circuit(14), _mirror(6, 6, 4, 9141, 2), _mirror(5, 8, 4, 9144, 3)]
+    assert [w.n_qubits for w in ws] == [20, 20, 36, 40]
+    reqs = serve.poisson_requests(len(ws), lambda i: ws[i].n_qubits, rate=400.0, duration=0.05, max_bits=16, seed=9)
+    for r in reqs:  # every request on a mirror circuit also asks for 0...0
+        if ws[r.circuit].n_qubits > 20:
+            r.bits[0] = 0
+    assert len(reqs) >= 10 and {r.circuit for r in reqs} == {0, 1, 2, 3}
+    srv = serve.Server(ws, precision=1, max_bits=64, chunk_flops=1e9, max_lanes_per_circuit=2)
+    done = srv.run(reqs, deadline=300)
+    assert len(done) == len(reqs)
+    for r in done:
+        w = ws[r.circuit]
+        if w.n_qubits == 20:
+            ref = oracle.sv_amplitudes(w.n_qubits, w.gates, w.open_mask, r.bits)
+        else:
+            ref = np.all(r.bits == 0, axis=1).astype(complex)[:, None]
+        assert_parity(r.amps, ref, what=w.name)
+    srv.close()
+    probe = max(done, key=lambda r: len(r.bits) + 100 * (ws[r.circuit].n_qubits == 40))
+    alone = serve.Server(ws, precision=1, max_bits=64, chunk_flops=1e9)
+    one = alone.run([serve.Request(0, probe.circuit, probe.bits, 0.0)], deadline=120)
+    assert_parity(one[0].amps, probe.amps)
+    alone.close()
