@@ -147,6 +147,28 @@ int qx_workspace_size(qx_handle h, int64_t max_bits, int64_t items, int64_t* byt
  * plan unbinds.  QX_ENOMEM if not even one pair fits. */
 int qx_bind_workspace(qx_handle h, void* dptr, int64_t bytes, int64_t max_bits);
 
+/* A workspace in two parts, so that handles whose calls never overlap on the
+ * GPU (enqueued one after another on one stream) can share the larger one
+ * (the paper has no counterpart; a batch of uneven circuits contracted in
+ * turn needs the batch regions of only one circuit at a time).
+ *   fixed part  what a handle keeps between calls: its network's tensors,
+ *               bitstrings, FP64 accumulators, invariant intermediates and
+ *               programs (its own buffer);
+ *   batch part  the per-slice and per-pair intermediates of one batch of
+ *               (slice, bitstring) pairs, which a call overwrites from the
+ *               start: it may be shared by handles whose calls run in stream
+ *               order, never by calls that overlap.
+ * qx_workspace_parts gives both sizes for calls of up to max_bits
+ * bitstrings in batches of `items` pairs (items <= 0: one pair);
+ * qx_bind_workspace_parts binds caller-owned device buffers (256-byte
+ * aligned, kept alive by the caller until the next bind or qx_destroy;
+ * batches are sized to fill the batch part).  Batched executor only
+ * (QX_EINVAL otherwise); QX_ENOMEM when the fixed part is too small or the
+ * batch part holds no pair.  Requires a plan; setting a new plan unbinds. */
+int qx_workspace_parts(qx_handle h, int64_t max_bits, int64_t items, int64_t* fixed_bytes, int64_t* batch_bytes);
+int qx_bind_workspace_parts(qx_handle h, void* d_fixed, int64_t fixed_bytes, void* d_batch, int64_t batch_bytes,
+                            int64_t max_bits);
+
 /* Contract for n_bits bitstrings (host, n_bits x n_qubits bytes of 0/1; bytes
  * at open qubits are ignored) and write amplitudes to amps_out (host,
  * caller-owned, n_bits x 2^n_open x {re, im} doubles).  Copies the

@@ -25,7 +25,10 @@ class UnevenBatch:
     precision applies to the heavy members (the persistent launch runs complex64);
     settings maps a heavy member's index to autotuned Contractor options
     ({"max_items": .., "gemm_min_bits": ..}); mem_budget caps the heavy members'
-    workspaces together (bytes, default 60% of the free device memory)."""
+    workspaces together (bytes, default 60% of the free device memory): each
+    keeps its own fixed part, and all share one buffer for their batch regions
+    (they run in turn on one stream), as large as the largest whole-call need
+    or what the budget leaves."""
 
     def __init__(self, workloads, device=0, precision=qx.QX_PREC_3XTF32, ctas_per_sm=0, settings=None,
                  mem_budget=None, stream=None):
@@ -50,37 +53,37 @@ class UnevenBatch:
                 self.light_members = members
             free, _ = torch.cuda.mem_get_info(self.dev)
             budget = int(mem_budget if mem_budget is not None else 0.6 * free)
+            # the heavy members run one after another on the batch's stream, so they share one buffer for
+            # their per-slice and per-pair regions (qx_bind_workspace_parts); each keeps its own fixed part
             self.heavy_members = {}
             need = {i: self._sizes(i, settings.get(i, {})) for i in self.heavy}
-            total_min = sum(lo for lo, _ in need.values())
-            if total_min > budget:
-                raise MemoryError(f"the heavy members need {total_min} bytes of workspace at least; {budget} available")
-            # each heavy member gets what a whole call needs if everything fits, else its minimum plus a
-            # share of the rest in proportion to what it would still use
-            total_full = sum(hi for _, hi in need.values())
-            extra = budget - total_min
+            fixed = sum(f for f, _, _ in need.values())
+            lo = max((b1 for _, b1, _ in need.values()), default=0)
+            hi = max((bn for _, _, bn in need.values()), default=0)
+            batch_bytes = min(hi, budget - fixed)
+            if self.heavy and batch_bytes < lo:
+                raise MemoryError(f"the heavy members need {fixed + lo} bytes at least; {budget} available")
+            self.batch_buffer = (torch.empty(int(batch_bytes), dtype=torch.uint8, device=self.dev)
+                                 if self.heavy else None)
             for i in self.heavy:
-                lo, hi = need[i]
-                ws = hi if total_full <= budget else lo + int(extra * (hi - lo) / max(total_full - total_min, 1))
                 s = settings.get(i, {})
-                c = self._contractor(i, precision, max_items=s.get("max_items", 0),
-                                     gemm_min_bits=s.get("gemm_min_bits", 0), workspace_bytes=ws)
-                self.heavy_members[i] = c
+                self.heavy_members[i] = self._contractor(i, precision, max_items=s.get("max_items", 0),
+                                                         gemm_min_bits=s.get("gemm_min_bits", 0),
+                                                         batch_buffer=self.batch_buffer)
                 w = self.workloads[i]
                 self.d_amps[i] = torch.empty((len(w.bitstrings), 1 << w.n_open, 2), dtype=torch.float64,
                                              device=self.dev)
         self.graph = None
 
     def _contractor(self, i, precision, executor=qx.EXEC_BATCHED, max_items=0, gemm_min_bits=0,
-                    workspace_bytes=None):
+                    batch_buffer=None):
         w = self.workloads[i]
         return qx.Contractor(w.n_qubits, w.gates, w.open_mask, w.order, w.sliced, len(w.bitstrings),
-                             device=self.dev.index, precision=precision, max_items=max_items,
-                             workspace_bytes=workspace_bytes, stream=self.stream, executor=executor,
-                             gemm_min_bits=gemm_min_bits)
+                             device=self.dev.index, precision=precision, max_items=max_items, stream=self.stream,
+                             executor=executor, gemm_min_bits=gemm_min_bits, batch_buffer=batch_buffer)
 
     def _sizes(self, i, s):
-        """(smallest, whole-call) workspace bytes of heavy member i under options s."""
+        """(fixed part, batch part for one pair, batch part for a whole call) of heavy member i, bytes."""
         w = self.workloads[i]
         h = qx.qx_create(-1, precision=self.precision, max_items=s.get("max_items", 0),
                          gemm_min_bits=s.get("gemm_min_bits", 0))
@@ -90,7 +93,8 @@ class UnevenBatch:
             nb = len(w.bitstrings)
             pairs = (1 << len(w.sliced)) * nb
             cap = s.get("max_items", 0) or pairs
-            return qx.qx_workspace_size(h, nb, 1), qx.qx_workspace_size(h, nb, min(cap, pairs))
+            fixed, one = qx.qx_workspace_parts(h, nb, 1)
+            return fixed, one, qx.qx_workspace_parts(h, nb, min(cap, pairs))[1]
         finally:
             qx.qx_destroy(h)
 

@@ -168,6 +168,7 @@ struct qx_ctx {
     bool memo = false;       // keep the invariant intermediates across calls (qx_set_memo)
     bool inv_ready = false;  // the bound workspace holds them
     char* static_err = nullptr;  // error flag of the last static-scratch call, until qx_device_status reads it
+    char* wb = nullptr;          // qx_bind_workspace_parts: the batch regions' own buffer (else inside ws)
     // Parts of one compensated slice sum (qx_submit_part): the next contraction clears the FP64
     // accumulators first (part_clear) and writes the amplitudes at the end (part_final); a sum left
     // open continues at slice part_next with the same bitstrings.
@@ -1137,8 +1138,8 @@ static void place_regions(qx_ctx* h, int64_t fixed, int64_t items, int64_t slice
     h->slices_cap = slices;
 }
 
-static float2* item_base(const qx_ctx* h) { return (float2*)(h->ws + h->off_item); }
-static float2* slice_base(const qx_ctx* h) { return (float2*)(h->ws + h->off_slice); }
+static float2* item_base(const qx_ctx* h) { return (float2*)((h->wb ? h->wb : h->ws) + h->off_item); }
+static float2* slice_base(const qx_ctx* h) { return (float2*)((h->wb ? h->wb : h->ws) + h->off_slice); }
 static float2* inv_base(const qx_ctx* h) { return (float2*)(h->ws + h->off_inv); }
 
 // device address and item stride of a storage
@@ -2018,6 +2019,7 @@ static void unbind(qx_ctx* h) {
         cudaFree(h->ws);
     }
     h->ws = nullptr;
+    h->wb = nullptr;
     h->ws_bytes = 0;
     h->ws_owned = false;
     h->items_cap = 0;
@@ -2073,6 +2075,49 @@ int qx_bind_workspace(qx_handle h, void* dptr, int64_t bytes, int64_t max_bits) 
     h->ws_bytes = bytes;
     h->max_bits = max_bits;
     place_regions(h, fixed, items, slices);
+    h->leaves_on_device = false;
+    h->pops_on_device = false;
+    h->waves_on_device = false;
+    return QX_OK;
+}
+
+int qx_workspace_parts(qx_handle h, int64_t max_bits, int64_t items, int64_t* fixed_bytes, int64_t* batch_bytes) {
+    if (!h || !fixed_bytes || !batch_bytes) return QX_EINVAL;
+    if (!h->have_plan) return fail(h, QX_ESTATE, "qx_workspace_parts before qx_set_plan");
+    if (max_bits < 1) return fail(h, QX_EINVAL, "max_bits < 1");
+    if (items < 1) items = 1;
+    int64_t fixed;
+    layout(h, max_bits, &fixed);
+    const int64_t slices = h->slice_entries ? std::min<int64_t>(h->n_slices, items) : 0;
+    *fixed_bytes = fixed;
+    *batch_bytes = align_up(slices * h->slice_entries * 8, 256) + items * h->item_entries * 8;
+    return QX_OK;
+}
+
+int qx_bind_workspace_parts(qx_handle h, void* d_fixed, int64_t fixed_bytes, void* d_batch, int64_t batch_bytes,
+                            int64_t max_bits) {
+    if (!h) return QX_EINVAL;
+    if (h->device < 0) return fail(h, QX_ESTATE, "host-only handle has no device");
+    if (!h->have_plan) return fail(h, QX_ESTATE, "qx_bind_workspace_parts before qx_set_plan");
+    if (max_bits < 1) return fail(h, QX_EINVAL, "max_bits < 1");
+    if (!d_fixed || !d_batch) return fail(h, QX_EINVAL, "null buffer");
+    if (((uintptr_t)d_fixed) % 256 || ((uintptr_t)d_batch) % 256)
+        return fail(h, QX_EINVAL, "workspace parts must be 256-byte aligned");
+    if (persist_member(h) || persist_active(h))
+        return fail(h, QX_EINVAL, "a split workspace is for the batched executor");
+    unbind(h);
+    int64_t fixed, items = 0, slices = 0;
+    layout(h, max_bits, &fixed);
+    if (fixed_bytes < fixed)
+        return fail(h, QX_ENOMEM, "fixed part of %lld bytes; need %lld", (long long)fixed_bytes, (long long)fixed);
+    if (!fit_regions(h, batch_bytes, max_bits, &items, &slices))
+        return fail(h, QX_ENOMEM, "batch part of %lld bytes holds no (slice, bitstring) pair; need %lld",
+                    (long long)batch_bytes, (long long)(256 + (h->item_entries + h->slice_entries) * 8));
+    h->ws = (char*)d_fixed;
+    h->wb = (char*)d_batch;
+    h->ws_bytes = fixed_bytes;
+    h->max_bits = max_bits;
+    place_regions(h, 0, items, slices);
     h->leaves_on_device = false;
     h->pops_on_device = false;
     h->waves_on_device = false;
@@ -2441,6 +2486,8 @@ int qx_internal_contract_in(qx_ctx* h, char* buf, int64_t buf_bytes, const uint8
                     (long long)n_bits, (long long)(fixed + 256 + (h->item_entries + h->slice_entries) * 8),
                     (long long)buf_bytes);
     }
+    char* const saved_wb = h->wb;
+    h->wb = nullptr;
     h->ws = buf;
     h->ws_bytes = buf_bytes;
     h->ws_owned = false;
@@ -2456,6 +2503,7 @@ int qx_internal_contract_in(qx_ctx* h, char* buf, int64_t buf_bytes, const uint8
     if (rc == QX_OK) rc = contract_impl(h, d_bits, n_bits, 0, h->n_slices, d_amps);
     if (rc == QX_OK) h->static_err = buf + h->off_err;  // read by the next qx_device_status
     restore();
+    h->wb = saved_wb;
     return rc;
 }
 

@@ -26,7 +26,8 @@ EXPORTS = ("qx_create", "qx_destroy", "qx_last_error", "qx_set_options", "qx_bui
            "qx_profile_read", "qx_contract_device_static", "qx_device_status", "qx_group_create",
            "qx_group_scratch_size", "qx_group_bind", "qx_group_run", "qx_group_last_error", "qx_group_destroy",
            "qx_set_graphs", "qx_set_streams", "qx_describe_plan", "qx_submit", "qx_poll", "qx_esup_accept",
-           "qx_esup_sample", "qx_set_memo", "qx_submit_part")
+           "qx_esup_sample", "qx_set_memo", "qx_submit_part", "qx_workspace_parts",
+           "qx_bind_workspace_parts")
 QX_STATIC_SCRATCH_BYTES = 64 << 20
 KERNEL_KINDS = ("permute", "small", "gemm", "sum", "tc_prep", "tc_gemm", "persist", "wave", "small_flat", "tc_direct")
 
@@ -70,6 +71,8 @@ def load(path=None):
         "qx_set_plan": ([vp, vp, i64, vp, i32, ctypes.POINTER(i64)], ctypes.c_int),
         "qx_workspace_size": ([vp, i64, i64, ctypes.POINTER(i64)], ctypes.c_int),
         "qx_bind_workspace": ([vp, vp, i64, i64], ctypes.c_int),
+        "qx_workspace_parts": ([vp, i64, i64, ctypes.POINTER(i64), ctypes.POINTER(i64)], ctypes.c_int),
+        "qx_bind_workspace_parts": ([vp, vp, i64, vp, i64, i64], ctypes.c_int),
         "qx_contract": ([vp, vp, i64, vp], ctypes.c_int),
         "qx_contract_device": ([vp, vp, i64, vp], ctypes.c_int),
         "qx_contract_slices": ([vp, vp, i64, i64, i64, vp], ctypes.c_int),
@@ -172,6 +175,18 @@ def qx_workspace_size(h, max_bits, items):
     b = ctypes.c_int64()
     _check(h, load().qx_workspace_size(h, int(max_bits), int(items), ctypes.byref(b)))
     return b.value
+
+
+def qx_workspace_parts(h, max_bits, items):
+    """(fixed bytes, batch bytes) of a two-part workspace."""
+    f, b = ctypes.c_int64(), ctypes.c_int64()
+    _check(h, load().qx_workspace_parts(h, int(max_bits), int(items), ctypes.byref(f), ctypes.byref(b)))
+    return f.value, b.value
+
+
+def qx_bind_workspace_parts(h, d_fixed, fixed_bytes, d_batch, batch_bytes, max_bits):
+    _check(h, load().qx_bind_workspace_parts(h, ctypes.c_void_p(int(d_fixed)), int(fixed_bytes),
+                                             ctypes.c_void_p(int(d_batch)), int(batch_bytes), int(max_bits)))
 
 
 def qx_bind_workspace(h, dptr, nbytes, max_bits):
@@ -308,7 +323,7 @@ class Contractor:
 
     def __init__(self, n_qubits, gate_records, open_mask, order, sliced, max_bits, device=0,
                  precision=QX_PREC_C64, max_items=0, workspace_bytes=None, stream=None, executor=EXEC_AUTO,
-                 no_slice_level=0, gemm_min_bits=0, timeout_cycles=0):
+                 no_slice_level=0, gemm_min_bits=0, timeout_cycles=0, batch_buffer=None):
         import torch
         self.torch = torch
         self.device = torch.device("cuda", device)
@@ -321,6 +336,14 @@ class Contractor:
         self.peak_entries = qx_set_plan(self.h, order, sliced)
         self.n_slices = 1 << len(np.asarray(sliced).reshape(-1))
         self.max_bits = int(max_bits)
+        if batch_buffer is not None:
+            # two-part workspace: own fixed part, batch regions in a caller-shared torch uint8 buffer
+            fixed, _ = qx_workspace_parts(self.h, max_bits, 1)
+            self.workspace = torch.empty(int(fixed), dtype=torch.uint8, device=self.device)
+            self.batch_buffer = batch_buffer
+            qx_bind_workspace_parts(self.h, self.workspace.data_ptr(), int(fixed), batch_buffer.data_ptr(),
+                                    batch_buffer.numel(), max_bits)
+            return
         if workspace_bytes is None and executor == EXEC_GROUP_MEMBER:
             workspace_bytes = qx_workspace_size(self.h, max_bits, 1)  # pair scratch comes from the group
         if workspace_bytes is None:

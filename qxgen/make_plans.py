@@ -125,7 +125,7 @@ def serving_plan(j, trials=10, iters=5000):
             "estimated_s_1bit": executed_time(legs, order, sliced, n_out, 1)}
 
 
-def serving_plans(workers=7):
+def serving_plans(workers=3):
     import multiprocessing as mp
     with mp.get_context("spawn").Pool(workers) as pool:
         plans = pool.map(serving_plan, range(32), chunksize=1)

@@ -312,7 +312,7 @@ def executed_time(legs, order, sliced, n_outputs, n_bits, rates=GB300_RATES, ten
 
 def level_aware_plan(legs, trials, seed, n_slice, open_edges, n_outputs, n_bits, max_peak=None,
                      settings=((1.0, 0.6), (0.75, 0.3), (0.75, 0.6), (0.5, 0.6), (0.25, 0.3), (1.0, 1.0),
-                               (1.0, 0.2))):
+                               (1.0, 0.2)), max_pair_peak=None):
     """Seeded greedy orders, each sliced by tree trimming, ranked by executed_cost.
 
     Same candidates as randomized_greedy (Gumbel-perturbed greedy orders under
@@ -332,6 +332,8 @@ def level_aware_plan(legs, trials, seed, n_slice, open_edges, n_outputs, n_bits,
         sliced = tree_trim_slices(legs, order, n_slice, seed + k, open_edges) if n_slice else []
         peak, _ = plan_cost(legs, order, sliced)
         if max_peak is not None and peak > max_peak:
+            continue
+        if max_pair_peak is not None and pair_peak(legs, order, sliced, n_outputs) > max_pair_peak:
             continue
         ex = executed_cost(legs, order, sliced, n_outputs, n_bits)
         key = (ex, peak, k)
@@ -365,6 +367,26 @@ def fitted_plan(legs, trials, seed, open_edges, n_outputs, n_bits, max_peak,
     return best[1], best[2], best[0][0]
 
 
+def pair_peak(legs, order, sliced, n_outputs):
+    """Largest rank (legs, fixed bonds removed) of an intermediate that an output bit reaches: those are
+    stored once per (slice, bitstring) pair, so they set the memory a batch of pairs needs."""
+    sl = frozenset(sliced)
+    first_out = len(legs) - n_outputs
+    out_wires = frozenset(e for t in range(first_out, len(legs)) for e in legs[t])
+    fixed = sl | out_wires
+    sets = [frozenset(l) for l in legs]
+    by_bits = [bool(out_wires & sets[t]) for t in range(len(legs))]
+    peak = 0
+    for a, b in order:
+        s = sets[a] ^ sets[b]
+        d = by_bits[a] or by_bits[b]
+        sets.append(s)
+        by_bits.append(d)
+        if d:
+            peak = max(peak, len(s - fixed))
+    return peak
+
+
 def _order_to_tree(n_leaves, order):
     return {n_leaves + t: (a, b) for t, (a, b) in enumerate(order)}, n_leaves + len(order) - 1
 
@@ -388,17 +410,22 @@ def _tree_to_order(n_leaves, children, root):
     return order
 
 
-def local_search_plan(legs, order, sliced, n_outputs, n_bits, max_peak, iters, seed, objective="flops"):
+def local_search_plan(legs, order, sliced, n_outputs, n_bits, max_peak, iters, seed, objective="flops",
+                      max_pair_peak=None):
     """Local optimisation of a plan (this project's own step beyond the paper's planner): seeded
     random rotations of the contraction tree, ((A, B), C) -> ((A, C), B), each kept when the plan
     costs less per call with every intermediate within max_peak legs; the sliced bonds stay as given.
     objective "flops": executed flops per call (executed_cost); "time": the roofline estimate of
-    executed_time.  Returns (order, cost, accepted moves).
+    executed_time; or a function (legs, order, sliced, n_outputs, n_bits) -> cost.  max_pair_peak, when
+    given, also bounds the intermediates stored per (slice, bitstring) pair (pair_peak).  Returns (order,
+    cost, accepted moves).
     """
     n = len(legs)
     children, root = _order_to_tree(n, order)
     internal = sorted(children)
-    if objective == "flops":
+    if callable(objective):
+        cost_of = objective
+    elif objective == "flops":
         cost_of = executed_cost
     elif objective == "time":
         cost_of = executed_time
@@ -418,7 +445,8 @@ def local_search_plan(legs, order, sliced, n_outputs, n_bits, max_peak, iters, s
         old_p, old_x = children[p], children[x]
         children[x], children[p] = (keep, y), (x, move)
         cand = _tree_to_order(n, children, root)
-        ok = plan_cost(legs, cand, sliced)[0] <= max_peak
+        ok = plan_cost(legs, cand, sliced)[0] <= max_peak and (
+            max_pair_peak is None or pair_peak(legs, cand, sliced, n_outputs) <= max_pair_peak)
         cost = cost_of(legs, cand, sliced, n_outputs, n_bits) if ok else None
         if cost is not None and cost < best:
             best, accepted = cost, accepted + 1
