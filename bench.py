@@ -46,9 +46,12 @@ def parse():
     p.add_argument("--workload", default="large", choices=["small", "sliced", "large", "batched", "serving", "sampling"])
     p.add_argument("--sample-batch", type=int, default=1024, help="candidates per contraction when sampling")
     p.add_argument("--samples-per-step", type=int, default=256)
-    p.add_argument("--serve-seconds", type=float, default=20.0, help="arrival window of the serving run")
+    p.add_argument("--serve-seconds", type=float, default=60.0, help="arrival window of the serving run")
     p.add_argument("--serve-rate", type=float, default=200.0, help="mean requests per second (Poisson)")
-    p.add_argument("--serve-max-flops", type=float, default=5e14, help="largest request the server admits")
+    p.add_argument("--serve-max-request-s", type=float, default=1.0,
+                   help="largest estimated service time of one request the server admits")
+    p.add_argument("--serve-max-backlog-s", type=float, default=2.0,
+                   help="estimated work admitted and not yet done beyond which arrivals are shed")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--max-items", type=int, default=0, help="cap on (slice, bitstring) pairs per batch (0 = fill)")
     p.add_argument("--precision", default="3xtf32", choices=list(PRECISIONS),
@@ -366,34 +369,51 @@ def group_bench(args):
 
 
 def serving_bench(args):
-    """Poisson arrivals on the 32 resident serving circuits; sustained throughput and latency."""
+    """Poisson arrivals on the 32 resident serving circuits, in the chosen form and in plain complex64:
+    offered, admitted and completed work, sustained amplitudes/s and latency of completed requests."""
     import torch
     from paper_2110_09894_gb300 import build as qxbuild
     from paper_2110_09894_gb300 import serve
     qxbuild.build()
     ws = [W.serving_circuit(j) for j in range(32)]
-    reqs = serve.poisson_requests(len(ws), lambda i: ws[i].n_qubits, args.serve_rate, args.serve_seconds, 1024, 5000)
-    srv = serve.Server(ws, precision=PRECISIONS[args.precision][0], max_bits=1024,
-                       max_request_flops=args.serve_max_flops)
-    sampler = ClockSampler(0)
-    sampler.start()
-    t0 = time.perf_counter()
-    done = srv.run(reqs, deadline=args.serve_seconds + 30.0)
-    wall = time.perf_counter() - t0
-    clocks = sampler.stop()
-    summ = serve.latency_summary(done)
-    offered_amps = sum(r.bits.shape[0] for r in reqs)
-    line = {"metric": "amplitudes/s", "value": summ["amplitudes"] / wall, "unit": "amplitudes/s", "n_gpus": 1,
-            "steps": 1, "warmup": 0, "ms_per_step": wall * 1e3, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
+    reqs0 = serve.poisson_requests(len(ws), lambda i: ws[i].n_qubits, args.serve_rate, args.serve_seconds, 1024,
+                                   5000)
+    offered_amps = sum(r.bits.shape[0] for r in reqs0)
+
+    def one_run(precision):
+        reqs = [serve.Request(r.rid, r.circuit, r.bits, r.arrival) for r in reqs0]
+        srv = serve.Server(ws, precision=precision, max_bits=1024, max_request_s=args.serve_max_request_s,
+                           max_backlog_s=args.serve_max_backlog_s)
+        sampler = ClockSampler(0)
+        sampler.start()
+        t0 = time.perf_counter()
+        done = srv.run(reqs, deadline=args.serve_seconds + 60.0)
+        wall = time.perf_counter() - t0
+        clocks = sampler.stop()
+        summ = serve.latency_summary(done)
+        out = {"amplitudes_per_s": summ["amplitudes"] / wall, "wall_s": wall, "completed": summ["completed"],
+               "completed_amplitudes": summ["amplitudes"], "admitted": srv.stats["admitted"],
+               "rejected_cost": srv.stats["rejected_cost"], "rejected_busy": srv.stats["rejected_busy"],
+               "rejected_memory": srv.stats["rejected"] - srv.stats["rejected_cost"] - srv.stats["rejected_busy"],
+               "latency_ms": {"p50": summ["p50_ms"], "p99": summ["p99_ms"]},
+               "merged_requests": srv.stats["merged_requests"], "chunks": srv.stats["chunks"],
+               "lanes": srv.stats["lanes"], "clocks": clocks,
+               "servable_circuits": sum(1 for sc in srv.circuits
+                                        if sc.servable and sc.est_a + sc.est_b <= args.serve_max_request_s)}
+        srv.close()
+        return out
+
+    main = one_run(PRECISIONS[args.precision][0])
+    c64 = one_run(0) if args.precision != "c64" else None
+    line = {"metric": "amplitudes/s", "value": main["amplitudes_per_s"], "unit": "amplitudes/s", "n_gpus": 1,
+            "steps": 1, "warmup": 0, "ms_per_step": main["wall_s"] * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
             "config": {"workload": "serving: 32 resident grid circuits (n 20..40, depth 10..16, peak <= 2^30)",
-                       "arrivals": f"Poisson {args.serve_rate}/s for {args.serve_seconds} s",
-                       "requests": len(reqs), "offered_amplitudes": offered_amps},
-            "latency_ms": {"p50": summ["p50_ms"], "p99": summ["p99_ms"]}, "completed": summ["completed"],
-            "rejected": srv.stats["rejected"], "rejected_cost": srv.stats["rejected_cost"],
-            "merged_requests": srv.stats["merged_requests"], "max_request_flops": srv.max_request_flops,
-            "chunks": srv.stats["chunks"], "lanes": srv.stats["lanes"], "clocks": clocks}
-    srv.close()
+                       "arrivals": f"Poisson {args.serve_rate}/s for {args.serve_seconds} s, 1..1024 bitstrings",
+                       "requests": len(reqs0), "offered_amplitudes": int(offered_amps),
+                       "admission": f"memory budget, estimated service <= {args.serve_max_request_s} s, "
+                                    f"admitted backlog <= {args.serve_max_backlog_s} s"},
+            "latency_ms": main["latency_ms"], "served": main, "plain_c64": c64, "clocks": main["clocks"]}
     print(json.dumps(line), flush=True)
 
 

@@ -1,0 +1,48 @@
+"""Time estimate of a contraction call from the library's compiled launch list.
+
+The plan compiler decides, for every pairwise step, the kernel family, the
+operand layouts (and so the permutes) and which operands a launch shares
+between its items; qx_describe_plan lists those launches.  This prices each
+listed launch on one GB300: its bytes (operands read once per item, an
+operand of a lower dependence level once per launch, the result written
+once) at the HBM rate its kernel family reaches, or its complex flops
+(8 M K N) at the family's arithmetic rate, whichever takes longer, plus a
+launch cost, and sums the launches.  The rates were measured per family on
+the 36-qubit sliced workload, where the sum matched the measured step time
+(325 vs 326 ms in 3xTF32).  The server uses it for admission, planners to
+rank plans.
+"""
+from __future__ import annotations
+
+# kernel family -> (complex flop/s, or None for data movement; bytes/s)
+GB300_LAUNCH_RATES = {"permute": (None, 6.0e12), "gather": (20e12, 4.7e12), "tc_direct": (150e12, 4.0e12),
+                      "tc_prep": (174e12, 5.0e12), "gemm": (35e12, 4.0e12), "dot_perm": (35e12, 5.0e12)}
+_LEVEL = {"shared": 0, "slice": 1, "pair": 2}
+
+
+def _regions(field):
+    out = []
+    for part in field.split(",") if field else ():
+        reg, rest = part.split(":")
+        out.append((reg, int(rest.split("+")[1])))
+    return out
+
+
+def launch_list_time(desc, n_slices, n_bits, rates=GB300_LAUNCH_RATES, launch=4e-6):
+    """Seconds of one call over n_slices slices and n_bits bitstrings from a qx_describe_plan listing
+    (launches priced one after another)."""
+    items = (1, n_slices, n_slices * n_bits)
+    total = 0.0
+    for line in desc.splitlines():
+        f = line.split()
+        kind, level = f[2], _LEVEL[f[3]]
+        kv = dict(x.split("=", 1) for x in f[4:] if "=" in x)
+        it = items[level]
+        nbytes = sum(8.0 * e * (it if _LEVEL[r] == level else items[_LEVEL[r]]) for r, e in _regions(kv.get("reads", "")))
+        nbytes += sum(8.0 * e * it for r, e in _regions(kv.get("writes", "")))
+        fr, br = rates.get(kind, (35e12, 4.0e12))
+        t = nbytes / br
+        if fr and "m" in kv:
+            t = max(t, 8.0 * 2.0 ** (int(kv["m"]) + int(kv["k"]) + int(kv["n"])) * it / fr)
+        total += t + launch
+    return total

@@ -22,8 +22,13 @@ while other work is on the GPU:
   host memory, on the lane's stream); completion is polled with ``qx_poll``;
   latency runs from a request's arrival to the host seeing its amplitudes;
 * a request is rejected at arrival if its circuit cannot get a lane within
-  the memory budget or if its estimated work (plan flops x slices x
-  bitstrings) exceeds max_request_flops.
+  the memory budget (admission by memory), if its estimated service time
+  exceeds max_request_s, or if the estimated work already admitted and not
+  yet done plus its own exceeds max_backlog_s (load shedding: under an
+  offered load beyond the GPU, admitted requests keep a bounded latency
+  instead of every request waiting in an unbounded queue).  Service times
+  are estimated from the library's compiled launch list of the circuit's
+  plan (cost.launch_list_time), linear in the number of bitstrings.
 
 The scheduling runs on the host in Python (it only marshals work); every
 contraction step runs in the library's kernels.
@@ -37,6 +42,7 @@ from dataclasses import dataclass, field
 import numpy as np
 
 from . import qx
+from .cost import launch_list_time
 
 
 @dataclass
@@ -47,6 +53,7 @@ class Request:
     arrival: float              # seconds (server clock)
     done: float = -1.0
     amps: np.ndarray | None = None
+    est: float = 0.0            # estimated service seconds (set at admission)
 
 
 @dataclass
@@ -86,13 +93,16 @@ class ServedCircuit:
     n_slices: int = 1
     lane_bytes: int = 0
     servable: bool = True
+    est_a: float = 0.0          # estimated seconds of a request of b bitstrings: est_a + est_b * b
+    est_b: float = 0.0
     lanes: list = field(default_factory=list)
     queue: collections.deque = field(default_factory=collections.deque)
 
 
 class Server:
     def __init__(self, circuits, device=0, precision=qx.QX_PREC_C64, max_bits=1024, mem_budget=None,
-                 chunk_flops=2e11, max_lanes_per_circuit=2, items_per_lane=4096, max_request_flops=5e14):
+                 chunk_flops=2e11, max_lanes_per_circuit=2, items_per_lane=4096, max_request_s=float("inf"),
+                 max_backlog_s=float("inf")):
         import torch
         self.torch = torch
         self.dev = torch.device("cuda", device)
@@ -100,7 +110,9 @@ class Server:
         self.max_bits = max_bits
         self.chunk_flops = chunk_flops
         self.max_lanes = max_lanes_per_circuit
-        self.max_request_flops = max_request_flops
+        self.max_request_s = max_request_s
+        self.max_backlog_s = max_backlog_s
+        self.backlog = 0.0
         free, _ = torch.cuda.mem_get_info(self.dev)
         self.budget = int(mem_budget if mem_budget is not None else free * 0.7)
         self.committed = 0
@@ -118,6 +130,10 @@ class Server:
             items = int(max(1, min(items_per_lane, sc.n_slices * max_bits, fit)))
             sc.lane_bytes = qx.qx_workspace_size(h, max_bits, items)
             sc.servable = sc.lane_bytes <= self.budget
+            desc = qx.qx_describe_plan(h)
+            t1 = launch_list_time(desc, sc.n_slices, 1)
+            sc.est_b = max((launch_list_time(desc, sc.n_slices, 256) - t1) / 255.0, 0.0)
+            sc.est_a = t1 - sc.est_b
             qx.qx_destroy(h)
             self.circuits.append(sc)
         self.clock0 = time.perf_counter()
@@ -146,10 +162,17 @@ class Server:
         if not sc.servable or len(req.bits) > self.max_bits:
             self.stats["rejected"] += 1  # needs more device memory than the budget, or too many bitstrings
             return False
-        if sc.flops_per_slice * sc.n_slices * len(req.bits) > self.max_request_flops:
+        req.est = sc.est_a + sc.est_b * len(req.bits)
+        if req.est > self.max_request_s:
             self.stats["rejected"] += 1  # more work than the server accepts for one request
             self.stats["rejected_cost"] += 1
             return False
+        if self.backlog + req.est > self.max_backlog_s:
+            self.stats["rejected"] += 1  # the GPU is already committed beyond the backlog bound
+            self.stats["rejected_busy"] += 1
+            return False
+        self.backlog += req.est
+        self.stats["admitted"] += 1
         sc.queue.append(req)
         return True
 
@@ -201,6 +224,7 @@ class Server:
             r.amps = amps[k:k + len(r.bits)].copy()
             k += len(r.bits)
             r.done = t_done
+            self.backlog -= r.est
             self.done.append(r)
         lane.batch = None
 
