@@ -839,6 +839,338 @@ __global__ void __launch_bounds__(TC2_THREADS, 1)
 }
 
 // ------------------------------------------------------------------------------------------------
+// The direct 3xTF32 kernel for a B that every item of the launch shares (an invariant operand, such
+// as a gate-sized tensor applied to a large per-slice one) and that one 128-column tile covers
+// (2N = BN), with at most Tc2Kb::MAXK k-stages: B' (hi and lo) of every stage is built once per CTA
+// and stays in shared memory, so per job TMA brings only A and the converter warps only split A into
+// TMEM -- half the converter work and no B traffic per job.  Roles and rings otherwise as in
+// k_gemm_tc2: warps 0 TMA, 1 and 14 MMA (even / odd stages), 2-9 drain, 10-13 convert.
+// ------------------------------------------------------------------------------------------------
+template <int BN>
+struct Tc2Kb {
+    static constexpr uint32_t A = 16384, BRAW = (BN / 2) * 128, BP = BN * 128;
+    static constexpr uint32_t LAND = A;                      // landing slot: a raw A slab (first: raw B)
+    static constexpr uint32_t OFF_BLO = BP, BSLOT = 2 * BP;  // resident B' of one stage: hi, lo
+    static constexpr int MAXK = BN == 128 ? 4 : 8;           // k-stages whose B' stays resident
+    static constexpr int NL = 5, NM = 3;                     // landing slots; A positions in TMEM
+    static constexpr uint32_t SMEM = NL * LAND + MAXK * BSLOT;
+    static constexpr int NTB = 2;                            // accumulator buffers
+    static constexpr uint32_t ACOL = NTB * BN;               // first TMEM column of the A parts
+    static constexpr uint32_t TMEM_COLS = 512;
+};
+
+// B' hi / lo of one stage from its raw slab (BN/2 complex rows of 16 K values): row 2n = (re, -im),
+// row 2n+1 = (im, re), 128-byte swizzled as the MMA descriptors read it
+template <int BN>
+__device__ __forceinline__ void tc2kb_build_b(const uint8_t* braw, uint8_t* bs, int ct) {
+    using L = Tc2Kb<BN>;
+    constexpr int NBC = (BN / 2) * 8 / TC2_CONV;
+    float4 vb[NBC];
+#pragma unroll
+    for (int i = 0; i < NBC; ++i) {
+        const int c = ct + TC2_CONV * i;
+        const int n = c >> 3, j = c & 7;
+        vb[i] = *(const float4*)(braw + n * 128 + ((j ^ (n & 7)) << 4));
+    }
+#pragma unroll
+    for (int i = 0; i < NBC; ++i) {
+        const int c = ct + TC2_CONV * i;
+        const int n = c >> 3, j = c & 7;
+        const float4 v = vb[i];
+        const float4 r0 = make_float4(v.x, -v.y, v.z, -v.w);
+        const float4 r1 = make_float4(v.y, v.x, v.w, v.z);
+        const int ra = 2 * n, rb = 2 * n + 1;
+        const uint32_t oa = ra * 128 + ((j ^ (ra & 7)) << 4), ob = rb * 128 + ((j ^ (rb & 7)) << 4);
+        float4 hi, lo;
+        split4(r0, hi, lo);
+        *(float4*)(bs + oa) = hi;
+        *(float4*)(bs + L::OFF_BLO + oa) = lo;
+        split4(r1, hi, lo);
+        *(float4*)(bs + ob) = hi;
+        *(float4*)(bs + L::OFF_BLO + ob) = lo;
+    }
+}
+
+// A hi / lo of one slab into TMEM: thread (quarter qq, lane) splits row 32 qq + lane into TMEM lane
+// 32 qq + lane, columns ahi (hi) and ahi + 32 (lo)
+__device__ __forceinline__ void tc2kb_split_a(const uint8_t* araw, uint32_t tmem, int qq, int lane, uint32_t ahi) {
+    const int r = 32 * qq + lane;
+    const uint32_t lanes = (uint32_t)(32 * qq) << 16;
+    float4 va[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) va[j] = *(const float4*)(araw + r * 128 + ((j ^ (r & 7)) << 4));
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        float hi[16], lo[16];
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj) {
+            float4 vh, vl;
+            split4(va[4 * h + jj], vh, vl);
+            hi[4 * jj] = vh.x; hi[4 * jj + 1] = vh.y; hi[4 * jj + 2] = vh.z; hi[4 * jj + 3] = vh.w;
+            lo[4 * jj] = vl.x; lo[4 * jj + 1] = vl.y; lo[4 * jj + 2] = vl.z; lo[4 * jj + 3] = vl.w;
+        }
+        tmem_st16(tmem + lanes + ahi + 16 * h, hi);
+        tmem_st16(tmem + lanes + ahi + 32 + 16 * h, lo);
+    }
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
+template <int BN>
+__global__ void __launch_bounds__(TC2_THREADS, 1)
+    k_gemm_tc2kb(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
+                 float* __restrict__ C, int64_t c_is, int N2, int K2, int tiles, int64_t n_items, int a_div,
+                 long long limit, int* err) {
+    // persistent over (item, m tile) jobs: job = blockIdx.x + t * gridDim.x; B' of every k-stage is
+    // resident, A's stages of successive jobs form one sequence g = t * nk + it.  The landing ring
+    // first takes the nk raw B slabs, then the A slabs: both producer and converters walk that one
+    // sequence (q = nk + g for A stage g).
+    using L = Tc2Kb<BN>;
+    constexpr int BK = 32;
+    constexpr int NL = L::NL, NM = L::NM, NTB = L::NTB;
+    constexpr uint32_t IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                               ((uint32_t)(TC_BM >> 4) << 24);
+    extern __shared__ uint8_t dyn[];
+    __shared__ uint64_t full[NL], lfree[NL], mfull[NM], mfree[NM], tfull[NTB], tempty[NTB], drain[2], bready;
+    __shared__ uint32_t tmem_slot;
+    __shared__ int abort_flag;
+    if (*(volatile const int*)err) return;
+    uint8_t* base = (uint8_t*)(((uintptr_t)dyn + 1023) & ~(uintptr_t)1023);
+    auto land = [&](int l) { return base + l * L::LAND; };
+    auto bslot = [&](int it) { return base + NL * L::LAND + it * L::BSLOT; };
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nk = K2 / BK;  // <= L::MAXK (checked by the host)
+    const int64_t jobs = (int64_t)tiles * n_items;
+    const int64_t my_jobs = jobs > blockIdx.x ? (jobs - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    const int64_t total = my_jobs * nk;
+    auto job_of = [&](int64_t t, int64_t* item, int* m0) {
+        const int64_t j = blockIdx.x + t * (int64_t)gridDim.x;
+        *item = j / tiles;
+        *m0 = (int)(j % tiles) * TC_BM;
+    };
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < NL; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&lfree[s], TC2_CONV / 32);
+        }
+        for (int s = 0; s < NM; ++s) {
+            mbar_init(&mfull[s], TC2_CONV / 32);
+            mbar_init(&mfree[s], 1);
+        }
+        for (int b = 0; b < NTB; ++b) {
+            mbar_init(&tfull[b], 1);
+            mbar_init(&tempty[b], 8);
+        }
+        mbar_init(&drain[0], 1);
+        mbar_init(&drain[1], 1);
+        mbar_init(&bready, TC2_CONV / 32);
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(s_addr(&tmem_slot)),
+                     "r"(L::TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_slot;
+
+    if (warp == 0 && lane == 0) {
+        int64_t issued = 0, t = 0, item = 0;
+        int l = 0, it = 0, m0 = 0;
+        uint32_t lph = 0;
+        bool ok = true;
+        for (int s = 0; s < nk && ok; ++s) {  // the raw B slab of every stage
+            if (!mbar_wait(&lfree[l], lph ^ 1u, limit, err) || *(volatile int*)&abort_flag) {
+                atomicExch(&abort_flag, 1);
+                ok = false;
+                break;
+            }
+            mbar_expect_tx(&full[l], L::BRAW);
+            tma_load_3d(land(l), &mapB, s * BK, 0, 0, &full[l]);
+            ++issued;
+            if (++l == NL) {
+                l = 0;
+                lph ^= 1u;
+            }
+        }
+        for (int64_t g = 0; g < total && ok; ++g) {
+            if (!mbar_wait(&lfree[l], lph ^ 1u, limit, err) || *(volatile int*)&abort_flag) {
+                atomicExch(&abort_flag, 1);
+                break;
+            }
+            if (it == 0) job_of(t, &item, &m0);
+            mbar_expect_tx(&full[l], L::A);
+            tma_load_3d(land(l), &mapA, it * BK, m0, (int)(item / a_div), &full[l]);
+            ++issued;
+            if (++it == nk) {
+                it = 0;
+                ++t;
+            }
+            if (++l == NL) {
+                l = 0;
+                lph ^= 1u;
+            }
+        }
+        // the copies in flight land before the CTA exits (immediate unless a wait gave up)
+        for (int64_t q = (issued > NL ? issued - NL : 0); q < issued; ++q)
+            mbar_wait_issued(&full[q % NL], (uint32_t)((q / NL) & 1));
+    } else if ((warp == 1 || warp == 14) && lane == 0) {
+        const int who = warp == 1 ? 0 : 1;
+        const int b = who;
+        bool ok = mbar_wait(&bready, 0, limit, err) && !*(volatile int*)&abort_flag;
+        if (!ok) atomicExch(&abort_flag, 1);
+        int m = who, it = who % nk;
+        uint32_t mph = 0;
+        int64_t u = 0;
+        for (int64_t g = who; g < total && ok; g += 2, ++u) {
+            if (!mbar_wait(&mfull[m], mph, limit, err) ||
+                (u > 0 && !mbar_wait(&tempty[b], (uint32_t)((u - 1) & 1), limit, err)) || *(volatile int*)&abort_flag) {
+                atomicExch(&abort_flag, 1);
+                ok = false;
+                break;
+            }
+            tc_fence_after();
+            const uint32_t st = s_addr(bslot(it));
+            const uint32_t d = tmem + b * BN;
+            const uint32_t acol = L::ACOL + 64 * (uint32_t)m;
+            // the correction products first, the main one last (see k_gemm_tc)
+#pragma unroll
+            for (int kk = 0; kk < BK / 8; ++kk) {
+                const uint32_t ahi = tmem + acol + 8 * kk, alo = ahi + 32;
+                const uint64_t bhi = sdesc(st + kk * 32), blo = sdesc(st + L::OFF_BLO + kk * 32);
+                mma_tf32_ta(d, ahi, blo, IDESC, kk != 0);
+                mma_tf32_ta(d, alo, bhi, IDESC, 1);
+            }
+#pragma unroll
+            for (int kk = 0; kk < BK / 8; ++kk)
+                mma_tf32_ta(d, tmem + acol + 8 * kk, sdesc(st + kk * 32), IDESC, 1);
+            tc_commit(&mfree[m]);
+            tc_commit(&tfull[b]);
+            m += 2;
+            if (m >= NM) {
+                m -= NM;
+                mph ^= 1u;
+            }
+            it += 2;
+            while (it >= nk) it -= nk;
+        }
+        // the MMAs this thread issued finish before TMEM is freed
+        tc_commit(&drain[who]);
+        mbar_wait_issued(&drain[who], 0);
+    } else if (warp >= 10 && warp <= 13) {
+        // converters: first B' of every stage into its resident slot, then A of every stage into TMEM
+        const int ct = threadIdx.x - 320;
+        int l = 0, m = 0;
+        uint32_t lph = 0, mph = 0;
+        bool ok = true;
+        for (int s = 0; s < nk; ++s) {
+            const bool go = mbar_wait(&full[l], lph, limit, err) && !*(volatile int*)&abort_flag;
+            if (!__all_sync(0xffffffffu, go)) {
+                atomicExch(&abort_flag, 1);
+                ok = false;
+                break;
+            }
+            tc2kb_build_b<BN>(land(l), bslot(s), ct);
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic writes -> tensor core
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(s_addr(&lfree[l])) : "memory");
+            if (++l == NL) {
+                l = 0;
+                lph ^= 1u;
+            }
+        }
+        if (ok && lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(s_addr(&bready)) : "memory");
+        for (int64_t g = 0; g < total && ok; ++g) {
+            // one decision per warp: the TMEM stores of the split are warp-wide (.sync.aligned)
+            const bool go = mbar_wait(&full[l], lph, limit, err) && mbar_wait(&mfree[m], mph ^ 1u, limit, err) &&
+                            !*(volatile int*)&abort_flag;
+            if (!__all_sync(0xffffffffu, go)) {
+                atomicExch(&abort_flag, 1);
+                break;
+            }
+            tc_fence_after();  // the MMAs that last read this A position have completed (mfree)
+            tc2kb_split_a(land(l), tmem, warp & 3, lane, L::ACOL + 64 * (uint32_t)m);
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) {
+                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(s_addr(&lfree[l])) : "memory");
+                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(s_addr(&mfull[m])) : "memory");
+            }
+            if (++l == NL) {
+                l = 0;
+                lph ^= 1u;
+            }
+            if (++m == NM) {
+                m = 0;
+                mph ^= 1u;
+            }
+        }
+    } else if (warp >= 2 && warp <= 9) {
+        // drain: TMEM lanes 32 (warp % 4), columns (BN / 2) ((warp - 2) / 4) .. + BN / 2 - 1
+        const int q = warp & 3, half = (warp - 2) >> 2;
+        float tot[BN / 2];
+#pragma unroll
+        for (int j = 0; j < BN / 2; ++j) tot[j] = 0.f;
+        int64_t g = 0;
+        for (int64_t t = 0; t < my_jobs; ++t) {
+            bool ok = true;
+            for (int it = 0; it < nk; ++it, ++g) {
+                const int b = (int)(g & 1);
+                // one decision per warp: the TMEM loads below are warp-wide (.sync.aligned)
+                const bool go = mbar_wait(&tfull[b], (uint32_t)((g >> 1) & 1), limit, err) &&
+                                !*(volatile int*)&abort_flag;
+                if (!__all_sync(0xffffffffu, go)) {
+                    atomicExch(&abort_flag, 1);
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+#pragma unroll
+                for (int c = 0; c < BN / 64; ++c) {
+                    float v[32];
+                    tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + b * BN + (BN / 2) * half + 32 * c, v);
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) tot[32 * c + j] += v[j];
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0)
+                    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(s_addr(&tempty[b])) : "memory");
+            }
+            if (!ok) break;
+            int64_t item;
+            int m0;
+            job_of(t, &item, &m0);
+            float* cb = C + item * c_is + (BN / 2) * half + (int64_t)(m0 + 32 * q + ((lane >> 3) << 3)) * N2 +
+                        ((lane & 7) << 2);
+#pragma unroll
+            for (int b32 = 0; b32 < BN / 64; ++b32) {
+                float* tt = tot + 32 * b32;
+                transpose_q4(tt, lane);
+#pragma unroll
+                for (int r = 0; r < 8; ++r) {
+                    *(float4*)(cb + (int64_t)r * N2 + 32 * b32) =
+                        make_float4(tt[4 * r], tt[4 * r + 1], tt[4 * r + 2], tt[4 * r + 3]);
+                    tt[4 * r] = tt[4 * r + 1] = tt[4 * r + 2] = tt[4 * r + 3] = 0.f;
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (abort_flag && threadIdx.x == 0) atomicExch(err, QX_ETIMEOUT);
+    if (warp == 1) {
+        __syncwarp();
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(L::TMEM_COLS) : "memory");
+    }
+}
+
+// ------------------------------------------------------------------------------------------------
 // host side
 // ------------------------------------------------------------------------------------------------
 static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
@@ -1010,6 +1342,39 @@ static cudaError_t run_tc2(const TcArgs& g, cudaStream_t st, bool pack2 = false)
     return cudaGetLastError();
 }
 
+template <int BN>
+static cudaError_t run_tc2kb(const TcArgs& g, cudaStream_t st) {
+    using L = Tc2Kb<BN>;
+    const int64_t M = 1ll << g.mb, N = 1ll << g.nb, K = 1ll << g.kb;
+    CUtensorMap ma, mb;
+    if (!map_raw(&ma, g.a, 2 * K, M, distinct_items(g.a_is, g.a_div, g.n_items), g.a_is ? g.a_is * 8 : M * K * 8,
+                 TC_BM))
+        return cudaErrorInvalidValue;
+    if (!map_raw(&mb, g.b, 2 * K, N, 1, N * K * 8, BN / 2)) return cudaErrorInvalidValue;
+    const int smem = (int)L::SMEM + 1024;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    static uint64_t done[4] = {0, 0, 0, 0};
+    static std::mutex mu;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        if (dev < 256 && !((done[dev >> 6] >> (dev & 63)) & 1)) {
+            e = cudaFuncSetAttribute(k_gemm_tc2kb<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            if (e != cudaSuccess) return e;
+            done[dev >> 6] |= 1ull << (dev & 63);
+        }
+    }
+    const int tiles = (int)(M / TC_BM);
+    int sms = 152;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 152;
+    const int64_t jobs = (int64_t)tiles * g.n_items;
+    const unsigned grid = (unsigned)std::min<int64_t>(jobs, sms);  // one CTA per SM (shared memory)
+    k_gemm_tc2kb<BN><<<grid, TC2_THREADS, smem, st>>>(ma, mb, (float*)g.c, g.c_is * 2, (int)(2 * N), (int)(2 * K),
+                                                      tiles, g.n_items, item_div(g.a_is, g.a_div), g.limit, g.err);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_tc2_gemm(const TcArgs& g, cudaStream_t st) {
     if (!(g.mb >= 7 && g.nb >= 5 && g.kb >= 4 && g.n_items > 0 && g.n_items <= 65535)) return cudaErrorInvalidValue;
     if (!g.a_kmajor || !g.b_kmajor) return cudaErrorInvalidValue;
@@ -1019,6 +1384,14 @@ cudaError_t launch_tc2_gemm(const TcArgs& g, cudaStream_t st) {
     const bool pack2 = g.nb == 5 && g.b_is == NK && g.b_div <= 1 && g.n_items % 2 == 0 &&
                        (g.a_is == 0 || (g.a_div > 1 && g.a_div % 2 == 0));
     if (pack2) return run_tc2<128>(g, st, true);
+    // B shared by every item, one tile wide (2N = BN), its B' small enough to stay resident, and A not
+    // shared by several items (else the kept-A mode of k_gemm_tc2 saves more): build B' once per CTA
+    const int nk = (int)((2ll << g.kb) / 32);
+    const bool a_kept = g.a_is && g.a_div > 1;
+    if (g.b_is == 0 && !a_kept) {
+        if (g.nb == 6 && nk <= Tc2Kb<128>::MAXK) return run_tc2kb<128>(g, st);
+        if (g.nb == 5 && nk <= Tc2Kb<64>::MAXK) return run_tc2kb<64>(g, st);
+    }
     return g.nb >= 6 ? run_tc2<128>(g, st) : run_tc2<64>(g, st);
 }
 
@@ -1048,6 +1421,11 @@ static_assert(TcForm<TC_FORM_BF16X3>::STAGES * 6 * TC_BM * TC_ROWB + 1024 <= TC_
 static_assert(TcForm<TC_FORM_FP16>::STAGES * 2 * TC_BM * TC_ROWB + 1024 <= TC_SMEM_LIMIT + 1024, "smem");
 static_assert(Tc2<128>::SMEM + 1024 <= 227 * 1024 - 512, "smem");
 static_assert(Tc2<64>::SMEM + 1024 <= 227 * 1024 - 512, "smem");
+static_assert(Tc2Kb<128>::SMEM + 1024 <= 227 * 1024 - 512, "smem");
+static_assert(Tc2Kb<64>::SMEM + 1024 <= 227 * 1024 - 512, "smem");
+static_assert(Tc2Kb<128>::ACOL + Tc2Kb<128>::NM * 64 <= Tc2Kb<128>::TMEM_COLS, "tmem");
+static_assert(Tc2Kb<64>::ACOL + Tc2Kb<64>::NM * 64 <= Tc2Kb<64>::TMEM_COLS, "tmem");
+static_assert(Tc2Kb<128>::BRAW <= Tc2Kb<128>::LAND && Tc2Kb<64>::BRAW <= Tc2Kb<64>::LAND, "raw B fits a slot");
 static_assert(Tc2<128>::ACOL + Tc2<128>::NM * 64 <= Tc2<128>::TMEM_COLS, "tmem");
 static_assert(Tc2<64>::ACOL + Tc2<64>::NM * 64 <= Tc2<64>::TMEM_COLS, "tmem");
 
