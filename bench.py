@@ -383,7 +383,7 @@ def serving_bench(args):
     def one_run(precision):
         reqs = [serve.Request(r.rid, r.circuit, r.bits, r.arrival) for r in reqs0]
         srv = serve.Server(ws, precision=precision, max_bits=1024, max_request_s=args.serve_max_request_s,
-                           max_backlog_s=args.serve_max_backlog_s)
+                           max_backlog_s=args.serve_max_backlog_s, warm=True)
         sampler = ClockSampler(0)
         sampler.start()
         t0 = time.perf_counter()
@@ -396,6 +396,13 @@ def serving_bench(args):
                "rejected_cost": srv.stats["rejected_cost"], "rejected_busy": srv.stats["rejected_busy"],
                "rejected_memory": srv.stats["rejected"] - srv.stats["rejected_cost"] - srv.stats["rejected_busy"],
                "latency_ms": {"p50": summ["p50_ms"], "p99": summ["p99_ms"]},
+               "service_over_estimate": {"p50": summ["service_over_estimate_p50"],
+                                         "p90": summ["service_over_estimate_p90"]},
+               "per_circuit": {str(ci): {"admitted": srv.circuit_stats[ci]["admitted"],
+                                         "completed": srv.circuit_stats[ci]["completed"],
+                                         "est_s_per_bitstring": srv.circuits[ci].est_b,
+                                         "est_s_fixed": srv.circuits[ci].est_a}
+                               for ci in range(len(ws)) if srv.circuit_stats[ci]["admitted"]},
                "merged_requests": srv.stats["merged_requests"], "chunks": srv.stats["chunks"],
                "lanes": srv.stats["lanes"], "clocks": clocks,
                "servable_circuits": sum(1 for sc in srv.circuits

@@ -7,16 +7,17 @@ while other work is on the GPU:
 * requests for the same circuit that wait together are merged into one
   contraction (their bitstrings concatenated: the slice-batched executor then
   runs all their (slice, bitstring) pairs in the same launches);
-* a merged batch runs in slice chunks sized to a target amount of work, so a
-  long request never holds the GPU for long and new arrivals start between
+* a merged batch runs in slice chunks of about chunk_s estimated seconds, so
+  a long request never holds the GPU for long and new arrivals start between
   chunks; the chunks are parts of one sum in the library (``qx_submit_part``):
   the lane's FP64 compensated accumulators carry from chunk to chunk on the
   device, so a chunked request gets the same sum, in the same slice order, as
   one call over all slices (Eq. 2);
 * each circuit owns a few execution lanes (a library handle with its own
-  workspace and CUDA stream); lanes are created on demand while the device
-  memory budget allows (admission by memory) and reused afterwards; a lane
-  keeps its circuit's invariant intermediates across requests (qx_set_memo);
+  workspace, CUDA stream and request buffers, allocated once); lanes are
+  created on demand (or at start, `warm`) while the device memory budget
+  allows (admission by memory) and reused afterwards; a lane keeps its
+  circuit's invariant intermediates across requests (qx_set_memo);
 * each chunk is one asynchronous request of the library (the contraction of
   its slices, and for the last chunk the copy of the amplitudes to pinned
   host memory, on the lane's stream); completion is polled with ``qx_poll``;
@@ -54,15 +55,13 @@ class Request:
     done: float = -1.0
     amps: np.ndarray | None = None
     est: float = 0.0            # estimated service seconds (set at admission)
+    started: float = -1.0       # when its batch started on a lane (server clock)
 
 
 @dataclass
 class _Batch:
     reqs: list
-    bits_host: object           # pinned uint8 tensor
-    bits_dev: object
-    amps_dev: object
-    amps_host: object           # pinned float64 tensor
+    n: int                      # bitstrings of the merged requests (rows of the lane's buffers in use)
     chunks: list                # [(s0, s1)] still to run
     first: bool = True          # the next chunk starts the sum
     req: int = 0                # library request number of the chunk in flight
@@ -78,6 +77,12 @@ class _Lane:
                                workspace_bytes=circ.lane_bytes)
         # every request of the lane's circuit reads the same invariant intermediates: keep them
         qx.qx_set_memo(self.c.h, 1)
+        # request buffers for up to max_bits bitstrings, allocated once (pinned host memory for the copies)
+        n_o = 1 << circ.n_open
+        self.bits_host = torch.empty((max_bits, circ.n_qubits), dtype=torch.uint8).pin_memory()
+        self.bits_dev = torch.empty((max_bits, circ.n_qubits), dtype=torch.uint8, device=dev)
+        self.amps_dev = torch.empty((max_bits, n_o, 2), dtype=torch.float64, device=dev)
+        self.amps_host = torch.empty((max_bits, n_o, 2), dtype=torch.float64).pin_memory()
         self.batch = None
 
 
@@ -101,14 +106,14 @@ class ServedCircuit:
 
 class Server:
     def __init__(self, circuits, device=0, precision=qx.QX_PREC_C64, max_bits=1024, mem_budget=None,
-                 chunk_flops=2e11, max_lanes_per_circuit=2, items_per_lane=4096, max_request_s=float("inf"),
-                 max_backlog_s=float("inf")):
+                 chunk_s=0.05, max_lanes_per_circuit=2, items_per_lane=4096, max_request_s=float("inf"),
+                 max_backlog_s=float("inf"), warm=False):
         import torch
         self.torch = torch
         self.dev = torch.device("cuda", device)
         self.precision = precision
         self.max_bits = max_bits
-        self.chunk_flops = chunk_flops
+        self.chunk_s = chunk_s
         self.max_lanes = max_lanes_per_circuit
         self.max_request_s = max_request_s
         self.max_backlog_s = max_backlog_s
@@ -123,10 +128,11 @@ class Server:
             h = qx.qx_create(-1, precision=precision)
             qx.qx_build_network(h, w.n_qubits, w.gates, w.open_mask)
             qx.qx_set_plan(h, w.order, w.sliced)
-            # pairs per batch: as many as a lane's share of the budget holds
+            # pairs per batch: as many as a lane's share of the budget holds (every circuit can hold a
+            # lane at once)
             one = qx.qx_workspace_size(h, max_bits, 1)
             per_pair = max(qx.qx_workspace_size(h, max_bits, 2) - one, 1)
-            fit = (self.budget // 8 - one) // per_pair
+            fit = (self.budget // (2 * max(len(circuits), 4)) - one) // per_pair
             items = int(max(1, min(items_per_lane, sc.n_slices * max_bits, fit)))
             sc.lane_bytes = qx.qx_workspace_size(h, max_bits, items)
             sc.servable = sc.lane_bytes <= self.budget
@@ -139,11 +145,35 @@ class Server:
         self.clock0 = time.perf_counter()
         self.done = []
         self.stats = collections.Counter()
+        self.circuit_stats = [collections.Counter() for _ in self.circuits]
+        if warm:
+            self._warm()
+
+    def _warm(self):
+        """Resident circuits: one lane per circuit that a request can be admitted for (within the memory
+        budget, one bitstring within max_request_s), its tensors uploaded and its invariant intermediates
+        computed by one contraction of one bitstring, before the first request arrives."""
+        torch = self.torch
+        for ci, sc in enumerate(self.circuits):
+            if not sc.servable or sc.est_a + sc.est_b > self.max_request_s:
+                continue
+            lane = self._free_lane(ci)
+            if lane is None:
+                continue
+            with torch.cuda.stream(lane.stream):
+                d_bits = torch.zeros((1, sc.n_qubits), dtype=torch.uint8, device=self.dev)
+                lane.c.contract_device(d_bits)
+            lane.stream.synchronize()
+            qx.qx_device_status(lane.c.h)
+            self.stats["warm_lanes"] += 1
 
     def now(self):
         return time.perf_counter() - self.clock0
 
     # -- admission ----------------------------------------------------------------------------------
+    def _can_lane(self, sc):
+        return bool(sc.lanes) or self.committed + sc.lane_bytes <= self.budget
+
     def _free_lane(self, ci):
         sc = self.circuits[ci]
         for lane in sc.lanes:
@@ -159,8 +189,9 @@ class Server:
 
     def submit(self, req: Request):
         sc = self.circuits[req.circuit]
-        if not sc.servable or len(req.bits) > self.max_bits:
-            self.stats["rejected"] += 1  # needs more device memory than the budget, or too many bitstrings
+        if not sc.servable or len(req.bits) > self.max_bits or not self._can_lane(sc):
+            # needs more device memory than the budget holds for it now, or too many bitstrings
+            self.stats["rejected"] += 1
             return False
         req.est = sc.est_a + sc.est_b * len(req.bits)
         if req.est > self.max_request_s:
@@ -173,6 +204,7 @@ class Server:
             return False
         self.backlog += req.est
         self.stats["admitted"] += 1
+        self.circuit_stats[req.circuit]["admitted"] += 1
         sc.queue.append(req)
         return True
 
@@ -186,16 +218,22 @@ class Server:
             n += len(r.bits)
         if not reqs:
             return False
-        bits = np.concatenate([r.bits for r in reqs]).astype(np.uint8)
-        bh = torch.from_numpy(bits).pin_memory()
+        bh = lane.bits_host.numpy()
+        k = 0
+        for r in reqs:
+            bh[k:k + len(r.bits)] = r.bits
+            k += len(r.bits)
         with torch.cuda.stream(lane.stream):
-            bd = bh.to(self.dev, non_blocking=True)
-            ad = torch.empty((n, 1 << sc.n_open, 2), dtype=torch.float64, device=self.dev)
-        ah = torch.empty((n, 1 << sc.n_open, 2), dtype=torch.float64).pin_memory()
-        per_slice = max(sc.flops_per_slice * n, 1.0)
-        step = int(max(1, min(sc.n_slices, self.chunk_flops // per_slice)))
+            lane.bits_dev[:n].copy_(lane.bits_host[:n], non_blocking=True)
+        # slice chunks of about chunk_s estimated seconds each
+        est = sc.est_a + sc.est_b * n
+        n_chunks = int(max(1, min(sc.n_slices, est // self.chunk_s)))
+        step = -(-sc.n_slices // n_chunks)
         chunks = [(s, min(s + step, sc.n_slices)) for s in range(0, sc.n_slices, step)]
-        lane.batch = _Batch(reqs, bh, bd, ad, ah, chunks)
+        lane.batch = _Batch(reqs, n, chunks)
+        t_start = self.now()
+        for r in reqs:
+            r.started = t_start
         self.stats["batches"] += 1
         self.stats["merged_requests"] += len(reqs) - 1
         self._launch_chunk(lane)
@@ -205,8 +243,8 @@ class Server:
         b = lane.batch
         s0, s1 = b.chunks.pop(0)
         last = not b.chunks
-        b.req = qx.qx_submit_part(lane.c.h, b.bits_dev.data_ptr(), b.bits_dev.shape[0], s0, s1, b.first, last,
-                                  b.amps_dev.data_ptr(), b.amps_host.data_ptr() if last else None)
+        b.req = qx.qx_submit_part(lane.c.h, lane.bits_dev.data_ptr(), b.n, s0, s1, b.first, last,
+                                  lane.amps_dev.data_ptr(), lane.amps_host.data_ptr() if last else None)
         b.first = False
         b.inflight = (s0, s1)
         self.stats["chunks"] += 1
@@ -216,7 +254,7 @@ class Server:
         if b.chunks:
             self._launch_chunk(lane)
             return
-        tot = b.amps_host.numpy()
+        tot = lane.amps_host.numpy()[:b.n]
         amps = tot[..., 0] + 1j * tot[..., 1]
         t_done = self.now()
         k = 0
@@ -225,6 +263,7 @@ class Server:
             k += len(r.bits)
             r.done = t_done
             self.backlog -= r.est
+            self.circuit_stats[r.circuit]["completed"] += 1
             self.done.append(r)
         lane.batch = None
 
@@ -291,6 +330,10 @@ def poisson_requests(n_circuits, n_qubits_of, rate, duration, max_bits, seed):
 def latency_summary(done):
     lat = np.array([r.done - r.arrival for r in done]) if done else np.zeros(0)
     amps = sum(r.amps.size for r in done)
+    # service time of a batch against the estimate the admission used (merged requests share a batch)
+    svc = np.array([(r.done - r.started) / max(r.est, 1e-9) for r in done if r.started >= 0]) if done else np.zeros(0)
     return {"completed": len(done), "amplitudes": int(amps),
+            "service_over_estimate_p50": float(np.percentile(svc, 50)) if len(svc) else None,
+            "service_over_estimate_p90": float(np.percentile(svc, 90)) if len(svc) else None,
             "p50_ms": float(np.percentile(lat, 50) * 1e3) if len(lat) else None,
             "p99_ms": float(np.percentile(lat, 99) * 1e3) if len(lat) else None}

@@ -33,7 +33,7 @@ def test_requests_match_oracle_and_alone_equals_mix(serve):
     ws = _circuits()
     reqs = serve.poisson_requests(len(ws), lambda i: ws[i].n_qubits, rate=2000.0, duration=0.05, max_bits=24, seed=5)
     assert len(reqs) > 20
-    srv = serve.Server(ws, max_bits=96, chunk_flops=2e5, max_lanes_per_circuit=2)
+    srv = serve.Server(ws, max_bits=96, chunk_s=1e-6, max_lanes_per_circuit=2)
     done = srv.run(reqs, deadline=120)
     assert len(done) == len(reqs)
     assert srv.stats["chunks"] > srv.stats["batches"]  # long batches ran in several slice chunks
@@ -46,7 +46,7 @@ def test_requests_match_oracle_and_alone_equals_mix(serve):
     srv.close()
     # the same request alone on an idle server
     probe = max(done, key=lambda r: len(r.bits))
-    alone = serve.Server(ws, max_bits=96, chunk_flops=2e5)
+    alone = serve.Server(ws, max_bits=96, chunk_s=1e-6)
     one = alone.run([serve.Request(0, probe.circuit, probe.bits, 0.0)], deadline=60)
     assert_parity(one[0].amps, probe.amps)
     alone.close()
@@ -168,7 +168,7 @@ def test_serving_circuits_of_the_workload_and_mirror_pins(serve):
         if ws[r.circuit].n_qubits > 20:
             r.bits[0] = 0
     assert len(reqs) >= 10 and {r.circuit for r in reqs} == {0, 1, 2, 3}
-    srv = serve.Server(ws, precision=1, max_bits=64, chunk_flops=1e9, max_lanes_per_circuit=2)
+    srv = serve.Server(ws, precision=1, max_bits=64, chunk_s=0.01, max_lanes_per_circuit=2)
     done = srv.run(reqs, deadline=300)
     assert len(done) == len(reqs)
     for r in done:
@@ -180,7 +180,7 @@ def test_serving_circuits_of_the_workload_and_mirror_pins(serve):
         assert_parity(r.amps, ref, what=w.name)
     srv.close()
     probe = max(done, key=lambda r: len(r.bits) + 100 * (ws[r.circuit].n_qubits == 40))
-    alone = serve.Server(ws, precision=1, max_bits=64, chunk_flops=1e9)
+    alone = serve.Server(ws, precision=1, max_bits=64, chunk_s=0.01)
     one = alone.run([serve.Request(0, probe.circuit, probe.bits, 0.0)], deadline=120)
     assert_parity(one[0].amps, probe.amps)
     alone.close()
