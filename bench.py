@@ -400,13 +400,14 @@ def serving_bench(args):
                                          "p90": summ["service_over_estimate_p90"]},
                "per_circuit": {str(ci): {"admitted": srv.circuit_stats[ci]["admitted"],
                                          "completed": srv.circuit_stats[ci]["completed"],
-                                         "est_s_per_bitstring": srv.circuits[ci].est_b,
-                                         "est_s_fixed": srv.circuits[ci].est_a}
+                                         "est_s_1024_bitstrings": srv.circuits[ci].estimate(1024),
+                                         "est_s_1_bitstring": srv.circuits[ci].estimate(1),
+                                         "pairs_per_batch": srv.circuits[ci].items}
                                for ci in range(len(ws)) if srv.circuit_stats[ci]["admitted"]},
                "merged_requests": srv.stats["merged_requests"], "chunks": srv.stats["chunks"],
                "lanes": srv.stats["lanes"], "clocks": clocks,
                "servable_circuits": sum(1 for sc in srv.circuits
-                                        if sc.servable and sc.est_a + sc.est_b <= args.serve_max_request_s)}
+                                        if sc.servable and sc.estimate(1) <= args.serve_max_request_s)}
         srv.close()
         return out
 

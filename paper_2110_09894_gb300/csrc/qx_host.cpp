@@ -1032,6 +1032,25 @@ static int compile_plan(qx_ctx* h, const int64_t* order, int64_t n_steps, const 
         }
     }
     if (!R.variant && R.storage >= 0) h->stor[R.storage].last = kLive;
+    // per-slice storages read by per-pair work stay resident too, so that when a slice's bitstrings
+    // need several batches of the per-pair region, the later batches run only the per-pair steps
+    for (const Op& op : h->ops) {
+        if (op.level != 2) continue;
+        auto keep_node = [&](int node) {
+            const Node& nd = h->nodes[node];
+            if (nd.storage >= 0 && h->stor[nd.storage].level == 1) h->stor[nd.storage].last = kLive;
+        };
+        auto keep_stor = [&](int sid) {
+            if (sid >= 0 && h->stor[sid].level == 1) h->stor[sid].last = kLive;
+        };
+        if (op.type == OP_PERM) keep_node(op.src);
+        if (op.type == OP_SMALL) { keep_node(op.x); keep_node(op.y); }
+        if (op.type == OP_GEMM) {
+            keep_stor(op.sa);
+            if (op.dot_perm) keep_node(op.perm_src);
+            else keep_stor(op.sb);
+        }
+    }
     h->item_entries = std::max<int64_t>(assign_offsets(h, 2), kAlignEntries);
     h->slice_entries = assign_offsets(h, 1);
     if (h->opt.executor < 2) {
@@ -1852,6 +1871,8 @@ static int contract_impl(qx_ctx* h, const uint8_t* d_bits, int64_t n_bits, int64
             for (size_t j = 0; j < h->ops.size(); ++j) {
                 const Op& op = h->ops[j];
                 if (!op.variant && !prologue) continue;
+                // a later batch of the same slices' bitstrings: the per-slice results are still there
+                if (op.level == 1 && b0 > 0) continue;
                 const ItemCtx& c = op.level == 2 ? ic : op.level == 1 ? ic_s : ic_inv;
                 if ((rc = dag.issue((int)j, c, c.n_items))) return rc;
             }

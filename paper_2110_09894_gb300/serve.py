@@ -98,8 +98,24 @@ class ServedCircuit:
     n_slices: int = 1
     lane_bytes: int = 0
     servable: bool = True
-    est_a: float = 0.0          # estimated seconds of a request of b bitstrings: est_a + est_b * b
+    est_a: float = 0.0          # estimated seconds of one batch of b bitstrings: est_a + est_b * b
     est_b: float = 0.0
+    items: int = 1              # (slice, bitstring) pairs per batch in a lane's workspace
+    slice_ops: int = 0          # launches per batch of the per-slice and the per-pair steps
+    pair_ops: int = 0
+
+    def estimate(self, n_bits, launch_s=4e-6):
+        """Estimated seconds of a request: its work, plus the launches of the extra batches its pairs
+        need in the lane's workspace (whole slices with all their bitstrings per batch when they fit,
+        else per slice the per-slice steps once and the per-pair steps once per piece of its
+        bitstrings)."""
+        if self.items >= n_bits:
+            per = self.items // n_bits
+            extra = (-(-self.n_slices // per) - 1) * (self.slice_ops + self.pair_ops)
+        else:
+            pieces = -(-n_bits // self.items)
+            extra = (self.n_slices - 1) * self.slice_ops + (self.n_slices * pieces - 1) * self.pair_ops
+        return self.est_a + self.est_b * n_bits + extra * launch_s
     lanes: list = field(default_factory=list)
     queue: collections.deque = field(default_factory=collections.deque)
 
@@ -134,9 +150,12 @@ class Server:
             per_pair = max(qx.qx_workspace_size(h, max_bits, 2) - one, 1)
             fit = (self.budget // (2 * max(len(circuits), 4)) - one) // per_pair
             items = int(max(1, min(items_per_lane, sc.n_slices * max_bits, fit)))
+            sc.items = items
             sc.lane_bytes = qx.qx_workspace_size(h, max_bits, items)
             sc.servable = sc.lane_bytes <= self.budget
             desc = qx.qx_describe_plan(h)
+            lv = [ln.split()[3] for ln in desc.splitlines()]
+            sc.slice_ops, sc.pair_ops = lv.count("slice"), lv.count("pair")
             t1 = launch_list_time(desc, sc.n_slices, 1)
             sc.est_b = max((launch_list_time(desc, sc.n_slices, 256) - t1) / 255.0, 0.0)
             sc.est_a = t1 - sc.est_b
@@ -155,7 +174,7 @@ class Server:
         computed by one contraction of one bitstring, before the first request arrives."""
         torch = self.torch
         for ci, sc in enumerate(self.circuits):
-            if not sc.servable or sc.est_a + sc.est_b > self.max_request_s:
+            if not sc.servable or sc.estimate(1) > self.max_request_s:
                 continue
             lane = self._free_lane(ci)
             if lane is None:
@@ -193,7 +212,7 @@ class Server:
             # needs more device memory than the budget holds for it now, or too many bitstrings
             self.stats["rejected"] += 1
             return False
-        req.est = sc.est_a + sc.est_b * len(req.bits)
+        req.est = sc.estimate(len(req.bits))
         if req.est > self.max_request_s:
             self.stats["rejected"] += 1  # more work than the server accepts for one request
             self.stats["rejected_cost"] += 1
@@ -226,7 +245,7 @@ class Server:
         with torch.cuda.stream(lane.stream):
             lane.bits_dev[:n].copy_(lane.bits_host[:n], non_blocking=True)
         # slice chunks of about chunk_s estimated seconds each
-        est = sc.est_a + sc.est_b * n
+        est = sc.estimate(n)
         n_chunks = int(max(1, min(sc.n_slices, est // self.chunk_s)))
         step = -(-sc.n_slices // n_chunks)
         chunks = [(s, min(s + step, sc.n_slices)) for s in range(0, sc.n_slices, step)]

@@ -345,11 +345,13 @@ def level_aware_plan(legs, trials, seed, n_slice, open_edges, n_outputs, n_bits,
 
 
 def fitted_plan(legs, trials, seed, open_edges, n_outputs, n_bits, max_peak,
-                settings=((1.0, 0.6), (0.75, 0.3), (0.75, 0.6), (0.5, 0.6), (0.25, 0.3), (1.0, 1.0), (1.0, 0.2))):
+                settings=((1.0, 0.6), (0.75, 0.3), (0.75, 0.6), (0.5, 0.6), (0.25, 0.3), (1.0, 1.0), (1.0, 0.2)),
+                max_pair_peak=None, max_slices=24):
     """Seeded greedy candidates (as level_aware_plan), each sliced by tree trimming with as few bonds as
-    keep every intermediate within max_peak legs (Sec. III-A: slicing trades memory for more
-    contractions); the candidate with the smallest executed_time for n_bits bitstrings wins (ties: fewer
-    sliced bonds, earlier candidate).  Returns (order, sliced, estimated seconds)."""
+    keep every intermediate within max_peak legs, and those stored per (slice, bitstring) pair within
+    max_pair_peak when given (Sec. III-A: slicing trades memory for more contractions); the candidate
+    with the smallest executed_time for n_bits bitstrings wins (ties: fewer sliced bonds, earlier
+    candidate).  Returns (order, sliced, estimated seconds)."""
     rng = SplitMix64(seed)
     orders = [_greedy(legs)]
     for alpha, temp in settings:
@@ -358,8 +360,11 @@ def fitted_plan(legs, trials, seed, open_edges, n_outputs, n_bits, max_peak,
     best = None
     for k, order in enumerate(orders):
         sliced = []
-        while plan_cost(legs, order, sliced)[0] > max_peak:
+        while len(sliced) < max_slices and (plan_cost(legs, order, sliced)[0] > max_peak or (
+                max_pair_peak is not None and pair_peak(legs, order, sliced, n_outputs) > max_pair_peak)):
             sliced = tree_trim_slices(legs, order, len(sliced) + 1, seed + k, open_edges)
+        if plan_cost(legs, order, sliced)[0] > max_peak:
+            continue
         t = executed_time(legs, order, sliced, n_outputs, n_bits)
         key = (t, len(sliced), k)
         if best is None or key < best[0]:

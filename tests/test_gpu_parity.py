@@ -458,3 +458,23 @@ def test_device_slice_sum_is_compensated(qx, executor):
         got = c.contract(bits)[0, 0]
         assert got == want, (got, want)
         c.close()
+
+
+def test_bitstring_batches_reuse_the_slice_results(qx):
+    """When a slice's bitstrings need several batches of the per-pair region (max_items below the number
+    of bitstrings), the later batches run only the per-pair steps and read the per-slice results the
+    first batch left in the per-slice region: amplitudes as the single-batch call's."""
+    w = W.sliced_level_aware()
+    ref = oracle.sv_amplitudes(w.n_qubits, w.gates, w.open_mask, w.bitstrings)
+    full = qx.Contractor(w.n_qubits, w.gates, w.open_mask, w.order, w.sliced, len(w.bitstrings), precision=1)
+    a = full.contract(w.bitstrings)
+    full.close()
+    for cap in (100, 7):
+        c = qx.Contractor(w.n_qubits, w.gates, w.open_mask, w.order, w.sliced, len(w.bitstrings), precision=1,
+                          max_items=cap)
+        assert "slice" in {ln.split()[3] for ln in qx.qx_describe_plan(c.h).splitlines()}
+        got = c.contract(w.bitstrings)
+        assert c.stats()["batches"] > w.n_slices  # several bitstring batches per slice
+        assert_parity(got, ref)
+        assert rel_l2(got, a) < 1e-6
+        c.close()
