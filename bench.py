@@ -371,6 +371,9 @@ def group_bench(args):
 def serving_bench(args):
     """Poisson arrivals on the 32 resident serving circuits, in the chosen form and in plain complex64:
     offered, admitted and completed work, sustained amplitudes/s and latency of completed requests."""
+    # one stream per lane and a few dozen lanes: give them hardware queues of their own (a process
+    # setting, read when CUDA initialises)
+    os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
     import torch
     from paper_2110_09894_gb300 import build as qxbuild
     from paper_2110_09894_gb300 import serve

@@ -62,8 +62,8 @@ class Request:
 class _Batch:
     reqs: list
     n: int                      # bitstrings of the merged requests (rows of the lane's buffers in use)
-    chunks: list                # [(s0, s1)] still to run
-    first: bool = True          # the next chunk starts the sum
+    chunks: list                # [(b0, b1, s0, s1, first, last)] still to run: bitstrings [b0, b1) of
+                                # the batch, slices [s0, s1), whether the part starts / ends its sum
     req: int = 0                # library request number of the chunk in flight
     inflight: tuple = None
 
@@ -77,6 +77,8 @@ class _Lane:
                                workspace_bytes=circ.lane_bytes)
         # every request of the lane's circuit reads the same invariant intermediates: keep them
         qx.qx_set_memo(self.c.h, 1)
+        # lanes already overlap on their own streams: a lane issues its launches in plan order on one
+        qx.qx_set_streams(self.c.h, 1)
         # request buffers for up to max_bits bitstrings, allocated once (pinned host memory for the copies)
         n_o = 1 << circ.n_open
         self.bits_host = torch.empty((max_bits, circ.n_qubits), dtype=torch.uint8).pin_memory()
@@ -104,7 +106,7 @@ class ServedCircuit:
     slice_ops: int = 0          # launches per batch of the per-slice and the per-pair steps
     pair_ops: int = 0
 
-    def estimate(self, n_bits, launch_s=4e-6):
+    def estimate(self, n_bits, launch_s=1e-5):
         """Estimated seconds of a request: its work, plus the launches of the extra batches its pairs
         need in the lane's workspace (whole slices with all their bitstrings per batch when they fit,
         else per slice the per-slice steps once and the per-pair steps once per piece of its
@@ -244,11 +246,17 @@ class Server:
             k += len(r.bits)
         with torch.cuda.stream(lane.stream):
             lane.bits_dev[:n].copy_(lane.bits_host[:n], non_blocking=True)
-        # slice chunks of about chunk_s estimated seconds each
-        est = sc.estimate(n)
-        n_chunks = int(max(1, min(sc.n_slices, est // self.chunk_s)))
-        step = -(-sc.n_slices // n_chunks)
-        chunks = [(s, min(s + step, sc.n_slices)) for s in range(0, sc.n_slices, step)]
+        # pieces of at most a batch of the lane's workspace worth of bitstrings (separate sums), each in
+        # slice chunks of about chunk_s estimated seconds (parts of one sum): every library call then
+        # enqueues a bounded amount of work, so the loop keeps admitting and starting other requests
+        piece = max(1, min(n, sc.items))
+        chunks = []
+        for b0 in range(0, n, piece):
+            b1 = min(n, b0 + piece)
+            n_chunks = int(max(1, min(sc.n_slices, sc.estimate(b1 - b0) // self.chunk_s)))
+            step = -(-sc.n_slices // n_chunks)
+            ranges = [(s0, min(s0 + step, sc.n_slices)) for s0 in range(0, sc.n_slices, step)]
+            chunks += [(b0, b1, s0, s1, k == 0, k == len(ranges) - 1) for k, (s0, s1) in enumerate(ranges)]
         lane.batch = _Batch(reqs, n, chunks)
         t_start = self.now()
         for r in reqs:
@@ -260,12 +268,12 @@ class Server:
 
     def _launch_chunk(self, lane):
         b = lane.batch
-        s0, s1 = b.chunks.pop(0)
-        last = not b.chunks
-        b.req = qx.qx_submit_part(lane.c.h, lane.bits_dev.data_ptr(), b.n, s0, s1, b.first, last,
-                                  lane.amps_dev.data_ptr(), lane.amps_host.data_ptr() if last else None)
-        b.first = False
-        b.inflight = (s0, s1)
+        b0, b1, s0, s1, first, last = b.chunks.pop(0)
+        nq, row = lane.bits_dev.shape[1], lane.amps_dev[0].numel() * 8
+        b.req = qx.qx_submit_part(lane.c.h, lane.bits_dev.data_ptr() + b0 * nq, b1 - b0, s0, s1, first, last,
+                                  lane.amps_dev.data_ptr() + b0 * row,
+                                  (lane.amps_host.data_ptr() + b0 * row) if last else None)
+        b.inflight = (b0, b1, s0, s1)
         self.stats["chunks"] += 1
 
     def _finish_chunk(self, lane):
