@@ -50,7 +50,7 @@ def parse():
     p.add_argument("--serve-rate", type=float, default=200.0, help="mean requests per second (Poisson)")
     p.add_argument("--serve-max-request-s", type=float, default=1.0,
                    help="largest estimated service time of one request the server admits")
-    p.add_argument("--serve-max-backlog-s", type=float, default=2.0,
+    p.add_argument("--serve-max-backlog-s", type=float, default=0.5,
                    help="estimated work admitted and not yet done beyond which arrivals are shed")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--max-items", type=int, default=0, help="cap on (slice, bitstring) pairs per batch (0 = fill)")
@@ -403,6 +403,9 @@ def serving_bench(args):
                                          "p90": summ["service_over_estimate_p90"]},
                "per_circuit": {str(ci): {"admitted": srv.circuit_stats[ci]["admitted"],
                                          "completed": srv.circuit_stats[ci]["completed"],
+                                         "service_over_estimate_p50": float(np.median(
+                                             [(r.done - r.started) / max(r.est, 1e-9) for r in done
+                                              if r.circuit == ci] or [0.0])),
                                          "est_s_1024_bitstrings": srv.circuits[ci].estimate(1024),
                                          "est_s_1_bitstring": srv.circuits[ci].estimate(1),
                                          "pairs_per_batch": srv.circuits[ci].items}

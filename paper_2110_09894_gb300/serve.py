@@ -151,6 +151,10 @@ class Server:
             one = qx.qx_workspace_size(h, max_bits, 1)
             per_pair = max(qx.qx_workspace_size(h, max_bits, 2) - one, 1)
             fit = (self.budget // (2 * max(len(circuits), 4)) - one) // per_pair
+            # at least 64 pairs per batch when a quarter of the budget holds them (a large fixed part
+            # would otherwise leave a lane one pair per batch)
+            if fit < 64 and one + 64 * per_pair <= self.budget // 4:
+                fit = 64
             items = int(max(1, min(items_per_lane, sc.n_slices * max_bits, fit)))
             sc.items = items
             sc.lane_bytes = qx.qx_workspace_size(h, max_bits, items)
@@ -246,10 +250,10 @@ class Server:
             k += len(r.bits)
         with torch.cuda.stream(lane.stream):
             lane.bits_dev[:n].copy_(lane.bits_host[:n], non_blocking=True)
-        # pieces of at most a batch of the lane's workspace worth of bitstrings (separate sums), each in
+        # pieces of at most 16 batches of the lane's workspace worth of bitstrings (separate sums), each in
         # slice chunks of about chunk_s estimated seconds (parts of one sum): every library call then
         # enqueues a bounded amount of work, so the loop keeps admitting and starting other requests
-        piece = max(1, min(n, sc.items))
+        piece = max(1, min(n, 16 * sc.items))
         chunks = []
         for b0 in range(0, n, piece):
             b1 = min(n, b0 + piece)
