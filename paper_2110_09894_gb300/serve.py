@@ -106,18 +106,23 @@ class ServedCircuit:
     slice_ops: int = 0          # launches per batch of the per-slice and the per-pair steps
     pair_ops: int = 0
 
+    def piece(self, n_bits):
+        """Bitstrings per piece of a request: a lane runs a request as pieces of at most one batch of
+        its workspace, each a sum of its own, so that one library call enqueues a bounded amount of
+        work."""
+        return max(1, min(n_bits, self.items))
+
     def estimate(self, n_bits, launch_s=1e-5):
-        """Estimated seconds of a request: its work, plus the launches of the extra batches its pairs
-        need in the lane's workspace (whole slices with all their bitstrings per batch when they fit,
-        else per slice the per-slice steps once and the per-pair steps once per piece of its
-        bitstrings)."""
-        if self.items >= n_bits:
-            per = self.items // n_bits
+        """Estimated seconds of a request: per piece its work (whole slices with all the piece's
+        bitstrings per batch, the launches of every extra batch counted) and its fixed part."""
+        total, left = 0.0, n_bits
+        while left > 0:
+            pn = self.piece(left)
+            per = max(1, self.items // pn)
             extra = (-(-self.n_slices // per) - 1) * (self.slice_ops + self.pair_ops)
-        else:
-            pieces = -(-n_bits // self.items)
-            extra = (self.n_slices - 1) * self.slice_ops + (self.n_slices * pieces - 1) * self.pair_ops
-        return self.est_a + self.est_b * n_bits + extra * launch_s
+            total += self.est_a + self.est_b * pn + extra * launch_s
+            left -= pn
+        return total
     lanes: list = field(default_factory=list)
     queue: collections.deque = field(default_factory=collections.deque)
 
@@ -151,10 +156,6 @@ class Server:
             one = qx.qx_workspace_size(h, max_bits, 1)
             per_pair = max(qx.qx_workspace_size(h, max_bits, 2) - one, 1)
             fit = (self.budget // (2 * max(len(circuits), 4)) - one) // per_pair
-            # at least 64 pairs per batch when a quarter of the budget holds them (a large fixed part
-            # would otherwise leave a lane one pair per batch)
-            if fit < 64 and one + 64 * per_pair <= self.budget // 4:
-                fit = 64
             items = int(max(1, min(items_per_lane, sc.n_slices * max_bits, fit)))
             sc.items = items
             sc.lane_bytes = qx.qx_workspace_size(h, max_bits, items)
@@ -250,10 +251,10 @@ class Server:
             k += len(r.bits)
         with torch.cuda.stream(lane.stream):
             lane.bits_dev[:n].copy_(lane.bits_host[:n], non_blocking=True)
-        # pieces of at most 16 batches of the lane's workspace worth of bitstrings (separate sums), each in
+        # pieces of at most one batch of the lane's workspace worth of bitstrings (separate sums), each in
         # slice chunks of about chunk_s estimated seconds (parts of one sum): every library call then
         # enqueues a bounded amount of work, so the loop keeps admitting and starting other requests
-        piece = max(1, min(n, 16 * sc.items))
+        piece = sc.piece(n)
         chunks = []
         for b0 in range(0, n, piece):
             b1 = min(n, b0 + piece)
