@@ -38,7 +38,7 @@
 
 namespace qx {
 
-constexpr int TC_BM = 128, TC_BN = 128, TC_ROWB = 128, TC_THREADS = 192, TC_SMEM_LIMIT = 196608;
+constexpr int TC_BM = 128, TC_ROWB = 128, TC_SMEM_LIMIT = 196608;
 
 template <int FORM>
 struct TcForm;
@@ -301,20 +301,35 @@ struct TcMaps {
 // ------------------------------------------------------------------------------------------------
 // the GEMM
 // ------------------------------------------------------------------------------------------------
-template <int FORM>
-__global__ void __launch_bounds__(TC_THREADS, 1)
+// B tile width BN = 128 or 256 rows of B' (64 or 128 complex columns of C): a 256-wide tile reads each A
+// slab once for twice the columns (a quarter less operand traffic per flop), with 8 epilogue warps
+// (two per TMEM lane quarter, 128 columns each) and two 256-column TMEM accumulators.
+template <int FORM, int BN>
+struct TcTile {
+    using F = TcForm<FORM>;
+    static constexpr int EW = BN / 32;                             // epilogue warps
+    static constexpr int THREADS = 64 + 32 * EW;
+    static constexpr int NTB = 512 / BN;                          // TMEM accumulator buffers
+    static constexpr uint32_t TILE_A = TC_BM * TC_ROWB, TILE_B = BN * TC_ROWB;
+    static constexpr uint32_t STAGE_BYTES = F::NPA * TILE_A + F::NPB * TILE_B;
+    static constexpr int STAGES = BN == 128 ? F::STAGES : (int)(TC_SMEM_LIMIT / STAGE_BYTES);
+};
+
+template <int FORM, int BN>
+__global__ void __launch_bounds__(TcTile<FORM, BN>::THREADS, 1)
     k_gemm_tc(const __grid_constant__ TcMaps maps, float* __restrict__ C, int64_t c_is, int M, int N2, int K2,
               int tiles_n, long long limit, int* err, const float* amax, int a_div, int b_div) {
     using F = TcForm<FORM>;
+    using T = TcTile<FORM, BN>;
     constexpr int BK = TC_ROWB / F::EB;                 // K elements per stage
     constexpr int KSTEP = 32 / F::EB;                   // K elements per MMA (32 bytes)
-    constexpr uint32_t TILE = TC_BM * TC_ROWB;          // bytes of one 128-row part tile
-    constexpr uint32_t STAGE_BYTES = (F::NPA + F::NPB) * TILE;
+    constexpr uint32_t TILE_A = T::TILE_A, TILE_B = T::TILE_B, STAGE_BYTES = T::STAGE_BYTES;
+    constexpr int STAGES = T::STAGES, EW = T::EW;
     constexpr uint32_t IDESC = (1u << 4) | ((uint32_t)F::FMT << 7) | ((uint32_t)F::FMT << 10) |
-                               ((uint32_t)(TC_BN >> 3) << 17) | ((uint32_t)(TC_BM >> 4) << 24);
+                               ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(TC_BM >> 4) << 24);
     extern __shared__ uint8_t dyn[];
-    constexpr int NTB = 4;  // TMEM accumulator buffers (4 x 128 columns: all of TMEM)
-    __shared__ uint64_t full[F::STAGES], empty[F::STAGES], tfull[NTB], tempty[NTB], drain;
+    constexpr int NTB = T::NTB;  // TMEM accumulator buffers (NTB x BN columns: all of TMEM)
+    __shared__ uint64_t full[STAGES], empty[STAGES], tfull[NTB], tempty[NTB], drain;
     __shared__ uint32_t tmem_slot;
     __shared__ int abort_flag;
     if (*(volatile const int*)err) return;  // an earlier CTA of this contraction gave up
@@ -322,17 +337,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int item = blockIdx.y;
     const int m0 = (blockIdx.x / tiles_n) * TC_BM;
-    const int n0 = (blockIdx.x % tiles_n) * TC_BN;
+    const int n0 = (blockIdx.x % tiles_n) * BN;
     const int nk = (K2 + BK - 1) / BK;
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < F::STAGES; ++s) {
+        for (int s = 0; s < STAGES; ++s) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
         for (int b = 0; b < NTB; ++b) {
             mbar_init(&tfull[b], 1);
-            mbar_init(&tempty[b], 4);  // one arrival per epilogue warp
+            mbar_init(&tempty[b], EW);  // one arrival per epilogue warp
         }
         mbar_init(&drain, 1);
         abort_flag = 0;
@@ -340,7 +355,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     }
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(s_addr(&tmem_slot)),
-                     "r"(NTB * TC_BN)
+                     "r"(NTB * BN)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -353,7 +368,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         // producer
         int issued = 0;
         for (int it = 0; it < nk; ++it) {
-            const int s = it % F::STAGES, n = it / F::STAGES;
+            const int s = it % STAGES, n = it / STAGES;
             if (!mbar_wait(&empty[s], (n & 1) ^ 1, limit, err) || *(volatile int*)&abort_flag) {
                 atomicExch(&abort_flag, 1);
                 break;
@@ -362,21 +377,21 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             uint8_t* st = base + s * STAGE_BYTES;
 #pragma unroll
             for (int p = 0; p < F::NPA; ++p)
-                tma_load_3d(st + p * TILE, &maps.a[p], it * BK, m0, item / a_div, &full[s]);
+                tma_load_3d(st + p * TILE_A, &maps.a[p], it * BK, m0, item / a_div, &full[s]);
 #pragma unroll
             for (int p = 0; p < F::NPB; ++p)
-                tma_load_3d(st + (F::NPA + p) * TILE, &maps.b[p], it * BK, n0, item / b_div, &full[s]);
+                tma_load_3d(st + F::NPA * TILE_A + p * TILE_B, &maps.b[p], it * BK, n0, item / b_div, &full[s]);
             ++issued;
         }
         // every copy issued lands before the CTA goes away (immediate unless a wait gave up: the
         // consumers then did not see every stage)
-        for (int it = (issued > F::STAGES ? issued - F::STAGES : 0); it < issued; ++it)
-            mbar_wait_issued(&full[it % F::STAGES], (it / F::STAGES) & 1);
+        for (int it = (issued > STAGES ? issued - STAGES : 0); it < issued; ++it)
+            mbar_wait_issued(&full[it % STAGES], (it / STAGES) & 1);
     } else if (warp == 1 && lane == 0) {
         // MMA issuer: stage `it` accumulates (fresh) into TMEM buffer it % NTB
         bool ok = true;
         for (int it = 0; it < nk && ok; ++it) {
-            const int s = it % F::STAGES, n = it / F::STAGES;
+            const int s = it % STAGES, n = it / STAGES;
             const int b = it % NTB, u = it / NTB;
             if (!mbar_wait(&full[s], n & 1, limit, err) ||
                 (u > 0 && !mbar_wait(&tempty[b], (u - 1) & 1, limit, err)) || *(volatile int*)&abort_flag) {
@@ -386,7 +401,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             }
             tc_fence_after();
             const uint32_t st = s_addr(base + s * STAGE_BYTES);
-            const uint32_t d = tmem + b * TC_BN;
+            const uint32_t d = tmem + b * BN;
             // the smallest part products first, the main one (p = 0) last: each MMA joins the FP32
             // accumulator with a truncated alignment, so correction terms summed while it is still
             // small keep their bits, and only the main product's MMAs add at full magnitude
@@ -394,8 +409,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             for (int p = F::NPROD - 1; p >= 0; --p) {
 #pragma unroll
                 for (int kk = 0; kk < BK / KSTEP; ++kk) {
-                    const uint64_t ad = sdesc(st + F::pa(p) * TILE + kk * 32);
-                    const uint64_t bd = sdesc(st + (F::NPA + F::pb(p)) * TILE + kk * 32);
+                    const uint64_t ad = sdesc(st + F::pa(p) * TILE_A + kk * 32);
+                    const uint64_t bd = sdesc(st + F::NPA * TILE_A + F::pb(p) * TILE_B + kk * 32);
                     mma<FORM>(d, ad, bd, IDESC, (p != F::NPROD - 1 || kk != 0) ? 1u : 0u);
                 }
             }
@@ -407,14 +422,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         tc_commit(&drain);
         mbar_wait_issued(&drain, 0);
     } else if (warp >= 2) {
-        // epilogue: TMEM lanes 32 (warp % 4) .. + 31 are rows of the tile.  The
-        // tensor cores' FP32 accumulation drifts toward zero over long sums, so
-        // each stage's partial (<= 24 MMAs) is added to an FP32 total in
-        // registers with round-to-nearest instead of accumulating K in TMEM.
-        const int q = warp & 3;
-        float tot[TC_BN];
+        // epilogue: TMEM lanes 32 (warp % 4) .. + 31 are rows of the tile, warp w drains columns
+        // 128 h .. + 127 (h = (w - 2) / 4).  The tensor cores' FP32 accumulation drifts toward zero over
+        // long sums, so each stage's partial (<= 24 MMAs) is added to an FP32 total in registers with
+        // round-to-nearest instead of accumulating K in TMEM.
+        const int q = warp & 3, h = (warp - 2) >> 2;
+        float tot[128];
 #pragma unroll
-        for (int j = 0; j < TC_BN; ++j) tot[j] = 0.f;
+        for (int j = 0; j < 128; ++j) tot[j] = 0.f;
         bool ok = true;
         for (int it = 0; it < nk; ++it) {
             const int b = it % NTB, u = it / NTB;
@@ -427,9 +442,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             }
             tc_fence_after();
 #pragma unroll
-            for (int c = 0; c < TC_BN / 32; ++c) {
+            for (int c = 0; c < 4; ++c) {
                 float v[32];
-                tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + b * TC_BN + 32 * c, v);
+                tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + b * BN + 128 * h + 32 * c, v);
 #pragma unroll
                 for (int j = 0; j < 32; ++j) tot[32 * c + j] += v[j];
             }
@@ -441,13 +456,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             if (amax) {  // undo the FP16 per-tensor scales (powers of two: exact)
                 const float inv = 1.f / (fp16_scale(amax[0]) * fp16_scale(amax[1]));
 #pragma unroll
-                for (int j = 0; j < TC_BN; ++j) tot[j] *= inv;
+                for (int j = 0; j < 128; ++j) tot[j] *= inv;
             }
             // tiles are whole (rows and columns multiples of 128; see tc_shape_ok)
-            float* cb = C + (int64_t)item * c_is + (int64_t)(m0 + 32 * q + ((lane >> 3) << 3)) * N2 + n0 +
+            float* cb = C + (int64_t)item * c_is + (int64_t)(m0 + 32 * q + ((lane >> 3) << 3)) * N2 + n0 + 128 * h +
                         ((lane & 7) << 2);
 #pragma unroll
-            for (int b32 = 0; b32 < TC_BN / 32; ++b32) {
+            for (int b32 = 0; b32 < 4; ++b32) {
                 float* t = tot + 32 * b32;
                 transpose_q4(t, lane);
 #pragma unroll
@@ -462,7 +477,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     if (warp == 1) {
         __syncwarp();
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(NTB * TC_BN) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(NTB * BN) : "memory");
     }
 }
 
@@ -1188,13 +1203,14 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 }
 
 template <int FORM>
-static bool make_map(CUtensorMap* m, const void* base, int64_t k2, int64_t rows, int64_t items, int64_t item_bytes) {
+static bool make_map(CUtensorMap* m, const void* base, int64_t k2, int64_t rows, int64_t items, int64_t item_bytes,
+                     int box_rows = TC_BM) {
     using F = TcForm<FORM>;
     auto fn = encode_fn();
     if (!fn) return false;
     const cuuint64_t dims[3] = {(cuuint64_t)k2, (cuuint64_t)rows, (cuuint64_t)items};
     const cuuint64_t strides[2] = {(cuuint64_t)(k2 * F::EB), (cuuint64_t)item_bytes};
-    const cuuint32_t box[3] = {(cuuint32_t)(TC_ROWB / F::EB), (cuuint32_t)TC_BM, 1};
+    const cuuint32_t box[3] = {(cuuint32_t)(TC_ROWB / F::EB), (cuuint32_t)box_rows, 1};
     const cuuint32_t es[3] = {1, 1, 1};
     const CUtensorMapDataType dt = F::EB == 4                 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
                                    : FORM == TC_FORM_FP16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
@@ -1248,9 +1264,10 @@ static cudaError_t run_prep(const TcArgs& g, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-template <int FORM>
-static cudaError_t run_gemm(const TcArgs& g, cudaStream_t st) {
+template <int FORM, int BN>
+static cudaError_t run_gemm_bn(const TcArgs& g, cudaStream_t st) {
     using F = TcForm<FORM>;
+    using T = TcTile<FORM, BN>;
     const int64_t M = 1ll << g.mb, N = 1ll << g.nb, K = 1ll << g.kb;
     const int64_t pa_part = M * 2 * K, pb_part = 4 * N * K;  // elements per part
     TcMaps maps;
@@ -1261,9 +1278,9 @@ static cudaError_t run_gemm(const TcArgs& g, cudaStream_t st) {
             return cudaErrorInvalidValue;
     for (int p = 0; p < F::NPB; ++p)
         if (!make_map<FORM>(&maps.b[p], (const char*)g.pb + p * pb_part * F::EB, 2 * K, 2 * N,
-                            distinct_items(g.b_is, g.b_div, g.n_items), g.pb_is_bytes))
+                            distinct_items(g.b_is, g.b_div, g.n_items), g.pb_is_bytes, BN))
             return cudaErrorInvalidValue;
-    const int smem = F::STAGES * (F::NPA + F::NPB) * TC_BM * TC_ROWB + 1024;
+    const int smem = T::STAGES * (int)T::STAGE_BYTES + 1024;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
@@ -1272,18 +1289,26 @@ static cudaError_t run_gemm(const TcArgs& g, cudaStream_t st) {
     {
         std::lock_guard<std::mutex> lk(mu);
         if (dev < 256 && !((attr_done[dev >> 6] >> (dev & 63)) & 1)) {
-            e = cudaFuncSetAttribute(k_gemm_tc<FORM>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            e = cudaFuncSetAttribute(k_gemm_tc<FORM, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
             if (e != cudaSuccess) return e;
             attr_done[dev >> 6] |= 1ull << (dev & 63);
         }
     }
-    const int tiles_m = (int)((M + TC_BM - 1) / TC_BM), tiles_n = (int)((2 * N + TC_BN - 1) / TC_BN);
+    const int tiles_m = (int)(M / TC_BM), tiles_n = (int)(2 * N / BN);
     dim3 grid((unsigned)(tiles_m * tiles_n), (unsigned)g.n_items);
-    k_gemm_tc<FORM><<<grid, TC_THREADS, smem, st>>>(maps, (float*)g.c, g.c_is * 2, (int)M, (int)(2 * N), (int)(2 * K),
-                                                   tiles_n, g.limit, g.err,
-                                                   FORM == TC_FORM_FP16 ? (const float*)g.amax : nullptr,
-                                                   item_div(g.a_is, g.a_div), item_div(g.b_is, g.b_div));
+    k_gemm_tc<FORM, BN><<<grid, T::THREADS, smem, st>>>(maps, (float*)g.c, g.c_is * 2, (int)M, (int)(2 * N),
+                                                        (int)(2 * K), tiles_n, g.limit, g.err,
+                                                        FORM == TC_FORM_FP16 ? (const float*)g.amax : nullptr,
+                                                        item_div(g.a_is, g.a_div), item_div(g.b_is, g.b_div));
     return cudaGetLastError();
+}
+
+// 256-wide B tiles where whole ones cover 2N and two pipeline stages of them fit (3xTF32, FP16),
+// else 128-wide
+template <int FORM>
+static cudaError_t run_gemm(const TcArgs& g, cudaStream_t st) {
+    if (TcTile<FORM, 256>::STAGES >= 2 && ((2ll << g.nb) % 256) == 0) return run_gemm_bn<FORM, 256>(g, st);
+    return run_gemm_bn<FORM, 128>(g, st);
 }
 
 static bool map_raw(CUtensorMap* m, const void* base, int64_t k2, int64_t rows, int64_t items, int64_t item_bytes,
@@ -1416,6 +1441,9 @@ cudaError_t launch_tc_gemm(int form, const TcArgs& g, cudaStream_t st) {
     return cudaErrorInvalidValue;
 }
 
+static_assert(TcTile<TC_FORM_3XTF32, 256>::STAGES == 2 && TcTile<TC_FORM_FP16, 256>::STAGES == 4, "stages");
+static_assert(TcTile<TC_FORM_3XTF32, 256>::STAGES * TcTile<TC_FORM_3XTF32, 256>::STAGE_BYTES <= TC_SMEM_LIMIT, "smem");
+static_assert(TcTile<TC_FORM_FP16, 256>::STAGES * TcTile<TC_FORM_FP16, 256>::STAGE_BYTES <= TC_SMEM_LIMIT, "smem");
 static_assert(TcForm<TC_FORM_3XTF32>::STAGES * 4 * TC_BM * TC_ROWB + 1024 <= TC_SMEM_LIMIT + 1024, "smem");
 static_assert(TcForm<TC_FORM_BF16X3>::STAGES * 6 * TC_BM * TC_ROWB + 1024 <= TC_SMEM_LIMIT + 1024, "smem");
 static_assert(TcForm<TC_FORM_FP16>::STAGES * 2 * TC_BM * TC_ROWB + 1024 <= TC_SMEM_LIMIT + 1024, "smem");
