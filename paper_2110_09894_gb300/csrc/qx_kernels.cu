@@ -536,28 +536,6 @@ cudaError_t launch_small(const SmallDesc& d, const ItemCtx& ic, int64_t n_items,
         const bool staged2 = !d.om.on && d.nb <= 4;
         const size_t smem2 = sizeof(float2) * ((size_t)((yn + 1) & ~1) + (staged2 ? 512 * ((1 << d.nb) + 1) : 0));
         dim3 grid2((unsigned)(m / 512), (unsigned)n_items);
-        // the staged output of 512 rows needs up to 70 KB: allow 100 KB of dynamic shared memory, once
-        // per device and instantiation
-        static uint64_t attr_done[5][4] = {};
-        static std::mutex mu;
-        int dev = 0;
-        cudaError_t e = cudaGetDevice(&dev);
-        if (e != cudaSuccess) return e;
-        {
-            std::lock_guard<std::mutex> lk(mu);
-            const int kb = d.kb;
-            if (dev < 256 && !((attr_done[kb][dev >> 6] >> (dev & 63)) & 1)) {
-                const void* fn = kb == 0   ? (const void*)k_small2<0>
-                                 : kb == 1 ? (const void*)k_small2<1>
-                                 : kb == 2 ? (const void*)k_small2<2>
-                                 : kb == 3 ? (const void*)k_small2<3>
-                                           : (const void*)k_small2<4>;
-                e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
-                if (e != cudaSuccess) return e;
-                attr_done[kb][dev >> 6] |= 1ull << (dev & 63);
-            }
-        }
-        if (smem2 > 100 * 1024) return cudaErrorInvalidValue;
         switch (d.kb) {
             case 0: k_small2<0><<<grid2, 256, smem2, st>>>(d, ic, out, out_is); break;
             case 1: k_small2<1><<<grid2, 256, smem2, st>>>(d, ic, out, out_is); break;
