@@ -9,14 +9,16 @@ once) at the HBM rate its kernel family reaches, or its complex flops
 (8 M K N) at the family's arithmetic rate, whichever takes longer, plus a
 launch cost, and sums the launches.  The rates were measured per family on
 the 36-qubit sliced workload, where the sum matched the measured step time
-(325 vs 326 ms in 3xTF32).  The server uses it for admission, planners to
+(325 vs 326 ms in 3xTF32, and again after the kernels changed).  The server uses it for admission, planners to
 rank plans.
 """
 from __future__ import annotations
 
-# kernel family -> (complex flop/s, or None for data movement; bytes/s)
-GB300_LAUNCH_RATES = {"permute": (None, 6.0e12), "gather": (20e12, 4.7e12), "tc_direct": (150e12, 4.0e12),
-                      "tc_prep": (174e12, 5.0e12), "gemm": (35e12, 4.0e12), "dot_perm": (35e12, 5.0e12)}
+# kernel family -> (complex flop/s, or None for data movement; bytes/s).  "tc_direct_kb": the direct
+# tensor-core kernel with B' resident per CTA (B shared by every item, one tile wide)
+GB300_LAUNCH_RATES = {"permute": (None, 6.0e12), "gather": (20e12, 3.9e12), "tc_direct": (150e12, 3.5e12),
+                      "tc_direct_kb": (150e12, 6.3e12), "tc_prep": (241e12, 5.0e12), "gemm": (35e12, 4.0e12),
+                      "dot_perm": (35e12, 5.0e12)}
 _LEVEL = {"shared": 0, "slice": 1, "pair": 2}
 
 
@@ -40,6 +42,14 @@ def launch_list_time(desc, n_slices, n_bits, rates=GB300_LAUNCH_RATES, launch=4e
         it = items[level]
         nbytes = sum(8.0 * e * (it if _LEVEL[r] == level else items[_LEVEL[r]]) for r, e in _regions(kv.get("reads", "")))
         nbytes += sum(8.0 * e * it for r, e in _regions(kv.get("writes", "")))
+        if kind == "tc_direct" and "m" in kv:
+            # the launch picks the resident-B' variant when B is shared by every item, one 128- or 64-wide
+            # tile (N = 64 or 32) and at most 4 or 8 K stages of 32 reals, and A is not kept per slice
+            regs = _regions(kv.get("reads", ""))
+            n, k = int(kv["n"]), int(kv["k"])
+            if len(regs) == 2 and regs[1][0] == "shared" and regs[0][0] == f[3] and (
+                    (n == 6 and (2 << k) // 32 <= 4) or (n == 5 and (2 << k) // 32 <= 8)):
+                kind = "tc_direct_kb"
         fr, br = rates.get(kind, (35e12, 4.0e12))
         t = nbytes / br
         if fr and "m" in kv:
