@@ -7,7 +7,8 @@ slices, each contracted and summed in FP64), in the 3xTF32 tensor-core form
 with the plain complex64 form and the split-BF16 and FP16-scaled forms timed
 beside it, under its stored local-search plan (`--plan greedy` gives the
 seeded greedy order).  `--workload sliced` runs the 20-qubit 4x5 grid circuit
-of depth 12 with 6 sliced bonds for 256 random bitstrings.  One step = one
+of depth 12 with 6 sliced bonds for 256 random bitstrings, under its stored
+checkpoint plan.  One step = one
 full contraction of the workload (every slice for every bitstring) from
 device-resident bitstrings to device-resident complex128 amplitudes.
 
@@ -58,10 +59,11 @@ def parse():
                    help="contraction form (3xtf32 and bf16x3 meet the 1e-5 tolerance; fp16 is reported)")
     p.add_argument("--executor", default="auto", choices=["auto", "batched", "persistent"])
     p.add_argument("--plan", default="auto", choices=["auto", "level-aware", "greedy", "checkpoint", "local-search"],
-                   help="auto: the large workload's stored local-search plan, the sliced workload's level-aware "
-                        "plan (the seeded greedy candidate that executes the fewest flops per call); greedy: the "
-                        "seeded greedy order of the workload definition; checkpoint: the sliced workload's stored "
-                        "level-aware plan improved by local search")
+                   help="auto: the large workload's stored local-search plan, the sliced workload's stored "
+                        "checkpoint plan (its level-aware plan improved by local search: each slice's environment "
+                        "contracted once, little work per bitstring); level-aware: the seeded greedy candidate that "
+                        "executes the fewest flops per call; greedy: the seeded greedy order of the workload "
+                        "definition")
     p.add_argument("--no-forms", action="store_true", help="skip timing the other tensor-core forms beside")
     p.add_argument("--slices", type=int, default=0,
                    help="contract only slices 0..S-1 per step (a smaller case of the same launches, for profiling; "
@@ -77,9 +79,9 @@ def parse():
 
 
 def workload(name, plan="auto"):
-    if name == "sliced" and plan in ("auto", "level-aware"):
+    if name == "sliced" and plan == "level-aware":
         return W.sliced_level_aware()
-    if name == "sliced" and plan == "checkpoint":
+    if name == "sliced" and plan in ("auto", "checkpoint"):
         return W.sliced_checkpoint()
     if name == "large" and plan in ("auto", "local-search"):
         return W.large_local_search()

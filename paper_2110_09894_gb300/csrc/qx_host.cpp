@@ -1489,8 +1489,21 @@ static int run_op(qx_ctx* h, const Op& op, const ItemCtx& ic, int64_t n_items, c
         storage_addr(h, op.sa, &ap, &ais);
         storage_addr(h, op.sb, &bp, &bis);
         const OutMap om = out_map(op);
-        e = launch_gemm_c64(ap, ais, op.a_km, bp, bis, op.b_km, dp, dis, op.mb, op.nb, op.kb, n_items, st, &om,
-                            div(op.sa), div(op.sb));
+        // A per-slice matrix times a per-pair vector (N = 1): the pairs of a slice are consecutive items
+        // and share the matrix, so g of them (the largest power of two dividing the bitstrings per slice,
+        // at most 256) form one product C'[g][M] = B'[g][K] A[M][K]^T, their vectors as the rows of B'
+        // (items dense) and their results as the rows of C' (results dense): one GEMM with M = g per
+        // g pairs instead of g matrix-vector products.  Each output is the same K-ordered sum.
+        const int ad = div(op.sa), bd = div(op.sb);
+        int g = 1, gb = 0;
+        if (op.nb == 0 && !om.on && ad > 1 && bd == 1 && bis == ((int64_t)1 << op.kb) && dis == ((int64_t)1 << op.mb))
+            while (g < 256 && ad % (2 * g) == 0) g *= 2, ++gb;
+        if (g >= 16)
+            e = launch_gemm_c64(bp, g * bis, true, ap, ais, op.a_km, dp, g * dis, gb, op.mb, op.kb, n_items / g, st,
+                                nullptr, 1, ad / g);
+        else
+            e = launch_gemm_c64(ap, ais, op.a_km, bp, bis, op.b_km, dp, dis, op.mb, op.nb, op.kb, n_items, st, &om,
+                                ad, bd);
     } else if (op.tc == TC_FORM_3XTF32_DIRECT) {
         TcArgs g{};
         float2 *ap, *bp;
@@ -2309,6 +2322,15 @@ int qx_describe_plan(qx_handle h, char* buf, int64_t len, int64_t* needed) {
             out += " xk=";
             for (int i = 0; i < op.kb; ++i) {
                 snprintf(line, sizeof line, "%s%d", i ? "," : "", (int)sd.xk_pos[i]);
+                out += line;
+            }
+            out += "\n";
+        }
+        if (!op.out_pos.empty()) {  // placed product: address position of each natural bit (columns, then rows)
+            out.pop_back();
+            out += " place=";
+            for (size_t i = 0; i < op.out_pos.size(); ++i) {
+                snprintf(line, sizeof line, "%s%d", i ? "," : "", (int)op.out_pos[i]);
                 out += line;
             }
             out += "\n";

@@ -293,6 +293,19 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
 struct TcMaps {
     CUtensorMap a[3];
     CUtensorMap b[3];
@@ -497,6 +510,8 @@ __global__ void __launch_bounds__(TcTile<FORM, BN>::THREADS, 1)
 // ------------------------------------------------------------------------------------------------
 // warps 0 TMA, 1 and 14 MMA (even / odd stages), 2-9 drain, 10-13 convert
 constexpr int TC2_THREADS = 480, TC2_CONV = 128;
+// k_gemm_tc2 adds a second converter group (warps 15-18): the groups convert alternate stages
+constexpr int TC2_THREADS2 = TC2_THREADS + TC2_CONV;
 // Two rings.  Landing slots take the raw TMA slabs: A (16 KB, 128 rows) and B (BN/2 complex
 // rows).  MMA slots hold what the tensor core reads: B' hi and B' lo (BN rows each) in shared
 // memory, A hi and A lo (2 x 32 columns) in TMEM after the NTB accumulator buffers.  A landing
@@ -576,7 +591,7 @@ __device__ __forceinline__ void tc2_convert(const uint8_t* land, uint8_t* ms, in
 }
 
 template <int BN>
-__global__ void __launch_bounds__(TC2_THREADS, 1)
+__global__ void __launch_bounds__(TC2_THREADS2, 1)
     k_gemm_tc2(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                float* __restrict__ C, int64_t c_is, int M, int N2, int K2, int tiles_n, int tiles, int64_t n_items,
                int a_div, int b_div, int keep_a, int pack2, long long limit, int* err) {
@@ -731,15 +746,18 @@ __global__ void __launch_bounds__(TC2_THREADS, 1)
         // warps gave up and stopped waiting for them
         tc_commit(&drain[who]);
         mbar_wait_issued(&drain[who], 0);
-    } else if (warp >= 10 && warp <= 13) {
+    } else if ((warp >= 10 && warp <= 13) || (warp >= 15 && !keep_a)) {
         // converters: landing slot -> MMA slot, ahead of the MMAs; warp w writes the A rows of TMEM
-        // lanes 32 (w % 4)
-        const int ct = threadIdx.x - 320;
-        int l = 0, m = 0, it = 0;
+        // lanes 32 (w % 4).  Two groups (warps 10-13 and 15-18) convert the even and the odd stages:
+        // one group's conversion of a stage takes about twice its MMAs.  With a kept A only the first
+        // group runs (its decision to overwrite the kept A waits on the two stages before, in order).
+        const int grp = warp >= 15 ? 1 : 0, ng = keep_a ? 1 : 2;
+        const int ct = threadIdx.x - (grp ? 480 : 320);
+        int l = grp, m = grp, it = grp % nk;
         uint32_t lph = 0, mph = 0;
-        int64_t t = 0, prev_key = -1;
+        int64_t t = grp / nk, prev_key = -1;
         bool with_a = true;
-        for (int64_t g = 0; g < total; ++g) {
+        for (int64_t g = grp; g < total; g += ng) {
             // one decision per warp: the TMEM stores of the conversion are warp-wide (.sync.aligned)
             const bool go = mbar_wait(&full[l], lph, limit, err) && mbar_wait(&mfree[m], mph ^ 1u, limit, err) &&
                             !*(volatile int*)&abort_flag;
@@ -776,16 +794,19 @@ __global__ void __launch_bounds__(TC2_THREADS, 1)
                 asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(s_addr(&lfree[l])) : "memory");
                 asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(s_addr(&mfull[m])) : "memory");
             }
-            if (++it == nk) {
-                it = 0;
+            it += ng;
+            while (it >= nk) {
+                it -= nk;
                 ++t;
             }
-            if (++l == NL) {
-                l = 0;
+            l += ng;  // ng <= 2 < NL, NM
+            if (l >= NL) {
+                l -= NL;
                 lph ^= 1u;
             }
-            if (++m == NM) {
-                m = 0;
+            m += ng;
+            if (m >= NM) {
+                m -= NM;
                 mph ^= 1u;
             }
         }
@@ -810,11 +831,11 @@ __global__ void __launch_bounds__(TC2_THREADS, 1)
                 }
                 tc_fence_after();
 #pragma unroll
-                for (int c = 0; c < BN / 64; ++c) {
-                    float v[32];
-                    tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + b * BN + (BN / 2) * half + 32 * c, v);
+                for (int c = 0; c < BN / 32; ++c) {  // 16 columns at a time (registers: 608 threads)
+                    float v[16];
+                    tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + b * BN + (BN / 2) * half + 16 * c, v);
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) tot[32 * c + j] += v[j];
+                    for (int j = 0; j < 16; ++j) tot[16 * c + j] += v[j];
                 }
                 tc_fence_before();
                 __syncwarp();
@@ -859,7 +880,8 @@ __global__ void __launch_bounds__(TC2_THREADS, 1)
 // (2N = BN), with at most Tc2Kb::MAXK k-stages: B' (hi and lo) of every stage is built once per CTA
 // and stays in shared memory, so per job TMA brings only A and the converter warps only split A into
 // TMEM -- half the converter work and no B traffic per job.  Roles and rings otherwise as in
-// k_gemm_tc2: warps 0 TMA, 1 and 14 MMA (even / odd stages), 2-9 drain, 10-13 convert.
+// k_gemm_tc2 with one converter group: warps 0 TMA, 1 and 14 MMA (even / odd stages), 2-9 drain,
+// 10-13 convert.
 // ------------------------------------------------------------------------------------------------
 template <int BN>
 struct Tc2Kb {
@@ -1360,7 +1382,7 @@ static cudaError_t run_tc2(const TcArgs& g, cudaStream_t st, bool pack2 = false)
     // keep it across the jobs of a CTA
     const int nk = (int)(2 * K / 32);
     const int keep_a = g.a_is && g.a_div > 1 && L::ACOL + 64 * nk <= L::TMEM_COLS;
-    k_gemm_tc2<BN><<<grid, TC2_THREADS, smem, st>>>(ma, mb, (float*)g.c, g.c_is * 2, (int)M, (int)(2 * N),
+    k_gemm_tc2<BN><<<grid, TC2_THREADS2, smem, st>>>(ma, mb, (float*)g.c, g.c_is * 2, (int)M, (int)(2 * N),
                                                     (int)(2 * K), tiles_n, tiles_m * tiles_n, job_items,
                                                     item_div(g.a_is, g.a_div), item_div(g.b_is, g.b_div), keep_a,
                                                     pack2 ? 1 : 0, g.limit, g.err);

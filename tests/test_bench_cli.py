@@ -30,6 +30,8 @@ def test_reference_arm_prints_one_contract_line():
 
 def test_reference_arm_sliced_workload_plans():
     d = _run("--impl", "reference", "--workload", "sliced", "--steps", "1", "--warmup", "1")
+    assert d["config"]["workload"] == "grid4x5_d12_s6_amp256_checkpoint"
+    d = _run("--impl", "reference", "--workload", "sliced", "--plan", "level-aware", "--steps", "1", "--warmup", "1")
     assert d["config"]["workload"] == "grid4x5_d12_s6_amp256_levelplan"
     d = _run("--impl", "reference", "--workload", "sliced", "--plan", "greedy", "--steps", "1", "--warmup", "1")
     assert d["config"]["workload"] == "grid4x5_d12_s6_amp256"
