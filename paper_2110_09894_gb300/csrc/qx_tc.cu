@@ -247,6 +247,22 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
     d |= (uint64_t)2 << 61;            // 128-byte swizzle
     return d;
 }
+// the same for ROWB-byte rows: 128 (above) or 64 (64-byte swizzle, 8-row groups 512 B apart)
+template <int ROWB>
+__device__ __forceinline__ uint64_t sdesc_rows(uint32_t saddr) {
+    if constexpr (ROWB == 128) {
+        return sdesc(saddr);
+    } else {
+        static_assert(ROWB == 64, "64- or 128-byte rows");
+        uint64_t d = 0;
+        d |= (uint64_t)((saddr & 0x3FFFF) >> 4);
+        d |= (uint64_t)1 << 16;
+        d |= (uint64_t)(512 >> 4) << 32;
+        d |= (uint64_t)1 << 46;
+        d |= (uint64_t)4 << 61;  // 64-byte swizzle
+        return d;
+    }
+}
 template <int FORM>
 __device__ __forceinline__ void mma(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
     if constexpr (FORM == TC_FORM_3XTF32) {
@@ -316,26 +332,35 @@ struct TcMaps {
 // ------------------------------------------------------------------------------------------------
 // B tile width BN = 128 or 256 rows of B' (64 or 128 complex columns of C): a 256-wide tile reads each A
 // slab once for twice the columns (a quarter less operand traffic per flop), with 8 epilogue warps
-// (two per TMEM lane quarter, 128 columns each) and two 256-column TMEM accumulators.
-template <int FORM, int BN>
+// (two per TMEM lane quarter, 128 columns each) and two 256-column TMEM accumulators.  A stage holds
+// ROWB bytes of K per row (a 128- or 64-byte swizzled slab): the 256-wide 3xTF32 tile takes 64-byte
+// slabs, so that four 48 KB stages fit instead of two 96 KB ones and three stages load while the
+// tensor core works on the fourth (with two, each load had one stage's MMA time to land).
+template <int FORM, int BN, int ROWB = TC_ROWB>
 struct TcTile {
     using F = TcForm<FORM>;
     static constexpr int EW = BN / 32;                             // epilogue warps
     static constexpr int THREADS = 64 + 32 * EW;
     static constexpr int NTB = 512 / BN;                          // TMEM accumulator buffers
-    static constexpr uint32_t TILE_A = TC_BM * TC_ROWB, TILE_B = BN * TC_ROWB;
+    static constexpr uint32_t TILE_A = TC_BM * ROWB, TILE_B = BN * ROWB;
     static constexpr uint32_t STAGE_BYTES = F::NPA * TILE_A + F::NPB * TILE_B;
-    static constexpr int STAGES = BN == 128 ? F::STAGES : (int)(TC_SMEM_LIMIT / STAGE_BYTES);
+    static constexpr int STAGES = BN == 128 && ROWB == 128 ? F::STAGES : (int)(TC_SMEM_LIMIT / STAGE_BYTES);
 };
 
-template <int FORM, int BN>
-__global__ void __launch_bounds__(TcTile<FORM, BN>::THREADS, 1)
+template <int FORM, int BN, int ROWB>
+__global__ void __launch_bounds__(TcTile<FORM, BN, ROWB>::THREADS, 1)
     k_gemm_tc(const __grid_constant__ TcMaps maps, float* __restrict__ C, int64_t c_is, int M, int N2, int K2,
-              int tiles_n, long long limit, int* err, const float* amax, int a_div, int b_div) {
+              int tiles_n, int tiles, int64_t n_items, long long limit, int* err, const float* amax, int a_div,
+              int b_div) {
+    // persistent over (item, tile) jobs: job = blockIdx.x + t * gridDim.x, tiles of an item in order (n
+    // fastest, so CTAs working at the same time share A's m tile in L2).  The stages of successive jobs
+    // form one sequence for the ring, and the TMEM partials one sequence for the accumulators, so the
+    // loads and MMAs of a job start while the epilogue still stores the job before.
     using F = TcForm<FORM>;
-    using T = TcTile<FORM, BN>;
-    constexpr int BK = TC_ROWB / F::EB;                 // K elements per stage
+    using T = TcTile<FORM, BN, ROWB>;
+    constexpr int BK = ROWB / F::EB;                    // K elements per stage
     constexpr int KSTEP = 32 / F::EB;                   // K elements per MMA (32 bytes)
+    constexpr int SPD = TC_ROWB / ROWB;                 // stages per TMEM partial (128 bytes of K each)
     constexpr uint32_t TILE_A = T::TILE_A, TILE_B = T::TILE_B, STAGE_BYTES = T::STAGE_BYTES;
     constexpr int STAGES = T::STAGES, EW = T::EW;
     constexpr uint32_t IDESC = (1u << 4) | ((uint32_t)F::FMT << 7) | ((uint32_t)F::FMT << 10) |
@@ -348,10 +373,16 @@ __global__ void __launch_bounds__(TcTile<FORM, BN>::THREADS, 1)
     if (*(volatile const int*)err) return;  // an earlier CTA of this contraction gave up
     uint8_t* base = (uint8_t*)(((uintptr_t)dyn + 1023) & ~(uintptr_t)1023);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int item = blockIdx.y;
-    const int m0 = (blockIdx.x / tiles_n) * TC_BM;
-    const int n0 = (blockIdx.x % tiles_n) * BN;
-    const int nk = (K2 + BK - 1) / BK;
+    const int nk = (K2 + BK - 1) / BK, np = (nk + SPD - 1) / SPD;
+    const int64_t jobs = (int64_t)tiles * n_items;
+    const int64_t my_jobs = jobs > blockIdx.x ? (jobs - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    auto job_of = [&](int64_t t, int* item, int* m0, int* n0) {
+        const int64_t j = blockIdx.x + t * (int64_t)gridDim.x;
+        *item = (int)(j / tiles);
+        const int tile = (int)(j % tiles);
+        *m0 = (tile / tiles_n) * TC_BM;
+        *n0 = (tile % tiles_n) * BN;
+    };
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
@@ -378,36 +409,54 @@ __global__ void __launch_bounds__(TcTile<FORM, BN>::THREADS, 1)
     const uint32_t tmem = tmem_slot;
 
     if (warp == 0 && lane == 0) {
-        // producer
-        int issued = 0;
-        for (int it = 0; it < nk; ++it) {
-            const int s = it % STAGES, n = it / STAGES;
-            if (!mbar_wait(&empty[s], (n & 1) ^ 1, limit, err) || *(volatile int*)&abort_flag) {
-                atomicExch(&abort_flag, 1);
-                break;
+        // producer: ring slot s and its phase advance one step per stage across the jobs
+        int64_t issued = 0;
+        int s = 0;
+        uint32_t ph = 0;
+        bool ok = true;
+        for (int64_t t = 0; t < my_jobs && ok; ++t) {
+            int item, m0, n0;
+            job_of(t, &item, &m0, &n0);
+            for (int it = 0; it < nk; ++it) {
+                if (!mbar_wait(&empty[s], ph ^ 1u, limit, err) || *(volatile int*)&abort_flag) {
+                    atomicExch(&abort_flag, 1);
+                    ok = false;
+                    break;
+                }
+                mbar_expect_tx(&full[s], STAGE_BYTES);
+                uint8_t* st = base + s * STAGE_BYTES;
+#pragma unroll
+                for (int p = 0; p < F::NPA; ++p)
+                    tma_load_3d(st + p * TILE_A, &maps.a[p], it * BK, m0, item / a_div, &full[s]);
+#pragma unroll
+                for (int p = 0; p < F::NPB; ++p)
+                    tma_load_3d(st + F::NPA * TILE_A + p * TILE_B, &maps.b[p], it * BK, n0, item / b_div, &full[s]);
+                ++issued;
+                if (++s == STAGES) {
+                    s = 0;
+                    ph ^= 1u;
+                }
             }
-            mbar_expect_tx(&full[s], STAGE_BYTES);
-            uint8_t* st = base + s * STAGE_BYTES;
-#pragma unroll
-            for (int p = 0; p < F::NPA; ++p)
-                tma_load_3d(st + p * TILE_A, &maps.a[p], it * BK, m0, item / a_div, &full[s]);
-#pragma unroll
-            for (int p = 0; p < F::NPB; ++p)
-                tma_load_3d(st + F::NPA * TILE_A + p * TILE_B, &maps.b[p], it * BK, n0, item / b_div, &full[s]);
-            ++issued;
         }
         // every copy issued lands before the CTA goes away (immediate unless a wait gave up: the
         // consumers then did not see every stage)
-        for (int it = (issued > STAGES ? issued - STAGES : 0); it < issued; ++it)
-            mbar_wait_issued(&full[it % STAGES], (it / STAGES) & 1);
+        for (int64_t g = (issued > STAGES ? issued - STAGES : 0); g < issued; ++g)
+            mbar_wait_issued(&full[g % STAGES], (uint32_t)((g / STAGES) & 1));
     } else if (warp == 1 && lane == 0) {
-        // MMA issuer: stage `it` accumulates (fresh) into TMEM buffer it % NTB
+        // MMA issuer: the SPD stages of a partial accumulate (fresh) into TMEM buffer b; partials of
+        // successive jobs take the buffers in turn
         bool ok = true;
+        int s = 0;
+        uint32_t ph = 0;  // ring slot and phase
+        int64_t pj = 0;   // partials so far: the next one goes to buffer pj % NTB, its use pj / NTB
+        for (int64_t t = 0; t < my_jobs && ok; ++t)
         for (int it = 0; it < nk && ok; ++it) {
-            const int s = it % STAGES, n = it / STAGES;
-            const int b = it % NTB, u = it / NTB;
-            if (!mbar_wait(&full[s], n & 1, limit, err) ||
-                (u > 0 && !mbar_wait(&tempty[b], (u - 1) & 1, limit, err)) || *(volatile int*)&abort_flag) {
+            const bool first = it % SPD == 0, last = it % SPD == SPD - 1 || it == nk - 1;
+            const int b = (int)(pj % NTB);
+            const int64_t u = pj / NTB;
+            if (!mbar_wait(&full[s], ph, limit, err) ||
+                (first && u > 0 && !mbar_wait(&tempty[b], (uint32_t)((u - 1) & 1), limit, err)) ||
+                *(volatile int*)&abort_flag) {
                 atomicExch(&abort_flag, 1);
                 ok = false;
                 break;
@@ -422,13 +471,20 @@ __global__ void __launch_bounds__(TcTile<FORM, BN>::THREADS, 1)
             for (int p = F::NPROD - 1; p >= 0; --p) {
 #pragma unroll
                 for (int kk = 0; kk < BK / KSTEP; ++kk) {
-                    const uint64_t ad = sdesc(st + F::pa(p) * TILE_A + kk * 32);
-                    const uint64_t bd = sdesc(st + F::NPA * TILE_A + F::pb(p) * TILE_B + kk * 32);
-                    mma<FORM>(d, ad, bd, IDESC, (p != F::NPROD - 1 || kk != 0) ? 1u : 0u);
+                    const uint64_t ad = sdesc_rows<ROWB>(st + F::pa(p) * TILE_A + kk * 32);
+                    const uint64_t bd = sdesc_rows<ROWB>(st + F::NPA * TILE_A + F::pb(p) * TILE_B + kk * 32);
+                    mma<FORM>(d, ad, bd, IDESC, (!first || p != F::NPROD - 1 || kk != 0) ? 1u : 0u);
                 }
             }
             tc_commit(&empty[s]);
-            tc_commit(&tfull[b]);
+            if (++s == STAGES) {
+                s = 0;
+                ph ^= 1u;
+            }
+            if (last) {
+                tc_commit(&tfull[b]);
+                ++pj;
+            }
         }
         // the MMAs this thread issued finish before TMEM is freed, also when the epilogue warps gave
         // up and stopped waiting for them
@@ -437,50 +493,57 @@ __global__ void __launch_bounds__(TcTile<FORM, BN>::THREADS, 1)
     } else if (warp >= 2) {
         // epilogue: TMEM lanes 32 (warp % 4) .. + 31 are rows of the tile, warp w drains columns
         // 128 h .. + 127 (h = (w - 2) / 4).  The tensor cores' FP32 accumulation drifts toward zero over
-        // long sums, so each stage's partial (<= 24 MMAs) is added to an FP32 total in registers with
-        // round-to-nearest instead of accumulating K in TMEM.
+        // long sums, so each partial over 128 bytes of K (one stage, or two of 64-byte slabs: <= 24 MMAs)
+        // is added to an FP32 total in registers with round-to-nearest instead of accumulating K in TMEM.
         const int q = warp & 3, h = (warp - 2) >> 2;
         float tot[128];
-#pragma unroll
-        for (int j = 0; j < 128; ++j) tot[j] = 0.f;
         bool ok = true;
-        for (int it = 0; it < nk; ++it) {
-            const int b = it % NTB, u = it / NTB;
-            // one decision per warp: the TMEM loads below are warp-wide (.sync.aligned)
-            const bool go = mbar_wait(&tfull[b], u & 1, limit, err) && !*(volatile int*)&abort_flag;
-            if (!__all_sync(0xffffffffu, go)) {
-                atomicExch(&abort_flag, 1);
-                ok = false;
-                break;
-            }
-            tc_fence_after();
+        int64_t pj = 0;  // partials so far (buffer pj % NTB, its use pj / NTB)
+        for (int64_t t = 0; t < my_jobs && ok; ++t) {
 #pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                float v[32];
-                tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + b * BN + 128 * h + 32 * c, v);
+            for (int j = 0; j < 128; ++j) tot[j] = 0.f;
+            for (int j = 0; j < np; ++j, ++pj) {
+                const int b = (int)(pj % NTB);
+                const uint32_t par = (uint32_t)((pj / NTB) & 1);
+                // one decision per warp: the TMEM loads below are warp-wide (.sync.aligned)
+                const bool go = mbar_wait(&tfull[b], par, limit, err) && !*(volatile int*)&abort_flag;
+                if (!__all_sync(0xffffffffu, go)) {
+                    atomicExch(&abort_flag, 1);
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
 #pragma unroll
-                for (int j = 0; j < 32; ++j) tot[32 * c + j] += v[j];
+                for (int c = 0; c < 4; ++c) {
+                    float v[32];
+                    tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + b * BN + 128 * h + 32 * c, v);
+#pragma unroll
+                    for (int jj = 0; jj < 32; ++jj) tot[32 * c + jj] += v[jj];
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0)
+                    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(s_addr(&tempty[b])) : "memory");
             }
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(s_addr(&tempty[b])) : "memory");
-        }
-        if (ok) {
+            if (!ok) break;
             if (amax) {  // undo the FP16 per-tensor scales (powers of two: exact)
                 const float inv = 1.f / (fp16_scale(amax[0]) * fp16_scale(amax[1]));
 #pragma unroll
                 for (int j = 0; j < 128; ++j) tot[j] *= inv;
             }
             // tiles are whole (rows and columns multiples of 128; see tc_shape_ok)
+            int item, m0, n0;
+            job_of(t, &item, &m0, &n0);
             float* cb = C + (int64_t)item * c_is + (int64_t)(m0 + 32 * q + ((lane >> 3) << 3)) * N2 + n0 + 128 * h +
                         ((lane & 7) << 2);
 #pragma unroll
             for (int b32 = 0; b32 < 4; ++b32) {
-                float* t = tot + 32 * b32;
-                transpose_q4(t, lane);
+                float* tt = tot + 32 * b32;
+                transpose_q4(tt, lane);
 #pragma unroll
                 for (int r = 0; r < 8; ++r)
-                    *(float4*)(cb + (int64_t)r * N2 + 32 * b32) = make_float4(t[4 * r], t[4 * r + 1], t[4 * r + 2], t[4 * r + 3]);
+                    *(float4*)(cb + (int64_t)r * N2 + 32 * b32) =
+                        make_float4(tt[4 * r], tt[4 * r + 1], tt[4 * r + 2], tt[4 * r + 3]);
             }
         }
     }
@@ -1226,19 +1289,19 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 
 template <int FORM>
 static bool make_map(CUtensorMap* m, const void* base, int64_t k2, int64_t rows, int64_t items, int64_t item_bytes,
-                     int box_rows = TC_BM) {
+                     int box_rows = TC_BM, int rowb = TC_ROWB) {
     using F = TcForm<FORM>;
     auto fn = encode_fn();
     if (!fn) return false;
     const cuuint64_t dims[3] = {(cuuint64_t)k2, (cuuint64_t)rows, (cuuint64_t)items};
     const cuuint64_t strides[2] = {(cuuint64_t)(k2 * F::EB), (cuuint64_t)item_bytes};
-    const cuuint32_t box[3] = {(cuuint32_t)(TC_ROWB / F::EB), (cuuint32_t)box_rows, 1};
+    const cuuint32_t box[3] = {(cuuint32_t)(rowb / F::EB), (cuuint32_t)box_rows, 1};
     const cuuint32_t es[3] = {1, 1, 1};
     const CUtensorMapDataType dt = F::EB == 4                 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
                                    : FORM == TC_FORM_FP16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
                                                           : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
     return fn(m, dt, 3, const_cast<void*>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-              CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              rowb == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
@@ -1286,21 +1349,21 @@ static cudaError_t run_prep(const TcArgs& g, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-template <int FORM, int BN>
+template <int FORM, int BN, int ROWB = TC_ROWB>
 static cudaError_t run_gemm_bn(const TcArgs& g, cudaStream_t st) {
     using F = TcForm<FORM>;
-    using T = TcTile<FORM, BN>;
+    using T = TcTile<FORM, BN, ROWB>;
     const int64_t M = 1ll << g.mb, N = 1ll << g.nb, K = 1ll << g.kb;
     const int64_t pa_part = M * 2 * K, pb_part = 4 * N * K;  // elements per part
     TcMaps maps;
     memset(&maps, 0, sizeof maps);
     for (int p = 0; p < F::NPA; ++p)
         if (!make_map<FORM>(&maps.a[p], (const char*)g.pa + p * pa_part * F::EB, 2 * K, M,
-                            distinct_items(g.a_is, g.a_div, g.n_items), g.pa_is_bytes))
+                            distinct_items(g.a_is, g.a_div, g.n_items), g.pa_is_bytes, TC_BM, ROWB))
             return cudaErrorInvalidValue;
     for (int p = 0; p < F::NPB; ++p)
         if (!make_map<FORM>(&maps.b[p], (const char*)g.pb + p * pb_part * F::EB, 2 * K, 2 * N,
-                            distinct_items(g.b_is, g.b_div, g.n_items), g.pb_is_bytes, BN))
+                            distinct_items(g.b_is, g.b_div, g.n_items), g.pb_is_bytes, BN, ROWB))
             return cudaErrorInvalidValue;
     const int smem = T::STAGES * (int)T::STAGE_BYTES + 1024;
     int dev = 0;
@@ -1311,25 +1374,32 @@ static cudaError_t run_gemm_bn(const TcArgs& g, cudaStream_t st) {
     {
         std::lock_guard<std::mutex> lk(mu);
         if (dev < 256 && !((attr_done[dev >> 6] >> (dev & 63)) & 1)) {
-            e = cudaFuncSetAttribute(k_gemm_tc<FORM, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            e = cudaFuncSetAttribute(k_gemm_tc<FORM, BN, ROWB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
             if (e != cudaSuccess) return e;
             attr_done[dev >> 6] |= 1ull << (dev & 63);
         }
     }
     const int tiles_m = (int)(M / TC_BM), tiles_n = (int)(2 * N / BN);
-    dim3 grid((unsigned)(tiles_m * tiles_n), (unsigned)g.n_items);
-    k_gemm_tc<FORM, BN><<<grid, T::THREADS, smem, st>>>(maps, (float*)g.c, g.c_is * 2, (int)M, (int)(2 * N),
-                                                        (int)(2 * K), tiles_n, g.limit, g.err,
+    int sms = 152;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 152;
+    const int64_t jobs = (int64_t)tiles_m * tiles_n * g.n_items;
+    const unsigned grid = (unsigned)std::min<int64_t>(jobs, sms);  // persistent: one CTA per SM (shared memory)
+    k_gemm_tc<FORM, BN, ROWB><<<grid, T::THREADS, smem, st>>>(maps, (float*)g.c, g.c_is * 2, (int)M, (int)(2 * N),
+                                                        (int)(2 * K), tiles_n, tiles_m * tiles_n, g.n_items,
+                                                        g.limit, g.err,
                                                         FORM == TC_FORM_FP16 ? (const float*)g.amax : nullptr,
                                                         item_div(g.a_is, g.a_div), item_div(g.b_is, g.b_div));
     return cudaGetLastError();
 }
 
-// 256-wide B tiles where whole ones cover 2N and two pipeline stages of them fit (3xTF32, FP16),
-// else 128-wide
+// 256-wide B tiles where whole ones cover 2N and two pipeline stages of them fit (3xTF32 with 64-byte
+// slabs, FP16), else 128-wide
 template <int FORM>
 static cudaError_t run_gemm(const TcArgs& g, cudaStream_t st) {
-    if (TcTile<FORM, 256>::STAGES >= 2 && ((2ll << g.nb) % 256) == 0) return run_gemm_bn<FORM, 256>(g, st);
+    if (((2ll << g.nb) % 256) == 0) {
+        if constexpr (FORM == TC_FORM_3XTF32) return run_gemm_bn<FORM, 256, 64>(g, st);
+        else if constexpr (TcTile<FORM, 256>::STAGES >= 2) return run_gemm_bn<FORM, 256>(g, st);
+    }
     return run_gemm_bn<FORM, 128>(g, st);
 }
 
@@ -1463,8 +1533,9 @@ cudaError_t launch_tc_gemm(int form, const TcArgs& g, cudaStream_t st) {
     return cudaErrorInvalidValue;
 }
 
-static_assert(TcTile<TC_FORM_3XTF32, 256>::STAGES == 2 && TcTile<TC_FORM_FP16, 256>::STAGES == 4, "stages");
-static_assert(TcTile<TC_FORM_3XTF32, 256>::STAGES * TcTile<TC_FORM_3XTF32, 256>::STAGE_BYTES <= TC_SMEM_LIMIT, "smem");
+static_assert(TcTile<TC_FORM_3XTF32, 256, 64>::STAGES == 4 && TcTile<TC_FORM_FP16, 256>::STAGES == 4, "stages");
+static_assert(TcTile<TC_FORM_3XTF32, 256, 64>::STAGES * TcTile<TC_FORM_3XTF32, 256, 64>::STAGE_BYTES <= TC_SMEM_LIMIT,
+              "smem");
 static_assert(TcTile<TC_FORM_FP16, 256>::STAGES * TcTile<TC_FORM_FP16, 256>::STAGE_BYTES <= TC_SMEM_LIMIT, "smem");
 static_assert(TcForm<TC_FORM_3XTF32>::STAGES * 4 * TC_BM * TC_ROWB + 1024 <= TC_SMEM_LIMIT + 1024, "smem");
 static_assert(TcForm<TC_FORM_BF16X3>::STAGES * 6 * TC_BM * TC_ROWB + 1024 <= TC_SMEM_LIMIT + 1024, "smem");
