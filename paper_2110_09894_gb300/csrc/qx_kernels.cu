@@ -265,7 +265,10 @@ __global__ void __launch_bounds__(256) k_small(const __grid_constant__ SmallDesc
         for (int kk = 0; kk < (1 << KB); ++kk) a[kk] = xp[kofs[kk]];
         float2* __restrict__ cp = out + item * out_is + (d.om.on ? place_bits(m, rpos) : (m << nb));
         if (nn >= 2) {
-            // two outputs per pass: their Y entries are adjacent, one 16-byte shared load per k
+            // two outputs per pass: their Y entries are adjacent, one 16-byte shared load per k; a placed
+            // product with column bit 0 at address bit 0 stores both with one 16-byte store (the other
+            // address bits of n and m are >= 1, so the pair starts on 16 bytes)
+            const bool pair16 = d.om.on && d.om.pos[0] == 0;
             const float4* __restrict__ ys4 = (const float4*)yp;
             for (int n = 0; n < nn; n += 2) {
                 float2 acc0 = make_float2(0.f, 0.f), acc1 = make_float2(0.f, 0.f);
@@ -279,8 +282,12 @@ __global__ void __launch_bounds__(256) k_small(const __grid_constant__ SmallDesc
                     stage[threadIdx.x * (nn + 1) + n] = acc0;
                     stage[threadIdx.x * (nn + 1) + n + 1] = acc1;
                 } else if (d.om.on) {
-                    cp[cofs[n]] = acc0;
-                    cp[cofs[n + 1]] = acc1;
+                    if (pair16) {  // column bit 0 at address bit 0: outputs n, n + 1 are adjacent
+                        *(float4*)(cp + cofs[n]) = make_float4(acc0.x, acc0.y, acc1.x, acc1.y);
+                    } else {
+                        cp[cofs[n]] = acc0;
+                        cp[cofs[n + 1]] = acc1;
+                    }
                 } else {
                     *(float4*)(cp + n) = make_float4(acc0.x, acc0.y, acc1.x, acc1.y);
                 }
