@@ -318,6 +318,107 @@ __global__ void __launch_bounds__(256) k_small(const __grid_constant__ SmallDesc
     for (int i = threadIdx.x; i < cnt; i += 256) dst[i] = stage[(i >> nb) * (nn + 1) + (i & (nn - 1))];
 }
 
+// Two adjacent rows per thread, for a large operand whose address bit 0 is a free row bit (rows 2t
+// and 2t + 1 are then neighbouring entries of every row of X): one 16-byte load brings X[m][k] and
+// X[m+1][k], and every shared-memory load of the small operand feeds both rows -- half the load
+// instructions per output of k_small, whose load/store unit it saturates.  256 threads x 2 rows per
+// CTA, one pair per grid.y; outputs staged for coalesced stores as in k_small, or placed.
+template <int KB>
+__global__ void __launch_bounds__(256) k_small2(const __grid_constant__ SmallDesc d, const ItemCtx ic,
+                                                float2* __restrict__ out, int64_t out_is) {
+    extern __shared__ float4 small_dyn[];
+    float2* ys = (float2*)small_dyn;
+    __shared__ int64_t kofs[1 << KB];
+    __shared__ int64_t cofs[1 << kSmallMaxN];
+    __shared__ int8_t rpos[kMaxRank];
+    const int nb = d.nb;
+    const int nn = 1 << nb;
+    const int yn = (1 << KB) << nb;
+    const int64_t M = (int64_t)1 << d.mb;
+    const int64_t item = blockIdx.y;
+    if (d.om.on) {
+        for (int n = threadIdx.x; n < nn; n += blockDim.x) cofs[n] = place_bits(n, d.om.pos);
+        for (int b = threadIdx.x; b < d.mb; b += blockDim.x) rpos[b] = d.om.pos[nb + b];
+    }
+    {
+        const int64_t yb = fix_offset(d.y, ic, item);
+        for (int e = threadIdx.x; e < yn; e += blockDim.x) {
+            const int kk = e >> nb, n = e & (nn - 1);
+            int64_t a = yb;
+            for (int i = 0; i < KB; ++i)
+                if ((kk >> i) & 1) a += (int64_t)1 << d.yk_pos[i];
+            for (int i = 0; i < nb; ++i)
+                if ((n >> i) & 1) a += (int64_t)1 << d.yn_pos[i];
+            ys[e] = d.y.base[a];
+        }
+    }
+    if (threadIdx.x < (1 << KB)) {
+        int64_t a = 0;
+        for (int i = 0; i < KB; ++i)
+            if ((threadIdx.x >> i) & 1) a += (int64_t)1 << d.xk_pos[i];
+        kofs[threadIdx.x] = a;
+    }
+    __syncthreads();
+    const int t = threadIdx.x;
+    const int64_t m = ((int64_t)blockIdx.x * 256 + t) * 2;  // even: rows m, m + 1
+    float2* stage = ys + ((yn + 1) & ~1);
+    const bool staged = !d.om.on && nb <= 4;
+    if (m < M) {
+        int64_t xa = m;
+        for (int h = 0; h < d.n_holes; ++h) {
+            const int q = d.holes[h];
+            xa = ((xa >> q) << (q + 1)) | (xa & (((int64_t)1 << q) - 1));
+        }
+        const float2* __restrict__ xp = d.x.base + fix_offset(d.x, ic, item) + xa;
+        float4 a[1 << KB];
+#pragma unroll
+        for (int kk = 0; kk < (1 << KB); ++kk) a[kk] = *(const float4*)(xp + kofs[kk]);
+        const float4* __restrict__ ys4 = (const float4*)ys;
+        float2* __restrict__ cp0 = out + item * out_is + (d.om.on ? place_bits(m, rpos) : (m << nb));
+        float2* __restrict__ cp1 = d.om.on ? cp0 + ((int64_t)1 << rpos[0]) : cp0 + nn;
+        const bool pair16 = d.om.on && d.om.pos[0] == 0;
+        for (int n = 0; n < nn; n += 2) {
+            float2 c00 = make_float2(0.f, 0.f), c01 = c00, c10 = c00, c11 = c00;
+#pragma unroll
+            for (int kk = 0; kk < (1 << KB); ++kk) {
+                const float4 y = ys4[(kk * nn + n) >> 1];
+                const float2 y0 = make_float2(y.x, y.y), y1 = make_float2(y.z, y.w);
+                const float2 a0 = make_float2(a[kk].x, a[kk].y), a1 = make_float2(a[kk].z, a[kk].w);
+                cfma(c00, a0, y0);
+                cfma(c01, a0, y1);
+                cfma(c10, a1, y0);
+                cfma(c11, a1, y1);
+            }
+            if (staged) {
+                stage[(2 * t) * (nn + 1) + n] = c00;
+                stage[(2 * t) * (nn + 1) + n + 1] = c01;
+                stage[(2 * t + 1) * (nn + 1) + n] = c10;
+                stage[(2 * t + 1) * (nn + 1) + n + 1] = c11;
+            } else if (d.om.on) {
+                if (pair16) {  // column bit 0 at address bit 0 (see k_small)
+                    *(float4*)(cp0 + cofs[n]) = make_float4(c00.x, c00.y, c01.x, c01.y);
+                    *(float4*)(cp1 + cofs[n]) = make_float4(c10.x, c10.y, c11.x, c11.y);
+                } else {
+                    cp0[cofs[n]] = c00;
+                    cp0[cofs[n + 1]] = c01;
+                    cp1[cofs[n]] = c10;
+                    cp1[cofs[n + 1]] = c11;
+                }
+            } else {
+                *(float4*)(cp0 + n) = make_float4(c00.x, c00.y, c01.x, c01.y);
+                *(float4*)(cp1 + n) = make_float4(c10.x, c10.y, c11.x, c11.y);
+            }
+        }
+    }
+    if (!staged) return;
+    __syncthreads();
+    const int64_t r0 = (int64_t)blockIdx.x * 512;
+    const int64_t rows = M - r0 < 512 ? M - r0 : 512;
+    float2* __restrict__ dst = out + item * out_is + (r0 << nb);
+    const int64_t cnt = rows * nn;
+    for (int64_t i = t; i < cnt; i += 256) dst[i] = stage[(i >> nb) * (nn + 1) + (i & (nn - 1))];
+}
+
 // Flat variant for small per-pair tensors (2^mb < 256): one thread per
 // (pair, m) across the whole batch, the small operand read through L1 with
 // per-pair offsets (its entries are shared by the threads of a pair).  The
@@ -441,6 +542,43 @@ cudaError_t launch_small(const SmallDesc& d, const ItemCtx& ic, int64_t n_items,
     if (m < 256 && (out_is == (m << d.nb) || n_items == 1)) {
         ppc = (int)(256 / m);
         while (ppc > 1 && !y_shared && ppc * yst > 1536) ppc >>= 1;
+    }
+    // two rows per thread when X's address bit 0 is a row bit (see k_small2)
+    if (ppc == 1 && m >= 512 && d.kb <= 4 && d.nb >= 1 && (d.n_holes == 0 || d.holes[0] != 0)) {
+        const int yn = (1 << d.kb) << d.nb;
+        const bool staged2 = !d.om.on && d.nb <= 4;
+        const size_t smem2 = sizeof(float2) * ((size_t)((yn + 1) & ~1) + (staged2 ? 512 * ((1 << d.nb) + 1) : 0));
+        dim3 grid2((unsigned)(m / 512), (unsigned)n_items);
+        // the staged output of 512 rows needs up to 70 KB: allow 100 KB of dynamic shared memory, once
+        // per device and instantiation
+        static uint64_t attr_done[5][4] = {};
+        static std::mutex mu;
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e != cudaSuccess) return e;
+        {
+            std::lock_guard<std::mutex> lk(mu);
+            const int kb = d.kb;
+            if (dev < 256 && !((attr_done[kb][dev >> 6] >> (dev & 63)) & 1)) {
+                const void* fn = kb == 0   ? (const void*)k_small2<0>
+                                 : kb == 1 ? (const void*)k_small2<1>
+                                 : kb == 2 ? (const void*)k_small2<2>
+                                 : kb == 3 ? (const void*)k_small2<3>
+                                           : (const void*)k_small2<4>;
+                e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
+                if (e != cudaSuccess) return e;
+                attr_done[kb][dev >> 6] |= 1ull << (dev & 63);
+            }
+        }
+        if (smem2 > 100 * 1024) return cudaErrorInvalidValue;
+        switch (d.kb) {
+            case 0: k_small2<0><<<grid2, 256, smem2, st>>>(d, ic, out, out_is); break;
+            case 1: k_small2<1><<<grid2, 256, smem2, st>>>(d, ic, out, out_is); break;
+            case 2: k_small2<2><<<grid2, 256, smem2, st>>>(d, ic, out, out_is); break;
+            case 3: k_small2<3><<<grid2, 256, smem2, st>>>(d, ic, out, out_is); break;
+            default: k_small2<4><<<grid2, 256, smem2, st>>>(d, ic, out, out_is); break;
+        }
+        return cudaGetLastError();
     }
     const int threads = ppc > 1 ? (int)(ppc * m) : (m < 256 ? (int)((m + 31) / 32 * 32) : 256);
     const bool staged = !d.om.on && d.nb <= 4 && threads == 256;
