@@ -686,7 +686,7 @@ def main():
     # or its operations at the unit's peak, whichever takes longer for the same work
     hbm_peak = pk["hbm_gbs"]
     t_bytes = d["bytes"] / (hbm_peak * 1e9)
-    if dom in ("tc_gemm", "tc_direct"):
+    if dom in ("tc_gemm", "tc_direct", "tc_direct_kb"):
         code, products, ratio = PRECISIONS[args.precision]
         peak = pk["bf16_tflops"] * ratio
         ops = d["flops"] * products  # issued real tensor flops

@@ -406,7 +406,9 @@ void qx_group_destroy(qx_group_t g);
 #define QX_KERNEL_WAVE    7  /* batched executor: the small invariant steps, one CTA per chain */
 #define QX_KERNEL_SMALL_FLAT 8  /* gathers of short per-pair rows, one thread per row (k_small_flat) */
 #define QX_KERNEL_TC_DIRECT 9  /* tcgen05 3xTF32 GEMM splitting raw complex64 slabs itself (k_gemm_tc2) */
-#define QX_KERNEL_KINDS   10
+#define QX_KERNEL_TC_DIRECT_KB 10  /* the same with B' built once per CTA and kept (k_gemm_tc2kb): B
+                                    * shared by every item and one tile wide */
+#define QX_KERNEL_KINDS   11
 int qx_set_profiling(qx_handle h, int enable);
 int qx_profile_read(qx_handle h, int kind, double* ms, int64_t* launches, double* flops, double* bytes);
 

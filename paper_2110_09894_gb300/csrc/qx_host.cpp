@@ -1452,15 +1452,38 @@ static int run_op(qx_ctx* h, const Op& op, const ItemCtx& ic, int64_t n_items, c
     const bool direct = op.tc == TC_FORM_3XTF32_DIRECT, prep = op.tc && !direct;
     SmallDesc sdesc{};
     if (op.type == OP_SMALL) sdesc = small_desc(h, op);
-    const int kind = op.type == OP_PERM    ? QX_KERNEL_PERMUTE
-                     : op.type == OP_SMALL ? (small_is_flat(sdesc) ? QX_KERNEL_SMALL_FLAT : QX_KERNEL_SMALL)
-                     : direct              ? QX_KERNEL_TC_DIRECT
-                     : prep                ? QX_KERNEL_TC_PREP
-                                           : QX_KERNEL_GEMM;
-    size_t slot;
     // item i of a per-pair launch reads a per-slice operand at its slice i / n_b
     const int64_t n_b = op.level == 2 ? ic.n_b : 1;
     auto div = [&](int sid) { return h->stor[sid].level == 1 && op.level == 2 ? (int)n_b : 1; };
+    TcArgs dg{};  // the direct kernel's arguments (its variant decides the profiling kind)
+    if (direct) {
+        float2 *ap, *bp;
+        int64_t ais, bis;
+        storage_addr(h, op.sa, &ap, &ais);
+        storage_addr(h, op.sb, &bp, &bis);
+        dg.a = ap;
+        dg.a_is = ais;
+        dg.a_kmajor = op.a_km;
+        dg.b = bp;
+        dg.b_is = bis;
+        dg.b_kmajor = op.b_km;
+        dg.c = dp;
+        dg.c_is = dis;
+        dg.mb = op.mb;
+        dg.nb = op.nb;
+        dg.kb = op.kb;
+        dg.n_items = n_items;
+        dg.a_div = div(op.sa);
+        dg.b_div = div(op.sb);
+        dg.limit = h->opt.timeout_cycles > 0 ? h->opt.timeout_cycles : 2000000000ll;
+        dg.err = (int*)(h->ws + h->off_err);
+    }
+    const int kind = op.type == OP_PERM    ? QX_KERNEL_PERMUTE
+                     : op.type == OP_SMALL ? (small_is_flat(sdesc) ? QX_KERNEL_SMALL_FLAT : QX_KERNEL_SMALL)
+                     : direct              ? (tc2_resident_b(dg) ? QX_KERNEL_TC_DIRECT_KB : QX_KERNEL_TC_DIRECT)
+                     : prep                ? QX_KERNEL_TC_PREP
+                                           : QX_KERNEL_GEMM;
+    size_t slot;
     auto stor_b = [&](int sid) { return 8.0 * (double)h->stor[sid].entries * copies(op, h->stor[sid].level, n_items, n_b); };
     // the split parts hold one copy per distinct operand item
     const double prep_bytes = prep ? stor_b(op.sa) + stor_b(op.sb) + 8.0 * (double)h->stor[op.spa].entries *
@@ -1504,29 +1527,8 @@ static int run_op(qx_ctx* h, const Op& op, const ItemCtx& ic, int64_t n_items, c
         else
             e = launch_gemm_c64(ap, ais, op.a_km, bp, bis, op.b_km, dp, dis, op.mb, op.nb, op.kb, n_items, st, &om,
                                 ad, bd);
-    } else if (op.tc == TC_FORM_3XTF32_DIRECT) {
-        TcArgs g{};
-        float2 *ap, *bp;
-        int64_t ais, bis;
-        storage_addr(h, op.sa, &ap, &ais);
-        storage_addr(h, op.sb, &bp, &bis);
-        g.a = ap;
-        g.a_is = ais;
-        g.a_kmajor = op.a_km;
-        g.b = bp;
-        g.b_is = bis;
-        g.b_kmajor = op.b_km;
-        g.c = dp;
-        g.c_is = dis;
-        g.mb = op.mb;
-        g.nb = op.nb;
-        g.kb = op.kb;
-        g.n_items = n_items;
-        g.a_div = div(op.sa);
-        g.b_div = div(op.sb);
-        g.limit = h->opt.timeout_cycles > 0 ? h->opt.timeout_cycles : 2000000000ll;
-        g.err = (int*)(h->ws + h->off_err);
-        e = launch_tc2_gemm(g, st);
+    } else if (direct) {
+        e = launch_tc2_gemm(dg, st);
     } else {
         TcArgs g{};
         float2 *ap, *bp, *pa, *pb;

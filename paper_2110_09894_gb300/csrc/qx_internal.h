@@ -225,6 +225,8 @@ cudaError_t launch_tc_prep(int form, const TcArgs& g, cudaStream_t st);
 cudaError_t launch_tc_gemm(int form, const TcArgs& g, cudaStream_t st);
 // 3xTF32 directly on the complex64 operands (split in shared memory; no pa / pb)
 cudaError_t launch_tc2_gemm(const TcArgs& g, cudaStream_t st);
+// whether launch_tc2_gemm runs g on the kernel with B' resident per CTA (k_gemm_tc2kb)
+bool tc2_resident_b(const TcArgs& g);
 // amps[i] = (sum + compensation) * (scale_re + i scale_im), all in FP64
 cudaError_t launch_finalize(const double* acc, double* amps, int64_t n, double scale_re, double scale_im,
                             cudaStream_t st);

@@ -1501,15 +1501,18 @@ cudaError_t launch_tc2_gemm(const TcArgs& g, cudaStream_t st) {
     const bool pack2 = g.nb == 5 && g.b_is == NK && g.b_div <= 1 && g.n_items % 2 == 0 &&
                        (g.a_is == 0 || (g.a_div > 1 && g.a_div % 2 == 0));
     if (pack2) return run_tc2<128>(g, st, true);
-    // B shared by every item, one tile wide (2N = BN), its B' small enough to stay resident, and A not
-    // shared by several items (else the kept-A mode of k_gemm_tc2 saves more): build B' once per CTA
+    if (tc2_resident_b(g)) return g.nb == 6 ? run_tc2kb<128>(g, st) : run_tc2kb<64>(g, st);
+    return g.nb >= 6 ? run_tc2<128>(g, st) : run_tc2<64>(g, st);
+}
+
+// B shared by every item, one tile wide (2N = BN), its B' small enough to stay resident, and A not
+// shared by several items (else the kept-A mode of k_gemm_tc2 saves more): k_gemm_tc2kb builds B' once
+// per CTA.  (Never with pack2, which needs a B per item.)
+bool tc2_resident_b(const TcArgs& g) {
     const int nk = (int)((2ll << g.kb) / 32);
     const bool a_kept = g.a_is && g.a_div > 1;
-    if (g.b_is == 0 && !a_kept) {
-        if (g.nb == 6 && nk <= Tc2Kb<128>::MAXK) return run_tc2kb<128>(g, st);
-        if (g.nb == 5 && nk <= Tc2Kb<64>::MAXK) return run_tc2kb<64>(g, st);
-    }
-    return g.nb >= 6 ? run_tc2<128>(g, st) : run_tc2<64>(g, st);
+    if (g.b_is != 0 || a_kept) return false;
+    return (g.nb == 6 && nk <= Tc2Kb<128>::MAXK) || (g.nb == 5 && nk <= Tc2Kb<64>::MAXK);
 }
 
 static bool tc_shape_ok(const TcArgs& g) {

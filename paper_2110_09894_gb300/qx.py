@@ -29,7 +29,8 @@ EXPORTS = ("qx_create", "qx_destroy", "qx_last_error", "qx_set_options", "qx_bui
            "qx_esup_sample", "qx_set_memo", "qx_submit_part", "qx_workspace_parts",
            "qx_bind_workspace_parts")
 QX_STATIC_SCRATCH_BYTES = 64 << 20
-KERNEL_KINDS = ("permute", "small", "gemm", "sum", "tc_prep", "tc_gemm", "persist", "wave", "small_flat", "tc_direct")
+KERNEL_KINDS = ("permute", "small", "gemm", "sum", "tc_prep", "tc_gemm", "persist", "wave", "small_flat", "tc_direct",
+                "tc_direct_kb")
 
 
 class QXError(RuntimeError):

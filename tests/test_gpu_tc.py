@@ -34,7 +34,7 @@ def _tc_launches(qx, c, run):
     out = run()
     prof = qx.qx_profile_read(c.h)
     qx.qx_set_profiling(c.h, False)
-    return out, prof["tc_gemm"]["launches"] + prof["tc_direct"]["launches"]
+    return out, prof["tc_gemm"]["launches"] + prof["tc_direct"]["launches"] + prof["tc_direct_kb"]["launches"]
 
 
 @pytest.mark.parametrize("precision", FORMS)
