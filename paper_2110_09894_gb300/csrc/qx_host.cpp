@@ -87,6 +87,10 @@ struct Op {
     int dst = -1;           // output storage
     int tc = 0;             // tensor-core form (0: SIMT)
     int spa = -1, spb = -1; // split-part storages of the tensor-core form
+    // direct 3xTF32 step on the resident-B' kernel that reads A where it is stored (no permute): address
+    // position of each row bit and of each complex K bit of A
+    bool a_gather = false;
+    std::vector<int8_t> ag_mpos, ag_kpos;
     double flops = 0;
 };
 
@@ -925,6 +929,30 @@ static int compile_plan(qx_ctx* h, const int64_t* order, int64_t n_steps, const 
             c.cost = (c.pa ? (double)node_entries(GA) : 0.0) + (c.pb ? (double)node_entries(GB) : 0.0);
             if (best.cost < 0 || c.cost < best.cost) best = c;
         }
+        // The resident-B' direct kernel (B invariant and one tile wide, every K stage of B' resident, A
+        // per item; the conditions of tc2_resident_b) gathers A where it is stored, row and K bits at
+        // their positions, instead of reading a copy permuted to K-major: the permute is left out.
+        // The stage tile must be a few contiguous blocks of A (agather_tile).
+        const int fa_n = (int)fA.size(), fb_n = (int)fB.size();
+        const bool kb_fits = (fb_n == 6 && kb <= 6) || (fb_n == 5 && kb <= 7);
+        bool a_gather = direct && best.pa && kb_fits && GB.level == 0 && GA.level == level && !GA.leaf &&
+                        GA.fix.empty() && fa_n + kb == (int)GA.legs.size() && fa_n <= kMaxRank;
+        std::vector<int8_t> ag_m, ag_k;
+        if (a_gather) {
+            auto pos_of = [&](int leg) {
+                return (int8_t)GA.pos[std::find(GA.legs.begin(), GA.legs.end(), leg) - GA.legs.begin()];
+            };
+            for (int i = 0; i < fa_n; ++i) ag_m.push_back(pos_of(fA[fa_n - 1 - i]));
+            for (int i = 0; i < kb; ++i) ag_k.push_back(pos_of(best.S[kb - 1 - i]));
+            AGather probe{};
+            for (int i = 0; i < fa_n; ++i) probe.mpos[i] = ag_m[i];
+            for (int i = 0; i < kb; ++i) probe.kpos[i] = ag_k[i];
+            a_gather = agather_tile(&probe, fa_n, kb);
+        }
+        if (a_gather) {
+            best.pa = false;
+            best.akm = true;
+        }
         lay_out(t, fA, best.pa, fB, best.pb);
         // the SIMT GEMM places its product with whole 128-byte runs along columns (16 complex); the
         // tensor-core kernels and the dot kernel store their natural layout (measured on GB300: placed
@@ -946,6 +974,11 @@ static int compile_plan(qx_ctx* h, const int64_t* order, int64_t n_steps, const 
         g.kb = kb;
         g.a_km = best.akm;
         g.b_km = best.bkm;
+        if (a_gather) {
+            g.a_gather = true;
+            g.ag_mpos = ag_m;
+            g.ag_kpos = ag_k;
+        }
         // a full contraction (scalar per pair) with exactly one operand to permute: the dot kernel
         // reads that operand through the permutation instead (no permuted copy in HBM)
         const bool fuse_dot = fA.empty() && fB.empty() && kb >= 8 && best.pa != best.pb && h->opt.executor < 2;
@@ -1477,6 +1510,13 @@ static int run_op(qx_ctx* h, const Op& op, const ItemCtx& ic, int64_t n_items, c
         dg.b_div = div(op.sb);
         dg.limit = h->opt.timeout_cycles > 0 ? h->opt.timeout_cycles : 2000000000ll;
         dg.err = (int*)(h->ws + h->off_err);
+        if (op.a_gather) {
+            dg.ag.on = 1;
+            for (size_t i = 0; i < op.ag_mpos.size() && i < (size_t)kMaxRank; ++i) dg.ag.mpos[i] = op.ag_mpos[i];
+            for (size_t i = 0; i < op.ag_kpos.size() && i < 16; ++i) dg.ag.kpos[i] = op.ag_kpos[i];
+            if (!agather_tile(&dg.ag, op.mb, op.kb)) return fail(h, QX_EINVAL, "step %lld: A tile not gatherable",
+                                                                 (long long)op.step);
+        }
     }
     const int kind = op.type == OP_PERM    ? QX_KERNEL_PERMUTE
                      : op.type == OP_SMALL ? (small_is_flat(sdesc) ? QX_KERNEL_SMALL_FLAT : QX_KERNEL_SMALL)
@@ -2310,13 +2350,24 @@ int qx_describe_plan(qx_handle h, char* buf, int64_t len, int64_t* needed) {
                            : op.tc == TC_FORM_3XTF32_DIRECT ? "tc_direct"
                            : op.tc                          ? "tc_prep"
                                                             : "gemm";
-        if (op.type == OP_PERM)
-            snprintf(line, sizeof line, "%zu step=%lld %s %s rank=%zu\n", i, (long long)op.step, kind,
+        if (op.type == OP_PERM) {
+            snprintf(line, sizeof line, "%zu step=%lld %s %s rank=%zu", i, (long long)op.step, kind,
                      op.level == 2 ? "pair" : op.level == 1 ? "slice" : "shared", op.target_legs.size());
-        else
-            snprintf(line, sizeof line, "%zu step=%lld %s %s m=%d k=%d n=%d a_kmajor=%d b_kmajor=%d scatter=%d\n", i,
-                     (long long)op.step, kind, op.level == 2 ? "pair" : op.level == 1 ? "slice" : "shared", op.mb, op.kb, op.nb, (int)op.a_km,
-                     (int)op.b_km, (int)!op.out_pos.empty());
+            out += line;
+            // source address position of each target bit, lowest target bit first
+            const PermDesc pd = perm_desc(h, op);
+            out += " from=";
+            for (int ob = 0; ob < pd.rank; ++ob) {
+                snprintf(line, sizeof line, "%s%d", ob ? "," : "", (int)pd.in_pos[ob]);
+                out += line;
+            }
+            snprintf(line, sizeof line, "\n");
+        } else {
+            snprintf(line, sizeof line,
+                     "%zu step=%lld %s %s m=%d k=%d n=%d a_kmajor=%d b_kmajor=%d scatter=%d a_gather=%d\n", i,
+                     (long long)op.step, kind, op.level == 2 ? "pair" : op.level == 1 ? "slice" : "shared", op.mb, op.kb,
+                     op.nb, (int)op.a_km, (int)op.b_km, (int)!op.out_pos.empty(), (int)op.a_gather);
+        }
         out += line;
         if (op.type == OP_SMALL) {  // address positions in X of the contracted legs
             const SmallDesc sd = small_desc(h, op);
@@ -2324,6 +2375,20 @@ int qx_describe_plan(qx_handle h, char* buf, int64_t len, int64_t* needed) {
             out += " xk=";
             for (int i = 0; i < op.kb; ++i) {
                 snprintf(line, sizeof line, "%s%d", i ? "," : "", (int)sd.xk_pos[i]);
+                out += line;
+            }
+            out += "\n";
+        }
+        if (op.a_gather) {  // A read in place: address positions of its K bits, then of its row bits
+            out.pop_back();
+            out += " ak=";
+            for (size_t i = 0; i < op.ag_kpos.size(); ++i) {
+                snprintf(line, sizeof line, "%s%d", i ? "," : "", (int)op.ag_kpos[i]);
+                out += line;
+            }
+            out += " am=";
+            for (size_t i = 0; i < op.ag_mpos.size(); ++i) {
+                snprintf(line, sizeof line, "%s%d", i ? "," : "", (int)op.ag_mpos[i]);
                 out += line;
             }
             out += "\n";

@@ -197,6 +197,25 @@ cudaError_t launch_single_sum(const GSum& g, int64_t total, cudaStream_t st);
 // (prep), then the tcgen05 kernel writes C [M][N] complex64.
 constexpr int TC_FORM_3XTF32 = 1, TC_FORM_BF16X3 = 2, TC_FORM_FP16 = 3;
 constexpr int TC_FORM_3XTF32_DIRECT = 4;  // 3xTF32 split in shared memory (launch_tc2_gemm)
+// A read where it is stored by the resident-B' direct kernel (no permuted copy): bit i of the row
+// index sits at address position mpos[i], bit i of the complex K index at kpos[i].  The tile of one
+// stage (row bits 0..6 of a 128-row job, K bits 0..3 of its 16 K entries) covers address positions
+// 0 .. run - 1 and nblk - 1 = 2^(11 - run) - 1 combinations of its other bits: nblk contiguous blocks
+// of 2^run entries, block b at blk_off[b] from the tile's base, copied to entries b * 2^run of the
+// landing slot, where row r / K entry j of the stage sit at lrow[r] + lk[j].
+struct AGather {
+    int32_t on;
+    int32_t run, nblk;
+    int8_t mpos[kMaxRank];
+    int8_t kpos[16];
+    int64_t blk_off[8];
+    int16_t lrow[128];
+    int16_t lk[16];
+};
+// fills run, nblk, blk_off, lrow and lk from mpos / kpos (mb >= 7, kb >= 4); false when the stage tile
+// is not made of at most 8 contiguous blocks
+bool agather_tile(AGather* g, int mb, int kb);
+
 struct TcArgs {
     const float2* a;
     int64_t a_is;
@@ -216,6 +235,7 @@ struct TcArgs {
     long long limit;  // clock cycles per bounded wait
     int* err;         // device error flag (QX_ETIMEOUT on expiry)
     float* amax;      // FP16 form: device max |x| of A and B (2 floats), sets the per-tensor scales
+    AGather ag;       // direct kernel: A gathered in place (on = 1; only with B' resident, tc2_resident_b)
 };
 int tc_parts_a(int form);
 int tc_parts_b(int form);

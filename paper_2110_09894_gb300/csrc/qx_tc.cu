@@ -1015,11 +1015,48 @@ __device__ __forceinline__ void tc2kb_split_a(const uint8_t* araw, uint32_t tmem
     asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 }
 
-template <int BN>
+// bulk copy of `bytes` (a multiple of 16, both addresses 16-byte aligned) into shared memory, completing
+// on an mbarrier's transaction count
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     s_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(s_addr(bar))
+                 : "memory");
+}
+
+// A hi / lo of one gathered slab (GA): row r's 16 K entries sit at entries lrow + lk[j] of the slot
+__device__ __forceinline__ void tc2kb_split_a_local(const uint8_t* araw, int lrow, const int16_t* lk, uint32_t tmem,
+                                                    int qq, int lane, uint32_t ahi) {
+    const uint32_t lanes = (uint32_t)(32 * qq) << 16;
+    float2 a[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) a[j] = *(const float2*)(araw + 8 * (lrow + lk[j]));
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        float hi[16], lo[16];
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj) {
+            float4 vh, vl;
+            const int c = 4 * h + jj;
+            split4(make_float4(a[2 * c].x, a[2 * c].y, a[2 * c + 1].x, a[2 * c + 1].y), vh, vl);
+            hi[4 * jj] = vh.x; hi[4 * jj + 1] = vh.y; hi[4 * jj + 2] = vh.z; hi[4 * jj + 3] = vh.w;
+            lo[4 * jj] = vl.x; lo[4 * jj + 1] = vl.y; lo[4 * jj + 2] = vl.z; lo[4 * jj + 3] = vl.w;
+        }
+        tmem_st16(tmem + lanes + ahi + 16 * h, hi);
+        tmem_st16(tmem + lanes + ahi + 32 + 16 * h, lo);
+    }
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
+// GA (A gathered in place, ag): the producer thread brings each stage's 128 x 16 tile of A with
+// ag.nblk bulk copies of its contiguous blocks (in A's stored order) instead of one TMA box, and the
+// converters read row r's entries at ag.lrow[r] + ag.lk[j] of the slot.
+template <int BN, bool GA>
 __global__ void __launch_bounds__(TC2_THREADS, 1)
     k_gemm_tc2kb(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                  float* __restrict__ C, int64_t c_is, int N2, int K2, int tiles, int64_t n_items, int a_div,
-                 long long limit, int* err) {
+                 long long limit, int* err, const float2* __restrict__ ga_base, int64_t ga_is, int ga_mb,
+                 const __grid_constant__ AGather ag) {
     // persistent over (item, m tile) jobs: job = blockIdx.x + t * gridDim.x; B' of every k-stage is
     // resident, A's stages of successive jobs form one sequence g = t * nk + it.  The landing ring
     // first takes the nk raw B slabs, then the A slabs: both producer and converters walk that one
@@ -1033,6 +1070,7 @@ __global__ void __launch_bounds__(TC2_THREADS, 1)
     __shared__ uint64_t full[NL], lfree[NL], mfull[NM], mfree[NM], tfull[NTB], tempty[NTB], drain[2], bready;
     __shared__ uint32_t tmem_slot;
     __shared__ int abort_flag;
+    __shared__ int16_t s_lrow[GA ? 128 : 1], s_lk[GA ? 16 : 1];  // GA: the slot offsets of rows / K entries
     if (*(volatile const int*)err) return;
     uint8_t* base = (uint8_t*)(((uintptr_t)dyn + 1023) & ~(uintptr_t)1023);
     auto land = [&](int l) { return base + l * L::LAND; };
@@ -1047,6 +1085,10 @@ __global__ void __launch_bounds__(TC2_THREADS, 1)
         *item = j / tiles;
         *m0 = (int)(j % tiles) * TC_BM;
     };
+    if (GA) {
+        if (threadIdx.x < 128) s_lrow[threadIdx.x] = ag.lrow[threadIdx.x];
+        if (threadIdx.x < 16) s_lk[threadIdx.x] = ag.lk[threadIdx.x];
+    }
     if (threadIdx.x == 0) {
         for (int s = 0; s < NL; ++s) {
             mbar_init(&full[s], 1);
@@ -1077,7 +1119,58 @@ __global__ void __launch_bounds__(TC2_THREADS, 1)
     tc_fence_after();
     const uint32_t tmem = tmem_slot;
 
-    if (warp == 0 && lane == 0) {
+    if (GA && warp == 0 && lane == 0) {
+        int64_t issued = 0, t = 0, item = 0;
+        int l = 0, it = 0, m0 = 0;
+        uint32_t lph = 0;
+        bool ok = true;
+        for (int s = 0; s < nk && ok; ++s) {  // the raw B slab of every stage (TMA)
+            if (!mbar_wait(&lfree[l], lph ^ 1u, limit, err) || *(volatile int*)&abort_flag) {
+                atomicExch(&abort_flag, 1);
+                ok = false;
+                break;
+            }
+            mbar_expect_tx(&full[l], L::BRAW);
+            tma_load_3d(land(l), &mapB, s * BK, 0, 0, &full[l]);
+            ++issued;
+            if (++l == NL) {
+                l = 0;
+                lph ^= 1u;
+            }
+        }
+        const uint32_t blk_bytes = 8u << ag.run;
+        int64_t rowb = 0;
+        for (int64_t g = 0; g < total && ok; ++g) {
+            if (!mbar_wait(&lfree[l], lph ^ 1u, limit, err) || *(volatile int*)&abort_flag) {
+                atomicExch(&abort_flag, 1);
+                break;
+            }
+            if (it == 0) {  // the job's tile base in A: its item and row bits 7 and up
+                job_of(t, &item, &m0);
+                rowb = (item / a_div) * ga_is;
+                for (int b = 7; b < ga_mb; ++b)
+                    if ((m0 >> b) & 1) rowb += (int64_t)1 << ag.mpos[b];
+            }
+            int64_t tb = rowb;  // and the stage's K bits 4 and up
+            for (int b = 0; (it >> b) > 0; ++b)
+                if ((it >> b) & 1) tb += (int64_t)1 << ag.kpos[4 + b];
+            mbar_expect_tx(&full[l], L::A);
+            for (int b = 0; b < ag.nblk; ++b)
+                bulk_load(land(l) + (size_t)b * blk_bytes, ga_base + tb + ag.blk_off[b], blk_bytes, &full[l]);
+            ++issued;
+            if (++it == nk) {
+                it = 0;
+                ++t;
+            }
+            if (++l == NL) {
+                l = 0;
+                lph ^= 1u;
+            }
+        }
+        // the copies in flight land before the CTA exits (immediate unless a wait gave up)
+        for (int64_t q = (issued > NL ? issued - NL : 0); q < issued; ++q)
+            mbar_wait_issued(&full[q % NL], (uint32_t)((q / NL) & 1));
+    } else if (!GA && warp == 0 && lane == 0) {
         int64_t issued = 0, t = 0, item = 0;
         int l = 0, it = 0, m0 = 0;
         uint32_t lph = 0;
@@ -1193,7 +1286,11 @@ __global__ void __launch_bounds__(TC2_THREADS, 1)
                 break;
             }
             tc_fence_after();  // the MMAs that last read this A position have completed (mfree)
-            tc2kb_split_a(land(l), tmem, warp & 3, lane, L::ACOL + 64 * (uint32_t)m);
+            if (GA)
+                tc2kb_split_a_local(land(l), s_lrow[32 * (warp & 3) + lane], s_lk, tmem, warp & 3, lane,
+                                    L::ACOL + 64 * (uint32_t)m);
+            else
+                tc2kb_split_a(land(l), tmem, warp & 3, lane, L::ACOL + 64 * (uint32_t)m);
             tc_fence_before();
             __syncwarp();
             if (lane == 0) {
@@ -1459,13 +1556,14 @@ static cudaError_t run_tc2(const TcArgs& g, cudaStream_t st, bool pack2 = false)
     return cudaGetLastError();
 }
 
-template <int BN>
+template <int BN, bool GA>
 static cudaError_t run_tc2kb(const TcArgs& g, cudaStream_t st) {
     using L = Tc2Kb<BN>;
     const int64_t M = 1ll << g.mb, N = 1ll << g.nb, K = 1ll << g.kb;
     CUtensorMap ma, mb;
-    if (!map_raw(&ma, g.a, 2 * K, M, distinct_items(g.a_is, g.a_div, g.n_items), g.a_is ? g.a_is * 8 : M * K * 8,
-                 TC_BM))
+    memset(&ma, 0, sizeof ma);
+    if (!GA && !map_raw(&ma, g.a, 2 * K, M, distinct_items(g.a_is, g.a_div, g.n_items),
+                        g.a_is ? g.a_is * 8 : M * K * 8, TC_BM))
         return cudaErrorInvalidValue;
     if (!map_raw(&mb, g.b, 2 * K, N, 1, N * K * 8, BN / 2)) return cudaErrorInvalidValue;
     const int smem = (int)L::SMEM + 1024;
@@ -1477,7 +1575,7 @@ static cudaError_t run_tc2kb(const TcArgs& g, cudaStream_t st) {
     {
         std::lock_guard<std::mutex> lk(mu);
         if (dev < 256 && !((done[dev >> 6] >> (dev & 63)) & 1)) {
-            e = cudaFuncSetAttribute(k_gemm_tc2kb<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            e = cudaFuncSetAttribute(k_gemm_tc2kb<BN, GA>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
             if (e != cudaSuccess) return e;
             done[dev >> 6] |= 1ull << (dev & 63);
         }
@@ -1487,21 +1585,72 @@ static cudaError_t run_tc2kb(const TcArgs& g, cudaStream_t st) {
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 152;
     const int64_t jobs = (int64_t)tiles * g.n_items;
     const unsigned grid = (unsigned)std::min<int64_t>(jobs, sms);  // one CTA per SM (shared memory)
-    k_gemm_tc2kb<BN><<<grid, TC2_THREADS, smem, st>>>(ma, mb, (float*)g.c, g.c_is * 2, (int)(2 * N), (int)(2 * K),
-                                                      tiles, g.n_items, item_div(g.a_is, g.a_div), g.limit, g.err);
+    k_gemm_tc2kb<BN, GA><<<grid, TC2_THREADS, smem, st>>>(ma, mb, (float*)g.c, g.c_is * 2, (int)(2 * N),
+                                                          (int)(2 * K), tiles, g.n_items, item_div(g.a_is, g.a_div),
+                                                          g.limit, g.err, g.a, g.a_is, g.mb, g.ag);
     return cudaGetLastError();
+}
+
+bool agather_tile(AGather* g, int mb, int kb) {
+    if (mb < 7 || kb < 4) return false;
+    int tpos[11];
+    for (int i = 0; i < 7; ++i) tpos[i] = g->mpos[i];
+    for (int i = 0; i < 4; ++i) tpos[7 + i] = g->kpos[i];
+    int sorted[11];
+    std::copy(tpos, tpos + 11, sorted);
+    std::sort(sorted, sorted + 11);
+    int run = 0;
+    while (run < 11 && sorted[run] == run) ++run;
+    if (run < 8) return false;
+    // local position of a tile bit: its own below run, else run + its rank among the others
+    int local[11];
+    for (int i = 0; i < 11; ++i) {
+        if (tpos[i] < run) {
+            local[i] = tpos[i];
+        } else {
+            int rk = 0;
+            for (int j = 0; j < 11; ++j) rk += sorted[j] >= run && sorted[j] < tpos[i];
+            local[i] = run + rk;
+        }
+    }
+    g->run = run;
+    g->nblk = 1 << (11 - run);
+    for (int b = 0; b < g->nblk; ++b) {
+        int64_t o = 0;
+        for (int i = 0; i < 11 - run; ++i)
+            if ((b >> i) & 1) o += (int64_t)1 << sorted[run + i];
+        g->blk_off[b] = o;
+    }
+    for (int r = 0; r < 128; ++r) {
+        int v = 0;
+        for (int i = 0; i < 7; ++i)
+            if ((r >> i) & 1) v += 1 << local[i];
+        g->lrow[r] = (int16_t)v;
+    }
+    for (int j = 0; j < 16; ++j) {
+        int v = 0;
+        for (int i = 0; i < 4; ++i)
+            if ((j >> i) & 1) v += 1 << local[7 + i];
+        g->lk[j] = (int16_t)v;
+    }
+    return true;
 }
 
 cudaError_t launch_tc2_gemm(const TcArgs& g, cudaStream_t st) {
     if (!(g.mb >= 7 && g.nb >= 5 && g.kb >= 4 && g.n_items > 0 && g.n_items <= 65535)) return cudaErrorInvalidValue;
-    if (!g.a_kmajor || !g.b_kmajor) return cudaErrorInvalidValue;
+    if ((!g.a_kmajor && !g.ag.on) || !g.b_kmajor) return cudaErrorInvalidValue;
+    if (g.ag.on) {  // A gathered where it is stored: only the resident-B' kernel reads it so
+        if (!tc2_resident_b(g) || g.ag.run < 8 || g.ag.run > 11 || g.ag.nblk != 1 << (11 - g.ag.run))
+            return cudaErrorInvalidValue;
+        return g.nb == 6 ? run_tc2kb<128, true>(g, st) : run_tc2kb<64, true>(g, st);
+    }
     // N = 32 complex per item: two items per 128-column tile when their B rows are contiguous and
     // they read the same A (shared, or per slice with an even number of items per slice)
     const int64_t NK = (1ll << g.nb) * (1ll << g.kb);
     const bool pack2 = g.nb == 5 && g.b_is == NK && g.b_div <= 1 && g.n_items % 2 == 0 &&
                        (g.a_is == 0 || (g.a_div > 1 && g.a_div % 2 == 0));
     if (pack2) return run_tc2<128>(g, st, true);
-    if (tc2_resident_b(g)) return g.nb == 6 ? run_tc2kb<128>(g, st) : run_tc2kb<64>(g, st);
+    if (tc2_resident_b(g)) return g.nb == 6 ? run_tc2kb<128, false>(g, st) : run_tc2kb<64, false>(g, st);
     return g.nb >= 6 ? run_tc2<128>(g, st) : run_tc2<64>(g, st);
 }
 
