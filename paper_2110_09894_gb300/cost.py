@@ -17,7 +17,7 @@ from __future__ import annotations
 # kernel family -> (complex flop/s, or None for data movement; bytes/s).  "tc_direct_kb": the direct
 # tensor-core kernel with B' resident per CTA (B shared by every item, one tile wide)
 GB300_LAUNCH_RATES = {"permute": (None, 6.0e12), "gather": (26e12, 4.7e12), "tc_direct": (150e12, 3.5e12),
-                      "tc_direct_kb": (150e12, 6.3e12), "tc_prep": (260e12, 5.0e12), "gemm": (35e12, 4.0e12),
+                      "tc_direct_kb": (150e12, 4.8e12), "tc_prep": (260e12, 5.0e12), "gemm": (35e12, 4.0e12),
                       "dot_perm": (35e12, 5.0e12)}
 _LEVEL = {"shared": 0, "slice": 1, "pair": 2}
 
