@@ -182,3 +182,35 @@ def test_chain_check_catches_a_step_in_the_wrong_chain():
     chains[j] = max(chains) + 1
     with pytest.raises(AssertionError):
         _check_chains(ops, chains)
+
+
+def test_in_place_a_steps_of_the_36_qubit_plan():
+    """The resident-B' direct steps that read A where it is stored (no permute before them): each
+    lists the address position of every K bit and row bit of A, together every position of A once;
+    the 128-row x 16-K tile of a stage starts with a run of at least 8 positions (at most 8
+    contiguous blocks), and the launch list stays ordered with those reads."""
+    from paper_2110_09894_gb300 import qx
+    w = W.large_local_search()
+    lines = _plan_lines(qx, w.n_qubits, w.gates, w.open_mask, w.order, w.sliced, 1)
+    gathered = [line for line in lines if " a_gather=1" in line]
+    assert len(gathered) >= 3
+    ops = _parse(lines)
+    for line in gathered:
+        f = dict(x.split("=", 1) for x in line.split()[4:] if "=" in x)
+        assert line.split()[2] == "tc_direct"
+        mb, kb, nb = int(f["m"]), int(f["k"]), int(f["n"])
+        ak = [int(x) for x in f["ak"].split(",")]
+        am = [int(x) for x in f["am"].split(",")]
+        assert len(ak) == kb and len(am) == mb and sorted(ak + am) == list(range(mb + kb))
+        tile = sorted(am[:7] + ak[:4])
+        run = 0
+        while run < 11 and tile[run] == run:
+            run += 1
+        assert run >= 8
+        assert nb in (5, 6)  # one B tile: the resident-B' kernel
+        # A comes straight from the step that produced it, not from a permute
+        i = int(line.split()[0])
+        a_read = ops[i]["r"][0]
+        producers = [j for j in range(i) if _overlap([a_read], ops[j]["w"])]
+        assert producers and lines[producers[-1]].split()[2] != "permute"
+    _check(ops)
