@@ -95,7 +95,8 @@ def _time_member(w, precision, s, dev, stream, reps):
                       precision=precision, max_items=s.get("max_items", 0), gemm_min_bits=s.get("gemm_min_bits", 0),
                       stream=stream, executor=qx.EXEC_BATCHED)
     try:
-        d_bits = torch.from_numpy(w.bitstrings).to(dev)
+        with torch.cuda.stream(stream):  # the copy is ordered before the contraction's launches
+            d_bits = torch.from_numpy(w.bitstrings).to(dev)
         out = c.contract_device(d_bits)
         c.contract_device(d_bits, out)  # eager, then the captured graph
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

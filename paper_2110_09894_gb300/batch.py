@@ -41,10 +41,11 @@ class UnevenBatch:
         self.heavy = [i for i, w in enumerate(self.workloads) if w.peak_rank > LIGHT_MAX_PEAK]
         self.precision = precision
         settings = settings or {}
-        self.d_bits = [torch.from_numpy(w.bitstrings).to(self.dev) for w in self.workloads]
         self.d_amps = [None] * len(self.workloads)
         self.group = None
         with torch.cuda.stream(self.stream):
+            # copied on the batch's stream, which every launch of the batch then follows
+            self.d_bits = [torch.from_numpy(w.bitstrings).to(self.dev) for w in self.workloads]
             if self.light:
                 members = [self._contractor(i, qx.QX_PREC_C64, executor=qx.EXEC_GROUP_MEMBER) for i in self.light]
                 self.group = qx.Group(members, [self.d_bits[i] for i in self.light], ctas_per_sm)

@@ -70,6 +70,7 @@ def test_all_256_members_in_one_graph_vs_statevectors(qx):
     eager = b.amplitudes()
     for a in b.d_amps:
         a.zero_()
+    torch.cuda.synchronize()  # the zeros (current stream) land before the replay (the batch's stream) writes
     b.replay()
     torch.cuda.synchronize()
     b.check()
@@ -104,6 +105,7 @@ def test_group_graph_replay_reproduces_the_run(qx):
     direct = g.amplitudes()
     for a in g.d_amps:
         a.zero_()
+    torch.cuda.synchronize()  # the zeros (current stream) land before the group's stream writes
     g.capture()
     g.replay()
     torch.cuda.synchronize()
