@@ -41,11 +41,11 @@ class UnevenBatch:
         self.heavy = [i for i, w in enumerate(self.workloads) if w.peak_rank > LIGHT_MAX_PEAK]
         self.precision = precision
         settings = settings or {}
+        self.d_bits = [torch.from_numpy(w.bitstrings).to(self.dev) for w in self.workloads]
+        torch.cuda.synchronize(self.dev)  # the bitstrings are on the device before the batch's stream reads them
         self.d_amps = [None] * len(self.workloads)
         self.group = None
         with torch.cuda.stream(self.stream):
-            # copied on the batch's stream, which every launch of the batch then follows
-            self.d_bits = [torch.from_numpy(w.bitstrings).to(self.dev) for w in self.workloads]
             if self.light:
                 members = [self._contractor(i, qx.QX_PREC_C64, executor=qx.EXEC_GROUP_MEMBER) for i in self.light]
                 self.group = qx.Group(members, [self.d_bits[i] for i in self.light], ctas_per_sm)
@@ -74,6 +74,7 @@ class UnevenBatch:
                 w = self.workloads[i]
                 self.d_amps[i] = torch.empty((len(w.bitstrings), 1 << w.n_open, 2), dtype=torch.float64,
                                              device=self.dev)
+        torch.cuda.synchronize(self.dev)  # set-up copies and memsets on any stream are done before the first run
         self.graph = None
 
     def _contractor(self, i, precision, executor=qx.EXEC_BATCHED, max_items=0, gemm_min_bits=0,
