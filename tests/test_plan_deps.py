@@ -214,3 +214,42 @@ def test_in_place_a_steps_of_the_36_qubit_plan():
         producers = [j for j in range(i) if _overlap([a_read], ops[j]["w"])]
         assert producers and lines[producers[-1]].split()[2] != "permute"
     _check(ops)
+
+
+def _gather_invariants(lines):
+    """Checks every in-place A step of a launch listing; returns how many there are."""
+    ops = _parse(lines)
+    n = 0
+    for line in lines:
+        if " a_gather=1" not in line:
+            continue
+        n += 1
+        f = dict(x.split("=", 1) for x in line.split()[4:] if "=" in x)
+        mb, kb = int(f["m"]), int(f["k"])
+        ak = [int(x) for x in f["ak"].split(",")]
+        am = [int(x) for x in f["am"].split(",")]
+        assert sorted(ak + am) == list(range(mb + kb))
+        tile = sorted(am[:7] + ak[:4])
+        run = 0
+        while run < 11 and tile[run] == run:
+            run += 1
+        assert run >= 8
+        i = int(line.split()[0])
+        producers = [j for j in range(i) if _overlap([ops[i]["r"][0]], ops[j]["w"])]
+        assert producers and lines[producers[-1]].split()[2] != "permute"
+    _check(ops)
+    return n
+
+
+def test_in_place_a_steps_of_the_batched_plans():
+    """The same invariants over the stored plans of the uneven batch's heavy circuits (the ones the
+    batched executor runs in 3xTF32)."""
+    from paper_2110_09894_gb300 import qx
+    total = 0
+    for j in range(0, 256, 3):
+        w = W.batched_circuit(j)
+        if w.peak_rank <= 18 or w.n_qubits > 26:
+            continue
+        lines = _plan_lines(qx, w.n_qubits, w.gates, w.open_mask, w.order, w.sliced, 1)
+        total += _gather_invariants(lines)
+    assert total > 0
