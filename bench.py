@@ -5,8 +5,9 @@ Default workload: the 36-qubit 6x6 grid circuit of depth 14 with qubits
 30..35 left open (64 amplitudes per contraction) and 10 sliced bonds (1024
 slices, each contracted and summed in FP64), in the 3xTF32 tensor-core form
 with the plain complex64 form and the split-BF16 and FP16-scaled forms timed
-beside it, under its stored local-search plan (`--plan greedy` gives the
-seeded greedy order).  `--workload sliced` runs the 20-qubit 4x5 grid circuit
+beside it, under its stored annealed plan (`--plan local-search` gives the
+plan it was annealed from, with the sliced bonds of the workload's seeded
+plan; `--plan greedy` the seeded greedy order).  `--workload sliced` runs the 20-qubit 4x5 grid circuit
 of depth 12 with 6 sliced bonds for 256 random bitstrings, under its stored
 checkpoint plan.  One step = one
 full contraction of the workload (every slice for every bitstring) from
@@ -58,8 +59,10 @@ def parse():
     p.add_argument("--precision", default="3xtf32", choices=list(PRECISIONS),
                    help="contraction form (3xtf32 and bf16x3 meet the 1e-5 tolerance; fp16 is reported)")
     p.add_argument("--executor", default="auto", choices=["auto", "batched", "persistent"])
-    p.add_argument("--plan", default="auto", choices=["auto", "level-aware", "greedy", "checkpoint", "local-search"],
-                   help="auto: the large workload's stored local-search plan, the sliced workload's stored "
+    p.add_argument("--plan", default="auto",
+                   choices=["auto", "level-aware", "greedy", "checkpoint", "local-search", "annealed"],
+                   help="auto: the large workload's stored annealed plan (its local-search plan annealed over the "
+                        "contraction tree and the choice of the 10 sliced bonds), the sliced workload's stored "
                         "checkpoint plan (its level-aware plan improved by local search: each slice's environment "
                         "contracted once, little work per bitstring); level-aware: the seeded greedy candidate that "
                         "executes the fewest flops per call; greedy: the seeded greedy order of the workload "
@@ -83,7 +86,9 @@ def workload(name, plan="auto"):
         return W.sliced_level_aware()
     if name == "sliced" and plan in ("auto", "checkpoint"):
         return W.sliced_checkpoint()
-    if name == "large" and plan in ("auto", "local-search"):
+    if name == "large" and plan in ("auto", "annealed"):
+        return W.large_annealed()
+    if name == "large" and plan == "local-search":
         return W.large_local_search()
     return {"small": W.small, "sliced": W.sliced, "large": W.large}[name]()
 
@@ -724,7 +729,8 @@ def main():
     # oracle's partial sum stored by tests/golden/make_large_golden.py (which calls only the oracle)
     parity = None
     if args.workload == "large":
-        gname = "large_ls_slices0_31.json" if w.name.endswith("_ls") else "large_slices0_31.json"
+        gname = {"_ls": "large_ls_slices0_31.json", "_sa": "large_sa_slices0_31.json"}.get(w.name[-3:],
+                                                                                          "large_slices0_31.json")
         gpath = os.path.join(ROOT, "tests", "golden", gname)
         if os.path.exists(gpath):
             with open(gpath) as f:

@@ -458,3 +458,78 @@ def local_search_plan(legs, order, sliced, n_outputs, n_bits, max_peak, iters, s
         else:
             children[p], children[x] = old_p, old_x
     return _tree_to_order(n, children, root), best, accepted
+
+
+def sliceable_bonds(legs, n_outputs, open_edges=()):
+    """Bonds a plan may slice: bonds between two tensors, other than the final wires of closed qubits
+    (their output vectors fix them already) and open legs."""
+    deg = {}
+    for L in legs:
+        for e in L:
+            deg[e] = deg.get(e, 0) + 1
+    no_slice = set(open_edges) | {legs[t][0] for t in range(len(legs) - n_outputs, len(legs))}
+    return sorted(e for e, d in deg.items() if d == 2 and e not in no_slice)
+
+
+def anneal_plan(legs, order, sliced, n_outputs, n_bits, max_peak, iters, seed, objective, candidates=(),
+                p_swap=0.0, t_start=3e-3, t_end=1e-5):
+    """Simulated annealing over the contraction tree and the choice of sliced bonds (this project's own
+    planner step; the paper's planner fixes the sliced bonds by tree trimming, which minimises the
+    largest intermediate, not the work a call executes once slice-invariant steps run once).
+
+    Each iteration draws a uniform u for the acceptance test, then with probability p_swap replaces one
+    sliced bond (a seeded draw) by a bond of `candidates` not sliced yet -- the number of sliced bonds,
+    and so of slices, stays -- and otherwise applies one seeded tree rotation ((A, B), C) -> ((A, C), B)
+    as local_search_plan does.  A candidate whose intermediates all fit max_peak legs is accepted when
+    it costs no more, or else when u < exp(-(cost - current) / T), with T falling geometrically from
+    t_start to t_end times the starting cost over the iterations.  objective: a function (legs, order,
+    sliced, n_outputs, n_bits) -> cost.  Returns (order, sliced, cost, accepted moves) of the cheapest
+    plan visited."""
+    n = len(legs)
+    children, root = _order_to_tree(n, order)
+    internal = sorted(children)
+    cands = list(candidates)
+    sliced = list(sliced)
+    cur = objective(legs, order, sliced, n_outputs, n_bits)
+    c0 = cur
+    best, best_order, best_sliced = cur, list(order), list(sliced)
+    rng = SplitMix64(seed)
+    accepted = 0
+    for i in range(iters):
+        T = c0 * t_start * (t_end / t_start) ** (i / max(1, iters - 1))
+        u = rng.uniform()
+        if rng.uniform() < p_swap:
+            j = rng.randint(len(sliced))
+            e = cands[rng.randint(len(cands))]
+            if e in sliced:
+                continue
+            new_sl = list(sliced)
+            new_sl[j] = e
+            cand = _tree_to_order(n, children, root)
+            c = objective(legs, cand, new_sl, n_outputs, n_bits) if plan_cost(legs, cand, new_sl)[0] <= max_peak \
+                else None
+            if c is not None and (c <= cur or u < math.exp(-(c - cur) / T)):
+                cur, sliced = c, new_sl
+                accepted += 1
+                if c < best:
+                    best, best_order, best_sliced = c, cand, list(sliced)
+            continue
+        p = internal[rng.randint(len(internal))]
+        a, b = children[p]
+        x, y = (a, b) if rng.randint(2) == 0 else (b, a)  # x: the child to open, y: its sibling
+        if x < n:
+            continue
+        xa, xb = children[x]
+        keep, move = (xa, xb) if rng.randint(2) == 0 else (xb, xa)
+        old_p, old_x = children[p], children[x]
+        children[x], children[p] = (keep, y), (x, move)
+        cand = _tree_to_order(n, children, root)
+        c = objective(legs, cand, sliced, n_outputs, n_bits) if plan_cost(legs, cand, sliced)[0] <= max_peak else None
+        if c is not None and (c <= cur or u < math.exp(-(c - cur) / T)):
+            cur = c
+            accepted += 1
+            if c < best:
+                best, best_order, best_sliced = c, cand, list(sliced)
+        else:
+            children[p], children[x] = old_p, old_x
+    return best_order, best_sliced, best, accepted

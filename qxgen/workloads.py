@@ -195,6 +195,25 @@ def large_local_search():
 
 
 @functools.lru_cache(maxsize=None)
+def large_annealed():
+    """The large workload (6x6 depth 14, qubits 30..35 open, 10 sliced bonds, the same bitstring) under
+    the local-search plan annealed over its contraction tree and the choice of its 10 sliced bonds
+    (qxgen/plans/grid6x6_d14_s10_open6_sa.json): 1024 slices of other sub-networks, whose sum is the
+    same amplitude vector (Eq. 2), with most steps independent of the slice."""
+    from .plan import sliceable_bonds
+    base = large()
+    order, sliced, peak, flops, executed, d = _load_stored_plan("grid6x6_d14_s10_open6_sa.json", base.circuit,
+                                                                base.open_mask, len(base.bitstrings))
+    legs, _, open_edges = network_legs(base.n_qubits, [g.qubits for g in base.circuit.gates], base.open_mask)
+    ok = set(sliceable_bonds(legs, base.n_qubits - len(open_edges), open_edges))
+    if len(sliced) != len(base.sliced) or len(set(sliced)) != len(sliced) or not set(sliced) <= ok:
+        raise ValueError("stored plan does not slice 10 distinct sliceable bonds")
+    return Workload("grid6x6_d14_s10_open6_sa", base.circuit, base.open_mask, order, sliced, base.bitstrings, peak,
+                    flops, {"plan": "local-search plan annealed over its tree and its sliced bonds (stored)",
+                            "executed_flops": executed, "made_by": d["made_by"]})
+
+
+@functools.lru_cache(maxsize=None)
 def large():
     cseed = 3001
     circ = random_grid_circuit(6, 6, 14, cseed)

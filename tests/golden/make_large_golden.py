@@ -4,12 +4,16 @@ Calls only the oracle (complex128 plan einsum, compensated slice sum) on the
 seeded workload: `greedy` follows qxgen.workloads.large() (its seeded greedy
 order; several minutes of CPU) into large_slices0_31.json, `ls` follows
 qxgen.workloads.large_local_search() (the stored local-search order of the
-same sliced bonds; about a minute) into large_ls_slices0_31.json.  Each file
+same sliced bonds; about a minute) into large_ls_slices0_31.json, `sa`
+follows qxgen.workloads.large_annealed() (the stored annealed plan, which
+slices other bonds) into large_sa_slices0_31.json.  Each file
 carries a digest of its plan so a changed planner is detected instead of
 silently compared against stale values.  The two orders contract the same 32
-sub-networks (Eq. 2), so the two files agree to complex128 rounding.
+sub-networks (Eq. 2), so the two files agree to complex128 rounding; the
+annealed plan's slices 0..31 are other sub-networks, so its file holds
+another partial sum.
 
-    python tests/golden/make_large_golden.py [greedy] [ls]
+    python tests/golden/make_large_golden.py [greedy] [ls] [sa]
 """
 import hashlib
 import json
@@ -35,7 +39,7 @@ def plan_digest(w):
 
 
 def main(which="greedy", n_slices=32):
-    w = workloads.large() if which == "greedy" else workloads.large_local_search()
+    w = {"greedy": workloads.large, "ls": workloads.large_local_search, "sa": workloads.large_annealed}[which]()
     amps = einsum.amplitudes(w.n_qubits, w.gates, w.open_mask, w.order, w.sliced, w.bitstrings,
                              slices=range(n_slices))
     out = {
@@ -47,7 +51,7 @@ def main(which="greedy", n_slices=32):
         "im": amps[0].imag.tolist(),
         "source": "oracle.einsum.amplitudes (complex128, Neumaier slice sum)",
     }
-    name = f"large_slices0_{n_slices - 1}.json" if which == "greedy" else f"large_ls_slices0_{n_slices - 1}.json"
+    name = f"large_slices0_{n_slices - 1}.json" if which == "greedy" else f"large_{which}_slices0_{n_slices - 1}.json"
     with open(os.path.join(HERE, name), "w") as f:
         json.dump(out, f, indent=1)
 

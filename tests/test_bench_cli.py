@@ -23,7 +23,7 @@ def test_reference_arm_prints_one_contract_line():
                 "cpu_baseline", "e2e"):
         assert key in d, key
     assert d["impl"] == "reference" and d["metric"] == "amplitudes/s" and d["value"] > 0
-    assert d["config"]["workload"] == "grid6x6_d14_s10_open6_ls"
+    assert d["config"]["workload"] == "grid6x6_d14_s10_open6_sa"
     assert d["config"]["amplitudes_per_gpu"] == 64 and d["config"]["slices"] == 1024
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
 

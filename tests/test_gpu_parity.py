@@ -186,13 +186,15 @@ def _golden_large(name="large_slices0_31.json"):
 
 
 LARGE_PLANS = {"greedy": ("large", "large_slices0_31.json"),
-               "local-search": ("large_local_search", "large_ls_slices0_31.json")}
+               "local-search": ("large_local_search", "large_ls_slices0_31.json"),
+               "annealed": ("large_annealed", "large_sa_slices0_31.json")}
 
 
 @pytest.mark.parametrize("plan", list(LARGE_PLANS))
 def test_large_workload_32_slices_vs_einsum_oracle(qx, plan):
-    """6x6 depth-14 workload, bench launch configuration, slices 0..31, under the seeded greedy plan
-    and under the local-search plan the benchmark runs."""
+    """6x6 depth-14 workload, bench launch configuration, slices 0..31, under the seeded greedy plan,
+    the local-search plan and the annealed plan the benchmark runs (which slices other bonds: its
+    slices 0..31 are other sub-networks, with their own golden partial sum)."""
     fn, gname = LARGE_PLANS[plan]
     w = getattr(W, fn)()
     g, ref = _golden_large(gname)

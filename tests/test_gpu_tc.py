@@ -59,11 +59,16 @@ def test_forms_with_open_legs_and_ragged_batches(qx, precision):
     assert_parity(got, ref)
 
 
-@pytest.mark.parametrize("plan", ["greedy", "local-search"])
+LARGE = {"greedy": ("large", "large_slices0_31.json"),
+         "local-search": ("large_local_search", "large_ls_slices0_31.json"),
+         "annealed": ("large_annealed", "large_sa_slices0_31.json")}
+
+
+@pytest.mark.parametrize("plan", list(LARGE))
 @pytest.mark.parametrize("precision", FORMS)
 def test_forms_on_large_workload_32_slices(qx, precision, plan):
-    w = W.large() if plan == "greedy" else W.large_local_search()
-    name = "large_slices0_31.json" if plan == "greedy" else "large_ls_slices0_31.json"
+    fn, name = LARGE[plan]
+    w = getattr(W, fn)()
     with open(os.path.join(HERE, "golden", name)) as f:
         g = json.load(f)
     ref = np.array(g["re"]) + 1j * np.array(g["im"])

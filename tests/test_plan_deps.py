@@ -253,3 +253,13 @@ def test_in_place_a_steps_of_the_batched_plans():
         lines = _plan_lines(qx, w.n_qubits, w.gates, w.open_mask, w.order, w.sliced, 1)
         total += _gather_invariants(lines)
     assert total > 0
+
+
+def test_launch_list_of_the_annealed_36_qubit_plan():
+    """The benchmark's default plan (the annealed plan, which slices other bonds): its in-place A steps
+    keep the invariants above and its launch list stays ordered with every read and write."""
+    from paper_2110_09894_gb300 import qx
+    w = W.large_annealed()
+    lines = _plan_lines(qx, w.n_qubits, w.gates, w.open_mask, w.order, w.sliced, 1)
+    assert len(lines) > 100
+    _gather_invariants(lines)

@@ -144,6 +144,56 @@ def test_large_local_search_plan_keeps_the_slices_and_its_golden_agrees():
     assert np.linalg.norm(a - b) / np.linalg.norm(a) < 1e-12
 
 
+def test_large_annealed_plan_and_its_golden_follow_eq2():
+    """The stored annealed plan of the large workload slices 10 distinct bonds the library accepts
+    (1024 slices), keeps every intermediate within 2^24 entries and executes fewer flops per call than
+    the local-search plan it started from.  Its golden file (the oracle's partial sum over slices
+    0..31, written by tests/golden/make_large_golden.py) carries its digest, and by Eq. 2 equals one
+    oracle contraction in which the five sliced bonds that slices 0..31 vary are left whole and the
+    other five are fixed to 0: summing a bond's slices is not slicing it."""
+    import json
+    import os
+    from qxgen.plan import sliceable_bonds
+    from tests.golden.make_large_golden import plan_digest
+    w, w0 = W.large_annealed(), W.large_local_search()
+    legs, n_out = _legs(w)
+    _, _, open_edges = network_legs(w.n_qubits, [g.qubits for g in w.circuit.gates], w.open_mask)
+    assert len(w.sliced) == 10 and len(set(w.sliced)) == 10 and w.n_slices == 1024
+    assert set(w.sliced) <= set(sliceable_bonds(legs, n_out, open_edges)) and w.peak_rank <= 24
+    assert set(w.sliced) != set(w0.sliced)
+    assert w.meta["executed_flops"] < w0.meta["executed_flops"]
+    here = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+    with open(os.path.join(here, "large_sa_slices0_31.json")) as f:
+        g = json.load(f)
+    assert g["plan_sha256"] == plan_digest(w) and g["slices"] == [0, 32]
+    ref = np.array(g["re"]) + 1j * np.array(g["im"])
+    whole = oe.amplitudes(w.n_qubits, w.gates, w.open_mask, w.order, w.sliced[5:], w.bitstrings, slices=[0])[0]
+    assert np.linalg.norm(whole - ref) / np.linalg.norm(ref) < 1e-12
+
+
+def test_anneal_plan_keeps_the_slice_count_and_finds_a_cheaper_plan():
+    """anneal_plan on the 20-qubit sliced circuit (six sliced bonds, executed flops as the cost): the
+    result slices six distinct sliceable bonds, fits the peak, costs no more than the start, and the
+    einsum oracle under it reproduces the state vector (any order and any sliced set give the same
+    amplitudes, Eq. 2)."""
+    from qxgen.plan import anneal_plan, plan_cost, sliceable_bonds
+    w = W.sliced()
+    legs, n_out = _legs(w)
+    _, _, open_edges = network_legs(w.n_qubits, [g.qubits for g in w.circuit.gates], w.open_mask)
+    cands = sliceable_bonds(legs, n_out, open_edges)
+    nb = 4
+    start = executed_cost(legs, w.order, w.sliced, n_out, nb)
+    order, sliced, cost, acc = anneal_plan(legs, w.order, w.sliced, n_out, nb, 16, 600, 5, executed_cost,
+                                           cands, p_swap=0.3)
+    assert len(sliced) == len(w.sliced) and len(set(sliced)) == len(sliced) and set(sliced) <= set(cands)
+    assert plan_cost(legs, order, sliced)[0] <= 16 and acc > 0
+    assert cost == executed_cost(legs, order, sliced, n_out, nb) <= start
+    bits = w.bitstrings[:nb]
+    ref = oracle.sv_amplitudes(w.n_qubits, w.gates, w.open_mask, bits)
+    got = oe.amplitudes(w.n_qubits, w.gates, w.open_mask, order, sliced, bits)
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 1e-10
+
+
 def test_executed_time_reduces_to_executed_flops_with_one_rate():
     """With every kernel family at one rate, unbounded memory bandwidth and no launch cost, the time
     estimate is the executed flops over that rate (the same levels and multiplicities); the memory
