@@ -1,6 +1,6 @@
 """Write the stored plans of qxgen/plans/ (plans are inputs; the paper keeps them in files).
 
-    python -m qxgen.make_plans [checkpoint] [large] [annealed] [batched] [serving]
+    python -m qxgen.make_plans [checkpoint] [large] [annealed] [batched] [batched-annealed] [serving]
 
 grid4x5_d12_s6_checkpoint.json: the 20-qubit sliced circuit (4x5 grid, depth
 12, six sliced bonds, 256 bitstrings) under the level-aware plan improved by
@@ -21,6 +21,11 @@ choice of 10 sliced bonds (80000 iterations, about 40 minutes of host time).
 batched_uneven.json: the 256 circuits of the batched workload, each under
 its level-aware plan improved by local search on the time estimate (about
 half an hour of host time on 7 processes).
+
+batched_annealed.json: the heaviest of those circuits under their stored
+plans annealed on the compiled launch-list time over the tree and the
+choice of their sliced bonds (the drawn number kept); the workload uses
+these entries in place of batched_uneven.json's.
 
 serving.json: the 32 resident circuits of the serving workload, each under
 the seeded greedy candidate that, sliced until its intermediates fit 2^30
@@ -133,6 +138,54 @@ def batched_plan(j, trials=20, iters=20000):
             "estimated_s": t}
 
 
+def batched_annealed_plan(j, seed, iters, t_start, start="stored"):
+    """Circuit j of the batched workload: a starting order -- its stored plan (batched_uneven.json), or
+    with start="sweep" the state-vector-like sweep_order with the stored sliced bonds -- annealed on the
+    compiled launch-list time of a 3xTF32 call (qxgen.compiled_cost) over its contraction tree and, when
+    it slices bonds, its choice of them (swap probability 0.15; the drawn number kept), every
+    intermediate within 2^28 entries."""
+    from .compiled_cost import CompiledTime
+    from .plan import anneal_plan, executed_cost, plan_cost, sliceable_bonds, sweep_order
+    w = W.batched_circuit(j, annealed=False)
+    circ = w.circuit
+    gq = [g.qubits for g in circ.gates]
+    legs, _, open_edges = network_legs(circ.n_qubits, gq, w.open_mask)
+    n_out = circ.n_qubits - len(open_edges)
+    nb = len(w.bitstrings)
+    order0 = sweep_order(legs, circ.n_qubits, n_out, gq) if start == "sweep" else w.order
+    obj = CompiledTime(circ.n_qubits, w.gates, w.open_mask, precision=1)
+    stored = obj(legs, w.order, w.sliced, n_out, nb)
+    p_swap = 0.15 if w.sliced else 0.0
+    order, sliced, t, _ = anneal_plan(legs, order0, w.sliced, n_out, nb, BATCHED_MAX_PEAK, iters, seed, obj,
+                                      sliceable_bonds(legs, n_out, open_edges), p_swap, t_start, 1e-5)
+    obj.close()
+    return {"j": j, "circuit_sha256": W.circuit_digest(circ), "order": [list(p) for p in order],
+            "sliced": [int(e) for e in sliced], "n_bits": nb, "max_peak": BATCHED_MAX_PEAK,
+            "peak": plan_cost(legs, order, sliced)[0], "executed_flops": int(executed_cost(legs, order, sliced, n_out, nb)),
+            "estimated_s": t, "stored_estimated_s": stored,
+            "made_by": f"{'sweep_order' if start == 'sweep' else 'the stored plan'} + anneal_plan ({iters} iterations, "
+                       f"seed {seed}, swap probability {p_swap}, temperature {t_start} -> 1e-05 of the starting "
+                       f"cost, compiled launch-list time)"}
+
+
+# (circuit, seed, iterations, starting temperature, start) of the batched workload's annealed plans:
+# its heaviest circuits by estimated time; the rest keep their batched_uneven.json plans
+BATCHED_ANNEALED = ()
+
+
+def _annealed_entry(args):
+    return batched_annealed_plan(*args)
+
+
+def batched_annealed_plans(workers=7):
+    import multiprocessing as mp
+    with mp.get_context("spawn").Pool(workers) as pool:
+        plans = pool.map(_annealed_entry, BATCHED_ANNEALED, chunksize=1)
+    return {"made_by": "the heaviest circuits' stored plans annealed on the compiled launch-list time "
+                       "(batched_annealed_plan); an entry replaces the circuit's plan in batched_uneven.json",
+            "plans": plans}
+
+
 def batched_plans(workers=7):
     import multiprocessing as mp
     with mp.get_context("spawn").Pool(workers) as pool:
@@ -199,6 +252,12 @@ if __name__ == "__main__":
         with open(path, "w") as f:
             json.dump(d, f)
         print(path, [round(p["estimated_s"], 3) for p in d["plans"]])
+    if "batched-annealed" in which:
+        d = batched_annealed_plans()
+        path = os.path.join(HERE, "batched_annealed.json")
+        with open(path, "w") as f:
+            json.dump(d, f)
+        print(path, [(p["j"], round(p["stored_estimated_s"], 3), round(p["estimated_s"], 3)) for p in d["plans"]])
     if "batched" in which:
         d = batched_plans()
         path = os.path.join(HERE, "batched_uneven.json")

@@ -533,3 +533,63 @@ def anneal_plan(legs, order, sliced, n_outputs, n_bits, max_peak, iters, seed, o
         else:
             children[p], children[x] = old_p, old_x
     return best_order, best_sliced, best, accepted
+
+
+def sweep_order(legs, n_qubits, n_outputs, gate_qubits):
+    """A state-vector-like contraction order (this project's own starting point for annealing): the
+    gates that touch no closed output wire are contracted onto the tensors holding their qubits in
+    circuit order, one-qubit gates first merged with the next two-qubit gate on their qubit, so the
+    growing tensor never has more legs than there are qubits; the gates of the final layer with their
+    output vectors come last.  Every step below the final layer reaches no output bit, so without
+    sliced bonds it runs once per call and each bitstring adds only the final layer's contractions.
+    gate_qubits: the qubits of each gate, in the order network_legs was given them."""
+    n = len(legs)
+    first_out = n - n_outputs
+    out_of = {legs[t][0]: t for t in range(first_out, n)}
+    order = []
+
+    def join(a, b):
+        order.append((a, b))
+        return n + len(order) - 1
+
+    holder = list(range(n_qubits))  # tensor holding each qubit's wire (its input tensor at first)
+    pend = {}                       # one-qubit gates on a qubit not yet merged into a larger gate
+    gates = range(n_qubits, first_out)
+    final = [t for t in gates if any(e in out_of for e in legs[t])]
+    fset = set(final)
+
+    def apply(cur, qs):
+        for q in qs:
+            if q in pend:
+                cur = join(cur, pend.pop(q))
+        hs = []
+        for q in qs:
+            if holder[q] not in hs:
+                hs.append(holder[q])
+        for h in hs:
+            cur = join(h, cur)
+        for q in range(n_qubits):
+            if holder[q] in hs:
+                holder[q] = cur
+
+    for t in gates:
+        if t in fset:
+            continue
+        qs = gate_qubits[t - n_qubits]
+        if len(qs) == 1:
+            pend[qs[0]] = join(pend[qs[0]], t) if qs[0] in pend else t
+        else:
+            apply(t, qs)
+    for f in final:
+        qs = gate_qubits[f - n_qubits]
+        cur = f
+        for e in legs[f][:len(qs)]:
+            if e in out_of:
+                cur = join(cur, out_of[e])
+        apply(cur, qs)
+    for q in sorted(pend):  # open qubits' trailing one-qubit gates
+        apply(pend.pop(q), [q])
+    roots = sorted(set(holder))
+    while len(roots) > 1:
+        roots = [join(roots[0], roots[1])] + roots[2:]
+    return order

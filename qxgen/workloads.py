@@ -259,15 +259,32 @@ def _batched_plans():
 
 
 @functools.lru_cache(maxsize=None)
-def batched_circuit(j):
-    """Circuit j of the batched workload under its stored plan (qxgen/plans/batched_uneven.json, written
-    by qxgen.make_plans: level-aware candidates + local search on the time estimate), checked against
-    the circuit and its recorded cost."""
+def _batched_annealed_plans():
+    """The annealed plans of the batched workload's heaviest circuits, by circuit index (may be empty)."""
+    import json
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "plans", "batched_annealed.json")
+    if not os.path.exists(path):
+        return {}
+    with open(path) as f:
+        return {d["j"]: d for d in json.load(f)["plans"]}
+
+
+@functools.lru_cache(maxsize=None)
+def batched_circuit(j, annealed=True):
+    """Circuit j of the batched workload under its stored plan, checked against the circuit and its
+    recorded cost: qxgen/plans/batched_annealed.json for the heaviest circuits (their plans annealed over
+    the tree and the choice of their sliced bonds, the drawn number kept), else
+    qxgen/plans/batched_uneven.json (level-aware candidates + local search on the time estimate; both
+    written by qxgen.make_plans).  annealed=False gives the latter for every circuit."""
     g = batched_circuit_greedy(j)
-    d = _batched_plans()[j]
+    d = _batched_annealed_plans().get(j) if annealed else None
+    d = d or _batched_plans()[j]
     n, depth, s, nb = batched_specs()[j]
     if d["j"] != j or d["circuit_sha256"] != circuit_digest(g.circuit) or d["n_bits"] != nb or len(d["sliced"]) != s:
         raise ValueError(f"stored plan {j} was made for another circuit")
+    if len(set(d["sliced"])) != s:
+        raise ValueError(f"stored plan {j} repeats a sliced bond")
     order = [tuple(p) for p in d["order"]]
     legs, _, open_edges = network_legs(n, [x.qubits for x in g.circuit.gates], g.open_mask)
     peak, flops = plan_cost(legs, order, d["sliced"])

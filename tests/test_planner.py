@@ -15,7 +15,7 @@ import pytest
 import oracle
 from oracle import einsum as oe
 from qxgen import workloads as W
-from qxgen.plan import executed_cost, network_legs
+from qxgen.plan import executed_cost, network_legs, plan_cost
 
 
 def _legs(w):
@@ -192,6 +192,45 @@ def test_anneal_plan_keeps_the_slice_count_and_finds_a_cheaper_plan():
     ref = oracle.sv_amplitudes(w.n_qubits, w.gates, w.open_mask, bits)
     got = oe.amplitudes(w.n_qubits, w.gates, w.open_mask, order, sliced, bits)
     assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 1e-10
+
+
+def test_sweep_order_contracts_the_network_with_the_qubit_count_as_peak():
+    """sweep_order on grid circuits with and without open qubits and sliced bonds: a full SSA order
+    (every tensor used once), no intermediate above n legs, every step below the final layer
+    independent of the bitstring, and the einsum oracle under it reproduces the state vector."""
+    from qxgen.plan import sweep_order
+    from tests._util import grid_case
+    from qxgen import circuits as C
+    for rows, cols, depth, n_open, n_slice, n_bits, seed in ((3, 3, 8, 0, 0, 5, 1), (3, 4, 6, 2, 2, 3, 2),
+                                                             (2, 5, 9, 0, 1, 4, 3)):
+        circ, om, _, sliced, bits = grid_case(rows, cols, depth, seed, n_open, n_slice, n_bits)
+        gq = [g.qubits for g in circ.gates]
+        legs, _, open_edges = network_legs(circ.n_qubits, gq, om)
+        n_out = circ.n_qubits - len(open_edges)
+        order = sweep_order(legs, circ.n_qubits, n_out, gq)
+        n = len(legs)
+        used = [x for p in order for x in p]
+        assert len(order) == n - 1 and sorted(used) == list(range(2 * n - 2))
+        assert plan_cost(legs, order)[0] <= circ.n_qubits
+        recs = C.gates_to_records(circ)
+        ref = oracle.sv_amplitudes(circ.n_qubits, recs, om, bits)
+        got = oe.amplitudes(circ.n_qubits, recs, om, order, sliced, bits)
+        assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 1e-10
+    # the steps that reach an output bit (their subtree holds an output vector) come last, after every
+    # bitstring-independent step; without sliced bonds a bitstring then adds a small part of a call
+    circ, om, _, _, _ = grid_case(3, 4, 12, 4, 0, 0, 1)
+    gq = [g.qubits for g in circ.gates]
+    legs, _, open_edges = network_legs(circ.n_qubits, gq, om)
+    n = len(legs)
+    order = sweep_order(legs, circ.n_qubits, circ.n_qubits, gq)
+    reach = [t >= n - circ.n_qubits for t in range(n)]
+    for a, b in order:
+        reach.append(reach[a] or reach[b])
+    steps = reach[n:]
+    first = steps.index(True)
+    assert all(steps[first:]) and first > len(steps) // 2
+    one, many = executed_cost(legs, order, [], circ.n_qubits, 1), executed_cost(legs, order, [], circ.n_qubits, 64)
+    assert (many - one) / 63 < one / 4
 
 
 def test_executed_time_reduces_to_executed_flops_with_one_rate():
