@@ -67,7 +67,9 @@ def parse():
                         "contracted once, little work per bitstring); level-aware: the seeded greedy candidate that "
                         "executes the fewest flops per call; greedy: the seeded greedy order of the workload "
                         "definition")
-    p.add_argument("--no-forms", action="store_true", help="skip timing the other tensor-core forms beside")
+    p.add_argument("--no-forms", action="store_true",
+                   help="skip timing the other forms beside (the large workload's split-BF16 and FP16-scaled "
+                        "forms; the batched workload's plain complex64 run)")
     p.add_argument("--slices", type=int, default=0,
                    help="contract only slices 0..S-1 per step (a smaller case of the same launches, for profiling; "
                         "the workload name then says so); 0 = all")
@@ -344,7 +346,7 @@ def group_bench(args):
                   "worst_rel_l2": worst_l2, "worst_max_elem_over_rms": worst_el}
     # the same members in plain complex64 (heavy members on the SIMT kernels), same settings
     vs_c64 = None
-    if prec != 0:
+    if prec != 0 and not args.no_forms:
         b64 = UnevenBatch(ws, precision=0, ctas_per_sm=choice["ctas_per_sm"],
                           settings={int(i): s for i, s in choice["settings"].items()})
         b64.capture()

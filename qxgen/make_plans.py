@@ -170,7 +170,13 @@ def batched_annealed_plan(j, seed, iters, t_start, start="stored"):
 
 # (circuit, seed, iterations, starting temperature, start) of the batched workload's annealed plans:
 # its heaviest circuits by estimated time; the rest keep their batched_uneven.json plans
-BATCHED_ANNEALED = ()
+BATCHED_ANNEALED = ((39, 1, 20000, 0.003, "sweep"), (71, 1, 20000, 0.003, "sweep"), (72, 1072, 20000, 0.01, "stored"),
+                    (73, 73, 20000, 0.003, "stored"), (91, 1, 20000, 0.003, "sweep"), (94, 1, 20000, 0.003, "sweep"),
+                    (102, 1, 20000, 0.003, "sweep"), (120, 120, 30000, 0.003, "stored"),
+                    (125, 1125, 20000, 0.01, "stored"), (137, 1, 20000, 0.003, "sweep"),
+                    (146, 146, 30000, 0.003, "stored"), (149, 1, 20000, 0.003, "sweep"),
+                    (162, 1, 20000, 0.003, "sweep"), (170, 2, 20000, 0.003, "sweep"), (181, 2, 20000, 0.003, "sweep"),
+                    (223, 1, 20000, 0.003, "sweep"), (243, 1243, 60000, 0.01, "stored"))
 
 
 def _annealed_entry(args):

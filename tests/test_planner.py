@@ -233,6 +233,36 @@ def test_sweep_order_contracts_the_network_with_the_qubit_count_as_peak():
     assert (many - one) / 63 < one / 4
 
 
+def test_batched_annealed_plans_keep_their_circuits_slices_and_peak():
+    """The annealed plans of the batched workload's heaviest circuits (qxgen/plans/batched_annealed.json)
+    replace their stored plans: each keeps its circuit's drawn number of sliced bonds (distinct bonds the
+    library accepts), every intermediate within 2^28 entries, and its recorded launch-list estimate is
+    below the stored plan's; the library compiles each (host-only handle) and the compiled launch list
+    stays ordered with every read and write.  Their amplitudes are checked against the state vectors on
+    the GPU (the 256-circuit test)."""
+    import json
+    import os
+    from qxgen.plan import sliceable_bonds
+    from paper_2110_09894_gb300 import qx
+    from tests.test_plan_deps import _check, _parse, _plan_lines
+    path = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "qxgen", "plans",
+                        "batched_annealed.json")
+    with open(path) as f:
+        plans = json.load(f)["plans"]
+    assert len(plans) >= 5
+    specs = W.batched_specs()
+    for d in plans:
+        j = d["j"]
+        w, w0 = W.batched_circuit(j), W.batched_circuit(j, annealed=False)
+        assert [tuple(p) for p in d["order"]] == list(w.order) and list(w.sliced) == d["sliced"]
+        legs, n_out = _legs(w)
+        _, _, open_edges = network_legs(w.n_qubits, [g.qubits for g in w.circuit.gates], w.open_mask)
+        assert len(w.sliced) == specs[j][2] == len(w0.sliced) and len(set(w.sliced)) == len(w.sliced)
+        assert set(w.sliced) <= set(sliceable_bonds(legs, n_out, open_edges)) and w.peak_rank <= 28
+        assert d["estimated_s"] < d["stored_estimated_s"]
+        _check(_parse(_plan_lines(qx, w.n_qubits, w.gates, w.open_mask, w.order, w.sliced, 1)))
+
+
 def test_executed_time_reduces_to_executed_flops_with_one_rate():
     """With every kernel family at one rate, unbounded memory bandwidth and no launch cost, the time
     estimate is the executed flops over that rate (the same levels and multiplicities); the memory
