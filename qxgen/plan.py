@@ -15,6 +15,13 @@ supplies stand-ins that produce valid plans for the synthetic workloads:
   that shrinks the largest intermediate; among those prefer the one in the
   most largest intermediates, then the one in the most intermediates, then
   the one saving the most total memory, then a seeded random choice.
+* ``level_aware_plan`` / ``local_search_plan`` / ``anneal_plan``: plans
+  ranked by what a call executes when steps run at their dependence level
+  (``executed_cost``, ``executed_time`` or the library's compiled launch
+  list), improved by seeded tree rotations and, in ``anneal_plan``, swaps of
+  sliced bonds under a cooling Metropolis rule; ``sweep_order`` is a
+  state-vector-like starting order whose steps below the final layer reach
+  no output bit.
 
 Only index bookkeeping lives here (which bond sits on which tensor); no
 tensor values are touched.  The network labelling below is the canonical
