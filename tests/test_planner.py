@@ -185,6 +185,9 @@ def test_anneal_plan_keeps_the_slice_count_and_finds_a_cheaper_plan():
     start = executed_cost(legs, w.order, w.sliced, n_out, nb)
     order, sliced, cost, acc = anneal_plan(legs, w.order, w.sliced, n_out, nb, 16, 600, 5, executed_cost,
                                            cands, p_swap=0.3)
+    # the same seed gives the same plan (plans are inputs written once and checked on load)
+    assert anneal_plan(legs, w.order, w.sliced, n_out, nb, 16, 600, 5, executed_cost, cands, p_swap=0.3) == \
+        (order, sliced, cost, acc)
     assert len(sliced) == len(w.sliced) and len(set(sliced)) == len(sliced) and set(sliced) <= set(cands)
     assert plan_cost(legs, order, sliced)[0] <= 16 and acc > 0
     assert cost == executed_cost(legs, order, sliced, n_out, nb) <= start
