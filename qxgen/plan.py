@@ -592,11 +592,16 @@ def sweep_order(legs, n_qubits, n_outputs, gate_qubits):
         cur = f
         for e in legs[f][:len(qs)]:
             if e in out_of:
-                cur = join(cur, out_of[e])
+                cur = join(cur, out_of.pop(e))
         apply(cur, qs)
     for q in sorted(pend):  # open qubits' trailing one-qubit gates
         apply(pend.pop(q), [q])
+    for q in range(n_qubits):  # closed qubits without gates: the output vector meets the input
+        if q in out_of:
+            apply(out_of.pop(q), [q])
     roots = sorted(set(holder))
     while len(roots) > 1:
         roots = [join(roots[0], roots[1])] + roots[2:]
+    if len(order) != n - 1:
+        raise ValueError("sweep_order: the network is not one contraction tree")
     return order

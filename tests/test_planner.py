@@ -219,6 +219,16 @@ def test_sweep_order_contracts_the_network_with_the_qubit_count_as_peak():
         ref = oracle.sv_amplitudes(circ.n_qubits, recs, om, bits)
         got = oe.amplitudes(circ.n_qubits, recs, om, order, sliced, bits)
         assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 1e-10
+    # a closed qubit that no gate touches: its output vector meets its input directly
+    circ = C.random_grid_circuit(1, 3, 4, 7)
+    gq = [g.qubits for g in circ.gates]
+    om = np.zeros(4, np.uint8)
+    legs, _, _ = network_legs(4, gq, om)
+    order = sweep_order(legs, 4, 4, gq)
+    recs = C.gates_to_records(circ)
+    bits = C.random_bitstrings(4, 3, 1)
+    ref = oracle.sv_amplitudes(4, recs, om, bits)
+    assert np.abs(oe.amplitudes(4, recs, om, order, [], bits) - ref).max() < 1e-12
     # the steps that reach an output bit (their subtree holds an output vector) come last, after every
     # bitstring-independent step; without sliced bonds a bitstring then adds a small part of a call
     circ, om, _, _, _ = grid_case(3, 4, 12, 4, 0, 0, 1)
